@@ -1,0 +1,256 @@
+/*
+ * cdl.h -- C ABI of the GB300 (sm_103a) CADDeLaG hot path.
+ *
+ * The library computes, on one GPU, the commute-time embedding of dense,
+ * fully connected similarity graphs and the CAD anomaly scores between two
+ * graphs (Basak, Das, Mengshoel, "CADDeLaG: Framework for distributed anomaly
+ * detection in large dense graph sequences", arXiv 1802.05421):
+ *
+ *   cdl_build_graph   Gaussian-kernel graph A, degrees D = A 1, volume
+ *                     (Sec. 2; kernel of Sec. 4.2.1; D = A 1 of Sec. 3.2)
+ *   cdl_chain_build   inverse-chain levels of Alg. 2, ChainProduct
+ *   cdl_project       random projection Y = (Q W^{1/2} B)^T of Alg. 1 / Alg. 3
+ *   cdl_chain_solve   L Z = Y by chain-preconditioned Richardson iteration
+ *                     (Alg. 2, EstimateSolution; multi-RHS loop of Sec. 3.3)
+ *   cdl_cad_score     node scores F_i = sum_j |A1-A2|_ij |c2-c1|_ij and the
+ *                     top anomalies (Alg. 4; CAD edge score of Sec. 2)
+ *   cdl_caddelag_pair the whole of Alg. 4 for one graph pair
+ *
+ * Conventions (all entry points):
+ *  - Return value: CDL_OK (0) or a negative CDL_ERR_* status.
+ *  - Pointers named "device" are CUDA device pointers on the context's
+ *    device; "host" pointers are ordinary host memory. The caller owns every
+ *    pointer it passes. The library owns cdl_ctx, cdl_chain and the
+ *    workspace inside them, and nothing else.
+ *  - Matrices are dense and row-major: element (i, j) of an n x n matrix is
+ *    at i * n + j; Y and Z (n x k) hold node i's k values in row i.
+ *  - Work is enqueued asynchronously on the context's stream unless the
+ *    entry point says it synchronises. cdl_sync() waits and reports deferred
+ *    device errors. A call that fails validation launches nothing.
+ *  - There is no CPU fallback and no silent change of precision.
+ */
+#ifndef CDL_H
+#define CDL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  CDL_OK = 0,
+  CDL_ERR_INVALID_ARG = -1,   /* bad size, null or misaligned pointer, bad enum  */
+  CDL_ERR_OOM = -2,           /* device allocation failed or workspace cap hit   */
+  CDL_ERR_CUDA = -3,          /* a CUDA runtime/driver call failed               */
+  CDL_ERR_NOT_CONVERGED = -4, /* solve stopped at max_iter above rel_tol         */
+  CDL_ERR_TIMEOUT = -5,       /* a bounded device-side wait expired              */
+  CDL_ERR_UNSUPPORTED = -6    /* valid request this build does not implement     */
+};
+
+typedef enum {
+  CDL_F64 = 0,      /* IEEE binary64                                    */
+  CDL_F32 = 1,      /* IEEE binary32                                    */
+  CDL_BF16 = 2,     /* bfloat16, tensor-core chain (tcgen05)            */
+  CDL_FP8E4M3 = 3   /* float8 e4m3 (reserved; returns UNSUPPORTED)      */
+} cdl_dtype;
+
+typedef struct cdl_ctx cdl_ctx;
+typedef struct cdl_chain cdl_chain;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a borrowed
+ * cudaStream_t (NULL = the legacy default stream); every kernel of every call
+ * on this context is launched on it. `ws_cap_bytes` caps the device workspace
+ * the context may allocate (0 = no cap); a call that would exceed it returns
+ * CDL_ERR_OOM without launching. *out receives the context. */
+int cdl_ctx_create(cdl_ctx** out, int device, void* cuda_stream, size_t ws_cap_bytes);
+
+/* Synchronise the stream, free all workspace and the context. NULL is a no-op. */
+int cdl_ctx_destroy(cdl_ctx* ctx);
+
+/* Wait for all work on the context's stream; returns CDL_ERR_CUDA on a
+ * deferred device error and CDL_ERR_TIMEOUT if a kernel reported an expired
+ * bounded wait (the kernel returned early; the context stays usable). */
+int cdl_sync(cdl_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* cdl_status_string(int status);
+
+/* Text of the last CUDA failure recorded by the calling thread (the CUDA
+ * error string and where it was caught); empty if none. Diagnostics only. */
+const char* cdl_last_error_detail(void);
+
+/* Kernel-class timing. With timing enabled (nonzero), every launch is
+ * bracketed by CUDA events on the context's stream and its duration is
+ * added to the class totals when they are read. `cdl_ctx_timing` synchronises
+ * and returns, for class `kernel_class` (CDL_KC_*), the summed device time in
+ * ms, the number of launches and the algorithmic work (flops or bytes, see
+ * CDL_KC_*) those launches performed. `cdl_ctx_reset_counters` zeroes all
+ * class totals and the launch counter. */
+enum {
+  CDL_KC_DISTANCE = 0,   /* pairwise squared distances; work = n^2/2 T terms  */
+  CDL_KC_SELECT = 1,     /* median radix select; work = bytes read             */
+  CDL_KC_KERNEL = 2,     /* exp kernel + degrees; work = bytes moved           */
+  CDL_KC_CHAIN_INIT = 3, /* deflated level-0 formation; work = bytes moved     */
+  CDL_KC_SQUARE = 4,     /* chain squaring GEMM; work = flops (n^2 (n+1))      */
+  CDL_KC_APPLY = 5,      /* chain apply GEMM; work = bytes of levels read      */
+  CDL_KC_RESIDUAL = 6,   /* Y - L Z; work = multiply-adds n^2 k                */
+  CDL_KC_PROJECT = 7,    /* random projection; work = n(n-1) k signed adds     */
+  CDL_KC_SCORE = 8,      /* CAD scores; work = bytes of A1, A2 read            */
+  CDL_KC_TOPK = 9,
+  CDL_KC_MISC = 10,      /* small vector kernels (norms, centring, updates)    */
+  CDL_KC_COUNT = 11
+};
+int cdl_ctx_set_timing(cdl_ctx* ctx, int enable);
+int cdl_ctx_timing(cdl_ctx* ctx, int kernel_class, double* total_ms, int64_t* launches,
+                   double* work);
+int cdl_ctx_reset_counters(cdl_ctx* ctx);
+/* Total kernels this context launched since creation or the last reset. */
+int cdl_ctx_launch_count(cdl_ctx* ctx, int64_t* launches);
+
+/* ---------------------------------------------------------------- graph */
+
+/* Gaussian-kernel graph of n node series (Sec. 4.2.1 kernel; Sec. 2: no
+ * self edges; Sec. 3.2: D = A 1; Eq. 1: vol = sum_i D_i):
+ *   A_ij = exp(-||x_i - x_j||^2 / (2 sigma^2)) for i != j, A_ii = 0,
+ *   D_i = sum_j A_ij, vol = sum_i D_i.
+ * X:  device, n x T float64 row-major (node i's series in row i).
+ * sigma: kernel width; sigma <= 0 selects the lower median of the
+ *   n(n-1)/2 distances ||x_i - x_j||, i < j (exact selection).
+ * a_dtype: must be CDL_F64 (A is always produced in float64).
+ * A:  device, n x n float64 output. D: device, n float64 output.
+ * vol, sigma_out: device, one float64 each (sigma_out receives the sigma used).
+ * Squared distances are exact when every x is a multiple of 2^-16 below 2^7
+ * in magnitude (int64 arithmetic); otherwise they are computed in float64
+ * with one rounding per subtraction, product and sum, samples in order.
+ * Requires 2 <= n <= 2^20, 1 <= T <= 4096. */
+int cdl_build_graph(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, double sigma,
+                    cdl_dtype a_dtype, void* A, double* D, double* vol, double* sigma_out);
+
+/* ---------------------------------------------------------------- chain */
+
+/* Inverse chain of Alg. 2 (ChainProduct) for M = L = D - A.
+ * Stored levels are the deflated powers
+ *   S~_0 = D^{-1/2} A D^{-1/2} - u u^T,  u = D^{1/2} 1 / sqrt(vol),
+ *   S~_{i+1} = S~_i S~_i,  i = 0 .. d-2,
+ * which equal S^{2^i} - u u^T (u is the eigenvector of S for eigenvalue 1)
+ * and act like S^{2^i} on every vector D^{-1/2} b with b orthogonal to the
+ * ones vector, the only vectors the solve applies them to.
+ * A (device, n x n, a_dtype = CDL_F64), D (device, n), vol (device, 1).
+ * chain_dtype: CDL_F64, CDL_F32 (CUDA-core GEMM) or CDL_BF16 (tcgen05
+ *   tensor-core GEMM, float32 accumulation, bfloat16 levels).
+ * flags: CDL_CHAIN_* below.
+ * inout: if *inout is NULL a chain is allocated (cdl_chain_free releases it);
+ *   if it points to a chain created with the same (n, d, chain_dtype) its
+ *   storage is reused; any other chain returns CDL_ERR_INVALID_ARG.
+ * Levels occupy d * npad^2 elements, npad = n rounded up to 256. */
+enum { CDL_CHAIN_DEFAULT = 0 };
+int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double* D,
+                    const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
+                    int32_t flags, cdl_chain** inout);
+int cdl_chain_free(cdl_chain* chain);
+/* Device pointer to level i (npad x npad, chain dtype, zero padded) and npad. */
+int cdl_chain_level(const cdl_chain* chain, int32_t i, void** level, int64_t* npad);
+
+/* ---------------------------------------------------------------- projection */
+
+/* Random projection of Alg. 1 (line "y = W^{1/2} B q") and Alg. 3, formed
+ * edge by edge without materialising B or Q (Sec. 3.3: Map + ReduceByKey):
+ *   Y[i, r] = k^{-1/2} sum_{j != i} o_ij s_r(min(i,j), max(i,j)) sqrt(A_ij),
+ * o_ij = +1 if i < j (edge (i,j) has head i, tail j; Sec. 2), -1 otherwise.
+ * s_r(i, j) = +1 if bit (r mod 32) of word ((r mod 128) / 32) of
+ * Philox4x32-10(counter = (i, j, r / 128, 0), key = (seed & 0xffffffff,
+ * seed >> 32)) is set, else -1.
+ * A: device n x n (a_dtype = CDL_F64). Y: device n x k float64 output.
+ * Requires 1 <= k <= 1024. */
+int cdl_project(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, int64_t n, int32_t k,
+                uint64_t seed, double* Y);
+
+/* ---------------------------------------------------------------- solve */
+
+typedef struct {
+  int32_t max_iter;   /* preconditioner applications, >= 1 (paper's q - 1)   */
+  double rel_tol;     /* stop when ||Y - L Z||_F <= rel_tol ||Y||_F; 0 = run
+                         exactly max_iter applications                       */
+  int32_t flags;      /* reserved, 0                                         */
+} cdl_solve_opts;
+
+typedef struct {
+  int32_t iters;              /* preconditioner applications performed        */
+  double rel_res;             /* final ||Y - L Z||_F / ||Y||_F                 */
+  double history[64];         /* rel_res after each application (first iters) */
+} cdl_solve_stats;
+
+/* Solve L Z = Y (L = D - A, Y's columns orthogonal to the ones vector) with
+ * the chain as preconditioner P (Alg. 2, EstimateSolution, all k right-hand
+ * sides at once as in Sec. 3.3):
+ *   Z_0 = 0;  Z_{t+1} = Z_t + P (Y - L Z_t),
+ *   P R = D^{-1/2} prod_{i<d} (I + S~_i) D^{-1/2} R,
+ * then Z is shifted to D-weighted zero column means (sum_i D_i Z[i,:] = 0).
+ * For Z_0 = 0 this is the paper's y_{t+1} = y_t - P2 y_t + chi with
+ * chi = P1 b and P2 = P1 L. The residual Y - L Z is formed in float-float
+ * arithmetic (about 48 significant bits) from float64 A, D, Y, Z.
+ * Synchronises once per application to read the residual norm.
+ * chain: from cdl_chain_build on the same graph. A: device n x n (CDL_F64).
+ * Y: device n x k float64. Z: device n x k float64 output.
+ * stats: host, may be NULL. Returns CDL_ERR_NOT_CONVERGED (Z still written)
+ * when rel_tol > 0 was not reached within max_iter applications. */
+int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* chain, const void* A, cdl_dtype a_dtype,
+                    const double* Y, int32_t k, const cdl_solve_opts* opts, double* Z,
+                    cdl_solve_stats* stats);
+
+/* ---------------------------------------------------------------- scores */
+
+/* CAD scores between two graphs on the same nodes (Alg. 4; Sec. 2):
+ *   c_t(i,j) = vol_t ||Z_t[i,:] - Z_t[j,:]||^2   (Eq. 1 via the embedding),
+ *   F_i = sum_{j != i} |A1_ij - A2_ij| * |c_2(i,j) - c_1(i,j)|,
+ * and top_idx = the `topk` nodes of highest F, ties to the lower index.
+ * The commute-time difference is formed as (a_i - a_j).(b_i - b_j) with
+ * a = sqrt(vol2) Z2 - sqrt(vol1) Z1 and b = sqrt(vol2) Z2 + sqrt(vol1) Z1,
+ * which avoids cancelling two large commute times.
+ * score_dtype: CDL_F64 forms the k-term products and sums in float64;
+ *   CDL_F32 forms them in float32 from float-float a and b (about 1e-7
+ *   relative per pair, much faster on this GPU). Scores accumulate in float64.
+ * A1, A2: device n x n (CDL_F64). Z1, Z2: device n x k float64.
+ * vol1, vol2: device, one float64 each. F: device n float64 output.
+ * top_idx: device topk int64 output (may be NULL when topk == 0).
+ * Requires 0 <= topk <= min(n, 1024). */
+int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtype,
+                  const double* Z1, const double* Z2, const double* vol1, const double* vol2,
+                  int64_t n, int32_t k, cdl_dtype score_dtype, int32_t topk, double* F,
+                  int64_t* top_idx);
+
+/* ---------------------------------------------------------------- Alg. 4 */
+
+typedef struct {
+  int32_t k;               /* projection dimension                          */
+  int32_t d;               /* chain length (levels)                         */
+  cdl_dtype chain_dtype;   /* CDL_F64, CDL_F32 or CDL_BF16                  */
+  cdl_dtype score_dtype;   /* CDL_F64 or CDL_F32 (see cdl_cad_score)        */
+  uint64_t seed;           /* projection seed, shared by both graphs        */
+  double sigma;            /* <= 0: median rule per graph                   */
+  cdl_solve_opts solve;
+  int32_t topk;
+  int32_t host_io;         /* 1: X1, X2, F, top_idx are host pointers and
+                              the call copies them in and out (synchronous);
+                              0: device pointers (asynchronous)            */
+} cdl_pair_opts;
+
+/* One graph pair end to end (Alg. 4): graph build, chain, projection and
+ * solve for each graph (Alg. 3), then scores and top anomalies.
+ * X1, X2: n x T float64 (host or device per host_io). F: n float64,
+ * top_idx: topk int64 (host or device per host_io). stats1/stats2: host
+ * solve statistics, may be NULL. Device buffers (graphs, chain, embeddings)
+ * are owned by the context and reused across calls with the same sizes. */
+int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T,
+                      const cdl_pair_opts* opts, double* F, int64_t* top_idx,
+                      cdl_solve_stats* stats1, cdl_solve_stats* stats2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDL_H */

@@ -1,0 +1,193 @@
+"""ctypes binding of libcdl (the C ABI declared in include/cdl.h).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name and returns its integer status. Array arguments may be
+given as integers (raw pointers), as objects with ``data_ptr()`` (torch
+tensors) or ``ctypes.data`` (NumPy arrays), or as None (NULL). The library
+must have been built (``python -m paper_1802_05421_gb300.build``); importing
+this module without it raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdl.so")
+
+CDL_OK = 0
+CDL_ERR_INVALID_ARG = -1
+CDL_ERR_OOM = -2
+CDL_ERR_CUDA = -3
+CDL_ERR_NOT_CONVERGED = -4
+CDL_ERR_TIMEOUT = -5
+CDL_ERR_UNSUPPORTED = -6
+
+CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3 = 0, 1, 2, 3
+
+(CDL_KC_DISTANCE, CDL_KC_SELECT, CDL_KC_KERNEL, CDL_KC_CHAIN_INIT, CDL_KC_SQUARE, CDL_KC_APPLY,
+ CDL_KC_RESIDUAL, CDL_KC_PROJECT, CDL_KC_SCORE, CDL_KC_TOPK, CDL_KC_MISC, CDL_KC_COUNT) = range(12)
+KERNEL_CLASSES = ["distance", "select", "kernel", "chain_init", "square", "apply", "residual",
+                  "project", "score", "topk", "misc"]
+
+
+class cdl_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double), ("flags", ctypes.c_int32)]
+
+
+class cdl_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("history", ctypes.c_double * 64)]
+
+
+class cdl_pair_opts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("d", ctypes.c_int32), ("chain_dtype", ctypes.c_int),
+                ("score_dtype", ctypes.c_int), ("seed", ctypes.c_uint64), ("sigma", ctypes.c_double), ("solve", cdl_solve_opts),
+                ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcdl.so not built at {LIB_PATH}; run python -m paper_1802_05421_gb300.build")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_SIGS = {
+    "cdl_ctx_create": [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_size_t],
+    "cdl_ctx_destroy": [_P],
+    "cdl_sync": [_P],
+    "cdl_ctx_set_timing": [_P, ctypes.c_int],
+    "cdl_ctx_timing": [_P, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_D)],
+    "cdl_ctx_reset_counters": [_P],
+    "cdl_ctx_launch_count": [_P, ctypes.POINTER(_I64)],
+    "cdl_build_graph": [_P, _P, _I64, _I32, _D, ctypes.c_int, _P, _P, _P, _P],
+    "cdl_chain_build": [_P, _P, ctypes.c_int, _P, _P, _I64, _I32, ctypes.c_int, _I32, ctypes.POINTER(_P)],
+    "cdl_chain_free": [_P],
+    "cdl_chain_level": [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
+    "cdl_project": [_P, _P, ctypes.c_int, _I64, _I32, ctypes.c_uint64, _P],
+    "cdl_chain_solve": [_P, _P, _P, ctypes.c_int, _P, _I32, ctypes.POINTER(cdl_solve_opts), _P,
+                        ctypes.POINTER(cdl_solve_stats)],
+    "cdl_cad_score": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _I32, _P, _P],
+    "cdl_caddelag_pair": [_P, _P, _P, _I64, _I32, ctypes.POINTER(cdl_pair_opts), _P, _P,
+                          ctypes.POINTER(cdl_solve_stats), ctypes.POINTER(cdl_solve_stats)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.cdl_status_string.argtypes = [ctypes.c_int]
+_lib.cdl_status_string.restype = ctypes.c_char_p
+_lib.cdl_last_error_detail.argtypes = []
+_lib.cdl_last_error_detail.restype = ctypes.c_char_p
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    if isinstance(x, ctypes.c_void_p):
+        return x.value
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def cdl_status_string(status: int) -> str:
+    return _lib.cdl_status_string(status).decode()
+
+
+def cdl_last_error_detail() -> str:
+    return _lib.cdl_last_error_detail().decode()
+
+
+def cdl_ctx_create(device: int = 0, stream=None, ws_cap_bytes: int = 0):
+    """Returns (status, ctx handle)."""
+    h = _P()
+    st = _lib.cdl_ctx_create(ctypes.byref(h), device, _ptr(stream), ws_cap_bytes)
+    return st, h
+
+
+def cdl_ctx_destroy(ctx) -> int:
+    return _lib.cdl_ctx_destroy(ctx)
+
+
+def cdl_sync(ctx) -> int:
+    return _lib.cdl_sync(ctx)
+
+
+def cdl_ctx_set_timing(ctx, enable: bool) -> int:
+    return _lib.cdl_ctx_set_timing(ctx, int(enable))
+
+
+def cdl_ctx_timing(ctx, kernel_class: int):
+    """Returns (status, total_ms, launches, work)."""
+    ms, n, w = _D(), _I64(), _D()
+    st = _lib.cdl_ctx_timing(ctx, kernel_class, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w))
+    return st, ms.value, n.value, w.value
+
+
+def cdl_ctx_reset_counters(ctx) -> int:
+    return _lib.cdl_ctx_reset_counters(ctx)
+
+
+def cdl_ctx_launch_count(ctx):
+    n = _I64()
+    st = _lib.cdl_ctx_launch_count(ctx, ctypes.byref(n))
+    return st, n.value
+
+
+def cdl_build_graph(ctx, X, n, T, sigma, a_dtype, A, D, vol, sigma_out) -> int:
+    return _lib.cdl_build_graph(ctx, _ptr(X), n, T, sigma, a_dtype, _ptr(A), _ptr(D), _ptr(vol),
+                                _ptr(sigma_out))
+
+
+def cdl_chain_build(ctx, A, a_dtype, D, vol, n, d, chain_dtype, flags=0, chain=None):
+    """Returns (status, chain handle). Pass ``chain`` to rebuild into it."""
+    h = chain if chain is not None else _P()
+    st = _lib.cdl_chain_build(ctx, _ptr(A), a_dtype, _ptr(D), _ptr(vol), n, d, chain_dtype, flags,
+                              ctypes.byref(h))
+    return st, h
+
+
+def cdl_chain_free(chain) -> int:
+    return _lib.cdl_chain_free(chain)
+
+
+def cdl_chain_level(chain, i):
+    """Returns (status, device pointer, npad)."""
+    p, npad = _P(), _I64()
+    st = _lib.cdl_chain_level(chain, i, ctypes.byref(p), ctypes.byref(npad))
+    return st, p.value, npad.value
+
+
+def cdl_project(ctx, A, a_dtype, n, k, seed, Y) -> int:
+    return _lib.cdl_project(ctx, _ptr(A), a_dtype, n, k, seed, _ptr(Y))
+
+
+def cdl_chain_solve(ctx, chain, A, a_dtype, Y, k, opts: cdl_solve_opts, Z, stats=None) -> int:
+    return _lib.cdl_chain_solve(ctx, chain, _ptr(A), a_dtype, _ptr(Y), k, ctypes.byref(opts), _ptr(Z),
+                                ctypes.byref(stats) if stats is not None else None)
+
+
+def cdl_cad_score(ctx, A1, A2, a_dtype, Z1, Z2, vol1, vol2, n, k, score_dtype, topk, F,
+                  top_idx) -> int:
+    return _lib.cdl_cad_score(ctx, _ptr(A1), _ptr(A2), a_dtype, _ptr(Z1), _ptr(Z2), _ptr(vol1),
+                              _ptr(vol2), n, k, score_dtype, topk, _ptr(F), _ptr(top_idx))
+
+
+def cdl_caddelag_pair(ctx, X1, X2, n, T, opts: cdl_pair_opts, F, top_idx, stats1=None,
+                      stats2=None) -> int:
+    return _lib.cdl_caddelag_pair(ctx, _ptr(X1), _ptr(X2), n, T, ctypes.byref(opts), _ptr(F),
+                                  _ptr(top_idx),
+                                  ctypes.byref(stats1) if stats1 is not None else None,
+                                  ctypes.byref(stats2) if stats2 is not None else None)
+
+
+def exported_symbols():
+    """Names of the C entry points bound here (for the export check)."""
+    return sorted(list(_SIGS) + ["cdl_status_string", "cdl_last_error_detail"])

@@ -1,0 +1,279 @@
+// Inverse chain (Alg. 2, ChainProduct) on CUDA cores: the deflated level-0
+// formation used by every precision, the float32/float64 symmetric squaring
+// S~_{i+1} = S~_i^2 and the chain-apply products S~_i x of the solve.
+//
+// Deflation: S = D^{-1/2} A D^{-1/2} has eigenvalue 1 with unit eigenvector
+// u = D^{1/2} 1 / sqrt(vol). S~ = S - u u^T satisfies S~^{2^i} = S^{2^i} - u u^T
+// (u is orthogonal to the other eigenvectors), so the squarings of S~ give the
+// chain levels minus the u u^T part. The solve only applies the levels to
+// D^{-1/2} b with b orthogonal to 1, i.e. to vectors orthogonal to u, where
+// both act identically; without the eigenvalue 1 rounding errors are not
+// amplified by the repeated squaring.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace cdl {
+namespace {
+
+// rsqrt_d_i = D_i^{-1/2}, u_i = (D_i / vol)^{1/2}; zero in the padding.
+__global__ void k_chain_vectors(const double* __restrict__ D, const double* __restrict__ vol,
+                                int n, int npad, double* __restrict__ rsd, double* __restrict__ u) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  if (i < n) {
+    double di = D[i];
+    rsd[i] = 1.0 / sqrt(di);
+    u[i] = sqrt(di / *vol);
+  } else {
+    rsd[i] = 0.0;
+    u[i] = 0.0;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T to_level(double v);
+template <>
+__device__ __forceinline__ double to_level<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_level<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_level<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+
+// S~_0[i][j] = A_ij (rsd_i rsd_j) - u_i u_j (float64 arithmetic, each product
+// formed symmetrically in i and j so the level is exactly symmetric), zero padded.
+template <typename T>
+__global__ void __launch_bounds__(256) k_chain_init(const double* __restrict__ A, int n, int npad,
+                                                     const double* __restrict__ rsd,
+                                                     const double* __restrict__ u, T* __restrict__ L0) {
+  for (int i = blockIdx.x; i < npad; i += gridDim.x) {
+    T* out = L0 + (size_t)i * npad;
+    if (i >= n) {
+      for (int j = threadIdx.x; j < npad; j += blockDim.x) out[j] = to_level<T>(0.0);
+      continue;
+    }
+    const double ri = rsd[i], ui = u[i];
+    const double* row = A + (size_t)i * n;
+    for (int j = threadIdx.x; j < npad; j += blockDim.x) {
+      double v = 0.0;
+      if (j < n) v = row[j] * (ri * rsd[j]) - ui * u[j];
+      out[j] = to_level<T>(v);
+    }
+  }
+}
+
+__device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
+  double fnb = nb + 0.5;
+  int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
+  if (r < 0) r = 0;
+  if (r > nb - 1) r = nb - 1;
+  auto off = [nb](long long b) { return b * nb - b * (b - 1) / 2; };
+  while (r > 0 && off(r) > t) --r;
+  while (r + 1 < nb && off(r + 1) <= t) ++r;
+  bi = r;
+  bj = r + (int)(t - off(r));
+}
+
+// C = P^T Q on CUDA cores: C[m][c] = sum_k P[k][m] Q[k][c]; P is K x M and Q
+// is K x N, both row-major, so both tiles are contiguous k-major slabs.
+// SYM: P == Q == S symmetric, M == N; only tiles bi <= bj are computed and
+//      each is also written transposed (C = S^2 is symmetric).
+// Otherwise: split-K partial products, C + split * M * ldc.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool SYM>
+__global__ void __launch_bounds__(256) k_gemm_tn(const T* __restrict__ P, int ldp,
+                                                  const T* __restrict__ Q, int ldq, T* __restrict__ C,
+                                                  int ldc, int M, int N, int kchunk) {
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN];
+  int m0, c0, k0, k1;
+  bool mirror = false;
+  if (SYM) {
+    int bi, bj;
+    tri_index(blockIdx.x, M / BM, bi, bj);
+    m0 = bi * BM;
+    c0 = bj * BN;
+    mirror = bi != bj;
+    k0 = 0;
+    k1 = kchunk;
+  } else {
+    m0 = blockIdx.x * BM;
+    c0 = blockIdx.y * BN;
+    k0 = blockIdx.z * kchunk;
+    k1 = k0 + kchunk;
+    C += (size_t)blockIdx.z * M * ldc;
+  }
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  constexpr int A_LD = BM * BK / 256;   // elements each thread loads per tile
+  constexpr int B_LD = BN * BK / 256;
+  T ra[A_LD], rb[B_LD];
+  auto gload = [&](int kt) {
+#pragma unroll
+    for (int e = 0; e < A_LD; ++e) {
+      int idx = tid + e * 256;
+      int kk = idx / BM, mm = idx % BM;
+      ra[e] = P[(size_t)(kt + kk) * ldp + m0 + mm];
+    }
+#pragma unroll
+    for (int e = 0; e < B_LD; ++e) {
+      int idx = tid + e * 256;
+      int kk = idx / BN, cc = idx % BN;
+      int c = c0 + cc;
+      rb[e] = (c < N) ? Q[(size_t)(kt + kk) * ldq + c] : T(0);
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < A_LD; ++e) {
+      int idx = tid + e * 256;
+      As[buf][idx / BM][idx % BM] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < B_LD; ++e) {
+      int idx = tid + e * 256;
+      Bs[buf][idx / BN][idx % BN] = rb[e];
+    }
+  };
+  T acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+  gload(k0);
+  sstore(0);
+  __syncthreads();
+  int buf = 0;
+  for (int kt = k0; kt < k1; kt += BK) {
+    const bool more = kt + BK < k1;
+    if (more) gload(kt + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T av[TM], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM / 2; ++a) {
+        av[a] = As[buf][kk][ty * (TM / 2) + a];
+        av[TM / 2 + a] = As[buf][kk][BM / 2 + ty * (TM / 2) + a];
+      }
+#pragma unroll
+      for (int b = 0; b < TN / 2; ++b) {
+        bv[b] = Bs[buf][kk][tx * (TN / 2) + b];
+        bv[TN / 2 + b] = Bs[buf][kk][BN / 2 + tx * (TN / 2) + b];
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    if (more) {
+      sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    int m = m0 + (a < TM / 2 ? ty * (TM / 2) + a : BM / 2 + ty * (TM / 2) + a - TM / 2);
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      int c = c0 + (b < TN / 2 ? tx * (TN / 2) + b : BN / 2 + tx * (TN / 2) + b - TN / 2);
+      if (c < N) {
+        C[(size_t)m * ldc + c] = acc[a][b];
+        if (SYM && mirror) C[(size_t)c * ldc + m] = acc[a][b];
+      }
+    }
+  }
+}
+
+template <typename T>
+int square_impl(cdl_ctx* ctx, cdl_chain* ch, int level) {
+  const int np = (int)ch->npad;
+  const T* S = static_cast<const T*>(ch->level(level));
+  T* C = static_cast<T*>(ch->level(level + 1));
+  const double flops = (double)ch->n * ch->n * (ch->n + 1.0);   // symmetric product
+  if constexpr (sizeof(T) == 4) {
+    constexpr int B = 128;
+    const int nb = np / B;
+    Launch L(ctx, CDL_KC_SQUARE, flops);
+    k_gemm_tn<T, B, B, 8, 8, 8, true><<<nb * (nb + 1) / 2, 256, 0, ctx->stream>>>(S, np, S, np, C, np, np, np, np);
+    return L.done();
+  } else {
+    constexpr int B = 64;
+    const int nb = np / B;
+    Launch L(ctx, CDL_KC_SQUARE, flops);
+    k_gemm_tn<T, B, B, 8, 4, 4, true><<<nb * (nb + 1) / 2, 256, 0, ctx->stream>>>(S, np, S, np, C, np, np, np, np);
+    return L.done();
+  }
+}
+
+}  // namespace
+
+int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
+  const int n = (int)ch->n, np = (int)ch->npad;
+  void* wsu;
+  CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * sizeof(double), &wsu));
+  double* u = static_cast<double*>(wsu);
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_chain_vectors<<<(np + 255) / 256, 256, 0, ctx->stream>>>(ch->D, ch->vol, n, np, ch->rsqrt_d, u);
+    CDL_TRY(L.done());
+  }
+  const double bytes = 8.0 * n * (double)n + (double)ch->elem * np * (double)np;
+  const int blocks = std::min(np, ctx->sm_count * 8);
+  Launch L(ctx, CDL_KC_CHAIN_INIT, bytes);
+  switch (ch->dtype) {
+    case CDL_F64:
+      k_chain_init<double><<<blocks, 256, 0, ctx->stream>>>(A, n, np, ch->rsqrt_d, u,
+                                                            static_cast<double*>(ch->level(0)));
+      break;
+    case CDL_F32:
+      k_chain_init<float><<<blocks, 256, 0, ctx->stream>>>(A, n, np, ch->rsqrt_d, u,
+                                                           static_cast<float*>(ch->level(0)));
+      break;
+    case CDL_BF16:
+      k_chain_init<__nv_bfloat16><<<blocks, 256, 0, ctx->stream>>>(
+          A, n, np, ch->rsqrt_d, u, static_cast<__nv_bfloat16*>(ch->level(0)));
+      break;
+    default:
+      return CDL_ERR_UNSUPPORTED;
+  }
+  return L.done();
+}
+
+int chain_square_simt(cdl_ctx* ctx, cdl_chain* ch, int level) {
+  if (ch->dtype == CDL_F32) return square_impl<float>(ctx, ch, level);
+  if (ch->dtype == CDL_F64) return square_impl<double>(ctx, ch, level);
+  return CDL_ERR_UNSUPPORTED;
+}
+
+// partial[s] = (level_i)^T x restricted to k-range s (level_i is symmetric, so
+// this is level_i x). x: npad x kp row-major in the chain's dtype.
+int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void* partial, int kp,
+               int splits) {
+  const int np = (int)ch->npad;
+  const int kchunk = np / splits;
+  const double bytes = (double)ch->elem * np * (double)np;
+  if (ch->dtype == CDL_F32) {
+    constexpr int BM = 128, BN = 64;
+    dim3 grid(np / BM, (kp + BN - 1) / BN, splits);
+    Launch L(ctx, CDL_KC_APPLY, bytes);
+    k_gemm_tn<float, BM, BN, 8, 8, 4, false><<<grid, 256, 0, ctx->stream>>>(
+        static_cast<const float*>(ch->level(level)), np, static_cast<const float*>(x), kp,
+        static_cast<float*>(partial), kp, np, kp, kchunk);
+    return L.done();
+  }
+  if (ch->dtype == CDL_F64) {
+    constexpr int BM = 64, BN = 64;
+    dim3 grid(np / BM, (kp + BN - 1) / BN, splits);
+    Launch L(ctx, CDL_KC_APPLY, bytes);
+    k_gemm_tn<double, BM, BN, 8, 4, 4, false><<<grid, 256, 0, ctx->stream>>>(
+        static_cast<const double*>(ch->level(level)), np, static_cast<const double*>(x), kp,
+        static_cast<double*>(partial), kp, np, kp, kchunk);
+    return L.done();
+  }
+  return CDL_ERR_UNSUPPORTED;
+}
+
+}  // namespace cdl

@@ -1,0 +1,350 @@
+// Graph build (Sec. 2; kernel of Sec. 4.2.1; D = A 1 of Sec. 3.2):
+//   1. squared distances ||x_i - x_j||^2 for all pairs (upper-triangle tiles,
+//      mirrored), exact in int64 when X lies on the 2^-16 grid, otherwise in
+//      float64 with one rounding per subtraction, product and sum;
+//   2. sigma = lower median of the distances over i < j by an exact radix
+//      select on the float64 bit patterns (distances are >= 0, so their bit
+//      patterns order like the values);
+//   3. A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = sum_j A_ij, vol.
+#include <cmath>
+
+#include "internal.h"
+
+namespace cdl {
+namespace {
+
+constexpr int DT = 64;          // distance tile (rows and columns)
+constexpr int DTK = 32;         // samples per smem chunk
+constexpr int RADIX_BITS = 12;
+constexpr int RADIX_BINS = 1 << RADIX_BITS;
+
+struct SelectState {
+  unsigned long long prefix;    // selected high bits so far
+  unsigned long long mask;      // which bits are selected
+  long long rank;               // rank within the still-matching keys
+  int flags;                    // bit 0: input off the 2^-16 grid
+  int pad;
+};
+
+// X (float64, n x T) -> int32 fixed point a = x * 2^16, stored transposed
+// (T x n) for coalesced tile loads; flags input off the grid.
+__global__ void k_to_fixed(const double* __restrict__ X, int* __restrict__ Xt, int n, int T,
+                           SelectState* st) {
+  const size_t total = (size_t)n * T;
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  bool off = false;
+  for (; idx < total; idx += stride) {
+    double a = X[idx] * 65536.0;   // exact scaling by a power of two
+    bool ok = (a == rint(a)) && fabs(a) < 8388608.0;
+    off |= !ok;
+    size_t i = idx / T, t = idx % T;
+    Xt[t * n + i] = ok ? (int)a : 0;
+  }
+  if (__syncthreads_or(off) && threadIdx.x == 0) atomicOr(&st->flags, 1);
+}
+
+__device__ __forceinline__ void tri_index(long long t, int nb, int& bi, int& bj) {
+  // t enumerates (bi, bj), bi <= bj, row by row; row bi starts at
+  // off(bi) = bi*nb - bi*(bi-1)/2.
+  double fnb = nb + 0.5;
+  int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
+  if (r < 0) r = 0;
+  if (r > nb - 1) r = nb - 1;
+  auto off = [nb](long long b) { return b * nb - b * (b - 1) / 2; };
+  while (r > 0 && off(r) > t) --r;
+  while (r + 1 < nb && off(r + 1) <= t) ++r;
+  bi = r;
+  bj = r + (int)(t - off(r));
+}
+
+// Exact squared distances on the 2^-16 grid: int64 sums of squared int32
+// differences, written as float64 multiples of 2^-32 to both (i,j) and (j,i).
+__global__ void __launch_bounds__(256) k_dist_int(const int* __restrict__ Xt, int n, int T,
+                                                   double* __restrict__ A, const SelectState* st) {
+  if (st->flags & 1) return;   // off-grid input: the float64 kernel handles it
+  __shared__ __align__(16) int As[DTK][DT];
+  __shared__ __align__(16) int Bs[DTK][DT];
+  const int nb = (n + DT - 1) / DT;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = bi * DT, c0 = bj * DT;
+  long long acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+  for (int t0 = 0; t0 < T; t0 += DTK) {
+    // load 32 samples x 64 nodes of each side from the transposed copy
+    for (int e = threadIdx.x; e < DT * DTK; e += 256) {
+      int row = e % DT, tt = e / DT;
+      int ia = r0 + row, ib = c0 + row, t = t0 + tt;
+      As[tt][row] = (ia < n && t < T) ? Xt[(size_t)t * n + ia] : 0;
+      Bs[tt][row] = (ib < n && t < T) ? Xt[(size_t)t * n + ib] : 0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int tt = 0; tt < DTK; ++tt) {
+      int4 a = *reinterpret_cast<const int4*>(&As[tt][ty * 4]);
+      int4 b = *reinterpret_cast<const int4*>(&Bs[tt][tx * 4]);
+      int av[4] = {a.x, a.y, a.z, a.w};
+      int bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          int dd = av[u] - bv[v];
+          acc[u][v] += (long long)dd * dd;
+        }
+    }
+    __syncthreads();
+  }
+  const double q = 1.0 / 4294967296.0;   // 2^-32
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int i = r0 + ty * 4 + u;
+    if (i >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int j = c0 + tx * 4 + v;
+      if (j >= n) continue;
+      double d2 = (double)acc[u][v] * q;
+      A[(size_t)i * n + j] = d2;
+      if (bi != bj) A[(size_t)j * n + i] = d2;
+    }
+  }
+}
+
+// Float64 squared distances for inputs off the grid: same tiling, samples in
+// ascending order, explicit round-to-nearest operations (no contraction).
+__global__ void __launch_bounds__(256) k_dist_f64(const double* __restrict__ X, int n, int T,
+                                                   double* __restrict__ A, const SelectState* st) {
+  if (!(st->flags & 1)) return;
+  __shared__ double As[DTK][DT + 1];
+  __shared__ double Bs[DTK][DT + 1];
+  const int nb = (n + DT - 1) / DT;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = bi * DT, c0 = bj * DT;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int t0 = 0; t0 < T; t0 += DTK) {
+    for (int e = threadIdx.x; e < DT * DTK; e += 256) {
+      int row = e / DTK, tt = e % DTK;
+      int ia = r0 + row, ib = c0 + row, t = t0 + tt;
+      As[tt][row] = (ia < n && t < T) ? X[(size_t)ia * T + t] : 0.0;
+      Bs[tt][row] = (ib < n && t < T) ? X[(size_t)ib * T + t] : 0.0;
+    }
+    __syncthreads();
+    const int tmax = min(DTK, T - t0);
+    for (int tt = 0; tt < tmax; ++tt) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double dd = __dsub_rn(As[tt][ty * 4 + u], Bs[tt][tx * 4 + v]);
+          acc[u][v] = __dadd_rn(acc[u][v], __dmul_rn(dd, dd));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int i = r0 + ty * 4 + u;
+    if (i >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int j = c0 + tx * 4 + v;
+      if (j >= n) continue;
+      A[(size_t)i * n + j] = acc[u][v];
+      if (bi != bj) A[(size_t)j * n + i] = acc[u][v];
+    }
+  }
+}
+
+__global__ void k_select_init(SelectState* st, long long rank) {
+  st->prefix = 0;
+  st->mask = 0;
+  st->rank = rank;
+  st->flags = 0;
+}
+
+// Histogram of the `bits`-wide digit at `shift` over keys of the upper
+// triangle matching the current prefix.
+__global__ void __launch_bounds__(512) k_select_hist(const double* __restrict__ A, int n, int shift,
+                                                      int bits, const SelectState* __restrict__ st,
+                                                      unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int h[RADIX_BINS];
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  const unsigned long long dmask = (1ull << bits) - 1ull;
+  const unsigned long long* K = reinterpret_cast<const unsigned long long*>(A);
+  for (int i = blockIdx.x; i < n - 1; i += gridDim.x) {
+    const unsigned long long* row = K + (size_t)i * n;
+    for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      unsigned long long key = row[j];
+      if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & dmask], 1u);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+}
+
+// Pick the bin holding the remaining rank; extend the prefix; clear hist.
+__global__ void k_select_step(SelectState* st, unsigned long long* hist, int shift, int bits,
+                              double* sigma_out, int last) {
+  __shared__ unsigned long long cnt[RADIX_BINS];
+  const int nbins = 1 << bits;
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) {
+    cnt[b] = hist[b];
+    hist[b] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long r = st->rank;
+    int b = 0;
+    for (; b < nbins; ++b) {
+      if ((long long)cnt[b] > r) break;
+      r -= (long long)cnt[b];
+    }
+    if (b >= nbins) b = nbins - 1;   // unreachable for a consistent histogram
+    unsigned long long dm = (unsigned long long)(nbins - 1) << shift;
+    st->prefix |= (unsigned long long)b << shift;
+    st->mask |= dm;
+    st->rank = r;
+    if (last) {
+      double d2 = __longlong_as_double((long long)st->prefix);
+      *sigma_out = sqrt(d2);
+    }
+  }
+}
+
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+
+// A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = row sum. One block per row.
+__global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int n,
+                                                      const double* __restrict__ sigma,
+                                                      double* __restrict__ D) {
+  __shared__ double red[8];
+  const double s = *sigma;
+  const double two_s2 = 2.0 * (s * s);
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    double* row = A + (size_t)i * n;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double a = (j == i) ? 0.0 : exp(-(row[j] / two_s2));
+      row[j] = a;
+      acc += a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      D[i] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// vol = sum_i D_i (single block, fixed order per thread then tree).
+__global__ void k_sum(const double* __restrict__ v, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+}  // namespace
+
+int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma, double* A,
+                double* D, double* vol, double* sigma_out) {
+  const int n = (int)n64;
+  cudaStream_t s = ctx->stream;
+  void *wsXi, *wsSt, *wsHist;
+  CDL_TRY(ws_get(ctx, "graph.Xi", (size_t)n * T * sizeof(int), &wsXi));
+  CDL_TRY(ws_get(ctx, "graph.state", sizeof(SelectState), &wsSt));
+  CDL_TRY(ws_get(ctx, "graph.hist", RADIX_BINS * sizeof(unsigned long long), &wsHist));
+  SelectState* st = static_cast<SelectState*>(wsSt);
+  unsigned long long* hist = static_cast<unsigned long long*>(wsHist);
+  const long long m = (long long)n * (n - 1) / 2;
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_select_init<<<1, 1, 0, s>>>(st, (m - 1) / 2);
+    CDL_TRY(L.done());
+  }
+  CDL_CUDA_TRY(cudaMemsetAsync(hist, 0, RADIX_BINS * sizeof(unsigned long long), s));
+  {
+    size_t total = (size_t)n * T;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->sm_count * 8);
+    Launch L(ctx, CDL_KC_DISTANCE, 0);
+    k_to_fixed<<<blocks, 256, 0, s>>>(X, static_cast<int*>(wsXi), n, T, st);
+    CDL_TRY(L.done());
+  }
+  const int nb = (n + DT - 1) / DT;
+  const long long tiles = (long long)nb * (nb + 1) / 2;
+  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  const double terms = 0.5 * (double)n * (double)(n - 1) * T;
+  {
+    Launch L(ctx, CDL_KC_DISTANCE, terms);
+    k_dist_int<<<(unsigned)tiles, 256, 0, s>>>(static_cast<const int*>(wsXi), n, T, A, st);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_DISTANCE, 0);
+    k_dist_f64<<<(unsigned)tiles, 256, 0, s>>>(X, n, T, A, st);
+    CDL_TRY(L.done());
+  }
+  if (sigma > 0) {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_set_scalar<<<1, 1, 0, s>>>(sigma_out, sigma);
+    CDL_TRY(L.done());
+  } else {
+    // digits from the top: [52,64), [40,52), [28,40), [16,28), [4,16), [0,4)
+    const int shifts[6] = {52, 40, 28, 16, 4, 0};
+    const int widths[6] = {12, 12, 12, 12, 12, 4};
+    const int hblocks = std::min(n - 1, ctx->sm_count * 4);
+    for (int p = 0; p < 6; ++p) {
+      {
+        Launch L(ctx, CDL_KC_SELECT, 8.0 * (double)m);
+        k_select_hist<<<hblocks, 512, 0, s>>>(A, n, shifts[p], widths[p], st, hist);
+        CDL_TRY(L.done());
+      }
+      {
+        Launch L(ctx, CDL_KC_SELECT, 0);
+        k_select_step<<<1, 256, 0, s>>>(st, hist, shifts[p], widths[p], sigma_out, p == 5);
+        CDL_TRY(L.done());
+      }
+    }
+  }
+  {
+    Launch L(ctx, CDL_KC_KERNEL, 16.0 * (double)n * n);
+    k_kernel_rows<<<std::min(n, ctx->sm_count * 8), 256, 0, s>>>(A, n, sigma_out, D);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_sum<<<1, 1024, 0, s>>>(D, n, vol);
+    CDL_TRY(L.done());
+  }
+  return CDL_OK;
+}
+
+}  // namespace cdl

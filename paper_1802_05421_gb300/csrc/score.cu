@@ -1,0 +1,341 @@
+// CAD node scores and top anomalies (Alg. 4; edge score of Sec. 2):
+//   F_i = sum_{j != i} |A1_ij - A2_ij| |c2(i,j) - c1(i,j)|,
+//   c_t(i,j) = vol_t ||Z_t[i,:] - Z_t[j,:]||^2.
+// The commute-time difference is formed without cancelling the two commute
+// times: with a = sqrt(vol2) Z2 - sqrt(vol1) Z1 and b = sqrt(vol2) Z2 +
+// sqrt(vol1) Z1 (float64, then float hi + lo), c2 - c1 = (a_i - a_j).(b_i - b_j).
+// Each unordered pair (i < j) is visited once in 64 x 64 upper-triangle
+// tiles; the two row contributions of a tile go to a per-(partner block, node)
+// slot, and F is the fixed-order sum of those slots (deterministic).
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "internal.h"
+
+namespace cdl {
+namespace {
+
+constexpr int ST = 64;   // pair tile
+constexpr int RC = 8;    // projection rows per smem chunk
+
+// aT/bT hi/lo, stored transposed (k x n) for coalesced tile loads.
+__global__ void k_score_prep(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                             const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
+                             float* __restrict__ ah, float* __restrict__ al, float* __restrict__ bh,
+                             float* __restrict__ bl) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  const int i = (int)(idx / k), r = (int)(idx % k);
+  const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
+  const double w = s2 * Z2[idx], v = s1 * Z1[idx];
+  const double a = w - v, b = w + v;
+  const float a0 = (float)a, b0 = (float)b;
+  const size_t o = (size_t)r * n + i;
+  ah[o] = a0;
+  al[o] = (float)(a - (double)a0);
+  bh[o] = b0;
+  bl[o] = (float)(b - (double)b0);
+}
+
+// float64 variant: aT, bT (k x n).
+__global__ void k_score_prep64(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                               const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
+                               double* __restrict__ aT, double* __restrict__ bT) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  const int i = (int)(idx / k), r = (int)(idx % k);
+  const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
+  const double w = s2 * Z2[idx], v = s1 * Z1[idx];
+  const size_t o = (size_t)r * n + i;
+  aT[o] = w - v;
+  bT[o] = w + v;
+}
+
+__device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
+  double fnb = nb + 0.5;
+  int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
+  if (r < 0) r = 0;
+  if (r > nb - 1) r = nb - 1;
+  auto off = [nb](long long b) { return b * nb - b * (b - 1) / 2; };
+  while (r > 0 && off(r) > t) --r;
+  while (r + 1 < nb && off(r + 1) <= t) ++r;
+  bi = r;
+  bj = r + (int)(t - off(r));
+}
+
+// Per-tile accumulation of |A1 - A2| |c2 - c1| into row and column partials.
+__device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const double* __restrict__ A2,
+                                            int n, int i0, int j0, int bi, int bj, int tx, int ty,
+                                            const double (&dc)[4][4], double* __restrict__ contrib,
+                                            double (*rsum)[17], double (*csum)[17]) {
+  double rpart[4] = {0, 0, 0, 0}, cpart[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty * 4 + u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tx * 4 + v;
+      if (i < n && j < n && (bi != bj || i < j)) {
+        const size_t o = (size_t)i * n + j;
+        const double e = fabs(A1[o] - A2[o]) * fabs(dc[u][v]);
+        rpart[u] += e;
+        cpart[v] += e;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) rsum[ty * 4 + u][tx] = rpart[u];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) csum[tx * 4 + v][ty] = cpart[v];
+  __syncthreads();
+  const int tid = threadIdx.x;
+  if (tid < ST) {
+    double rs = 0.0, cs = 0.0;
+    for (int q = 0; q < 16; ++q) {
+      rs += rsum[tid][q];
+      cs += csum[tid][q];
+    }
+    const int i = i0 + tid, j = j0 + tid;
+    if (bi == bj) {
+      if (i < n) contrib[(size_t)bi * n + i] = rs + cs;
+    } else {
+      if (i < n) contrib[(size_t)bj * n + i] = rs;   // row i, partner block bj
+      if (j < n) contrib[(size_t)bi * n + j] = cs;   // node j, partner block bi
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ A1, const double* __restrict__ A2,
+                                                      const float* __restrict__ ah, const float* __restrict__ al,
+                                                      const float* __restrict__ bh, const float* __restrict__ bl,
+                                                      int n, int k, double* __restrict__ contrib) {
+  __shared__ __align__(16) float sI[4][RC][ST];   // ah, al, bh, bl of the row block
+  __shared__ __align__(16) float sJ[4][RC][ST];   // ... of the column block
+  __shared__ double rsum[ST][17];
+  __shared__ double csum[ST][17];
+  const int nb = (n + ST - 1) / ST;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  const int i0 = bi * ST, j0 = bj * ST;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  const float* src[4] = {ah, al, bh, bl};
+  for (int r0 = 0; r0 < k; r0 += RC) {
+    for (int e = tid; e < RC * ST; e += 256) {
+      const int rr = e / ST, c = e % ST;
+      const int r = r0 + rr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sI[q][rr][c] = (r < k && i0 + c < n) ? src[q][(size_t)r * n + i0 + c] : 0.f;
+        sJ[q][rr][c] = (r < k && j0 + c < n) ? src[q][(size_t)r * n + j0 + c] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < RC; ++rr) {
+      const float4 iah = *reinterpret_cast<const float4*>(&sI[0][rr][ty * 4]);
+      const float4 ial = *reinterpret_cast<const float4*>(&sI[1][rr][ty * 4]);
+      const float4 ibh = *reinterpret_cast<const float4*>(&sI[2][rr][ty * 4]);
+      const float4 ibl = *reinterpret_cast<const float4*>(&sI[3][rr][ty * 4]);
+      const float4 jah = *reinterpret_cast<const float4*>(&sJ[0][rr][tx * 4]);
+      const float4 jal = *reinterpret_cast<const float4*>(&sJ[1][rr][tx * 4]);
+      const float4 jbh = *reinterpret_cast<const float4*>(&sJ[2][rr][tx * 4]);
+      const float4 jbl = *reinterpret_cast<const float4*>(&sJ[3][rr][tx * 4]);
+      const float Iah[4] = {iah.x, iah.y, iah.z, iah.w}, Ial[4] = {ial.x, ial.y, ial.z, ial.w};
+      const float Ibh[4] = {ibh.x, ibh.y, ibh.z, ibh.w}, Ibl[4] = {ibl.x, ibl.y, ibl.z, ibl.w};
+      const float Jah[4] = {jah.x, jah.y, jah.z, jah.w}, Jal[4] = {jal.x, jal.y, jal.z, jal.w};
+      const float Jbh[4] = {jbh.x, jbh.y, jbh.z, jbh.w}, Jbl[4] = {jbl.x, jbl.y, jbl.z, jbl.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float da = __fadd_rn(__fsub_rn(Iah[u], Jah[v]), __fsub_rn(Ial[u], Jal[v]));
+          const float db = __fadd_rn(__fsub_rn(Ibh[u], Jbh[v]), __fsub_rn(Ibl[u], Jbl[v]));
+          acc[u][v] = __fmaf_rn(da, db, acc[u][v]);
+        }
+    }
+    __syncthreads();
+  }
+  double dc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dc[u][v] = (double)acc[u][v];
+  tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, dc, contrib, rsum, csum);
+}
+
+// float64 variant: c2 - c1 = sum_r (a_ir - a_jr)(b_ir - b_jr) in float64.
+__global__ void __launch_bounds__(256) k_score_pairs64(const double* __restrict__ A1,
+                                                        const double* __restrict__ A2,
+                                                        const double* __restrict__ aT,
+                                                        const double* __restrict__ bT, int n, int k,
+                                                        double* __restrict__ contrib) {
+  __shared__ __align__(16) double sI[2][RC][ST];
+  __shared__ __align__(16) double sJ[2][RC][ST];
+  __shared__ double rsum[ST][17];
+  __shared__ double csum[ST][17];
+  const int nb = (n + ST - 1) / ST;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  const int i0 = bi * ST, j0 = bj * ST;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  const double* src[2] = {aT, bT};
+  for (int r0 = 0; r0 < k; r0 += RC) {
+    for (int e = tid; e < RC * ST; e += 256) {
+      const int rr = e / ST, c = e % ST;
+      const int r = r0 + rr;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        sI[q][rr][c] = (r < k && i0 + c < n) ? src[q][(size_t)r * n + i0 + c] : 0.0;
+        sJ[q][rr][c] = (r < k && j0 + c < n) ? src[q][(size_t)r * n + j0 + c] : 0.0;
+      }
+    }
+    __syncthreads();
+    for (int rr = 0; rr < RC; ++rr) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double da = sI[0][rr][ty * 4 + u] - sJ[0][rr][tx * 4 + v];
+          const double db = sI[1][rr][ty * 4 + u] - sJ[1][rr][tx * 4 + v];
+          acc[u][v] = fma(da, db, acc[u][v]);
+        }
+    }
+    __syncthreads();
+  }
+  tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, acc, contrib, rsum, csum);
+}
+
+
+__global__ void k_score_reduce(const double* __restrict__ contrib, int nb, int n, double* __restrict__ F) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += contrib[(size_t)b * n + i];
+  F[i] = s;
+}
+
+// (v, i) precedes (w, j) in the anomaly order: larger score first, then the
+// lower index.
+__device__ __forceinline__ bool better(double v, int i, double w, int j) {
+  return v > w || (v == w && i < j);
+}
+
+__global__ void __launch_bounds__(1024) k_topk(const double* __restrict__ F, int n, int topk,
+                                                int64_t* __restrict__ out) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  double pv = INFINITY;
+  int pi = -1;
+  for (int t = 0; t < topk; ++t) {
+    double bv = -INFINITY;
+    int bidx = INT_MAX;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = F[i];
+      const bool after = v < pv || (v == pv && i > pi);
+      if (after && better(v, i, bv, bidx)) {
+        bv = v;
+        bidx = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (better(ov, oi, bv, bidx)) {
+        bv = ov;
+        bidx = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sv[threadIdx.x >> 5] = bv;
+      si[threadIdx.x >> 5] = bidx;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      bv = threadIdx.x < (blockDim.x >> 5) ? sv[threadIdx.x] : -INFINITY;
+      bidx = threadIdx.x < (blockDim.x >> 5) ? si[threadIdx.x] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (better(ov, oi, bv, bidx)) {
+          bv = ov;
+          bidx = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        sv[0] = bv;
+        si[0] = bidx;
+        out[t] = bidx == INT_MAX ? -1 : bidx;
+      }
+    }
+    __syncthreads();
+    pv = sv[0];
+    pi = si[0];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
+              const double* vol1, const double* vol2, int64_t n64, int k, bool fp64, int topk,
+              double* F, int64_t* top_idx) {
+  const int n = (int)n64;
+  cudaStream_t st = ctx->stream;
+  const int nb = (n + ST - 1) / ST;
+  void *vab, *vc;
+  const size_t nk = (size_t)n * k;
+  CDL_TRY(ws_get(ctx, "score.ab", 16 * nk, &vab));
+  CDL_TRY(ws_get(ctx, "score.contrib", (size_t)nb * n * sizeof(double), &vc));
+  const long long tiles = (long long)nb * (nb + 1) / 2;
+  if (fp64) {
+    double* aT = static_cast<double*>(vab);
+    double* bT = aT + nk;
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_score_prep64<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, aT, bT);
+      CDL_TRY(L.done());
+    }
+    Launch L(ctx, CDL_KC_SCORE, 8.0 * (double)n * (n - 1));
+    k_score_pairs64<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, aT, bT, n, k, static_cast<double*>(vc));
+    CDL_TRY(L.done());
+  } else {
+    float* ah = static_cast<float*>(vab);
+    float* al = ah + nk;
+    float* bh = al + nk;
+    float* bl = bh + nk;
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_score_prep<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, ah, al, bh, bl);
+      CDL_TRY(L.done());
+    }
+    Launch L(ctx, CDL_KC_SCORE, 8.0 * (double)n * (n - 1));
+    k_score_pairs<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, ah, al, bh, bl, n, k, static_cast<double*>(vc));
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_score_reduce<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const double*>(vc), nb, n, F);
+    CDL_TRY(L.done());
+  }
+  if (topk > 0) {
+    Launch L(ctx, CDL_KC_TOPK, 0);
+    k_topk<<<1, 1024, 0, st>>>(F, n, topk, top_idx);
+    CDL_TRY(L.done());
+  }
+  return CDL_OK;
+}
+
+}  // namespace cdl

@@ -1,0 +1,439 @@
+// Chain-preconditioned Richardson solve of L Z = Y (Alg. 2, EstimateSolution,
+// with the k right-hand sides of Alg. 3 processed together as in Sec. 3.3):
+//
+//   R_0 = Y, Z_0 = 0;  Z_{t+1} = Z_t + P R_t,  R_{t+1} = Y - L Z_{t+1},
+//   P R = D^{-1/2} (I + S~_{d-1}) ... (I + S~_0) D^{-1/2} R.
+//
+// Starting from zero this is the paper's y_{t+1} = y_t - P2 y_t + chi with
+// chi = P1 b and P2 = P1 L. The paper fixes the step count q; here the loop
+// also stops once ||R||_F <= rel_tol ||Y||_F. The residual is recomputed from
+// Z every step (not updated recursively), in float-float arithmetic on the
+// float32 pipes (error-free products by fma and error-free sums), because
+// float64 runs at about 1/64 of the float32 rate on this GPU.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace cdl {
+namespace {
+
+constexpr int RED_THREADS = 256;
+
+// per-block partial sums of squares (deterministic order)
+__global__ void __launch_bounds__(RED_THREADS) k_sumsq(const double* __restrict__ v, size_t count,
+                                                        double* __restrict__ part) {
+  __shared__ double red[RED_THREADS / 32];
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * RED_THREADS) {
+    double x = v[i];
+    acc = fma(x, x, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_reduce(const double* __restrict__ part, int count, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+template <typename T>
+__global__ void k_precond_in(const double* __restrict__ R, const double* __restrict__ rsd, int n,
+                             int k, int np, int kp, T* __restrict__ x) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)np * kp) return;
+  int i = (int)(idx / kp), r = (int)(idx % kp);
+  double v = (i < n && r < k) ? R[(size_t)i * k + r] * rsd[i] : 0.0;
+  x[idx] = (T)v;
+}
+
+template <typename T>
+__global__ void k_precond_out(const T* __restrict__ x, const double* __restrict__ rsd, int n, int k,
+                              int kp, double* __restrict__ Z) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  int i = (int)(idx / k), r = (int)(idx % k);
+  Z[idx] += (double)x[(size_t)i * kp + r] * rsd[i];
+}
+
+// x[i][r] += sum_s part[s][i][r] (CUDA-core chains)
+template <typename T>
+__global__ void k_update_simt(T* __restrict__ x, const T* __restrict__ part, int splits, size_t elems) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= elems) return;
+  T acc = x[idx];
+  for (int s = 0; s < splits; ++s) acc += part[(size_t)s * elems + idx];
+  x[idx] = acc;
+}
+
+// bf16 chains: x[i][r] += sum_s (part[s][i][r] + part[s][i][kp + r]) (hi and
+// lo halves of the right-hand side), then the tensor-core operand
+// xop[r][i] = bf16(x[i][r]), xop[kp + r][i] = bf16(x[i][r] - hi). 32 x 32 tiles.
+__global__ void __launch_bounds__(256) k_update_bf16(float* __restrict__ x, const float* __restrict__ part,
+                                                      int splits, int np, int kp,
+                                                      __nv_bfloat16* __restrict__ xop, int accumulate) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int a = ty; a < 32; a += 8) {
+    const int i = i0 + a, r = r0 + tx;
+    float v = 0.f;
+    if (i < np && r < kp) {
+      v = x[(size_t)i * kp + r];
+      if (accumulate) {
+        for (int s = 0; s < splits; ++s) {
+          const float* P = part + ((size_t)s * np + i) * (2 * kp);
+          v += P[r] + P[kp + r];
+        }
+        x[(size_t)i * kp + r] = v;
+      }
+    }
+    tile[a][tx] = v;
+  }
+  __syncthreads();
+  for (int a = ty; a < 32; a += 8) {
+    const int r = r0 + a, i = i0 + tx;
+    if (r < kp && i < np) {
+      const float v = tile[tx][a];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      xop[(size_t)r * np + i] = hi;
+      xop[(size_t)(kp + r) * np + i] = lo;
+    }
+  }
+}
+
+// Column sums s_r = sum_i D_i Z[i][r] in fixed-order per-block partials.
+__global__ void __launch_bounds__(256) k_colsum_dz(const double* __restrict__ Z, const double* __restrict__ D,
+                                                    int n, int k, int rows_per_block, double* __restrict__ part) {
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  const int i0 = blockIdx.x * rows_per_block, i1 = min(n, i0 + rows_per_block);
+  double acc = 0.0;
+  for (int i = i0; i < i1; ++i) acc = fma(D[i], Z[(size_t)i * k + r], acc);
+  part[(size_t)blockIdx.x * k + r] = acc;
+}
+
+__global__ void k_center(double* __restrict__ Z, const double* __restrict__ part, int nparts, int n, int k,
+                         const double* __restrict__ vol) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  const int r = (int)(idx % k);
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += part[(size_t)p * k + r];
+  Z[idx] -= s / *vol;
+}
+
+// Z (float64) -> float hi + lo pair for the float-float residual.
+__global__ void k_split(const double* __restrict__ Z, size_t count, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const double z = Z[idx];
+  const float h = (float)z;
+  hi[idx] = h;
+  lo[idx] = (float)(z - (double)h);
+}
+
+// Float-float accumulate of (ah + al)(zh + zl) into (s, c): the product's
+// rounding error is recovered exactly by fma, the sum's by TwoSum; the
+// al * zl term (below 2^-48 relative) is dropped.
+__device__ __forceinline__ void ff_mac(float ah, float al, float zh, float zl, float& s, float& c) {
+  const float p = __fmul_rn(ah, zh);
+  float e = __fmaf_rn(ah, zh, -p);
+  e = __fmaf_rn(ah, zl, e);
+  e = __fmaf_rn(al, zh, e);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+constexpr int RB_M = 64, RB_N = 128, RB_K = 16;
+
+// R = Y - D o Z + A Z for a 64-row x 128-column tile; per-block sum of R^2.
+__global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, const float* __restrict__ Zh,
+                                                   const float* __restrict__ Zl, const double* __restrict__ Z,
+                                                   const double* __restrict__ Y, const double* __restrict__ D,
+                                                   int n, int k, double* __restrict__ R,
+                                                   double* __restrict__ part) {
+  __shared__ float Ah[RB_K][RB_M + 1], Al[RB_K][RB_M + 1];
+  __shared__ __align__(16) float Bh[RB_K][RB_N], Bl[RB_K][RB_N];
+  __shared__ double red[8];
+  const int i0 = blockIdx.x * RB_M, c0 = blockIdx.y * RB_N;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float sh[4][8], sc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) sh[a][b] = sc[a][b] = 0.f;
+  int rows[4] = {ty * 2, ty * 2 + 1, 32 + ty * 2, 32 + ty * 2 + 1};
+  for (int j0 = 0; j0 < n; j0 += RB_K) {
+#pragma unroll
+    for (int e = 0; e < (RB_M * RB_K) / 256; ++e) {
+      const int idx = tid + e * 256;
+      const int ii = idx / RB_K, jj = idx % RB_K;
+      const int i = i0 + ii, j = j0 + jj;
+      double a = (i < n && j < n) ? A[(size_t)i * n + j] : 0.0;
+      const float h = (float)a;
+      Ah[jj][ii] = h;
+      Al[jj][ii] = (float)(a - (double)h);
+    }
+#pragma unroll
+    for (int e = 0; e < (RB_N * RB_K) / 256; ++e) {
+      const int idx = tid + e * 256;
+      const int jj = idx / RB_N, cc = idx % RB_N;
+      const int j = j0 + jj, c = c0 + cc;
+      const bool ok = j < n && c < k;
+      Bh[jj][cc] = ok ? Zh[(size_t)j * k + c] : 0.f;
+      Bl[jj][cc] = ok ? Zl[(size_t)j * k + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int jj = 0; jj < RB_K; ++jj) {
+      float ah[4], al[4], bh[8], bl[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ah[a] = Ah[jj][rows[a]];
+        al[a] = Al[jj][rows[a]];
+      }
+      const float4 h0 = *reinterpret_cast<const float4*>(&Bh[jj][tx * 4]);
+      const float4 h1 = *reinterpret_cast<const float4*>(&Bh[jj][64 + tx * 4]);
+      const float4 l0 = *reinterpret_cast<const float4*>(&Bl[jj][tx * 4]);
+      const float4 l1 = *reinterpret_cast<const float4*>(&Bl[jj][64 + tx * 4]);
+      bh[0] = h0.x; bh[1] = h0.y; bh[2] = h0.z; bh[3] = h0.w;
+      bh[4] = h1.x; bh[5] = h1.y; bh[6] = h1.z; bh[7] = h1.w;
+      bl[0] = l0.x; bl[1] = l0.y; bl[2] = l0.z; bl[3] = l0.w;
+      bl[4] = l1.x; bl[5] = l1.y; bl[6] = l1.z; bl[7] = l1.w;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) ff_mac(ah[a], al[a], bh[b], bl[b], sh[a][b], sc[a][b]);
+    }
+    __syncthreads();
+  }
+  double sq = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + rows[a];
+    if (i >= n) continue;
+    const double di = D[i];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int c = c0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
+      if (c >= k) continue;
+      const size_t o = (size_t)i * k + c;
+      const double az = (double)sh[a][b] + (double)sc[a][b];
+      const double r = (Y[o] - di * Z[o]) + az;
+      R[o] = r;
+      sq = fma(r, r, sq);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((tid & 31) == 0) red[tid >> 5] = sq;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+int largest_divisor_at_most(int total, int target) {
+  int best = 1;
+  for (int s = 1; s <= total && s <= target; ++s)
+    if (total % s == 0) best = s;
+  return best;
+}
+
+inline unsigned blocks_for(size_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
+
+}  // namespace
+
+int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
+                const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats) {
+  cudaStream_t st = ctx->stream;
+  const int n = (int)ch->n, np = (int)ch->npad;
+  const int kp = (int)round_up(k, 16);   // tensor-core N = 2 kp: multiple of 32
+  const bool bf16 = ch->dtype == CDL_BF16;
+  const size_t xe = ch->dtype == CDL_F64 ? 8 : 4;
+  const int kblocks = np / 64;
+  int splits;
+  if (bf16) {
+    const int target = std::max(1, (4 * ctx->sm_count + np / 128 - 1) / (np / 128));
+    splits = largest_divisor_at_most(kblocks, target);
+  } else {
+    const int bm = ch->dtype == CDL_F32 ? 128 : 64;
+    const int cols = (kp + 63) / 64;
+    const int target = std::max(1, (8 * ctx->sm_count) / ((np / bm) * cols));
+    splits = largest_divisor_at_most(np / 8, std::min(target, 16));
+  }
+  const size_t part_cols = bf16 ? 2 * (size_t)kp : (size_t)kp;
+  void *vR, *vx, *vxop = nullptr, *vpart, *vred, *vscal, *vzh, *vzl, *vcs;
+  const int res_gx = (n + RB_M - 1) / RB_M, res_gy = (k + RB_N - 1) / RB_N;
+  const int nred = std::max(res_gx * res_gy, 1024);
+  const int cs_rows = 256, cs_parts = (n + cs_rows - 1) / cs_rows;
+  CDL_TRY(ws_get(ctx, "solve.R", (size_t)n * k * 8, &vR));
+  CDL_TRY(ws_get(ctx, "solve.x", (size_t)np * kp * xe, &vx));
+  if (bf16) CDL_TRY(ws_get(ctx, "solve.xop", 2 * (size_t)kp * np * 2, &vxop));
+  CDL_TRY(ws_get(ctx, "solve.part", (size_t)splits * np * part_cols * xe, &vpart));
+  CDL_TRY(ws_get(ctx, "solve.red", (size_t)nred * 8, &vred));
+  CDL_TRY(ws_get(ctx, "solve.scal", 64, &vscal));
+  CDL_TRY(ws_get(ctx, "solve.zh", (size_t)n * k * 4, &vzh));
+  CDL_TRY(ws_get(ctx, "solve.zl", (size_t)n * k * 4, &vzl));
+  CDL_TRY(ws_get(ctx, "solve.colsum", (size_t)cs_parts * k * 8, &vcs));
+  double* R = static_cast<double*>(vR);
+  double* red = static_cast<double*>(vred);
+  double* scal = static_cast<double*>(vscal);
+  const size_t nk = (size_t)n * k;
+
+  auto sumsq = [&](const double* v, size_t count, double* out, double* host) -> int {
+    const int nb = (int)std::min<size_t>(1024, (count + RED_THREADS - 1) / RED_THREADS);
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_sumsq<<<nb, RED_THREADS, 0, st>>>(v, count, red);
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_reduce<<<1, 1024, 0, st>>>(red, nb, out);
+      CDL_TRY(L.done());
+    }
+    CDL_CUDA_TRY(cudaMemcpyAsync(host, out, 8, cudaMemcpyDeviceToHost, st));
+    CDL_CUDA_TRY(cudaStreamSynchronize(st));
+    return CDL_OK;
+  };
+
+  double yy = 0.0;
+  CDL_TRY(sumsq(Y, nk, scal, &yy));
+  CDL_CUDA_TRY(cudaMemsetAsync(Z, 0, nk * 8, st));
+  CDL_CUDA_TRY(cudaMemcpyAsync(R, Y, nk * 8, cudaMemcpyDeviceToDevice, st));
+  if (stats) {
+    stats->iters = 0;
+    stats->rel_res = yy > 0 ? 1.0 : 0.0;
+    for (double& h : stats->history) h = 0.0;
+  }
+  if (yy == 0.0) return CDL_OK;
+  double rel = 1.0;
+  int iters = 0;
+  while (true) {
+    if (opts->rel_tol > 0 && rel <= opts->rel_tol) break;
+    if (iters >= opts->max_iter) break;
+    // x = D^{-1/2} R in the chain's working precision
+    {
+      const size_t cnt = (size_t)np * kp;
+      Launch L(ctx, CDL_KC_MISC, 0);
+      if (ch->dtype == CDL_F64)
+        k_precond_in<double><<<blocks_for(cnt, 256), 256, 0, st>>>(R, ch->rsqrt_d, n, k, np, kp,
+                                                                    static_cast<double*>(vx));
+      else
+        k_precond_in<float><<<blocks_for(cnt, 256), 256, 0, st>>>(R, ch->rsqrt_d, n, k, np, kp,
+                                                                   static_cast<float*>(vx));
+      CDL_TRY(L.done());
+    }
+    if (bf16) {
+      dim3 g((np + 31) / 32, (kp + 31) / 32);
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_update_bf16<<<g, 256, 0, st>>>(static_cast<float*>(vx), nullptr, 0, np, kp,
+                                       static_cast<__nv_bfloat16*>(vxop), 0);
+      CDL_TRY(L.done());
+    }
+    // x <- (I + S~_lvl) x for every level
+    for (int lvl = 0; lvl < ch->d; ++lvl) {
+      if (bf16) {
+        CDL_TRY(apply_tc(ctx, ch, lvl, vxop, static_cast<float*>(vpart), kp, splits));
+        dim3 g((np + 31) / 32, (kp + 31) / 32);
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_update_bf16<<<g, 256, 0, st>>>(static_cast<float*>(vx), static_cast<const float*>(vpart), splits,
+                                         np, kp, static_cast<__nv_bfloat16*>(vxop), 1);
+        CDL_TRY(L.done());
+      } else {
+        CDL_TRY(apply_simt(ctx, ch, lvl, vx, vpart, kp, splits));
+        const size_t cnt = (size_t)np * kp;
+        Launch L(ctx, CDL_KC_MISC, 0);
+        if (ch->dtype == CDL_F64)
+          k_update_simt<double><<<blocks_for(cnt, 256), 256, 0, st>>>(
+              static_cast<double*>(vx), static_cast<const double*>(vpart), splits, cnt);
+        else
+          k_update_simt<float><<<blocks_for(cnt, 256), 256, 0, st>>>(
+              static_cast<float*>(vx), static_cast<const float*>(vpart), splits, cnt);
+        CDL_TRY(L.done());
+      }
+    }
+    // Z += D^{-1/2} x, then D-weighted centring
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      if (ch->dtype == CDL_F64)
+        k_precond_out<double><<<blocks_for(nk, 256), 256, 0, st>>>(static_cast<const double*>(vx), ch->rsqrt_d,
+                                                                    n, k, kp, Z);
+      else
+        k_precond_out<float><<<blocks_for(nk, 256), 256, 0, st>>>(static_cast<const float*>(vx), ch->rsqrt_d,
+                                                                   n, k, kp, Z);
+      CDL_TRY(L.done());
+    }
+    {
+      dim3 g(cs_parts, (k + 255) / 256);
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_colsum_dz<<<g, 256, 0, st>>>(Z, ch->D, n, k, cs_rows, static_cast<double*>(vcs));
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_center<<<blocks_for(nk, 256), 256, 0, st>>>(Z, static_cast<const double*>(vcs), cs_parts, n, k, ch->vol);
+      CDL_TRY(L.done());
+    }
+    ++iters;
+    // R = Y - L Z in float-float
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_split<<<blocks_for(nk, 256), 256, 0, st>>>(Z, nk, static_cast<float*>(vzh), static_cast<float*>(vzl));
+      CDL_TRY(L.done());
+    }
+    {
+      dim3 g(res_gx, res_gy);
+      Launch L(ctx, CDL_KC_RESIDUAL, (double)n * n * k);
+      k_residual<<<g, 256, 0, st>>>(A, static_cast<const float*>(vzh), static_cast<const float*>(vzl), Z, Y,
+                                     ch->D, n, k, R, red);
+      CDL_TRY(L.done());
+    }
+    double rr = 0.0;
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_reduce<<<1, 1024, 0, st>>>(red, res_gx * res_gy, scal + 1);
+      CDL_TRY(L.done());
+    }
+    CDL_CUDA_TRY(cudaMemcpyAsync(&rr, scal + 1, 8, cudaMemcpyDeviceToHost, st));
+    CDL_CUDA_TRY(cudaStreamSynchronize(st));
+    rel = std::sqrt(rr / yy);
+    if (stats && iters <= 64) stats->history[iters - 1] = rel;
+  }
+  if (stats) {
+    stats->iters = iters;
+    stats->rel_res = rel;
+  }
+  return (opts->rel_tol > 0 && rel > opts->rel_tol) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
+}
+
+}  // namespace cdl

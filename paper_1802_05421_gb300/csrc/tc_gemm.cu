@@ -1,0 +1,526 @@
+// Tensor-core (tcgen05, sm_103a) bfloat16 GEMMs of the inverse chain
+// (Alg. 2, ChainProduct, "2d matrix multiplications" of Sec. 3.1):
+//
+//  * square: S~_{i+1} = S~_i S~_i for the symmetric bf16 level S~_i. Only the
+//    256 x 256 blocks (I, J) with I <= J are computed (two 128 x 256 MMA
+//    tiles each); every block is also written transposed, so the stored
+//    level is exactly symmetric. Output bf16 (float32 accumulation).
+//  * apply: partial[s] = S~_i [x_hi | x_lo] over the k-range of split s,
+//    where x_hi + x_lo is a float32 block of right-hand sides split into two
+//    bfloat16 halves (about 16 significant bits). Output float32 partials.
+//
+// Structure: persistent CTAs (one per SM), warp-specialised. Warp 0 issues TMA
+// loads of 128-byte-swizzled K-major tiles into a 4-stage shared-memory ring;
+// warp 1 (one thread) issues tcgen05.mma (M = 128, N <= 256, K = 16) into one
+// of two TMEM accumulators; warps 2-5 drain the other accumulator with
+// tcgen05.ld and store to global memory. Every mbarrier wait is bounded: on
+// expiry the CTA records DEV_WAIT_TIMEOUT in the status word and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace cdl {
+namespace {
+
+constexpr int BM = 128;           // MMA M = TMEM lanes
+constexpr int BK = 64;            // bf16 per 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr int MAX_BN = 256;
+constexpr int A_TILE = BM * BK * 2;          // 16 KiB
+constexpr int B_TILE = MAX_BN * BK * 2;      // 32 KiB
+constexpr int STAGE_BYTES = A_TILE + B_TILE;
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 512;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
+
+enum { MODE_SQUARE = 0, MODE_APPLY = 1 };
+
+struct TcParams {
+  const uint32_t* tiles;   // packed tile descriptors
+  int num_tiles;
+  int kblocks;             // 64-wide k-blocks per tile
+  int bn;                  // MMA N (multiple of 16, <= 256)
+  uint32_t idesc;          // tcgen05 instruction descriptor
+  int mode;
+  int npad;                // matrix order
+  void* out;               // square: bf16 level (npad x npad); apply: float partials
+  int ldo;                 // apply: partial row stride (= bn)
+  unsigned* status;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait. Returns false (after flagging) if the phase did not complete
+// within WAIT_LIMIT_NS or another role of this CTA already gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+      *abort_flag = 1;
+      atomicOr(status, DEV_WAIT_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tile descriptors. square: I (bits 0-14), J (bits 15-29), half (bit 30).
+// apply: row block m (bits 0-15), split s (bits 16-31).
+__device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int& a_row, int& b_row,
+                                       int& k0, int& I, int& J, int& split) {
+  if (p.mode == MODE_SQUARE) {
+    I = t & 0x7FFF;
+    J = (t >> 15) & 0x7FFF;
+    const int half = (t >> 30) & 1;
+    a_row = I * 256 + half * 128;
+    b_row = J * 256;
+    k0 = 0;
+    split = 0;
+  } else {
+    const int m = t & 0xFFFF;
+    split = (t >> 16) & 0xFFFF;
+    a_row = m * 128;
+    b_row = 0;
+    k0 = split * p.kblocks * BK;
+    I = m;
+    J = 0;
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars[0..3] full, [4..7] empty, [8..9] tmem full, [10..11] tmem empty, [12] drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 17);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 128);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t b_bytes = (uint32_t)p.bn * BK * 2;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      int a_row, b_row, k0, I, J, split;
+      decode(p, p.tiles[t], a_row, b_row, k0, I, J, split);
+      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t r = (uint32_t)(it / STAGES);
+        if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t b_dst = a_dst + A_TILE;
+        mbar_expect_tx(full_bar(s), A_TILE + b_bytes);
+        tma_load_2d(a_dst, &tmA, k0 + kb * BK, a_row, full_bar(s));
+        tma_load_2d(b_dst, &tmB, k0 + kb * BK, b_row, full_bar(s));
+      }
+    }
+    if (!ok) {
+      // let copies already issued land before the CTA exits (bounded)
+      for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full_bar(j % STAGES), (uint32_t)(j / STAGES) & 1) &&
+               globaltimer() - t0 < WAIT_LIMIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer
+    int it = 0, tc = 0;
+    bool ok = true, issued = false;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++tc) {
+      const int acc = tc & 1;
+      const uint32_t ar = (uint32_t)(tc >> 1);
+      if (!mbar_wait(tempty_bar(acc), (ar & 1) ^ 1, abort_flag, p.status)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * MAX_BN);
+      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t r = (uint32_t)(it / STAGES);
+        if (!mbar_wait(full_bar(s), r & 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+        const uint64_t adesc = smem_desc(a_addr);
+        const uint64_t bdesc = smem_desc(a_addr + A_TILE);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          // advance 16 bf16 = 32 bytes along K inside the swizzle atom
+          mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc,
+                   (kb | kk) != 0);
+        }
+        issued = true;
+        mma_commit(empty_bar(s));
+      }
+      if (!ok) break;
+      mma_commit(tfull_bar(acc));
+    }
+    if (!ok && issued) {
+      mma_commit(drain_bar);   // wait (bounded) for MMAs in flight
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row_in_tile = q * 32 + lane;
+    int tc = 0;
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++tc) {
+      const int acc = tc & 1;
+      const uint32_t ar = (uint32_t)(tc >> 1);
+      if (!mbar_wait(tfull_bar(acc), ar & 1, abort_flag, p.status)) break;
+      tc_fence_after();
+      int a_row, b_row, k0, I, J, split;
+      decode(p, p.tiles[t], a_row, b_row, k0, I, J, split);
+      const int r = a_row + row_in_tile;
+      const uint32_t taddr = tmem_base + (uint32_t)(acc * MAX_BN) + ((uint32_t)(q * 32) << 16);
+      for (int c = 0; c < p.bn / 32; ++c) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(c * 32), v);
+        if (p.mode == MODE_SQUARE) {
+          __nv_bfloat16* C = static_cast<__nv_bfloat16*>(p.out);
+          const int col0 = b_row + c * 32;
+          if (I != J) {
+            uint32_t packed[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+              packed[e] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(C + (size_t)r * p.npad + col0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              dst[e] = make_uint4(packed[4 * e], packed[4 * e + 1], packed[4 * e + 2], packed[4 * e + 3]);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) C[(size_t)(col0 + e) * p.npad + r] = __float2bfloat16_rn(v[e]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int col = col0 + e;
+              const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
+              if (col >= r) C[(size_t)r * p.npad + col] = h;
+              if (col > r) C[(size_t)col * p.npad + r] = h;
+            }
+          }
+        } else {
+          float* P = static_cast<float*>(p.out) + ((size_t)split * p.npad + r) * p.ldo + c * 32;
+          float4* dst = reinterpret_cast<float4*>(P);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty_bar(acc));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor map over a rows x cols row-major matrix, box 64 x box_rows.
+int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return CDL_ERR_UNSUPPORTED;
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed", __FILE__, __LINE__);
+    return CDL_ERR_CUDA;
+  }
+  return CDL_OK;
+}
+
+uint32_t make_idesc(int n) {
+  return (1u << 4)                      // D: float32
+         | (1u << 7)                    // A: bf16
+         | (1u << 10)                   // B: bf16
+         | ((uint32_t)(n >> 3) << 17)   // N / 8
+         | ((uint32_t)(BM >> 4) << 24); // M / 16
+}
+
+// Upper-triangle 256-blocks in 8 x 8 super-block groups (L2 reuse), both
+// 128-row halves of a block adjacent.
+std::vector<uint32_t> square_tiles(int nb) {
+  std::vector<uint32_t> v;
+  const int G = 8;
+  for (int P = 0; P < nb; P += G)
+    for (int Q = P; Q < nb; Q += G)
+      for (int I = P; I < std::min(P + G, nb); ++I)
+        for (int J = std::max(Q, I); J < std::min(Q + G, nb); ++J)
+          for (int h = 0; h < 2; ++h) v.push_back((uint32_t)I | ((uint32_t)J << 15) | ((uint32_t)h << 30));
+  return v;
+}
+
+std::vector<uint32_t> apply_tiles(int mb, int splits) {
+  std::vector<uint32_t> v;
+  for (int s = 0; s < splits; ++s)
+    for (int m = 0; m < mb; ++m) v.push_back((uint32_t)m | ((uint32_t)s << 16));
+  return v;
+}
+
+// Device copy of a tile schedule, built once per (kind, sizes) and kept in
+// the context's workspace under a name that encodes those sizes.
+template <typename Builder>
+int get_tiles(cdl_ctx* ctx, const std::string& name, Builder build, const uint32_t** out, int* count) {
+  auto it = ctx->tile_lists.find(name);
+  if (it != ctx->tile_lists.end() && ctx->ws.count(name)) {
+    *out = static_cast<const uint32_t*>(ctx->ws[name].first);
+    *count = it->second;
+    return CDL_OK;
+  }
+  std::vector<uint32_t> tiles = build();
+  void* buf;
+  CDL_TRY(ws_get(ctx, name.c_str(), tiles.size() * sizeof(uint32_t), &buf));
+  CDL_CUDA_TRY(cudaMemcpyAsync(buf, tiles.data(), tiles.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));   // the host vector goes out of scope
+  ctx->tile_lists[name] = (int)tiles.size();
+  *out = static_cast<const uint32_t*>(buf);
+  *count = (int)tiles.size();
+  return CDL_OK;
+}
+
+int launch(cdl_ctx* ctx, const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int kc,
+           double work) {
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  const int grid = std::min(p.num_tiles, ctx->sm_count);
+  Launch L(ctx, kc, work);
+  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, ctx->stream>>>(a, b, p);
+  return L.done();
+}
+
+}  // namespace
+
+bool tc_supported(cdl_ctx* ctx) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
+  const int np = (int)ch->npad;
+  const int nb = np / 256;
+  const uint32_t* tiles;
+  int count;
+  CDL_TRY(get_tiles(ctx, "tc.square." + std::to_string(nb), [&] { return square_tiles(nb); }, &tiles, &count));
+  CUtensorMap ma, mb;
+  CDL_TRY(make_map(&ma, ch->level(level), np, np, 128));
+  CDL_TRY(make_map(&mb, ch->level(level), np, np, 256));
+  TcParams p;
+  p.tiles = tiles;
+  p.num_tiles = count;
+  p.kblocks = np / BK;
+  p.bn = 256;
+  p.idesc = make_idesc(256);
+  p.mode = MODE_SQUARE;
+  p.npad = np;
+  p.out = ch->level(level + 1);
+  p.ldo = np;
+  p.status = ctx->dev_status;
+  const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
+  return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops);
+}
+
+int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial, int kp,
+             int splits) {
+  const int np = (int)ch->npad;
+  const int bn = 2 * kp;
+  if (bn % 32 || bn < 32 || bn > MAX_BN) return CDL_ERR_UNSUPPORTED;
+  const int mb = np / BM;
+  if ((np / BK) % splits) return CDL_ERR_INVALID_ARG;
+  const uint32_t* tiles;
+  int count;
+  CDL_TRY(get_tiles(ctx, "tc.apply." + std::to_string(mb) + "." + std::to_string(splits),
+                    [&] { return apply_tiles(mb, splits); }, &tiles, &count));
+  CUtensorMap ma, mbm;
+  CDL_TRY(make_map(&ma, ch->level(level), np, np, 128));
+  CDL_TRY(make_map(&mbm, xop, bn, np, bn));
+  TcParams p;
+  p.tiles = tiles;
+  p.num_tiles = count;
+  p.kblocks = np / BK / splits;
+  p.bn = bn;
+  p.idesc = make_idesc(bn);
+  p.mode = MODE_APPLY;
+  p.npad = np;
+  p.out = partial;
+  p.ldo = bn;
+  p.status = ctx->dev_status;
+  const double bytes = 2.0 * np * (double)np;
+  return launch(ctx, ma, mbm, p, CDL_KC_APPLY, bytes);
+}
+
+}  // namespace cdl

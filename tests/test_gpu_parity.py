@@ -1,0 +1,330 @@
+"""Parity of the CUDA path (called through the C ABI) with the float64 oracle
+on seeded inputs: graph build, projection, chain levels (including the
+tcgen05 GEMM against an exact product of its own inputs), solve, scores, the
+whole pair, and argument validation. Sizes span several tiles and ragged
+tails; the oracle finishes each case in seconds."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import caddelag as O          # noqa: E402
+from workloads import iid_pair, field_sequence, to_grid   # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import Ctx, lib
+    c = Ctx(lib())
+    yield c
+    c.close()
+
+
+def _h(t):
+    from gpu_util import host
+    return host(t)
+
+
+# ------------------------------------------------------------------ graph
+
+@pytest.mark.parametrize("n,T", [(2, 3), (3, 1), (65, 7), (300, 64), (1000, 40)])
+def test_graph_matches_oracle(G, n, T):
+    X = iid_pair(n, T, 1, seed=n).X[0]
+    A, D, vol, sig = G.graph(X)
+    Ao, Do, volo, sigo = O.gaussian_graph(X)
+    assert _h(sig)[0] == sigo                       # exact selection on exact distances
+    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(_h(D), Do, rtol=1e-13)
+    assert math.isclose(_h(vol)[0], volo, rel_tol=1e-13)
+
+
+def test_graph_off_grid_uses_float64_path(G):
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((130, 7)) * 3.0 + 1e-9   # off the 2^-16 grid
+    A, D, vol, sig = G.graph(X)
+    Ao, Do, volo, sigo = O.gaussian_graph(X)
+    assert _h(sig)[0] == sigo
+    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+
+
+def test_graph_given_sigma(G):
+    X = iid_pair(100, 9, 1, seed=2).X[0]
+    A, D, vol, sig = G.graph(X, sigma=1.75)
+    Ao, Do, volo, _ = O.gaussian_graph(X, sigma=1.75)
+    assert _h(sig)[0] == 1.75
+    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+
+
+def test_graph_field_workload(G):
+    X = field_sequence(16, 32, 48, 2, patch=4, seed=3).X[1]
+    A, D, vol, sig = G.graph(X)
+    Ao, Do, volo, sigo = O.gaussian_graph(X)
+    assert _h(sig)[0] == sigo
+    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------------------------ projection
+
+@pytest.mark.parametrize("n,k,seed", [(50, 1, 1), (97, 5, 2), (300, 32, 3), (200, 130, 2 ** 40 + 7)])
+def test_projection_matches_oracle(G, n, k, seed):
+    X = iid_pair(n, 16, 1, seed=n + k).X[0]
+    Ao, *_ = O.gaussian_graph(X)
+    Y = _h(G.project(torch.from_numpy(Ao).cuda(), k, seed))
+    Yo = O.project(Ao, seed, k)
+    assert np.abs(Y - Yo).max() <= 1e-12 * np.abs(Yo).max()
+    assert np.abs(Y.sum(0)).max() <= 1e-11 * np.abs(Yo).max()
+
+
+# ------------------------------------------------------------------ chain
+
+def _deflated_levels(Ao, d):
+    D = Ao.sum(1)
+    u = np.sqrt(D / D.sum())
+    return [L - np.outer(u, u) for L in O.chain_levels(Ao, d)]
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 3e-2)])
+@pytest.mark.parametrize("n", [300, 1000])
+def test_chain_levels_match_oracle(G, dtype, tol, n):
+    cdl = G.cdl
+    dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}[dtype]
+    X = iid_pair(n, 32, 1, seed=7).X[0]
+    A, D, vol, _ = G.graph(X)
+    d = 4
+    ch = G.chain(A, D, vol, d, dt)
+    try:
+        ref = _deflated_levels(_h(A), d)
+        scale = np.linalg.norm(ref[0])
+        for i in range(d):
+            Lg = G.level(ch, i, {"f64": np.float64, "f32": np.float32, "bf16": "bf16"}[dtype])
+            Lg = Lg.double().cpu().numpy()
+            assert np.all(Lg[n:, :] == 0) and np.all(Lg[:, n:] == 0)   # zero padding
+            assert np.array_equal(Lg, Lg.T)                             # exact symmetry
+            err = np.linalg.norm(Lg[:n, :n] - ref[i]) / scale
+            assert err <= tol, (i, err)
+    finally:
+        cdl.cdl_chain_free(ch)
+
+
+@pytest.mark.parametrize("n", [300, 1000, 2100])
+def test_tcgen05_square_is_exact_product_of_its_inputs(G, n):
+    """One bf16 squaring against the float64 product of the same bf16 input:
+    the only errors allowed are float32 accumulation and the final bf16
+    rounding (n = 2100 pads to 2304: 9 x 9 blocks, crossing the 8 x 8
+    super-block grouping, diagonal and off-diagonal blocks)."""
+    cdl = G.cdl
+    X = iid_pair(n, 24, 1, seed=11).X[0]
+    A, D, vol, _ = G.graph(X)
+    ch = G.chain(A, D, vol, 2, cdl.CDL_BF16)
+    try:
+        L0 = G.level(ch, 0, "bf16").double().cpu().numpy()
+        L1 = G.level(ch, 1, "bf16").double().cpu().numpy()
+    finally:
+        cdl.cdl_chain_free(ch)
+    R = L0 @ L0
+    bound = 2.0 ** -8 * np.abs(R) + L0.shape[0] * 2.0 ** -23 * (np.abs(L0) @ np.abs(L0)) + 1e-30
+    assert np.all(np.abs(L1 - R) <= bound)
+    assert np.array_equal(L1, L1.T)
+
+
+def test_simt_f32_square_is_exact_product_of_its_inputs(G):
+    cdl = G.cdl
+    n = 700
+    X = iid_pair(n, 24, 1, seed=12).X[0]
+    A, D, vol, _ = G.graph(X)
+    ch = G.chain(A, D, vol, 2, cdl.CDL_F32)
+    try:
+        L0 = G.level(ch, 0, np.float32).double().cpu().numpy()
+        L1 = G.level(ch, 1, np.float32).double().cpu().numpy()
+    finally:
+        cdl.cdl_chain_free(ch)
+    R = L0 @ L0
+    bound = 2.0 ** -24 * np.abs(R) + L0.shape[0] * 2.0 ** -23 * (np.abs(L0) @ np.abs(L0)) + 1e-30
+    assert np.all(np.abs(L1 - R) <= bound)
+
+
+# ------------------------------------------------------------------ solve
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-10), ("bf16", 1e-10)])
+@pytest.mark.parametrize("n,k", [(300, 8), (1000, 32)])
+def test_solve_matches_exact_embedding(G, dtype, tol, n, k):
+    cdl = G.cdl
+    dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}[dtype]
+    X = iid_pair(n, 32, 1, seed=n + 1).X[0]
+    Ao, Do, volo, _ = O.gaussian_graph(X)
+    Yo = O.project(Ao, 9, k)
+    Zo = O.exact_embedding(Ao, Yo)
+    A = torch.from_numpy(Ao).cuda()
+    D = torch.from_numpy(Do).cuda()
+    vol = torch.tensor([volo], dtype=torch.float64, device="cuda")
+    ch = G.chain(A, D, vol, 6, dt)
+    try:
+        Z, stats = G.solve(ch, A, torch.from_numpy(Yo).cuda(), max_iter=30, rel_tol=tol)
+    finally:
+        cdl.cdl_chain_free(ch)
+    Zg = _h(Z)
+    assert stats.rel_res <= tol and stats.iters >= 1
+    assert O.residual_norm(Ao, Yo, Zg) <= 3 * tol
+    assert np.linalg.norm(Zg - Zo) <= 100 * tol * np.linalg.norm(Zo)
+    assert np.abs(Do @ Zg).max() <= 1e-12 * np.abs(Zg).max() * Do.sum()
+
+
+def test_solve_reports_not_converged(G):
+    cdl = G.cdl
+    X = iid_pair(300, 16, 1, seed=4).X[0]
+    Ao, Do, volo, _ = O.gaussian_graph(X)
+    A = torch.from_numpy(Ao).cuda()
+    D = torch.from_numpy(Do).cuda()
+    vol = torch.tensor([volo], dtype=torch.float64, device="cuda")
+    ch = G.chain(A, D, vol, 1, cdl.CDL_BF16)
+    try:
+        Y = torch.from_numpy(O.project(Ao, 1, 4)).cuda()
+        Z, stats = G.solve(ch, A, Y, max_iter=1, rel_tol=1e-14, expect=cdl.CDL_ERR_NOT_CONVERGED)
+    finally:
+        cdl.cdl_chain_free(ch)
+    assert stats.iters == 1 and stats.rel_res > 1e-14
+
+
+# ------------------------------------------------------------------ scores
+
+@pytest.mark.parametrize("score", ["f64", "f32"])
+def test_scores_match_oracle(G, score):
+    cdl = G.cdl
+    wl = iid_pair(333, 24, 6, seed=8)
+    g = [O.embed(X, 16, 3) for X in wl.X]
+    Fo = O.node_scores(g[0]["A"], g[1]["A"], g[0]["Z"], g[1]["Z"], g[0]["vol"], g[1]["vol"])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    v1 = torch.tensor([g[0]["vol"]], dtype=torch.float64, device="cuda")
+    v2 = torch.tensor([g[1]["vol"]], dtype=torch.float64, device="cuda")
+    sd = cdl.CDL_F64 if score == "f64" else cdl.CDL_F32
+    F, top = G.score(t(g[0]["A"]), t(g[1]["A"]), t(g[0]["Z"]), t(g[1]["Z"]), v1, v2, 8, sd)
+    rel = np.abs(_h(F) - Fo) / Fo
+    assert rel.max() <= (1e-12 if score == "f64" else 1e-6), rel.max()
+    if O.min_relative_gap(Fo, 8) > 1e-6:
+        assert list(_h(top)) == list(O.top_anomalies(Fo, 8))
+
+
+# ------------------------------------------------------------------ whole pair (Alg. 4)
+
+@pytest.fixture(scope="module")
+def iid1024():
+    wl = iid_pair(1024, 64, 10, 0)
+    out = O.caddelag_pair(wl.X[0], wl.X[1], k=32, seed=0, topk=10)
+    return wl, out
+
+
+@pytest.mark.parametrize("chain,score,tol,host_io", [
+    ("f64", "f64", 1e-9, False),
+    ("f64", "f64", 1e-9, True),
+    ("f32", "f64", 1e-9, False),
+    ("bf16", "f32", 1e-6, False),
+    ("bf16", "f32", 1e-6, True),
+])
+def test_pair_iid_n1024_matches_oracle(G, iid1024, chain, score, tol, host_io):
+    cdl = G.cdl
+    wl, out = iid1024
+    dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}
+    F, top, s1, s2 = G.pair(wl.X[0], wl.X[1], 32, 8, dt[chain], dt[score], 0, 10, host_io=host_io)
+    Fo = out["F"]
+    rel = np.abs(F - Fo) / Fo
+    assert rel.max() <= tol, rel.max()
+    assert s1.rel_res <= 1e-10 and s2.rel_res <= 1e-10
+    gap = O.min_relative_gap(Fo, 10)
+    assert gap > 10 * tol
+    assert list(top) == list(out["top"])
+    assert set(top.tolist()) == set(wl.planted[0].tolist())
+
+
+def test_pair_field_bf16_finds_patch(G):
+    cdl = G.cdl
+    wl = field_sequence(32, 64, 64, 2, patch=4, patch_transition=0, seed=5)
+    out = O.caddelag_pair(wl.X[0], wl.X[1], k=32, seed=1, topk=16)
+    F, top, s1, s2 = G.pair(wl.X[0], wl.X[1], 32, 10, cdl.CDL_BF16, cdl.CDL_F32, 1, 16)
+    rel = np.abs(F - out["F"]) / out["F"]
+    assert rel.max() <= 1e-6, rel.max()
+    if O.min_relative_gap(out["F"], 16) > 1e-5:
+        assert list(top) == list(out["top"])
+    assert len(set(top.tolist()) & set(wl.planted[0].tolist())) >= 12
+
+
+# ------------------------------------------------------------------ validation
+
+def test_invalid_arguments(G):
+    cdl = G.cdl
+    n, T = 64, 8
+    X = torch.zeros((n, T), dtype=torch.float64, device="cuda")
+    A = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    D = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s = torch.zeros(2, dtype=torch.float64, device="cuda")
+    Xh = np.zeros((n, T))
+    args = (s[0:1].data_ptr(), s[1:2].data_ptr())
+    assert cdl.cdl_build_graph(G.h, X, 1, T, 0.0, cdl.CDL_F64, A, D, *args) == cdl.CDL_ERR_INVALID_ARG
+    assert cdl.cdl_build_graph(G.h, X, n, 0, 0.0, cdl.CDL_F64, A, D, *args) == cdl.CDL_ERR_INVALID_ARG
+    assert cdl.cdl_build_graph(G.h, Xh, n, T, 0.0, cdl.CDL_F64, A, D, *args) == cdl.CDL_ERR_INVALID_ARG
+    assert cdl.cdl_build_graph(G.h, X, n, T, 0.0, cdl.CDL_F32, A, D, *args) == cdl.CDL_ERR_UNSUPPORTED
+    assert cdl.cdl_build_graph(G.h, X.data_ptr() + 4, n, T, 0.0, cdl.CDL_F64, A, D, *args) == \
+        cdl.CDL_ERR_INVALID_ARG
+    st, ch = cdl.cdl_chain_build(G.h, A, cdl.CDL_F64, D, s, n, 3, cdl.CDL_FP8E4M3)
+    assert st == cdl.CDL_ERR_UNSUPPORTED
+    assert cdl.cdl_project(G.h, A, cdl.CDL_F64, n, 0, 1, A) == cdl.CDL_ERR_INVALID_ARG
+    assert cdl.cdl_project(G.h, A, cdl.CDL_F64, n, 1025, 1, A) == cdl.CDL_ERR_INVALID_ARG
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    assert cdl.cdl_cad_score(G.h, A, A, cdl.CDL_F64, A, A, s, s, n, 4, cdl.CDL_BF16, 2, F, F) == \
+        cdl.CDL_ERR_INVALID_ARG
+    assert cdl.cdl_cad_score(G.h, A, A, cdl.CDL_F64, A, A, s, s, n, 4, cdl.CDL_F64, n + 1, F, F) == \
+        cdl.CDL_ERR_INVALID_ARG
+    assert cdl.cdl_sync(G.h) == cdl.CDL_OK
+
+
+def test_chain_reuse_and_mismatch(G):
+    cdl = G.cdl
+    X = iid_pair(200, 8, 1, seed=1).X[0]
+    A, D, vol, _ = G.graph(X)
+    ch = G.chain(A, D, vol, 3, cdl.CDL_F32)
+    try:
+        ch2 = G.chain(A, D, vol, 3, cdl.CDL_F32, chain=ch)   # same shape: storage reused
+        assert ch2.value == ch.value
+        st, _ = cdl.cdl_chain_build(G.h, A, cdl.CDL_F64, D, vol.data_ptr(), 200, 4, cdl.CDL_F32, 0, ch)
+        assert st == cdl.CDL_ERR_INVALID_ARG
+    finally:
+        cdl.cdl_chain_free(ch)
+
+
+def test_workspace_cap_gives_oom():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import lib
+    cdl = lib()
+    st, h = cdl.cdl_ctx_create(0, torch.cuda.current_stream().cuda_stream, 1 << 20)
+    assert st == 0
+    try:
+        n, T = 600, 8
+        X = torch.from_numpy(iid_pair(n, T, 1, seed=1).X[0]).cuda()
+        A = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        D = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s = torch.zeros(2, dtype=torch.float64, device="cuda")
+        assert cdl.cdl_build_graph(h, X, n, T, 0.0, cdl.CDL_F64, A, D, s[0:1].data_ptr(),
+                                   s[1:2].data_ptr()) == cdl.CDL_OK
+        st, ch = cdl.cdl_chain_build(h, A, cdl.CDL_F64, D, s[0:1].data_ptr(), n, 8, cdl.CDL_F64)
+        assert st == cdl.CDL_ERR_OOM
+    finally:
+        cdl.cdl_ctx_destroy(h)
+
+
+def test_launch_counter_and_timing(G):
+    cdl = G.cdl
+    cdl.cdl_ctx_reset_counters(G.h)
+    cdl.cdl_ctx_set_timing(G.h, True)
+    X = iid_pair(256, 8, 1, seed=1).X[0]
+    G.graph(X)
+    st, n = cdl.cdl_ctx_launch_count(G.h)
+    assert st == 0 and n >= 10
+    st, ms, launches, work = cdl.cdl_ctx_timing(G.h, cdl.CDL_KC_DISTANCE)
+    assert st == 0 and launches == 3 and ms > 0 and work == 0.5 * 256 * 255 * 8
+    cdl.cdl_ctx_set_timing(G.h, False)
