@@ -131,6 +131,27 @@ int cdl_ctx_launch_count(cdl_ctx* ctx, int64_t* launches);
 int cdl_build_graph(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, double sigma,
                     cdl_dtype a_dtype, void* A, double* D, double* vol, double* sigma_out);
 
+/* Same computation and results as cdl_build_graph (float64 A), for callers
+ * that cannot let a library allocate device memory: for example a process
+ * whose device memory is all handed to its own pool allocator, where an
+ * extra cudaMalloc would fail or fragment the pool, or a service that must
+ * not allocate once it is running. The paper has no counterpart; this entry
+ * point exists for such deployments.
+ * It needs no context and calls no cudaMalloc, cudaFree or other allocating
+ * routine: all scratch lives in one statically allocated device array of
+ * about 4 MiB inside the library, held by every GPU that loads it until the
+ * process exits. Work is enqueued on `cuda_stream` (NULL = legacy default
+ * stream) on the CURRENT device, which must own X and the outputs.
+ * Limit: n * T <= 2^20 (e.g. n = 4096 with T = 256); larger inputs return
+ * CDL_ERR_INVALID_ARG before launching anything. Other limits and argument
+ * meanings as for cdl_build_graph.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.
+ * Every call uses the same array: calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, double* A,
+                           double* D, double* vol, double* sigma_out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- chain */
 
 /* Inverse chain of Alg. 2 (ChainProduct) for M = L = D - A.

@@ -63,6 +63,7 @@ _SIGS = {
     "cdl_ctx_reset_counters": [_P],
     "cdl_ctx_launch_count": [_P, ctypes.POINTER(_I64)],
     "cdl_build_graph": [_P, _P, _I64, _I32, _D, ctypes.c_int, _P, _P, _P, _P],
+    "cdl_build_graph_static": [_P, _I64, _I32, _D, _P, _P, _P, _P, _P],
     "cdl_chain_build": [_P, _P, ctypes.c_int, _P, _P, _I64, _I32, ctypes.c_int, _I32, ctypes.POINTER(_P)],
     "cdl_chain_free": [_P],
     "cdl_chain_level": [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
@@ -144,6 +145,11 @@ def cdl_ctx_launch_count(ctx):
 def cdl_build_graph(ctx, X, n, T, sigma, a_dtype, A, D, vol, sigma_out) -> int:
     return _lib.cdl_build_graph(ctx, _ptr(X), n, T, sigma, a_dtype, _ptr(A), _ptr(D), _ptr(vol),
                                 _ptr(sigma_out))
+
+
+def cdl_build_graph_static(X, n, T, sigma, A, D, vol, sigma_out, stream=None) -> int:
+    return _lib.cdl_build_graph_static(_ptr(X), n, T, sigma, _ptr(A), _ptr(D), _ptr(vol), _ptr(sigma_out),
+                                       _ptr(stream))
 
 
 def cdl_chain_build(ctx, A, a_dtype, D, vol, n, d, chain_dtype, flags=0, chain=None):

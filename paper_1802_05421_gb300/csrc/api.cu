@@ -246,6 +246,11 @@ int cdl_build_graph(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, double 
   return graph_build(ctx, X, n, T, sigma, static_cast<double*>(A), D, vol, sigma_out);
 }
 
+int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, double* A,
+                           double* D, double* vol, double* sigma_out, void* cuda_stream) {
+  return graph_build_static(X, n, T, sigma, A, D, vol, sigma_out, static_cast<cudaStream_t>(cuda_stream));
+}
+
 int cdl_chain_free(cdl_chain* ch) {
   if (!ch) return CDL_OK;
   cudaSetDevice(ch->device);

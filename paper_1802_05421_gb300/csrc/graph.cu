@@ -7,6 +7,7 @@
 //      patterns order like the values);
 //   3. A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = sum_j A_ij, vol.
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -345,6 +346,129 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
     CDL_TRY(L.done());
   }
   return CDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Graph build without any device allocation.
+//
+// Some callers cannot let a library call cudaMalloc: a process that has
+// handed (almost) all device memory to its own pool allocator, where an extra
+// allocation would fail or fragment the pool, or a service that must not
+// allocate once it is running. For them cdl_build_graph_static runs the same
+// kernels as cdl_build_graph, with all of their scratch (the fixed-point copy
+// of X, the radix-select state and histogram) in the statically allocated
+// device array below, which every GPU that loads the library holds until the
+// process exits. The caller still owns X and the outputs.
+
+constexpr size_t STATIC_XT_ELEMS = size_t(1) << 20;   // n * T limit (4 MiB of int32)
+constexpr size_t STATIC_HIST_OFF = STATIC_XT_ELEMS * sizeof(int);
+constexpr size_t STATIC_STATE_OFF = STATIC_HIST_OFF + RADIX_BINS * sizeof(unsigned long long);
+constexpr size_t STATIC_SCRATCH_BYTES = STATIC_STATE_OFF + 256;
+
+static __device__ __align__(256) unsigned char g_graph_scratch[STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_static_mu;
+void* g_static_addr[MAX_DEVICES] = {nullptr};
+
+// Device address of g_graph_scratch on the current device. The host-side
+// name is only a stand-in for the symbol, so the address is looked up once
+// per device (with that device current) and cached.
+int static_scratch(void** out) {
+  int dev = 0;
+  CDL_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAX_DEVICES) return CDL_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    CDL_CUDA_TRY(cudaGetSymbolAddress(&p, g_graph_scratch));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return CDL_OK;
+}
+
+int on_current_device(const void* p) {
+  if (!p) return CDL_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(p) % 8) return CDL_ERR_INVALID_ARG;
+  int dev = 0;
+  CDL_CUDA_TRY(cudaGetDevice(&dev));
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return CDL_ERR_INVALID_ARG;
+  }
+  if (at.type != cudaMemoryTypeDevice || at.device != dev) return CDL_ERR_INVALID_ARG;
+  return CDL_OK;
+}
+
+int launched() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+    return CDL_ERR_CUDA;
+  }
+  return CDL_OK;
+}
+
+}  // namespace
+
+int graph_build_static(const double* X, int64_t n64, int T, double sigma, double* A, double* D,
+                       double* vol, double* sigma_out, cudaStream_t s) {
+  if (n64 < 2 || n64 > (1 << 20) || T < 1 || T > 4096) return CDL_ERR_INVALID_ARG;
+  if ((size_t)n64 * (size_t)T > STATIC_XT_ELEMS) {
+    set_last_error("n * T exceeds the static scratch limit of 2^20 samples", __FILE__, __LINE__);
+    return CDL_ERR_INVALID_ARG;
+  }
+  CDL_TRY(on_current_device(X));
+  CDL_TRY(on_current_device(A));
+  CDL_TRY(on_current_device(D));
+  CDL_TRY(on_current_device(vol));
+  CDL_TRY(on_current_device(sigma_out));
+  void* base = nullptr;
+  CDL_TRY(static_scratch(&base));
+  int dev = 0, sm_count = 0;
+  CDL_CUDA_TRY(cudaGetDevice(&dev));
+  CDL_CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+  const int n = (int)n64;
+  int* Xt = static_cast<int*>(base);
+  unsigned long long* hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(base) + STATIC_HIST_OFF);
+  SelectState* st = reinterpret_cast<SelectState*>(static_cast<char*>(base) + STATIC_STATE_OFF);
+  const long long m = (long long)n * (n - 1) / 2;
+  // The array keeps the previous call's contents: the select state and the
+  // histogram must start from zero, Xt is fully overwritten.
+  k_select_init<<<1, 1, 0, s>>>(st, (m - 1) / 2);
+  CDL_TRY(launched());
+  CDL_CUDA_TRY(cudaMemsetAsync(hist, 0, RADIX_BINS * sizeof(unsigned long long), s));
+  const size_t total = (size_t)n * T;
+  k_to_fixed<<<(int)std::min<size_t>((total + 255) / 256, (size_t)sm_count * 8), 256, 0, s>>>(X, Xt, n, T, st);
+  CDL_TRY(launched());
+  const int nb = (n + DT - 1) / DT;
+  const long long tiles = (long long)nb * (nb + 1) / 2;
+  k_dist_int<<<(unsigned)tiles, 256, 0, s>>>(Xt, n, T, A, st);
+  CDL_TRY(launched());
+  k_dist_f64<<<(unsigned)tiles, 256, 0, s>>>(X, n, T, A, st);
+  CDL_TRY(launched());
+  if (sigma > 0) {
+    k_set_scalar<<<1, 1, 0, s>>>(sigma_out, sigma);
+    CDL_TRY(launched());
+  } else {
+    const int shifts[6] = {52, 40, 28, 16, 4, 0};
+    const int widths[6] = {12, 12, 12, 12, 12, 4};
+    const int hblocks = std::min(n - 1, sm_count * 4);
+    for (int p = 0; p < 6; ++p) {
+      k_select_hist<<<hblocks, 512, 0, s>>>(A, n, shifts[p], widths[p], st, hist);
+      CDL_TRY(launched());
+      k_select_step<<<1, 256, 0, s>>>(st, hist, shifts[p], widths[p], sigma_out, p == 5);
+      CDL_TRY(launched());
+    }
+  }
+  k_kernel_rows<<<std::min(n, sm_count * 8), 256, 0, s>>>(A, n, sigma_out, D);
+  CDL_TRY(launched());
+  k_sum<<<1, 1024, 0, s>>>(D, n, vol);
+  return launched();
 }
 
 }  // namespace cdl

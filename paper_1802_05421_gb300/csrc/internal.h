@@ -102,6 +102,8 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // graph.cu
 int graph_build(cdl_ctx* ctx, const double* X, int64_t n, int T, double sigma, double* A,
                 double* D, double* vol, double* sigma_out);
+int graph_build_static(const double* X, int64_t n, int T, double sigma, double* A, double* D,
+                       double* vol, double* sigma_out, cudaStream_t stream);
 // chain.cu
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A);
 int chain_square_simt(cdl_ctx* ctx, cdl_chain* ch, int level);

@@ -1,0 +1,62 @@
+"""cdl_build_graph_static: the graph build for callers that cannot let a
+library allocate device memory (for example when all device memory belongs
+to the caller's own pool allocator). It must give the same results as
+cdl_build_graph while using only the library's static scratch array, on
+consecutive calls that reuse that array with different inputs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads import iid_pair, field_sequence   # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _outputs(n):
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    D = torch.empty(n, dtype=torch.float64, device="cuda")
+    s = torch.zeros(2, dtype=torch.float64, device="cuda")
+    return A, D, s
+
+
+def test_static_graph_build_matches_allocating_entry_point():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import lib
+    cdl = lib()
+    stream = torch.cuda.current_stream()
+    st, ctx = cdl.cdl_ctx_create(0, stream.cuda_stream, 0)
+    assert st == 0
+    try:
+        inputs = [iid_pair(1000, 64, 3, seed=31).X[1],             # exact integer distances
+                  field_sequence(16, 48, 100, 2, seed=32).X[1],     # second call, other sizes
+                  np.random.default_rng(33).standard_normal((700, 9)) + 1e-7]   # off-grid path
+        for X in inputs:
+            n, T = X.shape
+            Xd = torch.from_numpy(X).cuda()
+            A0, D0, s0 = _outputs(n)
+            assert cdl.cdl_build_graph(ctx, Xd, n, T, 0.0, cdl.CDL_F64, A0, D0, s0[0:1].data_ptr(),
+                                       s0[1:2].data_ptr()) == 0
+            A1, D1, s1 = _outputs(n)
+            assert cdl.cdl_build_graph_static(Xd, n, T, 0.0, A1, D1, s1[0:1].data_ptr(), s1[1:2].data_ptr(),
+                                              stream.cuda_stream) == 0
+            torch.cuda.synchronize()
+            assert torch.equal(s0, s1)                       # sigma and vol
+            assert torch.allclose(A0, A1, rtol=1e-15, atol=0)
+            assert torch.allclose(D0, D1, rtol=1e-13, atol=0)
+    finally:
+        cdl.cdl_ctx_destroy(ctx)
+
+
+def test_static_graph_build_rejects_oversized_input():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import lib
+    cdl = lib()
+    n, T = 8192, 256                      # n * T = 2^21 > 2^20
+    X = torch.zeros((n, T), dtype=torch.float64, device="cuda")
+    A = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+    s = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert cdl.cdl_build_graph_static(X, n, T, 0.0, A, s, s[0:1].data_ptr(), s[1:2].data_ptr(), None) == \
+        cdl.CDL_ERR_INVALID_ARG
