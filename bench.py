@@ -188,6 +188,54 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- profiling cases
+def run_case(args):
+    """Small single-kernel cases for profiler captures (not a bench line):
+    graph build, then per case: square (one bf16 chain squaring), solve
+    (bf16 chain d=4 + refinement), project, score."""
+    import torch
+    from paper_1802_05421_gb300 import build as B
+    B.build()
+    from paper_1802_05421_gb300 import cdl
+    from workloads import iid_pair
+    wl = iid_pair(args.n, 64, 8, seed=5)
+    n, T = wl.X[0].shape
+    st, ctx = cdl.cdl_ctx_create(0, torch.cuda.current_stream().cuda_stream, 0)
+    assert st == 0
+    X = torch.from_numpy(wl.X[0]).cuda()
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    D = torch.empty(n, dtype=torch.float64, device="cuda")
+    sc = torch.zeros(2, dtype=torch.float64, device="cuda")
+    vol, sig = sc[0:1].data_ptr(), sc[1:2].data_ptr()
+    k = K_PROJ
+    Y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    Z = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    ch = None
+    for _ in range(args.reps):
+        assert cdl.cdl_build_graph(ctx, X, n, T, 0.0, cdl.CDL_F64, A, D, vol, sig) == 0
+        if args.case in ("square", "solve"):
+            st, ch = cdl.cdl_chain_build(ctx, A, cdl.CDL_F64, D, vol, n, 2 if args.case == "square" else 4,
+                                         cdl.CDL_BF16, 0, ch)
+            assert st == 0
+        if args.case in ("project", "solve", "score"):
+            assert cdl.cdl_project(ctx, A, cdl.CDL_F64, n, k, SEED, Y) == 0
+        if args.case == "solve":
+            st = cdl.cdl_chain_solve(ctx, ch, A, cdl.CDL_F64, Y, k, cdl.cdl_solve_opts(3, 0.0, 0), Z, None)
+            assert st == 0
+        if args.case == "score":
+            F = torch.empty(n, dtype=torch.float64, device="cuda")
+            top = torch.empty(TOPK, dtype=torch.int64, device="cuda")
+            Z2 = Y * 1e-3
+            assert cdl.cdl_cad_score(ctx, A, A.flip(0).contiguous(), cdl.CDL_F64, Z2, Z2 * 1.5, vol, vol, n, k,
+                                     cdl.CDL_F32, TOPK, F, top) == 0
+    assert cdl.cdl_sync(ctx) == 0
+    if ch is not None:
+        cdl.cdl_chain_free(ch)
+    cdl.cdl_ctx_destroy(ctx)
+    print(f"case {args.case} n={n} reps={args.reps} ok")
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -198,7 +246,13 @@ def main():
     ap.add_argument("--chain", default="bf16", choices=["bf16", "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--case", default=None, choices=["square", "solve", "project", "score"],
+                    help="run a small single-kernel case for a profiler capture instead of the bench")
+    ap.add_argument("--n", type=int, default=12288)
+    ap.add_argument("--reps", type=int, default=1)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
