@@ -197,8 +197,11 @@ typedef struct {
   int32_t max_iter;   /* preconditioner applications, >= 1 (paper's q - 1)   */
   double rel_tol;     /* stop when ||Y - L Z||_F <= rel_tol ||Y||_F; 0 = run
                          exactly max_iter applications                       */
-  int32_t flags;      /* reserved, 0                                         */
+  int32_t flags;      /* CDL_SOLVE_* bits                                    */
 } cdl_solve_opts;
+/* Form the float-float residual after every application (default: after the
+ * first one, then update it recursively, R -= L dZ, in float32). */
+enum { CDL_SOLVE_FULL_RESIDUAL = 1 };
 
 typedef struct {
   int32_t iters;              /* preconditioner applications performed        */
@@ -214,7 +217,13 @@ typedef struct {
  * then Z is shifted to D-weighted zero column means (sum_i D_i Z[i,:] = 0).
  * For Z_0 = 0 this is the paper's y_{t+1} = y_t - P2 y_t + chi with
  * chi = P1 b and P2 = P1 L. The residual Y - L Z is formed in float-float
- * arithmetic (about 48 significant bits) from float64 A, D, Y, Z.
+ * arithmetic (about 48 significant bits) from float64 A, D, Y, Z after the
+ * first application; later steps update it recursively, R -= D dZ - A dZ,
+ * with A dZ in float32 (error about 1e-7 of ||L dZ||, i.e. of the previous
+ * residual). A bound on the accumulated error of these updates is kept; when
+ * the stopping test passes with that bound above rel_tol / 10, the residual
+ * is formed in float-float again before stopping. flags =
+ * CDL_SOLVE_FULL_RESIDUAL forms it in float-float after every application.
  * Synchronises once per application to read the residual norm.
  * chain: from cdl_chain_build on the same graph. A: device n x n (CDL_F64).
  * Y: device n x k float64. Z: device n x k float64 output.

@@ -24,6 +24,7 @@ CDL_ERR_TIMEOUT = -5
 CDL_ERR_UNSUPPORTED = -6
 
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3 = 0, 1, 2, 3
+CDL_SOLVE_FULL_RESIDUAL = 1
 
 (CDL_KC_DISTANCE, CDL_KC_SELECT, CDL_KC_KERNEL, CDL_KC_CHAIN_INIT, CDL_KC_SQUARE, CDL_KC_APPLY,
  CDL_KC_RESIDUAL, CDL_KC_PROJECT, CDL_KC_SCORE, CDL_KC_TOPK, CDL_KC_MISC, CDL_KC_COUNT) = range(12)

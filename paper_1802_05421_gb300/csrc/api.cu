@@ -339,7 +339,8 @@ int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const void* A, cdl_dtype 
                     const double* Y, int32_t k, const cdl_solve_opts* opts, double* Z,
                     cdl_solve_stats* stats) {
   if (!ctx || !ch || !opts) return CDL_ERR_INVALID_ARG;
-  if (k < 1 || k > 1024 || opts->max_iter < 1 || opts->rel_tol < 0 || opts->flags != 0)
+  if (k < 1 || k > 1024 || opts->max_iter < 1 || opts->rel_tol < 0 ||
+      (opts->flags & ~CDL_SOLVE_FULL_RESIDUAL) != 0)
     return CDL_ERR_INVALID_ARG;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
   if (ch->device != ctx->device) return CDL_ERR_INVALID_ARG;

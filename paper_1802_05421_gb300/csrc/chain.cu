@@ -64,6 +64,30 @@ __global__ void __launch_bounds__(256) k_chain_init(const double* __restrict__ A
   }
 }
 
+// bf16 levels: the same formula in float32 arithmetic, A_ij (rf_i rf_j) - uf_i uf_j
+// with float copies of D^{-1/2} and u; the float32 error (a few 1e-7 relative to
+// either product) is far below the bf16 rounding of the result.
+__global__ void __launch_bounds__(256) k_chain_init_bf16(const double* __restrict__ A, int n, int npad,
+                                                          const double* __restrict__ rsd,
+                                                          const double* __restrict__ u,
+                                                          __nv_bfloat16* __restrict__ L0) {
+  for (int i = blockIdx.x; i < npad; i += gridDim.x) {
+    __nv_bfloat16* out = L0 + (size_t)i * npad;
+    if (i >= n) {
+      for (int j = threadIdx.x; j < npad; j += blockDim.x) out[j] = __float2bfloat16_rn(0.f);
+      continue;
+    }
+    const float ri = (float)rsd[i], ui = (float)u[i];
+    const double* row = A + (size_t)i * n;
+    for (int j = threadIdx.x; j < npad; j += blockDim.x) {
+      float v = 0.f;
+      if (j < n)
+        v = __fmaf_rn(__double2float_rn(row[j]), __fmul_rn(ri, (float)rsd[j]), -__fmul_rn(ui, (float)u[j]));
+      out[j] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
 __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
   double fnb = nb + 0.5;
   int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
@@ -233,8 +257,8 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
                                                            static_cast<float*>(ch->level(0)));
       break;
     case CDL_BF16:
-      k_chain_init<__nv_bfloat16><<<blocks, 256, 0, ctx->stream>>>(
-          A, n, np, ch->rsqrt_d, u, static_cast<__nv_bfloat16*>(ch->level(0)));
+      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(A, n, np, ch->rsqrt_d, u,
+                                                          static_cast<__nv_bfloat16*>(ch->level(0)));
       break;
     default:
       return CDL_ERR_UNSUPPORTED;

@@ -1,0 +1,95 @@
+// Float-float ("double-float") arithmetic on the float32 pipes, built from the
+// classical error-free transformations: TwoSum (Knuth, TAOCP vol. 2), FastTwoSum
+// (Dekker 1971) and TwoProduct through a fused multiply-add. A value is hi + lo
+// with |lo| <= ulp(hi)/2, about 48 significant bits. Used where float64-class
+// accuracy is needed in O(n^2) work, because float64 runs at about 1/72 of the
+// float32 rate on this GPU.
+#pragma once
+
+#include <cstdint>
+
+namespace cdl {
+
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ ff ff_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// exp(-t) for float64 t >= 0, as the float-float pair q and the integer k with
+// exp(-t) = (q.hi + q.lo) 2^-k, to about 2^-46 relative. Written from the series
+// definition: t = k ln2 + r with k = round(t / ln2) and |r| <= ln2/2, so
+// exp(-t) = 2^-k exp(-r). The reduction is done in float64 with ln2 split
+// Cody-Waite style into a 40-bit head (k * head exact for |k| < 2^13) and a tail,
+// so r carries float64 accuracy. exp(-r) is the Taylor series to degree 12
+// (remainder below 2^-52 for |r| <= 0.35): degrees 7..12 in float32 (each term
+// below 2^-22 of the result), degrees 0..6 in float-float Horner steps; the
+// coefficients 1/m! are stored as float pairs. Valid for t < 700.
+__device__ __forceinline__ ff ff_exp_neg_scaled(double t, int& k_out) {
+  const float k = rintf(__fmul_rn(__double2float_rn(t), 0x1.715476p+0f));   // t / ln2
+  const double kd = (double)k;
+  double r = fma(-kd, 0x1.62e42fefa2000p-1, t);
+  r = fma(-kd, 0x1.9ef35793c7673p-41, r);
+  const ff rf = ff_from_double(r);
+  const ff x = {-rf.hi, -rf.lo};
+  float p = 0x1.1eed8ep-29f;                      // 1/12!
+  p = __fmaf_rn(p, x.hi, 0x1.ae6456p-26f);        // 1/11!
+  p = __fmaf_rn(p, x.hi, 0x1.27e4fcp-22f);        // 1/10!
+  p = __fmaf_rn(p, x.hi, 0x1.71de3ap-19f);        // 1/9!
+  p = __fmaf_rn(p, x.hi, 0x1.a01a02p-16f);        // 1/8!
+  p = __fmaf_rn(p, x.hi, 0x1.a01a02p-13f);        // 1/7!
+  ff q = {p, 0.f};
+  q = ff_add(ff_mul(q, x), ff{0x1.6c16c2p-10f, -0x1.27d27ep-35f});   // 1/6!
+  q = ff_add(ff_mul(q, x), ff{0x1.111112p-7f, -0x1.dddddep-32f});    // 1/5!
+  q = ff_add(ff_mul(q, x), ff{0x1.555556p-5f, -0x1.555556p-30f});    // 1/4!
+  q = ff_add(ff_mul(q, x), ff{0x1.555556p-3f, -0x1.555556p-28f});    // 1/3!
+  q = ff_add(ff_mul(q, x), ff{0x1p-1f, 0.f});                        // 1/2!
+  q = ff_add(ff_mul(q, x), ff{1.f, 0.f});                            // 1/1!
+  q = ff_add(ff_mul(q, x), ff{1.f, 0.f});                            // 1/0!
+  k_out = (int)k;
+  return q;                                                          // in [0.70, 1.42]
+}
+
+// exp(-t) as float64 (see ff_exp_neg_scaled); float64 exp beyond t = 700.
+__device__ __forceinline__ double ff_exp_neg(double t) {
+  if (!(t < 700.0)) return exp(-t);
+  int k;
+  const ff q = ff_exp_neg_scaled(t, k);
+  const double v = ff_to_double(q);
+  // times 2^-k through the exponent field (v and the result are normal numbers)
+  return __longlong_as_double(__double_as_longlong(v) - ((long long)k << 52));
+}
+
+}  // namespace cdl

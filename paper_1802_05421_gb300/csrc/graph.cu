@@ -9,6 +9,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace cdl {
@@ -230,23 +231,43 @@ __global__ void k_select_step(SelectState* st, unsigned long long* hist, int shi
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 // A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = row sum. One block per row.
+// The exponential is ff_exp_neg_scaled (float64 argument reduction, float-float
+// series, about 1e-14 relative); the argument is d2 * (1 / (2 sigma^2)) (one
+// float64 product); the row sum is accumulated in float-float (terms below
+// 2^-100 are dropped from the sum, not from A).
 __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int n,
                                                       const double* __restrict__ sigma,
                                                       double* __restrict__ D) {
   __shared__ double red[8];
   const double s = *sigma;
-  const double two_s2 = 2.0 * (s * s);
+  const double rcp = 1.0 / (2.0 * (s * s));
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     double* row = A + (size_t)i * n;
-    double acc = 0.0;
+    ff acc = {0.f, 0.f};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double a = (j == i) ? 0.0 : exp(-(row[j] / two_s2));
+      const double t = row[j] * rcp;
+      double a = 0.0;
+      if (j != i) {
+        if (t < 700.0) {
+          int k;
+          const ff q = ff_exp_neg_scaled(t, k);
+          a = __longlong_as_double(__double_as_longlong(ff_to_double(q)) - ((long long)k << 52));
+          if (k <= 100) {
+            const float sc = __int_as_float((127 - k) << 23);   // 2^-k
+            const ff ts = two_sum(acc.hi, __fmul_rn(q.hi, sc));
+            acc.hi = ts.hi;
+            acc.lo = __fadd_rn(acc.lo, __fadd_rn(ts.lo, __fmul_rn(q.lo, sc)));
+          }
+        } else {
+          a = exp(-t);
+        }
+      }
       row[j] = a;
-      acc += a;
     }
+    double accd = (double)acc.hi + (double)acc.lo;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) accd += __shfl_xor_sync(0xffffffffu, accd, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;

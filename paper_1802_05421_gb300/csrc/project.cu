@@ -7,9 +7,10 @@
 // (i, j, r / 128, 0) with key (seed low word, seed high word): bit (r mod 32)
 // of output word ((r mod 128) / 32) set means +1.
 //
-// Each thread owns one node row i and 32 projection rows (one Philox word);
-// sqrt(A_ij) is formed once per tile in float-float, and the signed sums are
-// accumulated in float-float (TwoSum) on the float32 pipes.
+// Each thread owns one node row i and 32 projection rows (one Philox word).
+// Per tile of 32 edges the block forms sqrt(A_ij) in float-float once per
+// (row, edge) and one Philox call per (row, edge, 128 projection rows), shared
+// through shared memory by the threads of the row.
 #include <cmath>
 
 #include "internal.h"
@@ -39,76 +40,111 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-constexpr int JT = 32;   // j-tile
+constexpr int JT = 32;       // j-tile
+constexpr int CHUNK = 4096;  // exact float32 accumulation length (multiple of JT)
+constexpr int MAX_RPB = 64;  // node rows per block
 
+// Each (node row i, edge j) term o_ij sqrt(A_ij) is split into three float
+// pieces p1 + p2 + p3: p1 on the 2^-12 grid (|p1| <= 1), p2 on the 2^-24 grid
+// (|p2| <= 2^-13) and the remainder p3 (|p3| <= 2^-24). Signed sums of up to
+// 4096 p1 (or p2) values stay on their grid below 2^24 grid steps, so float32
+// adds them exactly; p3 is small enough for plain float32 sums. The three
+// partial sums are flushed to float64 in Y every 4096 edges. Per term and
+// projection row this is one sign construction and three fused multiply-adds
+// with +-1 (exact products).
 __global__ void __launch_bounds__(256) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
                                                   uint32_t key0, uint32_t key1, double scale,
                                                   double* __restrict__ Y) {
-  extern __shared__ float sm[];
-  float* Sh = sm;                    // [rpb][JT]
-  float* Sl = sm + rpb * JT;         // [rpb][JT]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* P1 = reinterpret_cast<float*>(smraw);          // [rpb][JT]
+  float* P2 = P1 + rpb * JT;                            // [rpb][JT]
+  float* P3 = P2 + rpb * JT;                            // [rpb][JT]
+  uint4* Wd = reinterpret_cast<uint4*>(P3 + rpb * JT);  // [rpb][JT][nrb]
+  const int nrb = (W + 3) / 4;
   const int t = threadIdx.x;
   const int rl = t / W, w = t % W;
   const int i0 = blockIdx.x * rpb;
   const int i = i0 + rl;
   const bool active = rl < rpb && i < n;
-  float ah[32], al[32];
+  float a1[32], a2[32], a3[32];
 #pragma unroll
-  for (int b = 0; b < 32; ++b) ah[b] = al[b] = 0.f;
+  for (int b = 0; b < 32; ++b) a1[b] = a2[b] = a3[b] = 0.f;
+  auto flush = [&]() {
+    if (!active) return;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const int r = w * 32 + b;
+      if (r < k) Y[(size_t)i * k + r] += ((double)a1[b] + (double)a2[b]) + (double)a3[b];
+      a1[b] = a2[b] = a3[b] = 0.f;
+    }
+  };
   for (int j0 = 0; j0 < n; j0 += JT) {
+    if (j0 > 0 && j0 % CHUNK == 0) flush();
     __syncthreads();
+    // pieces of o_ij sqrt(A_ij) for the tile
     for (int e = t; e < rpb * JT; e += blockDim.x) {
       const int rr = e / JT, jj = e % JT;
       const int ii = i0 + rr, j = j0 + jj;
-      float sh = 0.f, sl = 0.f;
-      if (ii < n && j < n) {
-        const double a = A[(size_t)ii * n + j];
-        const float h = (float)a;
-        const float l = (float)(a - (double)h);
-        if (h > 0.f) {
-          sh = sqrtf(h);
-          // sqrt(h + l) = sh + (h - sh^2 + l) / (2 sh) to float-float accuracy
-          const float res = __fadd_rn(__fmaf_rn(-sh, sh, h), l);
-          sl = res / (2.f * sh);
+      float p1 = 0.f, p2 = 0.f, p3 = 0.f;
+      if (ii < n && j < n && j != ii) {
+        const double av = A[(size_t)ii * n + j];
+        const float ah = __double2float_rn(av);
+        const float al = __double2float_rn(av - (double)ah);
+        if (ah > 0.f) {
+          // sqrt(ah + al) = sh + sl with sl = (ah - sh^2 + al) / (2 sh)
+          const float sh = __fsqrt_rn(ah);
+          const float res = __fadd_rn(__fmaf_rn(-sh, sh, ah), al);
+          const float sl = __fmul_rn(res, __fdiv_rn(0.5f, sh));
+          p1 = __fmul_rn(rintf(__fmul_rn(sh, 4096.f)), 0x1p-12f);
+          const float rem = __fsub_rn(sh, p1);                   // exact
+          p2 = __fmul_rn(rintf(__fmul_rn(rem, 16777216.f)), 0x1p-24f);
+          p3 = __fadd_rn(__fsub_rn(rem, p2), sl);
+          if (j < ii) {   // ii is the tail of edge (j, ii)
+            p1 = -p1;
+            p2 = -p2;
+            p3 = -p3;
+          }
         }
       }
-      Sh[e] = sh;
-      Sl[e] = sl;
+      P1[e] = p1;
+      P2[e] = p2;
+      P3[e] = p3;
+    }
+    // Philox words: one call per (row, edge, 128-row block of the projection)
+    for (int c = t; c < rpb * JT * nrb; c += blockDim.x) {
+      const int rb = c % nrb, e = c / nrb;
+      const int rr = e / JT, jj = e % JT;
+      const int ii = i0 + rr, j = j0 + jj;
+      uint4 o = make_uint4(0u, 0u, 0u, 0u);
+      if (ii < n && j < n && j != ii)
+        o = philox4x32_10(make_uint4((uint32_t)min(ii, j), (uint32_t)max(ii, j), (uint32_t)rb, 0u), key0, key1);
+      Wd[e * nrb + rb] = o;
     }
     __syncthreads();
     if (!active) continue;
     const int jmax = min(JT, n - j0);
+    const int wi = w & 3, rb = w >> 2;
     for (int jj = 0; jj < jmax; ++jj) {
-      const int j = j0 + jj;
-      if (j == i) continue;
-      float sh = Sh[rl * JT + jj], sl = Sl[rl * JT + jj];
-      if (j < i) {   // i is the tail of edge (j, i)
-        sh = -sh;
-        sl = -sl;
-      }
-      const uint32_t lo = (uint32_t)min(i, j), hi = (uint32_t)max(i, j);
-      const uint4 o = philox4x32_10(make_uint4(lo, hi, (uint32_t)(w >> 2), 0u), key0, key1);
-      const uint32_t wi = w & 3;
+      const int e = rl * JT + jj;
+      const float p1 = P1[e], p2 = P2[e], p3 = P3[e];
+      const uint4 o = Wd[e * nrb + rb];
       const uint32_t bits = wi == 0 ? o.x : wi == 1 ? o.y : wi == 2 ? o.z : o.w;
-      const uint32_t shb = __float_as_uint(sh), slb = __float_as_uint(sl);
+      const uint32_t nb = ~bits;   // clear bit -> -1
 #pragma unroll
       for (int b = 0; b < 32; ++b) {
-        const uint32_t neg = ((~bits >> b) & 1u) << 31;   // clear bit -> -1
-        const float th = __uint_as_float(shb ^ neg);
-        const float tl = __uint_as_float(slb ^ neg);
-        const float s = __fadd_rn(ah[b], th);
-        const float bp = __fsub_rn(s, ah[b]);
-        const float err = __fadd_rn(__fsub_rn(ah[b], __fsub_rn(s, bp)), __fsub_rn(th, bp));
-        ah[b] = s;
-        al[b] = __fadd_rn(al[b], __fadd_rn(err, tl));
+        const float sg = __uint_as_float(((nb << (31 - b)) & 0x80000000u) | 0x3f800000u);
+        a1[b] = __fmaf_rn(sg, p1, a1[b]);
+        a2[b] = __fmaf_rn(sg, p2, a2[b]);
+        a3[b] = __fmaf_rn(sg, p3, a3[b]);
       }
     }
   }
+  flush();
   if (!active) return;
 #pragma unroll
   for (int b = 0; b < 32; ++b) {
     const int r = w * 32 + b;
-    if (r < k) Y[(size_t)i * k + r] = ((double)ah[b] + (double)al[b]) * scale;
+    if (r < k) Y[(size_t)i * k + r] *= scale;
   }
 }
 
@@ -117,16 +153,18 @@ __global__ void __launch_bounds__(256) k_project(const double* __restrict__ A, i
 int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, double* Y) {
   const int n = (int)n64;
   const int W = (k + 31) / 32;
-  const int rpb = std::max(1, std::min(128, 256 / W));
+  const int rpb = std::max(1, std::min(MAX_RPB, 256 / W));
   const int threads = rpb * W;
-  const size_t smem = 2 * (size_t)rpb * JT * sizeof(float);
+  const int nrb = (W + 3) / 4;
+  const size_t smem = 3 * (size_t)rpb * JT * sizeof(float) + (size_t)rpb * JT * nrb * sizeof(uint4);
   const int blocks = (n + rpb - 1) / rpb;
   const double scale = 1.0 / std::sqrt((double)k);
   static bool attr = false;
   if (!attr) {
-    CDL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
+  CDL_CUDA_TRY(cudaMemsetAsync(Y, 0, (size_t)n * k * sizeof(double), ctx->stream));
   Launch L(ctx, CDL_KC_PROJECT, (double)n * (n - 1) * k);
   k_project<<<blocks, threads, smem, ctx->stream>>>(A, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
                                                     (uint32_t)(seed >> 32), scale, Y);

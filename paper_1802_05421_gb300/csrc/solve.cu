@@ -67,13 +67,17 @@ __global__ void k_precond_in(const double* __restrict__ R, const double* __restr
   x[idx] = (T)v;
 }
 
+// Z += dZ with dZ = D^{-1/2} x; dZ is also kept in float32 for the recursive
+// residual update.
 template <typename T>
 __global__ void k_precond_out(const T* __restrict__ x, const double* __restrict__ rsd, int n, int k,
-                              int kp, double* __restrict__ Z) {
+                              int kp, double* __restrict__ Z, float* __restrict__ dZ) {
   size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * k) return;
   int i = (int)(idx / k), r = (int)(idx % k);
-  Z[idx] += (double)x[(size_t)i * kp + r] * rsd[i];
+  const double dz = (double)x[(size_t)i * kp + r] * rsd[i];
+  Z[idx] += dz;
+  dZ[idx] = (float)dz;
 }
 
 // x[i][r] += sum_s part[s][i][r] (CUDA-core chains)
@@ -261,6 +265,83 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, 
   }
 }
 
+// Recursive residual update R -= D o dZ - A dZ for a 64-row x 128-column tile,
+// A dZ accumulated in float32; per-block sum of the new R^2. The update is
+// small (|dZ| shrinks with the residual), so its float32 error, about 1e-7 of
+// ||L dZ||, stays far below the float-float residual it corrects.
+__global__ void __launch_bounds__(256) k_residual_update(const double* __restrict__ A, const float* __restrict__ dZ,
+                                                          const double* __restrict__ D, int n, int k,
+                                                          double* __restrict__ R, double* __restrict__ part) {
+  __shared__ float As[RB_K][RB_M + 1];
+  __shared__ __align__(16) float Bs[RB_K][RB_N];
+  __shared__ double red[8];
+  const int i0 = blockIdx.x * RB_M, c0 = blockIdx.y * RB_N;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  const int rows[4] = {ty * 2, ty * 2 + 1, 32 + ty * 2, 32 + ty * 2 + 1};
+  for (int j0 = 0; j0 < n; j0 += RB_K) {
+#pragma unroll
+    for (int e = 0; e < (RB_M * RB_K) / 256; ++e) {
+      const int idx = tid + e * 256;
+      const int ii = idx / RB_K, jj = idx % RB_K;
+      const int i = i0 + ii, j = j0 + jj;
+      As[jj][ii] = (i < n && j < n) ? (float)A[(size_t)i * n + j] : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < (RB_N * RB_K) / 256; ++e) {
+      const int idx = tid + e * 256;
+      const int jj = idx / RB_N, cc = idx % RB_N;
+      const int j = j0 + jj, c = c0 + cc;
+      Bs[jj][cc] = (j < n && c < k) ? dZ[(size_t)j * k + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < RB_K; ++jj) {
+      float av[4], bv[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[jj][rows[a]];
+      const float4 h0 = *reinterpret_cast<const float4*>(&Bs[jj][tx * 4]);
+      const float4 h1 = *reinterpret_cast<const float4*>(&Bs[jj][64 + tx * 4]);
+      bv[0] = h0.x; bv[1] = h0.y; bv[2] = h0.z; bv[3] = h0.w;
+      bv[4] = h1.x; bv[5] = h1.y; bv[6] = h1.z; bv[7] = h1.w;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  double sq = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + rows[a];
+    if (i >= n) continue;
+    const double di = D[i];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int c = c0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
+      if (c >= k) continue;
+      const size_t o = (size_t)i * k + c;
+      const double r = R[o] - (di * (double)dZ[o] - (double)acc[a][b]);
+      R[o] = r;
+      sq = fma(r, r, sq);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((tid & 31) == 0) red[tid >> 5] = sq;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 int largest_divisor_at_most(int total, int target) {
   int best = 1;
   for (int s = 1; s <= total && s <= target; ++s)
@@ -304,6 +385,8 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   CDL_TRY(ws_get(ctx, "solve.zh", (size_t)n * k * 4, &vzh));
   CDL_TRY(ws_get(ctx, "solve.zl", (size_t)n * k * 4, &vzl));
   CDL_TRY(ws_get(ctx, "solve.colsum", (size_t)cs_parts * k * 8, &vcs));
+  void* vdz;
+  CDL_TRY(ws_get(ctx, "solve.dz", (size_t)n * k * 4, &vdz));
   double* R = static_cast<double*>(vR);
   double* red = static_cast<double*>(vred);
   double* scal = static_cast<double*>(vscal);
@@ -336,10 +419,60 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
     for (double& h : stats->history) h = 0.0;
   }
   if (yy == 0.0) return CDL_OK;
+  // Full float-float residual R = Y - L Z; returns ||R|| / ||Y||.
+  auto full_residual = [&](double* rel_out) -> int {
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_split<<<blocks_for(nk, 256), 256, 0, st>>>(Z, nk, static_cast<float*>(vzh), static_cast<float*>(vzl));
+      CDL_TRY(L.done());
+    }
+    {
+      dim3 g(res_gx, res_gy);
+      Launch L(ctx, CDL_KC_RESIDUAL, (double)n * n * k);
+      k_residual<<<g, 256, 0, st>>>(A, static_cast<const float*>(vzh), static_cast<const float*>(vzl), Z, Y,
+                                     ch->D, n, k, R, red);
+      CDL_TRY(L.done());
+    }
+    return CDL_OK;
+  };
+  // Recursive update R -= L dZ in float32.
+  auto update_residual = [&]() -> int {
+    dim3 g(res_gx, res_gy);
+    Launch L(ctx, CDL_KC_RESIDUAL, (double)n * n * k);
+    k_residual_update<<<g, 256, 0, st>>>(A, static_cast<const float*>(vdz), ch->D, n, k, R, red);
+    return L.done();
+  };
+  auto read_norm = [&](double* rel_out) -> int {
+    double rr = 0.0;
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_reduce<<<1, 1024, 0, st>>>(red, res_gx * res_gy, scal + 1);
+      CDL_TRY(L.done());
+    }
+    CDL_CUDA_TRY(cudaMemcpyAsync(&rr, scal + 1, 8, cudaMemcpyDeviceToHost, st));
+    CDL_CUDA_TRY(cudaStreamSynchronize(st));
+    *rel_out = std::sqrt(rr / yy);
+    return CDL_OK;
+  };
+
   double rel = 1.0;
   int iters = 0;
+  bool exact_r = true;      // R was last formed in full (not recursively)
+  double drift = 0.0;       // bound on the recursive residual's accumulated error
+  const bool always_full = (opts->flags & CDL_SOLVE_FULL_RESIDUAL) != 0;
   while (true) {
-    if (opts->rel_tol > 0 && rel <= opts->rel_tol) break;
+    if (opts->rel_tol > 0 && rel <= opts->rel_tol) {
+      if (!exact_r && rel + drift > 0.1 * opts->rel_tol) {
+        // certify a recursively updated residual with a full one
+        CDL_TRY(full_residual(nullptr));
+        CDL_TRY(read_norm(&rel));
+        exact_r = true;
+        drift = 0.0;
+        if (stats && iters >= 1 && iters <= 64) stats->history[iters - 1] = rel;
+        continue;
+      }
+      break;
+    }
     if (iters >= opts->max_iter) break;
     // x = D^{-1/2} R in the chain's working precision
     {
@@ -387,10 +520,10 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       Launch L(ctx, CDL_KC_MISC, 0);
       if (ch->dtype == CDL_F64)
         k_precond_out<double><<<blocks_for(nk, 256), 256, 0, st>>>(static_cast<const double*>(vx), ch->rsqrt_d,
-                                                                    n, k, kp, Z);
+                                                                    n, k, kp, Z, static_cast<float*>(vdz));
       else
         k_precond_out<float><<<blocks_for(nk, 256), 256, 0, st>>>(static_cast<const float*>(vx), ch->rsqrt_d,
-                                                                   n, k, kp, Z);
+                                                                   n, k, kp, Z, static_cast<float*>(vdz));
       CDL_TRY(L.done());
     }
     {
@@ -405,28 +538,16 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       CDL_TRY(L.done());
     }
     ++iters;
-    // R = Y - L Z in float-float
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_split<<<blocks_for(nk, 256), 256, 0, st>>>(Z, nk, static_cast<float*>(vzh), static_cast<float*>(vzl));
-      CDL_TRY(L.done());
+    if (iters == 1 || always_full) {
+      CDL_TRY(full_residual(nullptr));
+      exact_r = true;
+      drift = 0.0;
+    } else {
+      CDL_TRY(update_residual());
+      drift += 1e-6 * rel;   // float32 error of L dZ, with |L dZ| about |R| before the step
+      exact_r = false;
     }
-    {
-      dim3 g(res_gx, res_gy);
-      Launch L(ctx, CDL_KC_RESIDUAL, (double)n * n * k);
-      k_residual<<<g, 256, 0, st>>>(A, static_cast<const float*>(vzh), static_cast<const float*>(vzl), Z, Y,
-                                     ch->D, n, k, R, red);
-      CDL_TRY(L.done());
-    }
-    double rr = 0.0;
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_reduce<<<1, 1024, 0, st>>>(red, res_gx * res_gy, scal + 1);
-      CDL_TRY(L.done());
-    }
-    CDL_CUDA_TRY(cudaMemcpyAsync(&rr, scal + 1, 8, cudaMemcpyDeviceToHost, st));
-    CDL_CUDA_TRY(cudaStreamSynchronize(st));
-    rel = std::sqrt(rr / yy);
+    CDL_TRY(read_norm(&rel));
     if (stats && iters <= 64) stats->history[iters - 1] = rel;
   }
   if (stats) {

@@ -78,11 +78,11 @@ class Ctx:
         self.check(st)
         return view_device(ptr, (npad, npad), dtype)
 
-    def solve(self, ch, A, Y, max_iter=20, rel_tol=1e-10, expect=0):
+    def solve(self, ch, A, Y, max_iter=20, rel_tol=1e-10, expect=0, flags=0):
         cdl = self.cdl
         n, k = Y.shape
         Z = torch.empty((n, k), dtype=torch.float64, device="cuda")
-        opts = cdl.cdl_solve_opts(max_iter, rel_tol, 0)
+        opts = cdl.cdl_solve_opts(max_iter, rel_tol, flags)
         stats = cdl.cdl_solve_stats()
         st = cdl.cdl_chain_solve(self.h, ch, A, cdl.CDL_F64, Y, k, opts, Z, stats)
         assert st == expect, cdl.cdl_status_string(st)

@@ -15,6 +15,12 @@ from workloads import iid_pair, field_sequence, to_grid   # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
+# The kernel values come from a float-float exponential (float64 argument
+# reduction, degree-12 series in float-float): relative error below 1e-14
+# for the arguments d^2 / (2 sigma^2) < 60 that occur here; numpy's exp is
+# within one float64 ulp.
+A_RTOL = 2e-14
+
 
 @pytest.fixture(scope="module")
 def G():
@@ -39,7 +45,7 @@ def test_graph_matches_oracle(G, n, T):
     A, D, vol, sig = G.graph(X)
     Ao, Do, volo, sigo = O.gaussian_graph(X)
     assert _h(sig)[0] == sigo                       # exact selection on exact distances
-    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(_h(A), Ao, rtol=A_RTOL, atol=0)
     np.testing.assert_allclose(_h(D), Do, rtol=1e-13)
     assert math.isclose(_h(vol)[0], volo, rel_tol=1e-13)
 
@@ -50,7 +56,7 @@ def test_graph_off_grid_uses_float64_path(G):
     A, D, vol, sig = G.graph(X)
     Ao, Do, volo, sigo = O.gaussian_graph(X)
     assert _h(sig)[0] == sigo
-    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(_h(A), Ao, rtol=A_RTOL, atol=0)
 
 
 def test_graph_given_sigma(G):
@@ -58,7 +64,7 @@ def test_graph_given_sigma(G):
     A, D, vol, sig = G.graph(X, sigma=1.75)
     Ao, Do, volo, _ = O.gaussian_graph(X, sigma=1.75)
     assert _h(sig)[0] == 1.75
-    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(_h(A), Ao, rtol=A_RTOL, atol=0)
 
 
 def test_graph_field_workload(G):
@@ -66,7 +72,7 @@ def test_graph_field_workload(G):
     A, D, vol, sig = G.graph(X)
     Ao, Do, volo, sigo = O.gaussian_graph(X)
     assert _h(sig)[0] == sigo
-    np.testing.assert_allclose(_h(A), Ao, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(_h(A), Ao, rtol=A_RTOL, atol=0)
 
 
 # ------------------------------------------------------------------ projection
@@ -151,9 +157,10 @@ def test_simt_f32_square_is_exact_product_of_its_inputs(G):
 
 # ------------------------------------------------------------------ solve
 
+@pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-10), ("bf16", 1e-10)])
 @pytest.mark.parametrize("n,k", [(300, 8), (1000, 32)])
-def test_solve_matches_exact_embedding(G, dtype, tol, n, k):
+def test_solve_matches_exact_embedding(G, dtype, tol, n, k, full):
     cdl = G.cdl
     dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}[dtype]
     X = iid_pair(n, 32, 1, seed=n + 1).X[0]
@@ -165,7 +172,8 @@ def test_solve_matches_exact_embedding(G, dtype, tol, n, k):
     vol = torch.tensor([volo], dtype=torch.float64, device="cuda")
     ch = G.chain(A, D, vol, 6, dt)
     try:
-        Z, stats = G.solve(ch, A, torch.from_numpy(Yo).cuda(), max_iter=30, rel_tol=tol)
+        Z, stats = G.solve(ch, A, torch.from_numpy(Yo).cuda(), max_iter=30, rel_tol=tol,
+                           flags=cdl.CDL_SOLVE_FULL_RESIDUAL if full else 0)
     finally:
         cdl.cdl_chain_free(ch)
     Zg = _h(Z)
