@@ -168,7 +168,9 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  * inout: if *inout is NULL a chain is allocated (cdl_chain_free releases it);
  *   if it points to a chain created with the same (n, d, chain_dtype) its
  *   storage is reused; any other chain returns CDL_ERR_INVALID_ARG.
- * Levels occupy d * npad^2 elements, npad = n rounded up to 256. */
+ * Levels occupy d * npad^2 elements, npad = n rounded up to 256; bf16
+ * chains also keep A as two bf16 matrices (A_hi + A_lo, 4 npad^2 bytes),
+ * the operand of the solve's tensor-core residual update. */
 enum { CDL_CHAIN_DEFAULT = 0 };
 int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double* D,
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,

@@ -255,6 +255,7 @@ int cdl_chain_free(cdl_chain* ch) {
   if (!ch) return CDL_OK;
   cudaSetDevice(ch->device);
   cudaFree(ch->levels);
+  cudaFree(ch->aop);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
   cudaFree(ch->vol);
@@ -296,11 +297,13 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     ch->dtype = chain_dtype;
     ch->elem = chain_dtype == CDL_F64 ? 8 : chain_dtype == CDL_F32 ? 4 : 2;
     size_t bytes = (size_t)d * npad * npad * ch->elem;
-    if (ctx->ws_cap && ctx->ws_used + bytes > ctx->ws_cap) {
+    const size_t aop_bytes = chain_dtype == CDL_BF16 ? 2 * (size_t)npad * npad * 2 : 0;
+    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes > ctx->ws_cap) {
       delete ch;
       return CDL_ERR_OOM;
     }
-    if (cudaMalloc(&ch->levels, bytes) != cudaSuccess ||
+    if ((aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
+        cudaMalloc(&ch->levels, bytes) != cudaSuccess ||
         cudaMalloc(&ch->rsqrt_d, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->D, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->vol, sizeof(double)) != cudaSuccess) {

@@ -17,8 +17,10 @@ namespace cdl {
 namespace {
 
 // rsqrt_d_i = D_i^{-1/2}, u_i = (D_i / vol)^{1/2}; zero in the padding.
+// Float copies rsf, uf feed the bf16 level-0 pass.
 __global__ void k_chain_vectors(const double* __restrict__ D, const double* __restrict__ vol,
-                                int n, int npad, double* __restrict__ rsd, double* __restrict__ u) {
+                                int n, int npad, double* __restrict__ rsd, double* __restrict__ u,
+                                float* __restrict__ rsf, float* __restrict__ uf) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npad) return;
   if (i < n) {
@@ -29,6 +31,8 @@ __global__ void k_chain_vectors(const double* __restrict__ D, const double* __re
     rsd[i] = 0.0;
     u[i] = 0.0;
   }
+  rsf[i] = (float)rsd[i];
+  uf[i] = (float)u[i];
 }
 
 template <typename T>
@@ -67,23 +71,33 @@ __global__ void __launch_bounds__(256) k_chain_init(const double* __restrict__ A
 // bf16 levels: the same formula in float32 arithmetic, A_ij (rf_i rf_j) - uf_i uf_j
 // with float copies of D^{-1/2} and u; the float32 error (a few 1e-7 relative to
 // either product) is far below the bf16 rounding of the result.
+// The same pass also writes A = A_hi + A_lo as two bf16 matrices (16
+// significant bits), the operand of the tensor-core residual update.
 __global__ void __launch_bounds__(256) k_chain_init_bf16(const double* __restrict__ A, int n, int npad,
-                                                          const double* __restrict__ rsd,
-                                                          const double* __restrict__ u,
-                                                          __nv_bfloat16* __restrict__ L0) {
+                                                          const float* __restrict__ rsf,
+                                                          const float* __restrict__ uf,
+                                                          __nv_bfloat16* __restrict__ L0,
+                                                          __nv_bfloat16* __restrict__ Ahi,
+                                                          __nv_bfloat16* __restrict__ Alo) {
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
   for (int i = blockIdx.x; i < npad; i += gridDim.x) {
-    __nv_bfloat16* out = L0 + (size_t)i * npad;
+    const size_t off = (size_t)i * npad;
     if (i >= n) {
-      for (int j = threadIdx.x; j < npad; j += blockDim.x) out[j] = __float2bfloat16_rn(0.f);
+      for (int j = threadIdx.x; j < npad; j += blockDim.x) L0[off + j] = Ahi[off + j] = Alo[off + j] = z;
       continue;
     }
-    const float ri = (float)rsd[i], ui = (float)u[i];
+    const float ri = rsf[i], ui = uf[i];
     const double* row = A + (size_t)i * n;
     for (int j = threadIdx.x; j < npad; j += blockDim.x) {
-      float v = 0.f;
-      if (j < n)
-        v = __fmaf_rn(__double2float_rn(row[j]), __fmul_rn(ri, (float)rsd[j]), -__fmul_rn(ui, (float)u[j]));
-      out[j] = __float2bfloat16_rn(v);
+      float v = 0.f, a = 0.f;
+      if (j < n) {
+        a = __double2float_rn(row[j]);
+        v = __fmaf_rn(a, __fmul_rn(ri, rsf[j]), -__fmul_rn(ui, uf[j]));
+      }
+      L0[off + j] = __float2bfloat16_rn(v);
+      const __nv_bfloat16 h = __float2bfloat16_rn(a);
+      Ahi[off + j] = h;
+      Alo[off + j] = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(h)));
     }
   }
 }
@@ -237,14 +251,16 @@ int square_impl(cdl_ctx* ctx, cdl_chain* ch, int level) {
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
   const int n = (int)ch->n, np = (int)ch->npad;
   void* wsu;
-  CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * sizeof(double), &wsu));
+  CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * (sizeof(double) + 2 * sizeof(float)), &wsu));
   double* u = static_cast<double*>(wsu);
+  float* rsf = reinterpret_cast<float*>(u + np);
+  float* uf = rsf + np;
   {
     Launch L(ctx, CDL_KC_MISC, 0);
-    k_chain_vectors<<<(np + 255) / 256, 256, 0, ctx->stream>>>(ch->D, ch->vol, n, np, ch->rsqrt_d, u);
+    k_chain_vectors<<<(np + 255) / 256, 256, 0, ctx->stream>>>(ch->D, ch->vol, n, np, ch->rsqrt_d, u, rsf, uf);
     CDL_TRY(L.done());
   }
-  const double bytes = 8.0 * n * (double)n + (double)ch->elem * np * (double)np;
+  const double bytes = 8.0 * n * (double)n + (double)ch->elem * np * (double)np * (ch->dtype == CDL_BF16 ? 3 : 1);
   const int blocks = std::min(np, ctx->sm_count * 8);
   Launch L(ctx, CDL_KC_CHAIN_INIT, bytes);
   switch (ch->dtype) {
@@ -257,8 +273,9 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
                                                            static_cast<float*>(ch->level(0)));
       break;
     case CDL_BF16:
-      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(A, n, np, ch->rsqrt_d, u,
-                                                          static_cast<__nv_bfloat16*>(ch->level(0)));
+      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
+          A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(ch->level(0)), static_cast<__nv_bfloat16*>(ch->aop),
+          static_cast<__nv_bfloat16*>(ch->aop) + (size_t)np * np);
       break;
     default:
       return CDL_ERR_UNSUPPORTED;

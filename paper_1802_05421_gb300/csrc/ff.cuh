@@ -48,6 +48,31 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// Conversions between float and double done with integer operations (the
+// float64 pipe also executes the hardware conversions, and it is the scarce
+// one on this GPU). f2d_bits is exact for normal floats and zero (subnormal
+// floats map to zero); d2f_trunc truncates a double to 24 significant bits
+// (exact for the top 24 bits; doubles below the float normal range map to
+// zero, beyond it the result is meaningless, callers keep |x| < 2^127).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long ed = (unsigned long long)(e - 127 + 1023) << 52;
+  const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | ed | m));
+}
+
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return 0.f;
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint32_t m = (uint32_t)(b >> 29) & 0x7FFFFFu;
+  return __uint_as_float(sign | ((uint32_t)e << 23) | m);
+}
+
 // exp(-t) for float64 t >= 0, as the float-float pair q and the integer k with
 // exp(-t) = (q.hi + q.lo) 2^-k, to about 2^-46 relative. Written from the series
 // definition: t = k ln2 + r with k = round(t / ln2) and |r| <= ln2/2, so
@@ -58,12 +83,15 @@ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (do
 // below 2^-22 of the result), degrees 0..6 in float-float Horner steps; the
 // coefficients 1/m! are stored as float pairs. Valid for t < 700.
 __device__ __forceinline__ ff ff_exp_neg_scaled(double t, int& k_out) {
-  const float k = rintf(__fmul_rn(__double2float_rn(t), 0x1.715476p+0f));   // t / ln2
-  const double kd = (double)k;
+  const float k = rintf(__fmul_rn(d2f_trunc(t), 0x1.715476p+0f));   // t / ln2
+  const double kd = f2d_bits(k);
   double r = fma(-kd, 0x1.62e42fefa2000p-1, t);
   r = fma(-kd, 0x1.9ef35793c7673p-41, r);
-  const ff rf = ff_from_double(r);
-  const ff x = {-rf.hi, -rf.lo};
+  // float-float split of r with integer conversions: rh exact top bits, rl the
+  // remainder truncated to 24 bits (error below 2^-48 |r|)
+  const float rh = d2f_trunc(r);
+  const float rl = d2f_trunc(r - f2d_bits(rh));
+  const ff x = {-rh, -rl};
   float p = 0x1.1eed8ep-29f;                      // 1/12!
   p = __fmaf_rn(p, x.hi, 0x1.ae6456p-26f);        // 1/11!
   p = __fmaf_rn(p, x.hi, 0x1.27e4fcp-22f);        // 1/10!
@@ -87,7 +115,7 @@ __device__ __forceinline__ double ff_exp_neg(double t) {
   if (!(t < 700.0)) return exp(-t);
   int k;
   const ff q = ff_exp_neg_scaled(t, k);
-  const double v = ff_to_double(q);
+  const double v = f2d_bits(q.hi) + f2d_bits(q.lo);
   // times 2^-k through the exponent field (v and the result are normal numbers)
   return __longlong_as_double(__double_as_longlong(v) - ((long long)k << 52));
 }

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int
         if (t < 700.0) {
           int k;
           const ff q = ff_exp_neg_scaled(t, k);
-          a = __longlong_as_double(__double_as_longlong(ff_to_double(q)) - ((long long)k << 52));
+          a = __longlong_as_double(__double_as_longlong(f2d_bits(q.hi) + f2d_bits(q.lo)) - ((long long)k << 52));
           if (k <= 100) {
             const float sc = __int_as_float((127 - k) << 23);   // 2^-k
             const ff ts = two_sum(acc.hi, __fmul_rn(q.hi, sc));

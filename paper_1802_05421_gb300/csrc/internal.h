@@ -72,6 +72,7 @@ struct cdl_chain {
   cdl_dtype dtype = CDL_F64;
   size_t elem = 8;
   void* levels = nullptr;     // d * npad * npad elements
+  void* aop = nullptr;        // bf16 chains: A = A_hi + A_lo as two bf16 npad x npad matrices
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
@@ -113,6 +114,8 @@ int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial,
              int k, int splits);
+int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp,
+                 int splits);
 bool tc_supported(cdl_ctx* ctx);
 // solve.cu
 int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,

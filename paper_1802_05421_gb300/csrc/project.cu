@@ -7,7 +7,7 @@
 // (i, j, r / 128, 0) with key (seed low word, seed high word): bit (r mod 32)
 // of output word ((r mod 128) / 32) set means +1.
 //
-// Each thread owns one node row i and 32 projection rows (one Philox word).
+// Each thread owns one node row i and 16 projection rows (half a Philox word).
 // Per tile of 32 edges the block forms sqrt(A_ij) in float-float once per
 // (row, edge) and one Philox call per (row, edge, 128 projection rows), shared
 // through shared memory by the threads of the row.
@@ -52,28 +52,32 @@ constexpr int MAX_RPB = 64;  // node rows per block
 // partial sums are flushed to float64 in Y every 4096 edges. Per term and
 // projection row this is one sign construction and three fused multiply-adds
 // with +-1 (exact products).
-__global__ void __launch_bounds__(256) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
-                                                  uint32_t key0, uint32_t key1, double scale,
-                                                  double* __restrict__ Y) {
+constexpr int RB = 16;       // projection rows per thread (half a Philox word)
+
+__global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
+                                                     uint32_t key0, uint32_t key1, double scale,
+                                                     double* __restrict__ Y) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* P1 = reinterpret_cast<float*>(smraw);          // [rpb][JT]
   float* P2 = P1 + rpb * JT;                            // [rpb][JT]
   float* P3 = P2 + rpb * JT;                            // [rpb][JT]
   uint4* Wd = reinterpret_cast<uint4*>(P3 + rpb * JT);  // [rpb][JT][nrb]
   const int nrb = (W + 3) / 4;
+  const int H = 2 * W;                 // threads per node row
   const int t = threadIdx.x;
-  const int rl = t / W, w = t % W;
+  const int rl = t / H, h = t % H;
+  const int w = h >> 1, shift = (h & 1) * RB;
   const int i0 = blockIdx.x * rpb;
   const int i = i0 + rl;
   const bool active = rl < rpb && i < n;
-  float a1[32], a2[32], a3[32];
+  float a1[RB], a2[RB], a3[RB];
 #pragma unroll
-  for (int b = 0; b < 32; ++b) a1[b] = a2[b] = a3[b] = 0.f;
+  for (int b = 0; b < RB; ++b) a1[b] = a2[b] = a3[b] = 0.f;
   auto flush = [&]() {
     if (!active) return;
 #pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const int r = w * 32 + b;
+    for (int b = 0; b < RB; ++b) {
+      const int r = w * 32 + shift + b;
       if (r < k) Y[(size_t)i * k + r] += ((double)a1[b] + (double)a2[b]) + (double)a3[b];
       a1[b] = a2[b] = a3[b] = 0.f;
     }
@@ -129,9 +133,9 @@ __global__ void __launch_bounds__(256) k_project(const double* __restrict__ A, i
       const float p1 = P1[e], p2 = P2[e], p3 = P3[e];
       const uint4 o = Wd[e * nrb + rb];
       const uint32_t bits = wi == 0 ? o.x : wi == 1 ? o.y : wi == 2 ? o.z : o.w;
-      const uint32_t nb = ~bits;   // clear bit -> -1
+      const uint32_t nb = ~(bits >> shift);   // clear bit -> -1
 #pragma unroll
-      for (int b = 0; b < 32; ++b) {
+      for (int b = 0; b < RB; ++b) {
         const float sg = __uint_as_float(((nb << (31 - b)) & 0x80000000u) | 0x3f800000u);
         a1[b] = __fmaf_rn(sg, p1, a1[b]);
         a2[b] = __fmaf_rn(sg, p2, a2[b]);
@@ -142,8 +146,8 @@ __global__ void __launch_bounds__(256) k_project(const double* __restrict__ A, i
   flush();
   if (!active) return;
 #pragma unroll
-  for (int b = 0; b < 32; ++b) {
-    const int r = w * 32 + b;
+  for (int b = 0; b < RB; ++b) {
+    const int r = w * 32 + shift + b;
     if (r < k) Y[(size_t)i * k + r] *= scale;
   }
 }
@@ -153,8 +157,8 @@ __global__ void __launch_bounds__(256) k_project(const double* __restrict__ A, i
 int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, double* Y) {
   const int n = (int)n64;
   const int W = (k + 31) / 32;
-  const int rpb = std::max(1, std::min(MAX_RPB, 256 / W));
-  const int threads = rpb * W;
+  const int rpb = std::max(1, std::min(MAX_RPB, 256 / (2 * W)));
+  const int threads = rpb * 2 * W;
   const int nrb = (W + 3) / 4;
   const size_t smem = 3 * (size_t)rpb * JT * sizeof(float) + (size_t)rpb * JT * nrb * sizeof(uint4);
   const int blocks = (n + rpb - 1) / rpb;

@@ -67,17 +67,21 @@ __global__ void k_precond_in(const double* __restrict__ R, const double* __restr
   x[idx] = (T)v;
 }
 
-// Z += dZ with dZ = D^{-1/2} x; dZ is also kept in float32 for the recursive
-// residual update.
+// Z += dZ with dZ = D^{-1/2} x; dZ is also kept in float32 (npad x kp, zero
+// padded) for the recursive residual update.
 template <typename T>
 __global__ void k_precond_out(const T* __restrict__ x, const double* __restrict__ rsd, int n, int k,
-                              int kp, double* __restrict__ Z, float* __restrict__ dZ) {
+                              int np, int kp, double* __restrict__ Z, float* __restrict__ dZ) {
   size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (idx >= (size_t)n * k) return;
-  int i = (int)(idx / k), r = (int)(idx % k);
-  const double dz = (double)x[(size_t)i * kp + r] * rsd[i];
-  Z[idx] += dz;
-  dZ[idx] = (float)dz;
+  if (idx >= (size_t)np * kp) return;
+  int i = (int)(idx / kp), r = (int)(idx % kp);
+  float dzf = 0.f;
+  if (i < n && r < k) {
+    const double dz = (double)x[idx] * rsd[i];
+    Z[(size_t)i * k + r] += dz;
+    dzf = (float)dz;
+  }
+  dZ[idx] = dzf;
 }
 
 // x[i][r] += sum_s part[s][i][r] (CUDA-core chains)
@@ -265,51 +269,51 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, 
   }
 }
 
-// Recursive residual update R -= D o dZ - A dZ for a 64-row x 128-column tile,
-// A dZ accumulated in float32; per-block sum of the new R^2. The update is
-// small (|dZ| shrinks with the residual), so its float32 error, about 1e-7 of
-// ||L dZ||, stays far below the float-float residual it corrects.
+// Recursive residual update R -= D o dZ - A dZ for a 128-row x 128-column
+// tile (8 x 8 outputs per thread), A dZ accumulated in float32; per-block sum of
+// the new R^2. The update is small (|dZ| shrinks with the residual), so its
+// float32 error, about 1e-7 of ||L dZ||, stays far below the float-float
+// residual it corrects.
+constexpr int RU_M = 128, RU_N = 128, RU_K = 16;
 __global__ void __launch_bounds__(256) k_residual_update(const double* __restrict__ A, const float* __restrict__ dZ,
-                                                          const double* __restrict__ D, int n, int k,
+                                                          const double* __restrict__ D, int n, int k, int kp,
                                                           double* __restrict__ R, double* __restrict__ part) {
-  __shared__ float As[RB_K][RB_M + 1];
-  __shared__ __align__(16) float Bs[RB_K][RB_N];
+  __shared__ __align__(16) float As[RU_K][RU_M + 4];
+  __shared__ __align__(16) float Bs[RU_K][RU_N];
   __shared__ double red[8];
-  const int i0 = blockIdx.x * RB_M, c0 = blockIdx.y * RB_N;
+  const int i0 = blockIdx.x * RU_M, c0 = blockIdx.y * RU_N;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][8];
+  float acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-  const int rows[4] = {ty * 2, ty * 2 + 1, 32 + ty * 2, 32 + ty * 2 + 1};
-  for (int j0 = 0; j0 < n; j0 += RB_K) {
+  for (int j0 = 0; j0 < n; j0 += RU_K) {
 #pragma unroll
-    for (int e = 0; e < (RB_M * RB_K) / 256; ++e) {
+    for (int e = 0; e < (RU_M * RU_K) / 256; ++e) {
       const int idx = tid + e * 256;
-      const int ii = idx / RB_K, jj = idx % RB_K;
+      const int ii = idx / RU_K, jj = idx % RU_K;
       const int i = i0 + ii, j = j0 + jj;
-      As[jj][ii] = (i < n && j < n) ? (float)A[(size_t)i * n + j] : 0.f;
+      As[jj][ii] = (i < n && j < n) ? __double2float_rn(A[(size_t)i * n + j]) : 0.f;
     }
 #pragma unroll
-    for (int e = 0; e < (RB_N * RB_K) / 256; ++e) {
+    for (int e = 0; e < (RU_N * RU_K) / 256; ++e) {
       const int idx = tid + e * 256;
-      const int jj = idx / RB_N, cc = idx % RB_N;
+      const int jj = idx / RU_N, cc = idx % RU_N;
       const int j = j0 + jj, c = c0 + cc;
-      Bs[jj][cc] = (j < n && c < k) ? dZ[(size_t)j * k + c] : 0.f;
+      Bs[jj][cc] = (j < n && c < k) ? dZ[(size_t)j * kp + c] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
-    for (int jj = 0; jj < RB_K; ++jj) {
-      float av[4], bv[8];
+    for (int jj = 0; jj < RU_K; ++jj) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[jj][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[jj][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[jj][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[jj][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[jj][rows[a]];
-      const float4 h0 = *reinterpret_cast<const float4*>(&Bs[jj][tx * 4]);
-      const float4 h1 = *reinterpret_cast<const float4*>(&Bs[jj][64 + tx * 4]);
-      bv[0] = h0.x; bv[1] = h0.y; bv[2] = h0.z; bv[3] = h0.w;
-      bv[4] = h1.x; bv[5] = h1.y; bv[6] = h1.z; bv[7] = h1.w;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
     }
@@ -317,8 +321,8 @@ __global__ void __launch_bounds__(256) k_residual_update(const double* __restric
   }
   double sq = 0.0;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = i0 + rows[a];
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + a - 4);
     if (i >= n) continue;
     const double di = D[i];
 #pragma unroll
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(256) k_residual_update(const double* __restric
       const int c = c0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
       if (c >= k) continue;
       const size_t o = (size_t)i * k + c;
-      const double r = R[o] - (di * (double)dZ[o] - (double)acc[a][b]);
+      const double r = R[o] - (di * (double)dZ[(size_t)i * kp + c] - (double)acc[a][b]);
       R[o] = r;
       sq = fma(r, r, sq);
     }
@@ -339,6 +343,40 @@ __global__ void __launch_bounds__(256) k_residual_update(const double* __restric
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w];
     part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Tensor-core residual update, second half: the products A_hi [dZ_hi|dZ_lo]
+// and A_lo [dZ_hi|dZ_lo] arrive as float32 split-K partials (bf16 operands:
+// about 16 significant bits of A and of dZ); R -= D o dZ - (sum of the four
+// products); per-block sums of the new R^2.
+__global__ void __launch_bounds__(256) k_residual_update_tc(const float* __restrict__ pa, const float* __restrict__ pb,
+                                                             int splits, int np, const float* __restrict__ dZ,
+                                                             const double* __restrict__ D, int n, int k, int kp,
+                                                             double* __restrict__ R, double* __restrict__ part) {
+  __shared__ double red[8];
+  double sq = 0.0;
+  const size_t total = (size_t)n * k;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / k), c = (int)(idx % k);
+    double az = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      const size_t o = ((size_t)s * np + i) * (2 * kp);
+      az += (double)pa[o + c] + (double)pa[o + kp + c] + (double)pb[o + c] + (double)pb[o + kp + c];
+    }
+    const double r = R[idx] - (D[i] * (double)dZ[(size_t)i * kp + c] - az);
+    R[idx] = r;
+    sq = fma(r, r, sq);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
   }
 }
 
@@ -374,7 +412,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   const size_t part_cols = bf16 ? 2 * (size_t)kp : (size_t)kp;
   void *vR, *vx, *vxop = nullptr, *vpart, *vred, *vscal, *vzh, *vzl, *vcs;
   const int res_gx = (n + RB_M - 1) / RB_M, res_gy = (k + RB_N - 1) / RB_N;
-  const int nred = std::max(res_gx * res_gy, 1024);
+  const int nred = std::max(res_gx * res_gy, std::max(1024, ctx->sm_count * 4));
   const int cs_rows = 256, cs_parts = (n + cs_rows - 1) / cs_rows;
   CDL_TRY(ws_get(ctx, "solve.R", (size_t)n * k * 8, &vR));
   CDL_TRY(ws_get(ctx, "solve.x", (size_t)np * kp * xe, &vx));
@@ -385,8 +423,12 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   CDL_TRY(ws_get(ctx, "solve.zh", (size_t)n * k * 4, &vzh));
   CDL_TRY(ws_get(ctx, "solve.zl", (size_t)n * k * 4, &vzl));
   CDL_TRY(ws_get(ctx, "solve.colsum", (size_t)cs_parts * k * 8, &vcs));
-  void* vdz;
-  CDL_TRY(ws_get(ctx, "solve.dz", (size_t)n * k * 4, &vdz));
+  void *vdz, *vpart2 = nullptr, *vdzop = nullptr;
+  CDL_TRY(ws_get(ctx, "solve.dz", (size_t)np * kp * 4, &vdz));
+  if (bf16) {
+    CDL_TRY(ws_get(ctx, "solve.part2", (size_t)splits * np * part_cols * xe, &vpart2));
+    CDL_TRY(ws_get(ctx, "solve.dzop", 2 * (size_t)kp * np * 2, &vdzop));
+  }
   double* R = static_cast<double*>(vR);
   double* red = static_cast<double*>(vred);
   double* scal = static_cast<double*>(vscal);
@@ -419,7 +461,9 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
     for (double& h : stats->history) h = 0.0;
   }
   if (yy == 0.0) return CDL_OK;
-  // Full float-float residual R = Y - L Z; returns ||R|| / ||Y||.
+  const int upd_gx = (n + RU_M - 1) / RU_M, upd_gy = (k + RU_N - 1) / RU_N;
+  int nparts = res_gx * res_gy;   // per-block partial sums of R^2 written by the last residual kernel
+  // Full float-float residual R = Y - L Z.
   auto full_residual = [&](double* rel_out) -> int {
     {
       Launch L(ctx, CDL_KC_MISC, 0);
@@ -433,20 +477,41 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
                                      ch->D, n, k, R, red);
       CDL_TRY(L.done());
     }
+    nparts = res_gx * res_gy;
     return CDL_OK;
   };
   // Recursive update R -= L dZ in float32.
   auto update_residual = [&]() -> int {
-    dim3 g(res_gx, res_gy);
+    if (bf16 && ch->aop) {
+      // dZ -> bf16 hi/lo operand, then A_hi and A_lo times it on the tensor cores
+      {
+        dim3 g((np + 31) / 32, (kp + 31) / 32);
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_update_bf16<<<g, 256, 0, st>>>(static_cast<float*>(vdz), nullptr, 0, np, kp,
+                                         static_cast<__nv_bfloat16*>(vdzop), 0);
+        CDL_TRY(L.done());
+      }
+      const __nv_bfloat16* ahi = static_cast<const __nv_bfloat16*>(ch->aop);
+      CDL_TRY(apply_tc_mat(ctx, ahi, np, vdzop, static_cast<float*>(vpart), kp, splits));
+      CDL_TRY(apply_tc_mat(ctx, ahi + (size_t)np * np, np, vdzop, static_cast<float*>(vpart2), kp, splits));
+      const int nb = (int)std::min<size_t>((nk + 255) / 256, (size_t)ctx->sm_count * 4);
+      Launch L(ctx, CDL_KC_RESIDUAL, 0);
+      k_residual_update_tc<<<nb, 256, 0, st>>>(static_cast<const float*>(vpart), static_cast<const float*>(vpart2),
+                                               splits, np, static_cast<const float*>(vdz), ch->D, n, k, kp, R, red);
+      nparts = nb;
+      return L.done();
+    }
+    dim3 g(upd_gx, upd_gy);
     Launch L(ctx, CDL_KC_RESIDUAL, (double)n * n * k);
-    k_residual_update<<<g, 256, 0, st>>>(A, static_cast<const float*>(vdz), ch->D, n, k, R, red);
+    k_residual_update<<<g, 256, 0, st>>>(A, static_cast<const float*>(vdz), ch->D, n, k, kp, R, red);
+    nparts = upd_gx * upd_gy;
     return L.done();
   };
   auto read_norm = [&](double* rel_out) -> int {
     double rr = 0.0;
     {
       Launch L(ctx, CDL_KC_MISC, 0);
-      k_reduce<<<1, 1024, 0, st>>>(red, res_gx * res_gy, scal + 1);
+      k_reduce<<<1, 1024, 0, st>>>(red, nparts, scal + 1);
       CDL_TRY(L.done());
     }
     CDL_CUDA_TRY(cudaMemcpyAsync(&rr, scal + 1, 8, cudaMemcpyDeviceToHost, st));
@@ -519,11 +584,11 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
     {
       Launch L(ctx, CDL_KC_MISC, 0);
       if (ch->dtype == CDL_F64)
-        k_precond_out<double><<<blocks_for(nk, 256), 256, 0, st>>>(static_cast<const double*>(vx), ch->rsqrt_d,
-                                                                    n, k, kp, Z, static_cast<float*>(vdz));
+        k_precond_out<double><<<blocks_for((size_t)np * kp, 256), 256, 0, st>>>(
+            static_cast<const double*>(vx), ch->rsqrt_d, n, k, np, kp, Z, static_cast<float*>(vdz));
       else
-        k_precond_out<float><<<blocks_for(nk, 256), 256, 0, st>>>(static_cast<const float*>(vx), ch->rsqrt_d,
-                                                                   n, k, kp, Z, static_cast<float*>(vdz));
+        k_precond_out<float><<<blocks_for((size_t)np * kp, 256), 256, 0, st>>>(
+            static_cast<const float*>(vx), ch->rsqrt_d, n, k, np, kp, Z, static_cast<float*>(vdz));
       CDL_TRY(L.done());
     }
     {
@@ -544,7 +609,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       drift = 0.0;
     } else {
       CDL_TRY(update_residual());
-      drift += 1e-6 * rel;   // float32 error of L dZ, with |L dZ| about |R| before the step
+      drift += 1e-5 * rel;   // error of the L dZ product (16-bit operands or float32), |L dZ| ~ |R| before
       exact_r = false;
     }
     CDL_TRY(read_norm(&rel));

@@ -5,9 +5,11 @@
 //    256 x 256 blocks (I, J) with I <= J are computed (two 128 x 256 MMA
 //    tiles each); every block is also written transposed, so the stored
 //    level is exactly symmetric. Output bf16 (float32 accumulation).
-//  * apply: partial[s] = S~_i [x_hi | x_lo] over the k-range of split s,
-//    where x_hi + x_lo is a float32 block of right-hand sides split into two
-//    bfloat16 halves (about 16 significant bits). Output float32 partials.
+//  * apply: partial[s] = M [x_hi | x_lo] over the k-range of split s for a
+//    bf16 matrix M (a chain level, or a bf16 half of the graph for the
+//    residual update), where x_hi + x_lo is a float32 block of right-hand
+//    sides split into two bfloat16 halves (about 16 significant bits). Output
+//    float32 partials.
 //
 // Structure: persistent CTAs (one per SM), warp-specialised. Warp 0 issues TMA
 // loads of 128-byte-swizzled K-major tiles into a 4-stage shared-memory ring;
@@ -496,7 +498,10 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
 
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial, int kp,
              int splits) {
-  const int np = (int)ch->npad;
+  return apply_tc_mat(ctx, ch->level(level), (int)ch->npad, xop, partial, kp, splits);
+}
+
+int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp, int splits) {
   const int bn = 2 * kp;
   if (bn % 32 || bn < 32 || bn > MAX_BN) return CDL_ERR_UNSUPPORTED;
   const int mb = np / BM;
@@ -506,7 +511,7 @@ int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, floa
   CDL_TRY(get_tiles(ctx, "tc.apply." + std::to_string(mb) + "." + std::to_string(splits),
                     [&] { return apply_tiles(mb, splits); }, &tiles, &count));
   CUtensorMap ma, mbm;
-  CDL_TRY(make_map(&ma, ch->level(level), np, np, 128));
+  CDL_TRY(make_map(&ma, amat, np, np, 128));
   CDL_TRY(make_map(&mbm, xop, bn, np, bn));
   TcParams p;
   p.tiles = tiles;
