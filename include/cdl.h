@@ -54,7 +54,7 @@ typedef enum {
   CDL_F64 = 0,      /* IEEE binary64                                    */
   CDL_F32 = 1,      /* IEEE binary32                                    */
   CDL_BF16 = 2,     /* bfloat16, tensor-core chain (tcgen05)            */
-  CDL_FP8E4M3 = 3   /* float8 e4m3 (reserved; returns UNSUPPORTED)      */
+  CDL_FP8E4M3 = 3   /* float8 e4m3 with one scale per level (tcgen05)   */
 } cdl_dtype;
 
 typedef struct cdl_ctx cdl_ctx;
@@ -162,8 +162,13 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  * and act like S^{2^i} on every vector D^{-1/2} b with b orthogonal to the
  * ones vector, the only vectors the solve applies them to.
  * A (device, n x n, a_dtype = CDL_F64), D (device, n), vol (device, 1).
- * chain_dtype: CDL_F64, CDL_F32 (CUDA-core GEMM) or CDL_BF16 (tcgen05
- *   tensor-core GEMM, float32 accumulation, bfloat16 levels).
+ * chain_dtype: CDL_F64, CDL_F32 (CUDA-core GEMM), CDL_BF16 (tcgen05
+ *   tensor-core GEMM, float32 accumulation, bfloat16 levels) or CDL_FP8E4M3
+ *   (tcgen05 kind::f8f6f4 GEMM, float32 accumulation, e4m3 levels with one
+ *   scale per level: level i stores value / s_i, s_i = m_i / 448 where m_0 =
+ *   max |S~_0| and m_{i+1} = max_r |row r of S~_i|^2 bounds every entry of
+ *   S~_i^2 (|(S S)_ab| <= |row a| |row b|; attained on the diagonal); a bf16
+ *   copy of each level is kept for the solve's apply).
  * flags: CDL_CHAIN_* below.
  * inout: if *inout is NULL a chain is allocated (cdl_chain_free releases it);
  *   if it points to a chain created with the same (n, d, chain_dtype) its
@@ -178,6 +183,13 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
 int cdl_chain_free(cdl_chain* chain);
 /* Device pointer to level i (npad x npad, chain dtype, zero padded) and npad. */
 int cdl_chain_level(const cdl_chain* chain, int32_t i, void** level, int64_t* npad);
+/* Device pointer to the bf16 view of level i that the solve's tensor-core
+ * apply reads (npad x npad): the level itself for CDL_BF16 chains, its bf16
+ * copy for CDL_FP8E4M3 chains; NULL (and CDL_ERR_INVALID_ARG) otherwise. */
+int cdl_chain_apply_level(const cdl_chain* chain, int32_t i, void** level);
+/* Scale of level i: stored value times *scale is the level's value (1 for
+ * every dtype but CDL_FP8E4M3). Synchronises the chain's device. */
+int cdl_chain_level_scale(const cdl_chain* chain, int32_t i, double* scale);
 
 /* ---------------------------------------------------------------- projection */
 
@@ -230,7 +242,10 @@ typedef struct {
  * chain: from cdl_chain_build on the same graph. A: device n x n (CDL_F64).
  * Y: device n x k float64. Z: device n x k float64 output.
  * stats: host, may be NULL. Returns CDL_ERR_NOT_CONVERGED (Z still written)
- * when rel_tol > 0 was not reached within max_iter applications. */
+ * when rel_tol > 0 was not reached within max_iter applications, and stops
+ * early with it when the residual is not finite or exceeds 1e6 ||Y|| (a
+ * preconditioner that does not contract, e.g. an e4m3 chain whose single
+ * per-level scale cannot hold the graph's dynamic range). */
 int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* chain, const void* A, cdl_dtype a_dtype,
                     const double* Y, int32_t k, const cdl_solve_opts* opts, double* Z,
                     cdl_solve_stats* stats);
@@ -277,7 +292,9 @@ typedef struct {
  * X1, X2: n x T float64 (host or device per host_io). F: n float64,
  * top_idx: topk int64 (host or device per host_io). stats1/stats2: host
  * solve statistics, may be NULL. Device buffers (graphs, chain, embeddings)
- * are owned by the context and reused across calls with the same sizes. */
+ * are owned by the context and reused across calls with the same sizes.
+ * Returns CDL_ERR_NOT_CONVERGED (scores still written) when either solve
+ * missed its tolerance. */
 int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T,
                       const cdl_pair_opts* opts, double* F, int64_t* top_idx,
                       cdl_solve_stats* stats1, cdl_solve_stats* stats2);

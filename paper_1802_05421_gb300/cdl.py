@@ -68,6 +68,8 @@ _SIGS = {
     "cdl_chain_build": [_P, _P, ctypes.c_int, _P, _P, _I64, _I32, ctypes.c_int, _I32, ctypes.POINTER(_P)],
     "cdl_chain_free": [_P],
     "cdl_chain_level": [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
+    "cdl_chain_level_scale": [_P, _I32, ctypes.POINTER(_D)],
+    "cdl_chain_apply_level": [_P, _I32, ctypes.POINTER(_P)],
     "cdl_project": [_P, _P, ctypes.c_int, _I64, _I32, ctypes.c_uint64, _P],
     "cdl_chain_solve": [_P, _P, _P, ctypes.c_int, _P, _I32, ctypes.POINTER(cdl_solve_opts), _P,
                         ctypes.POINTER(cdl_solve_stats)],
@@ -170,6 +172,20 @@ def cdl_chain_level(chain, i):
     p, npad = _P(), _I64()
     st = _lib.cdl_chain_level(chain, i, ctypes.byref(p), ctypes.byref(npad))
     return st, p.value, npad.value
+
+
+def cdl_chain_apply_level(chain, i):
+    """Returns (status, device pointer of the bf16 apply view of level i)."""
+    p = _P()
+    st = _lib.cdl_chain_apply_level(chain, i, ctypes.byref(p))
+    return st, p.value
+
+
+def cdl_chain_level_scale(chain, i):
+    """Returns (status, scale of level i)."""
+    sc = _D()
+    st = _lib.cdl_chain_level_scale(chain, i, ctypes.byref(sc))
+    return st, sc.value
 
 
 def cdl_project(ctx, A, a_dtype, n, k, seed, Y) -> int:

@@ -256,6 +256,8 @@ int cdl_chain_free(cdl_chain* ch) {
   cudaSetDevice(ch->device);
   cudaFree(ch->levels);
   cudaFree(ch->aop);
+  cudaFree(ch->levels16);
+  cudaFree(ch->amax);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
   cudaFree(ch->vol);
@@ -270,19 +272,44 @@ int cdl_chain_level(const cdl_chain* ch, int32_t i, void** level, int64_t* npad)
   return CDL_OK;
 }
 
+int cdl_chain_apply_level(const cdl_chain* ch, int32_t i, void** level) {
+  if (!level) return CDL_ERR_INVALID_ARG;
+  *level = nullptr;
+  if (!ch || i < 0 || i >= ch->d) return CDL_ERR_INVALID_ARG;
+  if (ch->dtype != CDL_BF16 && ch->dtype != CDL_FP8E4M3) return CDL_ERR_INVALID_ARG;
+  *level = ch->level16(i);
+  return CDL_OK;
+}
+
+int cdl_chain_level_scale(const cdl_chain* ch, int32_t i, double* scale) {
+  if (!ch || !scale || i < 0 || i >= ch->d) return CDL_ERR_INVALID_ARG;
+  *scale = 1.0;
+  if (ch->dtype != CDL_FP8E4M3) return CDL_OK;
+  CDL_CUDA_TRY(cudaSetDevice(ch->device));
+  CDL_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned bits = 0;
+  CDL_CUDA_TRY(cudaMemcpy(&bits, ch->amax + i, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  float a;
+  std::memcpy(&a, &bits, sizeof(float));
+  *scale = a > 0.f ? (double)(a * (1.0f / 448.0f)) : 1.0;
+  return CDL_OK;
+}
+
 int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double* D,
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
                     int32_t flags, cdl_chain** inout) {
   if (!ctx || !inout) return CDL_ERR_INVALID_ARG;
   if (n < 2 || n > (1 << 20) || d < 1 || d > 64 || flags != 0) return CDL_ERR_INVALID_ARG;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
-  if (chain_dtype != CDL_F64 && chain_dtype != CDL_F32 && chain_dtype != CDL_BF16)
-    return chain_dtype == CDL_FP8E4M3 ? CDL_ERR_UNSUPPORTED : CDL_ERR_INVALID_ARG;
+  if (chain_dtype != CDL_F64 && chain_dtype != CDL_F32 && chain_dtype != CDL_BF16 &&
+      chain_dtype != CDL_FP8E4M3)
+    return CDL_ERR_INVALID_ARG;
   CDL_TRY(set_device(ctx));
   CDL_TRY(dev_ptr(ctx, A));
   CDL_TRY(dev_ptr(ctx, D));
   CDL_TRY(dev_ptr(ctx, vol));
-  if (chain_dtype == CDL_BF16 && !tc_supported(ctx)) return CDL_ERR_UNSUPPORTED;
+  const bool tensor = chain_dtype == CDL_BF16 || chain_dtype == CDL_FP8E4M3;
+  if (tensor && !tc_supported(ctx)) return CDL_ERR_UNSUPPORTED;
   const int64_t npad = round_up(n, 256);
   cdl_chain* ch = *inout;
   if (ch) {
@@ -295,14 +322,17 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     ch->npad = npad;
     ch->d = d;
     ch->dtype = chain_dtype;
-    ch->elem = chain_dtype == CDL_F64 ? 8 : chain_dtype == CDL_F32 ? 4 : 2;
+    ch->elem = chain_dtype == CDL_F64 ? 8 : chain_dtype == CDL_F32 ? 4 : chain_dtype == CDL_BF16 ? 2 : 1;
     size_t bytes = (size_t)d * npad * npad * ch->elem;
-    const size_t aop_bytes = chain_dtype == CDL_BF16 ? 2 * (size_t)npad * npad * 2 : 0;
-    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes > ctx->ws_cap) {
+    const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
+    const size_t l16_bytes = chain_dtype == CDL_FP8E4M3 ? (size_t)d * npad * npad * 2 : 0;
+    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes + l16_bytes > ctx->ws_cap) {
       delete ch;
       return CDL_ERR_OOM;
     }
     if ((aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
+        (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
+                       cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||
         cudaMalloc(&ch->levels, bytes) != cudaSuccess ||
         cudaMalloc(&ch->rsqrt_d, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->D, npad * sizeof(double)) != cudaSuccess ||
@@ -317,8 +347,10 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     CDL_CUDA_TRY(cudaMemsetAsync(ch->D + n, 0, (npad - n) * sizeof(double), ctx->stream));
   CDL_CUDA_TRY(cudaMemcpyAsync(ch->vol, vol, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   int st = chain_init(ctx, ch, static_cast<const double*>(A));
-  for (int i = 0; st == CDL_OK && i + 1 < d; ++i)
-    st = chain_dtype == CDL_BF16 ? chain_square_tc(ctx, ch, i) : chain_square_simt(ctx, ch, i);
+  for (int i = 0; st == CDL_OK && i + 1 < d; ++i) {
+    if (chain_dtype == CDL_FP8E4M3) st = fp8_level_bound(ctx, ch, i);
+    if (st == CDL_OK) st = tensor ? chain_square_tc(ctx, ch, i) : chain_square_simt(ctx, ch, i);
+  }
   if (st != CDL_OK) {
     if (!*inout) cdl_chain_free(ch);
     return st;
@@ -421,6 +453,7 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
     cdl_chain_free(ctx->pair_chain);
     ctx->pair_chain = nullptr;
   }
+  bool converged = true;
   for (int g = 0; g < 2; ++g) {
     CDL_TRY(graph_build(ctx, Xs[g], n, T, o->sigma, As[g], Ds[g], sc + g, sc + 2 + g));
     CDL_TRY(cdl_chain_build(ctx, As[g], CDL_F64, Ds[g], sc + g, n, o->d, o->chain_dtype, 0,
@@ -429,6 +462,7 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
     int st = chain_solve(ctx, ctx->pair_chain, As[g], static_cast<double*>(dY), o->k, &o->solve,
                          Zs[g], sts[g]);
     if (st != CDL_OK && st != CDL_ERR_NOT_CONVERGED) return st;
+    converged = converged && st == CDL_OK;
   }
   double* Fd = o->host_io ? static_cast<double*>(dF) : F;
   int64_t* topd = o->host_io ? static_cast<int64_t*>(dtop) : top_idx;
@@ -441,7 +475,7 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
                                    cudaMemcpyDeviceToHost, ctx->stream));
     CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   }
-  return CDL_OK;
+  return converged ? CDL_OK : CDL_ERR_NOT_CONVERGED;
 }
 
 }  // extern "C"

@@ -10,6 +10,7 @@
 // both act identically; without the eigenvalue 1 rounding errors are not
 // amplified by the repeated squaring.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "internal.h"
 
@@ -100,6 +101,69 @@ __global__ void __launch_bounds__(256) k_chain_init_bf16(const double* __restric
       Alo[off + j] = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(h)));
     }
   }
+}
+
+// ---- fp8 (e4m3) chains: level i stores value / s_i with s_i = amax_i / 448,
+// amax_i a bound on |value| (float bits, so atomicMax on the bits orders them).
+
+__device__ __forceinline__ float fp8_scale_of(unsigned amax_bits) {
+  const float a = __uint_as_float(amax_bits);
+  return a > 0.f ? a * (1.0f / 448.0f) : 1.0f;
+}
+
+// amax_0 = max |level 0| over the bf16 level.
+__global__ void __launch_bounds__(256) k_absmax_bf16(const __nv_bfloat16* __restrict__ L, size_t count,
+                                                      unsigned* __restrict__ amax) {
+  float m = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(__bfloat162float(L[i])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
+}
+
+// level 0 in e4m3 from its bf16 copy.
+__global__ void __launch_bounds__(256) k_quant_fp8(const __nv_bfloat16* __restrict__ L, size_t count,
+                                                    const unsigned* __restrict__ amax, uint8_t* __restrict__ Q) {
+  const float inv = 1.0f / fp8_scale_of(*amax);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    Q[i] = (uint8_t)__nv_cvt_float_to_fp8(__bfloat162float(L[i]) * inv, __NV_SATFINITE, __NV_E4M3);
+}
+
+// amax_{i+1} = (1 + 2^-16) max_r sum_c (s_i q_rc)^2: for the symmetric level S,
+// |(S S)_ab| <= |row a| |row b| <= max_r |row r|^2, attained on the diagonal,
+// so the bound is tight and the squaring's output never overflows e4m3.
+__global__ void __launch_bounds__(256) k_rownorm_fp8(const uint8_t* __restrict__ Q, int npad,
+                                                      const unsigned* __restrict__ amax_in,
+                                                      unsigned* __restrict__ amax_out) {
+  __shared__ float red[8];
+  const float s = fp8_scale_of(*amax_in);
+  float m = 0.f;
+  for (int r = blockIdx.x; r < npad; r += gridDim.x) {
+    const uint8_t* row = Q + (size_t)r * npad;
+    float acc = 0.f;
+    for (int c = threadIdx.x * 4; c < npad; c += blockDim.x * 4) {
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(row + c);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        __nv_fp8_e4m3 q;
+        q.__x = (__nv_fp8_storage_t)((w >> (8 * b)) & 0xFFu);
+        const float v = (float)q;
+        acc = __fmaf_rn(v, v, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      m = fmaxf(m, t * s * s);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(amax_out, __float_as_uint(m * (1.0f + 0x1p-16f)));
 }
 
 __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
@@ -272,6 +336,25 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
       k_chain_init<float><<<blocks, 256, 0, ctx->stream>>>(A, n, np, ch->rsqrt_d, u,
                                                            static_cast<float*>(ch->level(0)));
       break;
+    case CDL_FP8E4M3: {
+      // bf16 level 0 (apply copy) and A_hi/A_lo, then the bound and the e4m3 level
+      CDL_CUDA_TRY(cudaMemsetAsync(ch->amax, 0, ch->d * sizeof(unsigned), ctx->stream));
+      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
+          A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(ch->level16(0)), static_cast<__nv_bfloat16*>(ch->aop),
+          static_cast<__nv_bfloat16*>(ch->aop) + (size_t)np * np);
+      CDL_TRY(L.done());
+      const size_t cnt = (size_t)np * np;
+      {
+        Launch L2(ctx, CDL_KC_CHAIN_INIT, 2.0 * cnt);
+        k_absmax_bf16<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(
+            static_cast<const __nv_bfloat16*>(ch->level16(0)), cnt, ch->amax);
+        CDL_TRY(L2.done());
+      }
+      Launch L3(ctx, CDL_KC_CHAIN_INIT, 3.0 * cnt);
+      k_quant_fp8<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(static_cast<const __nv_bfloat16*>(ch->level16(0)),
+                                                              cnt, ch->amax, static_cast<uint8_t*>(ch->level(0)));
+      return L3.done();
+    }
     case CDL_BF16:
       k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
           A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(ch->level(0)), static_cast<__nv_bfloat16*>(ch->aop),
@@ -280,6 +363,14 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
     default:
       return CDL_ERR_UNSUPPORTED;
   }
+  return L.done();
+}
+
+int fp8_level_bound(cdl_ctx* ctx, cdl_chain* ch, int level) {
+  const int np = (int)ch->npad;
+  Launch L(ctx, CDL_KC_MISC, (double)np * np);
+  k_rownorm_fp8<<<std::min(np, ctx->sm_count * 8), 256, 0, ctx->stream>>>(
+      static_cast<const uint8_t*>(ch->level(level)), np, ch->amax + level, ch->amax + level + 1);
   return L.done();
 }
 

@@ -73,11 +73,18 @@ struct cdl_chain {
   size_t elem = 8;
   void* levels = nullptr;     // d * npad * npad elements
   void* aop = nullptr;        // bf16 chains: A = A_hi + A_lo as two bf16 npad x npad matrices
+  void* levels16 = nullptr;   // fp8 chains: bf16 copies of the levels (the apply's operand)
+  unsigned* amax = nullptr;   // fp8 chains: per-level bound of |value| (float bits), scale = amax/448
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
   void* level(int i) const {
     return static_cast<char*>(levels) + (size_t)i * (size_t)npad * (size_t)npad * elem;
+  }
+  // bf16 view of level i used by the apply (the level itself for bf16 chains)
+  void* level16(int i) const {
+    if (!levels16) return level(i);
+    return static_cast<char*>(levels16) + (size_t)i * (size_t)npad * (size_t)npad * 2;
   }
 };
 
@@ -108,6 +115,7 @@ int graph_build_static(const double* X, int64_t n, int T, double sigma, double* 
 // chain.cu
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A);
 int chain_square_simt(cdl_ctx* ctx, cdl_chain* ch, int level);
+int fp8_level_bound(cdl_ctx* ctx, cdl_chain* ch, int level);
 int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void* partial,
                int k, int splits);
 // tc_gemm.cu

@@ -396,7 +396,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   cudaStream_t st = ctx->stream;
   const int n = (int)ch->n, np = (int)ch->npad;
   const int kp = (int)round_up(k, 16);   // tensor-core N = 2 kp: multiple of 32
-  const bool bf16 = ch->dtype == CDL_BF16;
+  const bool bf16 = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3;   // tensor-core apply
   const size_t xe = ch->dtype == CDL_F64 ? 8 : 4;
   const int kblocks = np / 64;
   int splits;
@@ -539,6 +539,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       break;
     }
     if (iters >= opts->max_iter) break;
+    if (!(rel <= 1e6)) break;   // NaN or a growing residual: the preconditioner does not converge
     // x = D^{-1/2} R in the chain's working precision
     {
       const size_t cnt = (size_t)np * kp;
@@ -619,7 +620,8 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
     stats->iters = iters;
     stats->rel_res = rel;
   }
-  return (opts->rel_tol > 0 && rel > opts->rel_tol) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
+  if (!(rel <= 1e6)) return CDL_ERR_NOT_CONVERGED;
+  return (opts->rel_tol > 0 && !(rel <= opts->rel_tol)) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
 }
 
 }  // namespace cdl

@@ -19,6 +19,7 @@
 // expiry the CTA records DEV_WAIT_TIMEOUT in the status word and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <string>
@@ -42,7 +43,7 @@ constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
-enum { MODE_SQUARE = 0, MODE_APPLY = 1 };
+enum { MODE_SQUARE = 0, MODE_APPLY = 1, MODE_SQUARE_FP8 = 2 };
 
 struct TcParams {
   const uint32_t* tiles;   // packed tile descriptors
@@ -55,6 +56,11 @@ struct TcParams {
   void* out;               // square: bf16 level (npad x npad); apply: float partials
   int ldo;                 // apply: partial row stride (= bn)
   unsigned* status;
+  // fp8 squaring: level value = amax/448 * stored value; amax[level] of the
+  // input, amax[level + 1] of the output (float bits); out16 = bf16 copy
+  const unsigned* amax;
+  int level;
+  void* out16;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -137,6 +143,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void mma_fp8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -158,11 +173,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Per-level scale of an fp8 level from its bound amax (float bits): the level
+// holds value / scale with scale = amax / 448 (448 = largest finite e4m3).
+__device__ __forceinline__ float fp8_scale(unsigned amax_bits) {
+  const float a = __uint_as_float(amax_bits);
+  return a > 0.f ? a * (1.0f / 448.0f) : 1.0f;
+}
+
 // Tile descriptors. square: I (bits 0-14), J (bits 15-29), half (bit 30).
-// apply: row block m (bits 0-15), split s (bits 16-31).
-__device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int& a_row, int& b_row,
+// apply: row block m (bits 0-15), split s (bits 16-31). bke = elements per
+// 128-byte k-block (64 bf16 or 128 fp8).
+__device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int bke, int& a_row, int& b_row,
                                        int& k0, int& I, int& J, int& split) {
-  if (p.mode == MODE_SQUARE) {
+  if (p.mode != MODE_APPLY) {
     I = t & 0x7FFF;
     J = (t >> 15) & 0x7FFF;
     const int half = (t >> 30) & 1;
@@ -175,15 +198,17 @@ __device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int& a_row
     split = (t >> 16) & 0xFFFF;
     a_row = m * 128;
     b_row = 0;
-    k0 = split * p.kblocks * BK;
+    k0 = split * p.kblocks * bke;
     I = m;
     J = 0;
   }
 }
 
+template <bool FP8>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const TcParams p) {
+  constexpr int BKE = FP8 ? 128 : 64;   // elements per 128-byte k-block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -232,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
       int a_row, b_row, k0, I, J, split;
-      decode(p, p.tiles[t], a_row, b_row, k0, I, J, split);
+      decode(p, p.tiles[t], BKE, a_row, b_row, k0, I, J, split);
       for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t r = (uint32_t)(it / STAGES);
@@ -243,8 +268,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_TILE;
         mbar_expect_tx(full_bar(s), A_TILE + b_bytes);
-        tma_load_2d(a_dst, &tmA, k0 + kb * BK, a_row, full_bar(s));
-        tma_load_2d(b_dst, &tmB, k0 + kb * BK, b_row, full_bar(s));
+        tma_load_2d(a_dst, &tmA, k0 + kb * BKE, a_row, full_bar(s));
+        tma_load_2d(b_dst, &tmB, k0 + kb * BKE, b_row, full_bar(s));
       }
     }
     if (!ok) {
@@ -281,10 +306,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint64_t adesc = smem_desc(a_addr);
         const uint64_t bdesc = smem_desc(a_addr + A_TILE);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          // advance 16 bf16 = 32 bytes along K inside the swizzle atom
-          mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc,
-                   (kb | kk) != 0);
+        for (int kk = 0; kk < 4; ++kk) {
+          // advance 32 bytes (16 bf16 or 32 fp8) along K inside the swizzle atom
+          if constexpr (FP8)
+            mma_fp8(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
+          else
+            mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
         }
         issued = true;
         mma_commit(empty_bar(s));
@@ -309,7 +336,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!mbar_wait(tfull_bar(acc), ar & 1, abort_flag, p.status)) break;
       tc_fence_after();
       int a_row, b_row, k0, I, J, split;
-      decode(p, p.tiles[t], a_row, b_row, k0, I, J, split);
+      decode(p, p.tiles[t], BKE, a_row, b_row, k0, I, J, split);
       const int r = a_row + row_in_tile;
       const uint32_t taddr = tmem_base + (uint32_t)(acc * MAX_BN) + ((uint32_t)(q * 32) << 16);
       for (int c = 0; c < p.bn / 32; ++c) {
@@ -338,6 +365,57 @@ __global__ void __launch_bounds__(THREADS, 1)
               const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
               if (col >= r) C[(size_t)r * p.npad + col] = h;
               if (col > r) C[(size_t)col * p.npad + r] = h;
+            }
+          }
+        } else if (p.mode == MODE_SQUARE_FP8) {
+          // value = acc * s_in^2; fp8 level stores value / s_out, bf16 copy the value
+          const float s_in = fp8_scale(p.amax[p.level]);
+          const float sc = s_in * s_in;
+          const float inv_out = 1.0f / fp8_scale(p.amax[p.level + 1]);
+          uint8_t* C8 = static_cast<uint8_t*>(p.out);
+          __nv_bfloat16* C16 = static_cast<__nv_bfloat16*>(p.out16);
+          const int col0 = b_row + c * 32;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] *= sc;
+          uint8_t q8[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) q8[e] = (uint8_t)__nv_cvt_float_to_fp8(v[e] * inv_out, __NV_SATFINITE, __NV_E4M3);
+          if (I != J) {
+            uint32_t w8[8], packed[16];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              w8[e] = (uint32_t)q8[4 * e] | ((uint32_t)q8[4 * e + 1] << 8) | ((uint32_t)q8[4 * e + 2] << 16) |
+                      ((uint32_t)q8[4 * e + 3] << 24);
+            uint4* d8 = reinterpret_cast<uint4*>(C8 + (size_t)r * p.npad + col0);
+            d8[0] = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+            d8[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+              packed[e] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            uint4* d16 = reinterpret_cast<uint4*>(C16 + (size_t)r * p.npad + col0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              d16[e] = make_uint4(packed[4 * e], packed[4 * e + 1], packed[4 * e + 2], packed[4 * e + 3]);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              C8[(size_t)(col0 + e) * p.npad + r] = q8[e];
+              C16[(size_t)(col0 + e) * p.npad + r] = __float2bfloat16_rn(v[e]);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int col = col0 + e;
+              const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
+              if (col >= r) {
+                C8[(size_t)r * p.npad + col] = q8[e];
+                C16[(size_t)r * p.npad + col] = h;
+              }
+              if (col > r) {
+                C8[(size_t)col * p.npad + r] = q8[e];
+                C16[(size_t)col * p.npad + r] = h;
+              }
             }
           }
         } else {
@@ -382,15 +460,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D bf16 tensor map over a rows x cols row-major matrix, box 64 x box_rows.
-int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows) {
+// 2-D tensor map over a rows x cols row-major matrix of bf16 (elem = 2) or
+// fp8 bytes (elem = 1); box = one 128-byte row segment x box_rows.
+int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows, int elem = 2) {
   auto fn = encode_fn();
   if (!fn) return CDL_ERR_UNSUPPORTED;
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * elem};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box,
+  CUresult r = fn(map, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  const_cast<void*>(base), gdim, gstride, box,
                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -400,10 +480,11 @@ int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int
   return CDL_OK;
 }
 
-uint32_t make_idesc(int n) {
+uint32_t make_idesc(int n, bool fp8 = false) {
+  const uint32_t fmt = fp8 ? 0u : 1u;   // kind::f8f6f4: e4m3 = 0; kind::f16: bf16 = 1
   return (1u << 4)                      // D: float32
-         | (1u << 7)                    // A: bf16
-         | (1u << 10)                   // B: bf16
+         | (fmt << 7)                   // A format
+         | (fmt << 10)                  // B format
          | ((uint32_t)(n >> 3) << 17)   // N / 8
          | ((uint32_t)(BM >> 4) << 24); // M / 16
 }
@@ -451,15 +532,19 @@ int get_tiles(cdl_ctx* ctx, const std::string& name, Builder build, const uint32
 }
 
 int launch(cdl_ctx* ctx, const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int kc,
-           double work) {
+           double work, bool fp8 = false) {
   static bool attr = false;
   if (!attr) {
-    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr = true;
   }
   const int grid = std::min(p.num_tiles, ctx->sm_count);
   Launch L(ctx, kc, work);
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, ctx->stream>>>(a, b, p);
+  if (fp8)
+    k_tc_gemm<true><<<grid, THREADS, SMEM_BYTES, ctx->stream>>>(a, b, p);
+  else
+    k_tc_gemm<false><<<grid, THREADS, SMEM_BYTES, ctx->stream>>>(a, b, p);
   return L.done();
 }
 
@@ -478,27 +563,32 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   const uint32_t* tiles;
   int count;
   CDL_TRY(get_tiles(ctx, "tc.square." + std::to_string(nb), [&] { return square_tiles(nb); }, &tiles, &count));
+  const bool fp8 = ch->dtype == CDL_FP8E4M3;
+  const int elem = fp8 ? 1 : 2;
   CUtensorMap ma, mb;
-  CDL_TRY(make_map(&ma, ch->level(level), np, np, 128));
-  CDL_TRY(make_map(&mb, ch->level(level), np, np, 256));
+  CDL_TRY(make_map(&ma, ch->level(level), np, np, 128, elem));
+  CDL_TRY(make_map(&mb, ch->level(level), np, np, 256, elem));
   TcParams p;
   p.tiles = tiles;
   p.num_tiles = count;
-  p.kblocks = np / BK;
+  p.kblocks = np / (128 / elem);
   p.bn = 256;
-  p.idesc = make_idesc(256);
-  p.mode = MODE_SQUARE;
+  p.idesc = make_idesc(256, fp8);
+  p.mode = fp8 ? MODE_SQUARE_FP8 : MODE_SQUARE;
   p.npad = np;
   p.out = ch->level(level + 1);
   p.ldo = np;
   p.status = ctx->dev_status;
+  p.amax = ch->amax;
+  p.level = level;
+  p.out16 = fp8 ? ch->level16(level + 1) : nullptr;
   const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
-  return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops);
+  return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8);
 }
 
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial, int kp,
              int splits) {
-  return apply_tc_mat(ctx, ch->level(level), (int)ch->npad, xop, partial, kp, splits);
+  return apply_tc_mat(ctx, ch->level16(level), (int)ch->npad, xop, partial, kp, splits);
 }
 
 int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp, int splits) {
@@ -524,6 +614,9 @@ int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float*
   p.out = partial;
   p.ldo = bn;
   p.status = ctx->dev_status;
+  p.amax = nullptr;
+  p.level = 0;
+  p.out16 = nullptr;
   const double bytes = 2.0 * np * (double)np;
   return launch(ctx, ma, mbm, p, CDL_KC_APPLY, bytes);
 }

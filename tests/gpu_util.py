@@ -31,6 +31,8 @@ class _CAI:
 def view_device(ptr, shape, dtype):
     if dtype == "bf16":
         return torch.as_tensor(_CAI(ptr, shape, "<i2"), device="cuda").view(torch.bfloat16)
+    if dtype == "fp8":
+        return torch.as_tensor(_CAI(ptr, shape, "|u1"), device="cuda").view(torch.float8_e4m3fn)
     return torch.as_tensor(_CAI(ptr, shape, np.dtype(dtype).str), device="cuda")
 
 
@@ -77,6 +79,20 @@ class Ctx:
         st, ptr, npad = self.cdl.cdl_chain_level(ch, i)
         self.check(st)
         return view_device(ptr, (npad, npad), dtype)
+
+    def level16(self, ch, i):
+        """bf16 view of level i read by the apply, as float64 on the host."""
+        st, ptr = self.cdl.cdl_chain_apply_level(ch, i)
+        self.check(st)
+        st, _, npad = self.cdl.cdl_chain_level(ch, i)
+        return view_device(ptr, (npad, npad), "bf16").double().cpu().numpy()
+
+    def level_values(self, ch, i, dtype):
+        """Level i as float64 values on the host (fp8 levels times their scale)."""
+        v = self.level(ch, i, dtype).double().cpu().numpy()
+        st, sc = self.cdl.cdl_chain_level_scale(ch, i)
+        self.check(st)
+        return v * sc
 
     def solve(self, ch, A, Y, max_iter=20, rel_tol=1e-10, expect=0, flags=0):
         cdl = self.cdl

@@ -95,11 +95,14 @@ def _deflated_levels(Ao, d):
     return [L - np.outer(u, u) for L in O.chain_levels(Ao, d)]
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 3e-2)])
+DT = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 3e-2), ("fp8", 0.2)])
 @pytest.mark.parametrize("n", [300, 1000])
 def test_chain_levels_match_oracle(G, dtype, tol, n):
     cdl = G.cdl
-    dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}[dtype]
+    dt = DT[dtype]
     X = iid_pair(n, 32, 1, seed=7).X[0]
     A, D, vol, _ = G.graph(X)
     d = 4
@@ -108,8 +111,7 @@ def test_chain_levels_match_oracle(G, dtype, tol, n):
         ref = _deflated_levels(_h(A), d)
         scale = np.linalg.norm(ref[0])
         for i in range(d):
-            Lg = G.level(ch, i, {"f64": np.float64, "f32": np.float32, "bf16": "bf16"}[dtype])
-            Lg = Lg.double().cpu().numpy()
+            Lg = G.level_values(ch, i, {"f64": np.float64, "f32": np.float32, "bf16": "bf16", "fp8": "fp8"}[dtype])
             assert np.all(Lg[n:, :] == 0) and np.all(Lg[:, n:] == 0)   # zero padding
             assert np.array_equal(Lg, Lg.T)                             # exact symmetry
             err = np.linalg.norm(Lg[:n, :n] - ref[i]) / scale
@@ -139,6 +141,33 @@ def test_tcgen05_square_is_exact_product_of_its_inputs(G, n):
     assert np.array_equal(L1, L1.T)
 
 
+@pytest.mark.parametrize("n", [300, 1000, 2100])
+def test_tcgen05_fp8_square_is_exact_product_of_its_inputs(G, n):
+    """One e4m3 squaring (kind::f8f6f4) against the float64 product of the same
+    dequantized e4m3 input: the bf16 copy of the output may differ only by
+    float32 accumulation and bf16 rounding; the e4m3 output additionally by
+    e4m3 rounding (2^-4 relative, or one subnormal step) and must respect the
+    per-level bound (no overflow)."""
+    cdl = G.cdl
+    X = iid_pair(n, 24, 1, seed=13).X[0]
+    A, D, vol, _ = G.graph(X)
+    ch = G.chain(A, D, vol, 2, cdl.CDL_FP8E4M3)
+    try:
+        V0 = G.level_values(ch, 0, "fp8")
+        V1 = G.level_values(ch, 1, "fp8")
+        st, sc1 = cdl.cdl_chain_level_scale(ch, 1)
+        st2, p16, npad = cdl.cdl_chain_level(ch, 1)
+        L16 = G.level16(ch, 1)
+    finally:
+        cdl.cdl_chain_free(ch)
+    R = V0 @ V0
+    acc = V0.shape[0] * 2.0 ** -23 * (np.abs(V0) @ np.abs(V0))
+    assert np.all(np.abs(L16 - R) <= 2.0 ** -8 * np.abs(R) + acc + 1e-30)
+    assert np.all(np.abs(V1 - R) <= 2.0 ** -4 * np.abs(R) + sc1 * 2.0 ** -9 + acc + 1e-30)
+    assert np.abs(V1).max() <= 448 * sc1 * (1 + 1e-6)
+    assert np.array_equal(V1, V1.T) and np.array_equal(L16, L16.T)
+
+
 def test_simt_f32_square_is_exact_product_of_its_inputs(G):
     cdl = G.cdl
     n = 700
@@ -158,11 +187,11 @@ def test_simt_f32_square_is_exact_product_of_its_inputs(G):
 # ------------------------------------------------------------------ solve
 
 @pytest.mark.parametrize("full", [False, True])
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-10), ("bf16", 1e-10)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-10), ("bf16", 1e-10), ("fp8", 1e-10)])
 @pytest.mark.parametrize("n,k", [(300, 8), (1000, 32)])
 def test_solve_matches_exact_embedding(G, dtype, tol, n, k, full):
     cdl = G.cdl
-    dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}[dtype]
+    dt = DT[dtype]
     X = iid_pair(n, 32, 1, seed=n + 1).X[0]
     Ao, Do, volo, _ = O.gaussian_graph(X)
     Yo = O.project(Ao, 9, k)
@@ -233,11 +262,12 @@ def iid1024():
     ("f32", "f64", 1e-9, False),
     ("bf16", "f32", 1e-6, False),
     ("bf16", "f32", 1e-6, True),
+    ("fp8", "f32", 1e-6, False),
 ])
 def test_pair_iid_n1024_matches_oracle(G, iid1024, chain, score, tol, host_io):
     cdl = G.cdl
     wl, out = iid1024
-    dt = {"f64": cdl.CDL_F64, "f32": cdl.CDL_F32, "bf16": cdl.CDL_BF16}
+    dt = DT
     F, top, s1, s2 = G.pair(wl.X[0], wl.X[1], 32, 8, dt[chain], dt[score], 0, 10, host_io=host_io)
     Fo = out["F"]
     rel = np.abs(F - Fo) / Fo
@@ -278,8 +308,8 @@ def test_invalid_arguments(G):
     assert cdl.cdl_build_graph(G.h, X, n, T, 0.0, cdl.CDL_F32, A, D, *args) == cdl.CDL_ERR_UNSUPPORTED
     assert cdl.cdl_build_graph(G.h, X.data_ptr() + 4, n, T, 0.0, cdl.CDL_F64, A, D, *args) == \
         cdl.CDL_ERR_INVALID_ARG
-    st, ch = cdl.cdl_chain_build(G.h, A, cdl.CDL_F64, D, s, n, 3, cdl.CDL_FP8E4M3)
-    assert st == cdl.CDL_ERR_UNSUPPORTED
+    st, ch = cdl.cdl_chain_build(G.h, A, cdl.CDL_F64, D, s, n, 3, 7)     # no such dtype
+    assert st == cdl.CDL_ERR_INVALID_ARG
     assert cdl.cdl_project(G.h, A, cdl.CDL_F64, n, 0, 1, A) == cdl.CDL_ERR_INVALID_ARG
     assert cdl.cdl_project(G.h, A, cdl.CDL_F64, n, 1025, 1, A) == cdl.CDL_ERR_INVALID_ARG
     F = torch.zeros(n, dtype=torch.float64, device="cuda")
