@@ -258,6 +258,7 @@ int cdl_chain_free(cdl_chain* ch) {
   cudaFree(ch->aop);
   cudaFree(ch->levels16);
   cudaFree(ch->amax);
+  cudaFree(ch->ahl);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
   cudaFree(ch->vol);
@@ -326,11 +327,13 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     size_t bytes = (size_t)d * npad * npad * ch->elem;
     const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
     const size_t l16_bytes = chain_dtype == CDL_FP8E4M3 ? (size_t)d * npad * npad * 2 : 0;
-    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes + l16_bytes > ctx->ws_cap) {
+    const size_t ahl_bytes = 2 * (size_t)n * n * sizeof(float);
+    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes + l16_bytes + ahl_bytes > ctx->ws_cap) {
       delete ch;
       return CDL_ERR_OOM;
     }
-    if ((aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
+    if (cudaMalloc(&ch->ahl, ahl_bytes) != cudaSuccess ||
+        (aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
         (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
                        cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||
         cudaMalloc(&ch->levels, bytes) != cudaSuccess ||

@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace cdl {
@@ -166,6 +167,16 @@ __global__ void __launch_bounds__(256) k_rownorm_fp8(const uint8_t* __restrict__
   if (threadIdx.x == 0) atomicMax(amax_out, __float_as_uint(m * (1.0f + 0x1p-16f)));
 }
 
+// A as float hi + lo planes for the float-float residual (integer split).
+__global__ void __launch_bounds__(256) k_split_a(const double* __restrict__ A, size_t count,
+                                                  float* __restrict__ hi, float* __restrict__ lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const ff v = split_nonneg(A[i]);
+    hi[i] = v.hi;
+    lo[i] = v.lo;
+  }
+}
+
 __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
   double fnb = nb + 0.5;
   int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
@@ -314,6 +325,12 @@ int square_impl(cdl_ctx* ctx, cdl_chain* ch, int level) {
 
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
   const int n = (int)ch->n, np = (int)ch->npad;
+  {
+    const size_t cnt = (size_t)n * n;
+    Launch L(ctx, CDL_KC_CHAIN_INIT, 16.0 * cnt);
+    k_split_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, cnt, ch->ahl, ch->ahl + cnt);
+    CDL_TRY(L.done());
+  }
   void* wsu;
   CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * (sizeof(double) + 2 * sizeof(float)), &wsu));
   double* u = static_cast<double*>(wsu);

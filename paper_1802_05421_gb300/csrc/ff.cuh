@@ -64,6 +64,20 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)(sign | ed | m));
 }
 
+// Split a float64 x >= 0 into floats hi + lo with hi = x truncated to 24 bits
+// and lo the remaining 29 mantissa bits rounded to 24 (|x - hi - lo| <=
+// 2^-48 x), by integer operations only. Values below 2^-90 give lo = 0.
+__device__ __forceinline__ ff split_nonneg(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;      // x in [2^e, 2^(e+1))
+  if (e < -100) return {0.f, 0.f};
+  const uint32_t hi_bits = ((uint32_t)(e + 127) << 23) | ((uint32_t)(b >> 29) & 0x7FFFFFu);
+  const uint32_t low29 = (uint32_t)(b & 0x1FFFFFFFull);
+  // lo = low29 * 2^(e - 52): float of the integer, then the power of two
+  const float lo = __uint2float_rn(low29) * __uint_as_float((uint32_t)(e - 52 + 127) << 23);
+  return {__uint_as_float(hi_bits), lo};
+}
+
 __device__ __forceinline__ float d2f_trunc(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;

@@ -75,6 +75,7 @@ struct cdl_chain {
   void* aop = nullptr;        // bf16 chains: A = A_hi + A_lo as two bf16 npad x npad matrices
   void* levels16 = nullptr;   // fp8 chains: bf16 copies of the levels (the apply's operand)
   unsigned* amax = nullptr;   // fp8 chains: per-level bound of |value| (float bits), scale = amax/448
+  float* ahl = nullptr;       // A as float hi + lo planes (n x n each), the float-float residual's operand
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1

@@ -178,35 +178,36 @@ __device__ __forceinline__ void ff_mac(float ah, float al, float zh, float zl, f
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
-constexpr int RB_M = 64, RB_N = 128, RB_K = 16;
+constexpr int RB_M = 64, RB_N = 64, RB_K = 16;
 
-// R = Y - D o Z + A Z for a 64-row x 128-column tile; per-block sum of R^2.
-__global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, const float* __restrict__ Zh,
-                                                   const float* __restrict__ Zl, const double* __restrict__ Z,
-                                                   const double* __restrict__ Y, const double* __restrict__ D,
-                                                   int n, int k, double* __restrict__ R,
-                                                   double* __restrict__ part) {
-  __shared__ float Ah[RB_K][RB_M + 1], Al[RB_K][RB_M + 1];
+// R = Y - D o Z + A Z for a 64-row x 64-column tile, 4 x 4 float-float
+// accumulators per thread; A and Z arrive as float hi + lo planes. Per-block
+// sum of R^2.
+__global__ void __launch_bounds__(256) k_residual(const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                                   const float* __restrict__ Zh, const float* __restrict__ Zl,
+                                                   const double* __restrict__ Z, const double* __restrict__ Y,
+                                                   const double* __restrict__ D, int n, int k,
+                                                   double* __restrict__ R, double* __restrict__ part) {
+  __shared__ __align__(16) float Ah[RB_K][RB_M + 4], Al[RB_K][RB_M + 4];
   __shared__ __align__(16) float Bh[RB_K][RB_N], Bl[RB_K][RB_N];
   __shared__ double red[8];
   const int i0 = blockIdx.x * RB_M, c0 = blockIdx.y * RB_N;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float sh[4][8], sc[4][8];
+  float sh[4][4], sc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) sh[a][b] = sc[a][b] = 0.f;
-  int rows[4] = {ty * 2, ty * 2 + 1, 32 + ty * 2, 32 + ty * 2 + 1};
+    for (int b = 0; b < 4; ++b) sh[a][b] = sc[a][b] = 0.f;
   for (int j0 = 0; j0 < n; j0 += RB_K) {
 #pragma unroll
     for (int e = 0; e < (RB_M * RB_K) / 256; ++e) {
       const int idx = tid + e * 256;
       const int ii = idx / RB_K, jj = idx % RB_K;
       const int i = i0 + ii, j = j0 + jj;
-      double a = (i < n && j < n) ? A[(size_t)i * n + j] : 0.0;
-      const float h = (float)a;
-      Ah[jj][ii] = h;
-      Al[jj][ii] = (float)(a - (double)h);
+      const bool ok = i < n && j < n;
+      const size_t o = (size_t)i * n + j;
+      Ah[jj][ii] = ok ? Ahi[o] : 0.f;
+      Al[jj][ii] = ok ? Alo[o] : 0.f;
     }
 #pragma unroll
     for (int e = 0; e < (RB_N * RB_K) / 256; ++e) {
@@ -218,38 +219,30 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, 
       Bl[jj][cc] = ok ? Zl[(size_t)j * k + c] : 0.f;
     }
     __syncthreads();
-#pragma unroll 2
+#pragma unroll 4
     for (int jj = 0; jj < RB_K; ++jj) {
-      float ah[4], al[4], bh[8], bl[8];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        ah[a] = Ah[jj][rows[a]];
-        al[a] = Al[jj][rows[a]];
-      }
-      const float4 h0 = *reinterpret_cast<const float4*>(&Bh[jj][tx * 4]);
-      const float4 h1 = *reinterpret_cast<const float4*>(&Bh[jj][64 + tx * 4]);
-      const float4 l0 = *reinterpret_cast<const float4*>(&Bl[jj][tx * 4]);
-      const float4 l1 = *reinterpret_cast<const float4*>(&Bl[jj][64 + tx * 4]);
-      bh[0] = h0.x; bh[1] = h0.y; bh[2] = h0.z; bh[3] = h0.w;
-      bh[4] = h1.x; bh[5] = h1.y; bh[6] = h1.z; bh[7] = h1.w;
-      bl[0] = l0.x; bl[1] = l0.y; bl[2] = l0.z; bl[3] = l0.w;
-      bl[4] = l1.x; bl[5] = l1.y; bl[6] = l1.z; bl[7] = l1.w;
+      const float4 ah = *reinterpret_cast<const float4*>(&Ah[jj][ty * 4]);
+      const float4 al = *reinterpret_cast<const float4*>(&Al[jj][ty * 4]);
+      const float4 bh = *reinterpret_cast<const float4*>(&Bh[jj][tx * 4]);
+      const float4 bl = *reinterpret_cast<const float4*>(&Bl[jj][tx * 4]);
+      const float avh[4] = {ah.x, ah.y, ah.z, ah.w}, avl[4] = {al.x, al.y, al.z, al.w};
+      const float bvh[4] = {bh.x, bh.y, bh.z, bh.w}, bvl[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) ff_mac(ah[a], al[a], bh[b], bl[b], sh[a][b], sc[a][b]);
+        for (int b = 0; b < 4; ++b) ff_mac(avh[a], avl[a], bvh[b], bvl[b], sh[a][b], sc[a][b]);
     }
     __syncthreads();
   }
   double sq = 0.0;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const int i = i0 + rows[a];
+    const int i = i0 + ty * 4 + a;
     if (i >= n) continue;
     const double di = D[i];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int c = c0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
       if (c >= k) continue;
       const size_t o = (size_t)i * k + c;
       const double az = (double)sh[a][b] + (double)sc[a][b];
@@ -473,8 +466,8 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
     {
       dim3 g(res_gx, res_gy);
       Launch L(ctx, CDL_KC_RESIDUAL, (double)n * n * k);
-      k_residual<<<g, 256, 0, st>>>(A, static_cast<const float*>(vzh), static_cast<const float*>(vzl), Z, Y,
-                                     ch->D, n, k, R, red);
+      k_residual<<<g, 256, 0, st>>>(ch->ahl, ch->ahl + (size_t)n * n, static_cast<const float*>(vzh),
+                                     static_cast<const float*>(vzl), Z, Y, ch->D, n, k, R, red);
       CDL_TRY(L.done());
     }
     nparts = res_gx * res_gy;
