@@ -188,6 +188,23 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- ranks
+def rank_max(values, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (identity
+    without a process group)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def pairs_per_second(step_ms_max: float, world: int) -> float:
+    """Whole-job rate: every rank processes one pair per step, the job is as
+    fast as its slowest rank."""
+    return world * 1000.0 / step_ms_max
+
+
 # ---------------------------------------------------------------- profiling cases
 def run_case(args):
     """Small single-kernel cases for profiler captures (not a bench line):
@@ -246,6 +263,8 @@ def main():
     ap.add_argument("--chain", default="bf16", choices=["bf16", "fp8", "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-compare-f32", dest="compare_f32", action="store_false",
+                    help="skip the plain float32 GPU path comparison step")
     ap.add_argument("--case", default=None, choices=["square", "solve", "project", "score"],
                     help="run a small single-kernel case for a profiler capture instead of the bench")
     ap.add_argument("--n", type=int, default=12288)
@@ -336,12 +355,28 @@ def main():
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     same_top = htop.tolist() == top.cpu().tolist()
 
+    # plain float32 GPU path on the same pair (comparison of the metric)
+    f32 = None
+    if args.compare_f32 and args.chain == "bf16":
+        of = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_F32, cdl.CDL_F32, SEED, 0.0,
+                               cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0)
+        Ff = torch.empty(n, dtype=torch.float64, device="cuda")
+        tf = torch.empty(TOPK, dtype=torch.int64, device="cuda")
+        step(of, X1, X2, Ff, tf)   # warm-up (allocates the float32 chain)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(of, X1, X2, Ff, tf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f32_ms = e0.elapsed_time(e1)
+        rel = float(((Ff - F).abs() / F).max())
+        f32 = {"value": 1000.0 / f32_ms, "unit": "pairs/s", "ms_per_step": f32_ms, "steps": 1, "warmup": 1,
+               "same_top": tf.cpu().tolist() == top.cpu().tolist(), "max_rel_diff_F_vs_bf16": rel}
+
     # max over ranks
-    t_all = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    step_ms, e2e_s = float(t_all[0]), float(t_all[1])
-    value = world * 1000.0 / step_ms
+    step_ms, e2e_s = rank_max([step_ms, e2e_s], dist, "cuda")
+    value = pairs_per_second(step_ms, world)
 
     if rank == 0:
         pk, src = peaks()
@@ -375,7 +410,9 @@ def main():
                              "chain levels, far larger than the 129 MB L2"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 2 * n * T * 8,
+            "f32_path": f32,
+            "e2e": {"value": pairs_per_second(e2e_s * 1000.0, world), "unit": "pairs/s",
+                    "h2d_bytes_per_step": 2 * n * T * 8,
                     "d2h_bytes_per_step": n * 8 + TOPK * 8, "same_top_as_device_run": same_top},
             "gpu_launches": int(launches),
             "clocks": clocks,

@@ -112,6 +112,14 @@ int cdl_ctx_reset_counters(cdl_ctx* ctx);
 /* Total kernels this context launched since creation or the last reset. */
 int cdl_ctx_launch_count(cdl_ctx* ctx, int64_t* launches);
 
+/* Test hooks (0 = none). CDL_DEBUG_WITHHOLD_TC_LOAD: the next tensor-core
+ * squarings never issue their first tile load, so the kernel's bounded wait
+ * for it expires (about 2 s); the kernel records the expiry and returns, and
+ * cdl_sync reports CDL_ERR_TIMEOUT. Used to test the bounded-wait path; the
+ * outputs of such a launch are meaningless. */
+enum { CDL_DEBUG_WITHHOLD_TC_LOAD = 1 };
+int cdl_ctx_set_debug(cdl_ctx* ctx, int flags);
+
 /* ---------------------------------------------------------------- graph */
 
 /* Gaussian-kernel graph of n node series (Sec. 4.2.1 kernel; Sec. 2: no

@@ -94,9 +94,13 @@ def median_sigma(d2: np.ndarray) -> float:
     rule of the workloads; the paper fixes sigma by hand for its climate
     graph). Pinned by brute force on small inputs."""
     n = d2.shape[0]
-    iu = np.triu_indices(n, 1)
-    d = np.sqrt(d2[iu])
-    m = d.size
+    m = n * (n - 1) // 2
+    d = np.empty(m)
+    o = 0
+    for i in range(n - 1):                   # upper triangle, row by row
+        d[o:o + n - 1 - i] = d2[i, i + 1:]
+        o += n - 1 - i
+    np.sqrt(d, out=d)
     h = (m - 1) // 2
     return float(np.partition(d, h)[h])
 
@@ -198,7 +202,7 @@ def project_rows(A_rows: np.ndarray, rows: Sequence[int], seed: int, k: int) -> 
         hi = np.maximum(i, j)
         sgn = np.where(edge_sign_bits(seed, lo, hi, k), 1.0, -1.0)
         orient = np.where(j > i, 1.0, -1.0)
-        Y[t] = ((orient * np.sqrt(A_rows[t, j]))[:, None] * sgn).sum(axis=0)
+        Y[t] = (orient * np.sqrt(A_rows[t, j])) @ sgn
     return Y / math.sqrt(k)
 
 
@@ -206,6 +210,26 @@ def project(A: np.ndarray, seed: int, k: int) -> np.ndarray:
     """All rows of Y (see ``project_rows``)."""
     n = A.shape[0]
     return project_rows(A, range(n), seed, k)
+
+
+def project_rows_c(A_rows: np.ndarray, rows: Sequence[int], seed: int, k: int) -> np.ndarray:
+    """``project_rows`` computed by the oracle's plain C version (oracle/cproj.c,
+    same definition, OpenMP over rows) for large graphs. Pinned against
+    ``project_rows`` and ``project_explicit`` in the tests."""
+    import ctypes
+    from . import cbuild
+    lib = ctypes.CDLL(cbuild.build())
+    A_rows = np.ascontiguousarray(np.atleast_2d(A_rows), dtype=np.float64)
+    rows = np.ascontiguousarray(np.asarray(list(rows), dtype=np.int64))
+    n = A_rows.shape[1]
+    if k > 1024:
+        raise ValueError("k <= 1024")
+    Y = np.empty((rows.size, k))
+    P = ctypes.c_void_p
+    lib.cdl_oracle_project_rows.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_uint64, P]
+    lib.cdl_oracle_project_rows(A_rows.ctypes.data, rows.ctypes.data, rows.size, n, k, seed, Y.ctypes.data)
+    return Y
 
 
 # --------------------------------------------------------------------------

@@ -64,8 +64,9 @@ def edge_sign_bits(seed: int, i, j, k: int) -> np.ndarray:
     k1 = (seed >> 32) & 0xFFFFFFFF
     out = np.empty((i.size, k), dtype=bool)
     for rb in range((k + 127) // 128):
-        words = philox4x32(i, j, rb, 0, k0, k1)
-        for r in range(rb * 128, min(k, rb * 128 + 128)):
-            w = (r % 128) // 32
-            out[:, r] = ((words[w] >> np.uint32(r % 32)) & np.uint32(1)).astype(bool)
+        words = np.stack(philox4x32(i, j, rb, 0, k0, k1), axis=1).astype("<u4")   # (N, 4)
+        # bit b of word w is projection row 128 rb + 32 w + b
+        bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")      # (N, 128)
+        r1 = min(k, rb * 128 + 128)
+        out[:, rb * 128:r1] = bits[:, :r1 - rb * 128].astype(bool)
     return out

@@ -25,6 +25,7 @@ CDL_ERR_UNSUPPORTED = -6
 
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3 = 0, 1, 2, 3
 CDL_SOLVE_FULL_RESIDUAL = 1
+CDL_DEBUG_WITHHOLD_TC_LOAD = 1
 
 (CDL_KC_DISTANCE, CDL_KC_SELECT, CDL_KC_KERNEL, CDL_KC_CHAIN_INIT, CDL_KC_SQUARE, CDL_KC_APPLY,
  CDL_KC_RESIDUAL, CDL_KC_PROJECT, CDL_KC_SCORE, CDL_KC_TOPK, CDL_KC_MISC, CDL_KC_COUNT) = range(12)
@@ -63,6 +64,7 @@ _SIGS = {
     "cdl_ctx_timing": [_P, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_D)],
     "cdl_ctx_reset_counters": [_P],
     "cdl_ctx_launch_count": [_P, ctypes.POINTER(_I64)],
+    "cdl_ctx_set_debug": [_P, ctypes.c_int],
     "cdl_build_graph": [_P, _P, _I64, _I32, _D, ctypes.c_int, _P, _P, _P, _P],
     "cdl_build_graph_static": [_P, _I64, _I32, _D, _P, _P, _P, _P, _P],
     "cdl_chain_build": [_P, _P, ctypes.c_int, _P, _P, _I64, _I32, ctypes.c_int, _I32, ctypes.POINTER(_P)],
@@ -137,6 +139,10 @@ def cdl_ctx_timing(ctx, kernel_class: int):
 
 def cdl_ctx_reset_counters(ctx) -> int:
     return _lib.cdl_ctx_reset_counters(ctx)
+
+
+def cdl_ctx_set_debug(ctx, flags: int) -> int:
+    return _lib.cdl_ctx_set_debug(ctx, flags)
 
 
 def cdl_ctx_launch_count(ctx):

@@ -226,6 +226,12 @@ int cdl_ctx_reset_counters(cdl_ctx* ctx) {
   return CDL_OK;
 }
 
+int cdl_ctx_set_debug(cdl_ctx* ctx, int flags) {
+  if (!ctx || (flags & ~CDL_DEBUG_WITHHOLD_TC_LOAD)) return CDL_ERR_INVALID_ARG;
+  ctx->debug_flags = flags;
+  return CDL_OK;
+}
+
 int cdl_ctx_launch_count(cdl_ctx* ctx, int64_t* launches) {
   if (!ctx || !launches) return CDL_ERR_INVALID_ARG;
   *launches = ctx->launches;

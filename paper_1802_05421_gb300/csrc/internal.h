@@ -63,6 +63,7 @@ struct cdl_ctx {
   cdl_chain* pair_chain = nullptr;
   // tile schedules uploaded to the workspace, by workspace name -> tile count
   std::map<std::string, int> tile_lists;
+  int debug_flags = 0;   // CDL_DEBUG_* test hooks
 };
 
 struct cdl_chain {

@@ -13,6 +13,7 @@
 // through shared memory by the threads of the row.
 #include <cmath>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace cdl {
@@ -91,9 +92,8 @@ __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A
       const int ii = i0 + rr, j = j0 + jj;
       float p1 = 0.f, p2 = 0.f, p3 = 0.f;
       if (ii < n && j < n && j != ii) {
-        const double av = A[(size_t)ii * n + j];
-        const float ah = __double2float_rn(av);
-        const float al = __double2float_rn(av - (double)ah);
+        const ff a = split_nonneg(A[(size_t)ii * n + j]);   // integer split, no float64 ops
+        const float ah = a.hi, al = a.lo;
         if (ah > 0.f) {
           // sqrt(ah + al) = sh + sl with sl = (ah - sh^2 + al) / (2 sh)
           const float sh = __fsqrt_rn(ah);

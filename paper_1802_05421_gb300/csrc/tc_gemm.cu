@@ -61,6 +61,7 @@ struct TcParams {
   const unsigned* amax;
   int level;
   void* out16;
+  int debug_withhold_load;   // test hook: never issue the first A load (its wait must expire)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_TILE;
         mbar_expect_tx(full_bar(s), A_TILE + b_bytes);
-        tma_load_2d(a_dst, &tmA, k0 + kb * BKE, a_row, full_bar(s));
+        if (!(p.debug_withhold_load && it == 0)) tma_load_2d(a_dst, &tmA, k0 + kb * BKE, a_row, full_bar(s));
         tma_load_2d(b_dst, &tmB, k0 + kb * BKE, b_row, full_bar(s));
       }
     }
@@ -582,6 +583,7 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   p.amax = ch->amax;
   p.level = level;
   p.out16 = fp8 ? ch->level16(level + 1) : nullptr;
+  p.debug_withhold_load = ctx->debug_flags & 1;
   const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
   return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8);
 }
@@ -617,6 +619,7 @@ int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float*
   p.amax = nullptr;
   p.level = 0;
   p.out16 = nullptr;
+  p.debug_withhold_load = 0;
   const double bytes = 2.0 * np * (double)np;
   return launch(ctx, ma, mbm, p, CDL_KC_APPLY, bytes);
 }

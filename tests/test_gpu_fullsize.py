@@ -1,0 +1,114 @@
+"""Full-size parity on the n = 32768 field pair the benchmark times (bf16
+chain, d = 14, k = 128, refinement to 1e-10, float32 scores), called through
+the same C entry points and kernels as cdl_caddelag_pair.
+
+The oracle computes everything it compares from the node series alone:
+exact squared distances (exact-grid Gram, bit-equal to the plain definition
+on grid inputs), sigma, the full float64 graphs, the full projection (plain C
+oracle), the exact embeddings by dense Cholesky and the node scores of sampled
+rows plus the GPU's top anomalies. Checked: sigma bit-exact; sampled rows of
+A, D and Y; the float64 residual of the GPU's Z; Z against the exact
+embedding; node scores on the sampled rows; the top-10 order and its
+validity on the sample; the planted patch on top. Takes a few minutes of
+host time."""
+import gc
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import caddelag as O            # noqa: E402
+from workloads import field_sequence        # noqa: E402
+
+pytestmark = [pytest.mark.gpu, pytest.mark.fullsize]
+
+K, DCH, SEED, TOPK, TOL = 128, 14, 2024, 10, 1e-10
+
+
+def test_field_pair_n32768_full_size():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import Ctx, lib
+    G = Ctx(lib())
+    cdl = G.cdl
+    wl = field_sequence(128, 256, 256, 2, patch=8, patch_transition=0, seed=2)
+    n = wl.X[0].shape[0]
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.choice(n, 24, replace=False), wl.planted[0][:4]]))
+    gpu = []
+    try:
+        for X in wl.X:
+            A, D, vol, sig = G.graph(X)
+            ch = G.chain(A, D, vol, DCH, cdl.CDL_BF16)
+            try:
+                Y = G.project(A, K, SEED)
+                Z, st = G.solve(ch, A, Y, max_iter=40, rel_tol=TOL)
+            finally:
+                cdl.cdl_chain_free(ch)
+            gpu.append(dict(A=A, D=D.cpu().numpy(), vol=float(vol.item()), sig=float(sig.item()),
+                            Y=Y.cpu().numpy(), Z=Z.cpu().numpy(), Arows=A[rows].cpu().numpy(),
+                            rel=st.rel_res))
+        F, top = G.score(gpu[0]["A"], gpu[1]["A"], torch.from_numpy(gpu[0]["Z"]).cuda(),
+                         torch.from_numpy(gpu[1]["Z"]).cuda(),
+                         torch.tensor([gpu[0]["vol"]], dtype=torch.float64, device="cuda"),
+                         torch.tensor([gpu[1]["vol"]], dtype=torch.float64, device="cuda"), TOPK, cdl.CDL_F32)
+        F = F.cpu().numpy()
+        top = top.cpu().numpy()
+        # the pair driver runs the same kernels: identical scores
+        Fp, topp, s1, s2 = G.pair(wl.X[0], wl.X[1], K, DCH, cdl.CDL_BF16, cdl.CDL_F32, SEED, TOPK,
+                                  max_iter=40, rel_tol=TOL)
+        assert np.array_equal(Fp, F) and list(topp) == list(top)
+        for g in gpu:
+            del g["A"]
+        torch.cuda.empty_cache()
+    finally:
+        G.close()
+
+    oracle = []
+    for g, X in zip(gpu, wl.X):
+        d2 = O.squared_distances_exact_grid(X)
+        sig = O.median_sigma(d2)
+        assert sig == g["sig"]                                    # exact selection
+        two_s2 = 2.0 * (sig * sig)
+        np.divide(d2, -two_s2, out=d2)
+        A = np.exp(d2, out=d2)                                    # A_ij = exp(-d2 / (2 sigma^2))
+        np.fill_diagonal(A, 0.0)
+        D = A.sum(axis=1)
+        vol = float(D.sum())
+        np.testing.assert_allclose(g["Arows"], A[rows], rtol=2e-14, atol=0)
+        np.testing.assert_allclose(g["D"], D, rtol=1e-13)
+        assert math.isclose(g["vol"], vol, rel_tol=1e-13)
+        Yo = O.project_rows_c(A, range(n), SEED, K)
+        assert np.abs(g["Y"] - Yo).max() <= 1e-12 * np.abs(Yo).max()
+        # float64 residual of the GPU's solution, against the oracle's graph
+        R = Yo - (D[:, None] * g["Z"] - A @ g["Z"])
+        assert np.linalg.norm(R) <= 3 * TOL * np.linalg.norm(Yo)
+        Arows = A[rows].copy()
+        # exact embedding: Cholesky of L + (vol / n^2) 1 1^T, in place
+        np.negative(A, out=A)
+        A[np.diag_indices(n)] = D
+        A += vol / (n * n)
+        import scipy.linalg
+        c = scipy.linalg.cho_factor(A, lower=False, overwrite_a=True, check_finite=False)
+        Zo = O.dweighted_center(scipy.linalg.cho_solve(c, Yo, check_finite=False), D)
+        del A, c, d2
+        gc.collect()
+        assert np.linalg.norm(g["Z"] - Zo) <= 1e-6 * np.linalg.norm(Zo)
+        oracle.append(dict(Z=Zo, vol=vol, sig=sig))
+    # node scores: sampled rows and the GPU's top anomalies
+    chk = np.unique(np.concatenate([rows, top]))
+    A1r = O.graph_rows(wl.X[0], oracle[0]["sig"], chk)
+    A2r = O.graph_rows(wl.X[1], oracle[1]["sig"], chk)
+    Fo = O.node_scores(A1r, A2r, oracle[0]["Z"], oracle[1]["Z"], oracle[0]["vol"], oracle[1]["vol"], rows=chk)
+    rel = np.abs(F[chk] - Fo) / Fo
+    assert rel.max() <= 1e-6, rel.max()
+    fo = dict(zip(chk.tolist(), Fo.tolist()))
+    top_vals = [fo[int(i)] for i in top]
+    for t in range(TOPK - 1):              # oracle agrees on the order wherever it is decided
+        if abs(top_vals[t] - top_vals[t + 1]) > 1e-5 * max(top_vals[t], top_vals[t + 1]):
+            assert top_vals[t] > top_vals[t + 1]
+    others = [fo[int(i)] for i in chk if int(i) not in set(top.tolist())]
+    assert max(others) < top_vals[-1]                                      # valid on the sample
+    assert len(set(top.tolist()) & set(wl.planted[0].tolist())) >= 8       # the planted patch

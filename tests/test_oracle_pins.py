@@ -249,6 +249,16 @@ def test_project_matches_incidence_form():
         assert np.allclose(O.project(A, 2024, k), O.project_explicit(A, Q), rtol=1e-13, atol=1e-14)
 
 
+def test_c_projection_matches_numpy_and_incidence_form():
+    X = iid_pair(150, 8, 2, 12).X[0]
+    A, *_ = O.gaussian_graph(X)
+    for k, seed in ((7, 3), (128, 2 ** 33 + 5), (200, 11)):
+        Yc = O.project_rows_c(A, range(150), seed, k)
+        assert np.allclose(Yc, O.project(A, seed, k), rtol=1e-13, atol=1e-13)
+        assert np.allclose(Yc, O.project_explicit(A, O.projection_matrix(150, seed, k)), rtol=1e-12, atol=1e-13)
+    assert np.allclose(O.project_rows_c(A[[5, 90]], [5, 90], 4, 16), O.project(A, 4, 16)[[5, 90]], rtol=1e-13)
+
+
 def test_project_columns_sum_to_zero_and_rows():
     A = _random_graph(50, 12)
     Y = O.project(A, 5, 16)
