@@ -208,6 +208,9 @@ int cdl_chain_level_scale(const cdl_chain* chain, int32_t i, double* scale);
  * s_r(i, j) = +1 if bit (r mod 32) of word ((r mod 128) / 32) of
  * Philox4x32-10(counter = (i, j, r / 128, 0), key = (seed & 0xffffffff,
  * seed >> 32)) is set, else -1.
+ * The exact Y has zero column sums (B^T 1 = 0); the computed columns have
+ * their means subtracted, which removes the rounding residue of the row sums
+ * (a component in the null space of L that no solve could match).
  * A: device n x n (a_dtype = CDL_F64). Y: device n x k float64 output.
  * Requires 1 <= k <= 1024. */
 int cdl_project(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, int64_t n, int32_t k,
@@ -268,8 +271,12 @@ int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* chain, const void* A, cdl_dty
  * a = sqrt(vol2) Z2 - sqrt(vol1) Z1 and b = sqrt(vol2) Z2 + sqrt(vol1) Z1,
  * which avoids cancelling two large commute times.
  * score_dtype: CDL_F64 forms the k-term products and sums in float64;
- *   CDL_F32 forms them in float32 from float-float a and b (about 1e-7
- *   relative per pair, much faster on this GPU). Scores accumulate in float64.
+ *   CDL_F32 forms them on the float32 pipes (much faster on this GPU):
+ *   a and b split per column into hi + lo with hi on a fixed grid (23 bits
+ *   of the column maximum, so hi_i - hi_j is exact), products made exact by
+ *   fused multiply-add and the k-term sum compensated (TwoSum); each
+ *   difference c_2 - c_1 is within about 2^-44 sum_r |a_ir - a_jr||b_ir -
+ *   b_jr| even where the k terms cancel. Scores accumulate in float64.
  * A1, A2: device n x n (CDL_F64). Z1, Z2: device n x k float64.
  * vol1, vol2: device, one float64 each. F: device n float64 output.
  * top_idx: device topk int64 output (may be NULL when topk == 0).
@@ -306,6 +313,51 @@ typedef struct {
 int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T,
                       const cdl_pair_opts* opts, double* F, int64_t* top_idx,
                       cdl_solve_stats* stats1, cdl_solve_stats* stats2);
+
+/* ---------------------------------------------------------------- batched form */
+
+typedef struct {
+  int32_t k;               /* projection dimension, 1..128                  */
+  int32_t d;               /* chain length (levels), 1..64                  */
+  cdl_dtype chain_dtype;   /* CDL_BF16 (tensor-core chain)                  */
+  cdl_dtype score_dtype;   /* CDL_F64 or CDL_F32 (see cdl_cad_score)        */
+  uint64_t seed;           /* projection seed, shared by every graph        */
+  double sigma;            /* <= 0: median rule per graph                   */
+  cdl_solve_opts solve;    /* per graph (see cdl_caddelag_batched)          */
+  int32_t topk;            /* per pair; <= the smallest n                   */
+  int32_t host_io;         /* 1: X1, X2, F, top_idx are host pointers       */
+  int32_t use_graph;       /* 1: record the whole batch as a CUDA graph on
+                              the first call and replay it on later calls
+                              with the same sizes and options              */
+} cdl_batch_opts;
+
+/* G independent graph pairs of uneven order, end to end (Alg. 4 for each
+ * pair), run together: per step, one launch covers every graph of the batch
+ * (one grouped tcgen05 launch per chain level, one grouped launch per
+ * refinement kernel, one grouped launch per scoring kernel). Each pair's
+ * results equal what cdl_caddelag_pair computes for it up to the rounding
+ * order of the chain apply (no split-K here).
+ * n: host array of G orders, 2 <= n[p] <= 32768, sum <= 2^26.
+ * X1, X2: (sum n) x T float64, row-major; pair p's nodes are rows
+ *   off_p .. off_p + n[p] - 1 with off_p = n[0] + ... + n[p-1].
+ * F: sum n float64 output at the same offsets. top_idx: G x topk int64
+ *   output (pair-major; node indices within the pair).
+ * stats: host array of 2G entries (graph 2p is pair p's first graph, 2p+1
+ *   its second) or NULL.
+ * Refinement: each graph follows the rules of cdl_chain_solve, decided on
+ * the device; the host issues max_iter + 4 step slots (max_iter with
+ * CDL_SOLVE_FULL_RESIDUAL), where a slot is one application of the
+ * preconditioner or one float-float certification of a recursively updated
+ * residual; a graph that has stopped skips the remaining slots.
+ * Device buffers of the batch (graphs, chains, embeddings; about
+ * sum over graphs of (d + 2) 2 npad^2 + 16 n^2 bytes, npad = n rounded up to
+ * 256) are owned by the context and kept for the next call with the same
+ * sizes and options. The call returns after the results are written (it
+ * synchronises); it returns CDL_ERR_NOT_CONVERGED (results still written)
+ * when any solve missed its tolerance, CDL_ERR_UNSUPPORTED without tcgen05. */
+int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, int32_t T, const double* X1,
+                         const double* X2, const cdl_batch_opts* opts, double* F, int64_t* top_idx,
+                         cdl_solve_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,13 @@ class cdl_pair_opts(ctypes.Structure):
                 ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32)]
 
 
+class cdl_batch_opts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("d", ctypes.c_int32), ("chain_dtype", ctypes.c_int),
+                ("score_dtype", ctypes.c_int), ("seed", ctypes.c_uint64), ("sigma", ctypes.c_double),
+                ("solve", cdl_solve_opts), ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libcdl.so not built at {LIB_PATH}; run python -m paper_1802_05421_gb300.build")
 _lib = ctypes.CDLL(LIB_PATH)
@@ -78,6 +85,7 @@ _SIGS = {
     "cdl_cad_score": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _I32, _P, _P],
     "cdl_caddelag_pair": [_P, _P, _P, _I64, _I32, ctypes.POINTER(cdl_pair_opts), _P, _P,
                           ctypes.POINTER(cdl_solve_stats), ctypes.POINTER(cdl_solve_stats)],
+    "cdl_caddelag_batched": [_P, _I32, _P, _I32, _P, _P, ctypes.POINTER(cdl_batch_opts), _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -215,6 +223,13 @@ def cdl_caddelag_pair(ctx, X1, X2, n, T, opts: cdl_pair_opts, F, top_idx, stats1
                                   _ptr(top_idx),
                                   ctypes.byref(stats1) if stats1 is not None else None,
                                   ctypes.byref(stats2) if stats2 is not None else None)
+
+
+def cdl_caddelag_batched(ctx, G, n, T, X1, X2, opts: cdl_batch_opts, F, top_idx, stats=None) -> int:
+    """n: int64 array of G orders (NumPy); stats: a ctypes array of 2G
+    cdl_solve_stats or None."""
+    return _lib.cdl_caddelag_batched(ctx, G, _ptr(n), T, _ptr(X1), _ptr(X2), ctypes.byref(opts), _ptr(F),
+                                     _ptr(top_idx), ctypes.cast(stats, _P) if stats is not None else None)
 
 
 def exported_symbols():

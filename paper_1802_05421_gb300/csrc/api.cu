@@ -115,6 +115,23 @@ static int dev_ptr(const cdl_ctx* ctx, const void* p, size_t align = 8) {
   return check_aligned(p, align);
 }
 
+int check_dev_ptr(const cdl_ctx* ctx, const void* p, size_t align) { return dev_ptr(ctx, p, align); }
+
+int ctx_absorb(cdl_ctx* dst, cdl_ctx* src) {
+  CDL_TRY(fold_timing(src));
+  dst->launches += src->launches;
+  src->launches = 0;
+  for (int i = 0; i < CDL_KC_COUNT; ++i) {
+    dst->kc_ms[i] += src->kc_ms[i];
+    dst->kc_launches[i] += src->kc_launches[i];
+    dst->kc_work[i] += src->kc_work[i];
+    src->kc_ms[i] = 0;
+    src->kc_launches[i] = 0;
+    src->kc_work[i] = 0;
+  }
+  return CDL_OK;
+}
+
 static int set_device(cdl_ctx* ctx) {
   CDL_CUDA_TRY(cudaSetDevice(ctx->device));
   return CDL_OK;
@@ -172,6 +189,7 @@ int cdl_ctx_destroy(cdl_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pair_chain) cdl_chain_free(ctx->pair_chain);
+  if (ctx->batch) batch_plan_free(ctx->batch);
   for (auto& kv : ctx->ws) cudaFree(kv.second.first);
   for (auto& ev : ctx->pending) {
     cudaEventDestroy(ev.a);

@@ -1,6 +1,7 @@
 // Library-internal declarations shared by the translation units of libcdl.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -41,6 +42,11 @@ struct Event2 {
 
 }  // namespace cdl
 
+namespace cdl {
+struct BatchPlan;
+void batch_plan_free(BatchPlan* p);
+}  // namespace cdl
+
 struct cdl_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -64,6 +70,7 @@ struct cdl_ctx {
   // tile schedules uploaded to the workspace, by workspace name -> tile count
   std::map<std::string, int> tile_lists;
   int debug_flags = 0;   // CDL_DEBUG_* test hooks
+  cdl::BatchPlan* batch = nullptr;   // plan of the last cdl_caddelag_batched call
 };
 
 struct cdl_chain {
@@ -96,6 +103,12 @@ namespace cdl {
 // reusing or growing it (respecting ctx->ws_cap).
 int ws_get(cdl_ctx* ctx, const char* name, size_t bytes, void** out);
 
+// Folds src's pending timings and adds its launch counters into dst, then
+// zeroes src's counters.
+int ctx_absorb(cdl_ctx* dst, cdl_ctx* src);
+// CDL_OK if p is device (or managed) memory of ctx's device, aligned to `align`.
+int check_dev_ptr(const cdl_ctx* ctx, const void* p, size_t align);
+
 // Launch accounting: call before and after each kernel launch.
 struct Launch {
   cdl_ctx* ctx;
@@ -122,11 +135,115 @@ int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void
                int k, int splits);
 // tc_gemm.cu
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
+// Grouped (batched) tcgen05 launches: one launch over the tiles of many
+// graphs. Each graph's tensor maps, output and k-loop length sit in a device
+// array of TcGroup; `host_first` is the host copy of entry 0.
+struct TcGroup {
+  CUtensorMap mapA;    // A operand (128-row boxes)
+  CUtensorMap mapB;    // B operand
+  void* out;           // squaring: bf16 level; apply: float npad x 2kp
+  const int* gate;     // apply: tiles run iff *gate & gate_mask (null: always)
+  int npad;
+  int kblocks;
+  int pad[10];
+};
+static_assert(sizeof(TcGroup) % 64 == 0, "TcGroup keeps its tensor maps 64-byte aligned in arrays");
+int tc_group_square(TcGroup* g, const void* level, void* out, int np);
+int tc_group_apply(TcGroup* g, const void* amat, const void* xop, float* out, int np, int kp, const int* gate);
+std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad);
+std::vector<uint32_t> tc_grouped_apply_tiles(const std::vector<int>& npad);
+int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
+                      int ntiles, double flops);
+int tc_apply_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
+                     int ntiles, int kp, int gate_mask, int kc, double work);
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial,
              int k, int splits);
 int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp,
                  int splits);
 bool tc_supported(cdl_ctx* ctx);
+// ---- batched form (one launch per step over many graphs) ----
+// Solve commands, per graph, set by the decision kernel after each step.
+enum { CMD_STEP = 1, CMD_FULL = 2, CMD_RECUR = 4 };
+
+// Buffers of one graph of a batch (device pointers; n x k row-major blocks,
+// npad-padded operands as in the single-graph solve).
+struct BGraph {
+  int n, np;
+  int res_tiles;    // 64 x 64 float-float residual tiles
+  int elem_blocks;  // 256-element blocks of n x k
+  const double* D;
+  const double* rsd;
+  const double* vol;
+  const float* ahi;
+  const float* alo;
+  const double* Y;
+  double* Z;
+  double* R;
+  float* x;
+  void* xop;        // bf16 2kp x npad
+  float* part;      // npad x 2kp
+  float* part2;
+  float* dz;        // npad x kp
+  void* dzop;       // bf16 2kp x npad
+  float* zh;
+  float* zl;
+  double* red;      // max(res_tiles, elem_blocks)
+  double* cs;       // ceil(n / 256) x k
+};
+
+// Refinement state of one graph, on the device.
+struct BState {
+  int cmd;
+  int iters;
+  int exact;
+  int pad;
+  double yy, rel, drift;
+  double hist[64];
+};
+
+// A device tile table: entries (b << 12) | g, or a kernel-specific packing.
+struct BTiles {
+  const uint32_t* p = nullptr;
+  int count = 0;
+};
+
+struct BatchSolve {
+  int G2 = 0, k = 0, kp = 0, d = 0, slots = 0, max_iter = 0;
+  double rel_tol = 0;
+  bool always_full = false;
+  const BGraph* gs = nullptr;
+  BState* st = nullptr;
+  BTiles t32, elem, res, cs, apply;
+  const TcGroup* lvl_groups = nullptr;   // device, d arrays of G2 (level-major)
+  const TcGroup* lvl_first = nullptr;    // host, entry 0 of each level array
+  const TcGroup* res_groups = nullptr;   // device, A_hi then A_lo arrays of G2
+  const TcGroup* res_first = nullptr;    // host, 2 entries
+  double apply_bytes = 0;                // per grouped level apply
+};
+int batch_solve(cdl_ctx* ctx, const BatchSolve& b);
+
+// One pair of a batch for the grouped scoring launches.
+struct ScoreJob {
+  const double* A1;
+  const double* A2;
+  const double* Z1;
+  const double* Z2;
+  const double* vol1;
+  const double* vol2;
+  void* ab;         // 16 n k bytes
+  double* contrib;  // ceil(n / 64) x n
+  double* F;
+  int64_t* top;
+  unsigned* cmax;   // 2k column bounds (float32 scoring)
+  int n;
+  int pad;
+};
+// elem: (b << 12) | p over n k / 256 blocks; pairs: p | bi << 12 | bj << 22
+// (64-node blocks, bi <= bj); nodes: (b << 12) | p over n / 256 blocks.
+// cmax_all: the G x 2k column bounds the jobs point into (one block).
+int cad_score_grouped(cdl_ctx* ctx, const ScoreJob* jobs, int G, int k, bool fp64, int topk, BTiles elem,
+                      BTiles pairs, BTiles nodes, double bytes, unsigned* cmax_all);
+
 // solve.cu
 int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
                 const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats);

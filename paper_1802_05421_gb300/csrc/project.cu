@@ -152,6 +152,41 @@ __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A
   }
 }
 
+// Column sums of Y over 256-row chunks (fixed order): part[b][r].
+__global__ void __launch_bounds__(256) k_colsum(const double* __restrict__ Y, int n, int k,
+                                                 double* __restrict__ part) {
+  __shared__ double sh[8][33];
+  const int b = blockIdx.x, i0 = b * 256, i1 = min(n, i0 + 256);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < k; r0 += 32) {
+    const int r = r0 + tx;
+    double acc = 0.0;
+    if (r < k)
+      for (int i = i0 + ty; i < i1; i += 8) acc += Y[(size_t)i * k + r];
+    sh[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && r < k) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += sh[q][tx];
+      part[(size_t)b * k + r] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Y -= column mean. The exact Y has zero column sums (each edge adds +x to
+// its head's row and -x to its tail's); the float sums of the two rows round
+// differently, and that residue lies in the null space of L, where no
+// solution Z can match it.
+__global__ void k_sub_mean(double* __restrict__ Y, int n, int k, const double* __restrict__ part, int nparts) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  const int r = (int)(idx % k);
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += part[(size_t)q * k + r];
+  Y[idx] -= s / n;
+}
+
 }  // namespace
 
 int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, double* Y) {
@@ -172,7 +207,19 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
   Launch L(ctx, CDL_KC_PROJECT, (double)n * (n - 1) * k);
   k_project<<<blocks, threads, smem, ctx->stream>>>(A, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
                                                     (uint32_t)(seed >> 32), scale, Y);
-  return L.done();
+  CDL_TRY(L.done());
+  const int nparts = (n + 255) / 256;
+  void* vpart;
+  CDL_TRY(ws_get(ctx, "project.colsum", (size_t)nparts * k * sizeof(double), &vpart));
+  {
+    Launch L2(ctx, CDL_KC_MISC, 0);
+    k_colsum<<<nparts, 256, 0, ctx->stream>>>(Y, n, k, static_cast<double*>(vpart));
+    CDL_TRY(L2.done());
+  }
+  Launch L3(ctx, CDL_KC_MISC, 0);
+  k_sub_mean<<<(unsigned)(((size_t)n * k + 255) / 256), 256, 0, ctx->stream>>>(Y, n, k,
+                                                                               static_cast<const double*>(vpart), nparts);
+  return L3.done();
 }
 
 }  // namespace cdl

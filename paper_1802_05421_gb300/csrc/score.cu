@@ -3,7 +3,14 @@
 //   c_t(i,j) = vol_t ||Z_t[i,:] - Z_t[j,:]||^2.
 // The commute-time difference is formed without cancelling the two commute
 // times: with a = sqrt(vol2) Z2 - sqrt(vol1) Z1 and b = sqrt(vol2) Z2 +
-// sqrt(vol1) Z1 (float64, then float hi + lo), c2 - c1 = (a_i - a_j).(b_i - b_j).
+// sqrt(vol1) Z1, c2 - c1 = (a_i - a_j).(b_i - b_j). The k-term sum itself
+// still cancels (its terms have both signs), so the float32 variant keeps
+// every term to about 2^-45 of its column's scale: a and b are split on a
+// per-column fixed grid into hi + lo, with hi on a grid fine enough for 23
+// bits of the column maximum, so that hi_i - hi_j is exact in float32;
+// products are made exact with a fused multiply-add and the sum is
+// compensated (TwoSum, Knuth), as in the doubled-precision dot product of
+// Ogita, Rump and Oishi (2005).
 // Each unordered pair (i < j) is visited once in 64 x 64 upper-triangle
 // tiles; the two row contributions of a tile go to a per-(partner block, node)
 // slot, and F is the fixed-order sum of those slots (deterministic).
@@ -19,30 +26,69 @@ namespace {
 constexpr int ST = 64;   // pair tile
 constexpr int RC = 8;    // projection rows per smem chunk
 
+// Column maxima of |a| and |b| (cmax[r], cmax[k + r]; float bits, rounded up
+// by 2^-20 so that they bound the float64 values).
+__device__ __forceinline__ void score_colmax(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                                             const double* __restrict__ vol1, const double* __restrict__ vol2,
+                                             int n, int k, unsigned* __restrict__ cmax, size_t idx) {
+  if (idx >= (size_t)n * k) return;
+  const int r = (int)(idx % k);
+  const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
+  const double w = s2 * Z2[idx], v = s1 * Z1[idx];
+  const float fa = (float)(fabs(w - v) * (1.0 + 0x1p-20)), fb = (float)(fabs(w + v) * (1.0 + 0x1p-20));
+  atomicMax(cmax + r, __float_as_uint(fa));        // non-negative floats order as their bits
+  atomicMax(cmax + k + r, __float_as_uint(fb));
+}
+
+// x = hi + lo with hi on the grid q = 2^(e - 21), 2^e <= M < 2^(e+1) the
+// column bound: |hi| / q <= 2^22 + 1, so differences of two hi values are
+// exact in float32; lo = x - hi (|lo| <= q / 2) rounded to float32.
+__device__ __forceinline__ void grid_split(double x, unsigned mbits, float& hi, float& lo) {
+  const int e = (int)((mbits >> 23) & 0xFF) - 127;
+  if (e < -90) {   // column of (near) zeros
+    hi = (float)x;
+    lo = 0.f;
+    return;
+  }
+  const double q = ldexp(1.0, e - 21);
+  const double h = rint(x / q) * q;
+  hi = (float)h;
+  lo = (float)(x - h);
+}
+
 // aT/bT hi/lo, stored transposed (k x n) for coalesced tile loads.
-__global__ void k_score_prep(const double* __restrict__ Z1, const double* __restrict__ Z2,
-                             const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
-                             float* __restrict__ ah, float* __restrict__ al, float* __restrict__ bh,
-                             float* __restrict__ bl) {
-  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void score_prep(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                                           const double* __restrict__ vol1, const double* __restrict__ vol2, int n,
+                                           int k, const unsigned* __restrict__ cmax, float* __restrict__ ah,
+                                           float* __restrict__ al, float* __restrict__ bh, float* __restrict__ bl,
+                                           size_t idx) {
   if (idx >= (size_t)n * k) return;
   const int i = (int)(idx / k), r = (int)(idx % k);
   const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
   const double w = s2 * Z2[idx], v = s1 * Z1[idx];
-  const double a = w - v, b = w + v;
-  const float a0 = (float)a, b0 = (float)b;
   const size_t o = (size_t)r * n + i;
-  ah[o] = a0;
-  al[o] = (float)(a - (double)a0);
-  bh[o] = b0;
-  bl[o] = (float)(b - (double)b0);
+  grid_split(w - v, cmax[r], ah[o], al[o]);
+  grid_split(w + v, cmax[k + r], bh[o], bl[o]);
+}
+
+__global__ void k_score_colmax(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                               const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
+                               unsigned* __restrict__ cmax) {
+  score_colmax(Z1, Z2, vol1, vol2, n, k, cmax, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
+}
+
+__global__ void k_score_prep(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                             const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
+                             const unsigned* __restrict__ cmax, float* __restrict__ ah, float* __restrict__ al,
+                             float* __restrict__ bh, float* __restrict__ bl) {
+  score_prep(Z1, Z2, vol1, vol2, n, k, cmax, ah, al, bh, bl, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
 }
 
 // float64 variant: aT, bT (k x n).
-__global__ void k_score_prep64(const double* __restrict__ Z1, const double* __restrict__ Z2,
-                               const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
-                               double* __restrict__ aT, double* __restrict__ bT) {
-  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void score_prep64(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                                             const double* __restrict__ vol1, const double* __restrict__ vol2,
+                                             int n, int k, double* __restrict__ aT, double* __restrict__ bT,
+                                             size_t idx) {
   if (idx >= (size_t)n * k) return;
   const int i = (int)(idx / k), r = (int)(idx % k);
   const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
@@ -50,6 +96,12 @@ __global__ void k_score_prep64(const double* __restrict__ Z1, const double* __re
   const size_t o = (size_t)r * n + i;
   aT[o] = w - v;
   bT[o] = w + v;
+}
+
+__global__ void k_score_prep64(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                               const double* __restrict__ vol1, const double* __restrict__ vol2, int n, int k,
+                               double* __restrict__ aT, double* __restrict__ bT) {
+  score_prep64(Z1, Z2, vol1, vol2, n, k, aT, bT, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
@@ -106,24 +158,21 @@ __device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const
   }
 }
 
-__global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ A1, const double* __restrict__ A2,
-                                                      const float* __restrict__ ah, const float* __restrict__ al,
-                                                      const float* __restrict__ bh, const float* __restrict__ bl,
-                                                      int n, int k, double* __restrict__ contrib) {
+__device__ __forceinline__ void score_tile(const double* __restrict__ A1, const double* __restrict__ A2,
+                                           const float* __restrict__ ah, const float* __restrict__ al,
+                                           const float* __restrict__ bh, const float* __restrict__ bl, int n, int k,
+                                           double* __restrict__ contrib, int bi, int bj) {
   __shared__ __align__(16) float sI[4][RC][ST];   // ah, al, bh, bl of the row block
   __shared__ __align__(16) float sJ[4][RC][ST];   // ... of the column block
   __shared__ double rsum[ST][17];
   __shared__ double csum[ST][17];
-  const int nb = (n + ST - 1) / ST;
-  int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
   const int i0 = bi * ST, j0 = bj * ST;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4];
+  float acc[4][4], cmp[4][4];   // compensated sum: acc + cmp
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int v = 0; v < 4; ++v) acc[u][v] = cmp[u][v] = 0.f;
   const float* src[4] = {ah, al, bh, bl};
   for (int r0 = 0; r0 < k; r0 += RC) {
     for (int e = tid; e < RC * ST; e += 256) {
@@ -154,9 +203,19 @@ __global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ 
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const float da = __fadd_rn(__fsub_rn(Iah[u], Jah[v]), __fsub_rn(Ial[u], Jal[v]));
-          const float db = __fadd_rn(__fsub_rn(Ibh[u], Jbh[v]), __fsub_rn(Ibl[u], Jbl[v]));
-          acc[u][v] = __fmaf_rn(da, db, acc[u][v]);
+          const float dah = __fsub_rn(Iah[u], Jah[v]);   // exact (grid split)
+          const float dal = __fsub_rn(Ial[u], Jal[v]);
+          const float dbh = __fsub_rn(Ibh[u], Jbh[v]);   // exact
+          const float dbl = __fsub_rn(Ibl[u], Jbl[v]);
+          const float p = __fmul_rn(dah, dbh);
+          float x = __fmaf_rn(dah, dbh, -p);             // p + x = dah dbh exactly
+          x = __fmaf_rn(dah, dbl, x);
+          x = __fmaf_rn(dal, dbh, x);
+          const float t = __fadd_rn(acc[u][v], p);       // TwoSum(acc, p)
+          const float z = __fsub_rn(t, acc[u][v]);
+          const float err = __fadd_rn(__fsub_rn(acc[u][v], __fsub_rn(t, z)), __fsub_rn(p, z));
+          acc[u][v] = t;
+          cmp[u][v] = __fadd_rn(cmp[u][v], __fadd_rn(err, x));
         }
     }
     __syncthreads();
@@ -165,23 +224,28 @@ __global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ 
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) dc[u][v] = (double)acc[u][v];
+    for (int v = 0; v < 4; ++v) dc[u][v] = (double)acc[u][v] + (double)cmp[u][v];
   tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, dc, contrib, rsum, csum);
 }
 
+__global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ A1, const double* __restrict__ A2,
+                                                      const float* __restrict__ ah, const float* __restrict__ al,
+                                                      const float* __restrict__ bh, const float* __restrict__ bl,
+                                                      int n, int k, double* __restrict__ contrib) {
+  const int nb = (n + ST - 1) / ST;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  score_tile(A1, A2, ah, al, bh, bl, n, k, contrib, bi, bj);
+}
+
 // float64 variant: c2 - c1 = sum_r (a_ir - a_jr)(b_ir - b_jr) in float64.
-__global__ void __launch_bounds__(256) k_score_pairs64(const double* __restrict__ A1,
-                                                        const double* __restrict__ A2,
-                                                        const double* __restrict__ aT,
-                                                        const double* __restrict__ bT, int n, int k,
-                                                        double* __restrict__ contrib) {
+__device__ __forceinline__ void score_tile64(const double* __restrict__ A1, const double* __restrict__ A2,
+                                             const double* __restrict__ aT, const double* __restrict__ bT, int n,
+                                             int k, double* __restrict__ contrib, int bi, int bj) {
   __shared__ __align__(16) double sI[2][RC][ST];
   __shared__ __align__(16) double sJ[2][RC][ST];
   __shared__ double rsum[ST][17];
   __shared__ double csum[ST][17];
-  const int nb = (n + ST - 1) / ST;
-  int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
   const int i0 = bi * ST, j0 = bj * ST;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   double acc[4][4];
@@ -216,6 +280,17 @@ __global__ void __launch_bounds__(256) k_score_pairs64(const double* __restrict_
   tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, acc, contrib, rsum, csum);
 }
 
+__global__ void __launch_bounds__(256) k_score_pairs64(const double* __restrict__ A1,
+                                                        const double* __restrict__ A2,
+                                                        const double* __restrict__ aT,
+                                                        const double* __restrict__ bT, int n, int k,
+                                                        double* __restrict__ contrib) {
+  const int nb = (n + ST - 1) / ST;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  score_tile64(A1, A2, aT, bT, n, k, contrib, bi, bj);
+}
+
 
 __global__ void k_score_reduce(const double* __restrict__ contrib, int nb, int n, double* __restrict__ F) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -231,8 +306,8 @@ __device__ __forceinline__ bool better(double v, int i, double w, int j) {
   return v > w || (v == w && i < j);
 }
 
-__global__ void __launch_bounds__(1024) k_topk(const double* __restrict__ F, int n, int topk,
-                                                int64_t* __restrict__ out) {
+__device__ __forceinline__ void topk_block(const double* __restrict__ F, int n, int topk,
+                                           int64_t* __restrict__ out) {
   __shared__ double sv[32];
   __shared__ int si[32];
   double pv = INFINITY;
@@ -287,6 +362,69 @@ __global__ void __launch_bounds__(1024) k_topk(const double* __restrict__ F, int
   }
 }
 
+__global__ void __launch_bounds__(1024) k_topk(const double* __restrict__ F, int n, int topk,
+                                                int64_t* __restrict__ out) {
+  topk_block(F, n, topk, out);
+}
+
+// ---------------------------------------------------------------- batched form
+// One launch per scoring step over all pairs of a batch; a block finds its
+// pair (and block or tile) in a tile table.
+__global__ void k_b_score_colmax(const uint32_t* __restrict__ tiles, const ScoreJob* __restrict__ jobs, int k) {
+  const uint32_t t = tiles[blockIdx.x];
+  const ScoreJob& J = jobs[t & 0xFFFu];
+  score_colmax(J.Z1, J.Z2, J.vol1, J.vol2, J.n, k, J.cmax, (size_t)(t >> 12) * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_b_score_prep(const uint32_t* __restrict__ tiles, const ScoreJob* __restrict__ jobs, int k, int fp64) {
+  const uint32_t t = tiles[blockIdx.x];
+  const ScoreJob& J = jobs[t & 0xFFFu];
+  const size_t idx = (size_t)(t >> 12) * blockDim.x + threadIdx.x;
+  const size_t nk = (size_t)J.n * k;
+  if (fp64) {
+    double* aT = static_cast<double*>(J.ab);
+    score_prep64(J.Z1, J.Z2, J.vol1, J.vol2, J.n, k, aT, aT + nk, idx);
+  } else {
+    float* ah = static_cast<float*>(J.ab);
+    score_prep(J.Z1, J.Z2, J.vol1, J.vol2, J.n, k, J.cmax, ah, ah + nk, ah + 2 * nk, ah + 3 * nk, idx);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_b_score_pairs(const uint32_t* __restrict__ tiles,
+                                                        const ScoreJob* __restrict__ jobs, int k) {
+  const uint32_t t = tiles[blockIdx.x];
+  const ScoreJob& J = jobs[t & 0xFFFu];
+  const size_t nk = (size_t)J.n * k;
+  const float* ah = static_cast<const float*>(J.ab);
+  score_tile(J.A1, J.A2, ah, ah + nk, ah + 2 * nk, ah + 3 * nk, J.n, k, J.contrib, (int)((t >> 12) & 0x3FFu),
+             (int)(t >> 22));
+}
+
+__global__ void __launch_bounds__(256) k_b_score_pairs64(const uint32_t* __restrict__ tiles,
+                                                          const ScoreJob* __restrict__ jobs, int k) {
+  const uint32_t t = tiles[blockIdx.x];
+  const ScoreJob& J = jobs[t & 0xFFFu];
+  const size_t nk = (size_t)J.n * k;
+  const double* aT = static_cast<const double*>(J.ab);
+  score_tile64(J.A1, J.A2, aT, aT + nk, J.n, k, J.contrib, (int)((t >> 12) & 0x3FFu), (int)(t >> 22));
+}
+
+__global__ void k_b_score_reduce(const uint32_t* __restrict__ tiles, const ScoreJob* __restrict__ jobs) {
+  const uint32_t t = tiles[blockIdx.x];
+  const ScoreJob& J = jobs[t & 0xFFFu];
+  const int i = (int)(t >> 12) * blockDim.x + threadIdx.x;
+  if (i >= J.n) return;
+  const int nb = (J.n + ST - 1) / ST;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += J.contrib[(size_t)b * J.n + i];
+  J.F[i] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_b_topk(const ScoreJob* __restrict__ jobs, int topk) {
+  const ScoreJob& J = jobs[blockIdx.x];
+  topk_block(J.F, J.n, topk, J.top);
+}
+
 }  // namespace
 
 int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
@@ -316,9 +454,18 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
     float* al = ah + nk;
     float* bh = al + nk;
     float* bl = bh + nk;
+    void* vmax;
+    CDL_TRY(ws_get(ctx, "score.cmax", 2 * (size_t)k * sizeof(unsigned), &vmax));
+    unsigned* cmax = static_cast<unsigned*>(vmax);
+    CDL_CUDA_TRY(cudaMemsetAsync(cmax, 0, 2 * (size_t)k * sizeof(unsigned), st));
     {
       Launch L(ctx, CDL_KC_MISC, 0);
-      k_score_prep<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, ah, al, bh, bl);
+      k_score_colmax<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cmax);
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_score_prep<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cmax, ah, al, bh, bl);
       CDL_TRY(L.done());
     }
     Launch L(ctx, CDL_KC_SCORE, 8.0 * (double)n * (n - 1));
@@ -333,6 +480,41 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
   if (topk > 0) {
     Launch L(ctx, CDL_KC_TOPK, 0);
     k_topk<<<1, 1024, 0, st>>>(F, n, topk, top_idx);
+    CDL_TRY(L.done());
+  }
+  return CDL_OK;
+}
+
+int cad_score_grouped(cdl_ctx* ctx, const ScoreJob* jobs, int G, int k, bool fp64, int topk, BTiles elem,
+                      BTiles pairs, BTiles nodes, double bytes, unsigned* cmax_all) {
+  cudaStream_t st = ctx->stream;
+  if (!fp64) {
+    CDL_CUDA_TRY(cudaMemsetAsync(cmax_all, 0, (size_t)G * 2 * k * sizeof(unsigned), st));
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_b_score_colmax<<<elem.count, 256, 0, st>>>(elem.p, jobs, k);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_b_score_prep<<<elem.count, 256, 0, st>>>(elem.p, jobs, k, fp64 ? 1 : 0);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_SCORE, bytes);
+    if (fp64)
+      k_b_score_pairs64<<<pairs.count, 256, 0, st>>>(pairs.p, jobs, k);
+    else
+      k_b_score_pairs<<<pairs.count, 256, 0, st>>>(pairs.p, jobs, k);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_b_score_reduce<<<nodes.count, 256, 0, st>>>(nodes.p, jobs);
+    CDL_TRY(L.done());
+  }
+  if (topk > 0) {
+    Launch L(ctx, CDL_KC_TOPK, 0);
+    k_b_topk<<<G, 1024, 0, st>>>(jobs, topk);
     CDL_TRY(L.done());
   }
   return CDL_OK;

@@ -14,6 +14,7 @@
 
 #include <cmath>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace cdl {
@@ -183,15 +184,14 @@ constexpr int RB_M = 64, RB_N = 64, RB_K = 16;
 // R = Y - D o Z + A Z for a 64-row x 64-column tile, 4 x 4 float-float
 // accumulators per thread; A and Z arrive as float hi + lo planes. Per-block
 // sum of R^2.
-__global__ void __launch_bounds__(256) k_residual(const float* __restrict__ Ahi, const float* __restrict__ Alo,
-                                                   const float* __restrict__ Zh, const float* __restrict__ Zl,
-                                                   const double* __restrict__ Z, const double* __restrict__ Y,
-                                                   const double* __restrict__ D, int n, int k,
-                                                   double* __restrict__ R, double* __restrict__ part) {
+__device__ __forceinline__ double residual_tile(const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                                const float* __restrict__ Zh, const float* __restrict__ Zl,
+                                                const double* __restrict__ Z, const double* __restrict__ Y,
+                                                const double* __restrict__ D, int n, int k,
+                                                double* __restrict__ R, int i0, int c0) {
   __shared__ __align__(16) float Ah[RB_K][RB_M + 4], Al[RB_K][RB_M + 4];
   __shared__ __align__(16) float Bh[RB_K][RB_N], Bl[RB_K][RB_N];
   __shared__ double red[8];
-  const int i0 = blockIdx.x * RB_M, c0 = blockIdx.y * RB_N;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float sh[4][4], sc[4][4];
 #pragma unroll
@@ -233,6 +233,16 @@ __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ Ahi,
         for (int b = 0; b < 4; ++b) ff_mac(avh[a], avl[a], bvh[b], bvl[b], sh[a][b], sc[a][b]);
     }
     __syncthreads();
+    // renormalise (s, c) so that the compensation stays below ulp(s): its own
+    // rounding errors then stay at 2^-48 of the sum per step
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const ff r = two_sum(sh[a][b], sc[a][b]);
+        sh[a][b] = r.hi;
+        sc[a][b] = r.lo;
+      }
   }
   double sq = 0.0;
 #pragma unroll
@@ -255,11 +265,19 @@ __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ Ahi,
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
   if ((tid & 31) == 0) red[tid >> 5] = sq;
   __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
+  double t = 0.0;
+  if (tid == 0)
     for (int w = 0; w < 8; ++w) t += red[w];
-    part[blockIdx.y * gridDim.x + blockIdx.x] = t;
-  }
+  return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_residual(const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                                   const float* __restrict__ Zh, const float* __restrict__ Zl,
+                                                   const double* __restrict__ Z, const double* __restrict__ Y,
+                                                   const double* __restrict__ D, int n, int k,
+                                                   double* __restrict__ R, double* __restrict__ part) {
+  const double t = residual_tile(Ahi, Alo, Zh, Zl, Z, Y, D, n, k, R, blockIdx.x * RB_M, blockIdx.y * RB_N);
+  if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // Recursive residual update R -= D o dZ - A dZ for a 128-row x 128-column
@@ -339,10 +357,22 @@ __global__ void __launch_bounds__(256) k_residual_update(const double* __restric
   }
 }
 
+// The value of dZ the tensor-core products see: its bf16 hi + lo split.
+// The diagonal term D o dZ uses the same value, so that the update applies
+// one operator to one vector: were D o dZ taken at full float precision, the
+// common rounding of a column's constant part (which A, close to a multiple
+// of the all-ones matrix, sums n times) would leave a residual along D 1
+// that the deflated preconditioner cannot see, and the refinement would stall.
+__device__ __forceinline__ float bf16_pair_value(float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  return __bfloat162float(hi) + __bfloat162float(lo);
+}
+
 // Tensor-core residual update, second half: the products A_hi [dZ_hi|dZ_lo]
 // and A_lo [dZ_hi|dZ_lo] arrive as float32 split-K partials (bf16 operands:
 // about 16 significant bits of A and of dZ); R -= D o dZ - (sum of the four
-// products); per-block sums of the new R^2.
+// products) with dZ as the products see it; per-block sums of the new R^2.
 __global__ void __launch_bounds__(256) k_residual_update_tc(const float* __restrict__ pa, const float* __restrict__ pb,
                                                              int splits, int np, const float* __restrict__ dZ,
                                                              const double* __restrict__ D, int n, int k, int kp,
@@ -358,7 +388,7 @@ __global__ void __launch_bounds__(256) k_residual_update_tc(const float* __restr
       const size_t o = ((size_t)s * np + i) * (2 * kp);
       az += (double)pa[o + c] + (double)pa[o + kp + c] + (double)pb[o + c] + (double)pb[o + kp + c];
     }
-    const double r = R[idx] - (D[i] * (double)dZ[(size_t)i * kp + c] - az);
+    const double r = R[idx] - (D[i] * (double)bf16_pair_value(dZ[(size_t)i * kp + c]) - az);
     R[idx] = r;
     sq = fma(r, r, sq);
   }
@@ -371,6 +401,298 @@ __global__ void __launch_bounds__(256) k_residual_update_tc(const float* __restr
     for (int w = 0; w < 8; ++w) t += red[w];
     part[blockIdx.x] = t;
   }
+}
+
+
+// ---------------------------------------------------------------- batched form
+// The kernels below run one step of the refinement for every graph of a
+// batch in one launch; a block finds its graph and block index in a tile
+// table and returns at once when its graph's command does not include the
+// step (converged graphs cost one load per block).
+
+__device__ __forceinline__ void tdec(uint32_t t, int& g, int& b) {
+  g = (int)(t & 0xFFFu);
+  b = (int)(t >> 12);
+}
+
+// sum over a 256-thread block in a fixed order (result in thread 0)
+__device__ __forceinline__ double block_sum256(double v) {
+  __shared__ double sh[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) t += sh[w];
+  return t;
+}
+
+// R = Y, Z = 0, and per-block sums of Y^2.
+__global__ void __launch_bounds__(256) k_b_start(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                  int k) {
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  const BGraph& G = gs[g];
+  const size_t idx = (size_t)b * 256 + threadIdx.x;
+  double y2 = 0.0;
+  if (idx < (size_t)G.n * k) {
+    const double y = G.Y[idx];
+    G.R[idx] = y;
+    G.Z[idx] = 0.0;
+    y2 = y * y;
+  }
+  const double t = block_sum256(y2);
+  if (threadIdx.x == 0) G.red[b] = t;
+}
+
+// ||Y||^2 per graph and the first command (a step with a full residual).
+__global__ void __launch_bounds__(256) k_b_begin(const BGraph* __restrict__ gs, BState* __restrict__ st) {
+  const BGraph& G = gs[blockIdx.x];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < G.elem_blocks; b += 256) acc += G.red[b];
+  const double yy = block_sum256(acc);
+  if (threadIdx.x == 0) {
+    BState& s = st[blockIdx.x];
+    s.yy = yy;
+    s.iters = 0;
+    s.exact = 1;
+    s.drift = 0.0;
+    s.rel = yy > 0.0 ? 1.0 : 0.0;
+    for (int h = 0; h < 64; ++h) s.hist[h] = 0.0;
+    s.cmd = yy > 0.0 ? (CMD_STEP | CMD_FULL) : 0;
+  }
+}
+
+// bf16 hi/lo transposed operand of a 32-row block: op[r][i], op[kp + r][i].
+__device__ __forceinline__ void write_op_tile(float (*tile)[33], int i0, int r0, int kp, int np,
+                                              __nv_bfloat16* __restrict__ op) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int a = ty; a < 32; a += 8) {
+    const int r = r0 + a, i = i0 + tx;
+    if (r < kp) {
+      const float v = tile[tx][a];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      op[(size_t)r * np + i] = hi;
+      op[(size_t)(kp + r) * np + i] = lo;
+    }
+  }
+}
+
+// x = D^{-1/2} R (float, zero padded) and its bf16 operand.
+__global__ void __launch_bounds__(256) k_b_precond_in(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                       const BState* __restrict__ st, int k, int kp) {
+  __shared__ float tile[32][33];
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_STEP)) return;
+  const BGraph& G = gs[g];
+  const int i0 = b * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < kp; r0 += 32) {
+    for (int a = ty; a < 32; a += 8) {
+      const int i = i0 + a, r = r0 + tx;
+      const float v = (i < G.n && r < k) ? (float)(G.R[(size_t)i * k + r] * G.rsd[i]) : 0.f;
+      if (r < kp) G.x[(size_t)i * kp + r] = v;
+      tile[a][tx] = v;
+    }
+    __syncthreads();
+    write_op_tile(tile, i0, r0, kp, G.np, static_cast<__nv_bfloat16*>(G.xop));
+    __syncthreads();
+  }
+}
+
+// x += (I + S~) contribution of one level: x += part_hi + part_lo; new operand.
+__global__ void __launch_bounds__(256) k_b_update(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                   const BState* __restrict__ st, int kp) {
+  __shared__ float tile[32][33];
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_STEP)) return;
+  const BGraph& G = gs[g];
+  const int i0 = b * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < kp; r0 += 32) {
+    for (int a = ty; a < 32; a += 8) {
+      const int i = i0 + a, r = r0 + tx;
+      float v = 0.f;
+      if (r < kp) {
+        const float* P = G.part + (size_t)i * (2 * kp);
+        v = G.x[(size_t)i * kp + r];
+        v += P[r] + P[kp + r];
+        G.x[(size_t)i * kp + r] = v;
+      }
+      tile[a][tx] = v;
+    }
+    __syncthreads();
+    write_op_tile(tile, i0, r0, kp, G.np, static_cast<__nv_bfloat16*>(G.xop));
+    __syncthreads();
+  }
+}
+
+// Z += dZ = D^{-1/2} x; dZ kept in float (and as a bf16 operand when the
+// residual is updated recursively).
+__global__ void __launch_bounds__(256) k_b_precond_out(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                        const BState* __restrict__ st, int k, int kp) {
+  __shared__ float tile[32][33];
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  const int cmd = st[g].cmd;
+  if (!(cmd & CMD_STEP)) return;
+  const BGraph& G = gs[g];
+  const int i0 = b * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < kp; r0 += 32) {
+    for (int a = ty; a < 32; a += 8) {
+      const int i = i0 + a, r = r0 + tx;
+      float dzf = 0.f;
+      if (i < G.n && r < k) {
+        const double dz = (double)G.x[(size_t)i * kp + r] * G.rsd[i];
+        G.Z[(size_t)i * k + r] += dz;
+        dzf = (float)dz;
+      }
+      if (r < kp) G.dz[(size_t)i * kp + r] = dzf;
+      tile[a][tx] = dzf;
+    }
+    __syncthreads();
+    if (cmd & CMD_RECUR) write_op_tile(tile, i0, r0, kp, G.np, static_cast<__nv_bfloat16*>(G.dzop));
+    __syncthreads();
+  }
+}
+
+// Column sums of D o Z over 256-row chunks (fixed order).
+__global__ void __launch_bounds__(256) k_b_colsum(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                   const BState* __restrict__ st, int k) {
+  __shared__ double sh[8][33];
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_STEP)) return;
+  const BGraph& G = gs[g];
+  const int i0 = b * 256, i1 = min(G.n, i0 + 256);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < k; r0 += 32) {
+    const int r = r0 + tx;
+    double acc = 0.0;
+    if (r < k)
+      for (int i = i0 + ty; i < i1; i += 8) acc = fma(G.D[i], G.Z[(size_t)i * k + r], acc);
+    sh[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && r < k) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += sh[q][tx];
+      G.cs[(size_t)b * k + r] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// D-weighted centring: Z -= (sum_i D_i Z_i) / vol.
+__global__ void __launch_bounds__(256) k_b_center(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                   const BState* __restrict__ st, int k) {
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_STEP)) return;
+  const BGraph& G = gs[g];
+  const size_t idx = (size_t)b * 256 + threadIdx.x;
+  if (idx >= (size_t)G.n * k) return;
+  const int r = (int)(idx % k);
+  const int nparts = (G.n + 255) / 256;
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += G.cs[(size_t)q * k + r];
+  G.Z[idx] -= s / *G.vol;
+}
+
+// Z -> float hi + lo for the float-float residual.
+__global__ void __launch_bounds__(256) k_b_split(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                  const BState* __restrict__ st, int k) {
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_FULL)) return;
+  const BGraph& G = gs[g];
+  const size_t idx = (size_t)b * 256 + threadIdx.x;
+  if (idx >= (size_t)G.n * k) return;
+  const double z = G.Z[idx];
+  const float h = (float)z;
+  G.zh[idx] = h;
+  G.zl[idx] = (float)(z - (double)h);
+}
+
+// Full float-float residual R = Y - D o Z + A Z, one 64 x 64 tile per block.
+__global__ void __launch_bounds__(256) k_b_residual(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                     const BState* __restrict__ st, int k) {
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_FULL)) return;
+  const BGraph& G = gs[g];
+  const int ncb = (k + RB_N - 1) / RB_N;
+  const double t = residual_tile(G.ahi, G.alo, G.zh, G.zl, G.Z, G.Y, G.D, G.n, k, G.R, (b / ncb) * RB_M,
+                                 (b % ncb) * RB_N);
+  if (threadIdx.x == 0) G.red[b] = t;
+}
+
+// Recursive update R -= D o dZ - A dZ from the tensor-core products.
+__global__ void __launch_bounds__(256) k_b_residual_update(const uint32_t* __restrict__ tiles,
+                                                            const BGraph* __restrict__ gs,
+                                                            const BState* __restrict__ st, int k, int kp) {
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_RECUR)) return;
+  const BGraph& G = gs[g];
+  const size_t idx = (size_t)b * 256 + threadIdx.x;
+  double sq = 0.0;
+  if (idx < (size_t)G.n * k) {
+    const int i = (int)(idx / k), c = (int)(idx % k);
+    const size_t o = (size_t)i * (2 * kp);
+    double az = 0.0;
+    az += (double)G.part[o + c] + (double)G.part[o + kp + c] + (double)G.part2[o + c] + (double)G.part2[o + kp + c];
+    const double r = G.R[idx] - (G.D[i] * (double)bf16_pair_value(G.dz[(size_t)i * kp + c]) - az);
+    G.R[idx] = r;
+    sq = r * r;
+  }
+  const double t = block_sum256(sq);
+  if (threadIdx.x == 0) G.red[b] = t;
+}
+
+// Residual norm of each graph and its next command: stop when the residual is
+// certified below the tolerance, or at the iteration cap or on divergence;
+// certify a recursively updated residual with a full one before stopping.
+__global__ void __launch_bounds__(256) k_b_decide(const BGraph* __restrict__ gs, BState* __restrict__ st,
+                                                   double tol, int max_iter, int always_full) {
+  const int g = blockIdx.x;
+  const int cmd = st[g].cmd;
+  if (cmd == 0) return;
+  const BGraph& G = gs[g];
+  const int cnt = (cmd & CMD_FULL) ? G.res_tiles : G.elem_blocks;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < cnt; b += 256) acc += G.red[b];
+  const double rr = block_sum256(acc);
+  if (threadIdx.x != 0) return;
+  BState& s = st[g];
+  if (cmd & CMD_STEP) {
+    s.iters += 1;
+    if (cmd & CMD_RECUR) {
+      s.drift += 1e-5 * s.rel;   // error of the L dZ product, |L dZ| ~ |R| before the step
+      s.exact = 0;
+    }
+  }
+  if (cmd & CMD_FULL) {
+    s.exact = 1;
+    s.drift = 0.0;
+  }
+  const double rel = sqrt(rr / s.yy);
+  const double prev = s.rel;
+  s.rel = rel;
+  if (s.iters >= 1 && s.iters <= 64) s.hist[s.iters - 1] = rel;
+  int next;
+  if (!s.exact && rel > 0.5 * prev) {
+    next = CMD_FULL;   // a recursive residual that stops falling: form it in full
+  } else if (tol > 0 && rel <= tol) {
+    next = (!s.exact && rel + s.drift > 0.1 * tol) ? CMD_FULL : 0;
+  } else if (s.iters >= max_iter || !(rel <= 1e6)) {
+    next = 0;
+  } else {
+    next = CMD_STEP | (always_full ? CMD_FULL : CMD_RECUR);
+  }
+  s.cmd = next;
 }
 
 int largest_divisor_at_most(int total, int target) {
@@ -597,6 +919,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       CDL_TRY(L.done());
     }
     ++iters;
+    const double prev = rel;
     if (iters == 1 || always_full) {
       CDL_TRY(full_residual(nullptr));
       exact_r = true;
@@ -607,6 +930,14 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       exact_r = false;
     }
     CDL_TRY(read_norm(&rel));
+    if (!exact_r && rel > 0.5 * prev) {
+      // a recursive residual that stops falling is dominated by its own
+      // rounding: form it again in full
+      CDL_TRY(full_residual(nullptr));
+      CDL_TRY(read_norm(&rel));
+      exact_r = true;
+      drift = 0.0;
+    }
     if (stats && iters <= 64) stats->history[iters - 1] = rel;
   }
   if (stats) {
@@ -615,6 +946,48 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   }
   if (!(rel <= 1e6)) return CDL_ERR_NOT_CONVERGED;
   return (opts->rel_tol > 0 && !(rel <= opts->rel_tol)) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
+}
+
+int batch_solve(cdl_ctx* ctx, const BatchSolve& B) {
+  cudaStream_t st = ctx->stream;
+  auto run = [&](auto kern, const BTiles& t, int kc, double work, auto... args) -> int {
+    if (t.count == 0) return CDL_OK;
+    Launch L(ctx, kc, work);
+    kern<<<t.count, 256, 0, st>>>(t.p, B.gs, args...);
+    return L.done();
+  };
+  CDL_TRY(run(k_b_start, B.elem, CDL_KC_MISC, 0.0, B.k));
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_b_begin<<<B.G2, 256, 0, st>>>(B.gs, B.st);
+    CDL_TRY(L.done());
+  }
+  const BState* cst = B.st;
+  for (int slot = 0; slot < B.slots; ++slot) {
+    CDL_TRY(run(k_b_precond_in, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
+    for (int lvl = 0; lvl < B.d; ++lvl) {
+      CDL_TRY(tc_apply_grouped(ctx, B.lvl_first + lvl, B.lvl_groups + (size_t)lvl * B.G2, B.apply.p, B.apply.count,
+                               B.kp, CMD_STEP, CDL_KC_APPLY, B.apply_bytes));
+      CDL_TRY(run(k_b_update, B.t32, CDL_KC_MISC, 0.0, cst, B.kp));
+    }
+    CDL_TRY(run(k_b_precond_out, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
+    CDL_TRY(run(k_b_colsum, B.cs, CDL_KC_MISC, 0.0, cst, B.k));
+    CDL_TRY(run(k_b_center, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
+    // full residual (first step, certification) or recursive update
+    CDL_TRY(run(k_b_split, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
+    CDL_TRY(run(k_b_residual, B.res, CDL_KC_RESIDUAL, 0.0, cst, B.k));
+    if (!B.always_full) {
+      CDL_TRY(tc_apply_grouped(ctx, B.res_first, B.res_groups, B.apply.p, B.apply.count, B.kp, CMD_RECUR,
+                               CDL_KC_RESIDUAL, 0.0));
+      CDL_TRY(tc_apply_grouped(ctx, B.res_first + 1, B.res_groups + B.G2, B.apply.p, B.apply.count, B.kp,
+                               CMD_RECUR, CDL_KC_RESIDUAL, 0.0));
+      CDL_TRY(run(k_b_residual_update, B.elem, CDL_KC_RESIDUAL, 0.0, cst, B.k, B.kp));
+    }
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_b_decide<<<B.G2, 256, 0, st>>>(B.gs, B.st, B.rel_tol, B.max_iter, B.always_full ? 1 : 0);
+    CDL_TRY(L.done());
+  }
+  return CDL_OK;
 }
 
 }  // namespace cdl

@@ -22,6 +22,8 @@
 #include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -45,6 +47,8 @@ constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
 enum { MODE_SQUARE = 0, MODE_APPLY = 1, MODE_SQUARE_FP8 = 2 };
 
+
+
 struct TcParams {
   const uint32_t* tiles;   // packed tile descriptors
   int num_tiles;
@@ -62,6 +66,8 @@ struct TcParams {
   int level;
   void* out16;
   int debug_withhold_load;   // test hook: never issue the first A load (its wait must expire)
+  const TcGroup* groups;     // grouped launch: per-graph maps/outputs (nullptr otherwise)
+  int gate_mask;             // grouped: a graph's tiles run iff *gate & gate_mask (or gate is null)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -183,9 +189,29 @@ __device__ __forceinline__ float fp8_scale(unsigned amax_bits) {
 
 // Tile descriptors. square: I (bits 0-14), J (bits 15-29), half (bit 30).
 // apply: row block m (bits 0-15), split s (bits 16-31). bke = elements per
-// 128-byte k-block (64 bf16 or 128 fp8).
+// 128-byte k-block (64 bf16 or 128 fp8). Grouped launches carry the graph g in
+// bits 0-15; grouped squaring then I (16-22), J (23-29), half (30); grouped
+// apply the row block m (16-30), without split-K.
 __device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int bke, int& a_row, int& b_row,
-                                       int& k0, int& I, int& J, int& split) {
+                                       int& k0, int& I, int& J, int& split, int& g) {
+  if (p.groups) {
+    g = t & 0xFFFF;
+    split = 0;
+    k0 = 0;
+    if (p.mode == MODE_APPLY) {
+      I = (t >> 16) & 0x7FFF;
+      J = 0;
+      a_row = I * 128;
+      b_row = 0;
+    } else {
+      I = (t >> 16) & 0x7F;
+      J = (t >> 23) & 0x7F;
+      a_row = I * 256 + ((t >> 30) & 1) * 128;
+      b_row = J * 256;
+    }
+    return;
+  }
+  g = -1;
   if (p.mode != MODE_APPLY) {
     I = t & 0x7FFF;
     J = (t >> 15) & 0x7FFF;
@@ -203,6 +229,15 @@ __device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int bke, i
     I = m;
     J = 0;
   }
+}
+
+// Grouped launches: a tile runs unless its graph's gate word masks it out.
+// Every role of the CTA evaluates this for the same tile and sees the same
+// value (the gate is written by an earlier launch).
+__device__ __forceinline__ bool tile_runs(const TcParams& p, uint32_t t) {
+  if (!p.groups) return true;
+  const int* gate = p.groups[t & 0xFFFF].gate;
+  return gate == nullptr || (*gate & p.gate_mask) != 0;
 }
 
 template <bool FP8>
@@ -257,9 +292,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-      int a_row, b_row, k0, I, J, split;
-      decode(p, p.tiles[t], BKE, a_row, b_row, k0, I, J, split);
-      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+      const uint32_t td = p.tiles[t];
+      if (!tile_runs(p, td)) continue;
+      int a_row, b_row, k0, I, J, split, g;
+      decode(p, td, BKE, a_row, b_row, k0, I, J, split, g);
+      const CUtensorMap* ma = &tmA;
+      const CUtensorMap* mb = &tmB;
+      int kblocks = p.kblocks;
+      if (p.groups) {
+        const TcGroup& gd = p.groups[g];
+        ma = &gd.mapA;
+        mb = &gd.mapB;
+        kblocks = gd.kblocks;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma))
+                     : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb))
+                     : "memory");
+      }
+      for (int kb = 0; kb < kblocks; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t r = (uint32_t)(it / STAGES);
         if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
@@ -269,8 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_TILE;
         mbar_expect_tx(full_bar(s), A_TILE + b_bytes);
-        if (!(p.debug_withhold_load && it == 0)) tma_load_2d(a_dst, &tmA, k0 + kb * BKE, a_row, full_bar(s));
-        tma_load_2d(b_dst, &tmB, k0 + kb * BKE, b_row, full_bar(s));
+        if (!(p.debug_withhold_load && it == 0)) tma_load_2d(a_dst, ma, k0 + kb * BKE, a_row, full_bar(s));
+        tma_load_2d(b_dst, mb, k0 + kb * BKE, b_row, full_bar(s));
       }
     }
     if (!ok) {
@@ -286,16 +336,21 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------------------------ MMA issuer
     int it = 0, tc = 0;
     bool ok = true, issued = false;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++tc) {
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      const uint32_t td = p.tiles[t];
+      if (!tile_runs(p, td)) continue;
       const int acc = tc & 1;
       const uint32_t ar = (uint32_t)(tc >> 1);
+      ++tc;
       if (!mbar_wait(tempty_bar(acc), (ar & 1) ^ 1, abort_flag, p.status)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + (uint32_t)(acc * MAX_BN);
-      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+      int kblocks = p.kblocks;
+      if (p.groups) kblocks = p.groups[td & 0xFFFF].kblocks;
+      for (int kb = 0; kb < kblocks; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t r = (uint32_t)(it / STAGES);
         if (!mbar_wait(full_bar(s), r & 1, abort_flag, p.status)) {
@@ -331,20 +386,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;                 // TMEM lane quarter of this warp
     const int row_in_tile = q * 32 + lane;
     int tc = 0;
-    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++tc) {
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+      const uint32_t td = p.tiles[t];
+      if (!tile_runs(p, td)) continue;
       const int acc = tc & 1;
       const uint32_t ar = (uint32_t)(tc >> 1);
+      ++tc;
       if (!mbar_wait(tfull_bar(acc), ar & 1, abort_flag, p.status)) break;
       tc_fence_after();
-      int a_row, b_row, k0, I, J, split;
-      decode(p, p.tiles[t], BKE, a_row, b_row, k0, I, J, split);
+      int a_row, b_row, k0, I, J, split, g;
+      decode(p, td, BKE, a_row, b_row, k0, I, J, split, g);
       const int r = a_row + row_in_tile;
+      void* out = p.out;
+      int npad = p.npad;
+      if (p.groups) {
+        out = p.groups[g].out;
+        npad = p.groups[g].npad;
+      }
       const uint32_t taddr = tmem_base + (uint32_t)(acc * MAX_BN) + ((uint32_t)(q * 32) << 16);
       for (int c = 0; c < p.bn / 32; ++c) {
         float v[32];
         tmem_ld32(taddr + (uint32_t)(c * 32), v);
         if (p.mode == MODE_SQUARE) {
-          __nv_bfloat16* C = static_cast<__nv_bfloat16*>(p.out);
+          __nv_bfloat16* C = static_cast<__nv_bfloat16*>(out);
           const int col0 = b_row + c * 32;
           if (I != J) {
             uint32_t packed[16];
@@ -353,19 +417,19 @@ __global__ void __launch_bounds__(THREADS, 1)
               __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
               packed[e] = *reinterpret_cast<uint32_t*>(&h);
             }
-            uint4* dst = reinterpret_cast<uint4*>(C + (size_t)r * p.npad + col0);
+            uint4* dst = reinterpret_cast<uint4*>(C + (size_t)r * npad + col0);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
               dst[e] = make_uint4(packed[4 * e], packed[4 * e + 1], packed[4 * e + 2], packed[4 * e + 3]);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) C[(size_t)(col0 + e) * p.npad + r] = __float2bfloat16_rn(v[e]);
+            for (int e = 0; e < 32; ++e) C[(size_t)(col0 + e) * npad + r] = __float2bfloat16_rn(v[e]);
           } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int col = col0 + e;
               const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
-              if (col >= r) C[(size_t)r * p.npad + col] = h;
-              if (col > r) C[(size_t)col * p.npad + r] = h;
+              if (col >= r) C[(size_t)r * npad + col] = h;
+              if (col > r) C[(size_t)col * npad + r] = h;
             }
           }
         } else if (p.mode == MODE_SQUARE_FP8) {
@@ -373,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const float s_in = fp8_scale(p.amax[p.level]);
           const float sc = s_in * s_in;
           const float inv_out = 1.0f / fp8_scale(p.amax[p.level + 1]);
-          uint8_t* C8 = static_cast<uint8_t*>(p.out);
+          uint8_t* C8 = static_cast<uint8_t*>(out);
           __nv_bfloat16* C16 = static_cast<__nv_bfloat16*>(p.out16);
           const int col0 = b_row + c * 32;
 #pragma unroll
@@ -387,7 +451,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int e = 0; e < 8; ++e)
               w8[e] = (uint32_t)q8[4 * e] | ((uint32_t)q8[4 * e + 1] << 8) | ((uint32_t)q8[4 * e + 2] << 16) |
                       ((uint32_t)q8[4 * e + 3] << 24);
-            uint4* d8 = reinterpret_cast<uint4*>(C8 + (size_t)r * p.npad + col0);
+            uint4* d8 = reinterpret_cast<uint4*>(C8 + (size_t)r * npad + col0);
             d8[0] = make_uint4(w8[0], w8[1], w8[2], w8[3]);
             d8[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
 #pragma unroll
@@ -395,14 +459,14 @@ __global__ void __launch_bounds__(THREADS, 1)
               __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
               packed[e] = *reinterpret_cast<uint32_t*>(&h);
             }
-            uint4* d16 = reinterpret_cast<uint4*>(C16 + (size_t)r * p.npad + col0);
+            uint4* d16 = reinterpret_cast<uint4*>(C16 + (size_t)r * npad + col0);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
               d16[e] = make_uint4(packed[4 * e], packed[4 * e + 1], packed[4 * e + 2], packed[4 * e + 3]);
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
-              C8[(size_t)(col0 + e) * p.npad + r] = q8[e];
-              C16[(size_t)(col0 + e) * p.npad + r] = __float2bfloat16_rn(v[e]);
+              C8[(size_t)(col0 + e) * npad + r] = q8[e];
+              C16[(size_t)(col0 + e) * npad + r] = __float2bfloat16_rn(v[e]);
             }
           } else {
 #pragma unroll
@@ -410,17 +474,17 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int col = col0 + e;
               const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
               if (col >= r) {
-                C8[(size_t)r * p.npad + col] = q8[e];
-                C16[(size_t)r * p.npad + col] = h;
+                C8[(size_t)r * npad + col] = q8[e];
+                C16[(size_t)r * npad + col] = h;
               }
               if (col > r) {
-                C8[(size_t)col * p.npad + r] = q8[e];
-                C16[(size_t)col * p.npad + r] = h;
+                C8[(size_t)col * npad + r] = q8[e];
+                C16[(size_t)col * npad + r] = h;
               }
             }
           }
         } else {
-          float* P = static_cast<float*>(p.out) + ((size_t)split * p.npad + r) * p.ldo + c * 32;
+          float* P = static_cast<float*>(out) + ((size_t)split * npad + r) * p.ldo + c * 32;
           float4* dst = reinterpret_cast<float4*>(P);
 #pragma unroll
           for (int e = 0; e < 8; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
@@ -584,8 +648,91 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   p.level = level;
   p.out16 = fp8 ? ch->level16(level + 1) : nullptr;
   p.debug_withhold_load = ctx->debug_flags & 1;
+  p.groups = nullptr;
   const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
   return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8);
+}
+
+int tc_group_square(TcGroup* g, const void* level, void* out, int np) {
+  std::memset(g, 0, sizeof(TcGroup));
+  if (np % 256 || np > 32768) return CDL_ERR_INVALID_ARG;
+  CDL_TRY(make_map(&g->mapA, level, np, np, 128));
+  CDL_TRY(make_map(&g->mapB, level, np, np, 256));
+  g->out = out;
+  g->npad = np;
+  g->kblocks = np / BK;
+  return CDL_OK;
+}
+
+int tc_group_apply(TcGroup* g, const void* amat, const void* xop, float* out, int np, int kp, const int* gate) {
+  std::memset(g, 0, sizeof(TcGroup));
+  const int bn = 2 * kp;
+  if (np % 128 || np / 128 > 0x7FFF || bn % 32 || bn > MAX_BN) return CDL_ERR_INVALID_ARG;
+  CDL_TRY(make_map(&g->mapA, amat, np, np, 128));
+  CDL_TRY(make_map(&g->mapB, xop, bn, np, bn));
+  g->out = out;
+  g->gate = gate;
+  g->npad = np;
+  g->kblocks = np / BK;
+  return CDL_OK;
+}
+
+// Upper-triangle 256-blocks of every graph, graphs ordered largest first.
+std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad) {
+  std::vector<int> order(npad.size());
+  for (size_t g = 0; g < order.size(); ++g) order[g] = (int)g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return npad[a] > npad[b]; });
+  std::vector<uint32_t> v;
+  for (int g : order) {
+    const int nb = npad[g] / 256;
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J)
+        for (int h = 0; h < 2; ++h)
+          v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 23) | ((uint32_t)h << 30));
+  }
+  return v;
+}
+
+// 128-row blocks of every graph, largest graphs (longest k loops) first.
+std::vector<uint32_t> tc_grouped_apply_tiles(const std::vector<int>& npad) {
+  std::vector<int> order(npad.size());
+  for (size_t g = 0; g < order.size(); ++g) order[g] = (int)g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return npad[a] > npad[b]; });
+  std::vector<uint32_t> v;
+  for (int g : order)
+    for (int m = 0; m < npad[g] / 128; ++m) v.push_back((uint32_t)g | ((uint32_t)m << 16));
+  return v;
+}
+
+int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
+                      int ntiles, double flops) {
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.tiles = dtiles;
+  p.num_tiles = ntiles;
+  p.bn = 256;
+  p.idesc = make_idesc(256);
+  p.mode = MODE_SQUARE;
+  p.status = ctx->dev_status;
+  p.groups = dgroups;
+  // the kernel-parameter maps are unused in grouped mode: pass the first graph's
+  return launch(ctx, host_first->mapA, host_first->mapB, p, CDL_KC_SQUARE, flops);
+}
+
+int tc_apply_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
+                     int ntiles, int kp, int gate_mask, int kc, double work) {
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.tiles = dtiles;
+  p.num_tiles = ntiles;
+  p.bn = 2 * kp;
+  p.idesc = make_idesc(2 * kp);
+  p.mode = MODE_APPLY;
+  p.ldo = 2 * kp;
+  p.status = ctx->dev_status;
+  p.groups = dgroups;
+  p.gate_mask = gate_mask;
+  return launch(ctx, host_first->mapA, host_first->mapB, p, kc, work);
 }
 
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial, int kp,
@@ -620,6 +767,7 @@ int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float*
   p.level = 0;
   p.out16 = nullptr;
   p.debug_withhold_load = 0;
+  p.groups = nullptr;
   const double bytes = 2.0 * np * (double)np;
   return launch(ctx, ma, mbm, p, CDL_KC_APPLY, bytes);
 }
