@@ -44,6 +44,10 @@ struct BatchPlan {
   int64_t* top = nullptr;        // G x topk
   std::vector<int> order;        // graphs by order, largest first
   BatchSolve bs;
+  GraphBatch gb;
+  const PGraph* pgs = nullptr;
+  BTiles proj_blocks;
+  double proj_adds = 0;
   std::vector<TcGroup> sq_first, lvl_first, res_first;
   TcGroup* sq_groups = nullptr;
   BTiles sq_tiles, score_elem, score_pairs, score_nodes;
@@ -168,8 +172,26 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
       for (int bj = bi; bj < nb; ++bj) spairs.push_back((uint32_t)p | ((uint32_t)bi << 12) | ((uint32_t)bj << 22));
     for (int b = 0; b < (nn + 255) / 256; ++b) snodes.push_back(((uint32_t)b << 12) | (uint32_t)p);
   }
+  GraphTiles gt;
+  {
+    std::vector<int> gns(G2);
+    for (int g = 0; g < G2; ++g) gns[g] = gn(g);
+    graph_grouped_tiles(gns, T, gt);
+  }
+  std::vector<uint32_t> pblocks;
+  const int rpb = project_rows_per_block(k);
+  for (int g : P->order)
+    for (int b = 0; b * rpb < gn(g); ++b) pblocks.push_back(((uint32_t)b << 12) | (uint32_t)g);
   const size_t ntiles = sq.size() + ap.size() + t32.size() + elem.size() + res.size() + csb.size() + sel.size() +
-                        spairs.size() + snodes.size();
+                        spairs.size() + snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size() +
+                        pblocks.size();
+  std::vector<GGraph> ggs(G2);
+  std::vector<PGraph> pgs(G2);
+  GGraph* d_ggs = nullptr;
+  PGraph* d_pgs = nullptr;
+  int4* d_sel = nullptr;
+  char* sel_all = nullptr;
+  const size_t sel_one = graph_select_bytes();
 
   for (int pass = 0; pass < 2; ++pass) {
     Carver c;
@@ -185,11 +207,16 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     lvl_groups = c.take<TcGroup>(n_lvl_groups);
     res_groups = c.take<TcGroup>(2 * G2);
     d_tiles = c.take<uint32_t>(ntiles);
+    d_ggs = c.take<GGraph>(G2);
+    d_pgs = c.take<PGraph>(G2);
+    d_sel = c.take<int4>(gt.sel.size());
+    sel_all = c.take<char>(G2 * sel_one);
     for (int g = 0; g < G2; ++g) {
       const int nn = gn(g), np = gnp(g);
       const size_t nk = (size_t)nn * k;
       BGraph& B = gs[g];
       cdl_chain& ch = P->chains[g];
+      ggs[g].Xt = c.take<int>((size_t)nn * T);
       P->A[g] = c.take<double>((size_t)nn * nn);
       P->Dv[g] = c.take<double>(np);
       P->scal[g] = c.take<double>(2);   // vol, sigma
@@ -269,6 +296,22 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     B.ahi = ch.ahl;
     B.alo = ch.ahl + (size_t)nn * nn;
     B.Y = P->Y[g];
+    GGraph& Gg = ggs[g];
+    const int p = g / 2;
+    Gg.X = P->X + ((g & 1) ? P->N : 0) * (size_t)T + P->off[p] * (size_t)T;
+    Gg.A = P->A[g];
+    Gg.D = P->Dv[g];
+    Gg.vol = P->scal[g];
+    Gg.sigma = P->scal[g] + 1;
+    Gg.sel = sel_all + (size_t)g * sel_one;
+    Gg.n = nn;
+    Gg.T = T;
+    PGraph& Pg = pgs[g];
+    Pg.A = P->A[g];
+    Pg.Y = P->Y[g];
+    Pg.part = B.cs;
+    Pg.n = nn;
+    Pg.pad = 0;
   }
   P->sq_first.resize(std::max(d - 1, 1));
   P->lvl_first.resize(d);
@@ -336,9 +379,30 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   add(sel, P->score_elem);
   add(spairs, P->score_pairs);
   add(snodes, P->score_nodes);
+  GraphBatch& gb = P->gb;
+  add(gt.fixed, gb.fixed);
+  add(gt.dist, gb.dist);
+  add(gt.rows, gb.rows);
+  add(pblocks, P->proj_blocks);
   if ((st = upload(P->stream, d_tiles, all)) != CDL_OK || (st = upload(P->stream, d_gs, gs)) != CDL_OK ||
-      (st = upload(P->stream, P->jobs, jobs)) != CDL_OK)
+      (st = upload(P->stream, P->jobs, jobs)) != CDL_OK || (st = upload(P->stream, d_ggs, ggs)) != CDL_OK ||
+      (st = upload(P->stream, d_pgs, pgs)) != CDL_OK || (st = upload(P->stream, d_sel, gt.sel)) != CDL_OK)
     return fail(st);
+  gb.G2 = G2;
+  gb.sigma = o->sigma;
+  gb.gs = d_ggs;
+  gb.sel_all = sel_all;
+  gb.sel_bytes = (size_t)G2 * sel_one;
+  gb.sel = d_sel;
+  gb.sel_count = (int)gt.sel.size();
+  P->pgs = d_pgs;
+  for (int g = 0; g < G2; ++g) {
+    const double nn = gn(g);
+    gb.dist_terms += 0.5 * nn * (nn - 1) * T;
+    gb.select_bytes += 8.0 * nn * (nn - 1) / 2;
+    gb.kernel_bytes += 16.0 * nn * nn;
+    P->proj_adds += nn * (nn - 1) * k;
+  }
   if (cudaStreamSynchronize(P->stream) != cudaSuccess) return fail(CDL_ERR_CUDA);
   bs.G2 = G2;
   bs.k = k;
@@ -372,16 +436,12 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
 int run_batch(BatchPlan* P) {
   cdl_ctx* c = P->inner;
   const int G2 = 2 * P->G;
-  for (int g : P->order) {
-    const int p = g / 2;
-    const double* X = P->X + ((g & 1) ? P->N : 0) * (size_t)P->T + P->off[p] * (size_t)P->T;
-    CDL_TRY(graph_build(c, X, P->n[p], P->T, P->sigma, P->A[g], P->Dv[g], P->scal[g], P->scal[g] + 1));
-  }
+  CDL_TRY(graph_build_grouped(c, P->gb));
   for (int g : P->order) CDL_TRY(chain_init(c, &P->chains[g], P->A[g]));
   for (int l = 0; l + 1 < P->d; ++l)
     CDL_TRY(tc_square_grouped(c, &P->sq_first[l], P->sq_groups + (size_t)l * G2, P->sq_tiles.p, P->sq_tiles.count,
                               P->sq_flops));
-  for (int g : P->order) CDL_TRY(project(c, P->A[g], P->n[g / 2], P->k, P->seed, P->Y[g]));
+  CDL_TRY(project_grouped(c, P->pgs, G2, P->proj_blocks, P->k, P->seed, P->bs.cs, P->bs.elem, P->proj_adds));
   CDL_TRY(batch_solve(c, P->bs));
   return cad_score_grouped(c, P->jobs, P->G, P->k, P->score_dtype == CDL_F64, P->topk, P->score_elem,
                            P->score_pairs, P->score_nodes, P->score_bytes, P->cmax);

@@ -6,6 +6,7 @@
 //      select on the float64 bit patterns (distances are >= 0, so their bit
 //      patterns order like the values);
 //   3. A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = sum_j A_ij, vol.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -62,14 +63,10 @@ __device__ __forceinline__ void tri_index(long long t, int nb, int& bi, int& bj)
 
 // Exact squared distances on the 2^-16 grid: int64 sums of squared int32
 // differences, written as float64 multiples of 2^-32 to both (i,j) and (j,i).
-__global__ void __launch_bounds__(256) k_dist_int(const int* __restrict__ Xt, int n, int T,
-                                                   double* __restrict__ A, const SelectState* st) {
-  if (st->flags & 1) return;   // off-grid input: the float64 kernel handles it
+__device__ __forceinline__ void dist_int_tile(const int* __restrict__ Xt, int n, int T, double* __restrict__ A,
+                                              int bi, int bj) {
   __shared__ __align__(16) int As[DTK][DT];
   __shared__ __align__(16) int Bs[DTK][DT];
-  const int nb = (n + DT - 1) / DT;
-  int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int r0 = bi * DT, c0 = bj * DT;
   long long acc[4][4];
@@ -118,16 +115,21 @@ __global__ void __launch_bounds__(256) k_dist_int(const int* __restrict__ Xt, in
   }
 }
 
-// Float64 squared distances for inputs off the grid: same tiling, samples in
-// ascending order, explicit round-to-nearest operations (no contraction).
-__global__ void __launch_bounds__(256) k_dist_f64(const double* __restrict__ X, int n, int T,
+__global__ void __launch_bounds__(256) k_dist_int(const int* __restrict__ Xt, int n, int T,
                                                    double* __restrict__ A, const SelectState* st) {
-  if (!(st->flags & 1)) return;
-  __shared__ double As[DTK][DT + 1];
-  __shared__ double Bs[DTK][DT + 1];
+  if (st->flags & 1) return;   // off-grid input: the float64 kernel handles it
   const int nb = (n + DT - 1) / DT;
   int bi, bj;
   tri_index(blockIdx.x, nb, bi, bj);
+  dist_int_tile(Xt, n, T, A, bi, bj);
+}
+
+// Float64 squared distances for inputs off the grid: same tiling, samples in
+// ascending order, explicit round-to-nearest operations (no contraction).
+__device__ __forceinline__ void dist_f64_tile(const double* __restrict__ X, int n, int T, double* __restrict__ A,
+                                              int bi, int bj) {
+  __shared__ double As[DTK][DT + 1];
+  __shared__ double Bs[DTK][DT + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int r0 = bi * DT, c0 = bj * DT;
   double acc[4][4];
@@ -169,6 +171,15 @@ __global__ void __launch_bounds__(256) k_dist_f64(const double* __restrict__ X, 
   }
 }
 
+__global__ void __launch_bounds__(256) k_dist_f64(const double* __restrict__ X, int n, int T,
+                                                   double* __restrict__ A, const SelectState* st) {
+  if (!(st->flags & 1)) return;
+  const int nb = (n + DT - 1) / DT;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  dist_f64_tile(X, n, T, A, bi, bj);
+}
+
 __global__ void k_select_init(SelectState* st, long long rank) {
   st->prefix = 0;
   st->mask = 0;
@@ -178,16 +189,17 @@ __global__ void k_select_init(SelectState* st, long long rank) {
 
 // Histogram of the `bits`-wide digit at `shift` over keys of the upper
 // triangle matching the current prefix.
-__global__ void __launch_bounds__(512) k_select_hist(const double* __restrict__ A, int n, int shift,
-                                                      int bits, const SelectState* __restrict__ st,
-                                                      unsigned long long* __restrict__ hist) {
+// rows r0, r0 + rstep, ... < r1 of the upper triangle
+__device__ __forceinline__ void select_hist_rows(const double* __restrict__ A, int n, int shift, int bits,
+                                                 const SelectState* __restrict__ st,
+                                                 unsigned long long* __restrict__ hist, int r0, int r1, int rstep) {
   __shared__ unsigned int h[RADIX_BINS];
   for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) h[b] = 0;
   __syncthreads();
   const unsigned long long prefix = st->prefix, mask = st->mask;
   const unsigned long long dmask = (1ull << bits) - 1ull;
   const unsigned long long* K = reinterpret_cast<const unsigned long long*>(A);
-  for (int i = blockIdx.x; i < n - 1; i += gridDim.x) {
+  for (int i = r0; i < r1; i += rstep) {
     const unsigned long long* row = K + (size_t)i * n;
     for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
       unsigned long long key = row[j];
@@ -199,9 +211,15 @@ __global__ void __launch_bounds__(512) k_select_hist(const double* __restrict__ 
     if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
 }
 
+__global__ void __launch_bounds__(512) k_select_hist(const double* __restrict__ A, int n, int shift,
+                                                      int bits, const SelectState* __restrict__ st,
+                                                      unsigned long long* __restrict__ hist) {
+  select_hist_rows(A, n, shift, bits, st, hist, blockIdx.x, n - 1, gridDim.x);
+}
+
 // Pick the bin holding the remaining rank; extend the prefix; clear hist.
-__global__ void k_select_step(SelectState* st, unsigned long long* hist, int shift, int bits,
-                              double* sigma_out, int last) {
+__device__ __forceinline__ void select_step(SelectState* st, unsigned long long* hist, int shift, int bits,
+                                            double* sigma_out, int last) {
   __shared__ unsigned long long cnt[RADIX_BINS];
   const int nbins = 1 << bits;
   for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) {
@@ -228,6 +246,11 @@ __global__ void k_select_step(SelectState* st, unsigned long long* hist, int shi
   }
 }
 
+__global__ void k_select_step(SelectState* st, unsigned long long* hist, int shift, int bits,
+                              double* sigma_out, int last) {
+  select_step(st, hist, shift, bits, sigma_out, last);
+}
+
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 // A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = row sum. One block per row.
@@ -235,13 +258,10 @@ __global__ void k_set_scalar(double* p, double v) { *p = v; }
 // series, about 1e-14 relative); the argument is d2 * (1 / (2 sigma^2)) (one
 // float64 product); the row sum is accumulated in float-float (terms below
 // 2^-100 are dropped from the sum, not from A).
-__global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int n,
-                                                      const double* __restrict__ sigma,
-                                                      double* __restrict__ D) {
+__device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double rcp, double* __restrict__ D,
+                                           int i) {
   __shared__ double red[8];
-  const double s = *sigma;
-  const double rcp = 1.0 / (2.0 * (s * s));
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+  {
     double* row = A + (size_t)i * n;
     ff acc = {0.f, 0.f};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -278,8 +298,16 @@ __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int
   }
 }
 
+__global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int n,
+                                                      const double* __restrict__ sigma,
+                                                      double* __restrict__ D) {
+  const double s = *sigma;
+  const double rcp = 1.0 / (2.0 * (s * s));
+  for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row(A, n, rcp, D, i);
+}
+
 // vol = sum_i D_i (single block, fixed order per thread then tree).
-__global__ void k_sum(const double* __restrict__ v, int n, double* __restrict__ out) {
+__device__ __forceinline__ void block_sum_to(const double* __restrict__ v, int n, double* __restrict__ out) {
   __shared__ double red[32];
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
@@ -294,7 +322,156 @@ __global__ void k_sum(const double* __restrict__ v, int n, double* __restrict__ 
   }
 }
 
+__global__ void k_sum(const double* __restrict__ v, int n, double* __restrict__ out) { block_sum_to(v, n, out); }
+
+// ---------------------------------------------------------------- batched form
+// The same steps for every graph of a batch, one launch per step; a block
+// finds its graph and work item in a tile table.
+__global__ void k_g_select_init(const GGraph* __restrict__ gs) {
+  const GGraph& G = gs[blockIdx.x];
+  SelectState* st = static_cast<SelectState*>(G.sel);
+  const long long m = (long long)G.n * (G.n - 1) / 2;
+  st->prefix = 0;
+  st->mask = 0;
+  st->rank = (m - 1) / 2;
+  st->flags = 0;
+}
+
+__global__ void k_g_to_fixed(const uint32_t* __restrict__ tiles, const GGraph* __restrict__ gs) {
+  const uint32_t t = tiles[blockIdx.x];
+  const GGraph& G = gs[t & 0xFFFu];
+  const size_t total = (size_t)G.n * G.T;
+  const size_t base = (size_t)(t >> 12) * 1024;
+  bool off = false;
+  for (size_t idx = base + threadIdx.x; idx < total && idx < base + 1024; idx += blockDim.x) {
+    const double a = G.X[idx] * 65536.0;
+    const bool ok = (a == rint(a)) && fabs(a) < 8388608.0;
+    off |= !ok;
+    const size_t i = idx / G.T, tt = idx % G.T;
+    G.Xt[tt * G.n + i] = ok ? (int)a : 0;
+  }
+  if (__syncthreads_or(off) && threadIdx.x == 0) atomicOr(&static_cast<SelectState*>(G.sel)->flags, 1);
+}
+
+// tiles: g | bi << 12 | bj << 22 (64-node blocks, bi <= bj)
+__global__ void __launch_bounds__(256) k_g_dist(const uint32_t* __restrict__ tiles, const GGraph* __restrict__ gs) {
+  const uint32_t t = tiles[blockIdx.x];
+  const GGraph& G = gs[t & 0xFFFu];
+  const int bi = (int)((t >> 12) & 0x3FFu), bj = (int)(t >> 22);
+  if (static_cast<const SelectState*>(G.sel)->flags & 1)
+    dist_f64_tile(G.X, G.n, G.T, G.A, bi, bj);
+  else
+    dist_int_tile(G.Xt, G.n, G.T, G.A, bi, bj);
+}
+
+__global__ void __launch_bounds__(512) k_g_select_hist(const int4* __restrict__ tiles, const GGraph* __restrict__ gs,
+                                                        int shift, int bits) {
+  const int4 t = tiles[blockIdx.x];
+  const GGraph& G = gs[t.x];
+  SelectState* st = static_cast<SelectState*>(G.sel);
+  unsigned long long* hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(G.sel) + 64);
+  select_hist_rows(G.A, G.n, shift, bits, st, hist, t.y, t.z, 1);
+}
+
+__global__ void k_g_select_step(const GGraph* __restrict__ gs, int shift, int bits, int last) {
+  const GGraph& G = gs[blockIdx.x];
+  SelectState* st = static_cast<SelectState*>(G.sel);
+  unsigned long long* hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(G.sel) + 64);
+  select_step(st, hist, shift, bits, G.sigma, last);
+}
+
+__global__ void k_g_set_sigma(const GGraph* __restrict__ gs, double sigma) { *gs[blockIdx.x].sigma = sigma; }
+
+// tiles: (i << 12) | g, one row per block
+__global__ void __launch_bounds__(256) k_g_kernel_rows(const uint32_t* __restrict__ tiles,
+                                                        const GGraph* __restrict__ gs) {
+  const uint32_t t = tiles[blockIdx.x];
+  const GGraph& G = gs[t & 0xFFFu];
+  const double s = *G.sigma;
+  kernel_row(G.A, G.n, 1.0 / (2.0 * (s * s)), G.D, (int)(t >> 12));
+}
+
+__global__ void k_g_sum(const GGraph* __restrict__ gs) {
+  const GGraph& G = gs[blockIdx.x];
+  block_sum_to(G.D, G.n, G.vol);
+}
+
 }  // namespace
+
+size_t graph_select_bytes() { return 64 + RADIX_BINS * sizeof(unsigned long long); }
+
+void graph_grouped_tiles(const std::vector<int>& n, int T, GraphTiles& out) {
+  std::vector<int> order(n.size());
+  for (size_t g = 0; g < n.size(); ++g) order[g] = (int)g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  for (int g : order) {
+    const int nn = n[g], nb = (nn + DT - 1) / DT;
+    const size_t total = (size_t)nn * T;
+    for (size_t b = 0; b * 1024 < total; ++b) out.fixed.push_back(((uint32_t)b << 12) | (uint32_t)g);
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = bi; bj < nb; ++bj) out.dist.push_back((uint32_t)g | ((uint32_t)bi << 12) | ((uint32_t)bj << 22));
+    // selection: consecutive rows holding about 2^17 upper-triangle keys
+    int r0 = 0;
+    long long acc = 0;
+    for (int i = 0; i < nn - 1; ++i) {
+      acc += nn - 1 - i;
+      if (acc >= (1 << 17) || i == nn - 2) {
+        out.sel.push_back(make_int4(g, r0, i + 1, 0));
+        r0 = i + 1;
+        acc = 0;
+      }
+    }
+    for (int i = 0; i < nn; ++i) out.rows.push_back(((uint32_t)i << 12) | (uint32_t)g);
+  }
+}
+
+int graph_build_grouped(cdl_ctx* ctx, const GraphBatch& B) {
+  cudaStream_t s = ctx->stream;
+  CDL_CUDA_TRY(cudaMemsetAsync(B.sel_all, 0, B.sel_bytes, s));
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_g_select_init<<<B.G2, 1, 0, s>>>(B.gs);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_DISTANCE, 0);
+    k_g_to_fixed<<<B.fixed.count, 256, 0, s>>>(B.fixed.p, B.gs);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_DISTANCE, B.dist_terms);
+    k_g_dist<<<B.dist.count, 256, 0, s>>>(B.dist.p, B.gs);
+    CDL_TRY(L.done());
+  }
+  if (B.sigma > 0) {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_g_set_sigma<<<B.G2, 1, 0, s>>>(B.gs, B.sigma);
+    CDL_TRY(L.done());
+  } else {
+    const int shifts[6] = {52, 40, 28, 16, 4, 0};
+    const int widths[6] = {12, 12, 12, 12, 12, 4};
+    for (int p = 0; p < 6; ++p) {
+      {
+        Launch L(ctx, CDL_KC_SELECT, B.select_bytes);
+        k_g_select_hist<<<B.sel_count, 512, 0, s>>>(B.sel, B.gs, shifts[p], widths[p]);
+        CDL_TRY(L.done());
+      }
+      {
+        Launch L(ctx, CDL_KC_SELECT, 0);
+        k_g_select_step<<<B.G2, 256, 0, s>>>(B.gs, shifts[p], widths[p], p == 5);
+        CDL_TRY(L.done());
+      }
+    }
+  }
+  {
+    Launch L(ctx, CDL_KC_KERNEL, B.kernel_bytes);
+    k_g_kernel_rows<<<B.rows.count, 256, 0, s>>>(B.rows.p, B.gs);
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_g_sum<<<B.G2, 1024, 0, s>>>(B.gs);
+  return L.done();
+}
 
 int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma, double* A,
                 double* D, double* vol, double* sigma_out) {

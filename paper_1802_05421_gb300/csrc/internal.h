@@ -162,6 +162,56 @@ int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float*
                  int splits);
 bool tc_supported(cdl_ctx* ctx);
 // ---- batched form (one launch per step over many graphs) ----
+// A device tile table: entries (b << 12) | g, or a kernel-specific packing.
+struct BTiles {
+  const uint32_t* p = nullptr;
+  int count = 0;
+};
+// Graph build of one graph of a batch (device pointers).
+struct GGraph {
+  const double* X;  // n x T
+  int* Xt;          // T x n fixed-point copy
+  double* A;        // n x n
+  double* D;        // n
+  double* vol;
+  double* sigma;
+  void* sel;        // graph_select_bytes(): selection state and histogram
+  int n, T;
+};
+size_t graph_select_bytes();
+struct GraphTiles {
+  std::vector<uint32_t> fixed;   // (b << 12) | g, 1024-sample blocks of X
+  std::vector<uint32_t> dist;    // g | bi << 12 | bj << 22, 64-node blocks, bi <= bj
+  std::vector<int4> sel;         // (g, first row, end row, 0): about 2^17 keys each
+  std::vector<uint32_t> rows;    // (i << 12) | g
+};
+void graph_grouped_tiles(const std::vector<int>& n, int T, GraphTiles& out);
+struct GraphBatch {
+  int G2 = 0;
+  double sigma = 0;              // <= 0: median rule per graph
+  const GGraph* gs = nullptr;    // device
+  void* sel_all = nullptr;       // the graphs' selection blocks, contiguous
+  size_t sel_bytes = 0;
+  BTiles fixed, dist, rows;
+  const int4* sel = nullptr;
+  int sel_count = 0;
+  double dist_terms = 0, select_bytes = 0, kernel_bytes = 0;
+};
+int graph_build_grouped(cdl_ctx* ctx, const GraphBatch& b);
+
+// Projection of one graph of a batch.
+struct PGraph {
+  const double* A;
+  double* Y;
+  double* part;   // ceil(n / 256) x k column partial sums
+  int n, pad;
+};
+int project_rows_per_block(int k);
+// blocks: (b << 12) | g over ceil(n / rows_per_block); chunks: 256-row
+// chunks; elem: 256-element blocks of n x k.
+int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int k, uint64_t seed, BTiles chunks,
+                    BTiles elem, double adds);
+
 // Solve commands, per graph, set by the decision kernel after each step.
 enum { CMD_STEP = 1, CMD_FULL = 2, CMD_RECUR = 4 };
 
@@ -201,11 +251,6 @@ struct BState {
   double hist[64];
 };
 
-// A device tile table: entries (b << 12) | g, or a kernel-specific packing.
-struct BTiles {
-  const uint32_t* p = nullptr;
-  int count = 0;
-};
 
 struct BatchSolve {
   int G2 = 0, k = 0, kp = 0, d = 0, slots = 0, max_iter = 0;

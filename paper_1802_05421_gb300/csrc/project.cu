@@ -11,6 +11,7 @@
 // Per tile of 32 edges the block forms sqrt(A_ij) in float-float once per
 // (row, edge) and one Philox call per (row, edge, 128 projection rows), shared
 // through shared memory by the threads of the row.
+#include <algorithm>
 #include <cmath>
 
 #include "ff.cuh"
@@ -55,9 +56,10 @@ constexpr int MAX_RPB = 64;  // node rows per block
 // with +-1 (exact products).
 constexpr int RB = 16;       // projection rows per thread (half a Philox word)
 
-__global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
-                                                     uint32_t key0, uint32_t key1, double scale,
-                                                     double* __restrict__ Y) {
+// Rows [bidx * rpb, bidx * rpb + rpb) of Y (written, not accumulated).
+__device__ __forceinline__ void project_rows_block(const double* __restrict__ A, int n, int k, int W, int rpb,
+                                                   uint32_t key0, uint32_t key1, double scale,
+                                                   double* __restrict__ Y, int bidx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* P1 = reinterpret_cast<float*>(smraw);          // [rpb][JT]
   float* P2 = P1 + rpb * JT;                            // [rpb][JT]
@@ -68,20 +70,23 @@ __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A
   const int t = threadIdx.x;
   const int rl = t / H, h = t % H;
   const int w = h >> 1, shift = (h & 1) * RB;
-  const int i0 = blockIdx.x * rpb;
+  const int i0 = bidx * rpb;
   const int i = i0 + rl;
   const bool active = rl < rpb && i < n;
   float a1[RB], a2[RB], a3[RB];
 #pragma unroll
   for (int b = 0; b < RB; ++b) a1[b] = a2[b] = a3[b] = 0.f;
+  bool first = true;
   auto flush = [&]() {
     if (!active) return;
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
       const int r = w * 32 + shift + b;
-      if (r < k) Y[(size_t)i * k + r] += ((double)a1[b] + (double)a2[b]) + (double)a3[b];
+      const double v = ((double)a1[b] + (double)a2[b]) + (double)a3[b];
+      if (r < k) Y[(size_t)i * k + r] = first ? v : Y[(size_t)i * k + r] + v;
       a1[b] = a2[b] = a3[b] = 0.f;
     }
+    first = false;
   };
   for (int j0 = 0; j0 < n; j0 += JT) {
     if (j0 > 0 && j0 % CHUNK == 0) flush();
@@ -152,11 +157,17 @@ __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A
   }
 }
 
+__global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
+                                                     uint32_t key0, uint32_t key1, double scale,
+                                                     double* __restrict__ Y) {
+  project_rows_block(A, n, k, W, rpb, key0, key1, scale, Y, blockIdx.x);
+}
+
 // Column sums of Y over 256-row chunks (fixed order): part[b][r].
-__global__ void __launch_bounds__(256) k_colsum(const double* __restrict__ Y, int n, int k,
-                                                 double* __restrict__ part) {
+__device__ __forceinline__ void colsum_chunk(const double* __restrict__ Y, int n, int k, double* __restrict__ part,
+                                             int b) {
   __shared__ double sh[8][33];
-  const int b = blockIdx.x, i0 = b * 256, i1 = min(n, i0 + 256);
+  const int i0 = b * 256, i1 = min(n, i0 + 256);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int r0 = 0; r0 < k; r0 += 32) {
     const int r = r0 + tx;
@@ -174,17 +185,48 @@ __global__ void __launch_bounds__(256) k_colsum(const double* __restrict__ Y, in
   }
 }
 
+__global__ void __launch_bounds__(256) k_colsum(const double* __restrict__ Y, int n, int k,
+                                                 double* __restrict__ part) {
+  colsum_chunk(Y, n, k, part, blockIdx.x);
+}
+
 // Y -= column mean. The exact Y has zero column sums (each edge adds +x to
 // its head's row and -x to its tail's); the float sums of the two rows round
 // differently, and that residue lies in the null space of L, where no
 // solution Z can match it.
-__global__ void k_sub_mean(double* __restrict__ Y, int n, int k, const double* __restrict__ part, int nparts) {
-  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sub_mean(double* __restrict__ Y, int n, int k, const double* __restrict__ part,
+                                         int nparts, size_t idx) {
   if (idx >= (size_t)n * k) return;
   const int r = (int)(idx % k);
   double s = 0.0;
   for (int q = 0; q < nparts; ++q) s += part[(size_t)q * k + r];
   Y[idx] -= s / n;
+}
+
+__global__ void k_sub_mean(double* __restrict__ Y, int n, int k, const double* __restrict__ part, int nparts) {
+  sub_mean(Y, n, k, part, nparts, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------- batched form
+__global__ void __launch_bounds__(256, 2) k_g_project(const uint32_t* __restrict__ tiles, const PGraph* __restrict__ gs,
+                                                       int k, int W, int rpb, uint32_t key0, uint32_t key1,
+                                                       double scale) {
+  const uint32_t t = tiles[blockIdx.x];
+  const PGraph& G = gs[t & 0xFFFu];
+  project_rows_block(G.A, G.n, k, W, rpb, key0, key1, scale, G.Y, (int)(t >> 12));
+}
+
+__global__ void __launch_bounds__(256) k_g_colsum(const uint32_t* __restrict__ tiles, const PGraph* __restrict__ gs,
+                                                   int k) {
+  const uint32_t t = tiles[blockIdx.x];
+  const PGraph& G = gs[t & 0xFFFu];
+  colsum_chunk(G.Y, G.n, k, G.part, (int)(t >> 12));
+}
+
+__global__ void k_g_sub_mean(const uint32_t* __restrict__ tiles, const PGraph* __restrict__ gs, int k) {
+  const uint32_t t = tiles[blockIdx.x];
+  const PGraph& G = gs[t & 0xFFFu];
+  sub_mean(G.Y, G.n, k, G.part, (G.n + 255) / 256, (size_t)(t >> 12) * blockDim.x + threadIdx.x);
 }
 
 }  // namespace
@@ -203,7 +245,6 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
-  CDL_CUDA_TRY(cudaMemsetAsync(Y, 0, (size_t)n * k * sizeof(double), ctx->stream));
   Launch L(ctx, CDL_KC_PROJECT, (double)n * (n - 1) * k);
   k_project<<<blocks, threads, smem, ctx->stream>>>(A, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
                                                     (uint32_t)(seed >> 32), scale, Y);
@@ -220,6 +261,40 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
   k_sub_mean<<<(unsigned)(((size_t)n * k + 255) / 256), 256, 0, ctx->stream>>>(Y, n, k,
                                                                                static_cast<const double*>(vpart), nparts);
   return L3.done();
+}
+
+int project_rows_per_block(int k) {
+  const int W = (k + 31) / 32;
+  return std::max(1, std::min(MAX_RPB, 256 / (2 * W)));
+}
+
+int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int k, uint64_t seed, BTiles chunks,
+                    BTiles elem, double adds) {
+  const int W = (k + 31) / 32;
+  const int rpb = project_rows_per_block(k);
+  const int threads = rpb * 2 * W;
+  const int nrb = (W + 3) / 4;
+  const size_t smem = 3 * (size_t)rpb * JT * sizeof(float) + (size_t)rpb * JT * nrb * sizeof(uint4);
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_g_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr = true;
+  }
+  (void)G2;
+  {
+    Launch L(ctx, CDL_KC_PROJECT, adds);
+    k_g_project<<<blocks.count, threads, smem, ctx->stream>>>(blocks.p, gs, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
+                                                              (uint32_t)(seed >> 32), 1.0 / std::sqrt((double)k));
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_g_colsum<<<chunks.count, 256, 0, ctx->stream>>>(chunks.p, gs, k);
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_g_sub_mean<<<elem.count, 256, 0, ctx->stream>>>(elem.p, gs, k);
+  return L.done();
 }
 
 }  // namespace cdl
