@@ -55,6 +55,9 @@ struct BatchPlan {
   unsigned* cmax = nullptr;      // G x 2k column bounds of the float32 scoring
   std::vector<BState> st_host;
   double sq_flops = 0, score_bytes = 0;
+  int* active = nullptr;         // device: graphs still refining after the last slot
+  int slots_seen = 0;            // most slots a call has needed so far
+  int slots_captured = 0;        // slots recorded in the CUDA graph
   cudaGraphExec_t exec = nullptr;
   int64_t graph_launches = 0;
   int64_t graph_kc_launches[CDL_KC_COUNT] = {0};
@@ -151,13 +154,15 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   for (int g = 0; g < G2; ++g) npads[g] = gnp(g);
   const std::vector<uint32_t> sq = tc_grouped_square_tiles(npads);
   const std::vector<uint32_t> ap = tc_grouped_apply_tiles(npads);
-  const int ncb = (k + 63) / 64;
+  int res_tm, res_tn;
+  batch_residual_tile(k, &res_tm, &res_tn);
+  const int ncb = (k + res_tn - 1) / res_tn;
   for (int g : P->order) {
     const int nn = gn(g), np = gnp(g);
     for (int b = 0; b < np / 32; ++b) t32.push_back(((uint32_t)b << 12) | (uint32_t)g);
     const int eb = (int)(((size_t)nn * k + 255) / 256);
     for (int b = 0; b < eb; ++b) elem.push_back(((uint32_t)b << 12) | (uint32_t)g);
-    const int rt = ((nn + 63) / 64) * ncb;
+    const int rt = ((nn + res_tm - 1) / res_tm) * ncb;
     for (int b = 0; b < rt; ++b) res.push_back(((uint32_t)b << 12) | (uint32_t)g);
     for (int b = 0; b < (nn + 255) / 256; ++b) csb.push_back(((uint32_t)b << 12) | (uint32_t)g);
   }
@@ -203,6 +208,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     d_st = c.take<BState>(G2);
     P->jobs = c.take<ScoreJob>(G);
     P->cmax = c.take<unsigned>((size_t)G * 2 * k);
+    P->active = c.take<int>(1);
     P->sq_groups = c.take<TcGroup>(n_sq_groups);
     lvl_groups = c.take<TcGroup>(n_lvl_groups);
     res_groups = c.take<TcGroup>(2 * G2);
@@ -235,7 +241,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
       B.dzop = c.take<uint16_t>((size_t)2 * kp * np);
       B.zh = c.take<float>(nk);
       B.zl = c.take<float>(nk);
-      B.res_tiles = ((nn + 63) / 64) * ncb;
+      B.res_tiles = ((nn + res_tm - 1) / res_tm) * ncb;
       B.elem_blocks = (int)((nk + 255) / 256);
       B.red = c.take<double>(std::max(B.res_tiles, B.elem_blocks));
       B.cs = c.take<double>((size_t)((nn + 255) / 256) * k);
@@ -413,9 +419,10 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   bs.always_full = (o->solve.flags & CDL_SOLVE_FULL_RESIDUAL) != 0;
   // one slot is one refinement step or one certification of a recursively
   // updated residual; four slots beyond max_iter leave room for those
-  bs.slots = o->solve.max_iter + (bs.always_full ? 0 : 4);
+  bs.max_slots = o->solve.max_iter + (bs.always_full ? 0 : 4);
   bs.gs = d_gs;
   bs.st = d_st;
+  bs.active = P->active;
   bs.lvl_groups = lvl_groups;
   bs.lvl_first = P->lvl_first.data();
   bs.res_groups = res_groups;
@@ -431,9 +438,32 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   return CDL_OK;
 }
 
-// The whole batch on the plan's private context (stream-ordered, no host
-// synchronisation).
-int run_batch(BatchPlan* P) {
+// Refinement slots run eagerly until no graph is still refining (the count of
+// running graphs is read back after each slot) or the slot budget is spent.
+int solve_adaptive(BatchPlan* P, int done, int* used) {
+  cdl_ctx* c = P->inner;
+  int s = done;
+  while (s < P->bs.max_slots) {
+    CDL_TRY(batch_solve_slot(c, P->bs));
+    ++s;
+    int running = 0;
+    CDL_CUDA_TRY(cudaMemcpyAsync(&running, P->active, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    CDL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    if (running == 0) break;
+  }
+  *used = s;
+  return CDL_OK;
+}
+
+int score_batch(BatchPlan* P) {
+  return cad_score_grouped(P->inner, P->jobs, P->G, P->k, P->score_dtype == CDL_F64, P->topk, P->score_elem,
+                           P->score_pairs, P->score_nodes, P->score_bytes, P->cmax);
+}
+
+// The whole batch on the plan's private context. fixed_slots > 0 issues that
+// many refinement slots with no host synchronisation (the form recorded as a
+// CUDA graph); 0 runs them adaptively.
+int run_batch(BatchPlan* P, int fixed_slots) {
   cdl_ctx* c = P->inner;
   const int G2 = 2 * P->G;
   CDL_TRY(graph_build_grouped(c, P->gb));
@@ -442,12 +472,18 @@ int run_batch(BatchPlan* P) {
     CDL_TRY(tc_square_grouped(c, &P->sq_first[l], P->sq_groups + (size_t)l * G2, P->sq_tiles.p, P->sq_tiles.count,
                               P->sq_flops));
   CDL_TRY(project_grouped(c, P->pgs, G2, P->proj_blocks, P->k, P->seed, P->bs.cs, P->bs.elem, P->proj_adds));
-  CDL_TRY(batch_solve(c, P->bs));
-  return cad_score_grouped(c, P->jobs, P->G, P->k, P->score_dtype == CDL_F64, P->topk, P->score_elem,
-                           P->score_pairs, P->score_nodes, P->score_bytes, P->cmax);
+  CDL_TRY(batch_solve_start(c, P->bs));
+  if (fixed_slots > 0) {
+    for (int s = 0; s < fixed_slots; ++s) CDL_TRY(batch_solve_slot(c, P->bs));
+  } else {
+    int used = 0;
+    CDL_TRY(solve_adaptive(P, 0, &used));
+    P->slots_seen = std::max(P->slots_seen, used);
+  }
+  return score_batch(P);
 }
 
-int capture(BatchPlan* P) {
+int capture(BatchPlan* P, int slots) {
   cdl_ctx* c = P->inner;
   const bool timing = c->timing;
   c->timing = false;
@@ -459,7 +495,7 @@ int capture(BatchPlan* P) {
     kw0[i] = c->kc_work[i];
   }
   CDL_CUDA_TRY(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
-  const int st = run_batch(P);
+  const int st = run_batch(P, slots);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(P->stream, &graph);
   c->timing = timing;
@@ -485,6 +521,7 @@ int capture(BatchPlan* P) {
     set_last_error(cudaGetErrorString(ei), __FILE__, __LINE__);
     return CDL_ERR_CUDA;
   }
+  P->slots_captured = slots;
   return CDL_OK;
 }
 
@@ -535,16 +572,40 @@ extern "C" int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, i
   CDL_CUDA_TRY(cudaMemcpyAsync(P->X + (size_t)N * T, X2, xbytes, in, s));
   P->inner->timing = ctx->timing;
   P->inner->debug_flags = 0;
-  if (o->use_graph && P->exec) {
+  bool replayed = false;
+  const bool graph_current =
+      P->exec && (P->slots_captured > P->slots_seen || P->slots_captured >= P->bs.max_slots);
+  if (o->use_graph && graph_current) {
     CDL_CUDA_TRY(cudaGraphLaunch(P->exec, s));
+    replayed = true;
     ctx->launches += P->graph_launches;
     for (int i = 0; i < CDL_KC_COUNT; ++i) {
       ctx->kc_launches[i] += P->graph_kc_launches[i];
       ctx->kc_work[i] += P->graph_kc_work[i];
     }
   } else {
-    CDL_TRY(run_batch(P));
-    if (o->use_graph) CDL_TRY(capture(P));
+    CDL_TRY(run_batch(P, 0));
+    if (o->use_graph) {
+      if (P->exec) {
+        CDL_CUDA_TRY(cudaGraphExecDestroy(P->exec));
+        P->exec = nullptr;
+      }
+      // one slot beyond the most any call has needed
+      CDL_TRY(capture(P, std::min(P->slots_seen + 1, P->bs.max_slots)));
+    }
+  }
+  if (replayed) {
+    // graphs still refining after the recorded slots continue eagerly (and
+    // the graph is recorded again with more slots on the next call)
+    int running = 0;
+    CDL_CUDA_TRY(cudaMemcpyAsync(&running, P->active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CDL_CUDA_TRY(cudaStreamSynchronize(s));
+    if (running > 0 && P->slots_captured < P->bs.max_slots) {
+      int used = 0;
+      CDL_TRY(solve_adaptive(P, P->slots_captured, &used));
+      P->slots_seen = std::max(P->slots_seen, used);
+      CDL_TRY(score_batch(P));
+    }
   }
   CDL_CUDA_TRY(cudaMemcpyAsync(F, P->F, (size_t)N * sizeof(double), outk, s));
   if (o->topk > 0)

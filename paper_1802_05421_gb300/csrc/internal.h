@@ -253,11 +253,12 @@ struct BState {
 
 
 struct BatchSolve {
-  int G2 = 0, k = 0, kp = 0, d = 0, slots = 0, max_iter = 0;
+  int G2 = 0, k = 0, kp = 0, d = 0, max_slots = 0, max_iter = 0;
   double rel_tol = 0;
   bool always_full = false;
   const BGraph* gs = nullptr;
   BState* st = nullptr;
+  int* active = nullptr;                 // device: graphs still running after the last slot
   BTiles t32, elem, res, cs, apply;
   const TcGroup* lvl_groups = nullptr;   // device, d arrays of G2 (level-major)
   const TcGroup* lvl_first = nullptr;    // host, entry 0 of each level array
@@ -265,7 +266,13 @@ struct BatchSolve {
   const TcGroup* res_first = nullptr;    // host, 2 entries
   double apply_bytes = 0;                // per grouped level apply
 };
-int batch_solve(cdl_ctx* ctx, const BatchSolve& b);
+// R = Y, Z = 0, ||Y|| and the first command of every graph.
+int batch_solve_start(cdl_ctx* ctx, const BatchSolve& b);
+// One refinement slot (a step or a certification per graph that has not
+// stopped); *b.active counts the graphs still running after it.
+int batch_solve_slot(cdl_ctx* ctx, const BatchSolve& b);
+// Tile of the batched float-float residual for k right-hand sides.
+void batch_residual_tile(int k, int* tm, int* tn);
 
 // One pair of a batch for the grouped scoring launches.
 struct ScoreJob {

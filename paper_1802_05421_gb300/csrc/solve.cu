@@ -181,18 +181,20 @@ __device__ __forceinline__ void ff_mac(float ah, float al, float zh, float zl, f
 
 constexpr int RB_M = 64, RB_N = 64, RB_K = 16;
 
-// R = Y - D o Z + A Z for a 64-row x 64-column tile, 4 x 4 float-float
-// accumulators per thread; A and Z arrive as float hi + lo planes. Per-block
-// sum of R^2.
+// R = Y - D o Z + A Z for a TM-row x TN-column tile (64 x 64, or 128 x 32
+// for narrow right-hand sides), 4 x 4 float-float accumulators per thread; A
+// and Z arrive as float hi + lo planes. Per-block sum of R^2.
+template <int TM, int TN>
 __device__ __forceinline__ double residual_tile(const float* __restrict__ Ahi, const float* __restrict__ Alo,
                                                 const float* __restrict__ Zh, const float* __restrict__ Zl,
                                                 const double* __restrict__ Z, const double* __restrict__ Y,
                                                 const double* __restrict__ D, int n, int k,
                                                 double* __restrict__ R, int i0, int c0) {
-  __shared__ __align__(16) float Ah[RB_K][RB_M + 4], Al[RB_K][RB_M + 4];
-  __shared__ __align__(16) float Bh[RB_K][RB_N], Bl[RB_K][RB_N];
+  static_assert((TM / 4) * (TN / 4) == 256, "256 threads, 4 x 4 outputs each");
+  __shared__ __align__(16) float Ah[RB_K][TM + 4], Al[RB_K][TM + 4];
+  __shared__ __align__(16) float Bh[RB_K][TN], Bl[RB_K][TN];
   __shared__ double red[8];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % (TN / 4), ty = tid / (TN / 4);
   float sh[4][4], sc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -200,7 +202,7 @@ __device__ __forceinline__ double residual_tile(const float* __restrict__ Ahi, c
     for (int b = 0; b < 4; ++b) sh[a][b] = sc[a][b] = 0.f;
   for (int j0 = 0; j0 < n; j0 += RB_K) {
 #pragma unroll
-    for (int e = 0; e < (RB_M * RB_K) / 256; ++e) {
+    for (int e = 0; e < (TM * RB_K) / 256; ++e) {
       const int idx = tid + e * 256;
       const int ii = idx / RB_K, jj = idx % RB_K;
       const int i = i0 + ii, j = j0 + jj;
@@ -210,9 +212,9 @@ __device__ __forceinline__ double residual_tile(const float* __restrict__ Ahi, c
       Al[jj][ii] = ok ? Alo[o] : 0.f;
     }
 #pragma unroll
-    for (int e = 0; e < (RB_N * RB_K) / 256; ++e) {
+    for (int e = 0; e < (TN * RB_K) / 256; ++e) {
       const int idx = tid + e * 256;
-      const int jj = idx / RB_N, cc = idx % RB_N;
+      const int jj = idx / TN, cc = idx % TN;
       const int j = j0 + jj, c = c0 + cc;
       const bool ok = j < n && c < k;
       Bh[jj][cc] = ok ? Zh[(size_t)j * k + c] : 0.f;
@@ -276,7 +278,8 @@ __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ Ahi,
                                                    const double* __restrict__ Z, const double* __restrict__ Y,
                                                    const double* __restrict__ D, int n, int k,
                                                    double* __restrict__ R, double* __restrict__ part) {
-  const double t = residual_tile(Ahi, Alo, Zh, Zl, Z, Y, D, n, k, R, blockIdx.x * RB_M, blockIdx.y * RB_N);
+  const double t = residual_tile<RB_M, RB_N>(Ahi, Alo, Zh, Zl, Z, Y, D, n, k, R, blockIdx.x * RB_M,
+                                             blockIdx.y * RB_N);
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
@@ -616,16 +619,17 @@ __global__ void __launch_bounds__(256) k_b_split(const uint32_t* __restrict__ ti
   G.zl[idx] = (float)(z - (double)h);
 }
 
-// Full float-float residual R = Y - D o Z + A Z, one 64 x 64 tile per block.
+// Full float-float residual R = Y - D o Z + A Z, one TM x TN tile per block.
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) k_b_residual(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
                                                      const BState* __restrict__ st, int k) {
   int g, b;
   tdec(tiles[blockIdx.x], g, b);
   if (!(st[g].cmd & CMD_FULL)) return;
   const BGraph& G = gs[g];
-  const int ncb = (k + RB_N - 1) / RB_N;
-  const double t = residual_tile(G.ahi, G.alo, G.zh, G.zl, G.Z, G.Y, G.D, G.n, k, G.R, (b / ncb) * RB_M,
-                                 (b % ncb) * RB_N);
+  const int ncb = (k + TN - 1) / TN;
+  const double t = residual_tile<TM, TN>(G.ahi, G.alo, G.zh, G.zl, G.Z, G.Y, G.D, G.n, k, G.R, (b / ncb) * TM,
+                                         (b % ncb) * TN);
   if (threadIdx.x == 0) G.red[b] = t;
 }
 
@@ -656,7 +660,8 @@ __global__ void __launch_bounds__(256) k_b_residual_update(const uint32_t* __res
 // certified below the tolerance, or at the iteration cap or on divergence;
 // certify a recursively updated residual with a full one before stopping.
 __global__ void __launch_bounds__(256) k_b_decide(const BGraph* __restrict__ gs, BState* __restrict__ st,
-                                                   double tol, int max_iter, int always_full) {
+                                                   double tol, int max_iter, int always_full,
+                                                   int* __restrict__ active) {
   const int g = blockIdx.x;
   const int cmd = st[g].cmd;
   if (cmd == 0) return;
@@ -693,6 +698,7 @@ __global__ void __launch_bounds__(256) k_b_decide(const BGraph* __restrict__ gs,
     next = CMD_STEP | (always_full ? CMD_FULL : CMD_RECUR);
   }
   s.cmd = next;
+  if (next) atomicAdd(active, 1);
 }
 
 int largest_divisor_at_most(int total, int target) {
@@ -948,46 +954,56 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   return (opts->rel_tol > 0 && !(rel <= opts->rel_tol)) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
 }
 
-int batch_solve(cdl_ctx* ctx, const BatchSolve& B) {
-  cudaStream_t st = ctx->stream;
-  auto run = [&](auto kern, const BTiles& t, int kc, double work, auto... args) -> int {
-    if (t.count == 0) return CDL_OK;
-    Launch L(ctx, kc, work);
-    kern<<<t.count, 256, 0, st>>>(t.p, B.gs, args...);
-    return L.done();
-  };
-  CDL_TRY(run(k_b_start, B.elem, CDL_KC_MISC, 0.0, B.k));
-  {
-    Launch L(ctx, CDL_KC_MISC, 0);
-    k_b_begin<<<B.G2, 256, 0, st>>>(B.gs, B.st);
-    CDL_TRY(L.done());
-  }
+void batch_residual_tile(int k, int* tm, int* tn) {
+  *tm = k <= 32 ? 128 : 64;
+  *tn = k <= 32 ? 32 : 64;
+}
+
+namespace {
+template <typename K, typename... Args>
+int run_tiles(cdl_ctx* ctx, const BatchSolve& B, K kern, const BTiles& t, int kc, double work, Args... args) {
+  if (t.count == 0) return CDL_OK;
+  Launch L(ctx, kc, work);
+  kern<<<t.count, 256, 0, ctx->stream>>>(t.p, B.gs, args...);
+  return L.done();
+}
+}  // namespace
+
+int batch_solve_start(cdl_ctx* ctx, const BatchSolve& B) {
+  CDL_TRY(run_tiles(ctx, B, k_b_start, B.elem, CDL_KC_MISC, 0.0, B.k));
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_b_begin<<<B.G2, 256, 0, ctx->stream>>>(B.gs, B.st);
+  return L.done();
+}
+
+int batch_solve_slot(cdl_ctx* ctx, const BatchSolve& B) {
   const BState* cst = B.st;
-  for (int slot = 0; slot < B.slots; ++slot) {
-    CDL_TRY(run(k_b_precond_in, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
-    for (int lvl = 0; lvl < B.d; ++lvl) {
-      CDL_TRY(tc_apply_grouped(ctx, B.lvl_first + lvl, B.lvl_groups + (size_t)lvl * B.G2, B.apply.p, B.apply.count,
-                               B.kp, CMD_STEP, CDL_KC_APPLY, B.apply_bytes));
-      CDL_TRY(run(k_b_update, B.t32, CDL_KC_MISC, 0.0, cst, B.kp));
-    }
-    CDL_TRY(run(k_b_precond_out, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
-    CDL_TRY(run(k_b_colsum, B.cs, CDL_KC_MISC, 0.0, cst, B.k));
-    CDL_TRY(run(k_b_center, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
-    // full residual (first step, certification) or recursive update
-    CDL_TRY(run(k_b_split, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
-    CDL_TRY(run(k_b_residual, B.res, CDL_KC_RESIDUAL, 0.0, cst, B.k));
-    if (!B.always_full) {
-      CDL_TRY(tc_apply_grouped(ctx, B.res_first, B.res_groups, B.apply.p, B.apply.count, B.kp, CMD_RECUR,
-                               CDL_KC_RESIDUAL, 0.0));
-      CDL_TRY(tc_apply_grouped(ctx, B.res_first + 1, B.res_groups + B.G2, B.apply.p, B.apply.count, B.kp,
-                               CMD_RECUR, CDL_KC_RESIDUAL, 0.0));
-      CDL_TRY(run(k_b_residual_update, B.elem, CDL_KC_RESIDUAL, 0.0, cst, B.k, B.kp));
-    }
-    Launch L(ctx, CDL_KC_MISC, 0);
-    k_b_decide<<<B.G2, 256, 0, st>>>(B.gs, B.st, B.rel_tol, B.max_iter, B.always_full ? 1 : 0);
-    CDL_TRY(L.done());
+  CDL_CUDA_TRY(cudaMemsetAsync(B.active, 0, sizeof(int), ctx->stream));
+  CDL_TRY(run_tiles(ctx, B, k_b_precond_in, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
+  for (int lvl = 0; lvl < B.d; ++lvl) {
+    CDL_TRY(tc_apply_grouped(ctx, B.lvl_first + lvl, B.lvl_groups + (size_t)lvl * B.G2, B.apply.p, B.apply.count,
+                             B.kp, CMD_STEP, CDL_KC_APPLY, B.apply_bytes));
+    CDL_TRY(run_tiles(ctx, B, k_b_update, B.t32, CDL_KC_MISC, 0.0, cst, B.kp));
   }
-  return CDL_OK;
+  CDL_TRY(run_tiles(ctx, B, k_b_precond_out, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
+  CDL_TRY(run_tiles(ctx, B, k_b_colsum, B.cs, CDL_KC_MISC, 0.0, cst, B.k));
+  CDL_TRY(run_tiles(ctx, B, k_b_center, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
+  // full residual (first step, certification) or recursive update
+  CDL_TRY(run_tiles(ctx, B, k_b_split, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
+  if (B.k <= 32)
+    CDL_TRY(run_tiles(ctx, B, k_b_residual<128, 32>, B.res, CDL_KC_RESIDUAL, 0.0, cst, B.k));
+  else
+    CDL_TRY(run_tiles(ctx, B, k_b_residual<64, 64>, B.res, CDL_KC_RESIDUAL, 0.0, cst, B.k));
+  if (!B.always_full) {
+    CDL_TRY(tc_apply_grouped(ctx, B.res_first, B.res_groups, B.apply.p, B.apply.count, B.kp, CMD_RECUR,
+                             CDL_KC_RESIDUAL, 0.0));
+    CDL_TRY(tc_apply_grouped(ctx, B.res_first + 1, B.res_groups + B.G2, B.apply.p, B.apply.count, B.kp, CMD_RECUR,
+                             CDL_KC_RESIDUAL, 0.0));
+    CDL_TRY(run_tiles(ctx, B, k_b_residual_update, B.elem, CDL_KC_RESIDUAL, 0.0, cst, B.k, B.kp));
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_b_decide<<<B.G2, 256, 0, ctx->stream>>>(B.gs, B.st, B.rel_tol, B.max_iter, B.always_full ? 1 : 0, B.active);
+  return L.done();
 }
 
 }  // namespace cdl
