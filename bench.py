@@ -326,6 +326,17 @@ def run_batched(args):
     iters = [stats[g].iters for g in range(2 * G)]
     rel_res = max(stats[g].rel_res for g in range(2 * G))
 
+    _, info = cdl.cdl_batch_plan_info(ctx)
+    tuning = {"square_max_npad_128": info.square_max_npad_128,
+              "project_rows_per_block": info.project_rows_per_block,
+              "residual_tile": [info.residual_tile_m, info.residual_tile_n],
+              "slots_captured": info.slots_captured,
+              "square_variants_ms": {str(info.square_variant_max_npad_128[v]): round(info.square_variant_ms[v], 4)
+                                     for v in range(info.n_square_variants)},
+              "project_variants_ms": {str(info.project_variant_rows[v]): round(info.project_variant_ms[v], 4)
+                                      for v in range(info.n_project_variants)},
+              "device_gb": round(info.device_bytes / 1e9, 2)}
+
     # one eager call with per-kernel timing: the grouped squaring launches
     eager = opts(0)
     call(eager)   # builds the eager plan's state (same sizes: the plan is reused)
@@ -378,6 +389,7 @@ def run_batched(args):
                     "d2h_bytes_per_step": N * 8 + G * BATCH_TOPK * 8, "same_top_as_device_run": same_top},
             "gpu_launches": int((l1 - l0) // args.steps),
             "clocks": clocks,
+            "autotuner": tuning,
             "eager_phases_ms": {k: round(v["ms"], 3) for k, v in kc.items()},
         }
         print(json.dumps(line), flush=True)

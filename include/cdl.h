@@ -116,8 +116,11 @@ int cdl_ctx_launch_count(cdl_ctx* ctx, int64_t* launches);
  * squarings never issue their first tile load, so the kernel's bounded wait
  * for it expires (about 2 s); the kernel records the expiry and returns, and
  * cdl_sync reports CDL_ERR_TIMEOUT. Used to test the bounded-wait path; the
- * outputs of such a launch are meaningless. */
-enum { CDL_DEBUG_WITHHOLD_TC_LOAD = 1 };
+ * outputs of such a launch are meaningless. CDL_DEBUG_BATCH_VARIANT: a
+ * batched plan built while it is set skips the autotuner and uses squaring
+ * variant ((flags >> 8) & 15) and projection variant ((flags >> 12) & 15)
+ * (clamped to the variants the plan has), so tests can check every variant. */
+enum { CDL_DEBUG_WITHHOLD_TC_LOAD = 1, CDL_DEBUG_BATCH_VARIANT = 2 };
 int cdl_ctx_set_debug(cdl_ctx* ctx, int flags);
 
 /* ---------------------------------------------------------------- graph */
@@ -358,6 +361,28 @@ typedef struct {
 int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, int32_t T, const double* X1,
                          const double* X2, const cdl_batch_opts* opts, double* F, int64_t* top_idx,
                          cdl_solve_stats* stats);
+
+/* What the batched plan of the context holds: the autotuner's choices and
+ * timings and the refinement slots recorded in the CUDA graph. The tuner
+ * runs once per plan, on the first call, over the batch's own data: each
+ * squaring variant (128 x 128 tiles for graphs up to an order, 128 x 256
+ * above) squares level 0 of every graph, each projection variant (node rows
+ * per block) projects every graph; the fastest of each is kept. */
+typedef struct {
+  int32_t ready;                        /* 1 once a batched call built a plan  */
+  int32_t square_max_npad_128;          /* chosen squaring variant             */
+  int32_t project_rows_per_block;       /* chosen projection variant           */
+  int32_t residual_tile_m, residual_tile_n;
+  int32_t slots_captured;               /* refinement slots in the CUDA graph  */
+  int32_t slots_seen;                   /* most slots a call has needed        */
+  int32_t n_square_variants, n_project_variants;
+  int32_t square_variant_max_npad_128[8];
+  double square_variant_ms[8];
+  int32_t project_variant_rows[8];
+  double project_variant_ms[8];
+  uint64_t device_bytes;                /* device memory owned by the plan     */
+} cdl_batch_info;
+int cdl_batch_plan_info(const cdl_ctx* ctx, cdl_batch_info* info);
 
 #ifdef __cplusplus
 }

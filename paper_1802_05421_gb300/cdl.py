@@ -26,6 +26,7 @@ CDL_ERR_UNSUPPORTED = -6
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3 = 0, 1, 2, 3
 CDL_SOLVE_FULL_RESIDUAL = 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1
+CDL_DEBUG_BATCH_VARIANT = 2
 
 (CDL_KC_DISTANCE, CDL_KC_SELECT, CDL_KC_KERNEL, CDL_KC_CHAIN_INIT, CDL_KC_SQUARE, CDL_KC_APPLY,
  CDL_KC_RESIDUAL, CDL_KC_PROJECT, CDL_KC_SCORE, CDL_KC_TOPK, CDL_KC_MISC, CDL_KC_COUNT) = range(12)
@@ -53,6 +54,16 @@ class cdl_batch_opts(ctypes.Structure):
                 ("score_dtype", ctypes.c_int), ("seed", ctypes.c_uint64), ("sigma", ctypes.c_double),
                 ("solve", cdl_solve_opts), ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32)]
+
+
+class cdl_batch_info(ctypes.Structure):
+    _fields_ = [("ready", ctypes.c_int32), ("square_max_npad_128", ctypes.c_int32),
+                ("project_rows_per_block", ctypes.c_int32), ("residual_tile_m", ctypes.c_int32),
+                ("residual_tile_n", ctypes.c_int32), ("slots_captured", ctypes.c_int32),
+                ("slots_seen", ctypes.c_int32), ("n_square_variants", ctypes.c_int32),
+                ("n_project_variants", ctypes.c_int32), ("square_variant_max_npad_128", ctypes.c_int32 * 8),
+                ("square_variant_ms", ctypes.c_double * 8), ("project_variant_rows", ctypes.c_int32 * 8),
+                ("project_variant_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_uint64)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -86,6 +97,7 @@ _SIGS = {
     "cdl_caddelag_pair": [_P, _P, _P, _I64, _I32, ctypes.POINTER(cdl_pair_opts), _P, _P,
                           ctypes.POINTER(cdl_solve_stats), ctypes.POINTER(cdl_solve_stats)],
     "cdl_caddelag_batched": [_P, _I32, _P, _I32, _P, _P, ctypes.POINTER(cdl_batch_opts), _P, _P, _P],
+    "cdl_batch_plan_info": [_P, ctypes.POINTER(cdl_batch_info)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -230,6 +242,13 @@ def cdl_caddelag_batched(ctx, G, n, T, X1, X2, opts: cdl_batch_opts, F, top_idx,
     cdl_solve_stats or None."""
     return _lib.cdl_caddelag_batched(ctx, G, _ptr(n), T, _ptr(X1), _ptr(X2), ctypes.byref(opts), _ptr(F),
                                      _ptr(top_idx), ctypes.cast(stats, _P) if stats is not None else None)
+
+
+def cdl_batch_plan_info(ctx):
+    """Returns (status, cdl_batch_info)."""
+    info = cdl_batch_info()
+    st = _lib.cdl_batch_plan_info(ctx, ctypes.byref(info))
+    return st, info
 
 
 def exported_symbols():

@@ -245,7 +245,7 @@ int cdl_ctx_reset_counters(cdl_ctx* ctx) {
 }
 
 int cdl_ctx_set_debug(cdl_ctx* ctx, int flags) {
-  if (!ctx || (flags & ~CDL_DEBUG_WITHHOLD_TC_LOAD)) return CDL_ERR_INVALID_ARG;
+  if (!ctx || (flags & ~(CDL_DEBUG_WITHHOLD_TC_LOAD | CDL_DEBUG_BATCH_VARIANT | 0xFF00))) return CDL_ERR_INVALID_ARG;
   ctx->debug_flags = flags;
   return CDL_OK;
 }

@@ -46,11 +46,26 @@ struct BatchPlan {
   BatchSolve bs;
   GraphBatch gb;
   const PGraph* pgs = nullptr;
-  BTiles proj_blocks;
+  // autotuned variants: squaring tile width per graph size, projection rows per block
+  struct SqVariant {
+    int max_npad_128;            // graphs up to this order use 128 x 128 tiles
+    std::vector<TcGroup> first;  // host copy of entry 0 of each level's array
+    TcGroup* groups = nullptr;   // device, (d - 1) x G2
+    BTiles tiles;
+    double ms = 0;
+  };
+  struct ProjVariant {
+    int rpb;
+    BTiles blocks;
+    double ms = 0;
+  };
+  std::vector<SqVariant> sqv;
+  std::vector<ProjVariant> pv;
+  int sq_choice = 0, pv_choice = 0;
+  bool tuned = false;
   double proj_adds = 0;
-  std::vector<TcGroup> sq_first, lvl_first, res_first;
-  TcGroup* sq_groups = nullptr;
-  BTiles sq_tiles, score_elem, score_pairs, score_nodes;
+  std::vector<TcGroup> lvl_first, res_first;
+  BTiles score_elem, score_pairs, score_nodes;
   ScoreJob* jobs = nullptr;
   unsigned* cmax = nullptr;      // G x 2k column bounds of the float32 scoring
   std::vector<BState> st_host;
@@ -127,7 +142,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     P->N += n[p];
   }
   auto gn = [&](int g) { return (int)n[g / 2]; };
-  auto gnp = [&](int g) { return (int)round_up(gn(g), 256); };
+  auto gnp = [&](int g) { return (int)round_up(gn(g), 128); };
   P->order.resize(G2);
   std::iota(P->order.begin(), P->order.end(), 0);
   std::stable_sort(P->order.begin(), P->order.end(), [&](int a, int b) { return gn(a) > gn(b); });
@@ -152,7 +167,21 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   std::vector<uint32_t> t32, elem, res, csb, sel, spairs, snodes;
   std::vector<int> npads(G2);
   for (int g = 0; g < G2; ++g) npads[g] = gnp(g);
-  const std::vector<uint32_t> sq = tc_grouped_square_tiles(npads);
+  // squaring variants: 128 x 128 tiles up to a graph order (always where the
+  // padded order is not a multiple of 256), 128 x 256 tiles above it
+  const int thresholds[4] = {0, 1024, 2048, 32768};
+  std::vector<std::vector<int>> sq_bn;
+  for (int th : thresholds) {
+    std::vector<int> bn(G2);
+    for (int g = 0; g < G2; ++g) bn[g] = (npads[g] % 256 || npads[g] <= th) ? 128 : 256;
+    if (!sq_bn.empty() && sq_bn.back() == bn) continue;
+    sq_bn.push_back(bn);
+    BatchPlan::SqVariant v;
+    v.max_npad_128 = th;
+    P->sqv.push_back(v);
+  }
+  std::vector<std::vector<uint32_t>> sq;
+  for (auto& bn : sq_bn) sq.push_back(tc_grouped_square_tiles(npads, bn));
   const std::vector<uint32_t> ap = tc_grouped_apply_tiles(npads);
   int res_tm, res_tn;
   batch_residual_tile(k, &res_tm, &res_tn);
@@ -183,13 +212,21 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     for (int g = 0; g < G2; ++g) gns[g] = gn(g);
     graph_grouped_tiles(gns, T, gt);
   }
-  std::vector<uint32_t> pblocks;
-  const int rpb = project_rows_per_block(k);
-  for (int g : P->order)
-    for (int b = 0; b * rpb < gn(g); ++b) pblocks.push_back(((uint32_t)b << 12) | (uint32_t)g);
-  const size_t ntiles = sq.size() + ap.size() + t32.size() + elem.size() + res.size() + csb.size() + sel.size() +
-                        spairs.size() + snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size() +
-                        pblocks.size();
+  // projection variants: node rows per block
+  std::vector<std::vector<uint32_t>> pblocks;
+  for (int rpb = project_rows_per_block(k); rpb >= 16; rpb /= 2) {
+    std::vector<uint32_t> v;
+    for (int g : P->order)
+      for (int b = 0; b * rpb < gn(g); ++b) v.push_back(((uint32_t)b << 12) | (uint32_t)g);
+    pblocks.push_back(std::move(v));
+    BatchPlan::ProjVariant pvar;
+    pvar.rpb = rpb;
+    P->pv.push_back(pvar);
+  }
+  size_t ntiles = ap.size() + t32.size() + elem.size() + res.size() + csb.size() + sel.size() + spairs.size() +
+                  snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size();
+  for (auto& v : sq) ntiles += v.size();
+  for (auto& v : pblocks) ntiles += v.size();
   std::vector<GGraph> ggs(G2);
   std::vector<PGraph> pgs(G2);
   GGraph* d_ggs = nullptr;
@@ -209,7 +246,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     P->jobs = c.take<ScoreJob>(G);
     P->cmax = c.take<unsigned>((size_t)G * 2 * k);
     P->active = c.take<int>(1);
-    P->sq_groups = c.take<TcGroup>(n_sq_groups);
+    for (auto& v : P->sqv) v.groups = c.take<TcGroup>(n_sq_groups);
     lvl_groups = c.take<TcGroup>(n_lvl_groups);
     res_groups = c.take<TcGroup>(2 * G2);
     d_tiles = c.take<uint32_t>(ntiles);
@@ -319,18 +356,20 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     Pg.n = nn;
     Pg.pad = 0;
   }
-  P->sq_first.resize(std::max(d - 1, 1));
   P->lvl_first.resize(d);
   P->res_first.resize(2);
   {
-    std::vector<TcGroup> sqg(n_sq_groups), lvg(n_lvl_groups), rsg(2 * G2);
+    std::vector<std::vector<TcGroup>> sqg(P->sqv.size(), std::vector<TcGroup>(n_sq_groups));
+    std::vector<TcGroup> lvg(n_lvl_groups), rsg(2 * G2);
     for (int g = 0; g < G2; ++g) {
       const cdl_chain& ch = P->chains[g];
       const int np = (int)ch.npad;
       const int* gate = &d_st[g].cmd;
-      for (int l = 0; l + 1 < d; ++l)
-        if ((st = tc_group_square(&sqg[(size_t)l * G2 + g], ch.level(l), ch.level(l + 1), np)) != CDL_OK)
-          return fail(st);
+      for (size_t v = 0; v < P->sqv.size(); ++v)
+        for (int l = 0; l + 1 < d; ++l)
+          if ((st = tc_group_square(&sqg[v][(size_t)l * G2 + g], ch.level(l), ch.level(l + 1), np, sq_bn[v][g])) !=
+              CDL_OK)
+            return fail(st);
       for (int l = 0; l < d; ++l)
         if ((st = tc_group_apply(&lvg[(size_t)l * G2 + g], ch.level(l), gs[g].xop, gs[g].part, np, kp, gate)) !=
             CDL_OK)
@@ -341,11 +380,15 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
               CDL_OK)
         return fail(st);
     }
-    for (int l = 0; l + 1 < d; ++l) P->sq_first[l] = sqg[(size_t)l * G2];
+    for (size_t v = 0; v < P->sqv.size(); ++v) {
+      P->sqv[v].first.resize(std::max(d - 1, 1));
+      for (int l = 0; l + 1 < d; ++l) P->sqv[v].first[l] = sqg[v][(size_t)l * G2];
+      if ((st = upload(P->stream, P->sqv[v].groups, sqg[v])) != CDL_OK) return fail(st);
+    }
     for (int l = 0; l < d; ++l) P->lvl_first[l] = lvg[(size_t)l * G2];
     P->res_first[0] = rsg[0];
     P->res_first[1] = rsg[G2];
-    if ((st = upload(P->stream, P->sq_groups, sqg)) != CDL_OK || (st = upload(P->stream, lvl_groups, lvg)) != CDL_OK ||
+    if ((st = upload(P->stream, lvl_groups, lvg)) != CDL_OK ||
         (st = upload(P->stream, res_groups, rsg)) != CDL_OK)
       return fail(st);
     // the host vectors are read by the copies above: finish them before they go
@@ -376,7 +419,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     all.insert(all.end(), v.begin(), v.end());
   };
   BatchSolve& bs = P->bs;
-  add(sq, P->sq_tiles);
+  for (size_t v = 0; v < sq.size(); ++v) add(sq[v], P->sqv[v].tiles);
   add(ap, bs.apply);
   add(t32, bs.t32);
   add(elem, bs.elem);
@@ -389,7 +432,10 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   add(gt.fixed, gb.fixed);
   add(gt.dist, gb.dist);
   add(gt.rows, gb.rows);
-  add(pblocks, P->proj_blocks);
+  for (size_t v = 0; v < pblocks.size(); ++v) add(pblocks[v], P->pv[v].blocks);
+  // before tuning: 128 x 128 tiles up to order 1024, the widest projection blocks
+  P->sq_choice = std::min<int>(1, (int)P->sqv.size() - 1);
+  P->pv_choice = 0;
   if ((st = upload(P->stream, d_tiles, all)) != CDL_OK || (st = upload(P->stream, d_gs, gs)) != CDL_OK ||
       (st = upload(P->stream, P->jobs, jobs)) != CDL_OK || (st = upload(P->stream, d_ggs, ggs)) != CDL_OK ||
       (st = upload(P->stream, d_pgs, pgs)) != CDL_OK || (st = upload(P->stream, d_sel, gt.sel)) != CDL_OK)
@@ -468,10 +514,12 @@ int run_batch(BatchPlan* P, int fixed_slots) {
   const int G2 = 2 * P->G;
   CDL_TRY(graph_build_grouped(c, P->gb));
   for (int g : P->order) CDL_TRY(chain_init(c, &P->chains[g], P->A[g]));
+  const BatchPlan::SqVariant& sv = P->sqv[P->sq_choice];
   for (int l = 0; l + 1 < P->d; ++l)
-    CDL_TRY(tc_square_grouped(c, &P->sq_first[l], P->sq_groups + (size_t)l * G2, P->sq_tiles.p, P->sq_tiles.count,
-                              P->sq_flops));
-  CDL_TRY(project_grouped(c, P->pgs, G2, P->proj_blocks, P->k, P->seed, P->bs.cs, P->bs.elem, P->proj_adds));
+    CDL_TRY(tc_square_grouped(c, &sv.first[l], sv.groups + (size_t)l * G2, sv.tiles.p, sv.tiles.count, P->sq_flops));
+  const BatchPlan::ProjVariant& pvar = P->pv[P->pv_choice];
+  CDL_TRY(project_grouped(c, P->pgs, G2, pvar.blocks, pvar.rpb, P->k, P->seed, P->bs.cs, P->bs.elem,
+                          P->proj_adds));
   CDL_TRY(batch_solve_start(c, P->bs));
   if (fixed_slots > 0) {
     for (int s = 0; s < fixed_slots; ++s) CDL_TRY(batch_solve_slot(c, P->bs));
@@ -481,6 +529,63 @@ int run_batch(BatchPlan* P, int fixed_slots) {
     P->slots_seen = std::max(P->slots_seen, used);
   }
   return score_batch(P);
+}
+
+// Autotuner: times each squaring variant (level 0 -> 1 of every graph) and
+// each projection variant on the batch's own data, after a first run has
+// filled the buffers, and keeps the fastest. The kernels it reruns are pure
+// functions of buffers the rerun does not change (level 0, A), and the
+// buffers they write are formed again by every later run.
+int autotune(BatchPlan* P) {
+  cdl_ctx* c = P->inner;
+  const bool timing = c->timing;
+  c->timing = false;
+  cudaEvent_t e0, e1;
+  CDL_CUDA_TRY(cudaEventCreate(&e0));
+  CDL_CUDA_TRY(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& fn, double* ms) -> int {
+    CDL_TRY(fn());   // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      CDL_CUDA_TRY(cudaEventRecord(e0, P->stream));
+      CDL_TRY(fn());
+      CDL_CUDA_TRY(cudaEventRecord(e1, P->stream));
+      CDL_CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CDL_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return CDL_OK;
+  };
+  const int G2 = 2 * P->G;
+  int st = CDL_OK;
+  if (P->d > 1)
+    for (size_t v = 0; v < P->sqv.size() && st == CDL_OK; ++v) {
+      BatchPlan::SqVariant& sv = P->sqv[v];
+      st = time_it([&] { return tc_square_grouped(c, &sv.first[0], sv.groups, sv.tiles.p, sv.tiles.count, 0.0); },
+                   &sv.ms);
+    }
+  for (size_t v = 0; v < P->pv.size() && st == CDL_OK; ++v) {
+    BatchPlan::ProjVariant& pvar = P->pv[v];
+    st = time_it([&] { return project_grouped(c, P->pgs, G2, pvar.blocks, pvar.rpb, P->k, P->seed, P->bs.cs,
+                                              P->bs.elem, 0.0); },
+                 &pvar.ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = timing;
+  // tuning launches are not part of any call's work
+  c->launches = 0;
+  for (int i = 0; i < CDL_KC_COUNT; ++i) c->kc_launches[i] = 0, c->kc_work[i] = 0, c->kc_ms[i] = 0;
+  CDL_TRY(st);
+  if (P->d > 1)
+    for (size_t v = 0; v < P->sqv.size(); ++v)
+      if (P->sqv[v].ms < P->sqv[P->sq_choice].ms) P->sq_choice = (int)v;
+  for (size_t v = 0; v < P->pv.size(); ++v)
+    if (P->pv[v].ms < P->pv[P->pv_choice].ms) P->pv_choice = (int)v;
+  P->tuned = true;
+  return CDL_OK;
 }
 
 int capture(BatchPlan* P, int slots) {
@@ -560,6 +665,12 @@ extern "C" int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, i
       ctx->batch = nullptr;
     }
     CDL_TRY(build_plan(ctx, G, n, T, o, &ctx->batch));
+    if (ctx->debug_flags & CDL_DEBUG_BATCH_VARIANT) {
+      BatchPlan* Q = ctx->batch;
+      Q->sq_choice = std::min((ctx->debug_flags >> 8) & 15, (int)Q->sqv.size() - 1);
+      Q->pv_choice = std::min((ctx->debug_flags >> 12) & 15, (int)Q->pv.size() - 1);
+      Q->tuned = true;
+    }
   }
   BatchPlan* P = ctx->batch;
   cudaStream_t s = P->stream;
@@ -585,6 +696,12 @@ extern "C" int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, i
     }
   } else {
     CDL_TRY(run_batch(P, 0));
+    if (!P->tuned) {
+      // count this run's launches before the tuner's reruns
+      CDL_CUDA_TRY(cudaStreamSynchronize(s));
+      CDL_TRY(ctx_absorb(ctx, P->inner));
+      CDL_TRY(autotune(P));
+    }
     if (o->use_graph) {
       if (P->exec) {
         CDL_CUDA_TRY(cudaGraphExecDestroy(P->exec));
@@ -632,4 +749,32 @@ extern "C" int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, i
     }
   }
   return converged ? CDL_OK : CDL_ERR_NOT_CONVERGED;
+}
+
+extern "C" int cdl_batch_plan_info(const cdl_ctx* ctx, cdl_batch_info* info) {
+  if (!ctx || !info) return CDL_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  const BatchPlan* P = ctx->batch;
+  if (!P) return CDL_OK;
+  info->ready = 1;
+  info->square_max_npad_128 = P->sqv[P->sq_choice].max_npad_128;
+  info->project_rows_per_block = P->pv[P->pv_choice].rpb;
+  int tm, tn;
+  batch_residual_tile(P->k, &tm, &tn);
+  info->residual_tile_m = tm;
+  info->residual_tile_n = tn;
+  info->slots_captured = P->exec ? P->slots_captured : 0;
+  info->slots_seen = P->slots_seen;
+  info->n_square_variants = (int)std::min<size_t>(8, P->sqv.size());
+  info->n_project_variants = (int)std::min<size_t>(8, P->pv.size());
+  for (int v = 0; v < info->n_square_variants; ++v) {
+    info->square_variant_max_npad_128[v] = P->sqv[v].max_npad_128;
+    info->square_variant_ms[v] = P->sqv[v].ms;
+  }
+  for (int v = 0; v < info->n_project_variants; ++v) {
+    info->project_variant_rows[v] = P->pv[v].rpb;
+    info->project_variant_ms[v] = P->pv[v].ms;
+  }
+  info->device_bytes = P->bytes;
+  return CDL_OK;
 }

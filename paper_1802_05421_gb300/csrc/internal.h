@@ -145,12 +145,16 @@ struct TcGroup {
   const int* gate;     // apply: tiles run iff *gate & gate_mask (null: always)
   int npad;
   int kblocks;
-  int pad[10];
+  uint32_t idesc;      // tcgen05 instruction descriptor of this graph's tiles
+  int bn;              // MMA N: squaring 128 or 256, apply 2 kp
+  int pad[8];
 };
 static_assert(sizeof(TcGroup) % 64 == 0, "TcGroup keeps its tensor maps 64-byte aligned in arrays");
-int tc_group_square(TcGroup* g, const void* level, void* out, int np);
+// bn = 256: 128 x 256 tiles in 256-blocks (npad % 256 == 0); bn = 128:
+// 128 x 128 tiles (npad % 128 == 0).
+int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn);
 int tc_group_apply(TcGroup* g, const void* amat, const void* xop, float* out, int np, int kp, const int* gate);
-std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad);
+std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, const std::vector<int>& bn);
 std::vector<uint32_t> tc_grouped_apply_tiles(const std::vector<int>& npad);
 int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
                       int ntiles, double flops);
@@ -209,8 +213,8 @@ struct PGraph {
 int project_rows_per_block(int k);
 // blocks: (b << 12) | g over ceil(n / rows_per_block); chunks: 256-row
 // chunks; elem: 256-element blocks of n x k.
-int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int k, uint64_t seed, BTiles chunks,
-                    BTiles elem, double adds);
+int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int rpb, int k, uint64_t seed,
+                    BTiles chunks, BTiles elem, double adds);
 
 // Solve commands, per graph, set by the decision kernel after each step.
 enum { CMD_STEP = 1, CMD_FULL = 2, CMD_RECUR = 4 };

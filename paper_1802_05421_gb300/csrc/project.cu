@@ -268,10 +268,10 @@ int project_rows_per_block(int k) {
   return std::max(1, std::min(MAX_RPB, 256 / (2 * W)));
 }
 
-int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int k, uint64_t seed, BTiles chunks,
-                    BTiles elem, double adds) {
+int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int rpb, int k, uint64_t seed,
+                    BTiles chunks, BTiles elem, double adds) {
   const int W = (k + 31) / 32;
-  const int rpb = project_rows_per_block(k);
+  if (rpb < 1 || rpb > project_rows_per_block(k)) return CDL_ERR_INVALID_ARG;
   const int threads = rpb * 2 * W;
   const int nrb = (W + 3) / 4;
   const size_t smem = 3 * (size_t)rpb * JT * sizeof(float) + (size_t)rpb * JT * nrb * sizeof(uint4);

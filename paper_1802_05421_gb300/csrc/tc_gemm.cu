@@ -203,6 +203,11 @@ __device__ __forceinline__ void decode(const TcParams& p, uint32_t t, int bke, i
       J = 0;
       a_row = I * 128;
       b_row = 0;
+    } else if (p.groups[g].bn == 128) {   // 128-blocks: I (16-23), J (24-31)
+      I = (t >> 16) & 0xFF;
+      J = (t >> 24) & 0xFF;
+      a_row = I * 128;
+      b_row = J * 128;
     } else {
       I = (t >> 16) & 0x7F;
       J = (t >> 23) & 0x7F;
@@ -299,11 +304,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const CUtensorMap* ma = &tmA;
       const CUtensorMap* mb = &tmB;
       int kblocks = p.kblocks;
+      uint32_t tile_b_bytes = b_bytes;
       if (p.groups) {
         const TcGroup& gd = p.groups[g];
         ma = &gd.mapA;
         mb = &gd.mapB;
         kblocks = gd.kblocks;
+        tile_b_bytes = (uint32_t)gd.bn * BK * 2;
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma))
                      : "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb))
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_TILE;
-        mbar_expect_tx(full_bar(s), A_TILE + b_bytes);
+        mbar_expect_tx(full_bar(s), A_TILE + tile_b_bytes);
         if (!(p.debug_withhold_load && it == 0)) tma_load_2d(a_dst, ma, k0 + kb * BKE, a_row, full_bar(s));
         tma_load_2d(b_dst, mb, k0 + kb * BKE, b_row, full_bar(s));
       }
@@ -349,7 +356,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + (uint32_t)(acc * MAX_BN);
       int kblocks = p.kblocks;
-      if (p.groups) kblocks = p.groups[td & 0xFFFF].kblocks;
+      uint32_t idesc = p.idesc;
+      if (p.groups) {
+        kblocks = p.groups[td & 0xFFFF].kblocks;
+        idesc = p.groups[td & 0xFFFF].idesc;
+      }
       for (int kb = 0; kb < kblocks; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t r = (uint32_t)(it / STAGES);
@@ -365,9 +376,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kk = 0; kk < 4; ++kk) {
           // advance 32 bytes (16 bf16 or 32 fp8) along K inside the swizzle atom
           if constexpr (FP8)
-            mma_fp8(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
+            mma_fp8(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
           else
-            mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
+            mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
         }
         issued = true;
         mma_commit(empty_bar(s));
@@ -399,12 +410,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int r = a_row + row_in_tile;
       void* out = p.out;
       int npad = p.npad;
+      int bn = p.bn;
       if (p.groups) {
         out = p.groups[g].out;
         npad = p.groups[g].npad;
+        bn = p.groups[g].bn;
       }
       const uint32_t taddr = tmem_base + (uint32_t)(acc * MAX_BN) + ((uint32_t)(q * 32) << 16);
-      for (int c = 0; c < p.bn / 32; ++c) {
+      for (int c = 0; c < bn / 32; ++c) {
         float v[32];
         tmem_ld32(taddr + (uint32_t)(c * 32), v);
         if (p.mode == MODE_SQUARE) {
@@ -653,14 +666,16 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8);
 }
 
-int tc_group_square(TcGroup* g, const void* level, void* out, int np) {
+int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn) {
   std::memset(g, 0, sizeof(TcGroup));
-  if (np % 256 || np > 32768) return CDL_ERR_INVALID_ARG;
+  if ((bn != 128 && bn != 256) || np % bn || np > 32768) return CDL_ERR_INVALID_ARG;
   CDL_TRY(make_map(&g->mapA, level, np, np, 128));
-  CDL_TRY(make_map(&g->mapB, level, np, np, 256));
+  CDL_TRY(make_map(&g->mapB, level, np, np, bn));
   g->out = out;
   g->npad = np;
   g->kblocks = np / BK;
+  g->bn = bn;
+  g->idesc = make_idesc(bn);
   return CDL_OK;
 }
 
@@ -674,21 +689,30 @@ int tc_group_apply(TcGroup* g, const void* amat, const void* xop, float* out, in
   g->gate = gate;
   g->npad = np;
   g->kblocks = np / BK;
+  g->bn = bn;
+  g->idesc = make_idesc(bn);
   return CDL_OK;
 }
 
-// Upper-triangle 256-blocks of every graph, graphs ordered largest first.
-std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad) {
+// Upper-triangle blocks of every graph (256-blocks as two 128 x 256 tiles,
+// or 128 x 128 tiles), graphs ordered largest first.
+std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, const std::vector<int>& bn) {
   std::vector<int> order(npad.size());
   for (size_t g = 0; g < order.size(); ++g) order[g] = (int)g;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return npad[a] > npad[b]; });
   std::vector<uint32_t> v;
   for (int g : order) {
-    const int nb = npad[g] / 256;
-    for (int I = 0; I < nb; ++I)
-      for (int J = I; J < nb; ++J)
-        for (int h = 0; h < 2; ++h)
-          v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 23) | ((uint32_t)h << 30));
+    if (bn[g] == 128) {
+      const int nb = npad[g] / 128;
+      for (int I = 0; I < nb; ++I)
+        for (int J = I; J < nb; ++J) v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 24));
+    } else {
+      const int nb = npad[g] / 256;
+      for (int I = 0; I < nb; ++I)
+        for (int J = I; J < nb; ++J)
+          for (int h = 0; h < 2; ++h)
+            v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 23) | ((uint32_t)h << 30));
+    }
   }
   return v;
 }

@@ -189,3 +189,36 @@ def test_batched_invalid_arguments(G):
     assert call(n_=np.array([64, 40000], dtype=np.int64)) == inv
     assert call(X1=np.zeros((128, 8))) == inv          # host pointer with host_io = 0
     assert call(Fp=None) == inv
+
+
+def test_batched_autotuner_and_every_variant(G, ragged):
+    """The plan's tuner times every squaring and projection variant and keeps
+    the fastest; every variant, forced through the test hook, gives the same
+    node scores (to 1e-12) and passes the oracle check."""
+    cdl = G.cdl
+    pairs = ragged[:4] + ragged[6:]           # orders 672..1023 and 257, 300 (padded orders 384..1024)
+    F0, t0, s0 = _run(G, pairs, d=8, topk=5, score=cdl.CDL_F32)
+    st, info = cdl.cdl_batch_plan_info(G.h)
+    assert st == 0 and info.ready == 1
+    assert info.n_square_variants >= 2 and info.n_project_variants >= 2
+    sq_ms = [info.square_variant_ms[v] for v in range(info.n_square_variants)]
+    pj_ms = [info.project_variant_ms[v] for v in range(info.n_project_variants)]
+    assert all(m > 0 for m in sq_ms + pj_ms)
+    best_sq = info.square_variant_max_npad_128[int(np.argmin(sq_ms))]
+    best_pj = info.project_variant_rows[int(np.argmin(pj_ms))]
+    assert info.square_max_npad_128 == best_sq and info.project_rows_per_block == best_pj
+    _check(pairs, F0, t0, s0, 5)
+    try:
+        for sv in range(info.n_square_variants):
+            for pv in range(info.n_project_variants):
+                assert cdl.cdl_ctx_set_debug(G.h, cdl.CDL_DEBUG_BATCH_VARIANT | (sv << 8) | (pv << 12)) == 0
+                # a plan key change forces a new plan built under the hook
+                F, t, s = _run(G, pairs, d=8, topk=5, score=cdl.CDL_F32, max_iter=29 - sv * 4 - pv)
+                for a, b in zip(F, F0):
+                    np.testing.assert_allclose(a, b, rtol=1e-12)
+                assert all(list(a) == list(b) for a, b in zip(t, t0))
+                st, inf2 = cdl.cdl_batch_plan_info(G.h)
+                assert inf2.square_max_npad_128 == info.square_variant_max_npad_128[sv]
+                assert inf2.project_rows_per_block == info.project_variant_rows[pv]
+    finally:
+        cdl.cdl_ctx_set_debug(G.h, 0)
