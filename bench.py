@@ -399,6 +399,85 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------- host levels
+def run_host_levels(args):
+    """The larger-than-memory form at the n = 32768 field pair: chain levels
+    in pinned host memory (CDL_CHAIN_HOST_LEVELS), streamed through two
+    device slots, against the same pair with device-resident levels. Reports
+    the bytes moved over the host link, the link's measured copy rates and
+    how much of the transfer time the step hides."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1802_05421_gb300 import build as B
+    B.build()
+    from paper_1802_05421_gb300 import cdl
+    wl = make_workload()
+    n, T = wl.X[0].shape
+    stream = torch.cuda.Stream()
+    st, ctx = cdl.cdl_ctx_create(0, stream.cuda_stream, 0)
+    assert st == 0
+    X1 = torch.from_numpy(wl.X[0]).cuda()
+    X2 = torch.from_numpy(wl.X[1]).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    top = torch.empty(TOPK, dtype=torch.int64, device="cuda")
+    s1, s2 = cdl.cdl_solve_stats(), cdl.cdl_solve_stats()
+
+    def timed(flags, steps, warmup):
+        o = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_BF16, cdl.CDL_F32, SEED, 0.0,
+                              cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0, flags)
+        for _ in range(warmup):
+            assert cdl.cdl_caddelag_pair(ctx, X1, X2, n, T, o, F, top, s1, s2) == 0
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            assert cdl.cdl_caddelag_pair(ctx, X1, X2, n, T, o, F, top, s1, s2) == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, F.cpu().numpy().copy(), top.cpu().tolist(), (s1.iters, s2.iters)
+
+    sampler = ClockSampler(0)
+    ms_dev, F_dev, top_dev, it_dev = timed(0, max(1, args.steps), args.warmup)
+    ms_host, F_host, top_host, it_host = timed(cdl.CDL_CHAIN_HOST_LEVELS, max(1, args.steps), args.warmup)
+    clocks = sampler.stop()
+    # link copy rates with a pinned buffer of one level (npad^2 bf16)
+    npad = (n + 255) // 256 * 256
+    lb = npad * npad * 2
+    hbuf = torch.empty(lb, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(lb, dtype=torch.uint8, device="cuda")
+    rates = {}
+    for name, fn in (("h2d", lambda: dbuf.copy_(hbuf, non_blocking=True)),
+                     ("d2h", lambda: hbuf.copy_(dbuf, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        rates[name] = 5 * lb / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    # per graph: d - 1 squared levels + level 0 out; every application reads d levels in
+    out_b = 2 * D_CHAIN * lb
+    in_b = sum(it_host) * D_CHAIN * lb
+    t_link = out_b / (rates["d2h"] * 1e9) + in_b / (rates["h2d"] * 1e9)
+    hidden = 1.0 - max(0.0, (ms_host - ms_dev) * 1e-3) / t_link if t_link > 0 else None
+    line = {"metric": METRIC + " (chain levels in pinned host memory)", "value": 1000.0 / ms_host,
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_host,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "T": T, "k": K_PROJ, "d": D_CHAIN, "chain_flags": "HOST_LEVELS",
+                       "level_bytes": lb, "host_level_bytes": D_CHAIN * lb, "solve_iters": list(it_host)},
+            "device_levels_ms_per_step": ms_dev,
+            "identical_to_device_levels": bool(np.array_equal(F_dev, F_host) and top_dev == top_host),
+            "link": {"bytes_to_host": out_b, "bytes_to_device": in_b, "h2d_gbs": rates["h2d"],
+                     "d2h_gbs": rates["d2h"], "transfer_s_at_measured_rates": t_link,
+                     "fraction_hidden": hidden},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    cdl.cdl_ctx_destroy(ctx)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -415,8 +494,9 @@ def main():
                     help="run a small single-kernel case for a profiler capture instead of the bench")
     ap.add_argument("--n", type=int, default=12288)
     ap.add_argument("--reps", type=int, default=1)
-    ap.add_argument("--workload", default="pair", choices=["pair", "batched"],
-                    help="pair: the n = 32768 field pair (default); batched: 64 ragged pairs")
+    ap.add_argument("--workload", default="pair", choices=["pair", "batched", "host-levels"],
+                    help="pair: the n = 32768 field pair (default); batched: 64 ragged pairs; "
+                         "host-levels: the pair with chain levels in pinned host memory")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -426,6 +506,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "host-levels":
+        return run_host_levels(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

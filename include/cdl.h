@@ -186,8 +186,15 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  *   storage is reused; any other chain returns CDL_ERR_INVALID_ARG.
  * Levels occupy d * npad^2 elements, npad = n rounded up to 256; bf16
  * chains also keep A as two bf16 matrices (A_hi + A_lo, 4 npad^2 bytes),
- * the operand of the solve's tensor-core residual update. */
-enum { CDL_CHAIN_DEFAULT = 0 };
+ * the operand of the solve's tensor-core residual update.
+ * CDL_CHAIN_HOST_LEVELS (bf16 chains): the levels live in pinned host memory
+ * (d * npad^2 * 2 bytes, allocated by the library) and two device slots of
+ * npad^2 bf16 hold the ones in use: each squaring writes level i + 1 to a
+ * slot that is copied to the host on a copy stream while the next squaring
+ * runs, and each application of the chain loads level l + 1 over the link
+ * while level l is applied. Results are identical to device levels;
+ * cdl_chain_level then returns host pointers (and waits for the copies). */
+enum { CDL_CHAIN_DEFAULT = 0, CDL_CHAIN_HOST_LEVELS = 1 };
 int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double* D,
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
                     int32_t flags, cdl_chain** inout);
@@ -303,6 +310,7 @@ typedef struct {
   int32_t host_io;         /* 1: X1, X2, F, top_idx are host pointers and
                               the call copies them in and out (synchronous);
                               0: device pointers (asynchronous)            */
+  int32_t chain_flags;     /* CDL_CHAIN_* flags of cdl_chain_build          */
 } cdl_pair_opts;
 
 /* One graph pair end to end (Alg. 4): graph build, chain, projection and

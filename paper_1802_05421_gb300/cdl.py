@@ -25,6 +25,7 @@ CDL_ERR_UNSUPPORTED = -6
 
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3 = 0, 1, 2, 3
 CDL_SOLVE_FULL_RESIDUAL = 1
+CDL_CHAIN_HOST_LEVELS = 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1
 CDL_DEBUG_BATCH_VARIANT = 2
 
@@ -46,7 +47,7 @@ class cdl_solve_stats(ctypes.Structure):
 class cdl_pair_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("d", ctypes.c_int32), ("chain_dtype", ctypes.c_int),
                 ("score_dtype", ctypes.c_int), ("seed", ctypes.c_uint64), ("sigma", ctypes.c_double), ("solve", cdl_solve_opts),
-                ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32)]
+                ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32), ("chain_flags", ctypes.c_int32)]
 
 
 class cdl_batch_opts(ctypes.Structure):

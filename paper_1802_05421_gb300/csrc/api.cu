@@ -278,7 +278,10 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
 int cdl_chain_free(cdl_chain* ch) {
   if (!ch) return CDL_OK;
   cudaSetDevice(ch->device);
-  cudaFree(ch->levels);
+  if (ch->host_levels)
+    ooc_destroy(ch);
+  else
+    cudaFree(ch->levels);
   cudaFree(ch->aop);
   cudaFree(ch->levels16);
   cudaFree(ch->amax);
@@ -292,6 +295,7 @@ int cdl_chain_free(cdl_chain* ch) {
 
 int cdl_chain_level(const cdl_chain* ch, int32_t i, void** level, int64_t* npad) {
   if (!ch || i < 0 || i >= ch->d) return CDL_ERR_INVALID_ARG;
+  if (ch->host_levels) CDL_CUDA_TRY(cudaStreamSynchronize(ch->copy));   // copies to the host complete
   if (level) *level = ch->level(i);
   if (npad) *npad = ch->npad;
   return CDL_OK;
@@ -324,7 +328,9 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
                     int32_t flags, cdl_chain** inout) {
   if (!ctx || !inout) return CDL_ERR_INVALID_ARG;
-  if (n < 2 || n > (1 << 20) || d < 1 || d > 64 || flags != 0) return CDL_ERR_INVALID_ARG;
+  if (n < 2 || n > (1 << 20) || d < 1 || d > 64 || (flags & ~CDL_CHAIN_HOST_LEVELS)) return CDL_ERR_INVALID_ARG;
+  const bool host_levels = (flags & CDL_CHAIN_HOST_LEVELS) != 0;
+  if (host_levels && chain_dtype != CDL_BF16) return CDL_ERR_UNSUPPORTED;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
   if (chain_dtype != CDL_F64 && chain_dtype != CDL_F32 && chain_dtype != CDL_BF16 &&
       chain_dtype != CDL_FP8E4M3)
@@ -338,7 +344,8 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
   const int64_t npad = round_up(n, 256);
   cdl_chain* ch = *inout;
   if (ch) {
-    if (ch->n != n || ch->d != d || ch->dtype != chain_dtype || ch->device != ctx->device)
+    if (ch->n != n || ch->d != d || ch->dtype != chain_dtype || ch->device != ctx->device ||
+        ch->host_levels != host_levels)
       return CDL_ERR_INVALID_ARG;
   } else {
     ch = new cdl_chain();
@@ -348,7 +355,7 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     ch->d = d;
     ch->dtype = chain_dtype;
     ch->elem = chain_dtype == CDL_F64 ? 8 : chain_dtype == CDL_F32 ? 4 : chain_dtype == CDL_BF16 ? 2 : 1;
-    size_t bytes = (size_t)d * npad * npad * ch->elem;
+    size_t bytes = host_levels ? 2 * (size_t)npad * npad * ch->elem : (size_t)d * npad * npad * ch->elem;
     const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
     const size_t l16_bytes = chain_dtype == CDL_FP8E4M3 ? (size_t)d * npad * npad * 2 : 0;
     const size_t ahl_bytes = 2 * (size_t)n * n * sizeof(float);
@@ -360,7 +367,7 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
         (aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
         (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
                        cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||
-        cudaMalloc(&ch->levels, bytes) != cudaSuccess ||
+        (host_levels ? ooc_init(ch) != CDL_OK : cudaMalloc(&ch->levels, bytes) != cudaSuccess) ||
         cudaMalloc(&ch->rsqrt_d, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->D, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->vol, sizeof(double)) != cudaSuccess) {
@@ -475,7 +482,8 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
   const double* Xs[2] = {x1, x2};
   cdl_solve_stats* sts[2] = {stats1, stats2};
   if (ctx->pair_chain && (ctx->pair_chain->n != n || ctx->pair_chain->d != o->d ||
-                          ctx->pair_chain->dtype != o->chain_dtype)) {
+                          ctx->pair_chain->dtype != o->chain_dtype ||
+                          ctx->pair_chain->host_levels != ((o->chain_flags & CDL_CHAIN_HOST_LEVELS) != 0))) {
     CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     cdl_chain_free(ctx->pair_chain);
     ctx->pair_chain = nullptr;
@@ -483,7 +491,7 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
   bool converged = true;
   for (int g = 0; g < 2; ++g) {
     CDL_TRY(graph_build(ctx, Xs[g], n, T, o->sigma, As[g], Ds[g], sc + g, sc + 2 + g));
-    CDL_TRY(cdl_chain_build(ctx, As[g], CDL_F64, Ds[g], sc + g, n, o->d, o->chain_dtype, 0,
+    CDL_TRY(cdl_chain_build(ctx, As[g], CDL_F64, Ds[g], sc + g, n, o->d, o->chain_dtype, o->chain_flags,
                             &ctx->pair_chain));
     CDL_TRY(project(ctx, As[g], n, o->k, o->seed, static_cast<double*>(dY)));
     int st = chain_solve(ctx, ctx->pair_chain, As[g], static_cast<double*>(dY), o->k, &o->solve,

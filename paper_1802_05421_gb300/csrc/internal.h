@@ -87,6 +87,16 @@ struct cdl_chain {
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
+  // CDL_CHAIN_HOST_LEVELS: `levels` is pinned host memory; two device slots
+  // hold the levels in use, filled and drained on a copy stream.
+  bool host_levels = false;
+  void* slot[2] = {nullptr, nullptr};
+  int slot_level[2] = {-1, -1};
+  int last_level = -1;                            // level written or read last
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // slot content complete
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};    // slot's last copy-out or reader done
+  double link_bytes = 0;                          // host <-> device bytes moved
   void* level(int i) const {
     return static_cast<char*>(levels) + (size_t)i * (size_t)npad * (size_t)npad * elem;
   }
@@ -133,6 +143,19 @@ int chain_square_simt(cdl_ctx* ctx, cdl_chain* ch, int level);
 int fp8_level_bound(cdl_ctx* ctx, cdl_chain* ch, int level);
 int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void* partial,
                int k, int splits);
+// ooc.cu: levels in pinned host memory (bf16 chains)
+int ooc_init(cdl_chain* ch);
+void ooc_destroy(cdl_chain* ch);
+// Device slot to write level i into (waits until the slot's old level is
+// saved and read); ooc_write_end saves it to the host on the copy stream.
+void* ooc_write_begin(cdl_ctx* ctx, cdl_chain* ch, int i);
+int ooc_write_end(cdl_ctx* ctx, cdl_chain* ch, int i);
+// Device copy of level i for reading on ctx->stream (loaded if no slot holds
+// it); ooc_read_done marks the end of the reads; ooc_prefetch starts a load
+// without waiting for it.
+const void* ooc_read(cdl_ctx* ctx, cdl_chain* ch, int i);
+int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i);
+int ooc_prefetch(cdl_chain* ch, int i);
 // tc_gemm.cu
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
 // Grouped (batched) tcgen05 launches: one launch over the tiles of many

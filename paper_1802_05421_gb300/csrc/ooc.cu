@@ -1,0 +1,120 @@
+// Chain levels kept in pinned host memory (the larger-than-memory form: the
+// paper's larger-than-memory aim; here the host holds the levels and the GPU
+// streams them). Two device slots hold the levels in use. A squaring reads
+// level i from one slot and writes level i + 1 into the other, which is then
+// copied out to the host on a copy stream while the next squaring runs; an
+// application of the chain loads level l + 1 into the free slot while level l
+// is applied. Events order every slot reuse: a slot is overwritten only after
+// its previous level has been copied out and its last reader has finished.
+#include "internal.h"
+
+namespace cdl {
+
+namespace {
+size_t level_bytes(const cdl_chain* ch) { return (size_t)ch->npad * (size_t)ch->npad * 2; }
+
+int slot_holding(const cdl_chain* ch, int i) {
+  for (int s = 0; s < 2; ++s)
+    if (ch->slot_level[s] == i) return s;
+  return -1;
+}
+
+// the slot a new level may go to: not the one holding the level used last
+int victim(const cdl_chain* ch) {
+  if (ch->last_level < 0) return 0;
+  return ch->slot_level[0] == ch->last_level ? 1 : 0;
+}
+
+// issue the load of level i into slot s on the copy stream
+int load(cdl_chain* ch, int i, int s) {
+  CDL_CUDA_TRY(cudaStreamWaitEvent(ch->copy, ch->ev_free[s], 0));
+  CDL_CUDA_TRY(cudaMemcpyAsync(ch->slot[s], ch->level(i), level_bytes(ch), cudaMemcpyHostToDevice, ch->copy));
+  CDL_CUDA_TRY(cudaEventRecord(ch->ev_ready[s], ch->copy));
+  ch->slot_level[s] = i;
+  ch->link_bytes += (double)level_bytes(ch);
+  return CDL_OK;
+}
+}  // namespace
+
+int ooc_init(cdl_chain* ch) {
+  const size_t lb = level_bytes(ch);
+  if (cudaHostAlloc(&ch->levels, (size_t)ch->d * lb, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    ch->levels = nullptr;
+    return CDL_ERR_OOM;
+  }
+  for (int s = 0; s < 2; ++s) {
+    if (cudaMalloc(&ch->slot[s], lb) != cudaSuccess || cudaEventCreateWithFlags(&ch->ev_ready[s], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ch->ev_free[s], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return CDL_ERR_OOM;
+    }
+  }
+  if (cudaStreamCreateWithFlags(&ch->copy, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return CDL_ERR_CUDA;
+  }
+  ch->host_levels = true;
+  return CDL_OK;
+}
+
+void ooc_destroy(cdl_chain* ch) {
+  if (ch->copy) cudaStreamSynchronize(ch->copy);
+  for (int s = 0; s < 2; ++s) {
+    if (ch->slot[s]) cudaFree(ch->slot[s]);
+    if (ch->ev_ready[s]) cudaEventDestroy(ch->ev_ready[s]);
+    if (ch->ev_free[s]) cudaEventDestroy(ch->ev_free[s]);
+    ch->slot[s] = nullptr;
+  }
+  if (ch->copy) cudaStreamDestroy(ch->copy);
+  ch->copy = nullptr;
+  if (ch->levels) cudaFreeHost(ch->levels);
+  ch->levels = nullptr;
+}
+
+void* ooc_write_begin(cdl_ctx* ctx, cdl_chain* ch, int i) {
+  int s = slot_holding(ch, i);
+  if (s < 0) s = victim(ch);
+  cudaStreamWaitEvent(ctx->stream, ch->ev_free[s], 0);   // old level saved / read
+  ch->slot_level[s] = i;
+  return ch->slot[s];
+}
+
+int ooc_write_end(cdl_ctx* ctx, cdl_chain* ch, int i) {
+  const int s = slot_holding(ch, i);
+  if (s < 0) return CDL_ERR_INVALID_ARG;
+  CDL_CUDA_TRY(cudaEventRecord(ch->ev_ready[s], ctx->stream));
+  CDL_CUDA_TRY(cudaStreamWaitEvent(ch->copy, ch->ev_ready[s], 0));
+  CDL_CUDA_TRY(cudaMemcpyAsync(ch->level(i), ch->slot[s], level_bytes(ch), cudaMemcpyDeviceToHost, ch->copy));
+  CDL_CUDA_TRY(cudaEventRecord(ch->ev_free[s], ch->copy));
+  ch->link_bytes += (double)level_bytes(ch);
+  ch->last_level = i;
+  return CDL_OK;
+}
+
+const void* ooc_read(cdl_ctx* ctx, cdl_chain* ch, int i) {
+  int s = slot_holding(ch, i);
+  if (s < 0) {
+    s = victim(ch);
+    if (load(ch, i, s) != CDL_OK) return nullptr;
+  }
+  if (cudaStreamWaitEvent(ctx->stream, ch->ev_ready[s], 0) != cudaSuccess) return nullptr;
+  return ch->slot[s];
+}
+
+int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i) {
+  const int s = slot_holding(ch, i);
+  if (s < 0) return CDL_ERR_INVALID_ARG;
+  CDL_CUDA_TRY(cudaEventRecord(ch->ev_free[s], ctx->stream));
+  ch->last_level = i;
+  return CDL_OK;
+}
+
+// Issued after ooc_read_done of the level in use, so a load into its slot
+// (a chain of one level) waits for that reader.
+int ooc_prefetch(cdl_chain* ch, int i) {
+  if (slot_holding(ch, i) >= 0) return CDL_OK;
+  return load(ch, i, victim(ch));
+}
+
+}  // namespace cdl

@@ -643,9 +643,16 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   CDL_TRY(get_tiles(ctx, "tc.square." + std::to_string(nb), [&] { return square_tiles(nb); }, &tiles, &count));
   const bool fp8 = ch->dtype == CDL_FP8E4M3;
   const int elem = fp8 ? 1 : 2;
+  const void* in = ch->level(level);
+  void* out = ch->level(level + 1);
+  if (ch->host_levels) {   // level `level` is in a slot (just written); level + 1 goes to the other
+    in = ooc_read(ctx, ch, level);
+    out = ooc_write_begin(ctx, ch, level + 1);
+    if (!in) return CDL_ERR_CUDA;
+  }
   CUtensorMap ma, mb;
-  CDL_TRY(make_map(&ma, ch->level(level), np, np, 128, elem));
-  CDL_TRY(make_map(&mb, ch->level(level), np, np, 256, elem));
+  CDL_TRY(make_map(&ma, in, np, np, 128, elem));
+  CDL_TRY(make_map(&mb, in, np, np, 256, elem));
   TcParams p;
   p.tiles = tiles;
   p.num_tiles = count;
@@ -654,7 +661,7 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   p.idesc = make_idesc(256, fp8);
   p.mode = fp8 ? MODE_SQUARE_FP8 : MODE_SQUARE;
   p.npad = np;
-  p.out = ch->level(level + 1);
+  p.out = out;
   p.ldo = np;
   p.status = ctx->dev_status;
   p.amax = ch->amax;
@@ -663,7 +670,8 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   p.debug_withhold_load = ctx->debug_flags & 1;
   p.groups = nullptr;
   const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
-  return launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8);
+  CDL_TRY(launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8));
+  return ch->host_levels ? ooc_write_end(ctx, ch, level + 1) : CDL_OK;
 }
 
 int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn) {
@@ -761,7 +769,13 @@ int tc_apply_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgr
 
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial, int kp,
              int splits) {
-  return apply_tc_mat(ctx, ch->level16(level), (int)ch->npad, xop, partial, kp, splits);
+  if (!ch->host_levels) return apply_tc_mat(ctx, ch->level16(level), (int)ch->npad, xop, partial, kp, splits);
+  cdl_chain* mch = const_cast<cdl_chain*>(ch);   // slot bookkeeping only
+  const void* lv = ooc_read(ctx, mch, level);
+  if (!lv) return CDL_ERR_CUDA;
+  CDL_TRY(apply_tc_mat(ctx, lv, (int)ch->npad, xop, partial, kp, splits));
+  CDL_TRY(ooc_read_done(ctx, mch, level));
+  return ooc_prefetch(mch, (level + 1) % ch->d);   // overlaps the next level's load with this update
 }
 
 int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp, int splits) {

@@ -67,10 +67,10 @@ class Ctx:
         self.check(self.cdl.cdl_sync(self.h))
         return Y
 
-    def chain(self, A, D, vol, d, dtype, chain=None):
+    def chain(self, A, D, vol, d, dtype, chain=None, flags=0):
         n = A.shape[0]
         st, ch = self.cdl.cdl_chain_build(self.h, A, self.cdl.CDL_F64, D, vol.data_ptr(), n, d, dtype,
-                                          0, chain)
+                                          flags, chain)
         self.check(st)
         self.check(self.cdl.cdl_sync(self.h))
         return ch
@@ -79,6 +79,14 @@ class Ctx:
         st, ptr, npad = self.cdl.cdl_chain_level(ch, i)
         self.check(st)
         return view_device(ptr, (npad, npad), dtype)
+
+    def host_level(self, ch, i):
+        """Level i of a chain with host levels, as a bf16-valued float64 array."""
+        import ctypes
+        st, ptr, npad = self.cdl.cdl_chain_level(ch, i)
+        self.check(st)
+        raw = np.ctypeslib.as_array((ctypes.c_uint16 * (npad * npad)).from_address(ptr)).copy()
+        return (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64).reshape(npad, npad)
 
     def level16(self, ch, i):
         """bf16 view of level i read by the apply, as float64 on the host."""
@@ -116,11 +124,11 @@ class Ctx:
         return F, top[:topk]
 
     def pair(self, X1, X2, k, d, chain_dtype, score_dtype, seed, topk, max_iter=30, rel_tol=1e-10,
-             host_io=False, sigma=0.0):
+             host_io=False, sigma=0.0, chain_flags=0):
         cdl = self.cdl
         n, T = X1.shape
         opts = cdl.cdl_pair_opts(k, d, chain_dtype, score_dtype, seed, sigma,
-                                 cdl.cdl_solve_opts(max_iter, rel_tol, 0), topk, int(host_io))
+                                 cdl.cdl_solve_opts(max_iter, rel_tol, 0), topk, int(host_io), chain_flags)
         s1, s2 = cdl.cdl_solve_stats(), cdl.cdl_solve_stats()
         if host_io:
             F = np.empty(n)
