@@ -485,7 +485,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdl", choices=["cdl", "reference"])
-    ap.add_argument("--chain", default="bf16", choices=["bf16", "fp8", "f32", "f64"])
+    ap.add_argument("--chain", default="bf16", choices=["bf16", "fp8", "fp8t", "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-compare-f32", dest="compare_f32", action="store_false",
@@ -527,7 +527,8 @@ def main():
     stream = torch.cuda.Stream()
     st, ctx = cdl.cdl_ctx_create(local, stream.cuda_stream, 0)
     assert st == 0, cdl.cdl_status_string(st)
-    chain = {"bf16": cdl.CDL_BF16, "fp8": cdl.CDL_FP8E4M3, "f32": cdl.CDL_F32, "f64": cdl.CDL_F64}[args.chain]
+    chain = {"bf16": cdl.CDL_BF16, "fp8": cdl.CDL_FP8E4M3, "fp8t": cdl.CDL_FP8E4M3_T128, "f32": cdl.CDL_F32,
+             "f64": cdl.CDL_F64}[args.chain]
     score = cdl.CDL_F64 if args.chain == "f64" else cdl.CDL_F32
     X1 = torch.from_numpy(wl.X[0]).cuda()
     X2 = torch.from_numpy(wl.X[1]).cuda()
@@ -617,9 +618,10 @@ def main():
         peak = None
         if args.chain == "bf16":
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        elif args.chain == "fp8":   # measured bf16 peak x the nominal fp8/bf16 dense ratio (4.5 / 2.25)
+        elif args.chain in ("fp8", "fp8t"):   # measured bf16 peak x the nominal fp8/bf16 dense ratio (4.5 / 2.25)
             peak = 2.0 * pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        roof = {"kernel": "k_tc_gemm (chain squaring)" if args.chain in ("bf16", "fp8") else "k_gemm_tn (chain squaring)",
+        kname = {"bf16": "k_tc_gemm", "fp8": "k_tc_gemm<fp8>", "fp8t": "k_tc_fp8t"}.get(args.chain, "k_gemm_tn")
+        roof = {"kernel": kname + " (chain squaring)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if peak else None, "traffic": None,
                 "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside a long step)",

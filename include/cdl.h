@@ -54,7 +54,8 @@ typedef enum {
   CDL_F64 = 0,      /* IEEE binary64                                    */
   CDL_F32 = 1,      /* IEEE binary32                                    */
   CDL_BF16 = 2,     /* bfloat16, tensor-core chain (tcgen05)            */
-  CDL_FP8E4M3 = 3   /* float8 e4m3 with one scale per level (tcgen05)   */
+  CDL_FP8E4M3 = 3,  /* float8 e4m3 with one scale per level (tcgen05)   */
+  CDL_FP8E4M3_T128 = 4  /* float8 e4m3, one scale per 128 x 128 tile    */
 } cdl_dtype;
 
 typedef struct cdl_ctx cdl_ctx;
@@ -179,7 +180,11 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  *   scale per level: level i stores value / s_i, s_i = m_i / 448 where m_0 =
  *   max |S~_0| and m_{i+1} = max_r |row r of S~_i|^2 bounds every entry of
  *   S~_i^2 (|(S S)_ab| <= |row a| |row b|; attained on the diagonal); a bf16
- *   copy of each level is kept for the solve's apply).
+ *   copy of each level is kept for the solve's apply), or CDL_FP8E4M3_T128
+ *   (e4m3 levels with one scale per 128 x 128 tile, scale = tile max / 448:
+ *   each K-tile product runs on tcgen05 kind::f8f6f4 into TMEM and is added
+ *   to float32 accumulators times s_IK s_KJ; the finished tile's maximum sets
+ *   its scale; bf16 copies kept for the apply).
  * flags: CDL_CHAIN_* below.
  * inout: if *inout is NULL a chain is allocated (cdl_chain_free releases it);
  *   if it points to a chain created with the same (n, d, chain_dtype) its
@@ -203,8 +208,13 @@ int cdl_chain_free(cdl_chain* chain);
 int cdl_chain_level(const cdl_chain* chain, int32_t i, void** level, int64_t* npad);
 /* Device pointer to the bf16 view of level i that the solve's tensor-core
  * apply reads (npad x npad): the level itself for CDL_BF16 chains, its bf16
- * copy for CDL_FP8E4M3 chains; NULL (and CDL_ERR_INVALID_ARG) otherwise. */
+ * copy for CDL_FP8E4M3 and CDL_FP8E4M3_T128 chains; NULL (and
+ * CDL_ERR_INVALID_ARG) otherwise. */
 int cdl_chain_apply_level(const cdl_chain* chain, int32_t i, void** level);
+/* CDL_FP8E4M3_T128 chains: device pointer to the nt x nt float32 tile scales
+ * of level i (nt = npad / 128; value of tile (I, J) = scale[I nt + J] times
+ * the stored e4m3 values). CDL_ERR_INVALID_ARG for other chains. */
+int cdl_chain_tile_scales(const cdl_chain* chain, int32_t i, float** scales, int64_t* nt);
 /* Scale of level i: stored value times *scale is the level's value (1 for
  * every dtype but CDL_FP8E4M3). Synchronises the chain's device. */
 int cdl_chain_level_scale(const cdl_chain* chain, int32_t i, double* scale);

@@ -23,7 +23,7 @@ CDL_ERR_NOT_CONVERGED = -4
 CDL_ERR_TIMEOUT = -5
 CDL_ERR_UNSUPPORTED = -6
 
-CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3 = 0, 1, 2, 3
+CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3, CDL_FP8E4M3_T128 = 0, 1, 2, 3, 4
 CDL_SOLVE_FULL_RESIDUAL = 1
 CDL_CHAIN_HOST_LEVELS = 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1
@@ -91,6 +91,7 @@ _SIGS = {
     "cdl_chain_level": [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
     "cdl_chain_level_scale": [_P, _I32, ctypes.POINTER(_D)],
     "cdl_chain_apply_level": [_P, _I32, ctypes.POINTER(_P)],
+    "cdl_chain_tile_scales": [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
     "cdl_project": [_P, _P, ctypes.c_int, _I64, _I32, ctypes.c_uint64, _P],
     "cdl_chain_solve": [_P, _P, _P, ctypes.c_int, _P, _I32, ctypes.POINTER(cdl_solve_opts), _P,
                         ctypes.POINTER(cdl_solve_stats)],
@@ -206,6 +207,14 @@ def cdl_chain_apply_level(chain, i):
     p = _P()
     st = _lib.cdl_chain_apply_level(chain, i, ctypes.byref(p))
     return st, p.value
+
+
+def cdl_chain_tile_scales(chain, i):
+    """Returns (status, device pointer to the nt x nt float32 tile scales, nt)."""
+    p = _P()
+    nt = _I64()
+    st = _lib.cdl_chain_tile_scales(chain, i, ctypes.byref(p), ctypes.byref(nt))
+    return st, p.value, nt.value
 
 
 def cdl_chain_level_scale(chain, i):

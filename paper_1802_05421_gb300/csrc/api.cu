@@ -286,6 +286,7 @@ int cdl_chain_free(cdl_chain* ch) {
   cudaFree(ch->levels16);
   cudaFree(ch->amax);
   cudaFree(ch->ahl);
+  cudaFree(ch->tscale);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
   cudaFree(ch->vol);
@@ -305,8 +306,16 @@ int cdl_chain_apply_level(const cdl_chain* ch, int32_t i, void** level) {
   if (!level) return CDL_ERR_INVALID_ARG;
   *level = nullptr;
   if (!ch || i < 0 || i >= ch->d) return CDL_ERR_INVALID_ARG;
-  if (ch->dtype != CDL_BF16 && ch->dtype != CDL_FP8E4M3) return CDL_ERR_INVALID_ARG;
+  if (ch->dtype != CDL_BF16 && ch->dtype != CDL_FP8E4M3 && ch->dtype != CDL_FP8E4M3_T128) return CDL_ERR_INVALID_ARG;
   *level = ch->level16(i);
+  return CDL_OK;
+}
+
+int cdl_chain_tile_scales(const cdl_chain* ch, int32_t i, float** scales, int64_t* nt) {
+  if (!ch || !scales || i < 0 || i >= ch->d || ch->dtype != CDL_FP8E4M3_T128) return CDL_ERR_INVALID_ARG;
+  const int64_t t = ch->npad / 128;
+  *scales = ch->tscale + (size_t)i * t * t;
+  if (nt) *nt = t;
   return CDL_OK;
 }
 
@@ -333,13 +342,14 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
   if (host_levels && chain_dtype != CDL_BF16) return CDL_ERR_UNSUPPORTED;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
   if (chain_dtype != CDL_F64 && chain_dtype != CDL_F32 && chain_dtype != CDL_BF16 &&
-      chain_dtype != CDL_FP8E4M3)
+      chain_dtype != CDL_FP8E4M3 && chain_dtype != CDL_FP8E4M3_T128)
     return CDL_ERR_INVALID_ARG;
+  const bool fp8t = chain_dtype == CDL_FP8E4M3_T128;
   CDL_TRY(set_device(ctx));
   CDL_TRY(dev_ptr(ctx, A));
   CDL_TRY(dev_ptr(ctx, D));
   CDL_TRY(dev_ptr(ctx, vol));
-  const bool tensor = chain_dtype == CDL_BF16 || chain_dtype == CDL_FP8E4M3;
+  const bool tensor = chain_dtype == CDL_BF16 || chain_dtype == CDL_FP8E4M3 || fp8t;
   if (tensor && !tc_supported(ctx)) return CDL_ERR_UNSUPPORTED;
   const int64_t npad = round_up(n, 256);
   cdl_chain* ch = *inout;
@@ -357,7 +367,8 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     ch->elem = chain_dtype == CDL_F64 ? 8 : chain_dtype == CDL_F32 ? 4 : chain_dtype == CDL_BF16 ? 2 : 1;
     size_t bytes = host_levels ? 2 * (size_t)npad * npad * ch->elem : (size_t)d * npad * npad * ch->elem;
     const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
-    const size_t l16_bytes = chain_dtype == CDL_FP8E4M3 ? (size_t)d * npad * npad * 2 : 0;
+    const size_t l16_bytes = (chain_dtype == CDL_FP8E4M3 || fp8t) ? (size_t)d * npad * npad * 2 : 0;
+    const size_t ts_bytes = fp8t ? (size_t)d * (npad / 128) * (npad / 128) * sizeof(float) : 0;
     const size_t ahl_bytes = 2 * (size_t)n * n * sizeof(float);
     if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes + l16_bytes + ahl_bytes > ctx->ws_cap) {
       delete ch;
@@ -367,6 +378,7 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
         (aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
         (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
                        cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||
+        (ts_bytes && cudaMalloc(&ch->tscale, ts_bytes) != cudaSuccess) ||
         (host_levels ? ooc_init(ch) != CDL_OK : cudaMalloc(&ch->levels, bytes) != cudaSuccess) ||
         cudaMalloc(&ch->rsqrt_d, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->D, npad * sizeof(double)) != cudaSuccess ||
@@ -383,7 +395,8 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
   int st = chain_init(ctx, ch, static_cast<const double*>(A));
   for (int i = 0; st == CDL_OK && i + 1 < d; ++i) {
     if (chain_dtype == CDL_FP8E4M3) st = fp8_level_bound(ctx, ch, i);
-    if (st == CDL_OK) st = tensor ? chain_square_tc(ctx, ch, i) : chain_square_simt(ctx, ch, i);
+    if (st == CDL_OK)
+      st = fp8t ? chain_square_fp8t(ctx, ch, i) : tensor ? chain_square_tc(ctx, ch, i) : chain_square_simt(ctx, ch, i);
   }
   if (st != CDL_OK) {
     if (!*inout) cdl_chain_free(ch);

@@ -372,6 +372,12 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
                                                               cnt, ch->amax, static_cast<uint8_t*>(ch->level(0)));
       return L3.done();
     }
+    case CDL_FP8E4M3_T128:
+      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
+          A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(ch->level16(0)), static_cast<__nv_bfloat16*>(ch->aop),
+          static_cast<__nv_bfloat16*>(ch->aop) + (size_t)np * np);
+      CDL_TRY(L.done());
+      return fp8t_quantize_level0(ctx, ch);
     case CDL_BF16: {
       void* L0 = ch->host_levels ? ooc_write_begin(ctx, ch, 0) : ch->level(0);
       k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(

@@ -84,6 +84,7 @@ struct cdl_chain {
   void* levels16 = nullptr;   // fp8 chains: bf16 copies of the levels (the apply's operand)
   unsigned* amax = nullptr;   // fp8 chains: per-level bound of |value| (float bits), scale = amax/448
   float* ahl = nullptr;       // A as float hi + lo planes (n x n each), the float-float residual's operand
+  float* tscale = nullptr;    // per-tile e4m3 chains: d x (npad/128)^2 tile scales
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
@@ -158,6 +159,8 @@ int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i);
 int ooc_prefetch(cdl_chain* ch, int i);
 // tc_gemm.cu
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
+int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level);
+int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch);
 // Grouped (batched) tcgen05 launches: one launch over the tiles of many
 // graphs. Each graph's tensor maps, output and k-loop length sit in a device
 // array of TcGroup; `host_first` is the host copy of entry 0.

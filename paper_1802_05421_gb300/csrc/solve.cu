@@ -717,7 +717,8 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   cudaStream_t st = ctx->stream;
   const int n = (int)ch->n, np = (int)ch->npad;
   const int kp = (int)round_up(k, 16);   // tensor-core N = 2 kp: multiple of 32
-  const bool bf16 = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3;   // tensor-core apply
+  const bool bf16 = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3 ||
+                    ch->dtype == CDL_FP8E4M3_T128;   // tensor-core apply
   const size_t xe = ch->dtype == CDL_F64 ? 8 : 4;
   const int kblocks = np / 64;
   int splits;

@@ -96,11 +96,23 @@ class Ctx:
         return view_device(ptr, (npad, npad), "bf16").double().cpu().numpy()
 
     def level_values(self, ch, i, dtype):
-        """Level i as float64 values on the host (fp8 levels times their scale)."""
+        """Level i as float64 values on the host (fp8 levels times their
+        scale; "fp8t" levels times their 128 x 128 tile scales)."""
+        if dtype == "fp8t":
+            v = self.level(ch, i, "fp8").double().cpu().numpy()
+            st, ptr, nt = self.cdl.cdl_chain_tile_scales(ch, i)
+            self.check(st)
+            sc = view_device(ptr, (nt, nt), np.float32).double().cpu().numpy()
+            return v * np.kron(sc, np.ones((128, 128)))
         v = self.level(ch, i, dtype).double().cpu().numpy()
         st, sc = self.cdl.cdl_chain_level_scale(ch, i)
         self.check(st)
         return v * sc
+
+    def tile_scales(self, ch, i):
+        st, ptr, nt = self.cdl.cdl_chain_tile_scales(ch, i)
+        self.check(st)
+        return view_device(ptr, (nt, nt), np.float32).double().cpu().numpy()
 
     def solve(self, ch, A, Y, max_iter=20, rel_tol=1e-10, expect=0, flags=0):
         cdl = self.cdl

@@ -95,10 +95,11 @@ def _deflated_levels(Ao, d):
     return [L - np.outer(u, u) for L in O.chain_levels(Ao, d)]
 
 
-DT = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
+DT = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3, "fp8t": 4}
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 3e-2), ("fp8", 0.2)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 3e-2), ("fp8", 0.2),
+                                       ("fp8t", 0.1)])
 @pytest.mark.parametrize("n", [300, 1000])
 def test_chain_levels_match_oracle(G, dtype, tol, n):
     cdl = G.cdl
@@ -111,7 +112,8 @@ def test_chain_levels_match_oracle(G, dtype, tol, n):
         ref = _deflated_levels(_h(A), d)
         scale = np.linalg.norm(ref[0])
         for i in range(d):
-            Lg = G.level_values(ch, i, {"f64": np.float64, "f32": np.float32, "bf16": "bf16", "fp8": "fp8"}[dtype])
+            Lg = G.level_values(ch, i, {"f64": np.float64, "f32": np.float32, "bf16": "bf16", "fp8": "fp8",
+                                        "fp8t": "fp8t"}[dtype])
             assert np.all(Lg[n:, :] == 0) and np.all(Lg[:, n:] == 0)   # zero padding
             assert np.array_equal(Lg, Lg.T)                             # exact symmetry
             err = np.linalg.norm(Lg[:n, :n] - ref[i]) / scale
@@ -139,6 +141,42 @@ def test_tcgen05_square_is_exact_product_of_its_inputs(G, n):
     bound = 2.0 ** -8 * np.abs(R) + L0.shape[0] * 2.0 ** -23 * (np.abs(L0) @ np.abs(L0)) + 1e-30
     assert np.all(np.abs(L1 - R) <= bound)
     assert np.array_equal(L1, L1.T)
+
+
+@pytest.mark.parametrize("n", [300, 1000, 2100])
+def test_tcgen05_fp8_tile_square_is_exact_product_of_its_inputs(G, n):
+    """One e4m3 squaring with 128 x 128 tile scales against the float64
+    product of the same dequantized input: the bf16 copy may differ by the
+    float32 accumulation (per K-tile MMA plus the scaled promotion) and bf16
+    rounding; each output tile's scale is its maximum over 448 and its e4m3
+    values are the tile divided by the scale, rounded (2^-4 relative, or one
+    subnormal step of the tile)."""
+    cdl = G.cdl
+    X = iid_pair(n, 24, 1, seed=17).X[0]
+    A, D, vol, _ = G.graph(X)
+    ch = G.chain(A, D, vol, 2, cdl.CDL_FP8E4M3_T128)
+    try:
+        V0 = G.level_values(ch, 0, "fp8t")
+        V1 = G.level_values(ch, 1, "fp8t")
+        S1 = G.tile_scales(ch, 1)
+        L16 = G.level16(ch, 1)
+    finally:
+        cdl.cdl_chain_free(ch)
+    R = V0 @ V0
+    acc = V0.shape[0] * 2.0 ** -23 * (np.abs(V0) @ np.abs(V0))
+    assert np.all(np.abs(L16 - R) <= 2.0 ** -8 * np.abs(R) + acc + 1e-30)
+    s1 = np.kron(S1, np.ones((128, 128)))
+    assert np.all(np.abs(V1 - R) <= 2.0 ** -4 * np.abs(R) + s1 * 2.0 ** -9 + acc + 1e-30)
+    nt = S1.shape[0]
+    for I in range(nt):
+        for J in range(nt):
+            blk = np.s_[I * 128:(I + 1) * 128, J * 128:(J + 1) * 128]
+            m = np.abs(R[blk]).max()
+            if m > 0:
+                assert abs(448 * S1[I, J] - m) <= 2.0 ** -8 * m + acc[blk].max(), (I, J)
+            assert np.abs(V1[blk]).max() <= 448 * S1[I, J] * (1 + 1e-6)
+    assert np.array_equal(S1, S1.T)
+    assert np.array_equal(V1, V1.T) and np.array_equal(L16, L16.T)
 
 
 @pytest.mark.parametrize("n", [300, 1000, 2100])
@@ -286,6 +324,7 @@ def iid1024():
     ("bf16", "f32", 1e-6, False),
     ("bf16", "f32", 1e-6, True),
     ("fp8", "f32", 1e-6, False),
+    ("fp8t", "f32", 1e-6, False),
 ])
 def test_pair_iid_n1024_matches_oracle(G, iid1024, chain, score, tol, host_io):
     cdl = G.cdl
@@ -311,6 +350,20 @@ def test_pair_field_bf16_finds_patch(G):
     assert rel.max() <= 1e-6, rel.max()
     if O.min_relative_gap(out["F"], 16) > 1e-5:
         assert list(top) == list(out["top"])
+    assert len(set(top.tolist()) & set(wl.planted[0].tolist())) >= 12
+
+
+def test_pair_field_fp8_tiles_finds_patch(G):
+    """The field graph whose dynamic range defeats one scale per level: with
+    one scale per 128 x 128 tile the e4m3 chain preconditions the refinement
+    to the same tolerance and scores."""
+    cdl = G.cdl
+    wl = field_sequence(32, 64, 64, 2, patch=4, patch_transition=0, seed=5)
+    out = O.caddelag_pair(wl.X[0], wl.X[1], k=32, seed=1, topk=16)
+    F, top, s1, s2 = G.pair(wl.X[0], wl.X[1], 32, 10, cdl.CDL_FP8E4M3_T128, cdl.CDL_F32, 1, 16, max_iter=40)
+    assert s1.rel_res <= 1e-10 and s2.rel_res <= 1e-10
+    rel = np.abs(F - out["F"]) / out["F"]
+    assert rel.max() <= 1e-6, rel.max()
     assert len(set(top.tolist()) & set(wl.planted[0].tolist())) >= 12
 
 
