@@ -607,6 +607,37 @@ def main():
         f32 = {"value": 1000.0 / f32_ms, "unit": "pairs/s", "ms_per_step": f32_ms, "steps": 1, "warmup": 1,
                "same_top": tf.cpu().tolist() == top.cpu().tolist(), "max_rel_diff_F_vs_bf16": rel}
 
+    # e4m3 chain with 128 x 128 tile scales on the same pair
+    fp8t = None
+    if args.compare_f32 and args.chain == "bf16":
+        o8 = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_FP8E4M3_T128, cdl.CDL_F32, SEED, 0.0,
+                               cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0)
+        F8 = torch.empty(n, dtype=torch.float64, device="cuda")
+        t8 = torch.empty(TOPK, dtype=torch.int64, device="cuda")
+        step(o8, X1, X2, F8, t8)   # warm-up (allocates the e4m3 chain)
+        cdl.cdl_ctx_reset_counters(ctx)
+        cdl.cdl_ctx_set_timing(ctx, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(o8, X1, X2, F8, t8)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _, sq_ms, sq_cnt, sq_work = cdl.cdl_ctx_timing(ctx, cdl.CDL_KC_SQUARE)
+        cdl.cdl_ctx_set_timing(ctx, False)
+        f8_ms = e0.elapsed_time(e1)
+        pk8, _ = peaks()
+        peak8 = 2.0 * pk8.get("bf16_tflops_sustained", pk8.get("bf16_tflops"))
+        ach8 = (sq_work / max(sq_cnt, 1)) / (sq_ms / max(sq_cnt, 1) * 1e-3) / 1e12 if sq_ms else 0.0
+        fp8t = {"value": 1000.0 / f8_ms, "unit": "pairs/s", "ms_per_step": f8_ms, "steps": 1, "warmup": 1,
+                "solve_iters": [s1.iters, s2.iters], "rel_res": max(s1.rel_res, s2.rel_res),
+                "same_top": t8.cpu().tolist() == top.cpu().tolist(),
+                "max_rel_diff_F_vs_bf16": float(((F8 - F).abs() / F).max()),
+                "square_ms_per_launch": sq_ms / max(sq_cnt, 1),
+                "square_roofline": {"kernel": "k_tc_fp8t", "achieved": ach8, "peak": peak8, "unit": "TFLOP/s",
+                                    "frac": ach8 / peak8,
+                                    "peak_source": "2 x measured bf16_tflops_sustained (nominal e4m3/bf16 ratio)"}}
+
     # max over ranks
     step_ms, e2e_s = rank_max([step_ms, e2e_s], dist, "cuda")
     value = pairs_per_second(step_ms, world)
@@ -645,6 +676,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "f32_path": f32,
+            "fp8_tile_path": fp8t,
             "e2e": {"value": pairs_per_second(e2e_s * 1000.0, world), "unit": "pairs/s",
                     "h2d_bytes_per_step": 2 * n * T * 8,
                     "d2h_bytes_per_step": n * 8 + TOPK * 8, "same_top_as_device_run": same_top},
