@@ -231,8 +231,9 @@ def run_case(args):
     for _ in range(args.reps):
         assert cdl.cdl_build_graph(ctx, X, n, T, 0.0, cdl.CDL_F64, A, D, vol, sig) == 0
         if args.case in ("square", "solve"):
+            cdt = cdl.CDL_FP8E4M3_T128 if args.chain == "fp8t" else cdl.CDL_BF16
             st, ch = cdl.cdl_chain_build(ctx, A, cdl.CDL_F64, D, vol, n, 2 if args.case == "square" else 4,
-                                         cdl.CDL_BF16, 0, ch)
+                                         cdt, 0, ch)
             assert st == 0
         if args.case in ("project", "solve", "score"):
             assert cdl.cdl_project(ctx, A, cdl.CDL_F64, n, k, SEED, Y) == 0

@@ -700,8 +700,13 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       float acc[T8_COLS];
 #pragma unroll
       for (int c = 0; c < T8_COLS; ++c) acc[c] = 0.f;
+      const float* srow = p.sin + (size_t)R * nt;   // s_RK (the level's scales are symmetric: s_KC = s_CK)
+      const float* scol = p.sin + (size_t)C * nt;
+      float sc_next = srow[0] * scol[0];
       for (int kb = 0; kb < nt; ++kb, ++pc) {
         if (failed) continue;
+        const float sc = sc_next;
+        if (kb + 1 < nt) sc_next = srow[kb + 1] * scol[kb + 1];   // issued before the wait
         const int b = pc & 1;
         const uint32_t pr = (uint32_t)(pc >> 1);
         if (!mbar_wait(pfull_bar(b), pr & 1, abort_flag, p.status)) {
@@ -709,7 +714,6 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           continue;
         }
         tc_fence_after();
-        const float sc = p.sin[R * nt + kb] * p.sin[kb * nt + C];
 #pragma unroll
         for (int c = 0; c < T8_COLS / 16; ++c) {
           float v[16];
