@@ -49,6 +49,23 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def square_traffic():
+    """DRAM bytes per launch of the bf16 squaring from the committed ncu summary,
+    if the kernel source is unchanged since it was captured (else None)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "k_tc_gemm_square_n32768_traffic.md")
+    src = os.path.join(ROOT, "paper_1802_05421_gb300", "csrc", "tc_gemm.cu")
+    try:
+        text = open(path).read()
+        tb = int(re.search(r"traffic_bytes_per_launch:\s*(\d+)", text).group(1))
+        sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text).group(1)
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, AttributeError, ValueError):
+        return None
+    return tb if sha == cur else None
+
+
 def make_workload():
     from workloads import field_sequence
     wl = field_sequence(N_GRID[0], N_GRID[1], T_LEN, 2, patch=8, patch_transition=0, seed=2)
@@ -655,7 +672,8 @@ def main():
         kname = {"bf16": "k_tc_gemm", "fp8": "k_tc_gemm<fp8>", "fp8t": "k_tc_fp8t"}.get(args.chain, "k_gemm_tn")
         roof = {"kernel": kname + " (chain squaring)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "frac": (achieved / peak) if peak else None,
+                "traffic": square_traffic() if args.chain == "bf16" else None,
                 "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside a long step)",
                 "work_per_launch": sq["work"], "ms_per_launch": sq["ms_per_launch"]}
         cpu = None
