@@ -11,7 +11,7 @@
  *   cdl_chain_build   inverse-chain levels of Alg. 2, ChainProduct
  *   cdl_project       random projection Y = (Q W^{1/2} B)^T of Alg. 1 / Alg. 3
  *   cdl_chain_solve   L Z = Y by chain-preconditioned Richardson iteration
- *                     (Alg. 2, EstimateSolution; multi-RHS loop of Sec. 3.3)
+ *                     (Alg. 2, EstimateSolution; multi-RHS loop of Sec. 4.1)
  *   cdl_cad_score     node scores F_i = sum_j |A1-A2|_ij |c2-c1|_ij and the
  *                     top anomalies (Alg. 4; CAD edge score of Sec. 2)
  *   cdl_caddelag_pair the whole of Alg. 4 for one graph pair
@@ -222,7 +222,7 @@ int cdl_chain_level_scale(const cdl_chain* chain, int32_t i, double* scale);
 /* ---------------------------------------------------------------- projection */
 
 /* Random projection of Alg. 1 (line "y = W^{1/2} B q") and Alg. 3, formed
- * edge by edge without materialising B or Q (Sec. 3.3: Map + ReduceByKey):
+ * edge by edge without materialising B or Q (Sec. 4.1: Map + ReduceByKey):
  *   Y[i, r] = k^{-1/2} sum_{j != i} o_ij s_r(min(i,j), max(i,j)) sqrt(A_ij),
  * o_ij = +1 if i < j (edge (i,j) has head i, tail j; Sec. 2), -1 otherwise.
  * s_r(i, j) = +1 if bit (r mod 32) of word ((r mod 128) / 32) of
@@ -256,7 +256,7 @@ typedef struct {
 
 /* Solve L Z = Y (L = D - A, Y's columns orthogonal to the ones vector) with
  * the chain as preconditioner P (Alg. 2, EstimateSolution, all k right-hand
- * sides at once as in Sec. 3.3):
+ * sides at once as in Sec. 4.1):
  *   Z_0 = 0;  Z_{t+1} = Z_t + P (Y - L Z_t),
  *   P R = D^{-1/2} prod_{i<d} (I + S~_i) D^{-1/2} R,
  * then Z is shifted to D-weighted zero column means (sum_i D_i Z[i,:] = 0).
@@ -306,6 +306,32 @@ int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtyp
                   int64_t n, int32_t k, cdl_dtype score_dtype, int32_t topk, double* F,
                   int64_t* top_idx);
 
+/* Nodes whose series differ between X1 and X2 (any sample unequal; exact
+ * comparison): changed[0 .. *n_changed) in ascending order. X1, X2: device
+ * n x T float64; changed: device n int32 (capacity); n_changed: host.
+ * Synchronises the context's stream. */
+int cdl_changed_nodes(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T,
+                      int32_t* changed, int32_t* n_changed);
+
+/* CAD scores over the edges of the changed nodes only (Sec. 3.3: commute
+ * times are needed only for node pairs whose weight changed). When the two
+ * graphs share sigma (cdl_build_graph with the same sigma > 0), A1 and A2
+ * differ only in the rows and columns of the nodes whose series changed, so
+ * every edge with Delta A != 0 has an endpoint in `changed` and the scores
+ * equal cdl_cad_score's (same per-edge arithmetic, sums in another order).
+ * Work is n_changed x n edges instead of n^2 / 2. Precondition (not
+ * checked): A1_ij == A2_ij whenever neither i nor j is in `changed`.
+ * changed: device, n_changed node indices (distinct), 0 <= n_changed <=
+ * min(n, 65535). Other arguments as in cdl_cad_score. */
+int cdl_cad_score_changed(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtype,
+                          const double* Z1, const double* Z2, const double* vol1, const double* vol2,
+                          int64_t n, int32_t k, cdl_dtype score_dtype, const int32_t* changed,
+                          int32_t n_changed, int32_t topk, double* F, int64_t* top_idx);
+/* cdl_pair_opts.score_flags: with a shared sigma (sigma > 0), find the
+ * changed nodes (cdl_changed_nodes) and score only their edges
+ * (cdl_cad_score_changed); needs sigma > 0, else CDL_ERR_INVALID_ARG. */
+enum { CDL_SCORE_CHANGED_ONLY = 1 };
+
 /* ---------------------------------------------------------------- Alg. 4 */
 
 typedef struct {
@@ -321,6 +347,7 @@ typedef struct {
                               the call copies them in and out (synchronous);
                               0: device pointers (asynchronous)            */
   int32_t chain_flags;     /* CDL_CHAIN_* flags of cdl_chain_build          */
+  int32_t score_flags;     /* CDL_SCORE_* flags                             */
 } cdl_pair_opts;
 
 /* One graph pair end to end (Alg. 4): graph build, chain, projection and

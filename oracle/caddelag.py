@@ -167,7 +167,7 @@ def commute_times_pinv(A: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Random projection (Alg. 1 and Alg. 3; Sec. 3.3 complexity: Map + ReduceByKey)
+# Random projection (Alg. 1 and Alg. 3; Sec. 4.1 complexity: Map + ReduceByKey)
 # --------------------------------------------------------------------------
 
 def projection_matrix(n: int, seed: int, k: int) -> np.ndarray:
@@ -279,7 +279,7 @@ def chain_levels(A: np.ndarray, d: int):
 def estimate_solution(P1: np.ndarray, P2: np.ndarray, b: np.ndarray, q: int) -> np.ndarray:
     """Alg. 2, EstimateSolution: chi = P1 b; y_1 = 0;
     y_{j+1} = y_j - P2 y_j + chi for j = 1 .. q-1; returns y_q. b may hold
-    several right-hand sides as columns (Sec. 3.3, multi-RHS loop)."""
+    several right-hand sides as columns (Sec. 4.1, multi-RHS loop)."""
     chi = P1 @ b
     y = np.zeros_like(chi)
     for _ in range(q - 1):

@@ -26,6 +26,7 @@ CDL_ERR_UNSUPPORTED = -6
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3, CDL_FP8E4M3_T128 = 0, 1, 2, 3, 4
 CDL_SOLVE_FULL_RESIDUAL = 1
 CDL_CHAIN_HOST_LEVELS = 1
+CDL_SCORE_CHANGED_ONLY = 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1
 CDL_DEBUG_BATCH_VARIANT = 2
 
@@ -47,7 +48,8 @@ class cdl_solve_stats(ctypes.Structure):
 class cdl_pair_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("d", ctypes.c_int32), ("chain_dtype", ctypes.c_int),
                 ("score_dtype", ctypes.c_int), ("seed", ctypes.c_uint64), ("sigma", ctypes.c_double), ("solve", cdl_solve_opts),
-                ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32), ("chain_flags", ctypes.c_int32)]
+                ("topk", ctypes.c_int32), ("host_io", ctypes.c_int32), ("chain_flags", ctypes.c_int32),
+                ("score_flags", ctypes.c_int32)]
 
 
 class cdl_batch_opts(ctypes.Structure):
@@ -96,6 +98,9 @@ _SIGS = {
     "cdl_chain_solve": [_P, _P, _P, ctypes.c_int, _P, _I32, ctypes.POINTER(cdl_solve_opts), _P,
                         ctypes.POINTER(cdl_solve_stats)],
     "cdl_cad_score": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _I32, _P, _P],
+    "cdl_changed_nodes": [_P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_I32)],
+    "cdl_cad_score_changed": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _P, _I32, _I32,
+                              _P, _P],
     "cdl_caddelag_pair": [_P, _P, _P, _I64, _I32, ctypes.POINTER(cdl_pair_opts), _P, _P,
                           ctypes.POINTER(cdl_solve_stats), ctypes.POINTER(cdl_solve_stats)],
     "cdl_caddelag_batched": [_P, _I32, _P, _I32, _P, _P, ctypes.POINTER(cdl_batch_opts), _P, _P, _P],
@@ -237,6 +242,19 @@ def cdl_cad_score(ctx, A1, A2, a_dtype, Z1, Z2, vol1, vol2, n, k, score_dtype, t
                   top_idx) -> int:
     return _lib.cdl_cad_score(ctx, _ptr(A1), _ptr(A2), a_dtype, _ptr(Z1), _ptr(Z2), _ptr(vol1),
                               _ptr(vol2), n, k, score_dtype, topk, _ptr(F), _ptr(top_idx))
+
+
+def cdl_changed_nodes(ctx, X1, X2, n, T, changed):
+    """Returns (status, n_changed)."""
+    m = _I32()
+    st = _lib.cdl_changed_nodes(ctx, _ptr(X1), _ptr(X2), n, T, _ptr(changed), ctypes.byref(m))
+    return st, m.value
+
+
+def cdl_cad_score_changed(ctx, A1, A2, a_dtype, Z1, Z2, vol1, vol2, n, k, score_dtype, changed, n_changed, topk,
+                          F, top_idx) -> int:
+    return _lib.cdl_cad_score_changed(ctx, _ptr(A1), _ptr(A2), a_dtype, _ptr(Z1), _ptr(Z2), _ptr(vol1), _ptr(vol2),
+                                      n, k, score_dtype, _ptr(changed), n_changed, topk, _ptr(F), _ptr(top_idx))
 
 
 def cdl_caddelag_pair(ctx, X1, X2, n, T, opts: cdl_pair_opts, F, top_idx, stats1=None,

@@ -455,13 +455,54 @@ int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtyp
                    vol1, vol2, n, k, score_dtype == CDL_F64, topk, F, top_idx);
 }
 
+int cdl_changed_nodes(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T, int32_t* changed,
+                      int32_t* n_changed) {
+  if (!ctx || !n_changed) return CDL_ERR_INVALID_ARG;
+  if (n < 1 || n > (1 << 20) || T < 1 || T > 4096) return CDL_ERR_INVALID_ARG;
+  CDL_TRY(set_device(ctx));
+  CDL_TRY(dev_ptr(ctx, X1));
+  CDL_TRY(dev_ptr(ctx, X2));
+  CDL_TRY(dev_ptr(ctx, changed, 4));
+  void* vc;
+  CDL_TRY(ws_get(ctx, "score.changed_count", sizeof(int), &vc));
+  CDL_TRY(changed_nodes(ctx, X1, X2, n, T, changed, static_cast<int*>(vc)));
+  CDL_CUDA_TRY(cudaMemcpyAsync(n_changed, vc, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return CDL_OK;
+}
+
+int cdl_cad_score_changed(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtype, const double* Z1,
+                          const double* Z2, const double* vol1, const double* vol2, int64_t n, int32_t k,
+                          cdl_dtype score_dtype, const int32_t* changed, int32_t n_changed, int32_t topk,
+                          double* F, int64_t* top_idx) {
+  if (!ctx) return CDL_ERR_INVALID_ARG;
+  if (score_dtype != CDL_F64 && score_dtype != CDL_F32) return CDL_ERR_INVALID_ARG;
+  if (n < 2 || n > (1 << 20) || k < 1 || k > 1024 || topk < 0 || topk > 1024 || topk > n || n_changed < 0 ||
+      n_changed > n || n_changed > 65535)
+    return CDL_ERR_INVALID_ARG;
+  if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
+  CDL_TRY(set_device(ctx));
+  CDL_TRY(dev_ptr(ctx, A1));
+  CDL_TRY(dev_ptr(ctx, A2));
+  CDL_TRY(dev_ptr(ctx, Z1));
+  CDL_TRY(dev_ptr(ctx, Z2));
+  CDL_TRY(dev_ptr(ctx, vol1));
+  CDL_TRY(dev_ptr(ctx, vol2));
+  CDL_TRY(dev_ptr(ctx, F));
+  if (n_changed > 0) CDL_TRY(dev_ptr(ctx, changed, 4));
+  if (topk > 0) CDL_TRY(dev_ptr(ctx, top_idx));
+  return cad_score_changed(ctx, static_cast<const double*>(A1), static_cast<const double*>(A2), Z1, Z2, vol1, vol2,
+                           n, k, score_dtype == CDL_F64, changed, n_changed, topk, F, top_idx);
+}
+
 int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T,
                       const cdl_pair_opts* o, double* F, int64_t* top_idx,
                       cdl_solve_stats* stats1, cdl_solve_stats* stats2) {
   if (!ctx || !o || !X1 || !X2 || !F) return CDL_ERR_INVALID_ARG;
   if (n < 2 || n > (1 << 20) || T < 1 || T > 4096 || o->k < 1 || o->k > 1024 || o->d < 1 ||
       o->topk < 0 || o->topk > 1024 || o->topk > n || (o->topk > 0 && !top_idx) ||
-      (o->score_dtype != CDL_F64 && o->score_dtype != CDL_F32))
+      (o->score_dtype != CDL_F64 && o->score_dtype != CDL_F32) || (o->score_flags & ~CDL_SCORE_CHANGED_ONLY) ||
+      ((o->score_flags & CDL_SCORE_CHANGED_ONLY) && !(o->sigma > 0)))
     return CDL_ERR_INVALID_ARG;
   CDL_TRY(set_device(ctx));
   const size_t nn = (size_t)n * n;
@@ -514,8 +555,22 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
   }
   double* Fd = o->host_io ? static_cast<double*>(dF) : F;
   int64_t* topd = o->host_io ? static_cast<int64_t*>(dtop) : top_idx;
-  CDL_TRY(cad_score(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype == CDL_F64,
-                    o->topk, Fd, topd));
+  if (o->score_flags & CDL_SCORE_CHANGED_ONLY) {
+    // shared sigma: only edges of nodes whose series changed have Delta A != 0
+    void *vlist, *vcount;
+    CDL_TRY(ws_get(ctx, "pair.changed", (size_t)n * sizeof(int), &vlist));
+    CDL_TRY(ws_get(ctx, "pair.changed_count", sizeof(int), &vcount));
+    CDL_TRY(changed_nodes(ctx, x1, x2, n, T, static_cast<int*>(vlist), static_cast<int*>(vcount)));
+    int m = 0;
+    CDL_CUDA_TRY(cudaMemcpyAsync(&m, vcount, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (m > 65535) return CDL_ERR_UNSUPPORTED;
+    CDL_TRY(cad_score_changed(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype == CDL_F64,
+                              static_cast<const int*>(vlist), m, o->topk, Fd, topd));
+  } else {
+    CDL_TRY(cad_score(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype == CDL_F64,
+                      o->topk, Fd, topd));
+  }
   if (o->host_io) {
     CDL_CUDA_TRY(cudaMemcpyAsync(F, Fd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (o->topk > 0)

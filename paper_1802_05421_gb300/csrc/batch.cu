@@ -1,6 +1,6 @@
 // Batched form: many independent graph pairs of uneven order embedded and
 // scored together (Alg. 4 for each pair; the k right-hand sides of each graph
-// run together as in Sec. 3.3, and here the graphs of the batch do too).
+// run together as in Sec. 4.1, and here the graphs of the batch do too).
 //
 // A plan, built on the first call for a given set of sizes and options, owns
 // every device buffer of the batch in one allocation, the per-graph tensor

@@ -1,6 +1,6 @@
 // Random projection Y = (Q W^{1/2} B)^T of Alg. 1 ("y = W^{1/2} B q") and
 // Alg. 3, formed edge by edge without materialising B or Q (the Map +
-// ReduceByKey of Sec. 3.3):
+// ReduceByKey of Sec. 4.1):
 //   Y[i, r] = k^{-1/2} sum_{j != i} o_ij s_r(min(i,j), max(i,j)) sqrt(A_ij),
 // o_ij = +1 when i < j (i is the head of edge (i, j), Sec. 2), else -1.
 // The signs come from Philox4x32-10 (Salmon et al., SC'11) at counter

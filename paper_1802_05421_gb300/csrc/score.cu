@@ -367,6 +367,140 @@ __global__ void __launch_bounds__(1024) k_topk(const double* __restrict__ F, int
   topk_block(F, n, topk, out);
 }
 
+// ---------------------------------------------------------------- changed edges only
+// Sec. 3.3: only node pairs whose weight changed (Delta A != 0) need their
+// commute-time difference. When both graphs share sigma, A1 and A2 differ
+// only in the rows and columns of the nodes whose series changed, so every
+// edge score with a nonzero term has a changed endpoint: the pass below
+// scores the m x n strip of those edges (the same per-edge arithmetic as the
+// dense pass) and sums it per node.
+
+// c2 - c1 for nodes c, j from the grid-split hi/lo planes (as in score_tile).
+__device__ __forceinline__ double dc_pair_f32(const float* __restrict__ ah, const float* __restrict__ al,
+                                              const float* __restrict__ bh, const float* __restrict__ bl, int n,
+                                              int k, int c, int j) {
+  float acc = 0.f, cmp = 0.f;
+  for (int r = 0; r < k; ++r) {
+    const size_t oc = (size_t)r * n + c, oj = (size_t)r * n + j;
+    const float dah = __fsub_rn(ah[oc], ah[oj]);
+    const float dal = __fsub_rn(al[oc], al[oj]);
+    const float dbh = __fsub_rn(bh[oc], bh[oj]);
+    const float dbl = __fsub_rn(bl[oc], bl[oj]);
+    const float p = __fmul_rn(dah, dbh);
+    float x = __fmaf_rn(dah, dbh, -p);
+    x = __fmaf_rn(dah, dbl, x);
+    x = __fmaf_rn(dal, dbh, x);
+    const float t = __fadd_rn(acc, p);
+    const float z = __fsub_rn(t, acc);
+    const float err = __fadd_rn(__fsub_rn(acc, __fsub_rn(t, z)), __fsub_rn(p, z));
+    acc = t;
+    cmp = __fadd_rn(cmp, __fadd_rn(err, x));
+  }
+  return (double)acc + (double)cmp;
+}
+
+__device__ __forceinline__ double dc_pair_f64(const double* __restrict__ aT, const double* __restrict__ bT, int n,
+                                              int k, int c, int j) {
+  double acc = 0.0;
+  for (int r = 0; r < k; ++r) {
+    const size_t oc = (size_t)r * n + c, oj = (size_t)r * n + j;
+    acc = fma(aT[oc] - aT[oj], bT[oc] - bT[oj], acc);
+  }
+  return acc;
+}
+
+// E[ci][j] = |A1_cj - A2_cj| |c2(c, j) - c1(c, j)| for changed node c = changed[ci].
+__global__ void __launch_bounds__(256) k_changed_edges(const double* __restrict__ A1, const double* __restrict__ A2,
+                                                        const void* __restrict__ ab, int n, int k, int fp64,
+                                                        const int* __restrict__ changed, double* __restrict__ E) {
+  const int ci = blockIdx.y;
+  const int c = changed[ci];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double e = 0.0;
+  if (j != c) {
+    const size_t nk = (size_t)n * k;
+    double dc;
+    if (fp64) {
+      const double* aT = static_cast<const double*>(ab);
+      dc = dc_pair_f64(aT, aT + nk, n, k, c, j);
+    } else {
+      const float* ah = static_cast<const float*>(ab);
+      dc = dc_pair_f32(ah, ah + nk, ah + 2 * nk, ah + 3 * nk, n, k, c, j);
+    }
+    const size_t o = (size_t)c * n + j;
+    e = fabs(A1[o] - A2[o]) * fabs(dc);
+  }
+  E[(size_t)ci * n + j] = e;
+}
+
+// F_j = sum over changed c of E[c][j] (the terms of an unchanged node), in
+// list order; changed nodes are overwritten by k_changed_rowsum.
+__global__ void k_changed_colsum(const double* __restrict__ E, int m, int n, double* __restrict__ F) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int ci = 0; ci < m; ++ci) s += E[(size_t)ci * n + j];
+  F[j] = s;
+}
+
+// F_c = sum over j of E[c][j] for a changed node c (all of its terms).
+__global__ void __launch_bounds__(256) k_changed_rowsum(const double* __restrict__ E, const int* __restrict__ changed,
+                                                         int n, double* __restrict__ F) {
+  __shared__ double red[8];
+  const double* row = E + (size_t)blockIdx.x * n;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += 256) s += row[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    F[changed[blockIdx.x]] = t;
+  }
+}
+
+// Rows whose series differ (exact comparison): flag[i] = 1.
+__global__ void k_row_differs(const double* __restrict__ X1, const double* __restrict__ X2, int n, int T,
+                              int* __restrict__ flag) {
+  const int i = blockIdx.x;
+  bool d = false;
+  for (int t = threadIdx.x; t < T; t += blockDim.x) d |= X1[(size_t)i * T + t] != X2[(size_t)i * T + t];
+  d = __syncthreads_or(d);
+  if (threadIdx.x == 0) flag[i] = d ? 1 : 0;
+}
+
+// Ordered compaction of the flagged rows (one block): list[count] = i.
+__global__ void __launch_bounds__(1024) k_compact(const int* __restrict__ flag, int n, int* __restrict__ list,
+                                                   int* __restrict__ count) {
+  __shared__ int warp_sum[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < n; i0 += 1024) {
+    const int i = i0 + threadIdx.x;
+    const int f = (i < n) ? flag[i] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_sum[w] = __popc(bal);
+    __syncthreads();
+    int off = 0;
+    for (int q = 0; q < w; ++q) off += warp_sum[q];
+    if (f) list[base + off + before] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int q = 0; q < 32; ++q) tot += warp_sum[q];
+      base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
 // ---------------------------------------------------------------- batched form
 // One launch per scoring step over all pairs of a batch; a block finds its
 // pair (and block or tile) in a tile table.
@@ -427,6 +561,35 @@ __global__ void __launch_bounds__(1024) k_b_topk(const ScoreJob* __restrict__ jo
 
 }  // namespace
 
+// a and b of both graphs in the layout the pair kernels read (float hi/lo
+// planes on per-column grids, or float64), in the workspace buffer "score.ab".
+int score_prepare(cdl_ctx* ctx, const double* Z1, const double* Z2, const double* vol1, const double* vol2, int n,
+                  int k, bool fp64, void** vab) {
+  cudaStream_t st = ctx->stream;
+  const size_t nk = (size_t)n * k;
+  CDL_TRY(ws_get(ctx, "score.ab", 16 * nk, vab));
+  if (fp64) {
+    double* aT = static_cast<double*>(*vab);
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_score_prep64<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, aT, aT + nk);
+    return L.done();
+  }
+  float* ah = static_cast<float*>(*vab);
+  void* vmax;
+  CDL_TRY(ws_get(ctx, "score.cmax", 2 * (size_t)k * sizeof(unsigned), &vmax));
+  unsigned* cmax = static_cast<unsigned*>(vmax);
+  CDL_CUDA_TRY(cudaMemsetAsync(cmax, 0, 2 * (size_t)k * sizeof(unsigned), st));
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_score_colmax<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cmax);
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_score_prep<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cmax, ah, ah + nk,
+                                                             ah + 2 * nk, ah + 3 * nk);
+  return L.done();
+}
+
 int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
               const double* vol1, const double* vol2, int64_t n64, int k, bool fp64, int topk,
               double* F, int64_t* top_idx) {
@@ -435,47 +598,73 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
   const int nb = (n + ST - 1) / ST;
   void *vab, *vc;
   const size_t nk = (size_t)n * k;
-  CDL_TRY(ws_get(ctx, "score.ab", 16 * nk, &vab));
+  CDL_TRY(score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, fp64, &vab));
   CDL_TRY(ws_get(ctx, "score.contrib", (size_t)nb * n * sizeof(double), &vc));
   const long long tiles = (long long)nb * (nb + 1) / 2;
   if (fp64) {
-    double* aT = static_cast<double*>(vab);
-    double* bT = aT + nk;
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_score_prep64<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, aT, bT);
-      CDL_TRY(L.done());
-    }
+    const double* aT = static_cast<const double*>(vab);
     Launch L(ctx, CDL_KC_SCORE, 8.0 * (double)n * (n - 1));
-    k_score_pairs64<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, aT, bT, n, k, static_cast<double*>(vc));
+    k_score_pairs64<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, aT, aT + nk, n, k, static_cast<double*>(vc));
     CDL_TRY(L.done());
   } else {
-    float* ah = static_cast<float*>(vab);
-    float* al = ah + nk;
-    float* bh = al + nk;
-    float* bl = bh + nk;
-    void* vmax;
-    CDL_TRY(ws_get(ctx, "score.cmax", 2 * (size_t)k * sizeof(unsigned), &vmax));
-    unsigned* cmax = static_cast<unsigned*>(vmax);
-    CDL_CUDA_TRY(cudaMemsetAsync(cmax, 0, 2 * (size_t)k * sizeof(unsigned), st));
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_score_colmax<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cmax);
-      CDL_TRY(L.done());
-    }
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_score_prep<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cmax, ah, al, bh, bl);
-      CDL_TRY(L.done());
-    }
+    const float* ah = static_cast<const float*>(vab);
     Launch L(ctx, CDL_KC_SCORE, 8.0 * (double)n * (n - 1));
-    k_score_pairs<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, ah, al, bh, bl, n, k, static_cast<double*>(vc));
+    k_score_pairs<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, ah, ah + nk, ah + 2 * nk, ah + 3 * nk, n, k,
+                                                   static_cast<double*>(vc));
     CDL_TRY(L.done());
   }
   {
     Launch L(ctx, CDL_KC_MISC, 0);
     k_score_reduce<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const double*>(vc), nb, n, F);
     CDL_TRY(L.done());
+  }
+  if (topk > 0) {
+    Launch L(ctx, CDL_KC_TOPK, 0);
+    k_topk<<<1, 1024, 0, st>>>(F, n, topk, top_idx);
+    CDL_TRY(L.done());
+  }
+  return CDL_OK;
+}
+
+int changed_nodes(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int T, int* list, int* count_dev) {
+  void* vf;
+  CDL_TRY(ws_get(ctx, "score.changed_flag", (size_t)n * sizeof(int), &vf));
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_row_differs<<<(unsigned)n, 128, 0, ctx->stream>>>(X1, X2, (int)n, T, static_cast<int*>(vf));
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_compact<<<1, 1024, 0, ctx->stream>>>(static_cast<const int*>(vf), (int)n, list, count_dev);
+  return L.done();
+}
+
+int cad_score_changed(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
+                      const double* vol1, const double* vol2, int64_t n64, int k, bool fp64, const int* changed,
+                      int m, int topk, double* F, int64_t* top_idx) {
+  const int n = (int)n64;
+  cudaStream_t st = ctx->stream;
+  void *vab, *vE;
+  CDL_TRY(score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, fp64, &vab));
+  if (m > 0) {
+    CDL_TRY(ws_get(ctx, "score.changed_E", (size_t)m * n * sizeof(double), &vE));
+    double* E = static_cast<double*>(vE);
+    {
+      dim3 g((n + 255) / 256, m);
+      Launch L(ctx, CDL_KC_SCORE, 16.0 * (double)m * n);
+      k_changed_edges<<<g, 256, 0, st>>>(A1, A2, vab, n, k, fp64 ? 1 : 0, changed, E);
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_changed_colsum<<<(n + 255) / 256, 256, 0, st>>>(E, m, n, F);
+      CDL_TRY(L.done());
+    }
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_changed_rowsum<<<m, 256, 0, st>>>(E, changed, n, F);
+    CDL_TRY(L.done());
+  } else {
+    CDL_CUDA_TRY(cudaMemsetAsync(F, 0, (size_t)n * sizeof(double), st));
   }
   if (topk > 0) {
     Launch L(ctx, CDL_KC_TOPK, 0);

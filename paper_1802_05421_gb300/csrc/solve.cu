@@ -1,5 +1,5 @@
 // Chain-preconditioned Richardson solve of L Z = Y (Alg. 2, EstimateSolution,
-// with the k right-hand sides of Alg. 3 processed together as in Sec. 3.3):
+// with the k right-hand sides of Alg. 3 processed together as in Sec. 4.1):
 //
 //   R_0 = Y, Z_0 = 0;  Z_{t+1} = Z_t + P R_t,  R_{t+1} = Y - L Z_{t+1},
 //   P R = D^{-1/2} (I + S~_{d-1}) ... (I + S~_0) D^{-1/2} R.
