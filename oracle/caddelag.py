@@ -371,6 +371,53 @@ def node_scores(A1, A2, Z1, Z2, vol1, vol2, rows: Optional[Sequence[int]] = None
     return F
 
 
+def upper_edge_scores(A1, A2, Z1, Z2, vol1, vol2) -> np.ndarray:
+    """Delta E_ij for every edge i < j (Sec. 2; Alg. 4), as an n x n array
+    holding the upper triangle (zero on and below the diagonal)."""
+    C1 = commute_times(Z1, vol1)
+    C2 = commute_times(Z2, vol2)
+    return np.triu(edge_scores(A1, A2, C1, C2), 1)
+
+
+def anomalous_edges(E_upper: np.ndarray, delta: float):
+    """CAD's anomalous edge set (Sec. 3.3): the smallest set of edges whose
+    removal leaves the total change of the remaining edges below delta.
+    Edges are taken one at a time in descending Delta E (ties: lower (i, j)
+    first), subtracting each from the total, until the remainder is below
+    delta. Returns dict(edges: (s, 2) int64 (i, j) pairs in (i, j) order,
+    values, total, remaining)."""
+    n = E_upper.shape[0]
+    iu, ju = np.triu_indices(n, 1)
+    v = E_upper[iu, ju]
+    total = float(np.sum(v))
+    order = np.lexsort((ju, iu, -v))
+    rem = total
+    s = 0
+    while not (rem < delta) and s < v.size:
+        rem -= v[order[s]]
+        s += 1
+    chosen = order[:s]
+    pairs = np.stack([iu[chosen], ju[chosen]], axis=1).astype(np.int64)
+    vals = v[chosen]
+    srt = np.lexsort((pairs[:, 1], pairs[:, 0]))
+    return dict(edges=pairs[srt], values=vals[srt], total=total, remaining=rem)
+
+
+def node_top_edges(E_upper: np.ndarray, nodes: Sequence[int], m: int):
+    """For each node, its m largest Delta E partners (ties: lower partner
+    first); -1 past the end."""
+    Ef = E_upper + E_upper.T
+    n = Ef.shape[0]
+    out = np.full((len(nodes), m), -1, dtype=np.int64)
+    vals = np.zeros((len(nodes), m))
+    for t, i in enumerate(nodes):
+        j = np.array([x for x in range(n) if x != i])
+        o = np.lexsort((j, -Ef[i, j]))[:m]
+        out[t, :o.size] = j[o]
+        vals[t, :o.size] = Ef[i, j[o]]
+    return out, vals
+
+
 def top_anomalies(F: np.ndarray, k: int) -> np.ndarray:
     """Indices of the k highest node scores, ties broken by lower index."""
     F = np.asarray(F)

@@ -407,3 +407,59 @@ def test_pipeline_finds_planted_nodes():
     wl = iid_pair(200, 32, 4, 21)
     out = O.caddelag_pair(wl.X[0], wl.X[1], k=32, seed=5, topk=4)
     assert set(out["top"].tolist()) == set(wl.planted[0].tolist())
+
+
+# ------------------------------------------------------------------ anomalous edge set (Sec. 3.3)
+
+def _brute_min_set(v, delta):
+    """Smallest number of edges whose removal leaves the rest below delta, by
+    enumeration of all subsets."""
+    import itertools
+    m = v.size
+    for size in range(m + 1):
+        for sub in itertools.combinations(range(m), size):
+            if v.sum() - v[list(sub)].sum() < delta:
+                return size
+    return None
+
+
+def test_anomalous_edges_minimal_by_brute_force():
+    rng = np.random.default_rng(3)
+    for trial in range(30):
+        n = 5
+        E = np.triu(rng.exponential(size=(n, n)), 1)
+        total = E.sum()
+        delta = rng.uniform(0.05, 0.95) * total
+        out = O.anomalous_edges(E, delta)
+        iu, ju = np.triu_indices(n, 1)
+        assert len(out["edges"]) == _brute_min_set(E[iu, ju], delta)
+        assert out["remaining"] < delta
+        # removing the smallest chosen edge from the set breaks the bound
+        if len(out["edges"]):
+            keep = out["values"].sum() - out["values"].min()
+            assert total - keep >= delta
+
+
+def test_anomalous_edges_limits_and_ties():
+    E = np.triu(np.ones((4, 4)), 1)          # six equal edges
+    out = O.anomalous_edges(E, 10.0)          # total 6 < 10: nothing to take
+    assert len(out["edges"]) == 0 and out["remaining"] == 6.0
+    out = O.anomalous_edges(E, 3.5)           # take 3, ties to the lower (i, j)
+    assert [tuple(e) for e in out["edges"]] == [(0, 1), (0, 2), (0, 3)]
+    assert out["remaining"] == 3.0
+    out = O.anomalous_edges(E, 1e-9)          # every edge
+    assert len(out["edges"]) == 6 and out["remaining"] == 0.0
+
+
+def test_edge_scores_sum_to_node_scores():
+    wl = iid_pair(60, 8, 3, seed=2)
+    g = [O.embed(X, 8, 1) for X in wl.X]
+    E = O.upper_edge_scores(g[0]["A"], g[1]["A"], g[0]["Z"], g[1]["Z"], g[0]["vol"], g[1]["vol"])
+    F = O.node_scores(g[0]["A"], g[1]["A"], g[0]["Z"], g[1]["Z"], g[0]["vol"], g[1]["vol"])
+    np.testing.assert_allclose((E + E.T).sum(axis=1), F, rtol=1e-12)
+    part, vals = O.node_top_edges(E, [0, 5], 3)
+    Ef = E + E.T
+    for t, i in enumerate([0, 5]):
+        row = [(Ef[i, j], -j) for j in range(60) if j != i]
+        best = sorted(row, reverse=True)[:3]
+        assert list(part[t]) == [-b[1] for b in best]
