@@ -306,6 +306,36 @@ int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtyp
                   int64_t n, int32_t k, cdl_dtype score_dtype, int32_t topk, double* F,
                   int64_t* top_idx);
 
+/* CAD's anomalous edge set (Sec. 3.3): the smallest set S of edges (i < j)
+ * whose removal leaves sum_{e not in S} Delta E_e < delta, with
+ * Delta E_ij = |A1_ij - A2_ij| |c2(i,j) - c1(i,j)| (the per-edge term of
+ * cdl_cad_score). Taking edges in descending Delta E, ties to the lower
+ * (i, j), is optimal for this cardinality problem; S = {Delta E > tau} plus
+ * the first ties at tau, tau found by bisection on the float64 bit patterns
+ * with fixed-order sums (deterministic). The remaining sum is decided in
+ * float64 (a different summation order than a sequential sum: decisions
+ * within about 1e-15 relative of delta can differ from one).
+ * Outputs: edge_ij (device, 2 x max_edges int64, (i, j) pairs in (i, j)
+ * order) and edge_dE (device, max_edges) receive the first min(|S|,
+ * max_edges) edges of S; for each of the n_nodes nodes in `nodes` (device
+ * int64), its top_per_node largest edges (partner j, ties to the lower j;
+ * -1 past the end) go to partner / partner_dE (device, n_nodes x
+ * top_per_node); F (device n, may be NULL) receives the node scores; *res
+ * (host) the counts and sums. Needs n x n float64 workspace (8 n^2 bytes).
+ * Requires delta > 0, 0 <= top_per_node <= 1024. Synchronises. */
+typedef struct {
+  int64_t n_edges;        /* |S| (may exceed max_edges: then only max_edges written) */
+  int64_t n_ties_taken;   /* edges of S with Delta E equal to the threshold */
+  double threshold;       /* tau as a value (+inf when S is empty)          */
+  double remaining;       /* sum of Delta E outside S (< delta)             */
+  double total;           /* sum of Delta E over all edges                  */
+} cdl_edge_result;
+int cdl_cad_edges(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtype, const double* Z1,
+                  const double* Z2, const double* vol1, const double* vol2, int64_t n, int32_t k,
+                  cdl_dtype score_dtype, double delta, int64_t max_edges, int64_t* edge_ij,
+                  double* edge_dE, const int64_t* nodes, int32_t n_nodes, int32_t top_per_node,
+                  int64_t* partner, double* partner_dE, double* F, cdl_edge_result* res);
+
 /* Nodes whose series differ between X1 and X2 (any sample unequal; exact
  * comparison): changed[0 .. *n_changed) in ascending order. X1, X2: device
  * n x T float64; changed: device n int32 (capacity); n_changed: host.

@@ -69,6 +69,11 @@ class cdl_batch_info(ctypes.Structure):
                 ("project_variant_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_uint64)]
 
 
+class cdl_edge_result(ctypes.Structure):
+    _fields_ = [("n_edges", ctypes.c_int64), ("n_ties_taken", ctypes.c_int64), ("threshold", ctypes.c_double),
+                ("remaining", ctypes.c_double), ("total", ctypes.c_double)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libcdl.so not built at {LIB_PATH}; run python -m paper_1802_05421_gb300.build")
 _lib = ctypes.CDLL(LIB_PATH)
@@ -98,6 +103,8 @@ _SIGS = {
     "cdl_chain_solve": [_P, _P, _P, ctypes.c_int, _P, _I32, ctypes.POINTER(cdl_solve_opts), _P,
                         ctypes.POINTER(cdl_solve_stats)],
     "cdl_cad_score": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _I32, _P, _P],
+    "cdl_cad_edges": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _D, _I64, _P, _P, _P, _I32,
+                      _I32, _P, _P, _P, ctypes.POINTER(cdl_edge_result)],
     "cdl_changed_nodes": [_P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_I32)],
     "cdl_cad_score_changed": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _P, _I32, _I32,
                               _P, _P],
@@ -242,6 +249,16 @@ def cdl_cad_score(ctx, A1, A2, a_dtype, Z1, Z2, vol1, vol2, n, k, score_dtype, t
                   top_idx) -> int:
     return _lib.cdl_cad_score(ctx, _ptr(A1), _ptr(A2), a_dtype, _ptr(Z1), _ptr(Z2), _ptr(vol1),
                               _ptr(vol2), n, k, score_dtype, topk, _ptr(F), _ptr(top_idx))
+
+
+def cdl_cad_edges(ctx, A1, A2, a_dtype, Z1, Z2, vol1, vol2, n, k, score_dtype, delta, max_edges, edge_ij, edge_dE,
+                  nodes, n_nodes, top_per_node, partner, partner_dE, F):
+    """Returns (status, cdl_edge_result)."""
+    res = cdl_edge_result()
+    st = _lib.cdl_cad_edges(ctx, _ptr(A1), _ptr(A2), a_dtype, _ptr(Z1), _ptr(Z2), _ptr(vol1), _ptr(vol2), n, k,
+                            score_dtype, delta, max_edges, _ptr(edge_ij), _ptr(edge_dE), _ptr(nodes), n_nodes,
+                            top_per_node, _ptr(partner), _ptr(partner_dE), _ptr(F), ctypes.byref(res))
+    return st, res
 
 
 def cdl_changed_nodes(ctx, X1, X2, n, T, changed):

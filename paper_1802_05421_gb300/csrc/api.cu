@@ -455,6 +455,38 @@ int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtyp
                    vol1, vol2, n, k, score_dtype == CDL_F64, topk, F, top_idx);
 }
 
+int cdl_cad_edges(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtype, const double* Z1, const double* Z2,
+                  const double* vol1, const double* vol2, int64_t n, int32_t k, cdl_dtype score_dtype, double delta,
+                  int64_t max_edges, int64_t* edge_ij, double* edge_dE, const int64_t* nodes, int32_t n_nodes,
+                  int32_t top_per_node, int64_t* partner, double* partner_dE, double* F, cdl_edge_result* res) {
+  if (!ctx || !res) return CDL_ERR_INVALID_ARG;
+  if (score_dtype != CDL_F64 && score_dtype != CDL_F32) return CDL_ERR_INVALID_ARG;
+  if (n < 2 || n > 65536 || k < 1 || k > 1024 || !(delta > 0) || max_edges < 0 || n_nodes < 0 ||
+      n_nodes > 65535 || top_per_node < 0 || top_per_node > 1024)
+    return CDL_ERR_INVALID_ARG;
+  if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
+  CDL_TRY(set_device(ctx));
+  CDL_TRY(dev_ptr(ctx, A1));
+  CDL_TRY(dev_ptr(ctx, A2));
+  CDL_TRY(dev_ptr(ctx, Z1));
+  CDL_TRY(dev_ptr(ctx, Z2));
+  CDL_TRY(dev_ptr(ctx, vol1));
+  CDL_TRY(dev_ptr(ctx, vol2));
+  if (max_edges > 0) {
+    CDL_TRY(dev_ptr(ctx, edge_ij));
+    CDL_TRY(dev_ptr(ctx, edge_dE));
+  }
+  if (n_nodes > 0 && top_per_node > 0) {
+    CDL_TRY(dev_ptr(ctx, nodes));
+    CDL_TRY(dev_ptr(ctx, partner));
+    CDL_TRY(dev_ptr(ctx, partner_dE));
+  }
+  if (F) CDL_TRY(dev_ptr(ctx, F));
+  return cad_edges(ctx, static_cast<const double*>(A1), static_cast<const double*>(A2), Z1, Z2, vol1, vol2, n, k,
+                   score_dtype == CDL_F64, delta, max_edges, nodes, n_nodes, top_per_node, edge_ij, edge_dE, partner,
+                   partner_dE, F, res);
+}
+
 int cdl_changed_nodes(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int32_t T, int32_t* changed,
                       int32_t* n_changed) {
   if (!ctx || !n_changed) return CDL_ERR_INVALID_ARG;

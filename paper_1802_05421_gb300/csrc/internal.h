@@ -191,6 +191,12 @@ int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, floa
 int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp,
                  int splits);
 bool tc_supported(cdl_ctx* ctx);
+// Anomalous edge set and per-node top edges (score.cu).
+int cad_edges(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
+              const double* vol1, const double* vol2, int64_t n, int k, bool fp64, double delta, int64_t cap,
+              const int64_t* nodes, int n_nodes, int m, int64_t* ij, double* val, int64_t* partner, double* pval,
+              double* F, cdl_edge_result* res);
+
 // Sparse scoring over the edges of changed nodes (score.cu).
 int changed_nodes(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int T, int* list, int* count_dev);
 int cad_score_changed(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,

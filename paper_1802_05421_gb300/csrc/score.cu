@@ -14,9 +14,11 @@
 // Each unordered pair (i < j) is visited once in 64 x 64 upper-triangle
 // tiles; the two row contributions of a tile go to a per-(partner block, node)
 // slot, and F is the fixed-order sum of those slots (deterministic).
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstring>
 
 #include "internal.h"
 
@@ -120,7 +122,7 @@ __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
 __device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const double* __restrict__ A2,
                                             int n, int i0, int j0, int bi, int bj, int tx, int ty,
                                             const double (&dc)[4][4], double* __restrict__ contrib,
-                                            double (*rsum)[17], double (*csum)[17]) {
+                                            double (*rsum)[17], double (*csum)[17], double* __restrict__ Eout) {
   double rpart[4] = {0, 0, 0, 0}, cpart[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -131,6 +133,7 @@ __device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const
       if (i < n && j < n && (bi != bj || i < j)) {
         const size_t o = (size_t)i * n + j;
         const double e = fabs(A1[o] - A2[o]) * fabs(dc[u][v]);
+        if (Eout) Eout[o] = e;   // edge score of (i, j), i < j
         rpart[u] += e;
         cpart[v] += e;
       }
@@ -161,7 +164,8 @@ __device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const
 __device__ __forceinline__ void score_tile(const double* __restrict__ A1, const double* __restrict__ A2,
                                            const float* __restrict__ ah, const float* __restrict__ al,
                                            const float* __restrict__ bh, const float* __restrict__ bl, int n, int k,
-                                           double* __restrict__ contrib, int bi, int bj) {
+                                           double* __restrict__ contrib, int bi, int bj,
+                                           double* __restrict__ Eout = nullptr) {
   __shared__ __align__(16) float sI[4][RC][ST];   // ah, al, bh, bl of the row block
   __shared__ __align__(16) float sJ[4][RC][ST];   // ... of the column block
   __shared__ double rsum[ST][17];
@@ -225,7 +229,7 @@ __device__ __forceinline__ void score_tile(const double* __restrict__ A1, const 
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) dc[u][v] = (double)acc[u][v] + (double)cmp[u][v];
-  tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, dc, contrib, rsum, csum);
+  tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, dc, contrib, rsum, csum, Eout);
 }
 
 __global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ A1, const double* __restrict__ A2,
@@ -241,7 +245,8 @@ __global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ 
 // float64 variant: c2 - c1 = sum_r (a_ir - a_jr)(b_ir - b_jr) in float64.
 __device__ __forceinline__ void score_tile64(const double* __restrict__ A1, const double* __restrict__ A2,
                                              const double* __restrict__ aT, const double* __restrict__ bT, int n,
-                                             int k, double* __restrict__ contrib, int bi, int bj) {
+                                             int k, double* __restrict__ contrib, int bi, int bj,
+                                             double* __restrict__ Eout = nullptr) {
   __shared__ __align__(16) double sI[2][RC][ST];
   __shared__ __align__(16) double sJ[2][RC][ST];
   __shared__ double rsum[ST][17];
@@ -277,7 +282,7 @@ __device__ __forceinline__ void score_tile64(const double* __restrict__ A1, cons
     }
     __syncthreads();
   }
-  tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, acc, contrib, rsum, csum);
+  tile_finish(A1, A2, n, i0, j0, bi, bj, tx, ty, acc, contrib, rsum, csum, Eout);
 }
 
 __global__ void __launch_bounds__(256) k_score_pairs64(const double* __restrict__ A1,
@@ -365,6 +370,297 @@ __device__ __forceinline__ void topk_block(const double* __restrict__ F, int n, 
 __global__ void __launch_bounds__(1024) k_topk(const double* __restrict__ F, int n, int topk,
                                                 int64_t* __restrict__ out) {
   topk_block(F, n, topk, out);
+}
+
+// ---------------------------------------------------------------- anomalous edge set
+// CAD's anomalous edges (Sec. 3.3): the smallest set of edges whose removal
+// leaves a remaining total change Delta E below delta. Taking edges in
+// descending Delta E (ties by (i, j)) is optimal for that cardinality
+// problem, so the set is {Delta E > tau} plus the first c edges equal to
+// tau, for the largest tau whose set {Delta E >= tau} already suffices. tau
+// is found by bisection on the float64 bit patterns (non-negative doubles
+// order like their bits), each step a fixed-order sum over the upper
+// triangle, so the result does not depend on scheduling.
+
+__global__ void __launch_bounds__(256) k_edge_pairs(const double* __restrict__ A1, const double* __restrict__ A2,
+                                                     const void* __restrict__ ab, int n, int k, int fp64,
+                                                     double* __restrict__ contrib, double* __restrict__ E) {
+  const int nb = (n + ST - 1) / ST;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  const size_t nk = (size_t)n * k;
+  if (fp64) {
+    const double* aT = static_cast<const double*>(ab);
+    score_tile64(A1, A2, aT, aT + nk, n, k, contrib, bi, bj, E);
+  } else {
+    const float* ah = static_cast<const float*>(ab);
+    score_tile(A1, A2, ah, ah + nk, ah + 2 * nk, ah + 3 * nk, n, k, contrib, bi, bj, E);
+  }
+}
+
+__device__ __forceinline__ unsigned long long dkey(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// Per-block sums and counts of the upper-triangle entries with key >= tau
+// (rows i = block, block + grid, ...; fixed order).
+__global__ void __launch_bounds__(256) k_edge_mass(const double* __restrict__ E, int n, unsigned long long tau,
+                                                    double* __restrict__ psum, unsigned long long* __restrict__ pcnt) {
+  __shared__ double rs[8];
+  __shared__ unsigned long long rc[8];
+  double s = 0.0;
+  unsigned long long c = 0;
+  for (int i = blockIdx.x; i < n - 1; i += gridDim.x)
+    for (int j = i + 1 + threadIdx.x; j < n; j += 256) {
+      const double v = E[(size_t)i * n + j];
+      if (dkey(v) >= tau) {
+        s += v;
+        ++c;
+      }
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rs[threadIdx.x >> 5] = s;
+    rc[threadIdx.x >> 5] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long u = 0;
+    for (int w = 0; w < 8; ++w) {
+      t += rs[w];
+      u += rc[w];
+    }
+    psum[blockIdx.x] = t;
+    pcnt[blockIdx.x] = u;
+  }
+}
+
+__global__ void k_edge_mass_total(const double* __restrict__ psum, const unsigned long long* __restrict__ pcnt, int nb,
+                                  double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  unsigned long long u = 0;
+  for (int b = 0; b < nb; ++b) {
+    t += psum[b];
+    u += pcnt[b];
+  }
+  out[0] = t;
+  reinterpret_cast<unsigned long long*>(out)[1] = u;
+}
+
+// Largest key of the upper triangle (atomicMax on the bit patterns).
+__global__ void __launch_bounds__(256) k_edge_maxkey(const double* __restrict__ E, int n,
+                                                      unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  for (int i = blockIdx.x; i < n - 1; i += gridDim.x)
+    for (int j = i + 1 + threadIdx.x; j < n; j += 256) m = max(m, dkey(E[(size_t)i * n + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Per row i: entries j > i with key > tau, and with key == tau.
+__global__ void __launch_bounds__(256) k_edge_rowcount(const double* __restrict__ E, int n, unsigned long long tau,
+                                                        int* __restrict__ cgt, int* __restrict__ ceq) {
+  __shared__ int r1[8], r2[8];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    int a = 0, b = 0;
+    for (int j = i + 1 + threadIdx.x; j < n; j += 256) {
+      const unsigned long long kk = dkey(E[(size_t)i * n + j]);
+      a += kk > tau;
+      b += kk == tau;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      r1[threadIdx.x >> 5] = a;
+      r2[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int x = 0, y = 0;
+      for (int w = 0; w < 8; ++w) {
+        x += r1[w];
+        y += r2[w];
+      }
+      cgt[i] = x;
+      ceq[i] = y;
+    }
+    __syncthreads();
+  }
+}
+
+// Row offsets of the output (rows in order): row i writes its entries above
+// tau and its ties with a global tie rank below c. One block.
+__global__ void __launch_bounds__(1024) k_edge_offsets(const int* __restrict__ cgt, const int* __restrict__ ceq, int n,
+                                                        long long c, long long* __restrict__ off,
+                                                        long long* __restrict__ tie0, long long* __restrict__ total) {
+  __shared__ long long ws[32], wt[32];
+  __shared__ long long base, tbase;
+  if (threadIdx.x == 0) base = tbase = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < n; i0 += 1024) {
+    const int i = i0 + threadIdx.x;
+    const long long eq = i < n ? ceq[i] : 0;
+    // inclusive scan of ties, then of written counts
+    long long t = eq;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane == 31) wt[w] = t;
+    __syncthreads();
+    long long tw = 0;
+    for (int q = 0; q < w; ++q) tw += wt[q];
+    const long long ties_before = tbase + tw + t - eq;
+    const long long take = max(0LL, min(eq, c - ties_before));
+    const long long cnt = (i < n ? cgt[i] : 0) + take;
+    long long u = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += y;
+    }
+    if (lane == 31) ws[w] = u;
+    __syncthreads();
+    long long sw = 0;
+    for (int q = 0; q < w; ++q) sw += ws[q];
+    if (i < n) {
+      off[i] = base + sw + u - cnt;
+      tie0[i] = ties_before;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 32; ++q) {
+        base += ws[q];
+        tbase += wt[q];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = base;
+}
+
+// Ordered write of the selected entries of each row: (i, j) pairs and values.
+__global__ void __launch_bounds__(256) k_edge_write(const double* __restrict__ E, int n, unsigned long long tau,
+                                                     long long c, const long long* __restrict__ off,
+                                                     const long long* __restrict__ tie0, long long cap,
+                                                     long long* __restrict__ ij, double* __restrict__ val) {
+  __shared__ int wsel[8], wtie[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = blockIdx.x; i < n - 1; i += gridDim.x) {
+    long long pos = off[i];
+    long long tr = tie0[i];
+    for (int j0 = i + 1; j0 < n; j0 += 256) {
+      const int j = j0 + threadIdx.x;
+      double v = 0.0;
+      unsigned long long kk = 0;
+      if (j < n) {
+        v = E[(size_t)i * n + j];
+        kk = dkey(v);
+      }
+      const bool tie = j < n && kk == tau;
+      // tie rank within this chunk, then selection
+      const unsigned bt = __ballot_sync(0xffffffffu, tie);
+      if (lane == 0) wtie[w] = __popc(bt);
+      __syncthreads();
+      int tb = 0;
+      for (int q = 0; q < w; ++q) tb += wtie[q];
+      const long long my_tie = tr + tb + __popc(bt & ((1u << lane) - 1u));
+      const bool sel = j < n && (kk > tau || (tie && my_tie < c));
+      const unsigned bs = __ballot_sync(0xffffffffu, sel);
+      if (lane == 0) wsel[w] = __popc(bs);
+      __syncthreads();
+      int sb = 0;
+      for (int q = 0; q < w; ++q) sb += wsel[q];
+      if (sel) {
+        const long long p = pos + sb + __popc(bs & ((1u << lane) - 1u));
+        if (p < cap) {
+          ij[2 * p] = i;
+          ij[2 * p + 1] = j;
+          val[p] = v;
+        }
+      }
+      int st = 0, tt = 0;
+      for (int q = 0; q < 8; ++q) {
+        st += wsel[q];
+        tt += wtie[q];
+      }
+      pos += st;
+      tr += tt;
+      __syncthreads();
+    }
+  }
+}
+
+// The m largest edge scores of node nodes[b] (partners j != i; ties to the
+// lower j), from the upper triangle: value (i, j) = E[min][max].
+__global__ void __launch_bounds__(1024) k_node_top_edges(const double* __restrict__ E, int n,
+                                                          const long long* __restrict__ nodes, int m,
+                                                          long long* __restrict__ partner, double* __restrict__ pval) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  const int i = (int)nodes[blockIdx.x];
+  double pv = INFINITY;
+  int pi = -1;
+  for (int t = 0; t < m; ++t) {
+    double bv = -INFINITY;
+    int bidx = INT_MAX;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      if (j == i) continue;
+      const double v = i < j ? E[(size_t)i * n + j] : E[(size_t)j * n + i];
+      const bool after = v < pv || (v == pv && j > pi);
+      if (after && better(v, j, bv, bidx)) {
+        bv = v;
+        bidx = j;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (better(ov, oi, bv, bidx)) {
+        bv = ov;
+        bidx = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sv[threadIdx.x >> 5] = bv;
+      si[threadIdx.x >> 5] = bidx;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      bv = threadIdx.x < (blockDim.x >> 5) ? sv[threadIdx.x] : -INFINITY;
+      bidx = threadIdx.x < (blockDim.x >> 5) ? si[threadIdx.x] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (better(ov, oi, bv, bidx)) {
+          bv = ov;
+          bidx = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        sv[0] = bv;
+        si[0] = bidx;
+        partner[(size_t)blockIdx.x * m + t] = bidx == INT_MAX ? -1 : bidx;
+        pval[(size_t)blockIdx.x * m + t] = bidx == INT_MAX ? 0.0 : bv;
+      }
+    }
+    __syncthreads();
+    pv = sv[0];
+    pi = si[0];
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- changed edges only
@@ -623,6 +919,143 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
     k_topk<<<1, 1024, 0, st>>>(F, n, topk, top_idx);
     CDL_TRY(L.done());
   }
+  return CDL_OK;
+}
+
+int cad_edges(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
+              const double* vol1, const double* vol2, int64_t n64, int k, bool fp64, double delta, int64_t cap,
+              const int64_t* nodes, int n_nodes, int m, int64_t* ij, double* val, int64_t* partner, double* pval,
+              double* F, cdl_edge_result* res) {
+  const int n = (int)n64;
+  cudaStream_t st = ctx->stream;
+  const int nb = (n + ST - 1) / ST;
+  void *vab, *vc, *vE, *vF, *vp, *vs, *vcnt, *voff;
+  CDL_TRY(score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, fp64, &vab));
+  CDL_TRY(ws_get(ctx, "score.contrib", (size_t)nb * n * sizeof(double), &vc));
+  CDL_TRY(ws_get(ctx, "edges.E", (size_t)n * n * sizeof(double), &vE));
+  CDL_TRY(ws_get(ctx, "edges.F", (size_t)n * sizeof(double), &vF));
+  const int mb = std::min(n, ctx->sm_count * 8);
+  CDL_TRY(ws_get(ctx, "edges.part", (size_t)mb * 16, &vp));
+  CDL_TRY(ws_get(ctx, "edges.scal", 64, &vs));
+  CDL_TRY(ws_get(ctx, "edges.rowcnt", 2 * (size_t)n * sizeof(int), &vcnt));
+  CDL_TRY(ws_get(ctx, "edges.rowoff", 2 * (size_t)n * sizeof(long long) + 16, &voff));
+  double* E = static_cast<double*>(vE);
+  double* Fw = F ? F : static_cast<double*>(vF);
+  double* scal = static_cast<double*>(vs);
+  double* psum = static_cast<double*>(vp);
+  unsigned long long* pcnt = reinterpret_cast<unsigned long long*>(psum + mb);
+  const long long tiles = (long long)nb * (nb + 1) / 2;
+  {
+    Launch L(ctx, CDL_KC_SCORE, 8.0 * (double)n * (n - 1));
+    k_edge_pairs<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, vab, n, k, fp64 ? 1 : 0, static_cast<double*>(vc), E);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_score_reduce<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const double*>(vc), nb, n, Fw);
+    CDL_TRY(L.done());
+  }
+  // masses: total (tau = 0 counts every entry) and the largest key
+  auto mass = [&](unsigned long long tau, double* sum, unsigned long long* cnt) -> int {
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_edge_mass<<<mb, 256, 0, st>>>(E, n, tau, psum, pcnt);
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_edge_mass_total<<<1, 32, 0, st>>>(psum, pcnt, mb, scal);
+      CDL_TRY(L.done());
+    }
+    double h[2];
+    CDL_CUDA_TRY(cudaMemcpyAsync(h, scal, 16, cudaMemcpyDeviceToHost, st));
+    CDL_CUDA_TRY(cudaStreamSynchronize(st));
+    *sum = h[0];
+    std::memcpy(cnt, &h[1], 8);
+    return CDL_OK;
+  };
+  double total;
+  unsigned long long m_all;
+  CDL_TRY(mass(0ull, &total, &m_all));
+  unsigned long long* dmax = reinterpret_cast<unsigned long long*>(scal + 4);
+  CDL_CUDA_TRY(cudaMemsetAsync(dmax, 0, 8, st));
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_edge_maxkey<<<mb, 256, 0, st>>>(E, n, dmax);
+    CDL_TRY(L.done());
+  }
+  unsigned long long kmax = 0;
+  CDL_CUDA_TRY(cudaMemcpyAsync(&kmax, dmax, 8, cudaMemcpyDeviceToHost, st));
+  CDL_CUDA_TRY(cudaStreamSynchronize(st));
+  res->total = total;
+  unsigned long long tau = 0;
+  long long c = 0;
+  bool none = total < delta;
+  if (!none) {
+    // largest tau in [0, kmax] with total - mass(>= tau) < delta (tau = 0 qualifies)
+    unsigned long long lo = 0, hi = kmax;
+    while (lo < hi) {
+      const unsigned long long mid = lo + (hi - lo + 1) / 2;
+      double s;
+      unsigned long long cn;
+      CDL_TRY(mass(mid, &s, &cn));
+      if (total - s < delta)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    tau = lo;
+    // entries above tau are taken; ties at tau one by one in (i, j) order
+    double s_gt = 0.0, s_ge = 0.0;
+    unsigned long long c_gt = 0, c_ge = 0;
+    CDL_TRY(mass(tau + 1, &s_gt, &c_gt));
+    CDL_TRY(mass(tau, &s_ge, &c_ge));
+    const long long ties = (long long)(c_ge - c_gt);
+    double v;
+    std::memcpy(&v, &tau, 8);
+    double rem = total - s_gt;
+    while (!(rem < delta) && c < ties) {
+      rem -= v;
+      ++c;
+    }
+    res->remaining = rem;
+    res->threshold = v;
+  } else {
+    res->remaining = total;
+    res->threshold = INFINITY;
+    tau = ~0ull;   // nothing is above it
+  }
+  res->n_ties_taken = c;
+  int* cgt = static_cast<int*>(vcnt);
+  int* ceq = cgt + n;
+  long long* off = static_cast<long long*>(voff);
+  long long* tie0 = off + n;
+  long long* tot = tie0 + n;
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_edge_rowcount<<<mb, 256, 0, st>>>(E, n, tau, cgt, ceq);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_edge_offsets<<<1, 1024, 0, st>>>(cgt, ceq, n, none ? 0 : c, off, tie0, tot);
+    CDL_TRY(L.done());
+  }
+  if (cap > 0) {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_edge_write<<<mb, 256, 0, st>>>(E, n, tau, none ? 0 : c, off, tie0, cap, reinterpret_cast<long long*>(ij), val);
+    CDL_TRY(L.done());
+  }
+  if (n_nodes > 0 && m > 0) {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_node_top_edges<<<n_nodes, 1024, 0, st>>>(E, n, reinterpret_cast<const long long*>(nodes), m,
+                                               reinterpret_cast<long long*>(partner), pval);
+    CDL_TRY(L.done());
+  }
+  long long count = 0;
+  CDL_CUDA_TRY(cudaMemcpyAsync(&count, tot, 8, cudaMemcpyDeviceToHost, st));
+  CDL_CUDA_TRY(cudaStreamSynchronize(st));
+  res->n_edges = count;
   return CDL_OK;
 }
 
