@@ -656,6 +656,31 @@ def main():
                                     "frac": ach8 / peak8,
                                     "peak_source": "2 x measured bf16_tflops_sustained (nominal e4m3/bf16 ratio)"}}
 
+    # opt-in chain truncation (levels whose row sums fall to 2^-24 are not formed)
+    trunc = None
+    if args.compare_f32 and args.chain == "bf16":
+        ot = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_BF16, cdl.CDL_F32, SEED, 0.0,
+                               cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0, cdl.CDL_CHAIN_TRUNCATE)
+        Ft = torch.empty(n, dtype=torch.float64, device="cuda")
+        tt = torch.empty(TOPK, dtype=torch.int64, device="cuda")
+        step(ot, X1, X2, Ft, tt)   # warm-up
+        cdl.cdl_ctx_reset_counters(ctx)
+        cdl.cdl_ctx_set_timing(ctx, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(ot, X1, X2, Ft, tt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _, _, sq_cnt, _ = cdl.cdl_ctx_timing(ctx, cdl.CDL_KC_SQUARE)
+        cdl.cdl_ctx_set_timing(ctx, False)
+        t_ms = e0.elapsed_time(e1)
+        trunc = {"value": 1000.0 / t_ms, "unit": "pairs/s", "ms_per_step": t_ms, "steps": 1, "warmup": 1,
+                 "squarings_per_pair": int(sq_cnt), "configured_squarings_per_pair": 2 * (D_CHAIN - 1),
+                 "solve_iters": [s1.iters, s2.iters], "rel_res": max(s1.rel_res, s2.rel_res),
+                 "same_top": tt.cpu().tolist() == top.cpu().tolist(),
+                 "max_rel_diff_F_vs_full_chain": float(((Ft - F).abs() / F).max())}
+
     # max over ranks
     step_ms, e2e_s = rank_max([step_ms, e2e_s], dist, "cuda")
     value = pairs_per_second(step_ms, world)
@@ -696,6 +721,7 @@ def main():
             "cpu_baseline": cpu,
             "f32_path": f32,
             "fp8_tile_path": fp8t,
+            "truncated_chain_path": trunc,
             "e2e": {"value": pairs_per_second(e2e_s * 1000.0, world), "unit": "pairs/s",
                     "h2d_bytes_per_step": 2 * n * T * 8,
                     "d2h_bytes_per_step": n * 8 + TOPK * 8, "same_top_as_device_run": same_top},

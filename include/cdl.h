@@ -198,13 +198,24 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  * slot that is copied to the host on a copy stream while the next squaring
  * runs, and each application of the chain loads level l + 1 over the link
  * while level l is applied. Results are identical to device levels;
- * cdl_chain_level then returns host pointers (and waits for the copies). */
-enum { CDL_CHAIN_DEFAULT = 0, CDL_CHAIN_HOST_LEVELS = 1 };
+ * cdl_chain_level then returns host pointers (and waits for the copies).
+ * CDL_CHAIN_TRUNCATE (opt-in; not with CDL_CHAIN_HOST_LEVELS): after each
+ * squaring, stop when the new level's max absolute row sum (a bound on its
+ * spectral norm, the level being symmetric) is at most 2^-24: neither it nor
+ * any later level (their norms square) can change a float32 x + S~ x, so the
+ * chain keeps d_eff <= d levels (cdl_chain_depth) and the solve applies only
+ * those. For well-connected dense graphs the deflated levels decay like
+ * lambda_2^(2^i) and d_eff is a few levels. Changes the configured d, hence
+ * opt-in. */
+enum { CDL_CHAIN_DEFAULT = 0, CDL_CHAIN_HOST_LEVELS = 1, CDL_CHAIN_TRUNCATE = 2 };
+/* Levels in use: d, or fewer after CDL_CHAIN_TRUNCATE. */
+int cdl_chain_depth(const cdl_chain* chain, int32_t* d_eff);
 int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double* D,
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
                     int32_t flags, cdl_chain** inout);
 int cdl_chain_free(cdl_chain* chain);
-/* Device pointer to level i (npad x npad, chain dtype, zero padded) and npad. */
+/* Device pointer to level i (npad x npad, chain dtype, zero padded) and npad;
+ * i < d_eff (levels past a truncation are not formed). */
 int cdl_chain_level(const cdl_chain* chain, int32_t i, void** level, int64_t* npad);
 /* Device pointer to the bf16 view of level i that the solve's tensor-core
  * apply reads (npad x npad): the level itself for CDL_BF16 chains, its bf16

@@ -26,6 +26,7 @@ CDL_ERR_UNSUPPORTED = -6
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3, CDL_FP8E4M3_T128 = 0, 1, 2, 3, 4
 CDL_SOLVE_FULL_RESIDUAL = 1
 CDL_CHAIN_HOST_LEVELS = 1
+CDL_CHAIN_TRUNCATE = 2
 CDL_SCORE_CHANGED_ONLY = 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1
 CDL_DEBUG_BATCH_VARIANT = 2
@@ -95,6 +96,7 @@ _SIGS = {
     "cdl_build_graph_static": [_P, _I64, _I32, _D, _P, _P, _P, _P, _P],
     "cdl_chain_build": [_P, _P, ctypes.c_int, _P, _P, _I64, _I32, ctypes.c_int, _I32, ctypes.POINTER(_P)],
     "cdl_chain_free": [_P],
+    "cdl_chain_depth": [_P, ctypes.POINTER(_I32)],
     "cdl_chain_level": [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
     "cdl_chain_level_scale": [_P, _I32, ctypes.POINTER(_D)],
     "cdl_chain_apply_level": [_P, _I32, ctypes.POINTER(_P)],
@@ -201,6 +203,13 @@ def cdl_chain_build(ctx, A, a_dtype, D, vol, n, d, chain_dtype, flags=0, chain=N
     st = _lib.cdl_chain_build(ctx, _ptr(A), a_dtype, _ptr(D), _ptr(vol), n, d, chain_dtype, flags,
                               ctypes.byref(h))
     return st, h
+
+
+def cdl_chain_depth(chain):
+    """Returns (status, d_eff)."""
+    d = _I32()
+    st = _lib.cdl_chain_depth(chain, ctypes.byref(d))
+    return st, d.value
 
 
 def cdl_chain_free(chain) -> int:

@@ -294,8 +294,14 @@ int cdl_chain_free(cdl_chain* ch) {
   return CDL_OK;
 }
 
+int cdl_chain_depth(const cdl_chain* ch, int32_t* d_eff) {
+  if (!ch || !d_eff) return CDL_ERR_INVALID_ARG;
+  *d_eff = ch->d_eff;
+  return CDL_OK;
+}
+
 int cdl_chain_level(const cdl_chain* ch, int32_t i, void** level, int64_t* npad) {
-  if (!ch || i < 0 || i >= ch->d) return CDL_ERR_INVALID_ARG;
+  if (!ch || i < 0 || i >= ch->d_eff) return CDL_ERR_INVALID_ARG;
   if (ch->host_levels) CDL_CUDA_TRY(cudaStreamSynchronize(ch->copy));   // copies to the host complete
   if (level) *level = ch->level(i);
   if (npad) *npad = ch->npad;
@@ -337,8 +343,11 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
                     int32_t flags, cdl_chain** inout) {
   if (!ctx || !inout) return CDL_ERR_INVALID_ARG;
-  if (n < 2 || n > (1 << 20) || d < 1 || d > 64 || (flags & ~CDL_CHAIN_HOST_LEVELS)) return CDL_ERR_INVALID_ARG;
+  if (n < 2 || n > (1 << 20) || d < 1 || d > 64 || (flags & ~(CDL_CHAIN_HOST_LEVELS | CDL_CHAIN_TRUNCATE)))
+    return CDL_ERR_INVALID_ARG;
   const bool host_levels = (flags & CDL_CHAIN_HOST_LEVELS) != 0;
+  const bool truncate = (flags & CDL_CHAIN_TRUNCATE) != 0;
+  if (host_levels && truncate) return CDL_ERR_UNSUPPORTED;
   if (host_levels && chain_dtype != CDL_BF16) return CDL_ERR_UNSUPPORTED;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
   if (chain_dtype != CDL_F64 && chain_dtype != CDL_F32 && chain_dtype != CDL_BF16 &&
@@ -393,10 +402,32 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     CDL_CUDA_TRY(cudaMemsetAsync(ch->D + n, 0, (npad - n) * sizeof(double), ctx->stream));
   CDL_CUDA_TRY(cudaMemcpyAsync(ch->vol, vol, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   int st = chain_init(ctx, ch, static_cast<const double*>(A));
+  ch->d_eff = d;
+  unsigned* norm_bits = nullptr;
+  if (truncate) {
+    void* vn;
+    st = st == CDL_OK ? ws_get(ctx, "chain.norm", sizeof(unsigned), &vn) : st;
+    norm_bits = static_cast<unsigned*>(vn);
+  }
   for (int i = 0; st == CDL_OK && i + 1 < d; ++i) {
     if (chain_dtype == CDL_FP8E4M3) st = fp8_level_bound(ctx, ch, i);
     if (st == CDL_OK)
       st = fp8t ? chain_square_fp8t(ctx, ch, i) : tensor ? chain_square_tc(ctx, ch, i) : chain_square_simt(ctx, ch, i);
+    if (st == CDL_OK && truncate) {
+      // ||S~_{i+1}||_2 <= its max row sum; at 2^-24 or less neither it nor the
+      // levels after it (their norms square) can change a float32 x + S~ x
+      st = level_inf_norm(ctx, ch, i + 1, norm_bits);
+      unsigned bits = 0;
+      if (st == CDL_OK) st = cudaMemcpyAsync(&bits, norm_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream)
+                                 == cudaSuccess ? CDL_OK : CDL_ERR_CUDA;
+      if (st == CDL_OK) st = cudaStreamSynchronize(ctx->stream) == cudaSuccess ? CDL_OK : CDL_ERR_CUDA;
+      float eta;
+      std::memcpy(&eta, &bits, sizeof(float));
+      if (st == CDL_OK && eta <= 0x1p-24f) {
+        ch->d_eff = i + 1;
+        break;
+      }
+    }
   }
   if (st != CDL_OK) {
     if (!*inout) cdl_chain_free(ch);

@@ -392,6 +392,51 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
   return L.done();
 }
 
+// Max absolute row sum of an npad x npad level (rows of threads; atomicMax
+// on the bits of non-negative floats orders them like their values).
+template <typename T>
+__global__ void __launch_bounds__(256) k_level_inf_norm(const T* __restrict__ L, int np, unsigned* __restrict__ out) {
+  __shared__ float red[8];
+  for (int i = blockIdx.x; i < np; i += gridDim.x) {
+    float s = 0.f;
+    const T* row = L + (size_t)i * np;
+    for (int j = threadIdx.x; j < np; j += 256) s += fabsf((float)row[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      atomicMax(out, __float_as_uint(t * (1.0f + 0x1p-12f)));   // rounded up: a bound
+    }
+    __syncthreads();
+  }
+}
+
+int level_inf_norm(cdl_ctx* ctx, const cdl_chain* ch, int level, unsigned* out_bits) {
+  const int np = (int)ch->npad;
+  const int blocks = std::min(np, ctx->sm_count * 8);
+  CDL_CUDA_TRY(cudaMemsetAsync(out_bits, 0, sizeof(unsigned), ctx->stream));
+  Launch L(ctx, CDL_KC_MISC, 2.0 * np * (double)np);
+  switch (ch->dtype) {
+    case CDL_F64:
+      k_level_inf_norm<double><<<blocks, 256, 0, ctx->stream>>>(static_cast<const double*>(ch->level(level)), np,
+                                                                out_bits);
+      break;
+    case CDL_F32:
+      k_level_inf_norm<float><<<blocks, 256, 0, ctx->stream>>>(static_cast<const float*>(ch->level(level)), np,
+                                                               out_bits);
+      break;
+    default:   // bf16 levels, or the bf16 copies of e4m3 levels
+      if (ch->host_levels) return CDL_ERR_UNSUPPORTED;
+      k_level_inf_norm<__nv_bfloat16><<<blocks, 256, 0, ctx->stream>>>(
+          static_cast<const __nv_bfloat16*>(ch->level16(level)), np, out_bits);
+      break;
+  }
+  return L.done();
+}
+
 int fp8_level_bound(cdl_ctx* ctx, cdl_chain* ch, int level) {
   const int np = (int)ch->npad;
   Launch L(ctx, CDL_KC_MISC, (double)np * np);

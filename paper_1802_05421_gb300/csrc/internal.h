@@ -77,6 +77,7 @@ struct cdl_chain {
   int device = 0;
   int64_t n = 0, npad = 0;
   int32_t d = 0;
+  int32_t d_eff = 0;          // levels in use (d unless CDL_CHAIN_TRUNCATE stopped earlier)
   cdl_dtype dtype = CDL_F64;
   size_t elem = 8;
   void* levels = nullptr;     // d * npad * npad elements
@@ -142,6 +143,9 @@ int graph_build_static(const double* X, int64_t n, int T, double sigma, double* 
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A);
 int chain_square_simt(cdl_ctx* ctx, cdl_chain* ch, int level);
 int fp8_level_bound(cdl_ctx* ctx, cdl_chain* ch, int level);
+// Max absolute row sum of level i (an upper bound of its spectral norm, the
+// level being symmetric), as float bits in *out_bits (device).
+int level_inf_norm(cdl_ctx* ctx, const cdl_chain* ch, int level, unsigned* out_bits);
 int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void* partial,
                int k, int splits);
 // ooc.cu: levels in pinned host memory (bf16 chains)

@@ -882,7 +882,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       CDL_TRY(L.done());
     }
     // x <- (I + S~_lvl) x for every level
-    for (int lvl = 0; lvl < ch->d; ++lvl) {
+    for (int lvl = 0; lvl < ch->d_eff; ++lvl) {
       if (bf16) {
         CDL_TRY(apply_tc(ctx, ch, lvl, vxop, static_cast<float*>(vpart), kp, splits));
         dim3 g((np + 31) / 32, (kp + 31) / 32);
