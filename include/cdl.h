@@ -272,9 +272,14 @@ typedef struct {
  *   P R = D^{-1/2} prod_{i<d} (I + S~_i) D^{-1/2} R,
  * then Z is shifted to D-weighted zero column means (sum_i D_i Z[i,:] = 0).
  * For Z_0 = 0 this is the paper's y_{t+1} = y_t - P2 y_t + chi with
- * chi = P1 b and P2 = P1 L. The residual Y - L Z is formed in float-float
- * arithmetic (about 48 significant bits) from float64 A, D, Y, Z after the
- * first application; later steps update it recursively, R -= D dZ - A dZ,
+ * chi = P1 b and P2 = P1 L. The residual Y - L Z is formed from float64 A,
+ * D, Y, Z after the first application: for tensor-core chains A Z runs on
+ * the tensor cores from exact bf16 slices (A and Z / c_r, c_r a power of two
+ * per column, each as six signed base-256 digits on the grids 2^-8s; every
+ * slice product and every 256-term chunk sum is exact in float32; chunk sums
+ * are added as integers and scaled into float64), leaving about 2^-50 of
+ * |A||Z|; for CUDA-core chains in float-float arithmetic (about 48
+ * significant bits). Later steps update it recursively, R -= D dZ - A dZ,
  * with A dZ in float32 (error about 1e-7 of ||L dZ||, i.e. of the previous
  * residual). A bound on the accumulated error of these updates is kept; when
  * the stopping test passes with that bound above rel_tol / 10, the residual
@@ -282,7 +287,8 @@ typedef struct {
  * CDL_SOLVE_FULL_RESIDUAL forms it in float-float after every application.
  * Synchronises once per application to read the residual norm.
  * chain: from cdl_chain_build on the same graph. A: device n x n (CDL_F64).
- * Y: device n x k float64. Z: device n x k float64 output.
+ * Y: device n x k float64. Z: device n x k float64 output; k <= 128 for
+ * tensor-core chains (CDL_ERR_UNSUPPORTED above), k <= 1024 otherwise.
  * stats: host, may be NULL. Returns CDL_ERR_NOT_CONVERGED (Z still written)
  * when rel_tol > 0 was not reached within max_iter applications, and stops
  * early with it when the residual is not finite or exceeds 1e6 ||Y|| (a

@@ -286,6 +286,7 @@ int cdl_chain_free(cdl_chain* ch) {
   cudaFree(ch->levels16);
   cudaFree(ch->amax);
   cudaFree(ch->ahl);
+  cudaFree(ch->aslices);
   cudaFree(ch->tscale);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
@@ -378,12 +379,15 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
     const size_t l16_bytes = (chain_dtype == CDL_FP8E4M3 || fp8t) ? (size_t)d * npad * npad * 2 : 0;
     const size_t ts_bytes = fp8t ? (size_t)d * (npad / 128) * (npad / 128) * sizeof(float) : 0;
-    const size_t ahl_bytes = 2 * (size_t)n * n * sizeof(float);
-    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes + l16_bytes + ahl_bytes > ctx->ws_cap) {
+    // float-float residual operand (CUDA-core chains) or exact bf16 slices (tensor chains)
+    const size_t ahl_bytes = tensor ? 0 : 2 * (size_t)n * n * sizeof(float);
+    const size_t slice_bytes = tensor ? 6 * (size_t)npad * npad * 2 : 0;
+    if (ctx->ws_cap && ctx->ws_used + bytes + aop_bytes + l16_bytes + ahl_bytes + slice_bytes > ctx->ws_cap) {
       delete ch;
       return CDL_ERR_OOM;
     }
-    if (cudaMalloc(&ch->ahl, ahl_bytes) != cudaSuccess ||
+    if ((ahl_bytes && cudaMalloc(&ch->ahl, ahl_bytes) != cudaSuccess) ||
+        (slice_bytes && cudaMalloc(&ch->aslices, slice_bytes) != cudaSuccess) ||
         (aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
         (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
                        cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||
@@ -457,6 +461,7 @@ int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const void* A, cdl_dtype 
     return CDL_ERR_INVALID_ARG;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
   if (ch->device != ctx->device) return CDL_ERR_INVALID_ARG;
+  if (ch->dtype != CDL_F64 && ch->dtype != CDL_F32 && k > 128) return CDL_ERR_UNSUPPORTED;   // tensor-core apply: N = 2 kp <= 256
   CDL_TRY(set_device(ctx));
   CDL_TRY(dev_ptr(ctx, A));
   CDL_TRY(dev_ptr(ctx, Y));

@@ -177,6 +177,54 @@ __global__ void __launch_bounds__(256) k_split_a(const double* __restrict__ A, s
   }
 }
 
+// A as six bf16 planes on the grids 2^-8s: the signed base-256 digits of A
+// rounded to 2^-48 (A in [0, 1]); zero padded to npad x npad. The rounding
+// uses the float64 bit pattern (integer operations only): A = m 2^(e - 52),
+// N = m / 2^(4 - e) rounded to nearest (ties up).
+__device__ __forceinline__ long long grid48(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;                                   // zero (no subnormal kernel values)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = 1023 + 4 - e;                             // a = m 2^(e - 1075); a 2^48 = m 2^(e - 1027)
+  if (sh >= 60) return 0;
+  if (sh <= 0) return (long long)(m << -sh);
+  return (long long)((m + (1ull << (sh - 1))) >> sh);
+}
+
+__global__ void __launch_bounds__(256) k_slice_a(const double* __restrict__ A, int n, int np,
+                                                  __nv_bfloat16* __restrict__ S) {
+  const size_t plane = (size_t)np * np;
+  const size_t groups = plane / 8;                        // np is a multiple of 128
+  for (size_t gidx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; gidx < groups;
+       gidx += (size_t)gridDim.x * blockDim.x) {
+    const size_t idx0 = gidx * 8;
+    const int i = (int)(idx0 / np), j0 = (int)(idx0 % np);
+    long long N[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) N[e] = (i < n && j0 + e < n) ? grid48(A[(size_t)i * n + j0 + e]) : 0;
+#pragma unroll
+    for (int s = 1; s <= 6; ++s) {
+      const int sh = 48 - 8 * s;
+      const float scale = __int_as_float((127 - 8 * s) << 23);   // 2^-8s
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        long long d0 = N[e], d1 = N[e + 1];
+        if (sh > 0) {
+          d0 = (N[e] + (1LL << (sh - 1))) >> sh;
+          d1 = (N[e + 1] + (1LL << (sh - 1))) >> sh;
+        }
+        N[e] -= d0 << sh;
+        N[e + 1] -= d1 << sh;
+        __nv_bfloat162 h = __floats2bfloat162_rn((float)d0 * scale, (float)d1 * scale);
+        w[e / 2] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      *reinterpret_cast<uint4*>(S + (size_t)(s - 1) * plane + idx0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
   double fnb = nb + 0.5;
   int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
@@ -325,10 +373,15 @@ int square_impl(cdl_ctx* ctx, cdl_chain* ch, int level) {
 
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
   const int n = (int)ch->n, np = (int)ch->npad;
-  {
+  if (ch->ahl) {
     const size_t cnt = (size_t)n * n;
     Launch L(ctx, CDL_KC_CHAIN_INIT, 16.0 * cnt);
     k_split_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, cnt, ch->ahl, ch->ahl + cnt);
+    CDL_TRY(L.done());
+  }
+  if (ch->aslices) {
+    Launch L(ctx, CDL_KC_CHAIN_INIT, 8.0 * n * (double)n + 12.0 * np * (double)np);
+    k_slice_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, n, np, static_cast<__nv_bfloat16*>(ch->aslices));
     CDL_TRY(L.done());
   }
   void* wsu;

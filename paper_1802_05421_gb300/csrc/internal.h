@@ -86,6 +86,7 @@ struct cdl_chain {
   unsigned* amax = nullptr;   // fp8 chains: per-level bound of |value| (float bits), scale = amax/448
   float* ahl = nullptr;       // A as float hi + lo planes (n x n each), the float-float residual's operand
   float* tscale = nullptr;    // per-tile e4m3 chains: d x (npad/128)^2 tile scales
+  void* aslices = nullptr;    // tensor chains: A as 6 bf16 planes npad x npad on the grids 2^-8s
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
@@ -163,6 +164,9 @@ int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i);
 int ooc_prefetch(cdl_chain* ch, int i);
 // tc_gemm.cu
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
+// A Z on the tensor cores from exact bf16 slices (A's in the chain, Z / c in
+// zslices: 6 planes kp x npad) into G (npad x kp float64).
+int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, double* G);
 int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level);
 int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch);
 // Grouped (batched) tcgen05 launches: one launch over the tiles of many

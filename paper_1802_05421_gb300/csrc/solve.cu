@@ -407,6 +407,73 @@ __global__ void __launch_bounds__(256) k_residual_update_tc(const float* __restr
 }
 
 
+// ---- exact-slice residual (tensor chains): Z / c_r in six bf16 slices,
+// c_r the power of two just above column r's largest |Z|.
+__global__ void k_zcolmax(const double* __restrict__ Z, size_t count, int k, unsigned long long* __restrict__ mbits) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x)
+    atomicMax(mbits + idx % k, (unsigned long long)__double_as_longlong(fabs(Z[idx])));
+}
+
+__device__ __forceinline__ double pow2_above(unsigned long long bits) {
+  if (bits == 0) return 1.0;
+  const int e = (int)((bits >> 52) & 0x7FF);
+  return ldexp(1.0, e - 1022);
+}
+
+// planes S[t][rl][j] (t = 0..5, rl < kg, j < npad) for columns c0 + rl.
+__global__ void __launch_bounds__(256) k_zslice(const double* __restrict__ Z, int n, int k, int np, int c0, int kg,
+                                                 const unsigned long long* __restrict__ mbits,
+                                                 __nv_bfloat16* __restrict__ S, double* __restrict__ cs) {
+  const size_t plane = (size_t)kg * np;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane; idx += (size_t)gridDim.x * blockDim.x) {
+    const int rl = (int)(idx / np), j = (int)(idx % np);
+    const int r = c0 + rl;
+    long long N = 0;
+    if (r < k) {
+      const double c = pow2_above(mbits[r]);
+      if (j == 0) cs[r] = c;
+      if (j < n) N = llrint(Z[(size_t)j * k + r] / c * 0x1p48);   // |Z / c| < 1, division by a power of two is exact
+    }
+#pragma unroll
+    for (int t = 1; t <= 6; ++t) {
+      const int sh = 48 - 8 * t;
+      long long d = N;
+      if (sh > 0) d = (N + (1LL << (sh - 1))) >> sh;
+      N -= d << sh;
+      S[(size_t)(t - 1) * plane + idx] = __float2bfloat16_rn(ldexpf((float)d, -8 * t));
+    }
+  }
+}
+
+// R = (Y - D o Z) + c_r G (G from the column groups of at most 128), and
+// per-block sums of R^2.
+__global__ void __launch_bounds__(256) k_resid_combine(const double* __restrict__ Y, const double* __restrict__ Z,
+                                                        const double* __restrict__ D, int n, int k, int np,
+                                                        const double* __restrict__ G, const double* __restrict__ cs,
+                                                        double* __restrict__ R, double* __restrict__ part) {
+  __shared__ double red[8];
+  double sq = 0.0;
+  const size_t total = (size_t)n * k;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / k), r = (int)(idx % k);
+    const int g = r / 128, rl = r % 128;
+    const int kg = min(128, ((k - g * 128) + 31) / 32 * 32);
+    const double az = cs[r] * G[(size_t)g * np * 128 + (size_t)i * kg + rl];
+    const double v = (Y[idx] - D[i] * Z[idx]) + az;
+    R[idx] = v;
+    sq = fma(v, v, sq);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
 // ---------------------------------------------------------------- batched form
 // The kernels below run one step of the refinement for every graph of a
 // batch in one launch; a block finds its graph and block index in a tile
@@ -787,6 +854,41 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   int nparts = res_gx * res_gy;   // per-block partial sums of R^2 written by the last residual kernel
   // Full float-float residual R = Y - L Z.
   auto full_residual = [&](double* rel_out) -> int {
+    if (ch->aslices) {
+      // A Z from exact bf16 slices on the tensor cores, in column groups of <= 128
+      const int ngroups = (k + 127) / 128;
+      void *vzs, *vG, *vmb, *vcs;
+      CDL_TRY(ws_get(ctx, "solve.zslices", 6 * (size_t)128 * np * 2, &vzs));
+      CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * np * 128 * sizeof(double), &vG));
+      CDL_TRY(ws_get(ctx, "solve.zmax", (size_t)k * 8, &vmb));
+      CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcs));
+      CDL_CUDA_TRY(cudaMemsetAsync(vmb, 0, (size_t)k * 8, st));
+      {
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_zcolmax<<<std::min<size_t>(blocks_for(nk, 256), (size_t)ctx->sm_count * 8), 256, 0, st>>>(
+            Z, nk, k, static_cast<unsigned long long*>(vmb));
+        CDL_TRY(L.done());
+      }
+      for (int g = 0; g < ngroups; ++g) {
+        const int c0 = g * 128;
+        const int kg = std::min(128, (k - c0 + 31) / 32 * 32);
+        {
+          Launch L(ctx, CDL_KC_MISC, 0);
+          k_zslice<<<ctx->sm_count * 4, 256, 0, st>>>(Z, n, k, np, c0, kg,
+                                                       static_cast<const unsigned long long*>(vmb),
+                                                       static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcs));
+          CDL_TRY(L.done());
+        }
+        CDL_TRY(resid_tc(ctx, ch, vzs, kg, static_cast<double*>(vG) + (size_t)g * np * 128));
+      }
+      const int nb = std::min(1024, (int)blocks_for(nk, 256));
+      Launch L(ctx, CDL_KC_RESIDUAL, 0);
+      k_resid_combine<<<nb, 256, 0, st>>>(Y, Z, ch->D, n, k, np, static_cast<const double*>(vG),
+                                          static_cast<const double*>(vcs), R, red);
+      CDL_TRY(L.done());
+      nparts = nb;
+      return CDL_OK;
+    }
     {
       Launch L(ctx, CDL_KC_MISC, 0);
       k_split<<<blocks_for(nk, 256), 256, 0, st>>>(Z, nk, static_cast<float*>(vzh), static_cast<float*>(vzl));

@@ -818,6 +818,230 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- exact-slice residual product
+// A Z for the float64-class residual, on the bf16 tensor cores. A (entries in
+// [0, 1]) and Z / c (c a power of two per column) are written as sums of six
+// bf16 slices on the fixed grids 2^-8s (signed base-256 digits of the values
+// rounded to 2^-48), so every slice product a_s z_t is exact in float32 and
+// lies on the grid 2^-8(s+t), and a float32 sum of 256 of them (one K-chunk)
+// is exact too (at most 2^24 grid steps). The MMA sums one K-chunk of one
+// slice pair into a TMEM buffer; the epilogue converts it to an integer
+// count of grid steps, adds it to int32 accumulators, and every 64 chunks
+// (at most 2^30 steps) adds them, scaled by 2^-8(s+t), to the float64 result
+// G. The 21 slice pairs with s + t <= 7 leave about 2^-50 of |A| |Z / c|:
+// A Z = c G to float64 accuracy, as the ordering of the float64 additions
+// allows. Warp roles as in k_tc_fp8t (576 threads, 16 epilogue warps).
+constexpr int RS_SLICES = 6;
+constexpr int RS_MAX_PAIRS = 21;
+constexpr int RS_STAGES = 6;
+constexpr int RS_A = 128 * 128;                 // A k-block: 128 rows x 64 bf16
+constexpr int RS_STAGE_BYTES = RS_A + 128 * 128; // + B k-block: up to 128 rows x 64 bf16
+constexpr int RS_SMEM_BYTES = RS_STAGES * RS_STAGE_BYTES + 512 + 1024;
+constexpr int RS_TMEM_COLS = 256;                // two buffers of up to 128 columns
+constexpr int RS_CHUNK_KB = 4;                   // k-blocks (of 64) per exact chunk: K = 256
+constexpr int RS_FLUSH = 64;                     // chunks per int32 flush
+
+struct ResidMaps {
+  CUtensorMap a[RS_SLICES];   // slice planes of A, box 64 x 128 rows
+  CUtensorMap b[RS_SLICES];   // slice planes of Z / c, transposed (kp x npad), box 64 x kp rows
+};
+
+struct ResidParams {
+  int num_tiles;   // npad / 128
+  int kblocks;     // npad / 64
+  int kp;          // MMA N (multiple of 32, <= 128)
+  int npairs;
+  int pair_s[RS_MAX_PAIRS];
+  int pair_t[RS_MAX_PAIRS];
+  double* G;       // npad x kp, zeroed before
+  uint32_t idesc;
+  unsigned* status;
+};
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 18 warps: an SM sub-partition holds five of them, so at most 96 registers
+// per thread fit.
+__global__ void __launch_bounds__(T8_THREADS, 1)
+    k_tc_resid(const __grid_constant__ ResidMaps maps, const ResidParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RS_STAGES * RS_STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * RS_STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * RS_STAGES + 7);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (RS_STAGES + s); };
+  auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * RS_STAGES + b); };
+  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * RS_STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * RS_STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = p.kblocks / RS_CHUNK_KB;
+  const uint32_t b_bytes = (uint32_t)p.kp * 128;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RS_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(pfull_bar(b), 1);
+      mbar_init(pempty_bar(b), T8_EPI);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(RS_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
+      for (int pr = 0; pr < p.npairs && ok; ++pr) {
+        const CUtensorMap* ma = &maps.a[p.pair_s[pr] - 1];
+        const CUtensorMap* mb = &maps.b[p.pair_t[pr] - 1];
+        for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+          const int s = it % RS_STAGES;
+          const uint32_t r = (uint32_t)(it / RS_STAGES);
+          if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          const uint32_t a_dst = smem_u32(smem + s * RS_STAGE_BYTES);
+          mbar_expect_tx(full_bar(s), RS_A + b_bytes);
+          tma_load_2d(a_dst, ma, kb * 64, t * 128, full_bar(s));
+          tma_load_2d(a_dst + RS_A, mb, kb * 64, 0, full_bar(s));
+        }
+      }
+    if (!ok) {
+      for (int j = (it > RS_STAGES ? it - RS_STAGES : 0); j < it; ++j) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full_bar(j % RS_STAGES), (uint32_t)(j / RS_STAGES) & 1) &&
+               globaltimer() - t0 < WAIT_LIMIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer: one exact K-chunk per TMEM buffer
+    int it = 0, pc = 0;
+    bool ok = true, issued = false;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
+      for (int pr = 0; pr < p.npairs && ok; ++pr)
+        for (int c = 0; c < nchunks && ok; ++c, ++pc) {
+          const int b = pc & 1;
+          const uint32_t ph = (uint32_t)(pc >> 1);
+          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * 128);
+          for (int kb = 0; kb < RS_CHUNK_KB; ++kb, ++it) {
+            const int s = it % RS_STAGES;
+            if (!mbar_wait(full_bar(s), (uint32_t)(it / RS_STAGES) & 1, abort_flag, p.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(smem + s * RS_STAGE_BYTES);
+            const uint64_t adesc = smem_desc(a_addr);
+            const uint64_t bdesc = smem_desc(a_addr + RS_A);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
+            issued = true;
+            mma_commit(empty_bar(s));
+          }
+          if (!ok) break;
+          mma_commit(pfull_bar(b));
+        }
+    if (!ok && issued) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue: exact chunk counts, int32 sums, float64 flushes
+    const int q = warp & 3;
+    const int part = (warp - 2) >> 2;                 // column quarter
+    const int ncol = p.kp / 4;                        // columns of this warp (8, 16 or 32)
+    const int col0 = part * ncol;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    int pc = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+      const int row = t * 128 + q * 32 + lane;
+      double* Grow = p.G + (size_t)row * p.kp + col0;
+      for (int pr = 0; pr < p.npairs; ++pr) {
+        const int m = p.pair_s[pr] + p.pair_t[pr];
+        const float up = __int_as_float((127 + 8 * m) << 23);   // 2^(8m)
+        int acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0;
+        for (int ch = 0; ch < nchunks; ++ch, ++pc) {
+          if (!failed) {
+            const int b = pc & 1;
+            const uint32_t ph = (uint32_t)(pc >> 1);
+            if (!mbar_wait(pfull_bar(b), ph & 1, abort_flag, p.status)) {
+              failed = true;
+            } else {
+              tc_fence_after();
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                if (g * 8 < ncol) {
+                  float v[8];
+                  tmem_ld8(tmem_base + lane_off + (uint32_t)(b * 128 + col0 + g * 8), v);
+#pragma unroll
+                  for (int e = 0; e < 8; ++e) acc[g * 8 + e] += __float2int_rn(v[e] * up);
+                }
+              }
+              tc_fence_before();
+              mbar_arrive(pempty_bar(b));
+            }
+          }
+          if (!failed && ((ch + 1) % RS_FLUSH == 0 || ch + 1 == nchunks)) {
+            const double down = ldexp(1.0, -8 * m);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              if (c < ncol) Grow[c] += (double)acc[c] * down;
+              acc[c] = 0;
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(RS_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Level 0 of a per-tile e4m3 chain from its bf16 copy: one block per 128 x
 // 128 tile; scale = tile max / 448.
 __global__ void __launch_bounds__(256) k_quant_fp8_tiles(const __nv_bfloat16* __restrict__ L16, int np,
@@ -1133,6 +1357,45 @@ int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch) {
   Launch L(ctx, CDL_KC_CHAIN_INIT, 3.0 * np * (double)np);
   k_quant_fp8_tiles<<<nt * nt, 256, 0, ctx->stream>>>(static_cast<const __nv_bfloat16*>(ch->level16(0)), np,
                                                       static_cast<uint8_t*>(ch->level(0)), ch->tscale);
+  return L.done();
+}
+
+// A Z (A from its six slices in the chain, Z / c from `zslices`: six bf16
+// planes kp x npad) into G (npad x kp float64, overwritten).
+int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, double* G) {
+  const int np = (int)ch->npad;
+  if (kp % 32 || kp > 128 || np % 256) return CDL_ERR_INVALID_ARG;
+  ResidMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int s = 0; s < RS_SLICES; ++s) {
+    CDL_TRY(make_map(&maps.a[s], static_cast<const char*>(ch->aslices) + (size_t)s * np * np * 2, np, np, 128));
+    CDL_TRY(make_map(&maps.b[s], static_cast<const char*>(zslices) + (size_t)s * kp * np * 2, kp, np, kp));
+  }
+  ResidParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.num_tiles = np / 128;
+  p.kblocks = np / 64;
+  p.kp = kp;
+  for (int m = 2; m <= RS_SLICES + 1; ++m)
+    for (int sa = 1; sa < m; ++sa) {
+      const int sz = m - sa;
+      if (sa > RS_SLICES || sz > RS_SLICES) continue;
+      p.pair_s[p.npairs] = sa;
+      p.pair_t[p.npairs] = sz;
+      ++p.npairs;
+    }
+  p.G = G;
+  p.idesc = make_idesc(kp);
+  p.status = ctx->dev_status;
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_BYTES));
+    attr = true;
+  }
+  CDL_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)np * kp * sizeof(double), ctx->stream));
+  const int grid = std::min(p.num_tiles, ctx->sm_count);
+  Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * np * kp);
+  k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
 }
 

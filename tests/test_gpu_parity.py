@@ -442,3 +442,27 @@ def test_launch_counter_and_timing(G):
     st, ms, launches, work = cdl.cdl_ctx_timing(G.h, cdl.CDL_KC_DISTANCE)
     assert st == 0 and launches == 3 and ms > 0 and work == 0.5 * 256 * 255 * 8
     cdl.cdl_ctx_set_timing(G.h, False)
+
+
+@pytest.mark.parametrize("n,k", [(1000, 32), (700, 96), (1300, 128)])
+def test_exact_slice_residual(G, n, k):
+    """The tensor chains' full residual (A Z from exact bf16 slices on the
+    tensor cores): after each of a few refinement steps, the reported
+    residual norm equals the float64 residual of the returned Z computed on
+    the host in extended precision, to 1e-15 of ||Y||."""
+    cdl = G.cdl
+    X = iid_pair(n, 32, 1, seed=23).X[0]
+    A, D, vol, _ = G.graph(X)
+    ch = G.chain(A, D, vol, 6, cdl.CDL_BF16)
+    try:
+        Y = G.project(A, k, 9)
+        An, Dn, Yn = _h(A).astype(np.longdouble), _h(D).astype(np.longdouble), _h(Y).astype(np.longdouble)
+        ny = np.sqrt((Yn ** 2).sum())
+        for it in (1, 2, 3):
+            Z, st = G.solve(ch, A, Y, max_iter=it, rel_tol=0.0, flags=cdl.CDL_SOLVE_FULL_RESIDUAL)
+            Zn = _h(Z).astype(np.longdouble)
+            R = Yn - (Dn[:, None] * Zn - An @ Zn)
+            rel = float(np.sqrt((R ** 2).sum()) / ny)
+            assert abs(st.rel_res - rel) <= 1e-15, (it, st.rel_res, rel)
+    finally:
+        cdl.cdl_chain_free(ch)
