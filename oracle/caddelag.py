@@ -131,6 +131,39 @@ def graph_rows(X: np.ndarray, sigma: float, rows: Sequence[int]) -> np.ndarray:
     return A
 
 
+def exp_graph(X: np.ndarray, sigma: Optional[float] = 1.0, d2: Optional[np.ndarray] = None):
+    """Graph of the synthetic experiments (Sec. 4.2.1, "Synthetic Data"):
+    A_ij = exp(-d(i, j) / sigma) with d the Euclidean distance; the paper
+    writes exp(-d(i, j)), i.e. sigma = 1. A_ii = 0, D = A 1, vol = sum D.
+    sigma <= 0 or None selects the median rule. Returns (A, D, vol, sigma)."""
+    if d2 is None:
+        d2 = squared_distances(X)
+    if sigma is None or sigma <= 0:
+        sigma = median_sigma(d2)
+    A = np.exp(-(np.sqrt(d2) / sigma))
+    np.fill_diagonal(A, 0.0)
+    D, vol = degrees(A)
+    return A, D, vol, float(sigma)
+
+
+def degrees(A: np.ndarray):
+    """D = A 1 and vol = sum_i D_i (Sec. 3.2; Eq. 1) of a given adjacency
+    matrix. Returns (D, vol)."""
+    D = A.sum(axis=1)
+    return D, float(D.sum())
+
+
+def add_edge_weights(A: np.ndarray, ij: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """A + W with W_ij = W_ji = w_e for each listed pair e = (i, j), i != j
+    (distinct unordered pairs): the perturbation A_2 = Q + (R + R^T) / 2 of
+    the synthetic experiments (Sec. 4.2.1), w holding (R_ij + R_ji) / 2."""
+    n = A.shape[0]
+    W = np.zeros((n, n))
+    W[ij[:, 0], ij[:, 1]] = w
+    W[ij[:, 1], ij[:, 0]] = w
+    return A + W
+
+
 # --------------------------------------------------------------------------
 # Laplacian and incidence matrix (Sec. 2, Eq. 1-2)
 # --------------------------------------------------------------------------

@@ -463,3 +463,115 @@ def test_edge_scores_sum_to_node_scores():
         row = [(Ef[i, j], -j) for j in range(60) if j != i]
         best = sorted(row, reverse=True)[:3]
         assert list(part[t]) == [-b[1] for b in best]
+
+
+# ------------------------------------------------------------------ synthetic mixture data (Sec. 4.2.1)
+
+def test_exp_graph_closed_form_triangle():
+    """A 3-4-5 right triangle: the synthetic-data kernel exp(-d) by hand."""
+    X = np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 4.0]])
+    A, D, vol, s = O.exp_graph(X, 1.0)
+    e3, e4, e5 = math.exp(-3.0), math.exp(-4.0), math.exp(-5.0)
+    np.testing.assert_allclose(A, [[0, e3, e4], [e3, 0, e5], [e4, e5, 0]], rtol=1e-15, atol=0)
+    np.testing.assert_allclose(D, [e3 + e4, e3 + e5, e4 + e5], rtol=1e-15)
+    assert math.isclose(vol, 2 * (e3 + e4 + e5), rel_tol=1e-15)
+    assert s == 1.0
+    # the median rule picks the lower median of {3, 4, 5}
+    assert O.exp_graph(X, 0.0)[3] == 4.0
+    # width 2 on X is width 1 on X / 2 (halving is exact)
+    assert np.array_equal(O.exp_graph(X, 2.0)[0], O.exp_graph(X / 2, 1.0)[0])
+
+
+def test_degrees_and_edge_weights_brute_force():
+    A = _random_graph(7, 2)
+    np.fill_diagonal(A, 0.0)
+    ij = np.array([[0, 3], [2, 6], [1, 5], [4, 5]], dtype=np.int64)
+    w = np.array([0.5, 0.25, 0.125, 0.75])
+    B = O.add_edge_weights(A, ij, w)
+    for a in range(7):
+        for b in range(7):
+            add = sum(w[e] for e in range(4) if {a, b} == {int(ij[e, 0]), int(ij[e, 1])})
+            assert B[a, b] == A[a, b] + add
+    D, vol = O.degrees(B)
+    for a in range(7):
+        assert math.isclose(D[a], math.fsum(B[a]), rel_tol=1e-15)
+    assert math.isclose(vol, math.fsum(B.reshape(-1)), rel_tol=1e-14)
+
+
+def test_gmm_workload_matches_its_model():
+    from workloads import gmm_pair
+    n, p = 300, 0.05
+    g = gmm_pair(n, p=p, seed=4)
+    m = n * (n - 1) // 2
+    # an unordered pair carries weight unless both of its two draws were zero
+    q = 1 - (1 - p) ** 2
+    assert abs(len(g.w) - q * m) < 5 * math.sqrt(m * q * (1 - q))
+    assert np.all(g.ij[:, 0] < g.ij[:, 1])
+    flat = g.ij[:, 0] * n + g.ij[:, 1]
+    assert np.all(np.diff(flat) > 0)
+    assert np.all(g.w > 0) and np.all(g.w <= 1.0)
+    assert np.array_equal(g.w * 2 ** 17, np.rint(g.w * 2 ** 17))
+    assert np.array_equal(g.truth, g.labels[g.ij[:, 0]] != g.labels[g.ij[:, 1]])
+    # mixture components sit at (+-3, +-3); the noise is small
+    for c, mu in enumerate([(-3, -3), (-3, 3), (3, -3), (3, 3)]):
+        pts = g.X[0][g.labels == c]
+        assert np.all(np.abs(pts.mean(0) - mu) < 0.5)
+    assert np.abs(g.X[1] - g.X[0]).max() < 0.05 * 6
+
+
+def _auc(score, pos):
+    """Probability that a random positive outranks a random negative (ties 1/2)."""
+    s_pos, s_neg = score[pos], score[~pos]
+    order = np.sort(s_neg)
+    below = np.searchsorted(order, s_pos, side="left")
+    equal = np.searchsorted(order, s_pos, side="right") - below
+    return float((below + 0.5 * equal).sum() / (s_pos.size * s_neg.size))
+
+
+def test_gmm_detector_separates_cross_cluster_edges():
+    """Sec. 4.2.1's synthetic design: added edges that join two clusters change
+    the commute times, added edges inside a cluster barely do. Among the added
+    edges, Delta E ranks the cross-cluster ones first, while |Delta A| alone
+    (the added weight, independent of the clusters) does not. This holds with
+    the exact commute times of Eq. 1 (pseudoinverse, independent of the
+    oracle's solver) and with the oracle's own k = 128 embedding."""
+    from workloads import gmm_pair
+    n, k = 300, 128
+    g = gmm_pair(n, seed=9)
+    A1, _, vol1, _ = O.exp_graph(g.X[0], 1.0)
+    Q, _, _, _ = O.exp_graph(g.X[1], 1.0)
+    A2 = O.add_edge_weights(Q, g.ij, g.w)
+    _, vol2 = O.degrees(A2)
+    i, j = g.ij[:, 0], g.ij[:, 1]
+    dA = np.abs(A1 - A2)[i, j]
+    C1x, C2x = O.commute_times_pinv(A1), O.commute_times_pinv(A2)
+    e_exact = dA * np.abs(C2x - C1x)[i, j]
+    Z1 = O.exact_embedding(A1, O.project(A1, 3, k))
+    Z2 = O.exact_embedding(A2, O.project(A2, 3, k))
+    E = O.upper_edge_scores(A1, A2, Z1, Z2, vol1, vol2)
+    e_orc = E[i, j]
+    auc_dA, auc_x, auc_o = _auc(dA, g.truth), _auc(e_exact, g.truth), _auc(e_orc, g.truth)
+    assert abs(auc_dA - 0.5) < 0.06
+    assert auc_x > auc_dA + 0.15
+    assert auc_o > auc_dA + 0.08
+
+
+def test_gmm_commute_time_error_matches_jl_spread():
+    """Alg. 3's projected commute times against Eq. 1's exact ones on a mixture
+    graph: c_est / c = ||Q v||^2 / ||v||^2 for the edge-space vector v of the
+    pair, which for +-1/sqrt(k) signs and v spread over many edges is close to
+    normal with mean 1 and standard deviation sqrt(2 / k), so the median
+    absolute relative error is about 0.674 sqrt(2 / k)."""
+    from workloads import gmm_pair
+    n, k = 240, 64
+    g = gmm_pair(n, seed=2)
+    A, _, vol, _ = O.exp_graph(g.X[0], 1.0)
+    C = O.commute_times_pinv(A)
+    Z = O.exact_embedding(A, O.project(A, 8, k))
+    Ce = O.commute_times(Z, vol)
+    iu, ju = np.triu_indices(n, 1)
+    rel = Ce[iu, ju] / C[iu, ju] - 1.0
+    assert abs(np.mean(rel)) < 0.05
+    med = np.median(np.abs(rel))
+    expect = 0.6745 * math.sqrt(2.0 / k)
+    assert 0.75 * expect < med < 1.25 * expect

@@ -23,6 +23,12 @@ synthetic graphs; none of the paper's datasets is used):
   (in field standard deviations) in one transition.
 * ``ragged_pairs``: G independent pairs with n log-uniform in [n_lo, n_hi],
   N(0,1) series, 1-5 perturbed nodes per pair.
+* ``gmm_pair``: the paper's synthetic data (Sec. 4.2.1, "Synthetic Data"):
+  n points of a 2-D mixture of 4 Gaussians, the same points with small
+  Gaussian noise, and a sparse random matrix R whose symmetrised half
+  (R + R^T) / 2 is added to the second graph; ground truth marks the added
+  edges that join different clusters. The kernel matrices themselves are the
+  method's graph build and are not formed here.
 """
 from __future__ import annotations
 
@@ -128,6 +134,94 @@ def ragged_pairs(G: int = 64, n_lo: int = 256, n_hi: int = 4096, T: int = 64,
         out.append(GraphPairs([np.ascontiguousarray(X1), np.ascontiguousarray(X2)], [idx],
                               dict(kind="ragged_pair", n=n, T=T, seed=seed, index=g)))
     return out
+
+
+@dataclass
+class GMMPair:
+    """Points of the synthetic mixture pair (Sec. 4.2.1, "Synthetic Data").
+
+    ``X``: the two n x 2 point sets (float64 on the 2**-16 grid); graph t is
+    the kernel graph of X[t] and graph 2 additionally gets the edge weights
+    ``w`` on the node pairs ``ij``. ``ij``: (m, 2) int64, i < j, ascending
+    in (i, j); ``w``: (m,) float64, w = (R_ij + R_ji) / 2 > 0 with R_ij and
+    R_ji independent draws of the paper's R (zero with probability 1 - p,
+    else uniform on (0, 1], here on the 2**-16 grid, so w is exact).
+    ``labels``: mixture component of each point. ``truth``: (m,) bool, the
+    added edges that join different components (the anomalous edges); the
+    anomalous nodes are their endpoints."""
+    X: List[np.ndarray]
+    labels: np.ndarray
+    ij: np.ndarray
+    w: np.ndarray
+    truth: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    def anomalous_nodes(self) -> np.ndarray:
+        t = self.ij[self.truth]
+        return np.unique(t.reshape(-1))
+
+
+def _upper_pair(flat: np.ndarray, n: int):
+    """Row-major position in the strict upper triangle -> (i, j)."""
+    i_all = np.arange(n - 1, dtype=np.int64)
+    start = i_all * (2 * n - i_all - 1) // 2          # first position of row i
+    i = np.searchsorted(start, flat, side="right") - 1
+    j = flat - start[i] + i + 1
+    return i, j
+
+
+def _bernoulli_positions(rng: np.random.Generator, M: int, p: float) -> np.ndarray:
+    """Sorted positions in [0, M) of independent Bernoulli(p) successes
+    (geometric gaps between successes)."""
+    out = []
+    pos = -1
+    while True:
+        cnt = int(max(1024, 1.05 * p * max(M - pos, 0) + 64))
+        gaps = rng.geometric(p, size=cnt)
+        cs = pos + np.cumsum(gaps)
+        keep = cs[cs < M]
+        out.append(keep)
+        if keep.size < cs.size:
+            break
+        pos = int(cs[-1])
+    return np.concatenate(out).astype(np.int64)
+
+
+def gmm_pair(n: int = 2000, p: float = 0.05, noise: float = 0.05, sep: float = 3.0,
+             seed: int = 11) -> GMMPair:
+    """Mixture of 4 unit-covariance Gaussians in the plane with means
+    (+-sep, +-sep), equal weights; graph 2's points are graph 1's plus
+    N(0, noise^2) per coordinate; R_ij ~ p-Bernoulli times U(0, 1] for every
+    ordered pair i != j (the diagonal is left out: the graphs have no self
+    edges)."""
+    rng = np.random.default_rng(seed)
+    labels = rng.integers(0, 4, size=n).astype(np.int64)
+    means = np.array([[-sep, -sep], [-sep, sep], [sep, -sep], [sep, sep]])
+    X1 = to_grid(means[labels] + rng.standard_normal((n, 2)))
+    X2 = to_grid(X1 + noise * rng.standard_normal((n, 2)))
+    M = n * (n - 1) // 2
+    pos, val = [], []
+    for _ in range(2):                                  # R_ij (i < j), then R_ji
+        q = _bernoulli_positions(rng, M, p)
+        u = rng.integers(1, (1 << 16) + 1, size=q.size).astype(np.float64) * GRID
+        pos.append(q)
+        val.append(u)
+    (q1, q2), (u1, u2) = pos, val
+    # union of the two sorted position lists, values added where both drew
+    at = np.searchsorted(q1, q2)
+    both = at < q1.size
+    both[both] = q1[at[both]] == q2[both]
+    u1 = u1.copy()
+    u1[at[both]] += u2[both]
+    allpos = np.concatenate([q1, q2[~both]])
+    order = np.argsort(allpos, kind="stable")           # merge of two sorted runs
+    uniq = allpos[order]
+    w = np.concatenate([u1, u2[~both]])[order] * 0.5
+    i, j = _upper_pair(uniq, n)
+    ij = np.ascontiguousarray(np.stack([i, j], axis=1).astype(np.int64))
+    truth = labels[i] != labels[j]
+    return GMMPair([np.ascontiguousarray(X1), np.ascontiguousarray(X2)], labels, ij, w, truth,
+                   dict(kind="gmm_pair", n=n, p=p, noise=noise, sep=sep, seed=seed))
 
 
 # Named workloads with the method parameters they are run with.
