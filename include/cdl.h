@@ -164,6 +164,48 @@ int cdl_build_graph(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, double 
 int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, double* A,
                            double* D, double* vol, double* sigma_out, void* cuda_stream);
 
+/* Graph of n points under a chosen kernel: kernel = CDL_KERNEL_GAUSSIAN is
+ * cdl_build_graph; CDL_KERNEL_EXP is the kernel of the synthetic
+ * experiments (Sec. 4.2.1, "Synthetic Data", written there as exp(-d(i,j))
+ * with d the Euclidean distance, i.e. sigma = 1):
+ *   A_ij = exp(-||x_i - x_j|| / sigma) for i != j, A_ii = 0,
+ * computed as exp(-(sqrt(d2) * (1 / sigma))) with the correctly rounded
+ * float64 square root. sigma <= 0 selects the lower median distance, as for
+ * the Gaussian kernel. Other arguments, limits and errors as for
+ * cdl_build_graph; an unknown kernel returns CDL_ERR_INVALID_ARG. */
+enum { CDL_KERNEL_GAUSSIAN = 0, CDL_KERNEL_EXP = 1 };
+int cdl_build_graph_kernel(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, int32_t kernel,
+                           double sigma, cdl_dtype a_dtype, void* A, double* D, double* vol,
+                           double* sigma_out);
+
+/* Degrees of a caller's graph (Sec. 3.2: D = A 1; Eq. 1: vol = sum_i D_i),
+ * for adjacency matrices not made by cdl_build_graph (the paper's election
+ * graphs use their own similarity; the synthetic experiments add random
+ * edges). A: device n x n float64, symmetric, non-negative, zero diagonal
+ * (not checked). D: device n float64 output; vol: device one float64.
+ * Row sums are compensated float64 sums (a few units in the last place of
+ * the exact sum). Requires 1 <= n <= 2^20; a_dtype must be CDL_F64
+ * (else CDL_ERR_UNSUPPORTED). Asynchronous. */
+int cdl_graph_degrees(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, int64_t n, double* D,
+                      double* vol);
+
+/* Symmetric edge weights added to a graph: A_ij += w_e and A_ji += w_e for
+ * every listed pair e = (i, j). This forms the second graph of the synthetic
+ * experiments, A_2 = Q + (R + R^T) / 2 (Sec. 4.2.1), with w_e = (R_ij +
+ * R_ji) / 2 over the pairs where it is nonzero. A: device n x n float64,
+ * updated in place (degrees are not updated: call cdl_graph_degrees after).
+ * ij: device m x 2 int64, row-major (i, j) pairs, the layout of
+ * cdl_cad_edges' edge list; w: device m float64. Pairs must be distinct as
+ * unordered pairs for exact, order-free results (each entry then receives
+ * one float64 addition); repeated pairs are added in an unspecified order.
+ * Entries with an index outside [0, n), i == j, or w negative, infinite or
+ * NaN are skipped; their count goes to *n_bad (host, may be NULL) and the
+ * call returns CDL_ERR_INVALID_ARG after applying the valid entries.
+ * Requires 2 <= n <= 2^20, m >= 0 (ij and w may be NULL when m == 0).
+ * Synchronises the context's stream. */
+int cdl_graph_add_edges(cdl_ctx* ctx, void* A, cdl_dtype a_dtype, int64_t n, int64_t m,
+                        const int64_t* ij, const double* w, int64_t* n_bad);
+
 /* ---------------------------------------------------------------- chain */
 
 /* Inverse chain of Alg. 2 (ChainProduct) for M = L = D - A.
@@ -173,7 +215,8 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  * which equal S^{2^i} - u u^T (u is the eigenvector of S for eigenvalue 1)
  * and act like S^{2^i} on every vector D^{-1/2} b with b orthogonal to the
  * ones vector, the only vectors the solve applies them to.
- * A (device, n x n, a_dtype = CDL_F64), D (device, n), vol (device, 1).
+ * A (device, n x n, a_dtype = CDL_F64; weights finite and non-negative),
+ * D (device, n), vol (device, 1).
  * chain_dtype: CDL_F64, CDL_F32 (CUDA-core GEMM), CDL_BF16 (tcgen05
  *   tensor-core GEMM, float32 accumulation, bfloat16 levels) or CDL_FP8E4M3
  *   (tcgen05 kind::f8f6f4 GEMM, float32 accumulation, e4m3 levels with one
@@ -189,9 +232,12 @@ int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, 
  * inout: if *inout is NULL a chain is allocated (cdl_chain_free releases it);
  *   if it points to a chain created with the same (n, d, chain_dtype) its
  *   storage is reused; any other chain returns CDL_ERR_INVALID_ARG.
- * Levels occupy d * npad^2 elements, npad = n rounded up to 256; bf16
- * chains also keep A as two bf16 matrices (A_hi + A_lo, 4 npad^2 bytes),
- * the operand of the solve's tensor-core residual update.
+ * Levels occupy d * npad^2 elements, npad = n rounded up to 256; tensor
+ * chains (bf16, e4m3) also keep A as two bf16 matrices (A_hi + A_lo,
+ * 4 npad^2 bytes), the operand of the solve's tensor-core residual update,
+ * and A / 2^q as six exact bf16 slices (12 npad^2 bytes; 2^q, q >= 0, the
+ * least power of two not below max A, found by one pass over A), the operand
+ * of its full residual.
  * CDL_CHAIN_HOST_LEVELS (bf16 chains): the levels live in pinned host memory
  * (d * npad^2 * 2 bytes, allocated by the library) and two device slots of
  * npad^2 bf16 hold the ones in use: each squaring writes level i + 1 to a
@@ -242,8 +288,10 @@ int cdl_chain_level_scale(const cdl_chain* chain, int32_t i, double* scale);
  * The exact Y has zero column sums (B^T 1 = 0); the computed columns have
  * their means subtracted, which removes the rounding residue of the row sums
  * (a component in the null space of L that no solve could match).
- * A: device n x n (a_dtype = CDL_F64). Y: device n x k float64 output.
- * Requires 1 <= k <= 1024. */
+ * A: device n x n (a_dtype = CDL_F64), weights finite, non-negative and
+ * below 2^200 (any graph, not only kernel graphs: the terms are split on
+ * grids scaled to sqrt(max A), found by one pass over A). Y: device n x k
+ * float64 output. Requires 1 <= k <= 1024. */
 int cdl_project(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, int64_t n, int32_t k,
                 uint64_t seed, double* Y);
 

@@ -28,6 +28,7 @@ CDL_SOLVE_FULL_RESIDUAL = 1
 CDL_CHAIN_HOST_LEVELS = 1
 CDL_CHAIN_TRUNCATE = 2
 CDL_SCORE_CHANGED_ONLY = 1
+CDL_KERNEL_GAUSSIAN, CDL_KERNEL_EXP = 0, 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1
 CDL_DEBUG_BATCH_VARIANT = 2
 
@@ -94,6 +95,9 @@ _SIGS = {
     "cdl_ctx_set_debug": [_P, ctypes.c_int],
     "cdl_build_graph": [_P, _P, _I64, _I32, _D, ctypes.c_int, _P, _P, _P, _P],
     "cdl_build_graph_static": [_P, _I64, _I32, _D, _P, _P, _P, _P, _P],
+    "cdl_build_graph_kernel": [_P, _P, _I64, _I32, _I32, _D, ctypes.c_int, _P, _P, _P, _P],
+    "cdl_graph_degrees": [_P, _P, ctypes.c_int, _I64, _P, _P],
+    "cdl_graph_add_edges": [_P, _P, ctypes.c_int, _I64, _I64, _P, _P, ctypes.POINTER(_I64)],
     "cdl_chain_build": [_P, _P, ctypes.c_int, _P, _P, _I64, _I32, ctypes.c_int, _I32, ctypes.POINTER(_P)],
     "cdl_chain_free": [_P],
     "cdl_chain_depth": [_P, ctypes.POINTER(_I32)],
@@ -190,6 +194,22 @@ def cdl_ctx_launch_count(ctx):
 def cdl_build_graph(ctx, X, n, T, sigma, a_dtype, A, D, vol, sigma_out) -> int:
     return _lib.cdl_build_graph(ctx, _ptr(X), n, T, sigma, a_dtype, _ptr(A), _ptr(D), _ptr(vol),
                                 _ptr(sigma_out))
+
+
+def cdl_build_graph_kernel(ctx, X, n, T, kernel, sigma, a_dtype, A, D, vol, sigma_out) -> int:
+    return _lib.cdl_build_graph_kernel(ctx, _ptr(X), n, T, kernel, sigma, a_dtype, _ptr(A), _ptr(D),
+                                       _ptr(vol), _ptr(sigma_out))
+
+
+def cdl_graph_degrees(ctx, A, a_dtype, n, D, vol) -> int:
+    return _lib.cdl_graph_degrees(ctx, _ptr(A), a_dtype, n, _ptr(D), _ptr(vol))
+
+
+def cdl_graph_add_edges(ctx, A, a_dtype, n, m, ij, w):
+    """Returns (status, number of skipped invalid entries)."""
+    bad = _I64(0)
+    st = _lib.cdl_graph_add_edges(ctx, _ptr(A), a_dtype, n, m, _ptr(ij), _ptr(w), ctypes.byref(bad))
+    return st, bad.value
 
 
 def cdl_build_graph_static(X, n, T, sigma, A, D, vol, sigma_out, stream=None) -> int:

@@ -267,7 +267,47 @@ int cdl_build_graph(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, double 
   CDL_TRY(dev_ptr(ctx, D));
   CDL_TRY(dev_ptr(ctx, vol));
   CDL_TRY(dev_ptr(ctx, sigma_out));
-  return graph_build(ctx, X, n, T, sigma, static_cast<double*>(A), D, vol, sigma_out);
+  return graph_build(ctx, X, n, T, sigma, static_cast<double*>(A), D, vol, sigma_out, CDL_KERNEL_GAUSSIAN);
+}
+
+int cdl_build_graph_kernel(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, int32_t kernel, double sigma,
+                           cdl_dtype a_dtype, void* A, double* D, double* vol, double* sigma_out) {
+  if (!ctx) return CDL_ERR_INVALID_ARG;
+  if (kernel != CDL_KERNEL_GAUSSIAN && kernel != CDL_KERNEL_EXP) return CDL_ERR_INVALID_ARG;
+  if (n < 2 || n > (1 << 20) || T < 1 || T > 4096) return CDL_ERR_INVALID_ARG;
+  if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
+  CDL_TRY(set_device(ctx));
+  CDL_TRY(dev_ptr(ctx, X));
+  CDL_TRY(dev_ptr(ctx, A));
+  CDL_TRY(dev_ptr(ctx, D));
+  CDL_TRY(dev_ptr(ctx, vol));
+  CDL_TRY(dev_ptr(ctx, sigma_out));
+  return graph_build(ctx, X, n, T, sigma, static_cast<double*>(A), D, vol, sigma_out, kernel);
+}
+
+int cdl_graph_degrees(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, int64_t n, double* D, double* vol) {
+  if (!ctx) return CDL_ERR_INVALID_ARG;
+  if (n < 1 || n > (1 << 20)) return CDL_ERR_INVALID_ARG;
+  if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
+  CDL_TRY(set_device(ctx));
+  CDL_TRY(dev_ptr(ctx, A));
+  CDL_TRY(dev_ptr(ctx, D));
+  CDL_TRY(dev_ptr(ctx, vol));
+  return graph_degrees(ctx, static_cast<const double*>(A), n, D, vol);
+}
+
+int cdl_graph_add_edges(cdl_ctx* ctx, void* A, cdl_dtype a_dtype, int64_t n, int64_t m, const int64_t* ij,
+                        const double* w, int64_t* n_bad) {
+  if (!ctx) return CDL_ERR_INVALID_ARG;
+  if (n < 2 || n > (1 << 20) || m < 0) return CDL_ERR_INVALID_ARG;
+  if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
+  CDL_TRY(set_device(ctx));
+  CDL_TRY(dev_ptr(ctx, A));
+  if (m > 0) {
+    CDL_TRY(dev_ptr(ctx, ij));
+    CDL_TRY(dev_ptr(ctx, w));
+  }
+  return graph_add_edges(ctx, static_cast<double*>(A), n, m, ij, w, n_bad);
 }
 
 int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, double* A,
@@ -287,6 +327,7 @@ int cdl_chain_free(cdl_chain* ch) {
   cudaFree(ch->amax);
   cudaFree(ch->ahl);
   cudaFree(ch->aslices);
+  cudaFree(ch->a_scale);
   cudaFree(ch->tscale);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
@@ -387,7 +428,8 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
       return CDL_ERR_OOM;
     }
     if ((ahl_bytes && cudaMalloc(&ch->ahl, ahl_bytes) != cudaSuccess) ||
-        (slice_bytes && cudaMalloc(&ch->aslices, slice_bytes) != cudaSuccess) ||
+        (slice_bytes && (cudaMalloc(&ch->aslices, slice_bytes) != cudaSuccess ||
+                         cudaMalloc(&ch->a_scale, 2 * sizeof(double)) != cudaSuccess)) ||
         (aop_bytes && cudaMalloc(&ch->aop, aop_bytes) != cudaSuccess) ||
         (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
                        cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||

@@ -177,23 +177,43 @@ __global__ void __launch_bounds__(256) k_split_a(const double* __restrict__ A, s
   }
 }
 
-// A as six bf16 planes on the grids 2^-8s: the signed base-256 digits of A
-// rounded to 2^-48 (A in [0, 1]); zero padded to npad x npad. The rounding
-// uses the float64 bit pattern (integer operations only): A = m 2^(e - 52),
-// N = m / 2^(4 - e) rounded to nearest (ties up).
-__device__ __forceinline__ long long grid48(double a) {
+// max |x_i| as float64 bits (for x >= 0 the bit patterns order like the values).
+__global__ void __launch_bounds__(256) k_abs_max_bits(const double* __restrict__ x, size_t count,
+                                                       unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFull;
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// A / 2^s as six bf16 planes on the grids 2^-8t: the signed base-256 digits of
+// A / 2^s rounded to 2^-48, with 2^s the least power of two (s >= 0) not
+// below max A, so that A / 2^s lies in [0, 1] (the kernel graphs have s = 0); zero
+// padded to npad x npad. The rounding uses the float64 bit pattern (integer
+// operations only): A = m 2^(e - 52), N = m / 2^(4 - e + s) rounded to
+// nearest (ties up).
+__device__ __forceinline__ long long grid48(double a, int s) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const int e = (int)((b >> 52) & 0x7FF);
   if (e == 0) return 0;                                   // zero (no subnormal kernel values)
   const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = 1023 + 4 - e;                             // a = m 2^(e - 1075); a 2^48 = m 2^(e - 1027)
+  const int sh = 1023 + 4 - e + s;                         // a = m 2^(e - 1075); a 2^(48 - s) = m 2^(e - 1027 - s)
   if (sh >= 60) return 0;
   if (sh <= 0) return (long long)(m << -sh);
   return (long long)((m + (1ull << (sh - 1))) >> sh);
 }
 
 __global__ void __launch_bounds__(256) k_slice_a(const double* __restrict__ A, int n, int np,
-                                                  __nv_bfloat16* __restrict__ S) {
+                                                  __nv_bfloat16* __restrict__ S, double* __restrict__ a_scale) {
+  const int sexp = pow2_exp_above((unsigned long long)__double_as_longlong(a_scale[1]));
+  if (blockIdx.x == 0 && threadIdx.x == 0) a_scale[0] = __longlong_as_double((long long)(1023 + sexp) << 52);
   const size_t plane = (size_t)np * np;
   const size_t groups = plane / 8;                        // np is a multiple of 128
   for (size_t gidx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; gidx < groups;
@@ -202,7 +222,7 @@ __global__ void __launch_bounds__(256) k_slice_a(const double* __restrict__ A, i
     const int i = (int)(idx0 / np), j0 = (int)(idx0 % np);
     long long N[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) N[e] = (i < n && j0 + e < n) ? grid48(A[(size_t)i * n + j0 + e]) : 0;
+    for (int e = 0; e < 8; ++e) N[e] = (i < n && j0 + e < n) ? grid48(A[(size_t)i * n + j0 + e], sexp) : 0;
 #pragma unroll
     for (int s = 1; s <= 6; ++s) {
       const int sh = 48 - 8 * s;
@@ -371,6 +391,14 @@ int square_impl(cdl_ctx* ctx, cdl_chain* ch, int level) {
 
 }  // namespace
 
+int abs_max_bits(cdl_ctx* ctx, const double* x, size_t count, unsigned long long* out) {
+  CDL_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), ctx->stream));
+  Launch L(ctx, CDL_KC_MISC, 8.0 * (double)count);
+  const size_t blocks = std::min<size_t>((count + 255) / 256, (size_t)ctx->sm_count * 8);
+  k_abs_max_bits<<<(unsigned)std::max<size_t>(blocks, 1), 256, 0, ctx->stream>>>(x, count, out);
+  return L.done();
+}
+
 int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
   const int n = (int)ch->n, np = (int)ch->npad;
   if (ch->ahl) {
@@ -380,8 +408,10 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
     CDL_TRY(L.done());
   }
   if (ch->aslices) {
+    CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, reinterpret_cast<unsigned long long*>(ch->a_scale + 1)));
     Launch L(ctx, CDL_KC_CHAIN_INIT, 8.0 * n * (double)n + 12.0 * np * (double)np);
-    k_slice_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, n, np, static_cast<__nv_bfloat16*>(ch->aslices));
+    k_slice_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, n, np, static_cast<__nv_bfloat16*>(ch->aslices),
+                                                          ch->a_scale);
     CDL_TRY(L.done());
   }
   void* wsu;

@@ -78,6 +78,15 @@ __device__ __forceinline__ ff split_nonneg(double x) {
   return {__uint_as_float(hi_bits), lo};
 }
 
+// The least e >= 0 with x <= 2^e, for the float64 bit pattern of x >= 0
+// (zero gives 0).
+__device__ __forceinline__ int pow2_exp_above(unsigned long long bits) {
+  if (bits == 0) return 0;
+  const int e = (int)((bits >> 52) & 0x7FF) - 1023;
+  const int up = (bits & 0xFFFFFFFFFFFFFull) != 0 ? e + 1 : e;
+  return up > 0 ? up : 0;
+}
+
 __device__ __forceinline__ float d2f_trunc(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;

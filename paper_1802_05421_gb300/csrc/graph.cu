@@ -253,11 +253,17 @@ __global__ void k_select_step(SelectState* st, unsigned long long* hist, int shi
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
-// A_ij = exp(-d2_ij / (2 sigma^2)), A_ii = 0, D_i = row sum. One block per row.
+// A_ij = exp(-d2_ij / (2 sigma^2)) (KERN = KERNEL_GAUSSIAN) or
+// A_ij = exp(-sqrt(d2_ij) / sigma) (KERN = KERNEL_EXP, the synthetic-data
+// kernel of Sec. 4.2.1), A_ii = 0, D_i = row sum. One block per row.
 // The exponential is ff_exp_neg_scaled (float64 argument reduction, float-float
-// series, about 1e-14 relative); the argument is d2 * (1 / (2 sigma^2)) (one
-// float64 product); the row sum is accumulated in float-float (terms below
-// 2^-100 are dropped from the sum, not from A).
+// series, about 1e-14 relative); the argument is d2 * (1 / (2 sigma^2)), or the
+// correctly rounded sqrt(d2) times 1 / sigma (one float64 product); the row
+// sum is accumulated in float-float (terms below 2^-100 are dropped from the
+// sum, not from A).
+enum { KERNEL_GAUSSIAN = 0, KERNEL_EXP = 1 };
+
+template <int KERN = KERNEL_GAUSSIAN>
 __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double rcp, double* __restrict__ D,
                                            int i) {
   __shared__ double red[8];
@@ -265,7 +271,7 @@ __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double
     double* row = A + (size_t)i * n;
     ff acc = {0.f, 0.f};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const double t = row[j] * rcp;
+      const double t = (KERN == KERNEL_EXP ? __dsqrt_rn(row[j]) : row[j]) * rcp;
       double a = 0.0;
       if (j != i) {
         if (t < 700.0) {
@@ -298,12 +304,13 @@ __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double
   }
 }
 
+template <int KERN = KERNEL_GAUSSIAN>
 __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int n,
                                                       const double* __restrict__ sigma,
                                                       double* __restrict__ D) {
   const double s = *sigma;
-  const double rcp = 1.0 / (2.0 * (s * s));
-  for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row(A, n, rcp, D, i);
+  const double rcp = KERN == KERNEL_EXP ? 1.0 / s : 1.0 / (2.0 * (s * s));
+  for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row<KERN>(A, n, rcp, D, i);
 }
 
 // vol = sum_i D_i (single block, fixed order per thread then tree).
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(256) k_g_kernel_rows(const uint32_t* __restric
   const uint32_t t = tiles[blockIdx.x];
   const GGraph& G = gs[t & 0xFFFu];
   const double s = *G.sigma;
-  kernel_row(G.A, G.n, 1.0 / (2.0 * (s * s)), G.D, (int)(t >> 12));
+  kernel_row<KERNEL_GAUSSIAN>(G.A, G.n, 1.0 / (2.0 * (s * s)), G.D, (int)(t >> 12));
 }
 
 __global__ void k_g_sum(const GGraph* __restrict__ gs) {
@@ -474,7 +481,7 @@ int graph_build_grouped(cdl_ctx* ctx, const GraphBatch& B) {
 }
 
 int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma, double* A,
-                double* D, double* vol, double* sigma_out) {
+                double* D, double* vol, double* sigma_out, int kernel) {
   const int n = (int)n64;
   cudaStream_t s = ctx->stream;
   void *wsXi, *wsSt, *wsHist;
@@ -535,7 +542,11 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
   }
   {
     Launch L(ctx, CDL_KC_KERNEL, 16.0 * (double)n * n);
-    k_kernel_rows<<<std::min(n, ctx->sm_count * 8), 256, 0, s>>>(A, n, sigma_out, D);
+    const int blocks = std::min(n, ctx->sm_count * 8);
+    if (kernel == KERNEL_EXP)
+      k_kernel_rows<KERNEL_EXP><<<blocks, 256, 0, s>>>(A, n, sigma_out, D);
+    else
+      k_kernel_rows<KERNEL_GAUSSIAN><<<blocks, 256, 0, s>>>(A, n, sigma_out, D);
     CDL_TRY(L.done());
   }
   {
@@ -544,6 +555,105 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
     CDL_TRY(L.done());
   }
   return CDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Given graphs: degrees of a caller's adjacency matrix and symmetric edge
+// weights added to it (the second graph of the synthetic experiments,
+// A_2 = Q + (R + R^T) / 2, Sec. 4.2.1).
+
+// D_i = sum_j A_ij, one block (256 threads) per row: each thread adds its
+// strided terms in float64 with a running compensation (Neumaier's TwoSum
+// form), the (sum, compensation) pairs are combined the same way across the
+// warp and the block; D_i = sum + compensation (within a few units in the
+// last place of the exact row sum).
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double a) {
+  const double t = s + a;
+  c += fabs(s) >= fabs(a) ? (s - t) + a : (a - t) + s;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) k_degrees(const double* __restrict__ A, int n, double* __restrict__ D) {
+  __shared__ double red_s[8], red_c[8];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* row = A + (size_t)i * n;
+    double s = 0.0, c = 0.0;
+    for (int j = threadIdx.x; j < n; j += 256) neumaier_add(s, c, row[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      neumaier_add(s, c, s2);
+      c += c2;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red_s[threadIdx.x >> 5] = s;
+      red_c[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = red_s[0], tc = red_c[0];
+      for (int w = 1; w < 8; ++w) {
+        neumaier_add(t, tc, red_s[w]);
+        tc += red_c[w];
+      }
+      D[i] = t + tc;
+    }
+    __syncthreads();
+  }
+}
+
+// A_ij += w_e and A_ji += w_e for each pair e = (i, j) of ij (m x 2, row-major).
+// Invalid entries (an index outside [0, n), i == j, w negative, infinite or
+// NaN) are skipped and counted in *bad. Each listed unordered pair touches its
+// two entries once, so distinct pairs give exact, order-free results.
+__global__ void k_add_edges(double* __restrict__ A, int n, long long m, const long long* __restrict__ ij,
+                            const double* __restrict__ w, unsigned long long* __restrict__ bad) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const long long i = ij[2 * e], j = ij[2 * e + 1];
+    const double v = w[e];
+    if (i < 0 || i >= n || j < 0 || j >= n || i == j || !(v >= 0.0) || isinf(v)) {
+      atomicAdd(bad, 1ull);
+      continue;
+    }
+    atomicAdd(A + (size_t)i * n + j, v);
+    atomicAdd(A + (size_t)j * n + i, v);
+  }
+}
+
+int graph_degrees(cdl_ctx* ctx, const double* A, int64_t n64, double* D, double* vol) {
+  const int n = (int)n64;
+  cudaStream_t s = ctx->stream;
+  {
+    Launch L(ctx, CDL_KC_KERNEL, 8.0 * (double)n * n);
+    k_degrees<<<std::min(n, ctx->sm_count * 8), 256, 0, s>>>(A, n, D);
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_sum<<<1, 1024, 0, s>>>(D, n, vol);
+  return L.done();
+}
+
+int graph_add_edges(cdl_ctx* ctx, double* A, int64_t n, int64_t m, const int64_t* ij, const double* w,
+                    int64_t* n_bad) {
+  cudaStream_t s = ctx->stream;
+  void* wsBad;
+  CDL_TRY(ws_get(ctx, "graph.bad", sizeof(unsigned long long), &wsBad));
+  unsigned long long* bad = static_cast<unsigned long long*>(wsBad);
+  CDL_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+  if (m > 0) {
+    const long long blocks = std::min<long long>((m + 255) / 256, (long long)ctx->sm_count * 16);
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_add_edges<<<(unsigned)blocks, 256, 0, s>>>(A, (int)n, (long long)m, reinterpret_cast<const long long*>(ij),
+                                                 w, bad);
+    CDL_TRY(L.done());
+  }
+  unsigned long long h = 0;
+  CDL_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CDL_CUDA_TRY(cudaStreamSynchronize(s));
+  if (n_bad) *n_bad = (int64_t)h;
+  return h ? CDL_ERR_INVALID_ARG : CDL_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -663,7 +773,7 @@ int graph_build_static(const double* X, int64_t n64, int T, double sigma, double
       CDL_TRY(launched());
     }
   }
-  k_kernel_rows<<<std::min(n, sm_count * 8), 256, 0, s>>>(A, n, sigma_out, D);
+  k_kernel_rows<KERNEL_GAUSSIAN><<<std::min(n, sm_count * 8), 256, 0, s>>>(A, n, sigma_out, D);
   CDL_TRY(launched());
   k_sum<<<1, 1024, 0, s>>>(D, n, vol);
   return launched();

@@ -86,7 +86,9 @@ struct cdl_chain {
   unsigned* amax = nullptr;   // fp8 chains: per-level bound of |value| (float bits), scale = amax/448
   float* ahl = nullptr;       // A as float hi + lo planes (n x n each), the float-float residual's operand
   float* tscale = nullptr;    // per-tile e4m3 chains: d x (npad/128)^2 tile scales
-  void* aslices = nullptr;    // tensor chains: A as 6 bf16 planes npad x npad on the grids 2^-8s
+  void* aslices = nullptr;    // tensor chains: A / a_scale as 6 bf16 planes npad x npad on the grids 2^-8s
+  double* a_scale = nullptr;  // tensor chains (device, 2 words): [0] the power of two >= max A that the
+                              // slices are taken of, [1] the float64 bits of max |A|
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
@@ -116,6 +118,10 @@ namespace cdl {
 // reusing or growing it (respecting ctx->ws_cap).
 int ws_get(cdl_ctx* ctx, const char* name, size_t bytes, void** out);
 
+// *out (device) = the float64 bit pattern of max |x_i| over count values
+// (asynchronous; out is zeroed first).
+int abs_max_bits(cdl_ctx* ctx, const double* x, size_t count, unsigned long long* out);
+
 // Folds src's pending timings and adds its launch counters into dst, then
 // zeroes src's counters.
 int ctx_absorb(cdl_ctx* dst, cdl_ctx* src);
@@ -137,7 +143,10 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // ---- kernel launchers (one per translation unit family) ----
 // graph.cu
 int graph_build(cdl_ctx* ctx, const double* X, int64_t n, int T, double sigma, double* A,
-                double* D, double* vol, double* sigma_out);
+                double* D, double* vol, double* sigma_out, int kernel = 0);
+int graph_degrees(cdl_ctx* ctx, const double* A, int64_t n, double* D, double* vol);
+int graph_add_edges(cdl_ctx* ctx, double* A, int64_t n, int64_t m, const int64_t* ij, const double* w,
+                    int64_t* n_bad);
 int graph_build_static(const double* X, int64_t n, int T, double sigma, double* A, double* D,
                        double* vol, double* sigma_out, cudaStream_t stream);
 // chain.cu

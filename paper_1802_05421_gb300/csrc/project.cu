@@ -47,19 +47,24 @@ constexpr int CHUNK = 4096;  // exact float32 accumulation length (multiple of J
 constexpr int MAX_RPB = 64;  // node rows per block
 
 // Each (node row i, edge j) term o_ij sqrt(A_ij) is split into three float
-// pieces p1 + p2 + p3: p1 on the 2^-12 grid (|p1| <= 1), p2 on the 2^-24 grid
-// (|p2| <= 2^-13) and the remainder p3 (|p3| <= 2^-24). Signed sums of up to
-// 4096 p1 (or p2) values stay on their grid below 2^24 grid steps, so float32
-// adds them exactly; p3 is small enough for plain float32 sums. The three
-// partial sums are flushed to float64 in Y every 4096 edges. Per term and
-// projection row this is one sign construction and three fused multiply-adds
-// with +-1 (exact products).
+// pieces p1 + p2 + p3: with 2^h (h >= 0) the least power of two not below
+// sqrt(max A) (h = 0 for kernel graphs, whose weights are at most 1), p1 on
+// the 2^(h-12) grid (|p1| <= 2^h), p2 on the 2^(h-24) grid (|p2| <= 2^(h-13))
+// and the remainder p3 (|p3| <= 2^(h-24)). Signed sums of up to 4096 p1 (or
+// p2) values stay on their grid below 2^24 grid steps, so float32 adds them
+// exactly; p3 is small enough for plain float32 sums. The three partial sums
+// are flushed to float64 in Y every 4096 edges. Per term and projection row
+// this is one sign construction and three fused multiply-adds with +-1
+// (exact products).
 constexpr int RB = 16;       // projection rows per thread (half a Philox word)
 
 // Rows [bidx * rpb, bidx * rpb + rpb) of Y (written, not accumulated).
 __device__ __forceinline__ void project_rows_block(const double* __restrict__ A, int n, int k, int W, int rpb,
                                                    uint32_t key0, uint32_t key1, double scale,
-                                                   double* __restrict__ Y, int bidx) {
+                                                   double* __restrict__ Y, int bidx, int gexp) {
+  // piece grids 2^(gexp - 12) and 2^(gexp - 24) (gexp = h of the comment above)
+  const float up1 = __int_as_float((127 + 12 - gexp) << 23), dn1 = __int_as_float((127 - 12 + gexp) << 23);
+  const float up2 = __int_as_float((127 + 24 - gexp) << 23), dn2 = __int_as_float((127 - 24 + gexp) << 23);
   extern __shared__ __align__(16) unsigned char smraw[];
   float* P1 = reinterpret_cast<float*>(smraw);          // [rpb][JT]
   float* P2 = P1 + rpb * JT;                            // [rpb][JT]
@@ -104,9 +109,9 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
           const float sh = __fsqrt_rn(ah);
           const float res = __fadd_rn(__fmaf_rn(-sh, sh, ah), al);
           const float sl = __fmul_rn(res, __fdiv_rn(0.5f, sh));
-          p1 = __fmul_rn(rintf(__fmul_rn(sh, 4096.f)), 0x1p-12f);
+          p1 = __fmul_rn(rintf(__fmul_rn(sh, up1)), dn1);
           const float rem = __fsub_rn(sh, p1);                   // exact
-          p2 = __fmul_rn(rintf(__fmul_rn(rem, 16777216.f)), 0x1p-24f);
+          p2 = __fmul_rn(rintf(__fmul_rn(rem, up2)), dn2);
           p3 = __fadd_rn(__fsub_rn(rem, p2), sl);
           if (j < ii) {   // ii is the tail of edge (j, ii)
             p1 = -p1;
@@ -159,8 +164,10 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
 
 __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
                                                      uint32_t key0, uint32_t key1, double scale,
-                                                     double* __restrict__ Y) {
-  project_rows_block(A, n, k, W, rpb, key0, key1, scale, Y, blockIdx.x);
+                                                     double* __restrict__ Y,
+                                                     const unsigned long long* __restrict__ amax_bits) {
+  const int h = min((pow2_exp_above(*amax_bits) + 1) / 2, 100);   // sqrt(max A) <= 2^h (A < 2^200)
+  project_rows_block(A, n, k, W, rpb, key0, key1, scale, Y, blockIdx.x, h);
 }
 
 // Column sums of Y over 256-row chunks (fixed order): part[b][r].
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(256, 2) k_g_project(const uint32_t* __restrict
                                                        double scale) {
   const uint32_t t = tiles[blockIdx.x];
   const PGraph& G = gs[t & 0xFFFu];
-  project_rows_block(G.A, G.n, k, W, rpb, key0, key1, scale, G.Y, (int)(t >> 12));
+  project_rows_block(G.A, G.n, k, W, rpb, key0, key1, scale, G.Y, (int)(t >> 12), 0);   // kernel graphs: A <= 1
 }
 
 __global__ void __launch_bounds__(256) k_g_colsum(const uint32_t* __restrict__ tiles, const PGraph* __restrict__ gs,
@@ -245,9 +252,13 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
+  void* vmax;
+  CDL_TRY(ws_get(ctx, "project.amax", sizeof(unsigned long long), &vmax));
+  CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, static_cast<unsigned long long*>(vmax)));
   Launch L(ctx, CDL_KC_PROJECT, (double)n * (n - 1) * k);
   k_project<<<blocks, threads, smem, ctx->stream>>>(A, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
-                                                    (uint32_t)(seed >> 32), scale, Y);
+                                                    (uint32_t)(seed >> 32), scale, Y,
+                                                    static_cast<const unsigned long long*>(vmax));
   CDL_TRY(L.done());
   const int nparts = (n + 255) / 256;
   void* vpart;

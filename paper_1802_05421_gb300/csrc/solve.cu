@@ -445,20 +445,22 @@ __global__ void __launch_bounds__(256) k_zslice(const double* __restrict__ Z, in
   }
 }
 
-// R = (Y - D o Z) + c_r G (G from the column groups of at most 128), and
-// per-block sums of R^2.
+// R = (Y - D o Z) + (2^s c_r) G (G from the column groups of at most 128;
+// 2^s = a_scale[0], the scale of A's slices), and per-block sums of R^2.
 __global__ void __launch_bounds__(256) k_resid_combine(const double* __restrict__ Y, const double* __restrict__ Z,
                                                         const double* __restrict__ D, int n, int k, int np,
                                                         const double* __restrict__ G, const double* __restrict__ cs,
+                                                        const double* __restrict__ a_scale,
                                                         double* __restrict__ R, double* __restrict__ part) {
   __shared__ double red[8];
+  const double as = a_scale[0];
   double sq = 0.0;
   const size_t total = (size_t)n * k;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / k), r = (int)(idx % k);
     const int g = r / 128, rl = r % 128;
     const int kg = min(128, ((k - g * 128) + 31) / 32 * 32);
-    const double az = cs[r] * G[(size_t)g * np * 128 + (size_t)i * kg + rl];
+    const double az = (cs[r] * as) * G[(size_t)g * np * 128 + (size_t)i * kg + rl];   // powers of two: exact
     const double v = (Y[idx] - D[i] * Z[idx]) + az;
     R[idx] = v;
     sq = fma(v, v, sq);
@@ -884,7 +886,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       const int nb = std::min(1024, (int)blocks_for(nk, 256));
       Launch L(ctx, CDL_KC_RESIDUAL, 0);
       k_resid_combine<<<nb, 256, 0, st>>>(Y, Z, ch->D, n, k, np, static_cast<const double*>(vG),
-                                          static_cast<const double*>(vcs), R, red);
+                                          static_cast<const double*>(vcs), ch->a_scale, R, red);
       CDL_TRY(L.done());
       nparts = nb;
       return CDL_OK;

@@ -819,8 +819,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- exact-slice residual product
-// A Z for the float64-class residual, on the bf16 tensor cores. A (entries in
-// [0, 1]) and Z / c (c a power of two per column) are written as sums of six
+// A Z for the float64-class residual, on the bf16 tensor cores. A / 2^q (2^q
+// the least power of two, q >= 0, not below max A: entries in [0, 1]) and Z / c (c
+// a power of two per column) are written as sums of six
 // bf16 slices on the fixed grids 2^-8s (signed base-256 digits of the values
 // rounded to 2^-48), so every slice product a_s z_t is exact in float32 and
 // lies on the grid 2^-8(s+t), and a float32 sum of 256 of them (one K-chunk)
@@ -829,7 +830,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // count of grid steps, adds it to int32 accumulators, and every 64 chunks
 // (at most 2^30 steps) adds them, scaled by 2^-8(s+t), to the float64 result
 // G. The 21 slice pairs with s + t <= 7 leave about 2^-50 of |A| |Z / c|:
-// A Z = c G to float64 accuracy, as the ordering of the float64 additions
+// A Z = 2^q c G to float64 accuracy, as the ordering of the float64 additions
 // allows. Warp roles as in k_tc_fp8t (576 threads, 16 epilogue warps).
 constexpr int RS_SLICES = 6;
 constexpr int RS_MAX_PAIRS = 21;
