@@ -10,6 +10,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "ff.cuh"
 #include "internal.h"
 
@@ -45,6 +47,47 @@ __global__ void k_to_fixed(const double* __restrict__ X, int* __restrict__ Xt, i
     Xt[t * n + i] = ok ? (int)a : 0;
   }
   if (__syncthreads_or(off) && threadIdx.x == 0) atomicOr(&st->flags, 1);
+}
+
+// Three signed base-256 digit planes of a = x 2^16 for the tensor-core
+// distances (rows x tp bf16 each, zero padded): a = d0 + 2^8 d1 + 2^16 d2 with
+// |d| <= 128, exact in bf16. Inputs off the grid give zeros (the float64
+// kernel handles them).
+__global__ void __launch_bounds__(256) k_slice_x(const double* __restrict__ X, int n, int T, int rows, int tp,
+                                                  __nv_bfloat16* __restrict__ planes) {
+  const size_t plane = (size_t)rows * tp;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / tp), t = (int)(idx % tp);
+    int a = 0;
+    if (i < n && t < T) {
+      const double v = X[(size_t)i * T + t] * 65536.0;
+      if (v == rint(v) && fabs(v) < 8388608.0) a = (int)v;
+    }
+    const int d0 = ((a + 128) & 255) - 128;
+    const int a1 = (a - d0) >> 8;                         // exact: a - d0 is a multiple of 256
+    const int d1 = ((a1 + 128) & 255) - 128;
+    const int d2 = (a1 - d1) >> 8;
+    planes[idx] = __int2bfloat16_rn(d0);
+    planes[plane + idx] = __int2bfloat16_rn(d1);
+    planes[2 * plane + idx] = __int2bfloat16_rn(d2);
+  }
+}
+
+// |a_i|^2 = sum_t a_it^2 in int64 (exact), one warp per row; padded rows 0.
+__global__ void __launch_bounds__(256) k_row_norms(const double* __restrict__ X, int n, int T, int rows,
+                                                    long long* __restrict__ norms) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  long long acc = 0;
+  if (row < n)
+    for (int t = lane; t < T; t += 32) {
+      const double v = X[(size_t)row * T + t] * 65536.0;
+      const long long a = (v == rint(v) && fabs(v) < 8388608.0) ? (long long)v : 0;
+      acc += a * a;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norms[row] = acc;
 }
 
 __device__ __forceinline__ void tri_index(long long t, int nb, int& bi, int& bj) {
@@ -507,11 +550,25 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
   const int nb = (n + DT - 1) / DT;
   const long long tiles = (long long)nb * (nb + 1) / 2;
   if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
-  const double terms = 0.5 * (double)n * (double)(n - 1) * T;
   {
-    Launch L(ctx, CDL_KC_DISTANCE, terms);
-    k_dist_int<<<(unsigned)tiles, 256, 0, s>>>(static_cast<const int*>(wsXi), n, T, A, st);
-    CDL_TRY(L.done());
+    // grid inputs: exact Gram on the tensor cores (three bf16 digit planes)
+    const int rows = (n + 127) / 128 * 128, tp = (T + 63) / 64 * 64;
+    void *wsPl, *wsNo;
+    CDL_TRY(ws_get(ctx, "graph.xplanes", 3 * (size_t)rows * tp * 2, &wsPl));
+    CDL_TRY(ws_get(ctx, "graph.norms", (size_t)rows * sizeof(long long), &wsNo));
+    {
+      Launch L(ctx, CDL_KC_DISTANCE, 0);
+      const size_t cnt = (size_t)rows * tp;
+      k_slice_x<<<(unsigned)std::min<size_t>((cnt + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, s>>>(
+          X, n, T, rows, tp, static_cast<__nv_bfloat16*>(wsPl));
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_DISTANCE, 0);
+      k_row_norms<<<rows / 8, 256, 0, s>>>(X, n, T, rows, static_cast<long long*>(wsNo));
+      CDL_TRY(L.done());
+    }
+    CDL_TRY(dist_tc(ctx, wsPl, static_cast<const long long*>(wsNo), n, rows, tp, A, &st->flags));
   }
   {
     Launch L(ctx, CDL_KC_DISTANCE, 0);

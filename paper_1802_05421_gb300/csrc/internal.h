@@ -176,6 +176,12 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
 // A Z on the tensor cores from exact bf16 slices (A's in the chain, Z / c in
 // zslices: 6 planes kp x npad) into G (npad x kp float64).
 int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, double* G);
+// Exact squared distances of grid inputs on the tensor cores: planes = three
+// bf16 digit planes (rows x tp each, rows = n rounded up to 128, tp = T
+// rounded up to 64, zero padded), norms = |a_i|^2 (rows, int64); writes the
+// n x n float64 matrix A unless *offgrid & 1.
+int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
+            const int* offgrid);
 int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level);
 int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch);
 // Grouped (batched) tcgen05 launches: one launch over the tiles of many

@@ -1043,6 +1043,256 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- exact squared distances
+// d2_ij = |a_i|^2 + |a_j|^2 - 2 a_i . a_j for node series on the 2^-16 grid
+// (a = x 2^16, integers below 2^23 in magnitude). Each a is written as three
+// signed base-256 digits (|digit| <= 128, exact in bf16), so the Gram matrix is
+// a_i . a_j = sum_{s,t} 2^(8(s+t)) (D_s D_t^T)_ij over nine bf16 products.
+// Every digit product is exact in float32 (<= 2^14) and the slice pairs of
+// one weight w = s + t (at most three) summed over a 256-sample chunk stay
+// below 2^24, so the MMA's float32 accumulator holds an exact integer; the
+// epilogue adds it, shifted by 8w, to int64 accumulators. The result equals
+// the int64 sum of squared differences exactly; it is written as float64
+// multiples of 2^-32 to (i, j) and, off the diagonal blocks, to (j, i).
+// Tiles are 128 rows x 64 columns of the upper block triangle; warp roles as
+// in k_tc_resid.
+constexpr int DS_SLICES = 3;
+constexpr int DS_N = 64;
+constexpr int DS_STAGES = 8;
+constexpr int DS_A = 128 * 128;                  // 128 rows x 64 bf16
+constexpr int DS_B = DS_N * 128;                 // 64 rows x 64 bf16
+constexpr int DS_STAGE_BYTES = DS_A + DS_B;
+constexpr int DS_SMEM_BYTES = DS_STAGES * DS_STAGE_BYTES + 512 + 1024;
+constexpr int DS_TMEM_COLS = 2 * DS_N;           // two accumulator buffers
+constexpr int DS_CHUNK_KB = 4;                   // 256 samples per exact chunk
+
+struct DistMaps {
+  CUtensorMap a[DS_SLICES];   // digit planes, box 64 x 128 rows
+  CUtensorMap b[DS_SLICES];   // digit planes, box 64 x 64 rows
+};
+
+struct DistParams {
+  int nb128;                  // row blocks of 128
+  int nb64;                   // column blocks of 64 (2 nb128)
+  int num_tiles;              // tiles (I, J) with J >= 2 I
+  int kblocks;                // padded samples / 64
+  int n;
+  const long long* norms;     // |a_i|^2, rows padded with 0
+  double* A;                  // n x n output
+  const int* offgrid;         // bit 0 set: input off the grid (the float64 kernel runs instead)
+  uint32_t idesc;
+  unsigned* status;
+};
+
+// tile t -> (I, J): row block I holds nb64 - 2 I tiles J = 2 I .. nb64 - 1
+__device__ __forceinline__ void dist_tile(int t, int nb128, int nb64, int& I, int& J) {
+  int lo = 0, hi = nb128 - 1;
+  while (lo < hi) {                                      // last I with off(I) <= t
+    const int mid = (lo + hi + 1) >> 1;
+    const long long off = (long long)mid * nb64 - (long long)mid * (mid - 1);
+    if (off <= t) lo = mid; else hi = mid - 1;
+  }
+  I = lo;
+  J = 2 * lo + (int)(t - ((long long)lo * nb64 - (long long)lo * (lo - 1)));
+}
+
+__device__ __forceinline__ int ds_pairs(int w, int (&ps)[3], int (&pt)[3]) {
+  int c = 0;
+  for (int sa = 0; sa < DS_SLICES; ++sa) {
+    const int sb = w - sa;
+    if (sb >= 0 && sb < DS_SLICES) {
+      ps[c] = sa;
+      pt[c] = sb;
+      ++c;
+    }
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(T8_THREADS, 1)
+    k_tc_dist(const __grid_constant__ DistMaps maps, const DistParams p) {
+  if (*p.offgrid & 1) return;                            // uniform: before any barrier or allocation
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DS_STAGES * DS_STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * DS_STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * DS_STAGES + 7);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (DS_STAGES + s); };
+  auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * DS_STAGES + b); };
+  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * DS_STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * DS_STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (p.kblocks + DS_CHUNK_KB - 1) / DS_CHUNK_KB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < DS_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(pfull_bar(b), 1);
+      mbar_init(pempty_bar(b), T8_EPI);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(DS_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      int I, J;
+      dist_tile(t, p.nb128, p.nb64, I, J);
+      for (int w = 0; w <= 2 * (DS_SLICES - 1) && ok; ++w) {
+        int ps[3], pt[3];
+        const int np = ds_pairs(w, ps, pt);
+        for (int c = 0; c < nchunks && ok; ++c)
+          for (int pr = 0; pr < np && ok; ++pr)
+            for (int kb = c * DS_CHUNK_KB; kb < min(p.kblocks, (c + 1) * DS_CHUNK_KB); ++kb, ++it) {
+              const int s = it % DS_STAGES;
+              const uint32_t r = (uint32_t)(it / DS_STAGES);
+              if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              const uint32_t a_dst = smem_u32(smem + s * DS_STAGE_BYTES);
+              mbar_expect_tx(full_bar(s), DS_A + DS_B);
+              tma_load_2d(a_dst, &maps.a[ps[pr]], kb * 64, I * 128, full_bar(s));
+              tma_load_2d(a_dst + DS_A, &maps.b[pt[pr]], kb * 64, J * DS_N, full_bar(s));
+            }
+      }
+    }
+    if (!ok) {
+      for (int j = (it > DS_STAGES ? it - DS_STAGES : 0); j < it; ++j) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full_bar(j % DS_STAGES), (uint32_t)(j / DS_STAGES) & 1) &&
+               globaltimer() - t0 < WAIT_LIMIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer: one (weight, chunk) per TMEM buffer
+    int it = 0, pc = 0;
+    bool ok = true, issued = false;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
+      for (int w = 0; w <= 2 * (DS_SLICES - 1) && ok; ++w) {
+        int ps[3], pt[3];
+        const int np = ds_pairs(w, ps, pt);
+        for (int c = 0; c < nchunks && ok; ++c, ++pc) {
+          const int b = pc & 1;
+          const uint32_t ph = (uint32_t)(pc >> 1);
+          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * DS_N);
+          bool first = true;
+          for (int pr = 0; pr < np && ok; ++pr)
+            for (int kb = c * DS_CHUNK_KB; kb < min(p.kblocks, (c + 1) * DS_CHUNK_KB); ++kb, ++it) {
+              const int s = it % DS_STAGES;
+              if (!mbar_wait(full_bar(s), (uint32_t)(it / DS_STAGES) & 1, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(smem + s * DS_STAGE_BYTES);
+              const uint64_t adesc = smem_desc(a_addr);
+              const uint64_t bdesc = smem_desc(a_addr + DS_A);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, first ? 0u : 1u);
+                first = false;
+              }
+              issued = true;
+              mma_commit(empty_bar(s));
+            }
+          if (!ok) break;
+          mma_commit(pfull_bar(b));
+        }
+      }
+    if (!ok && issued) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue: exact integer Gram, d2, both triangles
+    const int q = warp & 3;                              // TMEM lane quarter
+    const int part = (warp - 2) >> 2;                    // 16-column part of the tile
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    int pc = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+      int I, J;
+      dist_tile(t, p.nb128, p.nb64, I, J);
+      long long g[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) g[e] = 0;
+      for (int w = 0; w <= 2 * (DS_SLICES - 1); ++w)
+        for (int c = 0; c < nchunks; ++c, ++pc) {
+          if (failed) continue;
+          const int b = pc & 1;
+          const uint32_t ph = (uint32_t)(pc >> 1);
+          if (!mbar_wait(pfull_bar(b), ph & 1, abort_flag, p.status)) {
+            failed = true;
+            continue;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[8];
+            tmem_ld8(tmem_base + lane_off + (uint32_t)(b * DS_N + part * 16 + h * 8), v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) g[h * 8 + e] += (long long)__float2int_rn(v[e]) * (1LL << (8 * w));
+          }
+          tc_fence_before();
+          mbar_arrive(pempty_bar(b));
+        }
+      if (failed) continue;
+      const int row = I * 128 + q * 32 + lane;
+      if (row >= p.n) continue;
+      const long long ni = p.norms[row];
+      const int col0 = J * DS_N + part * 16;
+      const bool mirror = J >= 2 * I + 2;                // off the diagonal 128-block
+      double* arow = p.A + (size_t)row * p.n;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int col = col0 + e;
+        if (col < p.n) {
+          const double d2 = (double)(ni + p.norms[col] - 2 * g[e]) * 0x1p-32;
+          arow[col] = d2;
+          if (mirror) p.A[(size_t)col * p.n + row] = d2;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(DS_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Level 0 of a per-tile e4m3 chain from its bf16 copy: one block per 128 x
 // 128 tile; scale = tile max / 448.
 __global__ void __launch_bounds__(256) k_quant_fp8_tiles(const __nv_bfloat16* __restrict__ L16, int np,
@@ -1397,6 +1647,42 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
   const int grid = std::min(p.num_tiles, ctx->sm_count);
   Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * np * kp);
   k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
+  return L.done();
+}
+
+int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
+            const int* offgrid) {
+  if (rows % 128 || tp % 64 || rows < n || tp < 64) return CDL_ERR_INVALID_ARG;
+  DistMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int s = 0; s < DS_SLICES; ++s) {
+    const char* base = static_cast<const char*>(planes) + (size_t)s * rows * tp * 2;
+    CDL_TRY(make_map(&maps.a[s], base, rows, tp, 128));
+    CDL_TRY(make_map(&maps.b[s], base, rows, tp, DS_N));
+  }
+  DistParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nb128 = rows / 128;
+  p.nb64 = 2 * p.nb128;
+  const long long tiles = (long long)p.nb128 * p.nb64 - (long long)p.nb128 * (p.nb128 - 1);
+  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  p.num_tiles = (int)tiles;
+  p.kblocks = tp / 64;
+  p.n = n;
+  p.norms = norms;
+  p.A = A;
+  p.offgrid = offgrid;
+  p.idesc = make_idesc(DS_N);
+  p.status = ctx->dev_status;
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, DS_SMEM_BYTES));
+    attr = true;
+  }
+  const int grid = (int)std::min<long long>(tiles, ctx->sm_count);
+  // 9 slice products over the computed tiles (upper block triangle)
+  Launch L(ctx, CDL_KC_DISTANCE, 2.0 * 9 * (double)tiles * 128 * DS_N * tp);
+  k_tc_dist<<<grid, T8_THREADS, DS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
 }
 
