@@ -43,6 +43,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 constexpr int JT = 32;       // j-tile
+constexpr int JTP = JT + 1;  // padded row stride of the piece arrays: the node rows of a warp fall in different banks
 constexpr int CHUNK = 4096;  // exact float32 accumulation length (multiple of JT)
 constexpr int MAX_RPB = 64;  // node rows per block
 
@@ -58,19 +59,33 @@ constexpr int MAX_RPB = 64;  // node rows per block
 // (exact products).
 constexpr int RB = 16;       // projection rows per thread (half a Philox word)
 
-// Rows [bidx * rpb, bidx * rpb + rpb) of Y (written, not accumulated).
+// Shared memory of a block: three piece arrays [rpb][JTP] floats, then (16-byte
+// aligned) the Philox words [rpb][JT * nrb + 1] (the extra word staggers banks).
+__host__ __device__ inline size_t project_words_offset(int rpb) {
+  return ((size_t)3 * rpb * JTP * sizeof(float) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t project_smem_bytes(int rpb, int W) {
+  const int nrb = (W + 3) / 4;
+  return project_words_offset(rpb) + (size_t)rpb * (JT * nrb + 1) * sizeof(uint4);
+}
+
+// Rows [bidx * rpb, bidx * rpb + rpb) of Y over the edges to nodes j in
+// [jbeg, jend) (jbeg a multiple of CHUNK): written, not accumulated, and
+// multiplied by `scale` when `final` (otherwise left unscaled: a partial sum).
 __device__ __forceinline__ void project_rows_block(const double* __restrict__ A, int n, int k, int W, int rpb,
                                                    uint32_t key0, uint32_t key1, double scale,
-                                                   double* __restrict__ Y, int bidx, int gexp) {
+                                                   double* __restrict__ Y, int bidx, int gexp, int jbeg, int jend,
+                                                   bool final) {
   // piece grids 2^(gexp - 12) and 2^(gexp - 24) (gexp = h of the comment above)
   const float up1 = __int_as_float((127 + 12 - gexp) << 23), dn1 = __int_as_float((127 - 12 + gexp) << 23);
   const float up2 = __int_as_float((127 + 24 - gexp) << 23), dn2 = __int_as_float((127 - 24 + gexp) << 23);
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* P1 = reinterpret_cast<float*>(smraw);          // [rpb][JT]
-  float* P2 = P1 + rpb * JT;                            // [rpb][JT]
-  float* P3 = P2 + rpb * JT;                            // [rpb][JT]
-  uint4* Wd = reinterpret_cast<uint4*>(P3 + rpb * JT);  // [rpb][JT][nrb]
+  float* P1 = reinterpret_cast<float*>(smraw);          // [rpb][JTP]
+  float* P2 = P1 + rpb * JTP;                           // [rpb][JTP]
+  float* P3 = P2 + rpb * JTP;                           // [rpb][JTP]
+  uint4* Wd = reinterpret_cast<uint4*>(smraw + project_words_offset(rpb));   // [rpb][WS]
   const int nrb = (W + 3) / 4;
+  const int WS = JT * nrb + 1;
   const int H = 2 * W;                 // threads per node row
   const int t = threadIdx.x;
   const int rl = t / H, h = t % H;
@@ -93,15 +108,15 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
     }
     first = false;
   };
-  for (int j0 = 0; j0 < n; j0 += JT) {
-    if (j0 > 0 && j0 % CHUNK == 0) flush();
+  for (int j0 = jbeg; j0 < jend; j0 += JT) {
+    if (j0 > jbeg && j0 % CHUNK == 0) flush();
     __syncthreads();
     // pieces of o_ij sqrt(A_ij) for the tile
     for (int e = t; e < rpb * JT; e += blockDim.x) {
       const int rr = e / JT, jj = e % JT;
       const int ii = i0 + rr, j = j0 + jj;
       float p1 = 0.f, p2 = 0.f, p3 = 0.f;
-      if (ii < n && j < n && j != ii) {
+      if (ii < n && j < jend && j != ii) {
         const ff a = split_nonneg(A[(size_t)ii * n + j]);   // integer split, no float64 ops
         const float ah = a.hi, al = a.lo;
         if (ah > 0.f) {
@@ -120,9 +135,9 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
           }
         }
       }
-      P1[e] = p1;
-      P2[e] = p2;
-      P3[e] = p3;
+      P1[rr * JTP + jj] = p1;
+      P2[rr * JTP + jj] = p2;
+      P3[rr * JTP + jj] = p3;
     }
     // Philox words: one call per (row, edge, 128-row block of the projection)
     for (int c = t; c < rpb * JT * nrb; c += blockDim.x) {
@@ -130,18 +145,18 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
       const int rr = e / JT, jj = e % JT;
       const int ii = i0 + rr, j = j0 + jj;
       uint4 o = make_uint4(0u, 0u, 0u, 0u);
-      if (ii < n && j < n && j != ii)
+      if (ii < n && j < jend && j != ii)
         o = philox4x32_10(make_uint4((uint32_t)min(ii, j), (uint32_t)max(ii, j), (uint32_t)rb, 0u), key0, key1);
-      Wd[e * nrb + rb] = o;
+      Wd[rr * WS + jj * nrb + rb] = o;
     }
     __syncthreads();
     if (!active) continue;
-    const int jmax = min(JT, n - j0);
+    const int jmax = min(JT, jend - j0);
     const int wi = w & 3, rb = w >> 2;
     for (int jj = 0; jj < jmax; ++jj) {
-      const int e = rl * JT + jj;
+      const int e = rl * JTP + jj;
       const float p1 = P1[e], p2 = P2[e], p3 = P3[e];
-      const uint4 o = Wd[e * nrb + rb];
+      const uint4 o = Wd[rl * WS + jj * nrb + rb];
       const uint32_t bits = wi == 0 ? o.x : wi == 1 ? o.y : wi == 2 ? o.z : o.w;
       const uint32_t nb = ~(bits >> shift);   // clear bit -> -1
 #pragma unroll
@@ -154,7 +169,7 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
     }
   }
   flush();
-  if (!active) return;
+  if (!active || !final) return;
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
     const int r = w * 32 + shift + b;
@@ -162,12 +177,28 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
   }
 }
 
+// Grid (row blocks, splits): split s covers the edge chunk [s CHUNK, (s + 1)
+// CHUNK) and, with more than one split, writes its unscaled partial sums to
+// Y + s n k (k_project_sum adds them in split order, which is the order in
+// which one block would have flushed its chunks, and scales).
 __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A, int n, int k, int W, int rpb,
                                                      uint32_t key0, uint32_t key1, double scale,
                                                      double* __restrict__ Y,
                                                      const unsigned long long* __restrict__ amax_bits) {
   const int h = min((pow2_exp_above(*amax_bits) + 1) / 2, 100);   // sqrt(max A) <= 2^h (A < 2^200)
-  project_rows_block(A, n, k, W, rpb, key0, key1, scale, Y, blockIdx.x, h);
+  const int split = blockIdx.y, nsplit = gridDim.y;
+  const int jbeg = split * CHUNK, jend = nsplit == 1 ? n : min(n, jbeg + CHUNK);
+  project_rows_block(A, n, k, W, rpb, key0, key1, scale, Y + (size_t)split * n * k, blockIdx.x, h, jbeg, jend,
+                     nsplit == 1);
+}
+
+__global__ void k_project_sum(const double* __restrict__ part, int nsplit, size_t count, double scale,
+                              double* __restrict__ Y) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
+    double v = part[idx];
+    for (int s = 1; s < nsplit; ++s) v += part[(size_t)s * count + idx];
+    Y[idx] = v * scale;
+  }
 }
 
 // Column sums of Y over 256-row chunks (fixed order): part[b][r].
@@ -220,7 +251,8 @@ __global__ void __launch_bounds__(256, 2) k_g_project(const uint32_t* __restrict
                                                        double scale) {
   const uint32_t t = tiles[blockIdx.x];
   const PGraph& G = gs[t & 0xFFFu];
-  project_rows_block(G.A, G.n, k, W, rpb, key0, key1, scale, G.Y, (int)(t >> 12), 0);   // kernel graphs: A <= 1
+  project_rows_block(G.A, G.n, k, W, rpb, key0, key1, scale, G.Y, (int)(t >> 12), 0, 0, G.n,
+                     true);   // kernel graphs: A <= 1
 }
 
 __global__ void __launch_bounds__(256) k_g_colsum(const uint32_t* __restrict__ tiles, const PGraph* __restrict__ gs,
@@ -243,10 +275,14 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
   const int W = (k + 31) / 32;
   const int rpb = std::max(1, std::min(MAX_RPB, 256 / (2 * W)));
   const int threads = rpb * 2 * W;
-  const int nrb = (W + 3) / 4;
-  const size_t smem = 3 * (size_t)rpb * JT * sizeof(float) + (size_t)rpb * JT * nrb * sizeof(uint4);
+  const size_t smem = project_smem_bytes(rpb, W);
   const int blocks = (n + rpb - 1) / rpb;
   const double scale = 1.0 / std::sqrt((double)k);
+  // One split per 4096-edge chunk, so that small row counts still fill the
+  // GPU in many waves; past 2 GB of partial sums (n above about 90k at
+  // k = 128) the row blocks alone are plenty and one split is used.
+  int nsplit = (n + CHUNK - 1) / CHUNK;
+  if ((double)nsplit * n * k * sizeof(double) > 2147483648.0) nsplit = 1;
   static bool attr = false;
   if (!attr) {
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
@@ -255,11 +291,26 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
   void* vmax;
   CDL_TRY(ws_get(ctx, "project.amax", sizeof(unsigned long long), &vmax));
   CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, static_cast<unsigned long long*>(vmax)));
-  Launch L(ctx, CDL_KC_PROJECT, (double)n * (n - 1) * k);
-  k_project<<<blocks, threads, smem, ctx->stream>>>(A, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
-                                                    (uint32_t)(seed >> 32), scale, Y,
-                                                    static_cast<const unsigned long long*>(vmax));
-  CDL_TRY(L.done());
+  double* out = Y;
+  if (nsplit > 1) {
+    void* vp;
+    CDL_TRY(ws_get(ctx, "project.partial", (size_t)nsplit * n * k * sizeof(double), &vp));
+    out = static_cast<double*>(vp);
+  }
+  {
+    Launch L(ctx, CDL_KC_PROJECT, (double)n * (n - 1) * k);
+    k_project<<<dim3(blocks, nsplit), threads, smem, ctx->stream>>>(A, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
+                                                                    (uint32_t)(seed >> 32), scale, out,
+                                                                    static_cast<const unsigned long long*>(vmax));
+    CDL_TRY(L.done());
+  }
+  if (nsplit > 1) {
+    const size_t cnt = (size_t)n * k;
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_project_sum<<<(unsigned)std::min<size_t>((cnt + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, ctx->stream>>>(
+        out, nsplit, cnt, scale, Y);
+    CDL_TRY(L.done());
+  }
   const int nparts = (n + 255) / 256;
   void* vpart;
   CDL_TRY(ws_get(ctx, "project.colsum", (size_t)nparts * k * sizeof(double), &vpart));
@@ -284,8 +335,7 @@ int project_grouped(cdl_ctx* ctx, const PGraph* gs, int G2, BTiles blocks, int r
   const int W = (k + 31) / 32;
   if (rpb < 1 || rpb > project_rows_per_block(k)) return CDL_ERR_INVALID_ARG;
   const int threads = rpb * 2 * W;
-  const int nrb = (W + 3) / 4;
-  const size_t smem = 3 * (size_t)rpb * JT * sizeof(float) + (size_t)rpb * JT * nrb * sizeof(uint4);
+  const size_t smem = project_smem_bytes(rpb, W);
   static bool attr = false;
   if (!attr) {
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_g_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
