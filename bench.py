@@ -262,7 +262,7 @@ def run_case(args):
             top = torch.empty(TOPK, dtype=torch.int64, device="cuda")
             Z2 = Y * 1e-3
             assert cdl.cdl_cad_score(ctx, A, A.flip(0).contiguous(), cdl.CDL_F64, Z2, Z2 * 1.5, vol, vol, n, k,
-                                     cdl.CDL_F32, TOPK, F, top) == 0
+                                     cdl.CDL_BF16 if args.score == "bf16" else cdl.CDL_F32, TOPK, F, top) == 0
     assert cdl.cdl_sync(ctx) == 0
     if ch is not None:
         cdl.cdl_chain_free(ch)
@@ -441,7 +441,8 @@ def run_host_levels(args):
     s1, s2 = cdl.cdl_solve_stats(), cdl.cdl_solve_stats()
 
     def timed(flags, steps, warmup):
-        o = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_BF16, cdl.CDL_F32, SEED, 0.0,
+        o = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_BF16, cdl.CDL_BF16 if args.score == "bf16" else cdl.CDL_F32,
+                              SEED, 0.0,
                               cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0, flags)
         for _ in range(warmup):
             assert cdl.cdl_caddelag_pair(ctx, X1, X2, n, T, o, F, top, s1, s2) == 0
@@ -544,6 +545,7 @@ def run_gmm(args):
     stream.synchronize()
     vol = [sc[0:1], sc[1:2]]
     chain = [None]
+    gscore = cdl.CDL_BF16 if args.score == "bf16" else cdl.CDL_F32
     stats = [cdl.cdl_solve_stats(), cdl.cdl_solve_stats()]
     sopts = cdl.cdl_solve_opts(40, REL_TOL, 0)
 
@@ -561,7 +563,7 @@ def run_gmm(args):
             ok(cdl.cdl_project(ctx, A[t], cdl.CDL_F64, n, K_PROJ, SEED, Y), "project")
             ok(cdl.cdl_chain_solve(ctx, chain[0], A[t], cdl.CDL_F64, Y, K_PROJ, sopts, Z[t], stats[t]), "solve")
         ok(cdl.cdl_cad_score(ctx, A[0], A[1], cdl.CDL_F64, Z[0], Z[1], vol[0].data_ptr(), vol[1].data_ptr(), n,
-                             K_PROJ, cdl.CDL_F32, TOPK, F, top), "cad_score")
+                             K_PROJ, gscore, TOPK, F, top), "cad_score")
 
     for _ in range(args.warmup):
         step()
@@ -654,7 +656,7 @@ def run_gmm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": GMM_WORKLOAD, "n": n, "points": "2-D, 4 components at (+-3, +-3), unit covariance",
                    "kernel": "exp(-d)", "noise": g.meta["noise"], "p": g.meta["p"], "added_edges": m,
-                   "k": K_PROJ, "d": D_CHAIN, "chain": "bf16", "score": "f32", "topk": TOPK,
+                   "k": K_PROJ, "d": D_CHAIN, "chain": "bf16", "score": args.score, "topk": TOPK,
                    "refine_rel_tol": REL_TOL, "solve_iters": iters, "rel_res": rel_res,
                    "l2": "no flush: each step writes two 8.6 GB float64 graphs and 2 x 30 GB of chain "
                          "levels, far larger than the 129 MB L2"},
@@ -683,6 +685,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdl", choices=["cdl", "reference"])
     ap.add_argument("--chain", default="bf16", choices=["bf16", "fp8", "fp8t", "f32", "f64"])
+    ap.add_argument("--score", default="bf16", choices=["bf16", "f32"],
+                    help="score arithmetic of the tensor-chain paths: bf16 = exact slices on the tensor cores, "
+                         "f32 = compensated float32 pipes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-compare-f32", dest="compare_f32", action="store_false",
@@ -729,7 +734,8 @@ def main():
     assert st == 0, cdl.cdl_status_string(st)
     chain = {"bf16": cdl.CDL_BF16, "fp8": cdl.CDL_FP8E4M3, "fp8t": cdl.CDL_FP8E4M3_T128, "f32": cdl.CDL_F32,
              "f64": cdl.CDL_F64}[args.chain]
-    score = cdl.CDL_F64 if args.chain == "f64" else cdl.CDL_F32
+    score = cdl.CDL_F64 if args.chain == "f64" else (cdl.CDL_BF16 if args.score == "bf16" else cdl.CDL_F32)
+    score_name = {cdl.CDL_F64: "f64", cdl.CDL_F32: "f32", cdl.CDL_BF16: "bf16"}[score]
     X1 = torch.from_numpy(wl.X[0]).cuda()
     X2 = torch.from_numpy(wl.X[1]).cuda()
     F = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -810,7 +816,7 @@ def main():
     # e4m3 chain with 128 x 128 tile scales on the same pair
     fp8t = None
     if args.compare_f32 and args.chain == "bf16":
-        o8 = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_FP8E4M3_T128, cdl.CDL_F32, SEED, 0.0,
+        o8 = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_FP8E4M3_T128, score, SEED, 0.0,
                                cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0)
         F8 = torch.empty(n, dtype=torch.float64, device="cuda")
         t8 = torch.empty(TOPK, dtype=torch.int64, device="cuda")
@@ -841,7 +847,7 @@ def main():
     # opt-in chain truncation (levels whose row sums fall to 2^-24 are not formed)
     trunc = None
     if args.compare_f32 and args.chain == "bf16":
-        ot = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_BF16, cdl.CDL_F32, SEED, 0.0,
+        ot = cdl.cdl_pair_opts(K_PROJ, D_CHAIN, cdl.CDL_BF16, score, SEED, 0.0,
                                cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0, cdl.CDL_CHAIN_TRUNCATE)
         Ft = torch.empty(n, dtype=torch.float64, device="cuda")
         tt = torch.empty(TOPK, dtype=torch.int64, device="cuda")
@@ -894,7 +900,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.chain, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "T": T, "k": K_PROJ, "d": D_CHAIN, "topk": TOPK,
-                       "chain": args.chain, "score": "f64" if score == cdl.CDL_F64 else "f32",
+                       "chain": args.chain, "score": score_name,
                        "refine_rel_tol": REL_TOL, "solve_iters": list(iters), "rel_res": rel_res,
                        "parallelism": f"replicas x{world}",
                        "l2": "no flush: each step streams two 8.6 GB float64 graphs and 30 GB of "

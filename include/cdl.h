@@ -362,6 +362,14 @@ int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* chain, const void* A, cdl_dty
  *   fused multiply-add and the k-term sum compensated (TwoSum); each
  *   difference c_2 - c_1 is within about 2^-44 sum_r |a_ir - a_jr||b_ir -
  *   b_jr| even where the k terms cancel. Scores accumulate in float64.
+ *   CDL_BF16 forms the k-term sums on the bf16 tensor cores, exactly:
+ *   c_2 - c_1 = d_i + d_j - M_ij with d_i = a_i.b_i and M_ij = a_i.b_j +
+ *   b_i.a_j, M from six exact bf16 slices of [a/g | b g] and [b g | a/g] (g a
+ *   power of two per column, c a power of two above every entry; slice
+ *   products and 128-term chunk sums exact in float32, combined in int64 in
+ *   units of c^2 2^-48), so c_2 - c_1 is within about 2^-47 c^2 of its
+ *   value wherever the terms cancel. Edge scores and sums in float64.
+ *   (cdl_cad_edges and cdl_cad_score_changed take CDL_F64 or CDL_F32.)
  * A1, A2: device n x n (CDL_F64). Z1, Z2: device n x k float64.
  * vol1, vol2: device, one float64 each. F: device n float64 output.
  * top_idx: device topk int64 output (may be NULL when topk == 0).
@@ -433,7 +441,9 @@ typedef struct {
   int32_t k;               /* projection dimension                          */
   int32_t d;               /* chain length (levels)                         */
   cdl_dtype chain_dtype;   /* CDL_F64, CDL_F32 or CDL_BF16                  */
-  cdl_dtype score_dtype;   /* CDL_F64 or CDL_F32 (see cdl_cad_score)        */
+  cdl_dtype score_dtype;   /* CDL_F64, CDL_F32 or CDL_BF16 (see
+                              cdl_cad_score; CDL_BF16 not with
+                              CDL_SCORE_CHANGED_ONLY)                       */
   uint64_t seed;           /* projection seed, shared by both graphs        */
   double sigma;            /* <= 0: median rule per graph                   */
   cdl_solve_opts solve;

@@ -516,7 +516,7 @@ int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtyp
                   int64_t n, int32_t k, cdl_dtype score_dtype, int32_t topk, double* F,
                   int64_t* top_idx) {
   if (!ctx) return CDL_ERR_INVALID_ARG;
-  if (score_dtype != CDL_F64 && score_dtype != CDL_F32) return CDL_ERR_INVALID_ARG;
+  if (score_dtype != CDL_F64 && score_dtype != CDL_F32 && score_dtype != CDL_BF16) return CDL_ERR_INVALID_ARG;
   if (n < 2 || n > (1 << 20) || k < 1 || k > 1024 || topk < 0 || topk > 1024 || topk > n)
     return CDL_ERR_INVALID_ARG;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
@@ -530,7 +530,7 @@ int cdl_cad_score(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtyp
   CDL_TRY(dev_ptr(ctx, F));
   if (topk > 0) CDL_TRY(dev_ptr(ctx, top_idx));
   return cad_score(ctx, static_cast<const double*>(A1), static_cast<const double*>(A2), Z1, Z2,
-                   vol1, vol2, n, k, score_dtype == CDL_F64, topk, F, top_idx);
+                   vol1, vol2, n, k, score_dtype, topk, F, top_idx);
 }
 
 int cdl_cad_edges(cdl_ctx* ctx, const void* A1, const void* A2, cdl_dtype a_dtype, const double* Z1, const double* Z2,
@@ -611,8 +611,9 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
   if (!ctx || !o || !X1 || !X2 || !F) return CDL_ERR_INVALID_ARG;
   if (n < 2 || n > (1 << 20) || T < 1 || T > 4096 || o->k < 1 || o->k > 1024 || o->d < 1 ||
       o->topk < 0 || o->topk > 1024 || o->topk > n || (o->topk > 0 && !top_idx) ||
-      (o->score_dtype != CDL_F64 && o->score_dtype != CDL_F32) || (o->score_flags & ~CDL_SCORE_CHANGED_ONLY) ||
-      ((o->score_flags & CDL_SCORE_CHANGED_ONLY) && !(o->sigma > 0)))
+      (o->score_dtype != CDL_F64 && o->score_dtype != CDL_F32 && o->score_dtype != CDL_BF16) ||
+      (o->score_flags & ~CDL_SCORE_CHANGED_ONLY) ||
+      ((o->score_flags & CDL_SCORE_CHANGED_ONLY) && (!(o->sigma > 0) || o->score_dtype == CDL_BF16)))
     return CDL_ERR_INVALID_ARG;
   CDL_TRY(set_device(ctx));
   const size_t nn = (size_t)n * n;
@@ -678,8 +679,7 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
     CDL_TRY(cad_score_changed(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype == CDL_F64,
                               static_cast<const int*>(vlist), m, o->topk, Fd, topd));
   } else {
-    CDL_TRY(cad_score(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype == CDL_F64,
-                      o->topk, Fd, topd));
+    CDL_TRY(cad_score(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype, o->topk, Fd, topd));
   }
   if (o->host_io) {
     CDL_CUDA_TRY(cudaMemcpyAsync(F, Fd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

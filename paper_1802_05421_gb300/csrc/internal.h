@@ -182,6 +182,12 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
 // n x n float64 matrix A unless *offgrid & 1.
 int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
             const int* offgrid);
+// Pair partials of the CAD scores with the Gram on the tensor cores: uplanes,
+// vplanes = six bf16 slice planes each (rows x k2p, zero padded) of u / c and
+// v / c; dint = d_i in units of c^2 2^-48; oscale = c^2 2^-48 (device);
+// writes contrib (64-node partner blocks x n) for k_score_reduce.
+int score_tc(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long long* dint, const double* oscale,
+             int n, int rows, int k2p, const double* A1, const double* A2, double* contrib);
 int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level);
 int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch);
 // Grouped (batched) tcgen05 launches: one launch over the tiles of many
@@ -369,6 +375,6 @@ int project(cdl_ctx* ctx, const double* A, int64_t n, int k, uint64_t seed, doub
 // score.cu
 int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1,
               const double* Z2, const double* vol1, const double* vol2, int64_t n, int k,
-              bool fp64, int topk, double* F, int64_t* top_idx);
+              cdl_dtype score_dtype, int topk, double* F, int64_t* top_idx);
 
 }  // namespace cdl

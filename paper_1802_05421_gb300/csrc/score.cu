@@ -14,6 +14,8 @@
 // Each unordered pair (i < j) is visited once in 64 x 64 upper-triangle
 // tiles; the two row contributions of a tile go to a per-(partner block, node)
 // slot, and F is the fixed-order sum of those slots (deterministic).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -303,6 +305,122 @@ __global__ void k_score_reduce(const double* __restrict__ contrib, int nb, int n
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += contrib[(size_t)b * n + i];
   F[i] = s;
+}
+
+// ---- tensor-core scores (score dtype bf16): slices of u = [a / g | b g] and
+// v = [b g | a / g], and d_i = a_i.b_i, for score_tc.
+__device__ __forceinline__ void tcs_ab(const double* __restrict__ Z1, const double* __restrict__ Z2, double s1,
+                                       double s2, size_t idx, double& a, double& b) {
+  const double w = s2 * Z2[idx], v = s1 * Z1[idx];
+  a = w - v;
+  b = w + v;
+}
+
+// column maxima of |a| (cm[r]) and |b| (cm[k + r]) as float64 bits
+__global__ void __launch_bounds__(256) k_tcs_colmax(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                                                     const double* __restrict__ vol1, const double* __restrict__ vol2,
+                                                     int n, int k, unsigned long long* __restrict__ cm) {
+  const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
+  const size_t nk = (size_t)n * k;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < nk; idx += (size_t)gridDim.x * blockDim.x) {
+    double a, b;
+    tcs_ab(Z1, Z2, s1, s2, idx, a, b);
+    const int r = (int)(idx % k);
+    atomicMax(cm + r, (unsigned long long)__double_as_longlong(fabs(a)));
+    atomicMax(cm + k + r, (unsigned long long)__double_as_longlong(fabs(b)));
+  }
+}
+
+// g_r = 2^e_r with e_r = floor((E(max|a_r|) - E(max|b_r|)) / 2) (E: binary
+// exponent), so that a / g and b g have maxima within a factor of 4; c = the
+// power of two strictly above every |a / g|, |b g| (cs[0]) and cs[1] =
+// c^2 2^-48, the unit of M and d. One block.
+__global__ void k_tcs_scales(const unsigned long long* __restrict__ cm, int k, double* __restrict__ g,
+                             double* __restrict__ cs) {
+  __shared__ int emax[256];
+  int em = -1100;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    const unsigned long long ba = cm[r], bb = cm[k + r];
+    int e = 0;
+    if (ba != 0 && bb != 0) {
+      const int ea = (int)((ba >> 52) & 0x7FF) - 1023, eb = (int)((bb >> 52) & 0x7FF) - 1023;
+      e = (ea - eb) >> 1;                                   // floor
+    }
+    g[r] = ldexp(1.0, e);
+    const double ma = __longlong_as_double((long long)ba) * ldexp(1.0, -e);
+    const double mb = __longlong_as_double((long long)bb) * ldexp(1.0, e);
+    const double mx = fmax(ma, mb);
+    if (mx > 0.0) em = max(em, (int)((__double_as_longlong(mx) >> 52) & 0x7FF) - 1023);
+  }
+  emax[threadIdx.x] = em;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int e = -1100;
+    for (int t = 0; t < (int)blockDim.x; ++t) e = max(e, emax[t]);
+    if (e < -1000) e = 0;                                   // all zero
+    cs[0] = ldexp(1.0, e + 1);                              // 2^E <= max < 2^(E+1) = c
+    cs[1] = ldexp(1.0, 2 * (e + 1) - 48);
+  }
+}
+
+// Six planes (rows x k2p bf16) each of u / c and v / c: signed base-256
+// digits of the values rounded to 2^-48 (|value| < 1: leading digit at most
+// 256, the others 128); zero padded.
+__global__ void __launch_bounds__(256) k_tcs_slice(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                                                    const double* __restrict__ vol1, const double* __restrict__ vol2,
+                                                    int n, int k, int rows, int k2p, const double* __restrict__ g,
+                                                    const double* __restrict__ cs, __nv_bfloat16* __restrict__ U,
+                                                    __nv_bfloat16* __restrict__ V) {
+  const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
+  const double rc = 1.0 / cs[0];                            // power of two: exact
+  const size_t plane = (size_t)rows * k2p;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / k2p), col = (int)(idx % k2p);
+    long long Nu = 0, Nv = 0;
+    if (i < n && col < 2 * k) {
+      const int r = col < k ? col : col - k;
+      double a, b;
+      tcs_ab(Z1, Z2, s1, s2, (size_t)i * k + r, a, b);
+      const double at = a / g[r], bt = b * g[r];            // powers of two: exact
+      const double xu = col < k ? at : bt, xv = col < k ? bt : at;
+      Nu = llrint(xu * rc * 0x1p48);
+      Nv = llrint(xv * rc * 0x1p48);
+    }
+#pragma unroll
+    for (int t = 1; t <= 6; ++t) {
+      const int sh = 48 - 8 * t;
+      long long du = Nu, dv = Nv;
+      if (sh > 0) {
+        du = (Nu + (1LL << (sh - 1))) >> sh;
+        dv = (Nv + (1LL << (sh - 1))) >> sh;
+      }
+      Nu -= du << sh;
+      Nv -= dv << sh;
+      U[(size_t)(t - 1) * plane + idx] = __float2bfloat16_rn(ldexpf((float)du, -8 * t));
+      V[(size_t)(t - 1) * plane + idx] = __float2bfloat16_rn(ldexpf((float)dv, -8 * t));
+    }
+  }
+}
+
+// d_i = sum_r a_ir b_ir (float64, columns in order), in units of c^2 2^-48,
+// one warp per row (padded rows 0).
+__global__ void __launch_bounds__(256) k_tcs_diag(const double* __restrict__ Z1, const double* __restrict__ Z2,
+                                                   const double* __restrict__ vol1, const double* __restrict__ vol2,
+                                                   int n, int k, int rows, const double* __restrict__ cs,
+                                                   long long* __restrict__ dint) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
+  double acc = 0.0;
+  if (row < n)
+    for (int r = lane; r < k; r += 32) {
+      double a, b;
+      tcs_ab(Z1, Z2, s1, s2, (size_t)row * k + r, a, b);
+      acc = fma(a, b, acc);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) dint[row] = llrint(acc / cs[1]);           // division by a power of two: exact
 }
 
 // (v, i) precedes (w, j) in the anomaly order: larger score first, then the
@@ -887,15 +1005,57 @@ int score_prepare(cdl_ctx* ctx, const double* Z1, const double* Z2, const double
 }
 
 int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
-              const double* vol1, const double* vol2, int64_t n64, int k, bool fp64, int topk,
+              const double* vol1, const double* vol2, int64_t n64, int k, cdl_dtype score_dtype, int topk,
               double* F, int64_t* top_idx) {
   const int n = (int)n64;
   cudaStream_t st = ctx->stream;
   const int nb = (n + ST - 1) / ST;
   void *vab, *vc;
   const size_t nk = (size_t)n * k;
-  CDL_TRY(score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, fp64, &vab));
+  const bool fp64 = score_dtype == CDL_F64;
   CDL_TRY(ws_get(ctx, "score.contrib", (size_t)nb * n * sizeof(double), &vc));
+  if (score_dtype == CDL_BF16) {
+    // Gram on the tensor cores from exact bf16 slices
+    const int rows = (n + 127) / 128 * 128, k2p = (2 * k + 63) / 64 * 64;
+    void *vcm, *vg, *vcs, *vu, *vv, *vd;
+    CDL_TRY(ws_get(ctx, "score.tc.cmax", 2 * (size_t)k * sizeof(unsigned long long), &vcm));
+    CDL_TRY(ws_get(ctx, "score.tc.g", (size_t)k * sizeof(double), &vg));
+    CDL_TRY(ws_get(ctx, "score.tc.scale", 2 * sizeof(double), &vcs));
+    CDL_TRY(ws_get(ctx, "score.tc.u", 6 * (size_t)rows * k2p * 2, &vu));
+    CDL_TRY(ws_get(ctx, "score.tc.v", 6 * (size_t)rows * k2p * 2, &vv));
+    CDL_TRY(ws_get(ctx, "score.tc.d", (size_t)rows * sizeof(long long), &vd));
+    unsigned long long* cm = static_cast<unsigned long long*>(vcm);
+    double* cs = static_cast<double*>(vcs);
+    CDL_CUDA_TRY(cudaMemsetAsync(cm, 0, 2 * (size_t)k * sizeof(unsigned long long), st));
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_tcs_colmax<<<(unsigned)std::min<size_t>((nk + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, st>>>(
+          Z1, Z2, vol1, vol2, n, k, cm);
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_tcs_scales<<<1, 256, 0, st>>>(cm, k, static_cast<double*>(vg), cs);
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      const size_t cnt = (size_t)rows * k2p;
+      k_tcs_slice<<<(unsigned)std::min<size_t>((cnt + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, st>>>(
+          Z1, Z2, vol1, vol2, n, k, rows, k2p, static_cast<const double*>(vg), cs,
+          static_cast<__nv_bfloat16*>(vu), static_cast<__nv_bfloat16*>(vv));
+      CDL_TRY(L.done());
+    }
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_tcs_diag<<<(rows + 7) / 8, 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, rows, cs,
+                                                 static_cast<long long*>(vd));
+      CDL_TRY(L.done());
+    }
+    CDL_TRY(score_tc(ctx, vu, vv, static_cast<const long long*>(vd), cs + 1, n, rows, k2p, A1, A2,
+                     static_cast<double*>(vc)));
+  } else {
+  CDL_TRY(score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, fp64, &vab));
   const long long tiles = (long long)nb * (nb + 1) / 2;
   if (fp64) {
     const double* aT = static_cast<const double*>(vab);
@@ -908,6 +1068,7 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
     k_score_pairs<<<(unsigned)tiles, 256, 0, st>>>(A1, A2, ah, ah + nk, ah + 2 * nk, ah + 3 * nk, n, k,
                                                    static_cast<double*>(vc));
     CDL_TRY(L.done());
+  }
   }
   {
     Launch L(ctx, CDL_KC_MISC, 0);

@@ -820,18 +820,20 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 
 // ---------------------------------------------------------------- exact-slice residual product
 // A Z for the float64-class residual, on the bf16 tensor cores. A / 2^q (2^q
-// the least power of two, q >= 0, not below max A: entries in [0, 1]) and Z / c (c
-// a power of two per column) are written as sums of six
-// bf16 slices on the fixed grids 2^-8s (signed base-256 digits of the values
-// rounded to 2^-48), so every slice product a_s z_t is exact in float32 and
-// lies on the grid 2^-8(s+t), and a float32 sum of 256 of them (one K-chunk)
-// is exact too (at most 2^24 grid steps). The MMA sums one K-chunk of one
-// slice pair into a TMEM buffer; the epilogue converts it to an integer
-// count of grid steps, adds it to int32 accumulators, and every 64 chunks
-// (at most 2^30 steps) adds them, scaled by 2^-8(s+t), to the float64 result
-// G. The 21 slice pairs with s + t <= 7 leave about 2^-50 of |A| |Z / c|:
-// A Z = 2^q c G to float64 accuracy, as the ordering of the float64 additions
-// allows. Warp roles as in k_tc_fp8t (576 threads, 16 epilogue warps).
+// the least power of two, q >= 0, not below max A: entries in [0, 1]) and
+// Z / c (c a power of two per column with |Z / c| < 1) are written as sums of
+// six bf16 slices on the fixed grids 2^-8s (signed base-256 digits of the
+// values rounded to 2^-48: the leading digit at most 256 in magnitude, the
+// others 128), so every slice product a_s z_t is exact in float32 (at most
+// 2^16 grid steps) and lies on the grid 2^-8(s+t), and a float32 sum of 256
+// of them (one K-chunk of one slice pair) is exact too (at most 2^24 grid
+// steps). The MMA sums one K-chunk of one slice pair into a TMEM buffer; the
+// epilogue converts it to an integer count of grid steps, adds it to int32
+// accumulators, and every 64 chunks (at most 2^30 steps) adds them, scaled
+// by 2^-8(s+t), to the float64 result G. The 21 slice pairs with s + t <= 7
+// leave about 2^-50 of |A| |Z / c|: A Z = 2^q c G to float64 accuracy, as
+// the ordering of the float64 additions allows. Warp roles as in k_tc_fp8t
+// (576 threads, 16 epilogue warps).
 constexpr int RS_SLICES = 6;
 constexpr int RS_MAX_PAIRS = 21;
 constexpr int RS_STAGES = 6;
@@ -1293,6 +1295,318 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- CAD scores, Gram on the tensor cores
+// Delta c_ij = c2(i,j) - c1(i,j) = (a_i - a_j).(b_i - b_j) = d_i + d_j - M_ij with
+// a = sqrt(vol2) Z2 - sqrt(vol1) Z1, b = sqrt(vol2) Z2 + sqrt(vol1) Z1,
+// d_i = a_i.b_i and M_ij = a_i.b_j + b_i.a_j = u_i.v_j for the rows
+// u = [a / g | b g] and v = [b g | a / g] (g a power of two per column that
+// balances the two halves; it cancels in every product). u / c and v / c
+// (c a power of two above every entry) are six bf16 slices on the grids
+// 2^-8s (signed base-256 digits of the values rounded to 2^-48: the leading
+// digit at most 256 in magnitude, the others 128). The slice pairs of one
+// weight w = s + t (w = 2 .. 7, 21 pairs) summed over a K-chunk of 128 stay
+// within 2^24 grid steps, so each TMEM buffer holds an exact integer; the
+// epilogue adds the chunks in int32 and the weights, shifted to the common
+// unit c^2 2^-48, in int64. With d_i in the same unit, Delta c_ij is formed
+// in int64 (no cancellation error beyond the slicing's 2^-49 of |a| |b|),
+// and E_ij = |A1_ij - A2_ij| |Delta c_ij| and its row and column sums are
+// float64. Tiles are 128 x 64 of the upper block triangle (pairs i < j only);
+// each 64 x 64 sub-block writes its row sums to contrib[partner block][i]
+// and column sums to contrib[row block][j] (row plus column sums on the
+// diagonal), the slots of the 64-node block layout of k_score_reduce, in
+// units of c^2 2^-48 times oscale. Warp roles as in k_tc_resid.
+constexpr int SC_SLICES = 6;
+constexpr int SC_N = 64;
+constexpr int SC_STAGES = 7;
+constexpr int SC_A = 128 * 128;                  // 128 rows x 64 bf16
+constexpr int SC_B = SC_N * 128;                 // 64 rows x 64 bf16
+constexpr int SC_STAGE_BYTES = SC_A + SC_B;
+constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N;
+constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + SC_EPI_DOUBLES * 8 + 1024;
+constexpr int SC_TMEM_COLS = 2 * SC_N;
+constexpr int SC_CHUNK_KB = 2;                   // 128 K per exact chunk
+
+struct ScoreMaps {
+  CUtensorMap u[SC_SLICES];   // slices of u, box 64 x 128 rows
+  CUtensorMap v[SC_SLICES];   // slices of v, box 64 x 64 rows
+};
+
+struct ScoreParams {
+  int nb128, nb64, num_tiles, kblocks, n;
+  const double* A1;
+  const double* A2;
+  const long long* dint;      // d_i in units of c^2 2^-48 (padded rows 0)
+  const double* oscale;       // c^2 2^-48
+  double* contrib;            // (n / 64 rounded up) x n partial sums
+  uint32_t idesc;
+  unsigned* status;
+};
+
+__device__ __forceinline__ int sc_pairs(int w, int (&ps)[SC_SLICES], int (&pt)[SC_SLICES]) {
+  int c = 0;
+  for (int sa = 1; sa <= SC_SLICES; ++sa) {
+    const int sb = w - sa;
+    if (sb >= 1 && sb <= SC_SLICES) {
+      ps[c] = sa - 1;
+      pt[c] = sb - 1;
+      ++c;
+    }
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(T8_THREADS, 1)
+    k_tc_score(const __grid_constant__ ScoreMaps maps, const ScoreParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SC_STAGES * SC_STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SC_STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * SC_STAGES + 7);
+  double* epi = reinterpret_cast<double*>(smem + SC_STAGES * SC_STAGE_BYTES + 512);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (SC_STAGES + s); };
+  auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * SC_STAGES + b); };
+  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * SC_STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * SC_STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (p.kblocks + SC_CHUNK_KB - 1) / SC_CHUNK_KB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SC_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(pfull_bar(b), 1);
+      mbar_init(pempty_bar(b), T8_EPI);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(SC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      int I, J;
+      dist_tile(t, p.nb128, p.nb64, I, J);
+      for (int w = 2; w <= SC_SLICES + 1 && ok; ++w) {
+        int ps[SC_SLICES], pt[SC_SLICES];
+        const int np = sc_pairs(w, ps, pt);
+        for (int c = 0; c < nchunks && ok; ++c)
+          for (int pr = 0; pr < np && ok; ++pr)
+            for (int kb = c * SC_CHUNK_KB; kb < min(p.kblocks, (c + 1) * SC_CHUNK_KB); ++kb, ++it) {
+              const int s = it % SC_STAGES;
+              const uint32_t r = (uint32_t)(it / SC_STAGES);
+              if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              const uint32_t a_dst = smem_u32(smem + s * SC_STAGE_BYTES);
+              mbar_expect_tx(full_bar(s), SC_A + SC_B);
+              tma_load_2d(a_dst, &maps.u[ps[pr]], kb * 64, I * 128, full_bar(s));
+              tma_load_2d(a_dst + SC_A, &maps.v[pt[pr]], kb * 64, J * SC_N, full_bar(s));
+            }
+      }
+    }
+    if (!ok) {
+      for (int j = (it > SC_STAGES ? it - SC_STAGES : 0); j < it; ++j) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full_bar(j % SC_STAGES), (uint32_t)(j / SC_STAGES) & 1) &&
+               globaltimer() - t0 < WAIT_LIMIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer: one (weight, chunk) per TMEM buffer
+    int it = 0, pc = 0;
+    bool ok = true, issued = false;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
+      for (int w = 2; w <= SC_SLICES + 1 && ok; ++w) {
+        int ps[SC_SLICES], pt[SC_SLICES];
+        const int np = sc_pairs(w, ps, pt);
+        for (int c = 0; c < nchunks && ok; ++c, ++pc) {
+          const int b = pc & 1;
+          const uint32_t ph = (uint32_t)(pc >> 1);
+          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * SC_N);
+          bool first = true;
+          for (int pr = 0; pr < np && ok; ++pr)
+            for (int kb = c * SC_CHUNK_KB; kb < min(p.kblocks, (c + 1) * SC_CHUNK_KB); ++kb, ++it) {
+              const int s = it % SC_STAGES;
+              if (!mbar_wait(full_bar(s), (uint32_t)(it / SC_STAGES) & 1, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(smem + s * SC_STAGE_BYTES);
+              const uint64_t adesc = smem_desc(a_addr);
+              const uint64_t bdesc = smem_desc(a_addr + SC_A);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, first ? 0u : 1u);
+                first = false;
+              }
+              issued = true;
+              mma_commit(empty_bar(s));
+            }
+          if (!ok) break;
+          mma_commit(pfull_bar(b));
+        }
+      }
+    if (!ok && issued) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue
+    const int q = warp & 3;                              // TMEM lane quarter (32 rows)
+    const int part = (warp - 2) >> 2;                    // 16-column part of the tile
+    const int et = threadIdx.x - 64;                     // epilogue thread 0 .. 511
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    double* rowpart = epi;                               // [128][4]
+    double* colpart = epi + 128 * 4;                     // [4][64]
+    const double osc = *p.oscale;
+    int pc = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+      int I, J;
+      dist_tile(t, p.nb128, p.nb64, I, J);
+      long long m[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) m[e] = 0;
+      for (int w = 2; w <= SC_SLICES + 1; ++w) {
+        const float up = __int_as_float((127 + 8 * w) << 23);   // 2^(8w)
+        int acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = 0;
+        for (int c = 0; c < nchunks; ++c, ++pc) {
+          if (failed) continue;
+          const int b = pc & 1;
+          const uint32_t ph = (uint32_t)(pc >> 1);
+          if (!mbar_wait(pfull_bar(b), ph & 1, abort_flag, p.status)) {
+            failed = true;
+            continue;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[8];
+            tmem_ld8(tmem_base + lane_off + (uint32_t)(b * SC_N + part * 16 + h * 8), v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[h * 8 + e] += __float2int_rn(v[e] * up);
+          }
+          tc_fence_before();
+          mbar_arrive(pempty_bar(b));
+        }
+        const int sh = 48 - 8 * w;                       // to the unit c^2 2^-48
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          m[e] += sh >= 0 ? (long long)acc[e] * (1LL << sh) : ((long long)acc[e] + (1LL << (-sh - 1))) >> (-sh);
+      }
+      // edge scores of the thread's 16 pairs (row i, columns col0 ..)
+      const int rl = q * 32 + lane;                      // row within the tile
+      const int row = I * 128 + rl;
+      const int col0 = J * SC_N + part * 16;
+      const int br = 2 * I + (q >> 1);                   // 64-row block of the row
+      const bool rowok = !failed && row < p.n && br <= J;
+      const long long di = rowok ? p.dint[row] : 0;
+      double ev[16];
+      double rs = 0.0;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int col = col0 + e;
+        double x = 0.0;
+        if (rowok && col < p.n && (br < J || row < col)) {
+          long long dc = di + p.dint[col] - m[e];
+          dc = dc < 0 ? -dc : dc;
+          const size_t o = (size_t)row * p.n + col;
+          x = fabs(p.A1[o] - p.A2[o]) * (double)dc;
+        }
+        ev[e] = x;
+        rs += x;
+      }
+      rowpart[rl * 4 + part] = rs;
+      // column sums over the warp's 32 rows: reduce-scatter, lane pairs end with one column each
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const bool hi = lane & 16;
+        const double keep = hi ? ev[e + 8] : ev[e], send = hi ? ev[e] : ev[e + 8];
+        ev[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool hi = lane & 8;
+        const double keep = hi ? ev[e + 4] : ev[e], send = hi ? ev[e] : ev[e + 4];
+        ev[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const bool hi = lane & 4;
+        const double keep = hi ? ev[e + 2] : ev[e], send = hi ? ev[e] : ev[e + 2];
+        ev[e] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      {
+        const bool hi = lane & 2;
+        const double keep = hi ? ev[1] : ev[0], send = hi ? ev[0] : ev[1];
+        ev[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+      }
+      ev[0] += __shfl_xor_sync(0xffffffffu, ev[0], 1);
+      const int cidx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+      if ((lane & 1) == 0) colpart[q * SC_N + part * 16 + cidx] = ev[0];
+      asm volatile("bar.sync 1, 512;" ::: "memory");
+      if (et < 128 && !failed) {
+        // row partial of tile row et over the 64 columns
+        const int r2 = I * 128 + et;
+        const int b2 = 2 * I + (et >> 6);
+        if (r2 < p.n && b2 <= J && J * SC_N < p.n) {
+          double v = ((rowpart[et * 4] + rowpart[et * 4 + 1]) + rowpart[et * 4 + 2]) + rowpart[et * 4 + 3];
+          if (b2 == J) {                                 // diagonal 64-block: add the column sum of the same node
+            const int hh = et >> 6, c = et - 64 * hh;
+            v += colpart[(2 * hh) * SC_N + c] + colpart[(2 * hh + 1) * SC_N + c];
+          }
+          p.contrib[(size_t)J * p.n + r2] = v * osc;
+        }
+      } else if (et < 256 && !failed) {
+        // column partial of column c over the 64 rows of half hh (off the diagonal 64-block)
+        const int x = et - 128, hh = x >> 6, c = x & 63;
+        const int col = J * SC_N + c, b2 = 2 * I + hh;
+        if (col < p.n && b2 < J)
+          p.contrib[(size_t)b2 * p.n + col] = (colpart[(2 * hh) * SC_N + c] + colpart[(2 * hh + 1) * SC_N + c]) * osc;
+      }
+      asm volatile("bar.sync 1, 512;" ::: "memory");
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(SC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Level 0 of a per-tile e4m3 chain from its bf16 copy: one block per 128 x
 // 128 tile; scale = tile max / 448.
 __global__ void __launch_bounds__(256) k_quant_fp8_tiles(const __nv_bfloat16* __restrict__ L16, int np,
@@ -1683,6 +1997,44 @@ int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int
   // 9 slice products over the computed tiles (upper block triangle)
   Launch L(ctx, CDL_KC_DISTANCE, 2.0 * 9 * (double)tiles * 128 * DS_N * tp);
   k_tc_dist<<<grid, T8_THREADS, DS_SMEM_BYTES, ctx->stream>>>(maps, p);
+  return L.done();
+}
+
+int score_tc(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long long* dint, const double* oscale,
+             int n, int rows, int k2p, const double* A1, const double* A2, double* contrib) {
+  if (rows % 128 || k2p % 64 || rows < n || k2p < 64) return CDL_ERR_INVALID_ARG;
+  ScoreMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int s = 0; s < SC_SLICES; ++s) {
+    const size_t off = (size_t)s * rows * k2p * 2;
+    CDL_TRY(make_map(&maps.u[s], static_cast<const char*>(uplanes) + off, rows, k2p, 128));
+    CDL_TRY(make_map(&maps.v[s], static_cast<const char*>(vplanes) + off, rows, k2p, SC_N));
+  }
+  ScoreParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nb128 = rows / 128;
+  p.nb64 = 2 * p.nb128;
+  const long long tiles = (long long)p.nb128 * p.nb64 - (long long)p.nb128 * (p.nb128 - 1);
+  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  p.num_tiles = (int)tiles;
+  p.kblocks = k2p / 64;
+  p.n = n;
+  p.A1 = A1;
+  p.A2 = A2;
+  p.dint = dint;
+  p.oscale = oscale;
+  p.contrib = contrib;
+  p.idesc = make_idesc(SC_N);
+  p.status = ctx->dev_status;
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_score, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_SMEM_BYTES));
+    attr = true;
+  }
+  const int grid = (int)std::min<long long>(tiles, ctx->sm_count);
+  // 21 slice products over the computed tiles
+  Launch L(ctx, CDL_KC_SCORE, 2.0 * 21 * (double)tiles * 128 * SC_N * k2p);
+  k_tc_score<<<grid, T8_THREADS, SC_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
 }
 

@@ -268,7 +268,10 @@ def test_solve_reports_not_converged(G):
 
 # ------------------------------------------------------------------ scores
 
-@pytest.mark.parametrize("score", ["f64", "f32"])
+SCORE_DT = {"f64": "CDL_F64", "f32": "CDL_F32", "bf16": "CDL_BF16"}
+
+
+@pytest.mark.parametrize("score", ["f64", "f32", "bf16"])
 def test_scores_match_oracle(G, score):
     cdl = G.cdl
     wl = iid_pair(333, 24, 6, seed=8)
@@ -277,17 +280,18 @@ def test_scores_match_oracle(G, score):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     v1 = torch.tensor([g[0]["vol"]], dtype=torch.float64, device="cuda")
     v2 = torch.tensor([g[1]["vol"]], dtype=torch.float64, device="cuda")
-    sd = cdl.CDL_F64 if score == "f64" else cdl.CDL_F32
+    sd = getattr(cdl, SCORE_DT[score])
     F, top = G.score(t(g[0]["A"]), t(g[1]["A"]), t(g[0]["Z"]), t(g[1]["Z"]), v1, v2, 8, sd)
     rel = np.abs(_h(F) - Fo) / Fo
-    # float32 pipes with grid-split differences and compensated sums: each
-    # commute-time difference to about 2^-45 of its terms' scale
+    # float32 pipes with grid-split differences and compensated sums, or exact
+    # bf16 slices on the tensor cores: each commute-time difference to about
+    # 2^-45 of its terms' scale
     assert rel.max() <= (1e-12 if score == "f64" else 1e-10), rel.max()
     if O.min_relative_gap(Fo, 8) > 1e-6:
         assert list(_h(top)) == list(O.top_anomalies(Fo, 8))
 
 
-@pytest.mark.parametrize("score", ["f64", "f32"])
+@pytest.mark.parametrize("score", ["f64", "f32", "bf16"])
 def test_scores_with_cancelling_sums(G, score):
     """Ragged-pair statistics (n = 407, 2 perturbed nodes, k = 32): for many
     node pairs the k-term commute-time difference cancels by a factor of 10^3;
@@ -300,12 +304,37 @@ def test_scores_with_cancelling_sums(G, score):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     v1 = torch.tensor([g[0]["vol"]], dtype=torch.float64, device="cuda")
     v2 = torch.tensor([g[1]["vol"]], dtype=torch.float64, device="cuda")
-    sd = cdl.CDL_F64 if score == "f64" else cdl.CDL_F32
+    sd = getattr(cdl, SCORE_DT[score])
     F, top = G.score(t(g[0]["A"]), t(g[1]["A"]), t(g[0]["Z"]), t(g[1]["Z"]), v1, v2, 5, sd)
     rel = np.abs(_h(F) - Fo) / Fo
     # float64 sums carry 2^-53 of the cancelling terms (up to 10^3 times the
     # difference): about 1e-11 on the worst node
     assert rel.max() <= 1e-10, rel.max()
+
+
+@pytest.mark.parametrize("n,k", [(130, 8), (1000, 128), (777, 96), (2, 1)])
+def test_scores_bf16_shapes(G, n, k):
+    """Tensor-core scores over ragged shapes: n not a multiple of the 128 x 64
+    tiles (partner blocks past n), k padded to the 64-wide K blocks, the
+    smallest graph; embeddings of unequal scale in the two graphs."""
+    cdl = G.cdl
+    rng = np.random.default_rng(n + k)
+    X1 = iid_pair(n, 12, 1, seed=n).X[0]
+    X2 = X1.copy()
+    X2[: max(1, n // 50)] += 0.25
+    A1, _, vol1, _ = O.gaussian_graph(X1)
+    A2, _, vol2, _ = O.gaussian_graph(X2)
+    Z1 = rng.standard_normal((n, k)) * 1e-2
+    Z2 = Z1 + rng.standard_normal((n, k)) * 1e-4
+    Fo = O.node_scores(A1, A2, Z1, Z2, vol1, vol2)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    v1 = torch.tensor([vol1], dtype=torch.float64, device="cuda")
+    v2 = torch.tensor([vol2], dtype=torch.float64, device="cuda")
+    F, top = G.score(t(A1), t(A2), t(Z1), t(Z2), v1, v2, min(n, 4), cdl.CDL_BF16)
+    F = _h(F)
+    ok = Fo > 0
+    assert np.all(F[~ok] == 0.0)
+    assert np.max(np.abs(F[ok] - Fo[ok]) / Fo[ok]) <= 1e-10
 
 
 # ------------------------------------------------------------------ whole pair (Alg. 4)
@@ -323,6 +352,7 @@ def iid1024():
     ("f32", "f64", 1e-9, False),
     ("bf16", "f32", 1e-6, False),
     ("bf16", "f32", 1e-6, True),
+    ("bf16", "bf16", 1e-6, False),
     ("fp8", "f32", 1e-6, False),
     ("fp8t", "f32", 1e-6, False),
 ])
