@@ -70,40 +70,6 @@ __global__ void __launch_bounds__(256) k_chain_init(const double* __restrict__ A
   }
 }
 
-// bf16 levels: the same formula in float32 arithmetic, A_ij (rf_i rf_j) - uf_i uf_j
-// with float copies of D^{-1/2} and u; the float32 error (a few 1e-7 relative to
-// either product) is far below the bf16 rounding of the result.
-// The same pass also writes A = A_hi + A_lo as two bf16 matrices (16
-// significant bits), the operand of the tensor-core residual update.
-__global__ void __launch_bounds__(256) k_chain_init_bf16(const double* __restrict__ A, int n, int npad,
-                                                          const float* __restrict__ rsf,
-                                                          const float* __restrict__ uf,
-                                                          __nv_bfloat16* __restrict__ L0,
-                                                          __nv_bfloat16* __restrict__ Ahi,
-                                                          __nv_bfloat16* __restrict__ Alo) {
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-  for (int i = blockIdx.x; i < npad; i += gridDim.x) {
-    const size_t off = (size_t)i * npad;
-    if (i >= n) {
-      for (int j = threadIdx.x; j < npad; j += blockDim.x) L0[off + j] = Ahi[off + j] = Alo[off + j] = z;
-      continue;
-    }
-    const float ri = rsf[i], ui = uf[i];
-    const double* row = A + (size_t)i * n;
-    for (int j = threadIdx.x; j < npad; j += blockDim.x) {
-      float v = 0.f, a = 0.f;
-      if (j < n) {
-        a = __double2float_rn(row[j]);
-        v = __fmaf_rn(a, __fmul_rn(ri, rsf[j]), -__fmul_rn(ui, uf[j]));
-      }
-      L0[off + j] = __float2bfloat16_rn(v);
-      const __nv_bfloat16 h = __float2bfloat16_rn(a);
-      Ahi[off + j] = h;
-      Alo[off + j] = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(h)));
-    }
-  }
-}
-
 // ---- fp8 (e4m3) chains: level i stores value / s_i with s_i = amax_i / 448,
 // amax_i a bound on |value| (float bits, so atomicMax on the bits orders them).
 
@@ -193,12 +159,11 @@ __global__ void __launch_bounds__(256) k_abs_max_bits(const double* __restrict__
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
-// A / 2^s as six bf16 planes on the grids 2^-8t: the signed base-256 digits of
-// A / 2^s rounded to 2^-48, with 2^s the least power of two (s >= 0) not
-// below max A, so that A / 2^s lies in [0, 1] (the kernel graphs have s = 0); zero
-// padded to npad x npad. The rounding uses the float64 bit pattern (integer
-// operations only): A = m 2^(e - 52), N = m / 2^(4 - e + s) rounded to
-// nearest (ties up).
+// A / 2^s on the grid 2^-48 as the integer N = round(A 2^(48 - s)), with 2^s
+// the least power of two (s >= 0) not below max A, so that A / 2^s lies in
+// [0, 1] (the kernel graphs have s = 0). The rounding uses the float64 bit
+// pattern (integer operations only): A = m 2^(e - 52), N = m / 2^(4 - e + s)
+// rounded to nearest (ties up).
 __device__ __forceinline__ long long grid48(double a, int s) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const int e = (int)((b >> 52) & 0x7FF);
@@ -210,37 +175,116 @@ __device__ __forceinline__ long long grid48(double a, int s) {
   return (long long)((m + (1ull << (sh - 1))) >> sh);
 }
 
-__global__ void __launch_bounds__(256) k_slice_a(const double* __restrict__ A, int n, int np,
-                                                  __nv_bfloat16* __restrict__ S, double* __restrict__ a_scale) {
-  const int sexp = pow2_exp_above((unsigned long long)__double_as_longlong(a_scale[1]));
-  if (blockIdx.x == 0 && threadIdx.x == 0) a_scale[0] = __longlong_as_double((long long)(1023 + sexp) << 52);
-  const size_t plane = (size_t)np * np;
-  const size_t groups = plane / 8;                        // np is a multiple of 128
-  for (size_t gidx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; gidx < groups;
-       gidx += (size_t)gridDim.x * blockDim.x) {
-    const size_t idx0 = gidx * 8;
-    const int i = (int)(idx0 / np), j0 = (int)(idx0 % np);
-    long long N[8];
+
+// Tensor chains: level 0 in bf16, A_ij (rf_i rf_j) - uf_i uf_j formed in
+// float32 with float copies of D^{-1/2} and u (the float32 error, a few 1e-7
+// relative to either product, is far below the bf16 rounding of the result);
+// A as two bf16 matrices A_hi + A_lo (the operand of the solve's recursive
+// residual update); and A / 2^s as six exact bf16 digit planes (N of grid48
+// split into signed base-256 digits d_t, plane t holding d_t 2^-8t), the
+// operand of its full residual; all in one pass over A; padding rows
+// and columns zero. Conversions use integer operations (float64 is the scarce
+// pipe): the float of A_ij rounded to nearest, the digits bottom-up (balanced
+// base 256 on two 24-bit halves of N = A_ij 2^(48-s): the five lower digits in
+// [-128, 128], the leading one at most 256) and their bf16 bit patterns.
+__device__ __forceinline__ float d2f_rn_nonneg(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126) return 0.f;                               // below the float normal range
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned q = (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1FFFFFFFull), half = 1u << 28;
+  if (rem > half || (rem == half && (q & 1u))) ++q;
+  if (q >> 23) {
+    q = 0;
+    ++e;
+  }
+  return __uint_as_float(((unsigned)(e + 127) << 23) | q);
+}
+
+__device__ __forceinline__ uint16_t digit_bf16(int d, int s) {   // d 2^-8s, |d| <= 256
+  if (d == 0) return 0;
+  const unsigned sg = d < 0 ? 0x8000u : 0u;
+  const unsigned a = d < 0 ? (unsigned)(-d) : (unsigned)d;
+  const int e = 31 - __clz(a);
+  const unsigned mant = (e <= 7 ? (a << (7 - e)) : (a >> (e - 7))) & 0x7Fu;
+  return (uint16_t)(sg | ((unsigned)(e + 127 - 8 * s) << 7) | mant);
+}
+
+__device__ __forceinline__ void digits6(long long N, int (&d)[6]) {   // N in [0, 2^48]
+  int lo = (int)(N & 0xFFFFFF), hi = (int)(N >> 24);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) N[e] = (i < n && j0 + e < n) ? grid48(A[(size_t)i * n + j0 + e], sexp) : 0;
+  for (int t = 5; t >= 3; --t) {
+    d[t] = ((lo + 128) & 255) - 128;
+    lo = (lo - d[t]) >> 8;
+  }
+  hi += lo;                                               // carry of the lower half
 #pragma unroll
-    for (int s = 1; s <= 6; ++s) {
-      const int sh = 48 - 8 * s;
-      const float scale = __int_as_float((127 - 8 * s) << 23);   // 2^-8s
-      uint32_t w[4];
+  for (int t = 2; t >= 1; --t) {
+    d[t] = ((hi + 128) & 255) - 128;
+    hi = (hi - d[t]) >> 8;
+  }
+  d[0] = hi;
+}
+
+// SL = false (the batched form's chains, which keep no slices): S and
+// a_scale are not touched (they may be null).
+template <bool SL>
+__global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict__ A, int n, int npad,
+                                                        const float* __restrict__ rsf, const float* __restrict__ uf,
+                                                        __nv_bfloat16* __restrict__ L0, __nv_bfloat16* __restrict__ Ahi,
+                                                        __nv_bfloat16* __restrict__ Alo, uint16_t* __restrict__ S,
+                                                        double* __restrict__ a_scale) {
+  int sexp = 0;
+  if constexpr (SL) {
+    sexp = pow2_exp_above((unsigned long long)__double_as_longlong(a_scale[1]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) a_scale[0] = __longlong_as_double((long long)(1023 + sexp) << 52);
+  }
+  const size_t plane = (size_t)npad * npad;
+  const int gpr = npad / 8;                               // groups of 8 columns per row
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < (size_t)npad * gpr;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(g / gpr), j0 = (int)(g % gpr) * 8;
+    const size_t o = (size_t)i * npad + j0;
+    uint32_t wl[4] = {0, 0, 0, 0}, wh[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0}, ws[6][4] = {};
+    if (i < n) {
+      const float ri = rsf[i], ui = uf[i];
+      const double* row = A + (size_t)i * n;
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
-        long long d0 = N[e], d1 = N[e + 1];
-        if (sh > 0) {
-          d0 = (N[e] + (1LL << (sh - 1))) >> sh;
-          d1 = (N[e + 1] + (1LL << (sh - 1))) >> sh;
+        float v[2] = {0.f, 0.f}, af[2] = {0.f, 0.f};
+        int dg[2][6] = {};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = j0 + e + h;
+          if (j < n) {
+            const double a = row[j];
+            af[h] = d2f_rn_nonneg(a);
+            v[h] = __fmaf_rn(af[h], __fmul_rn(ri, rsf[j]), -__fmul_rn(ui, uf[j]));
+            if constexpr (SL) digits6(grid48(a, sexp), dg[h]);
+          }
         }
-        N[e] -= d0 << sh;
-        N[e + 1] -= d1 << sh;
-        __nv_bfloat162 h = __floats2bfloat162_rn((float)d0 * scale, (float)d1 * scale);
-        w[e / 2] = *reinterpret_cast<uint32_t*>(&h);
+        const __nv_bfloat162 lv = __floats2bfloat162_rn(v[0], v[1]);
+        const __nv_bfloat162 hv = __floats2bfloat162_rn(af[0], af[1]);
+        const float2 hf = __bfloat1622float2(hv);
+        const __nv_bfloat162 ov = __floats2bfloat162_rn(__fsub_rn(af[0], hf.x), __fsub_rn(af[1], hf.y));
+        wl[e / 2] = *reinterpret_cast<const uint32_t*>(&lv);
+        wh[e / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+        wo[e / 2] = *reinterpret_cast<const uint32_t*>(&ov);
+        if constexpr (SL) {
+#pragma unroll
+          for (int t = 0; t < 6; ++t)
+            ws[t][e / 2] = (uint32_t)digit_bf16(dg[0][t], t + 1) | ((uint32_t)digit_bf16(dg[1][t], t + 1) << 16);
+        }
       }
-      *reinterpret_cast<uint4*>(S + (size_t)(s - 1) * plane + idx0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    *reinterpret_cast<uint4*>(L0 + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4*>(Alo + o) = make_uint4(wo[0], wo[1], wo[2], wo[3]);
+    if constexpr (SL) {
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        *reinterpret_cast<uint4*>(S + (size_t)t * plane + o) = make_uint4(ws[t][0], ws[t][1], ws[t][2], ws[t][3]);
     }
   }
 }
@@ -407,13 +451,8 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
     k_split_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, cnt, ch->ahl, ch->ahl + cnt);
     CDL_TRY(L.done());
   }
-  if (ch->aslices) {
+  if (ch->aslices)   // the slices' scale: max A, read before level 0 is formed
     CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, reinterpret_cast<unsigned long long*>(ch->a_scale + 1)));
-    Launch L(ctx, CDL_KC_CHAIN_INIT, 8.0 * n * (double)n + 12.0 * np * (double)np);
-    k_slice_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, n, np, static_cast<__nv_bfloat16*>(ch->aslices),
-                                                          ch->a_scale);
-    CDL_TRY(L.done());
-  }
   void* wsu;
   CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * (sizeof(double) + 2 * sizeof(float)), &wsu));
   double* u = static_cast<double*>(wsu);
@@ -424,8 +463,24 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
     k_chain_vectors<<<(np + 255) / 256, 256, 0, ctx->stream>>>(ch->D, ch->vol, n, np, ch->rsqrt_d, u, rsf, uf);
     CDL_TRY(L.done());
   }
-  const double bytes = 8.0 * n * (double)n + (double)ch->elem * np * (double)np * (ch->dtype == CDL_BF16 ? 3 : 1);
+  const bool tensor = ch->aslices != nullptr;
+  // algorithmic bytes: A read once; level 0 written (plus A hi, lo and, for
+  // single-graph tensor chains, six slices)
+  const double bytes = 8.0 * n * (double)n + (double)ch->elem * np * (double)np +
+                       (ch->aop ? 4.0 * np * (double)np : 0.0) + (tensor ? 12.0 * np * (double)np : 0.0);
   const int blocks = std::min(np, ctx->sm_count * 8);
+  // level 0 in bf16 with A hi/lo and the slices (tensor chains)
+  auto init16 = [&](void* L0) {
+    __nv_bfloat16* l0 = static_cast<__nv_bfloat16*>(L0);
+    __nv_bfloat16* ahi = static_cast<__nv_bfloat16*>(ch->aop);
+    __nv_bfloat16* alo = ahi + (size_t)np * np;
+    if (tensor)
+      k_chain_init_tc<true><<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(
+          A, n, np, rsf, uf, l0, ahi, alo, static_cast<uint16_t*>(ch->aslices), ch->a_scale);
+    else
+      k_chain_init_tc<false><<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, n, np, rsf, uf, l0, ahi, alo, nullptr,
+                                                                         nullptr);
+  };
   Launch L(ctx, CDL_KC_CHAIN_INIT, bytes);
   switch (ch->dtype) {
     case CDL_F64:
@@ -439,9 +494,7 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
     case CDL_FP8E4M3: {
       // bf16 level 0 (apply copy) and A_hi/A_lo, then the bound and the e4m3 level
       CDL_CUDA_TRY(cudaMemsetAsync(ch->amax, 0, ch->d * sizeof(unsigned), ctx->stream));
-      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
-          A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(ch->level16(0)), static_cast<__nv_bfloat16*>(ch->aop),
-          static_cast<__nv_bfloat16*>(ch->aop) + (size_t)np * np);
+      init16(ch->level16(0));
       CDL_TRY(L.done());
       const size_t cnt = (size_t)np * np;
       {
@@ -456,16 +509,12 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
       return L3.done();
     }
     case CDL_FP8E4M3_T128:
-      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
-          A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(ch->level16(0)), static_cast<__nv_bfloat16*>(ch->aop),
-          static_cast<__nv_bfloat16*>(ch->aop) + (size_t)np * np);
+      init16(ch->level16(0));
       CDL_TRY(L.done());
       return fp8t_quantize_level0(ctx, ch);
     case CDL_BF16: {
       void* L0 = ch->host_levels ? ooc_write_begin(ctx, ch, 0) : ch->level(0);
-      k_chain_init_bf16<<<blocks, 256, 0, ctx->stream>>>(
-          A, n, np, rsf, uf, static_cast<__nv_bfloat16*>(L0), static_cast<__nv_bfloat16*>(ch->aop),
-          static_cast<__nv_bfloat16*>(ch->aop) + (size_t)np * np);
+      init16(L0);
       CDL_TRY(L.done());
       return ch->host_levels ? ooc_write_end(ctx, ch, 0) : CDL_OK;
     }

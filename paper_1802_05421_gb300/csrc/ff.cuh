@@ -87,6 +87,46 @@ __device__ __forceinline__ int pow2_exp_above(unsigned long long bits) {
   return up > 0 ? up : 0;
 }
 
+// Unsigned 64-bit integers to floating point with integer operations only.
+// u64_top24: x truncated to its 24 leading bits, as a float (exact for x <
+// 2^24). ff_from_u64: x as hi + lo, both truncations (|x - hi - lo| < 2^-47 x).
+// u64_to_double_rn: x 2^scale_exp rounded to nearest even, the float64 the
+// hardware conversion gives (x 2^scale_exp in the normal range).
+__device__ __forceinline__ float u64_top24(unsigned long long x) {
+  if (x == 0) return 0.f;
+  const int e = 63 - __clzll((long long)x);
+  const unsigned long long top = e >= 23 ? (x >> (e - 23)) : (x << (23 - e));
+  return __uint_as_float(((uint32_t)(e + 127) << 23) | ((uint32_t)top & 0x7FFFFFu));
+}
+
+__device__ __forceinline__ ff ff_from_u64(unsigned long long x) {
+  if (x == 0) return {0.f, 0.f};
+  const int e = 63 - __clzll((long long)x);
+  const unsigned long long rest = e > 23 ? x & ((1ull << (e - 23)) - 1ull) : 0ull;
+  return {u64_top24(x), u64_top24(rest)};
+}
+
+__device__ __forceinline__ double u64_to_double_rn(unsigned long long x, int scale_exp) {
+  if (x == 0) return 0.0;
+  int e = 63 - __clzll((long long)x);
+  unsigned long long m;
+  if (e <= 52) {
+    m = x << (52 - e);
+  } else {
+    const int sh = e - 52;
+    unsigned long long q = x >> sh;
+    const unsigned long long rem = x & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    if (q >> 53) {
+      q >>= 1;
+      ++e;
+    }
+    m = q;
+  }
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(e + 1023 + scale_exp) << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
 __device__ __forceinline__ float d2f_trunc(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
@@ -105,16 +145,8 @@ __device__ __forceinline__ float d2f_trunc(double x) {
 // (remainder below 2^-52 for |r| <= 0.35): degrees 7..12 in float32 (each term
 // below 2^-22 of the result), degrees 0..6 in float-float Horner steps; the
 // coefficients 1/m! are stored as float pairs. Valid for t < 700.
-__device__ __forceinline__ ff ff_exp_neg_scaled(double t, int& k_out) {
-  const float k = rintf(__fmul_rn(d2f_trunc(t), 0x1.715476p+0f));   // t / ln2
-  const double kd = f2d_bits(k);
-  double r = fma(-kd, 0x1.62e42fefa2000p-1, t);
-  r = fma(-kd, 0x1.9ef35793c7673p-41, r);
-  // float-float split of r with integer conversions: rh exact top bits, rl the
-  // remainder truncated to 24 bits (error below 2^-48 |r|)
-  const float rh = d2f_trunc(r);
-  const float rl = d2f_trunc(r - f2d_bits(rh));
-  const ff x = {-rh, -rl};
+// e^x for a float-float |x| <= 0.35 (the series part of the exponentials below).
+__device__ __forceinline__ ff ff_exp_series(ff x) {
   float p = 0x1.1eed8ep-29f;                      // 1/12!
   p = __fmaf_rn(p, x.hi, 0x1.ae6456p-26f);        // 1/11!
   p = __fmaf_rn(p, x.hi, 0x1.27e4fcp-22f);        // 1/10!
@@ -129,8 +161,77 @@ __device__ __forceinline__ ff ff_exp_neg_scaled(double t, int& k_out) {
   q = ff_add(ff_mul(q, x), ff{0x1p-1f, 0.f});                        // 1/2!
   q = ff_add(ff_mul(q, x), ff{1.f, 0.f});                            // 1/1!
   q = ff_add(ff_mul(q, x), ff{1.f, 0.f});                            // 1/0!
+  return q;
+}
+
+__device__ __forceinline__ ff ff_exp_neg_scaled(double t, int& k_out) {
+  const float k = rintf(__fmul_rn(d2f_trunc(t), 0x1.715476p+0f));   // t / ln2
+  const double kd = f2d_bits(k);
+  double r = fma(-kd, 0x1.62e42fefa2000p-1, t);
+  r = fma(-kd, 0x1.9ef35793c7673p-41, r);
+  // float-float split of r with integer conversions: rh exact top bits, rl the
+  // remainder truncated to 24 bits (error below 2^-48 |r|)
+  const float rh = d2f_trunc(r);
+  const float rl = d2f_trunc(r - f2d_bits(rh));
   k_out = (int)k;
-  return q;                                                          // in [0.70, 1.42]
+  return ff_exp_series(ff{-rh, -rl});                                // in [0.70, 1.42]
+}
+
+// exp(-x y) for float64 x >= 0, y > 0 with x y < 690, as (q.hi + q.lo) 2^-k
+// with no float64 operation: the product t = x y is formed exactly as the
+// 106-bit product of the two 53-bit mantissas and kept to 64 fractional bits
+// (128-bit integers); k = round(t / ln2) from a float estimate; r = t - k ln2
+// with ln2 to 64 fractional bits (error below 2^-54 for k < 1024) is a signed
+// 64-bit fixed-point number, split into float-float with integer operations;
+// exp(-r) is the series above (|r| <= 0.35).
+__device__ __forceinline__ ff ff_exp_neg_prod(double x, double y, int& k_out) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+  const int ex = (int)((bx >> 52) & 0x7FF), ey = (int)((by >> 52) & 0x7FF);
+  unsigned __int128 T = 0;                                           // t 2^64
+  if (ex != 0 && ey != 0) {
+    const unsigned long long mx = (bx & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned long long my = (by & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned __int128 P = (unsigned __int128)mx * my;         // t = P 2^(ex + ey - 2150)
+    const int sh = ex + ey - 2150 + 64;                              // T = P 2^sh, sh < -30 for t < 2^10
+    if (sh >= 0)
+      T = P << sh;
+    else if (sh > -127)
+      T = P >> (-sh);
+  }
+  const float tf = __fmul_rn(u64_top24((unsigned long long)(T >> 40)), 0x1p-24f);
+  const int k = __float2int_rn(__fmul_rn(tf, 0x1.715476p+0f));       // t / ln2
+  const unsigned __int128 kl = (unsigned __int128)(unsigned)k * 0xB17217F7D1CF79ABull;   // k ln2 2^64
+  const long long r = (long long)(__int128)(T - kl);                 // |r| < 2^63
+  const unsigned long long ar = r < 0 ? (unsigned long long)(-r) : (unsigned long long)r;
+  const ff m = ff_from_u64(ar);
+  const float hi = __fmul_rn(m.hi, 0x1p-64f), lo = __fmul_rn(m.lo, 0x1p-64f);   // exact powers of two
+  k_out = k;
+  return ff_exp_series(r < 0 ? ff{hi, lo} : ff{-hi, -lo});           // exp(-r), in [0.70, 1.42]
+}
+
+// (q.hi + q.lo) 2^-k as float64 for q in [0.5, 2) (q.hi > 0, |q.lo| <= ulp(q.hi)),
+// rounded to nearest even, with integer operations only (2^-k in the normal range).
+__device__ __forceinline__ double ff_scaled_to_double(ff q, int k) {
+  const uint32_t hb = __float_as_uint(q.hi);
+  const int eh = (int)((hb >> 23) & 0xFF) - 127;                     // -1 or 0
+  long long V = (long long)((hb & 0x7FFFFFu) | 0x800000u) << (eh + 30);   // (q.hi) 2^53
+  const uint32_t lb = __float_as_uint(q.lo);
+  const int el = (int)((lb >> 23) & 0xFF) - 127;
+  if ((lb & 0x7FFFFFFFu) != 0 && el > -127) {
+    const long long ml = (long long)((lb & 0x7FFFFFu) | 0x800000u);
+    const int s = el + 30;
+    const long long L = s >= 0 ? (ml << s) : (s > -64 ? (ml >> (-s)) : 0);
+    V += (lb >> 31) ? -L : L;
+  }
+  int E = -1;
+  unsigned long long mant = (unsigned long long)V;                   // leading bit 52 or 53
+  if (mant >> 53) {
+    const unsigned long long h = mant >> 1;
+    mant = h + ((mant & 1ull) & (h & 1ull));                         // ties to even
+    E = 0;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(E - k + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 // exp(-t) as float64 (see ff_exp_neg_scaled); float64 exp beyond t = 700.

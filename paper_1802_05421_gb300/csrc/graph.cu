@@ -299,11 +299,13 @@ __global__ void k_set_scalar(double* p, double v) { *p = v; }
 // A_ij = exp(-d2_ij / (2 sigma^2)) (KERN = KERNEL_GAUSSIAN) or
 // A_ij = exp(-sqrt(d2_ij) / sigma) (KERN = KERNEL_EXP, the synthetic-data
 // kernel of Sec. 4.2.1), A_ii = 0, D_i = row sum. One block per row.
-// The exponential is ff_exp_neg_scaled (float64 argument reduction, float-float
-// series, about 1e-14 relative); the argument is d2 * (1 / (2 sigma^2)), or the
-// correctly rounded sqrt(d2) times 1 / sigma (one float64 product); the row
-// sum is accumulated in float-float (terms below 2^-100 are dropped from the
-// sum, not from A).
+// The exponential is ff_exp_neg_prod: the argument d2 * (1 / (2 sigma^2)), or
+// the correctly rounded sqrt(d2) times 1 / sigma, is formed exactly in 128-bit
+// integers and reduced there, then a float-float series (about 1e-14
+// relative) and an integer assembly of the float64 result: no float64
+// operation but the square root of the exp kernel, float64 being the scarce
+// pipe. The row sum is accumulated in float-float (terms below 2^-100 are
+// dropped from the sum, not from A).
 enum { KERNEL_GAUSSIAN = 0, KERNEL_EXP = 1 };
 
 template <int KERN = KERNEL_GAUSSIAN>
@@ -312,15 +314,16 @@ __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double
   __shared__ double red[8];
   {
     double* row = A + (size_t)i * n;
+    const float rcpf = d2f_trunc(rcp);
     ff acc = {0.f, 0.f};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const double t = (KERN == KERNEL_EXP ? __dsqrt_rn(row[j]) : row[j]) * rcp;
+      const double x = KERN == KERNEL_EXP ? __dsqrt_rn(row[j]) : row[j];
       double a = 0.0;
       if (j != i) {
-        if (t < 700.0) {
+        if (__fmul_rn(d2f_trunc(x), rcpf) < 680.f) {          // t = x rcp well below 690
           int k;
-          const ff q = ff_exp_neg_scaled(t, k);
-          a = __longlong_as_double(__double_as_longlong(f2d_bits(q.hi) + f2d_bits(q.lo)) - ((long long)k << 52));
+          const ff q = ff_exp_neg_prod(x, rcp, k);
+          a = ff_scaled_to_double(q, k);
           if (k <= 100) {
             const float sc = __int_as_float((127 - k) << 23);   // 2^-k
             const ff ts = two_sum(acc.hi, __fmul_rn(q.hi, sc));
@@ -328,7 +331,7 @@ __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double
             acc.lo = __fadd_rn(acc.lo, __fadd_rn(ts.lo, __fmul_rn(q.lo, sc)));
           }
         } else {
-          a = exp(-t);
+          a = exp(-(x * rcp));
         }
       }
       row[j] = a;
@@ -568,7 +571,8 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
       k_row_norms<<<rows / 8, 256, 0, s>>>(X, n, T, rows, static_cast<long long*>(wsNo));
       CDL_TRY(L.done());
     }
-    CDL_TRY(dist_tc(ctx, wsPl, static_cast<const long long*>(wsNo), n, rows, tp, A, &st->flags));
+    CDL_TRY(dist_tc(ctx, wsPl, static_cast<const long long*>(wsNo), n, rows, tp, A, &st->flags,
+                    0.5 * (double)n * (double)(n - 1) * T));
   }
   {
     Launch L(ctx, CDL_KC_DISTANCE, 0);

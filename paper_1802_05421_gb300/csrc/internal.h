@@ -179,9 +179,10 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
 // Exact squared distances of grid inputs on the tensor cores: planes = three
 // bf16 digit planes (rows x tp each, rows = n rounded up to 128, tp = T
 // rounded up to 64, zero padded), norms = |a_i|^2 (rows, int64); writes the
-// n x n float64 matrix A unless *offgrid & 1.
+// n x n float64 matrix A unless *offgrid & 1; terms = the algorithmic work
+// recorded for the launch.
 int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
-            const int* offgrid);
+            const int* offgrid, double terms);
 // Pair partials of the CAD scores with the Gram on the tensor cores: uplanes,
 // vplanes = six bf16 slice planes each (rows x k2p, zero padded) of u / c and
 // v / c; dint = d_i in units of c^2 2^-48; oscale = c^2 2^-48 (device);

@@ -316,19 +316,28 @@ __device__ __forceinline__ void tcs_ab(const double* __restrict__ Z1, const doub
   b = w + v;
 }
 
-// column maxima of |a| (cm[r]) and |b| (cm[k + r]) as float64 bits
+// column maxima of |a| (cm[r]) and |b| (cm[k + r]) as float64 bits: maxima of
+// a row chunk per block in shared memory, then one global atomic per column
+// and block (k <= 1024)
 __global__ void __launch_bounds__(256) k_tcs_colmax(const double* __restrict__ Z1, const double* __restrict__ Z2,
                                                      const double* __restrict__ vol1, const double* __restrict__ vol2,
                                                      int n, int k, unsigned long long* __restrict__ cm) {
+  __shared__ unsigned long long sm[2048];
+  for (int c = threadIdx.x; c < 2 * k; c += blockDim.x) sm[c] = 0ull;
+  __syncthreads();
   const double s1 = sqrt(*vol1), s2 = sqrt(*vol2);
-  const size_t nk = (size_t)n * k;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < nk; idx += (size_t)gridDim.x * blockDim.x) {
+  const int rows_per_block = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  for (size_t idx = (size_t)r0 * k + threadIdx.x; idx < (size_t)r1 * k; idx += blockDim.x) {
     double a, b;
     tcs_ab(Z1, Z2, s1, s2, idx, a, b);
     const int r = (int)(idx % k);
-    atomicMax(cm + r, (unsigned long long)__double_as_longlong(fabs(a)));
-    atomicMax(cm + k + r, (unsigned long long)__double_as_longlong(fabs(b)));
+    atomicMax(sm + r, (unsigned long long)__double_as_longlong(fabs(a)));
+    atomicMax(sm + k + r, (unsigned long long)__double_as_longlong(fabs(b)));
   }
+  __syncthreads();
+  for (int c = threadIdx.x; c < 2 * k; c += blockDim.x)
+    if (sm[c]) atomicMax(cm + c, sm[c]);
 }
 
 // g_r = 2^e_r with e_r = floor((E(max|a_r|) - E(max|b_r|)) / 2) (E: binary
@@ -1029,8 +1038,7 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
     CDL_CUDA_TRY(cudaMemsetAsync(cm, 0, 2 * (size_t)k * sizeof(unsigned long long), st));
     {
       Launch L(ctx, CDL_KC_MISC, 0);
-      k_tcs_colmax<<<(unsigned)std::min<size_t>((nk + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, st>>>(
-          Z1, Z2, vol1, vol2, n, k, cm);
+      k_tcs_colmax<<<(unsigned)std::min(n, ctx->sm_count * 4), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cm);
       CDL_TRY(L.done());
     }
     {

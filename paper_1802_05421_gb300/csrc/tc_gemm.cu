@@ -27,6 +27,7 @@
 #include <string>
 #include <vector>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace cdl {
@@ -1057,7 +1058,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // the int64 sum of squared differences exactly; it is written as float64
 // multiples of 2^-32 to (i, j) and, off the diagonal blocks, to (j, i).
 // Tiles are 128 rows x 64 columns of the upper block triangle; warp roles as
-// in k_tc_resid.
+// in k_tc_resid, with a ring of eight 64-column TMEM accumulators so that the
+// MMAs of a tile run ahead of its epilogue.
 constexpr int DS_SLICES = 3;
 constexpr int DS_N = 64;
 constexpr int DS_STAGES = 8;
@@ -1065,7 +1067,8 @@ constexpr int DS_A = 128 * 128;                  // 128 rows x 64 bf16
 constexpr int DS_B = DS_N * 128;                 // 64 rows x 64 bf16
 constexpr int DS_STAGE_BYTES = DS_A + DS_B;
 constexpr int DS_SMEM_BYTES = DS_STAGES * DS_STAGE_BYTES + 512 + 1024;
-constexpr int DS_TMEM_COLS = 2 * DS_N;           // two accumulator buffers
+constexpr int DS_NBUF = 8;                     // ring of TMEM accumulators
+constexpr int DS_TMEM_COLS = DS_NBUF * DS_N;
 constexpr int DS_CHUNK_KB = 4;                   // 256 samples per exact chunk
 
 struct DistMaps {
@@ -1117,14 +1120,14 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DS_STAGES * DS_STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * DS_STAGES + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * DS_STAGES + 7);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * DS_STAGES + 2 * DS_NBUF + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * DS_STAGES + 2 * DS_NBUF + 3);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (DS_STAGES + s); };
   auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * DS_STAGES + b); };
-  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * DS_STAGES + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * DS_STAGES + 4);
+  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * DS_STAGES + DS_NBUF + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * DS_STAGES + 2 * DS_NBUF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (p.kblocks + DS_CHUNK_KB - 1) / DS_CHUNK_KB;
 
@@ -1133,7 +1136,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < DS_NBUF; ++b) {
       mbar_init(pfull_bar(b), 1);
       mbar_init(pempty_bar(b), T8_EPI);
     }
@@ -1195,8 +1198,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         int ps[3], pt[3];
         const int np = ds_pairs(w, ps, pt);
         for (int c = 0; c < nchunks && ok; ++c, ++pc) {
-          const int b = pc & 1;
-          const uint32_t ph = (uint32_t)(pc >> 1);
+          const int b = pc % DS_NBUF;
+          const uint32_t ph = (uint32_t)(pc / DS_NBUF);
           if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
             ok = false;
             break;
@@ -1249,8 +1252,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       for (int w = 0; w <= 2 * (DS_SLICES - 1); ++w)
         for (int c = 0; c < nchunks; ++c, ++pc) {
           if (failed) continue;
-          const int b = pc & 1;
-          const uint32_t ph = (uint32_t)(pc >> 1);
+          const int b = pc % DS_NBUF;
+          const uint32_t ph = (uint32_t)(pc / DS_NBUF);
           if (!mbar_wait(pfull_bar(b), ph & 1, abort_flag, p.status)) {
             failed = true;
             continue;
@@ -1277,7 +1280,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       for (int e = 0; e < 16; ++e) {
         const int col = col0 + e;
         if (col < p.n) {
-          const double d2 = (double)(ni + p.norms[col] - 2 * g[e]) * 0x1p-32;
+          // d2 >= 0 exactly; integer-only conversion (float64 is the scarce pipe)
+          const double d2 = u64_to_double_rn((unsigned long long)(ni + p.norms[col] - 2 * g[e]), -32);
           arow[col] = d2;
           if (mirror) p.A[(size_t)col * p.n + row] = d2;
         }
@@ -1314,7 +1318,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // each 64 x 64 sub-block writes its row sums to contrib[partner block][i]
 // and column sums to contrib[row block][j] (row plus column sums on the
 // diagonal), the slots of the 64-node block layout of k_score_reduce, in
-// units of c^2 2^-48 times oscale. Warp roles as in k_tc_resid.
+// units of c^2 2^-48 times oscale. Warp roles as in k_tc_resid, with a ring
+// of eight 64-column TMEM accumulators.
 constexpr int SC_SLICES = 6;
 constexpr int SC_N = 64;
 constexpr int SC_STAGES = 7;
@@ -1323,7 +1328,8 @@ constexpr int SC_B = SC_N * 128;                 // 64 rows x 64 bf16
 constexpr int SC_STAGE_BYTES = SC_A + SC_B;
 constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N;
 constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + SC_EPI_DOUBLES * 8 + 1024;
-constexpr int SC_TMEM_COLS = 2 * SC_N;
+constexpr int SC_NBUF = 8;                     // ring of TMEM accumulators
+constexpr int SC_TMEM_COLS = SC_NBUF * SC_N;
 constexpr int SC_CHUNK_KB = 2;                   // 128 K per exact chunk
 
 struct ScoreMaps {
@@ -1360,15 +1366,15 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SC_STAGES * SC_STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SC_STAGES + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * SC_STAGES + 7);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SC_STAGES + 2 * SC_NBUF + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * SC_STAGES + 2 * SC_NBUF + 3);
   double* epi = reinterpret_cast<double*>(smem + SC_STAGES * SC_STAGE_BYTES + 512);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (SC_STAGES + s); };
   auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * SC_STAGES + b); };
-  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * SC_STAGES + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * SC_STAGES + 4);
+  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * SC_STAGES + SC_NBUF + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * SC_STAGES + 2 * SC_NBUF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (p.kblocks + SC_CHUNK_KB - 1) / SC_CHUNK_KB;
 
@@ -1377,7 +1383,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < SC_NBUF; ++b) {
       mbar_init(pfull_bar(b), 1);
       mbar_init(pempty_bar(b), T8_EPI);
     }
@@ -1439,8 +1445,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         int ps[SC_SLICES], pt[SC_SLICES];
         const int np = sc_pairs(w, ps, pt);
         for (int c = 0; c < nchunks && ok; ++c, ++pc) {
-          const int b = pc & 1;
-          const uint32_t ph = (uint32_t)(pc >> 1);
+          const int b = pc % SC_NBUF;
+          const uint32_t ph = (uint32_t)(pc / SC_NBUF);
           if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
             ok = false;
             break;
@@ -1491,6 +1497,17 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
       int I, J;
       dist_tile(t, p.nb128, p.nb64, I, J);
+      {
+        // bring this thread's A1 and A2 row segments into L2 while the MMAs run
+        const int prow = I * 128 + q * 32 + lane, pc0 = J * SC_N + part * 16;
+        if (prow < p.n && pc0 < p.n) {
+          const size_t o0 = (size_t)prow * p.n + pc0, o1 = o0 + min(15, p.n - 1 - pc0);
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o0));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o0));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o1));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o1));
+        }
+      }
       long long m[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) m[e] = 0;
@@ -1501,8 +1518,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         for (int e = 0; e < 16; ++e) acc[e] = 0;
         for (int c = 0; c < nchunks; ++c, ++pc) {
           if (failed) continue;
-          const int b = pc & 1;
-          const uint32_t ph = (uint32_t)(pc >> 1);
+          const int b = pc % SC_NBUF;
+          const uint32_t ph = (uint32_t)(pc / SC_NBUF);
           if (!mbar_wait(pfull_bar(b), ph & 1, abort_flag, p.status)) {
             failed = true;
             continue;
@@ -1523,56 +1540,58 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         for (int e = 0; e < 16; ++e)
           m[e] += sh >= 0 ? (long long)acc[e] * (1LL << sh) : ((long long)acc[e] + (1LL << (-sh - 1))) >> (-sh);
       }
-      // edge scores of the thread's 16 pairs (row i, columns col0 ..)
+      // edge scores of the thread's 16 pairs (row i, columns col0 ..): one
+      // float64 subtraction for Delta A, the rest in float-float on the float32
+      // pipes (float64 is the scarce pipe)
       const int rl = q * 32 + lane;                      // row within the tile
       const int row = I * 128 + rl;
       const int col0 = J * SC_N + part * 16;
       const int br = 2 * I + (q >> 1);                   // 64-row block of the row
       const bool rowok = !failed && row < p.n && br <= J;
       const long long di = rowok ? p.dint[row] : 0;
-      double ev[16];
-      double rs = 0.0;
+      ff ev[16];
+      ff rs = {0.f, 0.f};
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int col = col0 + e;
-        double x = 0.0;
+        ff x = {0.f, 0.f};
         if (rowok && col < p.n && (br < J || row < col)) {
-          long long dc = di + p.dint[col] - m[e];
-          dc = dc < 0 ? -dc : dc;
+          const long long dc = di + p.dint[col] - m[e];
+          const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
           const size_t o = (size_t)row * p.n + col;
-          x = fabs(p.A1[o] - p.A2[o]) * (double)dc;
+          x = ff_mul(split_nonneg(fabs(p.A1[o] - p.A2[o])), ff_from_u64(adc));
         }
         ev[e] = x;
-        rs += x;
+        rs = ff_add(rs, x);
       }
-      rowpart[rl * 4 + part] = rs;
+      rowpart[rl * 4 + part] = (double)rs.hi + (double)rs.lo;
       // column sums over the warp's 32 rows: reduce-scatter, lane pairs end with one column each
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const bool hi = lane & 16;
-        const double keep = hi ? ev[e + 8] : ev[e], send = hi ? ev[e] : ev[e + 8];
-        ev[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        const ff keep = hi ? ev[e + 8] : ev[e], send = hi ? ev[e] : ev[e + 8];
+        ev[e] = ff_add(keep, {__shfl_xor_sync(0xffffffffu, send.hi, 16), __shfl_xor_sync(0xffffffffu, send.lo, 16)});
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const bool hi = lane & 8;
-        const double keep = hi ? ev[e + 4] : ev[e], send = hi ? ev[e] : ev[e + 4];
-        ev[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        const ff keep = hi ? ev[e + 4] : ev[e], send = hi ? ev[e] : ev[e + 4];
+        ev[e] = ff_add(keep, {__shfl_xor_sync(0xffffffffu, send.hi, 8), __shfl_xor_sync(0xffffffffu, send.lo, 8)});
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const bool hi = lane & 4;
-        const double keep = hi ? ev[e + 2] : ev[e], send = hi ? ev[e] : ev[e + 2];
-        ev[e] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        const ff keep = hi ? ev[e + 2] : ev[e], send = hi ? ev[e] : ev[e + 2];
+        ev[e] = ff_add(keep, {__shfl_xor_sync(0xffffffffu, send.hi, 4), __shfl_xor_sync(0xffffffffu, send.lo, 4)});
       }
       {
         const bool hi = lane & 2;
-        const double keep = hi ? ev[1] : ev[0], send = hi ? ev[0] : ev[1];
-        ev[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        const ff keep = hi ? ev[1] : ev[0], send = hi ? ev[0] : ev[1];
+        ev[0] = ff_add(keep, {__shfl_xor_sync(0xffffffffu, send.hi, 2), __shfl_xor_sync(0xffffffffu, send.lo, 2)});
       }
-      ev[0] += __shfl_xor_sync(0xffffffffu, ev[0], 1);
+      ev[0] = ff_add(ev[0], {__shfl_xor_sync(0xffffffffu, ev[0].hi, 1), __shfl_xor_sync(0xffffffffu, ev[0].lo, 1)});
       const int cidx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-      if ((lane & 1) == 0) colpart[q * SC_N + part * 16 + cidx] = ev[0];
+      if ((lane & 1) == 0) colpart[q * SC_N + part * 16 + cidx] = (double)ev[0].hi + (double)ev[0].lo;
       asm volatile("bar.sync 1, 512;" ::: "memory");
       if (et < 128 && !failed) {
         // row partial of tile row et over the 64 columns
@@ -1965,7 +1984,7 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
 }
 
 int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
-            const int* offgrid) {
+            const int* offgrid, double terms) {
   if (rows % 128 || tp % 64 || rows < n || tp < 64) return CDL_ERR_INVALID_ARG;
   DistMaps maps;
   std::memset(&maps, 0, sizeof(maps));
@@ -1994,8 +2013,7 @@ int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int
     attr = true;
   }
   const int grid = (int)std::min<long long>(tiles, ctx->sm_count);
-  // 9 slice products over the computed tiles (upper block triangle)
-  Launch L(ctx, CDL_KC_DISTANCE, 2.0 * 9 * (double)tiles * 128 * DS_N * tp);
+  Launch L(ctx, CDL_KC_DISTANCE, terms);   // algorithmic work: n (n - 1) T / 2 squared differences
   k_tc_dist<<<grid, T8_THREADS, DS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
 }

@@ -419,7 +419,7 @@ def test_invalid_arguments(G):
     assert cdl.cdl_project(G.h, A, cdl.CDL_F64, n, 0, 1, A) == cdl.CDL_ERR_INVALID_ARG
     assert cdl.cdl_project(G.h, A, cdl.CDL_F64, n, 1025, 1, A) == cdl.CDL_ERR_INVALID_ARG
     F = torch.zeros(n, dtype=torch.float64, device="cuda")
-    assert cdl.cdl_cad_score(G.h, A, A, cdl.CDL_F64, A, A, s, s, n, 4, cdl.CDL_BF16, 2, F, F) == \
+    assert cdl.cdl_cad_score(G.h, A, A, cdl.CDL_F64, A, A, s, s, n, 4, cdl.CDL_FP8E4M3, 2, F, F) == \
         cdl.CDL_ERR_INVALID_ARG
     assert cdl.cdl_cad_score(G.h, A, A, cdl.CDL_F64, A, A, s, s, n, 4, cdl.CDL_F64, n + 1, F, F) == \
         cdl.CDL_ERR_INVALID_ARG
@@ -470,7 +470,8 @@ def test_launch_counter_and_timing(G):
     st, n = cdl.cdl_ctx_launch_count(G.h)
     assert st == 0 and n >= 10
     st, ms, launches, work = cdl.cdl_ctx_timing(G.h, cdl.CDL_KC_DISTANCE)
-    assert st == 0 and launches == 3 and ms > 0 and work == 0.5 * 256 * 255 * 8
+    # fixed-point check, digit planes, norms, tensor-core Gram, float64 fallback (returns at once)
+    assert st == 0 and launches == 5 and ms > 0 and work == 0.5 * 256 * 255 * 8
     cdl.cdl_ctx_set_timing(G.h, False)
 
 
