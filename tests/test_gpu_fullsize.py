@@ -1,6 +1,7 @@
 """Full-size parity on the n = 32768 field pair the benchmark times (bf16
-chain, d = 14, k = 128, refinement to 1e-10, float32 scores), called through
-the same C entry points and kernels as cdl_caddelag_pair.
+chain, d = 14, k = 128, refinement to 1e-10, tensor-core (bf16 slice) scores,
+and the float32-pipe scores beside them), called through the same C entry
+points and kernels as cdl_caddelag_pair.
 
 The oracle computes everything it compares from the node series alone:
 exact squared distances (exact-grid Gram, bit-equal to the plain definition
@@ -50,14 +51,17 @@ def test_field_pair_n32768_full_size():
             gpu.append(dict(A=A, D=D.cpu().numpy(), vol=float(vol.item()), sig=float(sig.item()),
                             Y=Y.cpu().numpy(), Z=Z.cpu().numpy(), Arows=A[rows].cpu().numpy(),
                             rel=st.rel_res))
-        F, top = G.score(gpu[0]["A"], gpu[1]["A"], torch.from_numpy(gpu[0]["Z"]).cuda(),
-                         torch.from_numpy(gpu[1]["Z"]).cuda(),
-                         torch.tensor([gpu[0]["vol"]], dtype=torch.float64, device="cuda"),
-                         torch.tensor([gpu[1]["vol"]], dtype=torch.float64, device="cuda"), TOPK, cdl.CDL_F32)
+        args = (gpu[0]["A"], gpu[1]["A"], torch.from_numpy(gpu[0]["Z"]).cuda(), torch.from_numpy(gpu[1]["Z"]).cuda(),
+                torch.tensor([gpu[0]["vol"]], dtype=torch.float64, device="cuda"),
+                torch.tensor([gpu[1]["vol"]], dtype=torch.float64, device="cuda"), TOPK)
+        F, top = G.score(*args, cdl.CDL_BF16)
         F = F.cpu().numpy()
         top = top.cpu().numpy()
+        F32, top32 = G.score(*args, cdl.CDL_F32)
+        F32 = F32.cpu().numpy()
+        assert np.max(np.abs(F32 - F) / F) <= 1e-9 and list(top32.cpu().numpy()) == list(top)
         # the pair driver runs the same kernels: identical scores
-        Fp, topp, s1, s2 = G.pair(wl.X[0], wl.X[1], K, DCH, cdl.CDL_BF16, cdl.CDL_F32, SEED, TOPK,
+        Fp, topp, s1, s2 = G.pair(wl.X[0], wl.X[1], K, DCH, cdl.CDL_BF16, cdl.CDL_BF16, SEED, TOPK,
                                   max_iter=40, rel_tol=TOL)
         assert np.array_equal(Fp, F) and list(topp) == list(top)
         for g in gpu:
