@@ -75,9 +75,10 @@ void ooc_destroy(cdl_chain* ch) {
 void* ooc_write_begin(cdl_ctx* ctx, cdl_chain* ch, int i) {
   int s = slot_holding(ch, i);
   if (s < 0) s = victim(ch);
-  cudaStreamWaitEvent(ctx->stream, ch->ev_free[s], 0);   // old level saved / read
-  ch->slot_level[s] = i;
-  return ch->slot[s];
+  cudaStreamWaitEvent(ctx->stream, ch->ev_free[s], 0);    // old level saved / read
+  cudaStreamWaitEvent(ctx->stream, ch->ev_ready[s], 0);   // and no load into the slot still in flight
+  ch->slot_level[s] = i;                                  // (a prefetch may have started one, e.g. of
+  return ch->slot[s];                                     // level 0 of the previous graph's chain)
 }
 
 int ooc_write_end(cdl_ctx* ctx, cdl_chain* ch, int i) {
