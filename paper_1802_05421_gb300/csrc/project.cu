@@ -55,8 +55,8 @@ constexpr int MAX_RPB = 64;  // node rows per block
 // p2) values stay on their grid below 2^24 grid steps, so float32 adds them
 // exactly; p3 is small enough for plain float32 sums. The three partial sums
 // are flushed to float64 in Y every 4096 edges. Per term and projection row
-// this is one sign construction and three fused multiply-adds with +-1
-// (exact products).
+// this is one bit test and three predicated adds (the terms with a set sign
+// bit; the plain totals are kept once per row and combined at the flush).
 constexpr int RB = 16;       // projection rows per thread (half a Philox word)
 
 // Shared memory of a block: three piece arrays [rpb][JTP] floats, then (16-byte
@@ -93,19 +93,26 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
   const int i0 = bidx * rpb;
   const int i = i0 + rl;
   const bool active = rl < rpb && i < n;
+  // With s = 2 bit - 1, sum_j s x_j = 2 sum_{bit set} x_j - sum_j x_j: the
+  // a-accumulators take the terms whose sign bit is set (one predicated add per
+  // piece), t the plain totals (shared by all projection rows of the thread).
   float a1[RB], a2[RB], a3[RB];
+  float t1 = 0.f, t2 = 0.f, t3 = 0.f;
 #pragma unroll
   for (int b = 0; b < RB; ++b) a1[b] = a2[b] = a3[b] = 0.f;
   bool first = true;
   auto flush = [&]() {
     if (!active) return;
+    const double s1 = t1, s2 = t2, s3 = t3;
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
       const int r = w * 32 + shift + b;
-      const double v = ((double)a1[b] + (double)a2[b]) + (double)a3[b];
+      // exact in float64 for the two grid pieces
+      const double v = ((2.0 * (double)a1[b] - s1) + (2.0 * (double)a2[b] - s2)) + (2.0 * (double)a3[b] - s3);
       if (r < k) Y[(size_t)i * k + r] = first ? v : Y[(size_t)i * k + r] + v;
       a1[b] = a2[b] = a3[b] = 0.f;
     }
+    t1 = t2 = t3 = 0.f;
     first = false;
   };
   for (int j0 = jbeg; j0 < jend; j0 += JT) {
@@ -157,15 +164,19 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
       const int e = rl * JTP + jj;
       const float p1 = P1[e], p2 = P2[e], p3 = P3[e];
       const uint4 o = Wd[rl * WS + jj * nrb + rb];
-      const uint32_t bits = wi == 0 ? o.x : wi == 1 ? o.y : wi == 2 ? o.z : o.w;
-      const uint32_t nb = ~(bits >> shift);   // clear bit -> -1
+      const uint32_t bits = (wi == 0 ? o.x : wi == 1 ? o.y : wi == 2 ? o.z : o.w) >> shift;   // set bit -> +1
+      t1 = __fadd_rn(t1, p1);
+      t2 = __fadd_rn(t2, p2);
+      t3 = __fadd_rn(t3, p3);
 #pragma unroll
-      for (int b = 0; b < RB; ++b) {
-        const float sg = __uint_as_float(((nb << (31 - b)) & 0x80000000u) | 0x3f800000u);
-        a1[b] = __fmaf_rn(sg, p1, a1[b]);
-        a2[b] = __fmaf_rn(sg, p2, a2[b]);
-        a3[b] = __fmaf_rn(sg, p3, a3[b]);
-      }
+      for (int b = 0; b < RB; ++b)
+        asm("{\n\t.reg .pred q;\n\t"
+            "setp.ne.b32 q, %3, 0;\n\t"
+            "@q add.rn.f32 %0, %0, %4;\n\t"
+            "@q add.rn.f32 %1, %1, %5;\n\t"
+            "@q add.rn.f32 %2, %2, %6;\n\t}"
+            : "+f"(a1[b]), "+f"(a2[b]), "+f"(a3[b])
+            : "r"(bits & (1u << b)), "f"(p1), "f"(p2), "f"(p3));
     }
   }
   flush();
