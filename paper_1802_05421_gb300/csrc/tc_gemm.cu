@@ -1062,11 +1062,12 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // MMAs of a tile run ahead of its epilogue.
 constexpr int DS_SLICES = 3;
 constexpr int DS_N = 64;
-constexpr int DS_STAGES = 8;
+constexpr int DS_STAGES = 5;
 constexpr int DS_A = 128 * 128;                  // 128 rows x 64 bf16
 constexpr int DS_B = DS_N * 128;                 // 64 rows x 64 bf16
 constexpr int DS_STAGE_BYTES = DS_A + DS_B;
-constexpr int DS_SMEM_BYTES = DS_STAGES * DS_STAGE_BYTES + 512 + 1024;
+constexpr int EPI_STAGE_DOUBLES = 16 * 32 * 17;          // per epilogue warp: 32 rows x 16 columns, padded
+constexpr int DS_SMEM_BYTES = DS_STAGES * DS_STAGE_BYTES + 512 + EPI_STAGE_DOUBLES * 8 + 1024;
 constexpr int DS_NBUF = 8;                     // ring of TMEM accumulators
 constexpr int DS_TMEM_COLS = DS_NBUF * DS_N;
 constexpr int DS_CHUNK_KB = 4;                   // 256 samples per exact chunk
@@ -1120,6 +1121,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DS_STAGES * DS_STAGE_BYTES);
+  double* stage = reinterpret_cast<double*>(smem + DS_STAGES * DS_STAGE_BYTES + 512);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * DS_STAGES + 2 * DS_NBUF + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * DS_STAGES + 2 * DS_NBUF + 3);
   const uint32_t bar0 = smem_u32(bars);
@@ -1269,23 +1271,33 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           tc_fence_before();
           mbar_arrive(pempty_bar(b));
         }
-      if (failed) continue;
+      if (__any_sync(0xffffffffu, failed)) continue;
       const int row = I * 128 + q * 32 + lane;
-      if (row >= p.n) continue;
-      const long long ni = p.norms[row];
+      const bool rowok = row < p.n;
+      const long long ni = rowok ? p.norms[row] : 0;
       const int col0 = J * DS_N + part * 16;
       const bool mirror = J >= 2 * I + 2;                // off the diagonal 128-block
-      double* arow = p.A + (size_t)row * p.n;
+      double* stg = stage + (warp - 2) * (32 * 17);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int col = col0 + e;
-        if (col < p.n) {
+        double d2 = 0.0;
+        if (rowok && col < p.n) {
           // d2 >= 0 exactly; integer-only conversion (float64 is the scarce pipe)
-          const double d2 = u64_to_double_rn((unsigned long long)(ni + p.norms[col] - 2 * g[e]), -32);
-          arow[col] = d2;
-          if (mirror) p.A[(size_t)col * p.n + row] = d2;
+          d2 = u64_to_double_rn((unsigned long long)(ni + p.norms[col] - 2 * g[e]), -32);
+          if (mirror) p.A[(size_t)col * p.n + row] = d2;   // lanes write 32 consecutive entries
         }
+        stg[lane * 17 + e] = d2;
       }
+      __syncwarp();
+      // the warp's 32 x 16 block row-wise, two 128-byte row segments per store
+#pragma unroll 4
+      for (int it = 0; it < 16; ++it) {
+        const int rr = 2 * it + (lane >> 4), c = lane & 15;
+        const int grow = I * 128 + q * 32 + rr, gcol = col0 + c;
+        if (grow < p.n && gcol < p.n) p.A[(size_t)grow * p.n + gcol] = stg[rr * 17 + c];
+      }
+      __syncwarp();
     }
   }
 
@@ -1322,12 +1334,12 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // of eight 64-column TMEM accumulators.
 constexpr int SC_SLICES = 6;
 constexpr int SC_N = 64;
-constexpr int SC_STAGES = 7;
+constexpr int SC_STAGES = 5;
 constexpr int SC_A = 128 * 128;                  // 128 rows x 64 bf16
 constexpr int SC_B = SC_N * 128;                 // 64 rows x 64 bf16
 constexpr int SC_STAGE_BYTES = SC_A + SC_B;
 constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N;
-constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + SC_EPI_DOUBLES * 8 + 1024;
+constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + (SC_EPI_DOUBLES + EPI_STAGE_DOUBLES) * 8 + 1024;
 constexpr int SC_NBUF = 8;                     // ring of TMEM accumulators
 constexpr int SC_TMEM_COLS = SC_NBUF * SC_N;
 constexpr int SC_CHUNK_KB = 2;                   // 128 K per exact chunk
@@ -1369,6 +1381,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SC_STAGES + 2 * SC_NBUF + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * SC_STAGES + 2 * SC_NBUF + 3);
   double* epi = reinterpret_cast<double*>(smem + SC_STAGES * SC_STAGE_BYTES + 512);
+  double* stage = epi + SC_EPI_DOUBLES;
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (SC_STAGES + s); };
@@ -1497,16 +1510,24 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
       int I, J;
       dist_tile(t, p.nb128, p.nb64, I, J);
-      {
-        // bring this thread's A1 and A2 row segments into L2 while the MMAs run
-        const int prow = I * 128 + q * 32 + lane, pc0 = J * SC_N + part * 16;
-        if (prow < p.n && pc0 < p.n) {
-          const size_t o0 = (size_t)prow * p.n + pc0, o1 = o0 + min(15, p.n - 1 - pc0);
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o0));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o0));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o1));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o1));
+      double* stg = stage + (warp - 2) * (32 * 17);
+      if (!__any_sync(0xffffffffu, failed)) {
+        // |A1 - A2| of the warp's 32 x 16 block, read in 128-byte row segments (eight
+        // lanes per row, two entries each) while the MMAs run, kept in shared memory
+        const int rs = lane >> 3, c2 = (lane & 7) * 2, pc0 = J * SC_N + part * 16 + c2;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int rr = it * 4 + rs, grow = I * 128 + q * 32 + rr;
+          double d0 = 0.0, d1 = 0.0;
+          if (grow < p.n) {
+            const size_t o = (size_t)grow * p.n + pc0;
+            if (pc0 < p.n) d0 = fabs(p.A1[o] - p.A2[o]);
+            if (pc0 + 1 < p.n) d1 = fabs(p.A1[o + 1] - p.A2[o + 1]);
+          }
+          stg[rr * 17 + c2] = d0;
+          stg[rr * 17 + c2 + 1] = d1;
         }
+        __syncwarp();
       }
       long long m[16];
 #pragma unroll
@@ -1558,8 +1579,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         if (rowok && col < p.n && (br < J || row < col)) {
           const long long dc = di + p.dint[col] - m[e];
           const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
-          const size_t o = (size_t)row * p.n + col;
-          x = ff_mul(split_nonneg(fabs(p.A1[o] - p.A2[o])), ff_from_u64(adc));
+          x = ff_mul(split_nonneg(stg[lane * 17 + e]), ff_from_u64(adc));
         }
         ev[e] = x;
         rs = ff_add(rs, x);
