@@ -658,7 +658,11 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
     CDL_TRY(graph_build(ctx, Xs[g], n, T, o->sigma, As[g], Ds[g], sc + g, sc + 2 + g));
     CDL_TRY(cdl_chain_build(ctx, As[g], CDL_F64, Ds[g], sc + g, n, o->d, o->chain_dtype, o->chain_flags,
                             &ctx->pair_chain));
-    CDL_TRY(project(ctx, As[g], n, o->k, o->seed, static_cast<double*>(dY)));
+    // tensor chains hold the float64 bits of max |A| (found by their build): the
+    // projection reuses them instead of another pass over A
+    const cdl_chain* pc = ctx->pair_chain;
+    CDL_TRY(project(ctx, As[g], n, o->k, o->seed, static_cast<double*>(dY),
+                    pc->a_scale ? reinterpret_cast<const unsigned long long*>(pc->a_scale + 1) : nullptr));
     int st = chain_solve(ctx, ctx->pair_chain, As[g], static_cast<double*>(dY), o->k, &o->solve,
                          Zs[g], sts[g]);
     if (st != CDL_OK && st != CDL_ERR_NOT_CONVERGED) return st;

@@ -372,7 +372,10 @@ int cad_score_grouped(cdl_ctx* ctx, const ScoreJob* jobs, int G, int k, bool fp6
 int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
                 const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats);
 // project.cu
-int project(cdl_ctx* ctx, const double* A, int64_t n, int k, uint64_t seed, double* Y);
+// amax_bits (device, optional): the float64 bits of max |A| if already known
+// (nullptr: found by a pass over A).
+int project(cdl_ctx* ctx, const double* A, int64_t n, int k, uint64_t seed, double* Y,
+            const unsigned long long* amax_bits = nullptr);
 // score.cu
 int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1,
               const double* Z2, const double* vol1, const double* vol2, int64_t n, int k,

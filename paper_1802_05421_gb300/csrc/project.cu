@@ -281,7 +281,8 @@ __global__ void k_g_sub_mean(const uint32_t* __restrict__ tiles, const PGraph* _
 
 }  // namespace
 
-int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, double* Y) {
+int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, double* Y,
+            const unsigned long long* amax_bits) {
   const int n = (int)n64;
   const int W = (k + 31) / 32;
   const int rpb = std::max(1, std::min(MAX_RPB, 256 / (2 * W)));
@@ -299,9 +300,13 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
-  void* vmax;
-  CDL_TRY(ws_get(ctx, "project.amax", sizeof(unsigned long long), &vmax));
-  CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, static_cast<unsigned long long*>(vmax)));
+  const void* vmax = amax_bits;
+  if (!vmax) {
+    void* w;
+    CDL_TRY(ws_get(ctx, "project.amax", sizeof(unsigned long long), &w));
+    CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, static_cast<unsigned long long*>(w)));
+    vmax = w;
+  }
   double* out = Y;
   if (nsplit > 1) {
     void* vp;

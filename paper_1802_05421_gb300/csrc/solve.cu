@@ -792,8 +792,22 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   const int kblocks = np / 64;
   int splits;
   if (bf16) {
-    const int target = std::max(1, (4 * ctx->sm_count + np / 128 - 1) / (np / 128));
-    splits = largest_divisor_at_most(kblocks, target);
+    // split-K of the persistent apply (one CTA per SM over np / 128 row tiles x
+    // splits): the fewest splits (a divisor of the K blocks, at most 16) whose
+    // tiles fill the last round of CTAs to 95 %, else the best filling
+    const int mb = np / 128, sm = ctx->sm_count;
+    splits = 1;
+    double best = 0.0;
+    for (int sp = 1; sp <= 16 && sp <= kblocks; ++sp) {
+      if (kblocks % sp) continue;
+      const long long tl = (long long)mb * sp;
+      const double fill = (double)tl / (double)(((tl + sm - 1) / sm) * sm);
+      if (fill > best + 1e-9) {
+        best = fill;
+        splits = sp;
+      }
+      if (fill >= 0.95) break;
+    }
   } else {
     const int bm = ch->dtype == CDL_F32 ? 128 : 64;
     const int cols = (kp + 63) / 64;
