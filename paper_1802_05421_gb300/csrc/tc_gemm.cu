@@ -1058,14 +1058,17 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // the int64 sum of squared differences exactly; it is written as float64
 // multiples of 2^-32 to (i, j) and, off the diagonal blocks, to (j, i).
 // Tiles are 128 rows x 64 columns of the upper block triangle; warp roles as
-// in k_tc_resid, with a ring of eight 64-column TMEM accumulators so that the
-// MMAs of a tile run ahead of its epilogue.
+// in k_tc_resid. Each pipeline stage holds the three digit planes of both
+// sides for one K block (72 KB, loaded once), and the MMA issuer feeds all
+// nine slice products into the five weight accumulators of the K chunk, slots
+// of a ring of eight 64-column TMEM accumulators, so that the MMAs of a tile
+// run ahead of its epilogue.
 constexpr int DS_SLICES = 3;
 constexpr int DS_N = 64;
-constexpr int DS_STAGES = 5;
-constexpr int DS_A = 128 * 128;                  // 128 rows x 64 bf16
-constexpr int DS_B = DS_N * 128;                 // 64 rows x 64 bf16
-constexpr int DS_STAGE_BYTES = DS_A + DS_B;
+constexpr int DS_STAGES = 2;
+constexpr int DS_A = 128 * 128;                  // one digit plane: 128 rows x 64 bf16
+constexpr int DS_B = DS_N * 128;                 // one digit plane: 64 rows x 64 bf16
+constexpr int DS_STAGE_BYTES = DS_SLICES * (DS_A + DS_B);   // all three planes of both sides
 constexpr int EPI_STAGE_DOUBLES = 16 * 32 * 17;          // per epilogue warp: 32 rows x 16 columns, padded
 constexpr int DS_SMEM_BYTES = DS_STAGES * DS_STAGE_BYTES + 512 + EPI_STAGE_DOUBLES * 8 + 1024;
 constexpr int DS_NBUF = 8;                     // ring of TMEM accumulators
@@ -1100,19 +1103,6 @@ __device__ __forceinline__ void dist_tile(int t, int nb128, int nb64, int& I, in
   }
   I = lo;
   J = 2 * lo + (int)(t - ((long long)lo * nb64 - (long long)lo * (lo - 1)));
-}
-
-__device__ __forceinline__ int ds_pairs(int w, int (&ps)[3], int (&pt)[3]) {
-  int c = 0;
-  for (int sa = 0; sa < DS_SLICES; ++sa) {
-    const int sb = w - sa;
-    if (sb >= 0 && sb < DS_SLICES) {
-      ps[c] = sa;
-      pt[c] = sb;
-      ++c;
-    }
-  }
-  return c;
 }
 
 __global__ void __launch_bounds__(T8_THREADS, 1)
@@ -1164,23 +1154,20 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
       int I, J;
       dist_tile(t, p.nb128, p.nb64, I, J);
-      for (int w = 0; w <= 2 * (DS_SLICES - 1) && ok; ++w) {
-        int ps[3], pt[3];
-        const int np = ds_pairs(w, ps, pt);
-        for (int c = 0; c < nchunks && ok; ++c)
-          for (int pr = 0; pr < np && ok; ++pr)
-            for (int kb = c * DS_CHUNK_KB; kb < min(p.kblocks, (c + 1) * DS_CHUNK_KB); ++kb, ++it) {
-              const int s = it % DS_STAGES;
-              const uint32_t r = (uint32_t)(it / DS_STAGES);
-              if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
-                ok = false;
-                break;
-              }
-              const uint32_t a_dst = smem_u32(smem + s * DS_STAGE_BYTES);
-              mbar_expect_tx(full_bar(s), DS_A + DS_B);
-              tma_load_2d(a_dst, &maps.a[ps[pr]], kb * 64, I * 128, full_bar(s));
-              tma_load_2d(a_dst + DS_A, &maps.b[pt[pr]], kb * 64, J * DS_N, full_bar(s));
-            }
+      // one stage per K block: the three digit planes of the row block and of the column block
+      for (int kb = 0; kb < p.kblocks && ok; ++kb, ++it) {
+        const int s = it % DS_STAGES;
+        const uint32_t r = (uint32_t)(it / DS_STAGES);
+        if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const uint32_t dst = smem_u32(smem + s * DS_STAGE_BYTES);
+        mbar_expect_tx(full_bar(s), DS_STAGE_BYTES);
+        for (int pl = 0; pl < DS_SLICES; ++pl) {
+          tma_load_2d(dst + pl * DS_A, &maps.a[pl], kb * 64, I * 128, full_bar(s));
+          tma_load_2d(dst + DS_SLICES * DS_A + pl * DS_B, &maps.b[pl], kb * 64, J * DS_N, full_bar(s));
+        }
       }
     }
     if (!ok) {
@@ -1192,45 +1179,47 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------ MMA issuer: one (weight, chunk) per TMEM buffer
+    // ------------------------------------------------ MMA issuer: per K chunk, the five weight
+    // accumulators (ring slots pc .. pc + 4) take all nine slice products of each K block
+    constexpr int NW = 2 * DS_SLICES - 1;
     int it = 0, pc = 0;
     bool ok = true, issued = false;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
-      for (int w = 0; w <= 2 * (DS_SLICES - 1) && ok; ++w) {
-        int ps[3], pt[3];
-        const int np = ds_pairs(w, ps, pt);
-        for (int c = 0; c < nchunks && ok; ++c, ++pc) {
-          const int b = pc % DS_NBUF;
-          const uint32_t ph = (uint32_t)(pc / DS_NBUF);
-          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
+      for (int c = 0; c < nchunks && ok; ++c, pc += NW) {
+        for (int w = 0; w < NW && ok; ++w) {
+          const int b = (pc + w) % DS_NBUF;
+          const uint32_t ph = (uint32_t)((pc + w) / DS_NBUF);
+          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) ok = false;
+        }
+        if (!ok) break;
+        tc_fence_after();
+        for (int kb = c * DS_CHUNK_KB; kb < min(p.kblocks, (c + 1) * DS_CHUNK_KB) && ok; ++kb, ++it) {
+          const int s = it % DS_STAGES;
+          if (!mbar_wait(full_bar(s), (uint32_t)(it / DS_STAGES) & 1, abort_flag, p.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(b * DS_N);
-          bool first = true;
-          for (int pr = 0; pr < np && ok; ++pr)
-            for (int kb = c * DS_CHUNK_KB; kb < min(p.kblocks, (c + 1) * DS_CHUNK_KB); ++kb, ++it) {
-              const int s = it % DS_STAGES;
-              if (!mbar_wait(full_bar(s), (uint32_t)(it / DS_STAGES) & 1, abort_flag, p.status)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t a_addr = smem_u32(smem + s * DS_STAGE_BYTES);
-              const uint64_t adesc = smem_desc(a_addr);
-              const uint64_t bdesc = smem_desc(a_addr + DS_A);
+          const uint32_t base = smem_u32(smem + s * DS_STAGE_BYTES);
+          const bool first_kb = kb == c * DS_CHUNK_KB;
+          for (int sa = 0; sa < DS_SLICES; ++sa)
+            for (int sb = 0; sb < DS_SLICES; ++sb) {
+              const int w = sa + sb;
+              const uint32_t d_tmem = tmem_base + (uint32_t)(((pc + w) % DS_NBUF) * DS_N);
+              // the first product of a weight in the chunk starts its accumulator
+              const bool first = first_kb && sa == (w < DS_SLICES ? 0 : w - (DS_SLICES - 1));
+              const uint64_t adesc = smem_desc(base + sa * DS_A);
+              const uint64_t bdesc = smem_desc(base + DS_SLICES * DS_A + sb * DS_B);
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, first ? 0u : 1u);
-                first = false;
-              }
-              issued = true;
-              mma_commit(empty_bar(s));
+              for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc,
+                         (first && kk == 0) ? 0u : 1u);
             }
-          if (!ok) break;
-          mma_commit(pfull_bar(b));
+          issued = true;
+          mma_commit(empty_bar(s));
         }
+        if (!ok) break;
+        for (int w = 0; w < NW; ++w) mma_commit(pfull_bar((pc + w) % DS_NBUF));
       }
     if (!ok && issued) {
       mma_commit(drain_bar);
@@ -1251,8 +1240,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       long long g[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) g[e] = 0;
-      for (int w = 0; w <= 2 * (DS_SLICES - 1); ++w)
-        for (int c = 0; c < nchunks; ++c, ++pc) {
+      for (int c = 0; c < nchunks; ++c)
+        for (int w = 0; w <= 2 * (DS_SLICES - 1); ++w, ++pc) {
           if (failed) continue;
           const int b = pc % DS_NBUF;
           const uint32_t ph = (uint32_t)(pc / DS_NBUF);
