@@ -1311,8 +1311,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // digit at most 256 in magnitude, the others 128). The slice pairs of one
 // weight w = s + t (w = 2 .. 7, 21 pairs) summed over a K-chunk of 128 stay
 // within 2^24 grid steps, so each TMEM buffer holds an exact integer; the
-// epilogue adds the chunks in int32 and the weights, shifted to the common
-// unit c^2 2^-48, in int64. With d_i in the same unit, Delta c_ij is formed
+// epilogue adds each chunk, shifted to the common unit c^2 2^-48, in int64.
+// Per K block two pipeline stages (u slices 1-3, then 4-6, each with all six
+// v slices) feed the six live weight accumulators of the chunk. With d_i in the same unit, Delta c_ij is formed
 // in int64 (no cancellation error beyond the slicing's 2^-49 of |a| |b|),
 // and E_ij = |A1_ij - A2_ij| |Delta c_ij| and its row and column sums are
 // float64. Tiles are 128 x 64 of the upper block triangle (pairs i < j only);
@@ -1323,12 +1324,13 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // of eight 64-column TMEM accumulators.
 constexpr int SC_SLICES = 6;
 constexpr int SC_N = 64;
-constexpr int SC_STAGES = 5;
-constexpr int SC_A = 128 * 128;                  // 128 rows x 64 bf16
-constexpr int SC_B = SC_N * 128;                 // 64 rows x 64 bf16
-constexpr int SC_STAGE_BYTES = SC_A + SC_B;
+constexpr int SC_STAGES = 2;
+constexpr int SC_A = 128 * 128;                  // one slice plane: 128 rows x 64 bf16
+constexpr int SC_B = SC_N * 128;                 // one slice plane: 64 rows x 64 bf16
+constexpr int SC_HALF = SC_SLICES / 2;           // u slices per stage (two stages per K block)
+constexpr int SC_STAGE_BYTES = SC_HALF * SC_A + SC_SLICES * SC_B;   // 3 u planes + all 6 v planes
 constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N;
-constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + (SC_EPI_DOUBLES + EPI_STAGE_DOUBLES) * 8 + 1024;
+constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + SC_EPI_DOUBLES * 8 + 1024;
 constexpr int SC_NBUF = 8;                     // ring of TMEM accumulators
 constexpr int SC_TMEM_COLS = SC_NBUF * SC_N;
 constexpr int SC_CHUNK_KB = 2;                   // 128 K per exact chunk
@@ -1370,7 +1372,6 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SC_STAGES + 2 * SC_NBUF + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * SC_STAGES + 2 * SC_NBUF + 3);
   double* epi = reinterpret_cast<double*>(smem + SC_STAGES * SC_STAGE_BYTES + 512);
-  double* stage = epi + SC_EPI_DOUBLES;
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (SC_STAGES + s); };
@@ -1405,30 +1406,28 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ------------------------------------------------ TMA producer
+    // ------------------------------------------------ TMA producer: per K block two stages, u slices
+    // 1-3 then 4-6, each with all six v slices
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
       int I, J;
       dist_tile(t, p.nb128, p.nb64, I, J);
-      for (int w = 2; w <= SC_SLICES + 1 && ok; ++w) {
-        int ps[SC_SLICES], pt[SC_SLICES];
-        const int np = sc_pairs(w, ps, pt);
-        for (int c = 0; c < nchunks && ok; ++c)
-          for (int pr = 0; pr < np && ok; ++pr)
-            for (int kb = c * SC_CHUNK_KB; kb < min(p.kblocks, (c + 1) * SC_CHUNK_KB); ++kb, ++it) {
-              const int s = it % SC_STAGES;
-              const uint32_t r = (uint32_t)(it / SC_STAGES);
-              if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
-                ok = false;
-                break;
-              }
-              const uint32_t a_dst = smem_u32(smem + s * SC_STAGE_BYTES);
-              mbar_expect_tx(full_bar(s), SC_A + SC_B);
-              tma_load_2d(a_dst, &maps.u[ps[pr]], kb * 64, I * 128, full_bar(s));
-              tma_load_2d(a_dst + SC_A, &maps.v[pt[pr]], kb * 64, J * SC_N, full_bar(s));
-            }
-      }
+      for (int kb = 0; kb < p.kblocks && ok; ++kb)
+        for (int h = 0; h < 2 && ok; ++h, ++it) {
+          const int s = it % SC_STAGES;
+          const uint32_t r = (uint32_t)(it / SC_STAGES);
+          if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = smem_u32(smem + s * SC_STAGE_BYTES);
+          mbar_expect_tx(full_bar(s), SC_STAGE_BYTES);
+          for (int pl = 0; pl < SC_HALF; ++pl)
+            tma_load_2d(dst + pl * SC_A, &maps.u[h * SC_HALF + pl], kb * 64, I * 128, full_bar(s));
+          for (int pl = 0; pl < SC_SLICES; ++pl)
+            tma_load_2d(dst + SC_HALF * SC_A + pl * SC_B, &maps.v[pl], kb * 64, J * SC_N, full_bar(s));
+        }
     }
     if (!ok) {
       for (int j = (it > SC_STAGES ? it - SC_STAGES : 0); j < it; ++j) {
@@ -1439,45 +1438,50 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------ MMA issuer: one (weight, chunk) per TMEM buffer
+    // ------------------------------------------------ MMA issuer: per K chunk, the six weight
+    // accumulators w = 2 .. 7 (ring slots pc .. pc + 5) take the 21 slice products of each K block
+    constexpr int NW = SC_SLICES;                        // weights 2 .. SC_SLICES + 1
     int it = 0, pc = 0;
     bool ok = true, issued = false;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
-      for (int w = 2; w <= SC_SLICES + 1 && ok; ++w) {
-        int ps[SC_SLICES], pt[SC_SLICES];
-        const int np = sc_pairs(w, ps, pt);
-        for (int c = 0; c < nchunks && ok; ++c, ++pc) {
-          const int b = pc % SC_NBUF;
-          const uint32_t ph = (uint32_t)(pc / SC_NBUF);
-          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(b * SC_N);
-          bool first = true;
-          for (int pr = 0; pr < np && ok; ++pr)
-            for (int kb = c * SC_CHUNK_KB; kb < min(p.kblocks, (c + 1) * SC_CHUNK_KB); ++kb, ++it) {
-              const int s = it % SC_STAGES;
-              if (!mbar_wait(full_bar(s), (uint32_t)(it / SC_STAGES) & 1, abort_flag, p.status)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t a_addr = smem_u32(smem + s * SC_STAGE_BYTES);
-              const uint64_t adesc = smem_desc(a_addr);
-              const uint64_t bdesc = smem_desc(a_addr + SC_A);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, first ? 0u : 1u);
-                first = false;
-              }
-              issued = true;
-              mma_commit(empty_bar(s));
-            }
-          if (!ok) break;
-          mma_commit(pfull_bar(b));
+      for (int c = 0; c < nchunks && ok; ++c, pc += NW) {
+        for (int w = 0; w < NW && ok; ++w) {
+          const int b = (pc + w) % SC_NBUF;
+          const uint32_t ph = (uint32_t)((pc + w) / SC_NBUF);
+          if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) ok = false;
         }
+        if (!ok) break;
+        tc_fence_after();
+        for (int kb = c * SC_CHUNK_KB; kb < min(p.kblocks, (c + 1) * SC_CHUNK_KB) && ok; ++kb)
+          for (int h = 0; h < 2 && ok; ++h, ++it) {
+            const int s = it % SC_STAGES;
+            if (!mbar_wait(full_bar(s), (uint32_t)(it / SC_STAGES) & 1, abort_flag, p.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * SC_STAGE_BYTES);
+            const bool first_kb = kb == c * SC_CHUNK_KB;
+            for (int pl = 0; pl < SC_HALF; ++pl) {
+              const int sa = h * SC_HALF + pl + 1;         // u slice, 1-based
+              for (int sb = 1; sa + sb <= SC_SLICES + 1; ++sb) {
+                const int w = sa + sb;                     // 2 .. 7
+                const uint32_t d_tmem = tmem_base + (uint32_t)(((pc + w - 2) % SC_NBUF) * SC_N);
+                // the first product of a weight in the chunk (u slice 1) starts its accumulator
+                const bool first = first_kb && sa == 1;
+                const uint64_t adesc = smem_desc(base + pl * SC_A);
+                const uint64_t bdesc = smem_desc(base + SC_HALF * SC_A + (sb - 1) * SC_B);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc,
+                           (first && kk == 0) ? 0u : 1u);
+              }
+            }
+            issued = true;
+            mma_commit(empty_bar(s));
+          }
+        if (!ok) break;
+        for (int w = 0; w < NW; ++w) mma_commit(pfull_bar((pc + w) % SC_NBUF));
       }
     if (!ok && issued) {
       mma_commit(drain_bar);
@@ -1499,34 +1503,25 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
       int I, J;
       dist_tile(t, p.nb128, p.nb64, I, J);
-      double* stg = stage + (warp - 2) * (32 * 17);
-      if (!__any_sync(0xffffffffu, failed)) {
-        // |A1 - A2| of the warp's 32 x 16 block, read in 128-byte row segments (eight
-        // lanes per row, two entries each) while the MMAs run, kept in shared memory
-        const int rs = lane >> 3, c2 = (lane & 7) * 2, pc0 = J * SC_N + part * 16 + c2;
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int rr = it * 4 + rs, grow = I * 128 + q * 32 + rr;
-          double d0 = 0.0, d1 = 0.0;
-          if (grow < p.n) {
-            const size_t o = (size_t)grow * p.n + pc0;
-            if (pc0 < p.n) d0 = fabs(p.A1[o] - p.A2[o]);
-            if (pc0 + 1 < p.n) d1 = fabs(p.A1[o + 1] - p.A2[o + 1]);
-          }
-          stg[rr * 17 + c2] = d0;
-          stg[rr * 17 + c2 + 1] = d1;
+      {
+        // bring this thread's A1 and A2 row segments into L2 while the MMAs run
+        const int prow = I * 128 + q * 32 + lane, pc0 = J * SC_N + part * 16;
+        if (prow < p.n && pc0 < p.n) {
+          const size_t o0 = (size_t)prow * p.n + pc0, o1 = o0 + min(15, p.n - 1 - pc0);
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o0));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o0));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o1));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o1));
         }
-        __syncwarp();
       }
       long long m[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) m[e] = 0;
-      for (int w = 2; w <= SC_SLICES + 1; ++w) {
-        const float up = __int_as_float((127 + 8 * w) << 23);   // 2^(8w)
-        int acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0;
-        for (int c = 0; c < nchunks; ++c, ++pc) {
+      // drains in the ring order of the MMA issuer: K chunk outer, weight inner; each
+      // exact chunk sum goes to the unit c^2 2^-48 (weight 7 rounded there: below
+      // one unit per chunk)
+      for (int c = 0; c < nchunks; ++c)
+        for (int w = 2; w <= SC_SLICES + 1; ++w, ++pc) {
           if (failed) continue;
           const int b = pc % SC_NBUF;
           const uint32_t ph = (uint32_t)(pc / SC_NBUF);
@@ -1535,21 +1530,21 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
             continue;
           }
           tc_fence_after();
+          const float up = __int_as_float((127 + 8 * w) << 23);   // 2^(8w)
+          const int sh = 48 - 8 * w;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float v[8];
             tmem_ld8(tmem_base + lane_off + (uint32_t)(b * SC_N + part * 16 + h * 8), v);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) acc[h * 8 + e] += __float2int_rn(v[e] * up);
+            for (int e = 0; e < 8; ++e) {
+              const long long x = __float2int_rn(v[e] * up);
+              m[h * 8 + e] += sh >= 0 ? x * (1LL << sh) : (x + (1LL << (-sh - 1))) >> (-sh);
+            }
           }
           tc_fence_before();
           mbar_arrive(pempty_bar(b));
         }
-        const int sh = 48 - 8 * w;                       // to the unit c^2 2^-48
-#pragma unroll
-        for (int e = 0; e < 16; ++e)
-          m[e] += sh >= 0 ? (long long)acc[e] * (1LL << sh) : ((long long)acc[e] + (1LL << (-sh - 1))) >> (-sh);
-      }
       // edge scores of the thread's 16 pairs (row i, columns col0 ..): one
       // float64 subtraction for Delta A, the rest in float-float on the float32
       // pipes (float64 is the scarce pipe)
@@ -1568,7 +1563,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         if (rowok && col < p.n && (br < J || row < col)) {
           const long long dc = di + p.dint[col] - m[e];
           const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
-          x = ff_mul(split_nonneg(stg[lane * 17 + e]), ff_from_u64(adc));
+          const size_t o = (size_t)row * p.n + col;
+          x = ff_mul(split_nonneg(fabs(p.A1[o] - p.A2[o])), ff_from_u64(adc));
         }
         ev[e] = x;
         rs = ff_add(rs, x);
