@@ -359,6 +359,77 @@ __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int
   for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row<KERN>(A, n, rcp, D, i);
 }
 
+// Kernel values over the upper block triangle of 64 x 64 tiles (A is
+// symmetric, so half the exponentials of the row-by-row pass): a block
+// evaluates tile (bi, bj), bj >= bi (a diagonal tile all of its entries),
+// writes it and, off the diagonal, its mirror through shared memory (both
+// writes coalesced), and leaves the tile's row and column sums of A
+// (float-float, the entries split with integer operations) in the slots of
+// the 64-node partner blocks: part[bj][i] for its rows, part[bi][j] for its
+// columns (rows only on the diagonal). D_i is the fixed-order sum of node i's
+// slots (k_part_sums). Same entry arithmetic as kernel_row.
+template <int KERN>
+__global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, int n, const double* __restrict__ sigma,
+                                                       double* __restrict__ part) {
+  __shared__ double tt[DT][DT + 1];                     // tt[c][r] = A(i0 + r, j0 + c)
+  const int nb = (n + DT - 1) / DT;
+  int bi, bj;
+  tri_index(blockIdx.x, nb, bi, bj);
+  const int i0 = bi * DT, j0 = bj * DT;
+  const double sg = *sigma;
+  const double rcp = KERN == KERNEL_EXP ? 1.0 / sg : 1.0 / (2.0 * (sg * sg));
+  const float rcpf = d2f_trunc(rcp);
+  const int c = threadIdx.x & (DT - 1), rg = threadIdx.x >> 6;
+#pragma unroll 4
+  for (int m = 0; m < DT / 4; ++m) {
+    const int r = rg + 4 * m, i = i0 + r, j = j0 + c;
+    double a = 0.0;
+    if (i < n && j < n) {
+      double* pa = A + (size_t)i * n + j;
+      if (i != j) {
+        const double x = KERN == KERNEL_EXP ? __dsqrt_rn(*pa) : *pa;
+        if (__fmul_rn(d2f_trunc(x), rcpf) < 680.f) {
+          int k;
+          const ff q = ff_exp_neg_prod(x, rcp, k);
+          a = ff_scaled_to_double(q, k);
+        } else {
+          a = exp(-(x * rcp));
+        }
+      }
+      *pa = a;
+    }
+    tt[c][r] = a;
+  }
+  __syncthreads();
+  if (bi != bj) {                                        // mirror: lanes write consecutive columns of row j
+#pragma unroll 4
+    for (int m = 0; m < DT / 4; ++m) {
+      const int cc = rg + 4 * m, r = threadIdx.x & (DT - 1);
+      const int j = j0 + cc, i = i0 + r;
+      if (j < n && i < n) A[(size_t)j * n + i] = tt[cc][r];
+    }
+  }
+  if (threadIdx.x < DT) {                                // row sums of the tile
+    const int r = threadIdx.x, i = i0 + r;
+    ff acc = {0.f, 0.f};
+    for (int cc = 0; cc < DT; ++cc) acc = ff_add(acc, split_nonneg(tt[cc][r]));
+    if (i < n) part[(size_t)bj * n + i] = (double)acc.hi + (double)acc.lo;
+  } else if (threadIdx.x < 2 * DT && bi != bj) {         // column sums (the mirror's row sums)
+    const int cc = threadIdx.x - DT, j = j0 + cc;
+    ff acc = {0.f, 0.f};
+    for (int r = 0; r < DT; ++r) acc = ff_add(acc, split_nonneg(tt[cc][r]));
+    if (j < n) part[(size_t)bi * n + j] = (double)acc.hi + (double)acc.lo;
+  }
+}
+
+__global__ void k_part_sums(const double* __restrict__ part, int nb, int n, double* __restrict__ D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(size_t)b * n + i];
+  D[i] = s;
+}
+
 // vol = sum_i D_i (single block, fixed order per thread then tree).
 __device__ __forceinline__ void block_sum_to(const double* __restrict__ v, int n, double* __restrict__ out) {
   __shared__ double red[32];
@@ -602,12 +673,19 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
     }
   }
   {
-    Launch L(ctx, CDL_KC_KERNEL, 16.0 * (double)n * n);
-    const int blocks = std::min(n, ctx->sm_count * 8);
-    if (kernel == KERNEL_EXP)
-      k_kernel_rows<KERNEL_EXP><<<blocks, 256, 0, s>>>(A, n, sigma_out, D);
-    else
-      k_kernel_rows<KERNEL_GAUSSIAN><<<blocks, 256, 0, s>>>(A, n, sigma_out, D);
+    void* wsPart;
+    CDL_TRY(ws_get(ctx, "graph.dpart", (size_t)nb * n * sizeof(double), &wsPart));
+    double* part = static_cast<double*>(wsPart);
+    {
+      Launch L(ctx, CDL_KC_KERNEL, 16.0 * (double)n * n);
+      if (kernel == KERNEL_EXP)
+        k_kernel_tiles<KERNEL_EXP><<<(unsigned)tiles, 256, 0, s>>>(A, n, sigma_out, part);
+      else
+        k_kernel_tiles<KERNEL_GAUSSIAN><<<(unsigned)tiles, 256, 0, s>>>(A, n, sigma_out, part);
+      CDL_TRY(L.done());
+    }
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_part_sums<<<(n + 255) / 256, 256, 0, s>>>(part, nb, n, D);
     CDL_TRY(L.done());
   }
   {
