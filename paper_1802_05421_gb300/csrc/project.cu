@@ -252,8 +252,18 @@ __device__ __forceinline__ void sub_mean(double* __restrict__ Y, int n, int k, c
   Y[idx] -= s / n;
 }
 
-__global__ void k_sub_mean(double* __restrict__ Y, int n, int k, const double* __restrict__ part, int nparts) {
-  sub_mean(Y, n, k, part, nparts, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
+// Column means once per column (the same ordered sums as sub_mean), then the subtraction.
+__global__ void k_col_mean(const double* __restrict__ part, int nparts, int n, int k, double* __restrict__ mean) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += part[(size_t)q * k + r];
+  mean[r] = s / n;
+}
+
+__global__ void k_sub_mean(double* __restrict__ Y, int n, int k, const double* __restrict__ mean) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx < (size_t)n * k) Y[idx] -= mean[idx % k];
 }
 
 // ---------------------------------------------------------------- batched form
@@ -329,15 +339,21 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
   }
   const int nparts = (n + 255) / 256;
   void* vpart;
-  CDL_TRY(ws_get(ctx, "project.colsum", (size_t)nparts * k * sizeof(double), &vpart));
+  CDL_TRY(ws_get(ctx, "project.colsum", (size_t)(nparts + 1) * k * sizeof(double), &vpart));
+  double* part = static_cast<double*>(vpart);
+  double* mean = part + (size_t)nparts * k;
   {
     Launch L2(ctx, CDL_KC_MISC, 0);
-    k_colsum<<<nparts, 256, 0, ctx->stream>>>(Y, n, k, static_cast<double*>(vpart));
+    k_colsum<<<nparts, 256, 0, ctx->stream>>>(Y, n, k, part);
+    CDL_TRY(L2.done());
+  }
+  {
+    Launch L2(ctx, CDL_KC_MISC, 0);
+    k_col_mean<<<(k + 255) / 256, 256, 0, ctx->stream>>>(part, nparts, n, k, mean);
     CDL_TRY(L2.done());
   }
   Launch L3(ctx, CDL_KC_MISC, 0);
-  k_sub_mean<<<(unsigned)(((size_t)n * k + 255) / 256), 256, 0, ctx->stream>>>(Y, n, k,
-                                                                               static_cast<const double*>(vpart), nparts);
+  k_sub_mean<<<(unsigned)(((size_t)n * k + 255) / 256), 256, 0, ctx->stream>>>(Y, n, k, mean);
   return L3.done();
 }
 

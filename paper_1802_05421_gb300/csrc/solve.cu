@@ -143,14 +143,20 @@ __global__ void __launch_bounds__(256) k_colsum_dz(const double* __restrict__ Z,
   part[(size_t)blockIdx.x * k + r] = acc;
 }
 
-__global__ void k_center(double* __restrict__ Z, const double* __restrict__ part, int nparts, int n, int k,
-                         const double* __restrict__ vol) {
-  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (idx >= (size_t)n * k) return;
-  const int r = (int)(idx % k);
+// shift[r] = (sum of the column's partial sums, in order) / vol, once per column.
+__global__ void k_center_shift(const double* __restrict__ part, int nparts, int k, const double* __restrict__ vol,
+                               double* __restrict__ shift) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
   double s = 0.0;
   for (int p = 0; p < nparts; ++p) s += part[(size_t)p * k + r];
-  Z[idx] -= s / *vol;
+  shift[r] = s / *vol;
+}
+
+__global__ void k_center(double* __restrict__ Z, const double* __restrict__ shift, int n, int k) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  Z[idx] -= shift[idx % k];
 }
 
 // Z (float64) -> float hi + lo pair for the float-float residual.
@@ -827,7 +833,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   CDL_TRY(ws_get(ctx, "solve.scal", 64, &vscal));
   CDL_TRY(ws_get(ctx, "solve.zh", (size_t)n * k * 4, &vzh));
   CDL_TRY(ws_get(ctx, "solve.zl", (size_t)n * k * 4, &vzl));
-  CDL_TRY(ws_get(ctx, "solve.colsum", (size_t)cs_parts * k * 8, &vcs));
+  CDL_TRY(ws_get(ctx, "solve.colsum", (size_t)(cs_parts + 1) * k * 8, &vcs));   // partial sums, then the shift
   void *vdz, *vpart2 = nullptr, *vdzop = nullptr;
   CDL_TRY(ws_get(ctx, "solve.dz", (size_t)np * kp * 4, &vdz));
   if (bf16) {
@@ -1039,8 +1045,14 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
       CDL_TRY(L.done());
     }
     {
+      double* shift = static_cast<double*>(vcs) + (size_t)cs_parts * k;
+      {
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_center_shift<<<(k + 255) / 256, 256, 0, st>>>(static_cast<const double*>(vcs), cs_parts, k, ch->vol, shift);
+        CDL_TRY(L.done());
+      }
       Launch L(ctx, CDL_KC_MISC, 0);
-      k_center<<<blocks_for(nk, 256), 256, 0, st>>>(Z, static_cast<const double*>(vcs), cs_parts, n, k, ch->vol);
+      k_center<<<blocks_for(nk, 256), 256, 0, st>>>(Z, shift, n, k);
       CDL_TRY(L.done());
     }
     ++iters;
