@@ -160,11 +160,12 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
     if (!active) continue;
     const int jmax = min(JT, jend - j0);
     const int wi = w & 3, rb = w >> 2;
+    const uint32_t* Ww = reinterpret_cast<const uint32_t*>(Wd + rl * WS + rb) + wi;   // this thread's word
+#pragma unroll 2
     for (int jj = 0; jj < jmax; ++jj) {
       const int e = rl * JTP + jj;
       const float p1 = P1[e], p2 = P2[e], p3 = P3[e];
-      const uint4 o = Wd[rl * WS + jj * nrb + rb];
-      const uint32_t bits = (wi == 0 ? o.x : wi == 1 ? o.y : wi == 2 ? o.z : o.w) >> shift;   // set bit -> +1
+      const uint32_t bits = Ww[jj * nrb * 4] >> shift;   // set bit -> +1
       t1 = __fadd_rn(t1, p1);
       t2 = __fadd_rn(t2, p2);
       t3 = __fadd_rn(t3, p3);
