@@ -654,10 +654,18 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
     ctx->pair_chain = nullptr;
   }
   bool converged = true;
+  void* vamax;
+  CDL_TRY(ws_get(ctx, "pair.amax", sizeof(unsigned long long), &vamax));
+  unsigned long long* amax = static_cast<unsigned long long*>(vamax);
   for (int g = 0; g < 2; ++g) {
-    CDL_TRY(graph_build(ctx, Xs[g], n, T, o->sigma, As[g], Ds[g], sc + g, sc + 2 + g));
-    CDL_TRY(cdl_chain_build(ctx, As[g], CDL_F64, Ds[g], sc + g, n, o->d, o->chain_dtype, o->chain_flags,
-                            &ctx->pair_chain));
+    CDL_TRY(graph_build(ctx, Xs[g], n, T, o->sigma, As[g], Ds[g], sc + g, sc + 2 + g, 0, amax));
+    ctx->amax_hint_A = As[g];   // the chain build takes max A from the graph build
+    ctx->amax_hint_bits = amax;
+    const int cst = cdl_chain_build(ctx, As[g], CDL_F64, Ds[g], sc + g, n, o->d, o->chain_dtype, o->chain_flags,
+                                    &ctx->pair_chain);
+    ctx->amax_hint_A = nullptr;
+    ctx->amax_hint_bits = nullptr;
+    CDL_TRY(cst);
     // tensor chains hold the float64 bits of max |A| (found by their build): the
     // projection reuses them instead of another pass over A
     const cdl_chain* pc = ctx->pair_chain;

@@ -451,8 +451,16 @@ int chain_init(cdl_ctx* ctx, cdl_chain* ch, const double* A) {
     k_split_a<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, cnt, ch->ahl, ch->ahl + cnt);
     CDL_TRY(L.done());
   }
-  if (ch->aslices)   // the slices' scale: max A, read before level 0 is formed
-    CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, reinterpret_cast<unsigned long long*>(ch->a_scale + 1)));
+  if (ch->aslices) {   // the slices' scale: max A, known before level 0 is formed
+    unsigned long long* mb = reinterpret_cast<unsigned long long*>(ch->a_scale + 1);
+    if (ctx->amax_hint_A == A && ctx->amax_hint_bits)
+      CDL_CUDA_TRY(cudaMemcpyAsync(mb, ctx->amax_hint_bits, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    else
+      CDL_TRY(abs_max_bits(ctx, A, (size_t)n * n, mb));
+  }
+  ctx->amax_hint_A = nullptr;
+  ctx->amax_hint_bits = nullptr;
   void* wsu;
   CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * (sizeof(double) + 2 * sizeof(float)), &wsu));
   double* u = static_cast<double*>(wsu);

@@ -370,8 +370,9 @@ __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int
 // slots (k_part_sums). Same entry arithmetic as kernel_row.
 template <int KERN>
 __global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, int n, const double* __restrict__ sigma,
-                                                       double* __restrict__ part) {
+                                                       double* __restrict__ part, unsigned long long* __restrict__ amax) {
   __shared__ double tt[DT][DT + 1];                     // tt[c][r] = A(i0 + r, j0 + c)
+  __shared__ unsigned long long wmax[8];
   const int nb = (n + DT - 1) / DT;
   int bi, bj;
   tri_index(blockIdx.x, nb, bi, bj);
@@ -400,7 +401,26 @@ __global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, in
     }
     tt[c][r] = a;
   }
+  if (amax) {                                            // max A (a >= 0: bit patterns order like values)
+    unsigned long long mb = 0;
+#pragma unroll 4
+    for (int m = 0; m < DT / 4; ++m) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(tt[c][rg + 4 * m]);
+      mb = b > mb ? b : mb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = v > mb ? v : mb;
+    }
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mb;
+  }
   __syncthreads();
+  if (amax && threadIdx.x == 0) {
+    unsigned long long mb = wmax[0];
+    for (int w = 1; w < 8; ++w) mb = wmax[w] > mb ? wmax[w] : mb;
+    if (mb) atomicMax(amax, mb);
+  }
   if (bi != bj) {                                        // mirror: lanes write consecutive columns of row j
 #pragma unroll 4
     for (int m = 0; m < DT / 4; ++m) {
@@ -598,7 +618,7 @@ int graph_build_grouped(cdl_ctx* ctx, const GraphBatch& B) {
 }
 
 int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma, double* A,
-                double* D, double* vol, double* sigma_out, int kernel) {
+                double* D, double* vol, double* sigma_out, int kernel, unsigned long long* amax_bits) {
   const int n = (int)n64;
   cudaStream_t s = ctx->stream;
   void *wsXi, *wsSt, *wsHist;
@@ -676,12 +696,13 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
     void* wsPart;
     CDL_TRY(ws_get(ctx, "graph.dpart", (size_t)nb * n * sizeof(double), &wsPart));
     double* part = static_cast<double*>(wsPart);
+    if (amax_bits) CDL_CUDA_TRY(cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long), s));
     {
       Launch L(ctx, CDL_KC_KERNEL, 16.0 * (double)n * n);
       if (kernel == KERNEL_EXP)
-        k_kernel_tiles<KERNEL_EXP><<<(unsigned)tiles, 256, 0, s>>>(A, n, sigma_out, part);
+        k_kernel_tiles<KERNEL_EXP><<<(unsigned)tiles, 256, 0, s>>>(A, n, sigma_out, part, amax_bits);
       else
-        k_kernel_tiles<KERNEL_GAUSSIAN><<<(unsigned)tiles, 256, 0, s>>>(A, n, sigma_out, part);
+        k_kernel_tiles<KERNEL_GAUSSIAN><<<(unsigned)tiles, 256, 0, s>>>(A, n, sigma_out, part, amax_bits);
       CDL_TRY(L.done());
     }
     Launch L(ctx, CDL_KC_MISC, 0);

@@ -71,6 +71,11 @@ struct cdl_ctx {
   std::map<std::string, int> tile_lists;
   int debug_flags = 0;   // CDL_DEBUG_* test hooks
   cdl::BatchPlan* batch = nullptr;   // plan of the last cdl_caddelag_batched call
+  // one-shot hint from the pair driver: the device float64 bits of max |A| of the
+  // graph at amax_hint_A (found while its kernel values were formed), taken and
+  // cleared by the next chain build of that graph instead of a pass over A
+  const double* amax_hint_A = nullptr;
+  const unsigned long long* amax_hint_bits = nullptr;
 };
 
 struct cdl_chain {
@@ -142,8 +147,10 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // ---- kernel launchers (one per translation unit family) ----
 // graph.cu
+// amax_bits (device, optional): receives the float64 bits of max A.
 int graph_build(cdl_ctx* ctx, const double* X, int64_t n, int T, double sigma, double* A,
-                double* D, double* vol, double* sigma_out, int kernel = 0);
+                double* D, double* vol, double* sigma_out, int kernel = 0,
+                unsigned long long* amax_bits = nullptr);
 int graph_degrees(cdl_ctx* ctx, const double* A, int64_t n, double* D, double* vol);
 int graph_add_edges(cdl_ctx* ctx, double* A, int64_t n, int64_t m, const int64_t* ij, const double* w,
                     int64_t* n_bad);
