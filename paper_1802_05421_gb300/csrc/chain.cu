@@ -183,10 +183,10 @@ __device__ __forceinline__ long long grid48(double a, int s) {
 // residual update); and A / 2^s as six exact bf16 digit planes (N of grid48
 // split into signed base-256 digits d_t, plane t holding d_t 2^-8t), the
 // operand of its full residual; all in one pass over A; padding rows
-// and columns zero. Conversions use integer operations (float64 is the scarce
-// pipe): the float of A_ij rounded to nearest, the digits bottom-up (balanced
-// base 256 on two 24-bit halves of N = A_ij 2^(48-s): the five lower digits in
-// [-128, 128], the leading one at most 256) and their bf16 bit patterns.
+// and columns zero. Conversions avoid the float64 pipe (the scarce one): the
+// float of A_ij rounded to nearest by integer operations, the digits bottom-up
+// (balanced base 256 on two 24-bit halves of N = A_ij 2^(48-s)) and their bf16
+// bit patterns by exact float32 arithmetic (digits6_fbits).
 __device__ __forceinline__ float d2f_rn_nonneg(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   int e = (int)((b >> 52) & 0x7FF) - 1023;
@@ -202,29 +202,33 @@ __device__ __forceinline__ float d2f_rn_nonneg(double x) {
   return __uint_as_float(((unsigned)(e + 127) << 23) | q);
 }
 
-__device__ __forceinline__ uint16_t digit_bf16(int d, int s) {   // d 2^-8s, |d| <= 256
-  if (d == 0) return 0;
-  const unsigned sg = d < 0 ? 0x8000u : 0u;
-  const unsigned a = d < 0 ? (unsigned)(-d) : (unsigned)d;
-  const int e = 31 - __clz(a);
-  const unsigned mant = (e <= 7 ? (a << (7 - e)) : (a >> (e - 7))) & 0x7Fu;
-  return (uint16_t)(sg | ((unsigned)(e + 127 - 8 * s) << 7) | mant);
+// The six signed base-256 digits of N (N in [0, 2^48]) as float32 bit
+// patterns of d_t 2^-8(t+1), computed bottom-up on two 24-bit halves of N
+// (the five lower digits in [-128, 128), the leading one in [0, 256]). Each
+// digit is formed exactly without a conversion instruction: with u = (v + 128)
+// mod 256, the float 2^23 + u (bit pattern 0x4B000000 | u) times 2^-8(t+1)
+// minus (2^23 + 128) 2^-8(t+1) is (u - 128) 2^-8(t+1) = d_t 2^-8(t+1), exact
+// in one fused multiply-add; the next v is (v + 128) >> 8. |d_t| <= 256 has at
+// most 8 significant bits, so the upper 16 bits of each pattern are the bf16
+// of the digit, exactly.
+template <int T>
+__device__ __forceinline__ uint32_t digit_fbits(int& v) {
+  constexpr float sc = (float)(1.0 / (double)(1ull << (8 * (T + 1))));
+  const int t = v + 128;
+  v = t >> 8;
+  return __float_as_uint(__fmaf_rn(__uint_as_float(0x4B000000u | (uint32_t)(t & 255)), sc, -8388736.0f * sc));
 }
 
-__device__ __forceinline__ void digits6(long long N, int (&d)[6]) {   // N in [0, 2^48]
+__device__ __forceinline__ void digits6_fbits(long long N, uint32_t (&f)[6]) {
   int lo = (int)(N & 0xFFFFFF), hi = (int)(N >> 24);
-#pragma unroll
-  for (int t = 5; t >= 3; --t) {
-    d[t] = ((lo + 128) & 255) - 128;
-    lo = (lo - d[t]) >> 8;
-  }
+  f[5] = digit_fbits<5>(lo);
+  f[4] = digit_fbits<4>(lo);
+  f[3] = digit_fbits<3>(lo);
   hi += lo;                                               // carry of the lower half
-#pragma unroll
-  for (int t = 2; t >= 1; --t) {
-    d[t] = ((hi + 128) & 255) - 128;
-    hi = (hi - d[t]) >> 8;
-  }
-  d[0] = hi;
+  f[2] = digit_fbits<2>(hi);
+  f[1] = digit_fbits<1>(hi);
+  constexpr float sc0 = 1.0f / 256.0f;                    // leading digit hi in [0, 256]
+  f[0] = __float_as_uint(__fmaf_rn(__uint_as_float(0x4B000000u | (uint32_t)hi), sc0, -8388608.0f * sc0));
 }
 
 // SL = false (the batched form's chains, which keep no slices): S and
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict_
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
         float v[2] = {0.f, 0.f}, af[2] = {0.f, 0.f};
-        int dg[2][6] = {};
+        uint32_t dg[2][6] = {};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int j = j0 + e + h;
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict_
             const double a = row[j];
             af[h] = d2f_rn_nonneg(a);
             v[h] = __fmaf_rn(af[h], __fmul_rn(ri, rsf[j]), -__fmul_rn(ui, uf[j]));
-            if constexpr (SL) digits6(grid48(a, sexp), dg[h]);
+            if constexpr (SL) digits6_fbits(grid48(a, sexp), dg[h]);
           }
         }
         const __nv_bfloat162 lv = __floats2bfloat162_rn(v[0], v[1]);
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict_
         if constexpr (SL) {
 #pragma unroll
           for (int t = 0; t < 6; ++t)
-            ws[t][e / 2] = (uint32_t)digit_bf16(dg[0][t], t + 1) | ((uint32_t)digit_bf16(dg[1][t], t + 1) << 16);
+            ws[t][e / 2] = __byte_perm(dg[0][t], dg[1][t], 0x7632);   // upper halves: the two bf16 digits
         }
       }
     }
