@@ -104,7 +104,11 @@ enum {
   CDL_KC_SCORE = 8,      /* CAD scores; work = bytes of A1, A2 read            */
   CDL_KC_TOPK = 9,
   CDL_KC_MISC = 10,      /* small vector kernels (norms, centring, updates)    */
-  CDL_KC_COUNT = 11
+  CDL_KC_HOST_LINK = 11, /* chain levels copied over the host link (CDL_CHAIN_HOST_LEVELS):
+                            copies, not kernels: "launches" counts copies and the
+                            launch counter excludes them; ms = summed copy time on
+                            the chain's copy stream; work = bytes copied           */
+  CDL_KC_COUNT = 12
 };
 int cdl_ctx_set_timing(cdl_ctx* ctx, int enable);
 int cdl_ctx_timing(cdl_ctx* ctx, int kernel_class, double* total_ms, int64_t* launches,

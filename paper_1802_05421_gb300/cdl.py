@@ -33,7 +33,7 @@ CDL_DEBUG_WITHHOLD_TC_LOAD = 1
 CDL_DEBUG_BATCH_VARIANT = 2
 
 (CDL_KC_DISTANCE, CDL_KC_SELECT, CDL_KC_KERNEL, CDL_KC_CHAIN_INIT, CDL_KC_SQUARE, CDL_KC_APPLY,
- CDL_KC_RESIDUAL, CDL_KC_PROJECT, CDL_KC_SCORE, CDL_KC_TOPK, CDL_KC_MISC, CDL_KC_COUNT) = range(12)
+ CDL_KC_RESIDUAL, CDL_KC_PROJECT, CDL_KC_SCORE, CDL_KC_TOPK, CDL_KC_MISC, CDL_KC_HOST_LINK, CDL_KC_COUNT) = range(13)
 KERNEL_CLASSES = ["distance", "select", "kernel", "chain_init", "square", "apply", "residual",
                   "project", "score", "topk", "misc"]
 

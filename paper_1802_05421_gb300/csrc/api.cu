@@ -80,11 +80,34 @@ int Launch::done() {
   return CDL_OK;
 }
 
+CopyTimer::CopyTimer(cdl_ctx* c, cudaStream_t st, double b) : ctx(c), s(st), bytes(b) {
+  if (ctx->timing) {
+    a = take_event(ctx);
+    cudaEventRecord(a, s);
+  }
+}
+
+void CopyTimer::done() {
+  ctx->kc_launches[CDL_KC_HOST_LINK] += 1;
+  ctx->kc_work[CDL_KC_HOST_LINK] += bytes;
+  if (ctx->timing) {
+    cudaEvent_t b = take_event(ctx);
+    cudaEventRecord(b, s);
+    Event2 ev;
+    ev.a = a;
+    ev.b = b;
+    ev.kc = CDL_KC_HOST_LINK;
+    ev.work = bytes;
+    ctx->pending.push_back(ev);
+  }
+}
+
 static int fold_timing(cdl_ctx* ctx) {
   if (ctx->pending.empty()) return CDL_OK;
   CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   for (auto& ev : ctx->pending) {
     float ms = 0.f;
+    cudaEventSynchronize(ev.b);   // copies run on a chain's own copy stream
     cudaEventElapsedTime(&ms, ev.a, ev.b);
     ctx->kc_ms[ev.kc] += ms;
     ctx->free_events.push_back(ev.a);

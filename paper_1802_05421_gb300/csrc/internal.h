@@ -143,6 +143,17 @@ struct Launch {
   int done();   // checks cudaGetLastError, records the end event
 };
 
+// Timing of one host-link copy on stream `s` (class CDL_KC_HOST_LINK): events
+// around it when timing is on; counted as a copy, not as a kernel launch.
+struct CopyTimer {
+  cdl_ctx* ctx;
+  cudaStream_t s;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  CopyTimer(cdl_ctx* c, cudaStream_t st, double b);
+  void done();
+};
+
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // ---- kernel launchers (one per translation unit family) ----
@@ -177,7 +188,7 @@ int ooc_write_end(cdl_ctx* ctx, cdl_chain* ch, int i);
 // without waiting for it.
 const void* ooc_read(cdl_ctx* ctx, cdl_chain* ch, int i);
 int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i);
-int ooc_prefetch(cdl_chain* ch, int i);
+int ooc_prefetch(cdl_ctx* ctx, cdl_chain* ch, int i);
 // tc_gemm.cu
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
 // A Z on the tensor cores from exact bf16 slices (A's in the chain, Z / c in

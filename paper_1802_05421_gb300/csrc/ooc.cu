@@ -26,9 +26,11 @@ int victim(const cdl_chain* ch) {
 }
 
 // issue the load of level i into slot s on the copy stream
-int load(cdl_chain* ch, int i, int s) {
+int load(cdl_ctx* ctx, cdl_chain* ch, int i, int s) {
   CDL_CUDA_TRY(cudaStreamWaitEvent(ch->copy, ch->ev_free[s], 0));
+  CopyTimer T(ctx, ch->copy, (double)level_bytes(ch));
   CDL_CUDA_TRY(cudaMemcpyAsync(ch->slot[s], ch->level(i), level_bytes(ch), cudaMemcpyHostToDevice, ch->copy));
+  T.done();
   CDL_CUDA_TRY(cudaEventRecord(ch->ev_ready[s], ch->copy));
   ch->slot_level[s] = i;
   ch->link_bytes += (double)level_bytes(ch);
@@ -86,7 +88,9 @@ int ooc_write_end(cdl_ctx* ctx, cdl_chain* ch, int i) {
   if (s < 0) return CDL_ERR_INVALID_ARG;
   CDL_CUDA_TRY(cudaEventRecord(ch->ev_ready[s], ctx->stream));
   CDL_CUDA_TRY(cudaStreamWaitEvent(ch->copy, ch->ev_ready[s], 0));
+  CopyTimer T(ctx, ch->copy, (double)level_bytes(ch));
   CDL_CUDA_TRY(cudaMemcpyAsync(ch->level(i), ch->slot[s], level_bytes(ch), cudaMemcpyDeviceToHost, ch->copy));
+  T.done();
   CDL_CUDA_TRY(cudaEventRecord(ch->ev_free[s], ch->copy));
   ch->link_bytes += (double)level_bytes(ch);
   ch->last_level = i;
@@ -97,7 +101,7 @@ const void* ooc_read(cdl_ctx* ctx, cdl_chain* ch, int i) {
   int s = slot_holding(ch, i);
   if (s < 0) {
     s = victim(ch);
-    if (load(ch, i, s) != CDL_OK) return nullptr;
+    if (load(ctx, ch, i, s) != CDL_OK) return nullptr;
   }
   if (cudaStreamWaitEvent(ctx->stream, ch->ev_ready[s], 0) != cudaSuccess) return nullptr;
   return ch->slot[s];
@@ -113,9 +117,9 @@ int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i) {
 
 // Issued after ooc_read_done of the level in use, so a load into its slot
 // (a chain of one level) waits for that reader.
-int ooc_prefetch(cdl_chain* ch, int i) {
+int ooc_prefetch(cdl_ctx* ctx, cdl_chain* ch, int i) {
   if (slot_holding(ch, i) >= 0) return CDL_OK;
-  return load(ch, i, victim(ch));
+  return load(ctx, ch, i, victim(ch));
 }
 
 }  // namespace cdl

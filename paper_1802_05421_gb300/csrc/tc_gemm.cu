@@ -2069,7 +2069,7 @@ int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, floa
   if (!lv) return CDL_ERR_CUDA;
   CDL_TRY(apply_tc_mat(ctx, lv, (int)ch->npad, xop, partial, kp, splits));
   CDL_TRY(ooc_read_done(ctx, mch, level));
-  return ooc_prefetch(mch, (level + 1) % ch->d_eff);   // overlaps the next level's load with this update
+  return ooc_prefetch(ctx, mch, (level + 1) % ch->d_eff);   // overlaps the next level's load with this update
 }
 
 int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float* partial, int kp, int splits) {

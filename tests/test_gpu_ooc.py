@@ -72,3 +72,40 @@ def test_host_levels_need_bf16(G):
         assert st == cdl.CDL_ERR_UNSUPPORTED and not ch
     st, ch = cdl.cdl_chain_build(G.h, A, cdl.CDL_F64, D, vol.data_ptr(), 300, 4, cdl.CDL_BF16, 4, None)
     assert st == cdl.CDL_ERR_INVALID_ARG
+
+
+def test_host_link_copy_timing(G):
+    """Host-link copies are timed as their own class (CDL_KC_HOST_LINK): one
+    copy out per level while the chain is built, loads while it is applied,
+    every copy one level of bytes, and none of them counted as a kernel
+    launch (the build issues the same kernels as with device levels)."""
+    cdl = G.cdl
+    n, d = 700, 3
+    npad = (n + 255) // 256 * 256
+    lb = npad * npad * 2
+    wl = iid_pair(n, 32, 4, seed=22)
+    A, D, vol, _ = G.graph(wl.X[0])
+    cdl.cdl_ctx_set_timing(G.h, 1)
+    try:
+        cdl.cdl_ctx_reset_counters(G.h)
+        dev = G.chain(A, D, vol, d, cdl.CDL_BF16)
+        _, dev_launches = cdl.cdl_ctx_launch_count(G.h)
+        _, _, dev_copies, _ = cdl.cdl_ctx_timing(G.h, cdl.CDL_KC_HOST_LINK)
+        assert dev_copies == 0
+        cdl.cdl_ctx_reset_counters(G.h)
+        host = G.chain(A, D, vol, d, cdl.CDL_BF16, flags=cdl.CDL_CHAIN_HOST_LEVELS)
+        _, host_launches = cdl.cdl_ctx_launch_count(G.h)
+        st, ms, copies, work = cdl.cdl_ctx_timing(G.h, cdl.CDL_KC_HOST_LINK)
+        assert st == 0 and host_launches == dev_launches
+        assert copies == d and work == d * lb and ms > 0
+        Y = G.project(A, 32, 5)
+        cdl.cdl_ctx_reset_counters(G.h)
+        _, s = G.solve(host, A, Y, max_iter=2, rel_tol=0.0)
+        st, ms, copies, work = cdl.cdl_ctx_timing(G.h, cdl.CDL_KC_HOST_LINK)
+        assert st == 0 and s.iters == 2
+        # each application reads the d levels (two of them may still sit in the slots)
+        assert 2 * d - 2 <= copies <= 2 * d + 1 and work == copies * lb and ms > 0
+    finally:
+        cdl.cdl_ctx_set_timing(G.h, 0)
+        cdl.cdl_chain_free(dev)
+        cdl.cdl_chain_free(host)
