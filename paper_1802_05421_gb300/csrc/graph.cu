@@ -29,7 +29,15 @@ struct SelectState {
   long long rank;               // rank within the still-matching keys
   int flags;                    // bit 0: input off the 2^-16 grid
   int pad;
+  unsigned long long ncomp;     // keys matching the prefix of the first two digits
 };
+// The third pass of the single-graph select also copies the keys that match
+// the first two digits (about 2^-12 of the value range around the median) to
+// a buffer of min(SELECT_CAP, max(m / 64, 1024)) keys (m keys in all); the
+// last three passes then read that buffer instead of the whole triangle,
+// unless more keys matched than it holds.
+constexpr long long SELECT_CAP = 1ll << 22;
+static_assert(sizeof(SelectState) <= 64, "the batched form keeps 64 bytes for the state");
 
 // X (float64, n x T) -> int32 fixed point a = x * 2^16, stored transposed
 // (T x n) for coalesced tile loads; flags input off the grid.
@@ -228,6 +236,7 @@ __global__ void k_select_init(SelectState* st, long long rank) {
   st->mask = 0;
   st->rank = rank;
   st->flags = 0;
+  st->ncomp = 0;
 }
 
 // Histogram of the `bits`-wide digit at `shift` over keys of the upper
@@ -258,6 +267,58 @@ __global__ void __launch_bounds__(512) k_select_hist(const double* __restrict__ 
                                                       int bits, const SelectState* __restrict__ st,
                                                       unsigned long long* __restrict__ hist) {
   select_hist_rows(A, n, shift, bits, st, hist, blockIdx.x, n - 1, gridDim.x);
+}
+
+// The third pass: the histogram of select_hist_rows, and every key matching
+// the current prefix appended to buf (the first `cap`; st->ncomp counts all).
+__global__ void __launch_bounds__(512) k_select_hist_compact(const double* __restrict__ A, int n, int shift, int bits,
+                                                              SelectState* st, unsigned long long* __restrict__ hist,
+                                                              unsigned long long* __restrict__ buf, long long cap) {
+  __shared__ unsigned int h[RADIX_BINS];
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  const unsigned long long dmask = (1ull << bits) - 1ull;
+  const unsigned long long* K = reinterpret_cast<const unsigned long long*>(A);
+  for (int i = blockIdx.x; i < n - 1; i += gridDim.x) {
+    const unsigned long long* row = K + (size_t)i * n;
+    for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const unsigned long long key = row[j];
+      if ((key & mask) == prefix) {
+        atomicAdd(&h[(key >> shift) & dmask], 1u);
+        const unsigned long long pos = atomicAdd(&st->ncomp, 1ull);
+        if (pos < (unsigned long long)cap) buf[pos] = key;
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+}
+
+// The later passes: the histogram over the copied keys, or over the whole
+// triangle when they did not fit.
+__global__ void __launch_bounds__(512) k_select_hist_buf(const double* __restrict__ A, int n, int shift, int bits,
+                                                          const SelectState* __restrict__ st,
+                                                          unsigned long long* __restrict__ hist,
+                                                          const unsigned long long* __restrict__ buf, long long cap) {
+  const unsigned long long nc = st->ncomp;
+  if (nc > (unsigned long long)cap) {
+    select_hist_rows(A, n, shift, bits, st, hist, blockIdx.x, n - 1, gridDim.x);
+    return;
+  }
+  __shared__ unsigned int h[RADIX_BINS];
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  const unsigned long long dmask = (1ull << bits) - 1ull;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nc; q += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = buf[q];
+    if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & dmask], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
 }
 
 // Pick the bin holding the remaining rank; extend the prefix; clear hist.
@@ -479,6 +540,7 @@ __global__ void k_g_select_init(const GGraph* __restrict__ gs) {
   st->mask = 0;
   st->rank = (m - 1) / 2;
   st->flags = 0;
+  st->ncomp = 0;
 }
 
 __global__ void k_g_to_fixed(const uint32_t* __restrict__ tiles, const GGraph* __restrict__ gs) {
@@ -679,10 +741,20 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
     const int shifts[6] = {52, 40, 28, 16, 4, 0};
     const int widths[6] = {12, 12, 12, 12, 12, 4};
     const int hblocks = std::min(n - 1, ctx->sm_count * 4);
+    const long long cap = std::min(SELECT_CAP, std::max(m / 64, 1024ll));
+    void* wsBuf;
+    CDL_TRY(ws_get(ctx, "graph.selbuf", (size_t)cap * sizeof(unsigned long long), &wsBuf));
+    unsigned long long* sbuf = static_cast<unsigned long long*>(wsBuf);
     for (int p = 0; p < 6; ++p) {
       {
-        Launch L(ctx, CDL_KC_SELECT, 8.0 * (double)m);
-        k_select_hist<<<hblocks, 512, 0, s>>>(A, n, shifts[p], widths[p], st, hist);
+        // work: bytes of the triangle for the full passes (the later ones read the copied keys)
+        Launch L(ctx, CDL_KC_SELECT, p < 3 ? 8.0 * (double)m : 0.0);
+        if (p < 2)
+          k_select_hist<<<hblocks, 512, 0, s>>>(A, n, shifts[p], widths[p], st, hist);
+        else if (p == 2)
+          k_select_hist_compact<<<hblocks, 512, 0, s>>>(A, n, shifts[p], widths[p], st, hist, sbuf, cap);
+        else
+          k_select_hist_buf<<<hblocks, 512, 0, s>>>(A, n, shifts[p], widths[p], st, hist, sbuf, cap);
         CDL_TRY(L.done());
       }
       {

@@ -50,6 +50,26 @@ def test_graph_matches_oracle(G, n, T):
     assert math.isclose(_h(vol)[0], volo, rel_tol=1e-13)
 
 
+@pytest.mark.parametrize("kind", ["three_points", "lattice"])
+def test_graph_select_with_tied_distances(G, kind):
+    """The median select when many distances are equal. Three distinct points
+    repeated: the keys matching the median's first two digits are far more
+    than the m / 64 the select copies for its last passes, so those passes
+    read the whole triangle again. Points on an integer lattice: hundreds of
+    keys tie at the median, fewer than the copy holds."""
+    rng = np.random.default_rng(7)
+    n, T = 700, 5
+    if kind == "three_points":
+        P = np.array([[0.0] * T, [1.0] * T, [0.5, -2.0, 3.0, 0.25, 1.5]])
+        X = P[rng.integers(0, 3, n)]
+    else:
+        X = rng.integers(-10, 11, (n, T)).astype(np.float64)   # 717 keys tie at the median
+    A, D, vol, sig = G.graph(X)
+    Ao, Do, volo, sigo = O.gaussian_graph(X)
+    assert _h(sig)[0] == sigo
+    np.testing.assert_allclose(_h(A), Ao, rtol=A_RTOL, atol=0)
+
+
 def test_graph_off_grid_uses_float64_path(G):
     rng = np.random.default_rng(5)
     X = rng.standard_normal((130, 7)) * 3.0 + 1e-9   # off the 2^-16 grid
