@@ -25,6 +25,7 @@ CDL_ERR_UNSUPPORTED = -6
 
 CDL_F64, CDL_F32, CDL_BF16, CDL_FP8E4M3, CDL_FP8E4M3_T128 = 0, 1, 2, 3, 4
 CDL_SOLVE_FULL_RESIDUAL = 1
+CDL_CHAIN_DEFAULT = 0
 CDL_CHAIN_HOST_LEVELS = 1
 CDL_CHAIN_TRUNCATE = 2
 CDL_SCORE_CHANGED_ONLY = 1

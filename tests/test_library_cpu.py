@@ -55,3 +55,23 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert cdl.cdl_sync(None) == cdl.CDL_ERR_INVALID_ARG
     assert cdl.cdl_ctx_destroy(None) == cdl.CDL_OK
     assert cdl.cdl_chain_free(None) == cdl.CDL_OK
+
+
+def declared_constants():
+    """Every enumerator of include/cdl.h with its value (explicit values only,
+    which is how the header writes them)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*(?:\w+\s*)?\{(.*?)\}", text, flags=re.S):
+        for name, value in re.findall(r"\b(CDL_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            out[name] = int(value)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    from paper_1802_05421_gb300 import cdl
+    consts = declared_constants()
+    assert len(consts) >= 30 and consts["CDL_KC_HOST_LINK"] == 11
+    wrong = {k: (v, getattr(cdl, k, None)) for k, v in consts.items() if getattr(cdl, k, None) != v}
+    assert not wrong, wrong
+    assert len(cdl.KERNEL_CLASSES) == consts["CDL_KC_HOST_LINK"]   # the kernel classes precede the copy class
