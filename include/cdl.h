@@ -47,7 +47,7 @@ enum {
   CDL_ERR_CUDA = -3,          /* a CUDA runtime/driver call failed               */
   CDL_ERR_NOT_CONVERGED = -4, /* solve stopped at max_iter above rel_tol         */
   CDL_ERR_TIMEOUT = -5,       /* a bounded device-side wait expired              */
-  CDL_ERR_UNSUPPORTED = -6    /* valid request this build does not implement     */
+  CDL_ERR_UNSUPPORTED = -6    /* valid request the library does not implement    */
 };
 
 typedef enum {
