@@ -66,15 +66,18 @@ __device__ __forceinline__ double f2d_bits(float f) {
 
 // Split a float64 x >= 0 into floats hi + lo with hi = x truncated to 24 bits
 // and lo the remaining 29 mantissa bits rounded to 24 (|x - hi - lo| <=
-// 2^-48 x), by integer operations only. Values below 2^-90 give lo = 0.
+// 2^-48 x; below 2^-74, where lo falls under the float normal range, lo is
+// subnormal and the bound is 2^-149 absolute), by integer operations and two
+// exact scalings. Values below 2^-100 give {0, 0}.
 __device__ __forceinline__ ff split_nonneg(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF) - 1023;      // x in [2^e, 2^(e+1))
   if (e < -100) return {0.f, 0.f};
   const uint32_t hi_bits = ((uint32_t)(e + 127) << 23) | ((uint32_t)(b >> 29) & 0x7FFFFFu);
   const uint32_t low29 = (uint32_t)(b & 0x1FFFFFFFull);
-  // lo = low29 * 2^(e - 52): float of the integer, then the power of two
-  const float lo = __uint2float_rn(low29) * __uint_as_float((uint32_t)(e - 52 + 127) << 23);
+  // lo = low29 2^(e - 52) = (low29 2^-52) 2^e: both factors are normal floats
+  // for e >= -100 (2^(e - 52) itself is not, below e = -74)
+  const float lo = __fmul_rn(__fmul_rn(__uint2float_rn(low29), 0x1p-52f), __uint_as_float((uint32_t)(e + 127) << 23));
   return {__uint_as_float(hi_bits), lo};
 }
 
@@ -134,6 +137,29 @@ __device__ __forceinline__ float d2f_trunc(double x) {
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
   const uint32_t m = (uint32_t)(b >> 29) & 0x7FFFFFu;
   return __uint_as_float(sign | ((uint32_t)e << 23) | m);
+}
+
+// sqrt(x) for float64 x >= 0, within one ulp (correctly rounded but within about
+// 2^-69 of a rounding midpoint), with three float64 operations: x = m 4^j with m in
+// [1, 4) by the exponent field; sqrt(m) in float-float (about 2^-46), one Newton
+// correction y + (m - y^2) / (2y) with the residual from one fused multiply-add
+// and the quotient in float32; the result rescaled by 2^j through the exponent
+// field. Zero and subnormal x take the float64 square root.
+__device__ __forceinline__ double sqrt_nonneg(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e == -1023) return __dsqrt_rn(x);
+  const int j = e >> 1;                                // floor(e / 2)
+  const double m = __longlong_as_double((long long)(b - ((unsigned long long)(long long)(2 * j) << 52)));
+  const ff a = split_nonneg(m);
+  const float sh = __fsqrt_rn(a.hi);
+  const float h = __fdiv_rn(0.5f, sh);
+  const float sl = __fmul_rn(__fadd_rn(__fmaf_rn(-sh, sh, a.hi), a.lo), h);
+  const double y = __dadd_rn(f2d_bits(sh), f2d_bits(sl));
+  const double r = __fma_rn(-y, y, m);
+  const double ym = __dadd_rn(y, f2d_bits(__fmul_rn(d2f_trunc(r), h)));   // sqrt(m) in [1, 2]
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(ym) +
+                                          ((unsigned long long)(long long)j << 52)));
 }
 
 // exp(-t) for float64 t >= 0, as the float-float pair q and the integer k with

@@ -361,11 +361,11 @@ __global__ void k_set_scalar(double* p, double v) { *p = v; }
 // A_ij = exp(-sqrt(d2_ij) / sigma) (KERN = KERNEL_EXP, the synthetic-data
 // kernel of Sec. 4.2.1), A_ii = 0, D_i = row sum. One block per row.
 // The exponential is ff_exp_neg_prod: the argument d2 * (1 / (2 sigma^2)), or
-// the correctly rounded sqrt(d2) times 1 / sigma, is formed exactly in 128-bit
-// integers and reduced there, then a float-float series (about 1e-14
+// sqrt(d2) (sqrt_nonneg: within one ulp) times 1 / sigma, is formed exactly in
+// 128-bit integers and reduced there, then a float-float series (about 1e-14
 // relative) and an integer assembly of the float64 result: no float64
-// operation but the square root of the exp kernel, float64 being the scarce
-// pipe. The row sum is accumulated in float-float (terms below 2^-100 are
+// operation but the three of the exp kernel's square root, float64 being the
+// scarce pipe. The row sum is accumulated in float-float (terms below 2^-100 are
 // dropped from the sum, not from A).
 enum { KERNEL_GAUSSIAN = 0, KERNEL_EXP = 1 };
 
@@ -378,7 +378,7 @@ __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double
     const float rcpf = d2f_trunc(rcp);
     ff acc = {0.f, 0.f};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const double x = KERN == KERNEL_EXP ? __dsqrt_rn(row[j]) : row[j];
+      const double x = KERN == KERNEL_EXP ? sqrt_nonneg(row[j]) : row[j];
       double a = 0.0;
       if (j != i) {
         if (__fmul_rn(d2f_trunc(x), rcpf) < 680.f) {          // t = x rcp well below 690
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, in
     if (i < n && j < n) {
       double* pa = A + (size_t)i * n + j;
       if (i != j) {
-        const double x = KERN == KERNEL_EXP ? __dsqrt_rn(*pa) : *pa;
+        const double x = KERN == KERNEL_EXP ? sqrt_nonneg(*pa) : *pa;
         if (__fmul_rn(d2f_trunc(x), rcpf) < 680.f) {
           int k;
           const ff q = ff_exp_neg_prod(x, rcp, k);

@@ -87,6 +87,31 @@ def test_graph_given_sigma(G):
     np.testing.assert_allclose(_h(A), Ao, rtol=A_RTOL, atol=0)
 
 
+def test_graph_with_tiny_kernel_values(G):
+    """A sigma small enough that a fifth of the kernel values lie in [2^-100,
+    2^-74], where splitting a float64 into two floats needs a subnormal low
+    part: values, degrees (the smallest about 6e-17) and the projection (square
+    roots of A) still match the oracle."""
+    X = iid_pair(300, 8, 1, seed=4).X[0]
+    sigma = 0.375
+    A, D, vol, sig = G.graph(X, sigma=sigma)
+    Ao, Do, volo, _ = O.gaussian_graph(X, sigma=sigma)
+    a = Ao[np.triu_indices(300, 1)]
+    assert np.mean((a > 2.0 ** -100) & (a < 2.0 ** -74)) > 0.2
+    # the arguments t = d2 / (2 sigma^2) reach about 150 here: the two sides round t
+    # differently (d2 times the rounded 1 / (2 sigma^2), against the rounded
+    # quotient), each within 2^-53 relative, which moves exp(-t) by up to t 2^-52
+    Ah = _h(A)
+    off = ~np.eye(300, dtype=bool)
+    t = -np.log(Ao[off])
+    assert np.all(np.abs(Ah[off] - Ao[off]) <= (A_RTOL + t * 2.0 ** -52) * Ao[off])
+    assert np.all(np.diag(Ah) == 0.0)
+    np.testing.assert_allclose(_h(D), Do, rtol=1e-13)
+    Y = _h(G.project(torch.from_numpy(Ao).cuda(), 32, 9))
+    Yo = O.project(Ao, 9, 32)
+    assert np.abs(Y - Yo).max() <= 1e-12 * np.abs(Yo).max()
+
+
 def test_graph_field_workload(G):
     X = field_sequence(16, 32, 48, 2, patch=4, seed=3).X[1]
     A, D, vol, sig = G.graph(X)
