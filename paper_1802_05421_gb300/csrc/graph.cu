@@ -112,6 +112,16 @@ __device__ __forceinline__ void tri_index(long long t, int nb, int& bi, int& bj)
   bj = r + (int)(t - off(r));
 }
 
+// tri_index of the block's own tile, formed once (thread 0: it takes a float64
+// square root) and shared; every thread of the block must call it.
+__device__ __forceinline__ void block_tri_index(int nb, int& bi, int& bj) {
+  __shared__ int tile[2];
+  if (threadIdx.x == 0) tri_index(blockIdx.x, nb, tile[0], tile[1]);
+  __syncthreads();
+  bi = tile[0];
+  bj = tile[1];
+}
+
 // Exact squared distances on the 2^-16 grid: int64 sums of squared int32
 // differences, written as float64 multiples of 2^-32 to both (i,j) and (j,i).
 __device__ __forceinline__ void dist_int_tile(const int* __restrict__ Xt, int n, int T, double* __restrict__ A,
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(256) k_dist_int(const int* __restrict__ Xt, in
   if (st->flags & 1) return;   // off-grid input: the float64 kernel handles it
   const int nb = (n + DT - 1) / DT;
   int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
+  block_tri_index(nb, bi, bj);
   dist_int_tile(Xt, n, T, A, bi, bj);
 }
 
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(256) k_dist_f64(const double* __restrict__ X, 
   if (!(st->flags & 1)) return;
   const int nb = (n + DT - 1) / DT;
   int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
+  block_tri_index(nb, bi, bj);
   dist_f64_tile(X, n, T, A, bi, bj);
 }
 
@@ -435,11 +445,17 @@ __global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, in
   __shared__ double tt[DT][DT + 1];                     // tt[c][r] = A(i0 + r, j0 + c)
   __shared__ unsigned long long wmax[8];
   const int nb = (n + DT - 1) / DT;
-  int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
+  __shared__ double rcp_s;                               // float64 division and square root once per block
+  __shared__ int tile_s[2];
+  if (threadIdx.x == 0) {
+    tri_index(blockIdx.x, nb, tile_s[0], tile_s[1]);
+    const double sg = *sigma;
+    rcp_s = KERN == KERNEL_EXP ? 1.0 / sg : 1.0 / (2.0 * (sg * sg));
+  }
+  __syncthreads();
+  const int bi = tile_s[0], bj = tile_s[1];
   const int i0 = bi * DT, j0 = bj * DT;
-  const double sg = *sigma;
-  const double rcp = KERN == KERNEL_EXP ? 1.0 / sg : 1.0 / (2.0 * (sg * sg));
+  const double rcp = rcp_s;
   const float rcpf = d2f_trunc(rcp);
   const int c = threadIdx.x & (DT - 1), rg = threadIdx.x >> 6;
 #pragma unroll 4
@@ -593,8 +609,13 @@ __global__ void __launch_bounds__(256) k_g_kernel_rows(const uint32_t* __restric
                                                         const GGraph* __restrict__ gs) {
   const uint32_t t = tiles[blockIdx.x];
   const GGraph& G = gs[t & 0xFFFu];
-  const double s = *G.sigma;
-  kernel_row<KERNEL_GAUSSIAN>(G.A, G.n, 1.0 / (2.0 * (s * s)), G.D, (int)(t >> 12));
+  __shared__ double rcp_s;                               // one float64 division per block
+  if (threadIdx.x == 0) {
+    const double s = *G.sigma;
+    rcp_s = 1.0 / (2.0 * (s * s));
+  }
+  __syncthreads();
+  kernel_row<KERNEL_GAUSSIAN>(G.A, G.n, rcp_s, G.D, (int)(t >> 12));
 }
 
 __global__ void k_g_sum(const GGraph* __restrict__ gs) {

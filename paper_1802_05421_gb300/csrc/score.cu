@@ -120,6 +120,16 @@ __device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
   bj = r + (int)(t - off(r));
 }
 
+// tri_index of the block's own tile, formed once (thread 0: it takes a float64
+// square root) and shared; every thread of the block must call it.
+__device__ __forceinline__ void block_tri_index(int nb, int& bi, int& bj) {
+  __shared__ int tile[2];
+  if (threadIdx.x == 0) tri_index(blockIdx.x, nb, tile[0], tile[1]);
+  __syncthreads();
+  bi = tile[0];
+  bj = tile[1];
+}
+
 // Per-tile accumulation of |A1 - A2| |c2 - c1| into row and column partials.
 __device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const double* __restrict__ A2,
                                             int n, int i0, int j0, int bi, int bj, int tx, int ty,
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(256) k_score_pairs(const double* __restrict__ 
                                                       int n, int k, double* __restrict__ contrib) {
   const int nb = (n + ST - 1) / ST;
   int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
+  block_tri_index(nb, bi, bj);
   score_tile(A1, A2, ah, al, bh, bl, n, k, contrib, bi, bj);
 }
 
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(256) k_score_pairs64(const double* __restrict_
                                                         double* __restrict__ contrib) {
   const int nb = (n + ST - 1) / ST;
   int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
+  block_tri_index(nb, bi, bj);
   score_tile64(A1, A2, aT, bT, n, k, contrib, bi, bj);
 }
 
@@ -514,7 +524,7 @@ __global__ void __launch_bounds__(256) k_edge_pairs(const double* __restrict__ A
                                                      double* __restrict__ contrib, double* __restrict__ E) {
   const int nb = (n + ST - 1) / ST;
   int bi, bj;
-  tri_index(blockIdx.x, nb, bi, bj);
+  block_tri_index(nb, bi, bj);
   const size_t nk = (size_t)n * k;
   if (fp64) {
     const double* aT = static_cast<const double*>(ab);
