@@ -682,6 +682,143 @@ def run_gmm(args):
     return 0
 
 
+# ---------------------------------------------------------------- float32 sequence
+SEQ_WORKLOAD = "field_n8192_seq4"
+
+
+def run_sequence(args):
+    """The plain float32 GPU path on a graph sequence: 4 graphs of the 64 x 128
+    correlated field (n = 8192, T = 128, AR(1) drift, an 8 x 8 patch shifted in
+    the second transition), each embedded once (float32 chain on CUDA cores,
+    d = 12; projection k = 64; solve to 1e-10) and reused by its two pairs,
+    then the 3 transitions scored in float32. One step = the whole sequence
+    through the C ABI stage by stage; value = transitions scored per second."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1802_05421_gb300 import build as B
+    B.build()
+    from paper_1802_05421_gb300 import cdl
+    from workloads import field_sequence
+    wl = field_sequence(64, 128, 128, 4, patch=8, patch_transition=1, seed=1)
+    G = len(wl.X)
+    n, T = wl.X[0].shape
+    k, d = 64, 12
+    stream = torch.cuda.Stream()
+    st, ctx = cdl.cdl_ctx_create(0, stream.cuda_stream, 0)
+    assert st == 0, cdl.cdl_status_string(st)
+
+    def ok(r, what):
+        if r != 0:
+            raise RuntimeError(f"{what}: {cdl.cdl_status_string(r)} {cdl.cdl_last_error_detail()}")
+
+    hX = [torch.from_numpy(x).pin_memory() for x in wl.X]
+    with torch.cuda.stream(stream):
+        X = [h.cuda() for h in hX]
+        A = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(G)]
+        D = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(G)]
+        sc = torch.zeros(2 * G, dtype=torch.float64, device="cuda")     # vol, sigma per graph
+        Y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+        Z = [torch.empty((n, k), dtype=torch.float64, device="cuda") for _ in range(G)]
+        F = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(G - 1)]
+        top = [torch.empty(TOPK, dtype=torch.int64, device="cuda") for _ in range(G - 1)]
+    stream.synchronize()
+    vol = [sc[t:t + 1] for t in range(G)]
+    chain = [None]
+    stats = [cdl.cdl_solve_stats() for _ in range(G)]
+    sopts = cdl.cdl_solve_opts(40, REL_TOL, 0)
+
+    def step():
+        for t in range(G):
+            ok(cdl.cdl_build_graph(ctx, X[t], n, T, 0.0, cdl.CDL_F64, A[t], D[t], vol[t].data_ptr(),
+                                   sc[G + t:G + t + 1].data_ptr()), "build_graph")
+            r, chain[0] = cdl.cdl_chain_build(ctx, A[t], cdl.CDL_F64, D[t], vol[t].data_ptr(), n, d, cdl.CDL_F32,
+                                              0, chain[0])
+            ok(r, "chain_build")
+            ok(cdl.cdl_project(ctx, A[t], cdl.CDL_F64, n, k, SEED, Y), "project")
+            ok(cdl.cdl_chain_solve(ctx, chain[0], A[t], cdl.CDL_F64, Y, k, sopts, Z[t], stats[t]), "solve")
+        for t in range(G - 1):
+            ok(cdl.cdl_cad_score(ctx, A[t], A[t + 1], cdl.CDL_F64, Z[t], Z[t + 1], vol[t].data_ptr(),
+                                 vol[t + 1].data_ptr(), n, k, cdl.CDL_F32, TOPK, F[t], top[t]), "cad_score")
+
+    for _ in range(args.warmup):
+        step()
+    ok(cdl.cdl_sync(ctx), "sync")
+    cdl.cdl_ctx_reset_counters(ctx)
+    cdl.cdl_ctx_set_timing(ctx, True)
+    sampler = ClockSampler(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_ms = ev0.elapsed_time(ev1) / args.steps
+    _, launches = cdl.cdl_ctx_launch_count(ctx)
+    kc = {}
+    for i, name in enumerate(cdl.KERNEL_CLASSES):
+        _, ms, cnt, work = cdl.cdl_ctx_timing(ctx, i)
+        kc[name] = dict(ms_per_step=ms / args.steps, work=work / max(cnt, 1), ms_per_launch=ms / max(cnt, 1))
+    cdl.cdl_ctx_set_timing(ctx, False)
+    tops = [tp.cpu().tolist() for tp in top]
+    planted_on_top = set(tops[1]) <= set(wl.planted[1].tolist())
+
+    # end to end: the 4 series copied in from pinned host memory, the 3 score
+    # vectors and top lists read back
+    hF = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(G - 1)]
+    htop = [torch.empty(TOPK, dtype=torch.int64).pin_memory() for _ in range(G - 1)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        with torch.cuda.stream(stream):
+            for t in range(G):
+                X[t].copy_(hX[t], non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            for t in range(G - 1):
+                hF[t].copy_(F[t], non_blocking=True)
+                htop[t].copy_(top[t], non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if chain[0] is not None:
+        cdl.cdl_chain_free(chain[0])
+
+    # the float32 squaring on the CUDA cores against the float32 FMA rate of the
+    # part: 152 SMs x 128 lanes x 2 flop x the maximum SM clock
+    pk, _ = peaks()
+    f32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    sq = kc["square"]
+    achieved = sq["work"] / (sq["ms_per_launch"] * 1e-3) / 1e12 if sq["ms_per_launch"] else 0.0
+    line = {
+        "metric": "graph pairs/s on the n=8192 sequence (plain float32 GPU path)",
+        "value": (G - 1) * 1000.0 / step_ms, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SEQ_WORKLOAD, "n": n, "T": T, "graphs": G, "transitions": G - 1, "k": k, "d": d,
+                   "chain": "f32", "score": "f32", "topk": TOPK, "refine_rel_tol": REL_TOL,
+                   "solve_iters": [s.iters for s in stats], "rel_res": max(s.rel_res for s in stats),
+                   "planted_patch_on_top": planted_on_top,
+                   "l2": "no flush: each step writes four 537 MB float64 graphs and their 3 GB float32 chains, "
+                         "larger than the 129 MB L2"},
+        "roofline": {"kernel": "k_gemm_tn (float32 chain squaring, CUDA cores)", "bound": "alu",
+                     "achieved": achieved, "peak": f32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / f32_peak if f32_peak else None, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 float32 lanes x 2 flop x sm_max_mhz",
+                     "work_per_launch": sq["work"], "ms_per_launch": sq["ms_per_launch"]},
+        "cpu_baseline": None,
+        "e2e": {"value": (G - 1) / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": G * n * T * 8,
+                "d2h_bytes_per_step": (G - 1) * (n * 8 + TOPK * 8),
+                "same_top_as_device_run": [h.tolist() for h in htop] == tops},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "phases_ms_per_step": {k2: round(v["ms_per_step"], 3) for k2, v in kc.items()},
+    }
+    print(json.dumps(line), flush=True)
+    cdl.cdl_ctx_destroy(ctx)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -701,7 +838,7 @@ def main():
                     help="run a small single-kernel case for a profiler capture instead of the bench")
     ap.add_argument("--n", type=int, default=12288)
     ap.add_argument("--reps", type=int, default=1)
-    ap.add_argument("--workload", default="pair", choices=["pair", "batched", "host-levels", "gmm"],
+    ap.add_argument("--workload", default="pair", choices=["pair", "batched", "host-levels", "gmm", "sequence"],
                     help="pair: the n = 32768 field pair (default); batched: 64 ragged pairs; "
                          "host-levels: the pair with chain levels in pinned host memory; "
                          "gmm: the synthetic mixture pair at n = 32768")
@@ -716,6 +853,8 @@ def main():
         return run_batched(args)
     if args.workload == "host-levels":
         return run_host_levels(args)
+    if args.workload == "sequence":
+        return run_sequence(args)
     if args.workload == "gmm":
         return run_gmm(args)
 
