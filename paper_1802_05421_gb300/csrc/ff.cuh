@@ -162,16 +162,11 @@ __device__ __forceinline__ double sqrt_nonneg(double x) {
                                           ((unsigned long long)(long long)j << 52)));
 }
 
-// exp(-t) for float64 t >= 0, as the float-float pair q and the integer k with
-// exp(-t) = (q.hi + q.lo) 2^-k, to about 2^-46 relative. Written from the series
-// definition: t = k ln2 + r with k = round(t / ln2) and |r| <= ln2/2, so
-// exp(-t) = 2^-k exp(-r). The reduction is done in float64 with ln2 split
-// Cody-Waite style into a 40-bit head (k * head exact for |k| < 2^13) and a tail,
-// so r carries float64 accuracy. exp(-r) is the Taylor series to degree 12
-// (remainder below 2^-52 for |r| <= 0.35): degrees 7..12 in float32 (each term
-// below 2^-22 of the result), degrees 0..6 in float-float Horner steps; the
-// coefficients 1/m! are stored as float pairs. Valid for t < 700.
-// e^x for a float-float |x| <= 0.35 (the series part of the exponentials below).
+// e^x for a float-float |x| <= 0.35, from the series definition: the Taylor
+// series to degree 12 (remainder below 2^-52), degrees 7..12 in float32 (each
+// term below 2^-22 of the result), degrees 0..6 in float-float Horner steps; the
+// coefficients 1/m! are stored as float pairs. It fills the table of
+// ff_exp_table.
 __device__ __forceinline__ ff ff_exp_series(ff x) {
   float p = 0x1.1eed8ep-29f;                      // 1/12!
   p = __fmaf_rn(p, x.hi, 0x1.ae6456p-26f);        // 1/11!
@@ -190,27 +185,39 @@ __device__ __forceinline__ ff ff_exp_series(ff x) {
   return q;
 }
 
-__device__ __forceinline__ ff ff_exp_neg_scaled(double t, int& k_out) {
-  const float k = rintf(__fmul_rn(d2f_trunc(t), 0x1.715476p+0f));   // t / ln2
-  const double kd = f2d_bits(k);
-  double r = fma(-kd, 0x1.62e42fefa2000p-1, t);
-  r = fma(-kd, 0x1.9ef35793c7673p-41, r);
-  // float-float split of r with integer conversions: rh exact top bits, rl the
-  // remainder truncated to 24 bits (error below 2^-48 |r|)
-  const float rh = d2f_trunc(r);
-  const float rl = d2f_trunc(r - f2d_bits(rh));
-  k_out = (int)k;
-  return ff_exp_series(ff{-rh, -rl});                                // in [0.70, 1.42]
-}
-
 // exp(-x y) for float64 x >= 0, y > 0 with x y < 690, as (q.hi + q.lo) 2^-k
 // with no float64 operation: the product t = x y is formed exactly as the
 // 106-bit product of the two 53-bit mantissas and kept to 64 fractional bits
 // (128-bit integers); k = round(t / ln2) from a float estimate; r = t - k ln2
 // with ln2 to 64 fractional bits (error below 2^-54 for k < 1024) is a signed
-// 64-bit fixed-point number, split into float-float with integer operations;
-// exp(-r) is the series above (|r| <= 0.35).
-__device__ __forceinline__ ff ff_exp_neg_prod(double x, double y, int& k_out) {
+// 64-bit fixed-point number. It is reduced once more, exactly, by j / 32 with j
+// = round(32 r) (|j| <= 11): exp(-r) = exp(-j / 32) exp(-r') with |r'| <= 1/64,
+// exp(-j / 32) from a table of float-float values (ff_exp_table) and exp(-r')
+// from the series to degree 6 (remainder below 2^-54): degrees 4..6 in float32,
+// 0..3 in float-float Horner steps. About 1.4e-14 relative, as the degree-12
+// series on r alone (a host emulation against quad precision over 2e7
+// arguments gives 1.33e-14 and 1.41e-14).
+__device__ __forceinline__ ff ff_exp_series6(ff x) {
+  float p = 0x1.6c16c2p-10f;                      // 1/6!
+  p = __fmaf_rn(p, x.hi, 0x1.111112p-7f);         // 1/5!
+  p = __fmaf_rn(p, x.hi, 0x1.555556p-5f);         // 1/4!
+  ff q = {p, 0.f};
+  q = ff_add(ff_mul(q, x), ff{0x1.555556p-3f, -0x1.555556p-28f});   // 1/3!
+  q = ff_add(ff_mul(q, x), ff{0x1p-1f, 0.f});                        // 1/2!
+  q = ff_add(ff_mul(q, x), ff{1.f, 0.f});                            // 1/1!
+  q = ff_add(ff_mul(q, x), ff{1.f, 0.f});                            // 1/0!
+  return q;
+}
+
+// exp(-j / 32) for j = -11 .. 11 at tab[j + 11], from the degree-12 series
+// (|j / 32| <= 0.35, exact in float). Threads 0 .. 22 of the block fill it;
+// the caller synchronises before use.
+constexpr int FF_EXP_TABLE = 23;
+__device__ __forceinline__ void ff_exp_table(ff* tab) {
+  if (threadIdx.x < FF_EXP_TABLE) tab[threadIdx.x] = ff_exp_series(ff{(float)(11 - (int)threadIdx.x) * 0.03125f, 0.f});
+}
+
+__device__ __forceinline__ ff ff_exp_neg_prod(double x, double y, int& k_out, const ff* __restrict__ tab) {
   const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
   const unsigned long long by = (unsigned long long)__double_as_longlong(y);
   const int ex = (int)((bx >> 52) & 0x7FF), ey = (int)((by >> 52) & 0x7FF);
@@ -229,11 +236,15 @@ __device__ __forceinline__ ff ff_exp_neg_prod(double x, double y, int& k_out) {
   const int k = __float2int_rn(__fmul_rn(tf, 0x1.715476p+0f));       // t / ln2
   const unsigned __int128 kl = (unsigned __int128)(unsigned)k * 0xB17217F7D1CF79ABull;   // k ln2 2^64
   const long long r = (long long)(__int128)(T - kl);                 // |r| < 2^63
-  const unsigned long long ar = r < 0 ? (unsigned long long)(-r) : (unsigned long long)r;
+  long long j = (r + (1ll << 58)) >> 59;                             // round(32 r), |j| <= 11
+  j = j < -11 ? -11 : (j > 11 ? 11 : j);                             // (a guard: |r| <= 0.35 here)
+  const long long r2 = r - j * (1ll << 59);                          // |r2| <= 2^58: |r'| <= 1/64
+  const unsigned long long ar = r2 < 0 ? (unsigned long long)(-r2) : (unsigned long long)r2;
   const ff m = ff_from_u64(ar);
   const float hi = __fmul_rn(m.hi, 0x1p-64f), lo = __fmul_rn(m.lo, 0x1p-64f);   // exact powers of two
   k_out = k;
-  return ff_exp_series(r < 0 ? ff{hi, lo} : ff{-hi, -lo});           // exp(-r), in [0.70, 1.42]
+  const ff e = ff_exp_series6(r2 < 0 ? ff{hi, lo} : ff{-hi, -lo});   // exp(-r')
+  return ff_mul(e, tab[j + 11]);                                      // exp(-r), in [0.70, 1.42]
 }
 
 // (q.hi + q.lo) 2^-k as float64 for q in [0.5, 2) (q.hi > 0, |q.lo| <= ulp(q.hi)),
@@ -258,16 +269,6 @@ __device__ __forceinline__ double ff_scaled_to_double(ff q, int k) {
     E = 0;
   }
   return __longlong_as_double((long long)(((unsigned long long)(E - k + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
-}
-
-// exp(-t) as float64 (see ff_exp_neg_scaled); float64 exp beyond t = 700.
-__device__ __forceinline__ double ff_exp_neg(double t) {
-  if (!(t < 700.0)) return exp(-t);
-  int k;
-  const ff q = ff_exp_neg_scaled(t, k);
-  const double v = f2d_bits(q.hi) + f2d_bits(q.lo);
-  // times 2^-k through the exponent field (v and the result are normal numbers)
-  return __longlong_as_double(__double_as_longlong(v) - ((long long)k << 52));
 }
 
 }  // namespace cdl

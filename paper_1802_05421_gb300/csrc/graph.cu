@@ -372,8 +372,9 @@ __global__ void k_set_scalar(double* p, double v) { *p = v; }
 // kernel of Sec. 4.2.1), A_ii = 0, D_i = row sum. One block per row.
 // The exponential is ff_exp_neg_prod: the argument d2 * (1 / (2 sigma^2)), or
 // sqrt(d2) (sqrt_nonneg: within one ulp) times 1 / sigma, is formed exactly in
-// 128-bit integers and reduced there, then a float-float series (about 1e-14
-// relative) and an integer assembly of the float64 result: no float64
+// 128-bit integers and reduced there (by k ln2, then by j / 32 through a
+// per-block table), then a float-float series (about 1.4e-14 relative) and an
+// integer assembly of the float64 result: no float64
 // operation but the three of the exp kernel's square root, float64 being the
 // scarce pipe. The row sum is accumulated in float-float (terms below 2^-100 are
 // dropped from the sum, not from A).
@@ -381,7 +382,7 @@ enum { KERNEL_GAUSSIAN = 0, KERNEL_EXP = 1 };
 
 template <int KERN = KERNEL_GAUSSIAN>
 __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double rcp, double* __restrict__ D,
-                                           int i) {
+                                           int i, const ff* __restrict__ tab) {
   __shared__ double red[8];
   {
     double* row = A + (size_t)i * n;
@@ -393,7 +394,7 @@ __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double
       if (j != i) {
         if (__fmul_rn(d2f_trunc(x), rcpf) < 680.f) {          // t = x rcp well below 690
           int k;
-          const ff q = ff_exp_neg_prod(x, rcp, k);
+          const ff q = ff_exp_neg_prod(x, rcp, k, tab);
           a = ff_scaled_to_double(q, k);
           if (k <= 100) {
             const float sc = __int_as_float((127 - k) << 23);   // 2^-k
@@ -427,7 +428,10 @@ __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int
                                                       double* __restrict__ D) {
   const double s = *sigma;
   const double rcp = KERN == KERNEL_EXP ? 1.0 / s : 1.0 / (2.0 * (s * s));
-  for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row<KERN>(A, n, rcp, D, i);
+  __shared__ ff tab[FF_EXP_TABLE];
+  ff_exp_table(tab);
+  __syncthreads();
+  for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row<KERN>(A, n, rcp, D, i, tab);
 }
 
 // Kernel values over the upper block triangle of 64 x 64 tiles (A is
@@ -447,6 +451,8 @@ __global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, in
   const int nb = (n + DT - 1) / DT;
   __shared__ double rcp_s;                               // float64 division and square root once per block
   __shared__ int tile_s[2];
+  __shared__ ff tab[FF_EXP_TABLE];
+  ff_exp_table(tab);
   if (threadIdx.x == 0) {
     tri_index(blockIdx.x, nb, tile_s[0], tile_s[1]);
     const double sg = *sigma;
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(256) k_kernel_tiles(double* __restrict__ A, in
         const double x = KERN == KERNEL_EXP ? sqrt_nonneg(*pa) : *pa;
         if (__fmul_rn(d2f_trunc(x), rcpf) < 680.f) {
           int k;
-          const ff q = ff_exp_neg_prod(x, rcp, k);
+          const ff q = ff_exp_neg_prod(x, rcp, k, tab);
           a = ff_scaled_to_double(q, k);
         } else {
           a = exp(-(x * rcp));
@@ -610,12 +616,14 @@ __global__ void __launch_bounds__(256) k_g_kernel_rows(const uint32_t* __restric
   const uint32_t t = tiles[blockIdx.x];
   const GGraph& G = gs[t & 0xFFFu];
   __shared__ double rcp_s;                               // one float64 division per block
+  __shared__ ff tab[FF_EXP_TABLE];
+  ff_exp_table(tab);
   if (threadIdx.x == 0) {
     const double s = *G.sigma;
     rcp_s = 1.0 / (2.0 * (s * s));
   }
   __syncthreads();
-  kernel_row<KERNEL_GAUSSIAN>(G.A, G.n, rcp_s, G.D, (int)(t >> 12));
+  kernel_row<KERNEL_GAUSSIAN>(G.A, G.n, rcp_s, G.D, (int)(t >> 12), tab);
 }
 
 __global__ void k_g_sum(const GGraph* __restrict__ gs) {
