@@ -140,8 +140,10 @@ int cdl_ctx_set_debug(cdl_ctx* ctx, int flags);
  *   0 (at least half of the pairs coincide) leaves the kernel undefined:
  *   the selection runs on the device without a host round trip, so this is
  *   not detected and A is not meaningful; pass sigma > 0 for such inputs.
- *   A node with no neighbour of nonzero weight has degree 0: a later
- *   cdl_chain_solve on that graph returns CDL_ERR_NOT_CONVERGED.
+ *   A node with no neighbour of nonzero weight has degree 0; the chain of
+ *   that graph is then not finite, and cdl_chain_solve's residual check
+ *   (which treats a non-finite residual as divergence) stops it with
+ *   CDL_ERR_NOT_CONVERGED.
  * a_dtype: must be CDL_F64 (A is always produced in float64).
  * A:  device, n x n float64 output. D: device, n float64 output.
  * vol, sigma_out: device, one float64 each (sigma_out receives the sigma used).
