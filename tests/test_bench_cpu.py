@@ -42,3 +42,29 @@ def test_reference_arm_other_ranks_do_no_work():
 def test_warmup_below_three_is_refused():
     r = _run({}, "--warmup", "2")
     assert r.returncode != 0 and "--warmup must be >= 3" in r.stderr
+
+
+def test_clock_sampler_parses_nvidia_smi(tmp_path, monkeypatch):
+    """The clocks record of a bench line: median SM clock, maximum, and the
+    throttle reasons seen active, from nvidia-smi's CSV (a stand-in script
+    prints three samples here)."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '1965, 2070, 1200.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '2010, 2070, 1150.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+        s = bench.ClockSampler(0)
+        import time
+        time.sleep(1.0)
+        rec = s.stop()
+    finally:
+        sys.path.remove(ROOT)
+    assert rec["samples"] == 3
+    assert rec["sm_mhz"] == 2010.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"]
