@@ -186,7 +186,9 @@ int cdl_ctx_create(cdl_ctx** out, int device, void* cuda_stream, size_t ws_cap_b
   if (!out) return CDL_ERR_INVALID_ARG;
   *out = nullptr;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+  const cudaError_t de = cudaGetDeviceCount(&ndev);
+  if (de != cudaSuccess) {
+    set_last_error(cudaGetErrorString(de), __FILE__, __LINE__);
     cudaGetLastError();
     return CDL_ERR_CUDA;
   }

@@ -75,3 +75,32 @@ def test_binding_constants_match_the_header():
     wrong = {k: (v, getattr(cdl, k, None)) for k, v in consts.items() if getattr(cdl, k, None) != v}
     assert not wrong, wrong
     assert len(cdl.KERNEL_CLASSES) == consts["CDL_KC_HOST_LINK"]   # the kernel classes precede the copy class
+
+
+def test_every_entry_point_rejects_null_arguments_without_a_gpu(lib):
+    """Each entry point called with null pointers and zero sizes returns
+    CDL_ERR_INVALID_ARG before touching CUDA; the two release calls accept
+    null. Context creation on a machine without a usable device reports
+    CDL_ERR_CUDA with the runtime's message and leaves the handle null."""
+    from paper_1802_05421_gb300 import cdl
+    release = {"cdl_ctx_destroy", "cdl_chain_free"}
+    wrong = {}
+    for name, args in cdl._SIGS.items():
+        vals = []
+        for a in args:
+            if a is ctypes.c_double:
+                vals.append(0.0)
+            elif a in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_uint64):
+                vals.append(0)
+            else:
+                vals.append(None)
+        r = getattr(cdl._lib, name)(*vals)
+        want = cdl.CDL_OK if name in release else cdl.CDL_ERR_INVALID_ARG
+        if r != want:
+            wrong[name] = r
+    assert not wrong, wrong
+    import torch
+    if not torch.cuda.is_available():
+        h = ctypes.c_void_p()
+        assert cdl._lib.cdl_ctx_create(ctypes.byref(h), 0, None, 0) == cdl.CDL_ERR_CUDA
+        assert h.value is None and cdl.cdl_last_error_detail()
