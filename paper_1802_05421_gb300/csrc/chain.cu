@@ -14,6 +14,7 @@
 
 #include "ff.cuh"
 #include "internal.h"
+#include "tiles.cuh"
 
 namespace cdl {
 namespace {
@@ -293,17 +294,6 @@ __global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict_
   }
 }
 
-__device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
-  double fnb = nb + 0.5;
-  int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
-  if (r < 0) r = 0;
-  if (r > nb - 1) r = nb - 1;
-  auto off = [nb](long long b) { return b * nb - b * (b - 1) / 2; };
-  while (r > 0 && off(r) > t) --r;
-  while (r + 1 < nb && off(r + 1) <= t) ++r;
-  bi = r;
-  bj = r + (int)(t - off(r));
-}
 
 // C = P^T Q on CUDA cores: C[m][c] = sum_k P[k][m] Q[k][c]; P is K x M and Q
 // is K x N, both row-major, so both tiles are contiguous k-major slabs.

@@ -14,6 +14,7 @@
 
 #include "ff.cuh"
 #include "internal.h"
+#include "tiles.cuh"
 
 namespace cdl {
 namespace {
@@ -98,29 +99,6 @@ __global__ void __launch_bounds__(256) k_row_norms(const double* __restrict__ X,
   if (lane == 0) norms[row] = acc;
 }
 
-__device__ __forceinline__ void tri_index(long long t, int nb, int& bi, int& bj) {
-  // t enumerates (bi, bj), bi <= bj, row by row; row bi starts at
-  // off(bi) = bi*nb - bi*(bi-1)/2.
-  double fnb = nb + 0.5;
-  int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
-  if (r < 0) r = 0;
-  if (r > nb - 1) r = nb - 1;
-  auto off = [nb](long long b) { return b * nb - b * (b - 1) / 2; };
-  while (r > 0 && off(r) > t) --r;
-  while (r + 1 < nb && off(r + 1) <= t) ++r;
-  bi = r;
-  bj = r + (int)(t - off(r));
-}
-
-// tri_index of the block's own tile, formed once (thread 0: it takes a float64
-// square root) and shared; every thread of the block must call it.
-__device__ __forceinline__ void block_tri_index(int nb, int& bi, int& bj) {
-  __shared__ int tile[2];
-  if (threadIdx.x == 0) tri_index(blockIdx.x, nb, tile[0], tile[1]);
-  __syncthreads();
-  bi = tile[0];
-  bj = tile[1];
-}
 
 // Exact squared distances on the 2^-16 grid: int64 sums of squared int32
 // differences, written as float64 multiples of 2^-32 to both (i,j) and (j,i).

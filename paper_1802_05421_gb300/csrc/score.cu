@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "tiles.cuh"
 
 namespace cdl {
 namespace {
@@ -108,27 +109,6 @@ __global__ void k_score_prep64(const double* __restrict__ Z1, const double* __re
   score_prep64(Z1, Z2, vol1, vol2, n, k, aT, bT, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
 }
 
-__device__ __forceinline__ void tri_index(int t, int nb, int& bi, int& bj) {
-  double fnb = nb + 0.5;
-  int r = (int)floor(fnb - sqrt(fnb * fnb - 2.0 * (double)t));
-  if (r < 0) r = 0;
-  if (r > nb - 1) r = nb - 1;
-  auto off = [nb](long long b) { return b * nb - b * (b - 1) / 2; };
-  while (r > 0 && off(r) > t) --r;
-  while (r + 1 < nb && off(r + 1) <= t) ++r;
-  bi = r;
-  bj = r + (int)(t - off(r));
-}
-
-// tri_index of the block's own tile, formed once (thread 0: it takes a float64
-// square root) and shared; every thread of the block must call it.
-__device__ __forceinline__ void block_tri_index(int nb, int& bi, int& bj) {
-  __shared__ int tile[2];
-  if (threadIdx.x == 0) tri_index(blockIdx.x, nb, tile[0], tile[1]);
-  __syncthreads();
-  bi = tile[0];
-  bj = tile[1];
-}
 
 // Per-tile accumulation of |A1 - A2| |c2 - c1| into row and column partials.
 __device__ __forceinline__ void tile_finish(const double* __restrict__ A1, const double* __restrict__ A2,
