@@ -575,3 +575,53 @@ def test_gmm_commute_time_error_matches_jl_spread():
     med = np.median(np.abs(rel))
     expect = 0.6745 * math.sqrt(2.0 / k)
     assert 0.75 * expect < med < 1.25 * expect
+
+
+def test_richardson_error_matches_the_spectral_form():
+    """Alg. 2's EstimateSolution: with chi = P1 b = P1 L z*, the error after j
+    updates is (I - P1 L)^j z*, and I - P1 L = D^{-1/2} S^{2^d} D^{1/2}. So, with
+    w = D^{1/2} z* written in the eigenvectors of S = D^{-1/2} A D^{-1/2}, the
+    D-norm error after q - 1 updates is |Lambda^{2^d (q-1)} c| / |c|, bounded by
+    the second largest |eigenvalue| to the power 2^d (q-1): the depth d and the
+    update count q trade off exactly as the telescoping product says."""
+    n = 30
+    A = _random_graph(n, 21, lo=0.2)
+    D = A.sum(1)
+    r = 1.0 / np.sqrt(D)
+    lam, V = np.linalg.eigh(r[:, None] * A * r[None, :])
+    lam2 = np.sort(np.abs(lam))[-2]                      # the largest is 1
+    b = O.project(A, 5, 3)
+    zs = O.exact_embedding(A, b)
+    c = V.T @ (np.sqrt(D)[:, None] * zs)
+    L = O.laplacian(A)
+
+    def dnorm(x):
+        return float(np.sqrt(np.einsum("ij,i,ij->", x, D, x)))
+
+    for d in (1, 2, 3):
+        P1, P2 = O.chain_product(L, d)
+        for q in (2, 3, 4):
+            y = O.estimate_solution(P1, P2, b, q)
+            err = dnorm(zs - y) / dnorm(zs)
+            p = 2 ** d * (q - 1)
+            pred = float(np.linalg.norm((lam[:, None] ** p) * c) / np.linalg.norm(c))
+            assert abs(err - pred) <= 1e-8 * pred + 1e-13, (d, q, err, pred)
+            assert err <= lam2 ** p * (1 + 1e-9) + 1e-13
+
+
+def test_projected_commute_times_error_scales_with_k():
+    """The JL estimate's relative error shrinks as sqrt(2/k) (Sec. 4.2.2: the
+    embedding dimension dominates the accuracy): the median relative error of
+    the projected commute times is near 0.674 sqrt(2/k) for k = 16, 64, 256."""
+    n = 60
+    A = _random_graph(n, 22)
+    exact = O.commute_times_pinv(A)
+    off = ~np.eye(n, dtype=bool)
+    meds = []
+    for k in (16, 64, 256):
+        Z = O.exact_embedding(A, O.project(A, 77, k))
+        rel = np.abs(O.commute_times(Z, A.sum()) - exact)[off] / exact[off]
+        med = float(np.median(rel))
+        meds.append(med)
+        assert 0.6 * 0.674 * math.sqrt(2 / k) < med < 1.5 * 0.674 * math.sqrt(2 / k), (k, med)
+    assert meds[0] > meds[1] > meds[2]
