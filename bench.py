@@ -116,6 +116,71 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- phase rooflines
+def phase_rooflines(kc, n, pk, src, sm_count, sm_mhz):
+    """Every phase of one pair against the roofline that binds it, from the
+    library's per-class CUDA-event times (kc: class -> ms_per_step, work per
+    launch, launches per step). Algorithmic work per pair:
+      distance    8 n^2 bytes written per graph (float64 squared distances,
+                  both triangles)                                     -> HBM
+      select      bytes the radix-select passes read (library count) -> HBM
+      kernel      bytes the kernel-value pass moves (library count)  -> HBM
+      chain_init  bytes level-0 formation moves (library count)      -> HBM
+      square      n^2 (n + 1) flops per squaring (library count)     -> bf16 tensor
+      project     n (n - 1) k signed adds per graph (library count)  -> one float32
+                  add per term on every lane: SMs x 128 x clock
+      apply       bytes of chain levels (and A operands) read        -> HBM
+      residual    bf16 slice-product flops of the exact residual     -> bf16 tensor
+      score       8 n (n - 1) bytes: the upper halves of float64 A1, A2 -> HBM
+    A phase's time includes its small helper kernels."""
+    hbm = pk.get("hbm_gbs")
+    bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    alu = sm_count * 128 * sm_mhz * 1e6 / 1e12     # T adds/s
+    spec = {
+        "distance": ("hbm", 2 * 8.0 * n * n),
+        "select": ("hbm", None),
+        "kernel": ("hbm", None),
+        "chain_init": ("hbm", None),
+        "square": ("tensor", None),
+        "project": ("alu", None),
+        "apply": ("hbm", None),
+        "residual": ("tensor", None),
+        "score": ("hbm", 8.0 * n * (n - 1)),
+    }
+    out = {}
+    for name, (bound, work) in spec.items():
+        v = kc.get(name)
+        if not v or not v["ms_per_step"]:
+            continue
+        if work is None:
+            work = v["work"] * v["launches"]
+        sec = v["ms_per_step"] * 1e-3
+        if bound == "hbm":
+            ach, peak, unit, ps = work / sec / 1e9, hbm, "GB/s", f"{src} hbm_gbs"
+        elif bound == "tensor":
+            ach, peak, unit, ps = work / sec / 1e12, bf16, "TFLOP/s", f"{src} bf16_tflops_sustained"
+        else:
+            ach, peak, unit = work / sec / 1e12, alu, "T adds/s"
+            ps = f"{sm_count} SMs x 128 float32 lanes x {sm_mhz:.0f} MHz"
+        out[name] = {"bound": bound, "ms_per_pair": round(v["ms_per_step"], 3), "work_per_pair": work,
+                     "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak if peak else None,
+                     "peak_source": ps}
+    return out
+
+
+def config1_oracle_full():
+    """The float64 oracle on the whole of the small pair (n = 1024, T = 64,
+    k = 32, top-10; exact embeddings), timed in full: a CPU baseline that is
+    measured, not extrapolated."""
+    from oracle import caddelag as O
+    from workloads import iid_pair
+    wl = iid_pair(1024, 64, 10, seed=0)
+    t0 = time.perf_counter()
+    out = O.caddelag_pair(wl.X[0], wl.X[1], 32, 0, 10)
+    sec = time.perf_counter() - t0
+    return sec, [int(i) for i in out["top"]], wl
+
+
 # ---------------------------------------------------------------- CPU oracle
 def oracle_sample(wl, budget_rows: int = 24, chol_n: int = 4096):
     """Time the float64 oracle on a bounded sample of one pair and scale each
@@ -185,21 +250,33 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = make_workload()
-    times = []
+    walls, est = [], []
     for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         t, desc, _ = oracle_sample(wl, budget_rows=8, chol_n=2048)
+        wall = time.perf_counter() - t0
         if s >= args.warmup:
-            times.append(t)
-    sec = statistics.median(times)
+            walls.append(wall)
+            est.append(t)
+    sec = statistics.median(est)        # extrapolated seconds for one whole pair
     value = 1.0 / sec
+    c1_sec, _, _ = config1_oracle_full()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": statistics.median(walls) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_GRID[0] * N_GRID[1], "T": T_LEN, "k": K_PROJ,
                        "d": D_CHAIN, "solver": "oracle exact (dense Cholesky)"},
+            "step_definition": "one bounded sample of the pair (8 rows of both graphs, Cholesky at n = 2048); "
+                               "ms_per_step is its wall time",
+            "value_basis": "extrapolated: each sampled phase scaled to the whole pair (rows by n / 8, "
+                           "the Cholesky by (n / 2048)^3)",
+            "extrapolated_ms_per_pair": sec * 1e3,
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc,
+                             "measured_full_pair_n1024": {"workload": "iid_n1024 (n = 1024, T = 64, k = 32, "
+                                                                      "top-10, exact embeddings)",
+                                                          "seconds": c1_sec, "pairs_per_s": 1.0 / c1_sec}},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -293,6 +370,17 @@ def run_batched(args):
     torch.cuda.set_device(local)
     from paper_1802_05421_gb300 import build as B
     B.build()
+    line = batched_measure(args.steps, args.warmup, args.e2e_steps, dist, world, local, sample_clocks=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def batched_measure(steps, warmup, e2e_steps, dist, world, local, sample_clocks):
+    """Time the batched workload (see run_batched) and return its JSON record."""
+    import torch
     from paper_1802_05421_gb300 import cdl
     from workloads import ragged_pairs
     pairs = ragged_pairs(G=64, n_lo=256, n_hi=4096, T=64, seed=7)
@@ -321,25 +409,25 @@ def run_batched(args):
             raise RuntimeError(f"cdl_caddelag_batched: {cdl.cdl_status_string(r)} {cdl.cdl_last_error_detail()}")
 
     og = opts(1)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         call(og)
     torch.cuda.synchronize()
     _, l0 = cdl.cdl_ctx_launch_count(ctx)
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local) if sample_clocks else None
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         call(og)
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = sampler.stop()
-    step_ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop() if sampler else None
+    step_ms = ev0.elapsed_time(ev1) / steps
     _, l1 = cdl.cdl_ctx_launch_count(ctx)
     iters = [stats[g].iters for g in range(2 * G)]
     rel_res = max(stats[g].rel_res for g in range(2 * G))
@@ -376,45 +464,41 @@ def run_batched(args):
     call(oh, h1.data_ptr(), h2.data_ptr(), hF.data_ptr(), ht.data_ptr())   # records the graph for host I/O
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         call(oh, h1.data_ptr(), h2.data_ptr(), hF.data_ptr(), ht.data_ptr())
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
     same_top = ht.tolist() == top.cpu().tolist()
     step_ms, e2e_s = rank_max([step_ms, e2e_s], dist, "cuda")
-    if rank == 0:
-        pk, src = peaks()
-        sq = kc["square"]
-        achieved = sq["work"] / (sq["ms_per_launch"] * 1e-3) / 1e12 if sq["ms_per_launch"] else 0.0
-        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        line = {
-            "metric": BATCH_METRIC, "value": world * G * 1000.0 / step_ms, "unit": "pairs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "pairs": G, "n_min": int(n.min()), "n_max": int(n.max()),
-                       "sum_n": N, "T": T, "k": BATCH_K, "d": BATCH_D, "topk": BATCH_TOPK, "score": "f32",
-                       "refine_rel_tol": BATCH_TOL, "solve_iters_max": max(iters), "rel_res_max": rel_res,
-                       "cuda_graph": True, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: each step writes 2 x 64 chains of 10 bf16 levels (about 30 GB), "
-                             "far larger than the 129 MB L2"},
-            "roofline": {"kernel": "k_tc_gemm grouped squaring (one launch per level over 128 graphs)",
-                         "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if peak else None, "traffic": None,
-                         "peak_source": f"{src} bf16_tflops_sustained",
-                         "work_per_launch": sq["work"], "ms_per_launch": sq["ms_per_launch"],
-                         "timed": "one eager call with per-launch CUDA events"},
-            "cpu_baseline": None,
-            "e2e": {"value": world * G / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 2 * N * T * 8,
-                    "d2h_bytes_per_step": N * 8 + G * BATCH_TOPK * 8, "same_top_as_device_run": same_top},
-            "gpu_launches": int((l1 - l0) // args.steps),
-            "clocks": clocks,
-            "autotuner": tuning,
-            "eager_phases_ms": {k: round(v["ms"], 3) for k, v in kc.items()},
-        }
-        print(json.dumps(line), flush=True)
+    pk, src = peaks()
+    sq = kc["square"]
+    achieved = sq["work"] / (sq["ms_per_launch"] * 1e-3) / 1e12 if sq["ms_per_launch"] else 0.0
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    line = {
+        "metric": BATCH_METRIC, "value": world * G * 1000.0 / step_ms, "unit": "pairs/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "pairs": G, "n_min": int(n.min()), "n_max": int(n.max()),
+                   "sum_n": N, "T": T, "k": BATCH_K, "d": BATCH_D, "topk": BATCH_TOPK, "score": "f32",
+                   "refine_rel_tol": BATCH_TOL, "solve_iters_max": max(iters), "rel_res_max": rel_res,
+                   "cuda_graph": True, "parallelism": f"replicas x{world}",
+                   "l2": "no flush: each step writes 2 x 64 chains of 10 bf16 levels (about 30 GB), "
+                         "far larger than the 129 MB L2"},
+        "roofline": {"kernel": "k_tc_gemm grouped squaring (one launch per level over 128 graphs)",
+                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_source": f"{src} bf16_tflops_sustained",
+                     "work_per_launch": sq["work"], "ms_per_launch": sq["ms_per_launch"],
+                     "timed": "one eager call with per-launch CUDA events"},
+        "cpu_baseline": None,
+        "e2e": {"value": world * G / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 2 * N * T * 8,
+                "d2h_bytes_per_step": N * 8 + G * BATCH_TOPK * 8, "same_top_as_device_run": same_top},
+        "gpu_launches": int((l1 - l0) // steps),
+        "clocks": clocks,
+        "autotuner": tuning,
+        "eager_phases_ms": {k: round(v["ms"], 3) for k, v in kc.items()},
+    }
     cdl.cdl_ctx_destroy(ctx)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------- host levels
@@ -1013,6 +1097,37 @@ def main():
                  "same_top": tt.cpu().tolist() == top.cpu().tolist(),
                  "max_rel_diff_F_vs_full_chain": float(((Ft - F).abs() / F).max())}
 
+    # the small pair (n = 1024, T = 64, k = 32, d = 8) on the float64 path, whole
+    c1 = None
+    if args.compare_f32 and args.chain == "bf16":
+        from workloads import iid_pair
+        w1 = iid_pair(1024, 64, 10, seed=0)
+        x1s, x2s = torch.from_numpy(w1.X[0]).cuda(), torch.from_numpy(w1.X[1]).cuda()
+        F1 = torch.empty(1024, dtype=torch.float64, device="cuda")
+        t1 = torch.empty(TOPK, dtype=torch.int64, device="cuda")
+        o1 = cdl.cdl_pair_opts(32, 8, cdl.CDL_F64, cdl.CDL_F64, 0, 0.0, cdl.cdl_solve_opts(40, REL_TOL, 0), TOPK, 0)
+        ctx1 = cdl.cdl_ctx_create(local, stream.cuda_stream, 0)[1]
+        for _ in range(3):
+            r = cdl.cdl_caddelag_pair(ctx1, x1s, x2s, 1024, 64, o1, F1, t1, s1, s2)
+            assert r == 0, cdl.cdl_status_string(r)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            cdl.cdl_caddelag_pair(ctx1, x1s, x2s, 1024, 64, o1, F1, t1, s1, s2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cdl.cdl_ctx_destroy(ctx1)
+        c1 = {"workload": "iid_n1024 (n = 1024, T = 64, k = 32, d = 8, float64 chain and scores, top-10)",
+              "ms_per_pair": e0.elapsed_time(e1) / 5, "top": t1.cpu().tolist()}
+
+    # the batched form (64 ragged pairs), a shorter run of --workload batched
+    batched = None
+    if args.compare_f32 and args.chain == "bf16":
+        b = batched_measure(5, 3, 1, dist, world, local, sample_clocks=False)
+        batched = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config",
+                                     "roofline", "e2e", "gpu_launches", "autotuner")}
+
     # max over ranks
     step_ms, e2e_s = rank_max([step_ms, e2e_s], dist, "cuda")
     value = pairs_per_second(step_ms, world)
@@ -1037,8 +1152,18 @@ def main():
         if not args.no_cpu_baseline:
             sec, desc, phases = oracle_sample(wl)
             cpu = {"value": 1.0 / sec, "unit": "pairs/s", "cores": cpu_cores(), "kind": "oracle",
-                   "sample": desc, "seconds_per_pair": sec,
+                   "sample": desc, "seconds_per_pair": sec, "value_basis": "extrapolated from the sample",
                    "phases_s": {k: round(v, 2) for k, v in phases.items()}}
+            c1_sec, c1_top, _ = config1_oracle_full()
+            cpu["measured_full_pair_n1024"] = {"workload": "iid_n1024 (n = 1024, T = 64, k = 32, top-10, "
+                                                           "exact embeddings)",
+                                               "seconds": c1_sec, "pairs_per_s": 1.0 / c1_sec}
+            if c1 is not None:
+                c1["oracle_s"] = c1_sec
+                c1["same_top_as_oracle"] = c1["top"] == c1_top
+        props = torch.cuda.get_device_properties(local)
+        phases_roof = phase_rooflines(kc, n, pk, src, props.multi_processor_count,
+                                      float(pk.get("sm_max_mhz", 2070.0)))
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -1051,9 +1176,12 @@ def main():
                              "chain levels, far larger than the 129 MB L2"},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "phase_rooflines": phases_roof,
             "f32_path": f32,
             "fp8_tile_path": fp8t,
             "truncated_chain_path": trunc,
+            "batched_path": batched,
+            "small_pair_f64_path": c1,
             "e2e": {"value": pairs_per_second(e2e_s * 1000.0, world), "unit": "pairs/s",
                     "h2d_bytes_per_step": 2 * n * T * 8,
                     "d2h_bytes_per_step": n * 8 + TOPK * 8, "same_top_as_device_run": same_top},

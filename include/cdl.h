@@ -166,10 +166,15 @@ int cdl_build_graph(cdl_ctx* ctx, const double* X, int64_t n, int32_t T, double 
  * process exits. Work is enqueued on `cuda_stream` (NULL = legacy default
  * stream) on the CURRENT device, which must own X and the outputs.
  * Limit: n * T <= 2^20 (e.g. n = 4096 with T = 256); larger inputs return
- * CDL_ERR_INVALID_ARG before launching anything. Other limits and argument
- * meanings as for cdl_build_graph.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.
+ * CDL_ERR_INVALID_ARG before launching anything. X and the outputs may be
+ * device memory of the current device or managed memory, 8-byte aligned.
+ * Other limits and argument meanings as for cdl_build_graph.
+ * Each CUDA context has its own copy of the array at its own address: the
+ * first call in a context (with that context current) looks the address up
+ * and caches it under the context's unique ID, so a context the caller
+ * makes current through the driver API, or a primary context re-created
+ * after cudaDeviceReset, gets its own lookup. Make the first call in each
+ * context before any stream capture.
  * Every call uses the same array: calls that may overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. */
 int cdl_build_graph_static(const double* X, int64_t n, int32_t T, double sigma, double* A,
@@ -346,8 +351,13 @@ typedef struct {
  * CDL_SOLVE_FULL_RESIDUAL forms it in float-float after every application.
  * Synchronises once per application to read the residual norm.
  * chain: from cdl_chain_build on the same graph. A: device n x n (CDL_F64).
- * Y: device n x k float64. Z: device n x k float64 output; k <= 128 for
- * tensor-core chains (CDL_ERR_UNSUPPORTED above), k <= 1024 otherwise.
+ * Y: device n x k float64. Z: device n x k float64 output; 1 <= k <= 1024.
+ * Tensor-core chains apply a level to at most 128 columns at a time, so
+ * with k > 128 they solve the columns as independent blocks of at most 128
+ * (the iteration acts on each column on its own): each block stops on its
+ * own test against its own ||Y_b||; stats then give the residual of all k
+ * columns, the largest block iteration count and, per step, the blocks'
+ * combined residual (a block that stopped earlier counts with its last).
  * stats: host, may be NULL. Returns CDL_ERR_NOT_CONVERGED (Z still written)
  * when rel_tol > 0 was not reached within max_iter applications, and stops
  * early with it when the residual is not finite or exceeds 1e6 ||Y|| (a

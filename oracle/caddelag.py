@@ -404,6 +404,31 @@ def node_scores(A1, A2, Z1, Z2, vol1, vol2, rows: Optional[Sequence[int]] = None
     return F
 
 
+def node_scores_c(A1_rows, A2_rows, rows: Sequence[int], Z1, Z2, vol1: float, vol2: float) -> np.ndarray:
+    """``node_scores`` for rows ``rows`` computed by the oracle's plain C
+    version (oracle/cscore.c: the same definition, direct differences, OpenMP
+    over rows) for large graphs. A1_rows and A2_rows hold exactly the
+    requested rows. Pinned against ``node_scores`` in the tests."""
+    import ctypes
+    from . import cbuild
+    lib = ctypes.CDLL(cbuild.build())
+    A1_rows = np.ascontiguousarray(np.atleast_2d(A1_rows), dtype=np.float64)
+    A2_rows = np.ascontiguousarray(np.atleast_2d(A2_rows), dtype=np.float64)
+    rows = np.ascontiguousarray(np.asarray(list(rows), dtype=np.int64))
+    Z1 = np.ascontiguousarray(Z1, dtype=np.float64)
+    Z2 = np.ascontiguousarray(Z2, dtype=np.float64)
+    n, k = Z1.shape
+    if A1_rows.shape != (rows.size, n) or A2_rows.shape != (rows.size, n) or Z2.shape != (n, k):
+        raise ValueError("shape mismatch")
+    F = np.empty(rows.size)
+    P = ctypes.c_void_p
+    lib.cdl_oracle_node_scores.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, P]
+    lib.cdl_oracle_node_scores(A1_rows.ctypes.data, A2_rows.ctypes.data, rows.ctypes.data, rows.size, n,
+                               Z1.ctypes.data, Z2.ctypes.data, k, float(vol1), float(vol2), F.ctypes.data)
+    return F
+
+
 def upper_edge_scores(A1, A2, Z1, Z2, vol1, vol2) -> np.ndarray:
     """Delta E_ij for every edge i < j (Sec. 2; Alg. 4), as an n x n array
     holding the upper triangle (zero on and below the diagonal)."""

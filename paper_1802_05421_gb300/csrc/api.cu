@@ -528,7 +528,6 @@ int cdl_chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const void* A, cdl_dtype 
     return CDL_ERR_INVALID_ARG;
   if (a_dtype != CDL_F64) return CDL_ERR_UNSUPPORTED;
   if (ch->device != ctx->device) return CDL_ERR_INVALID_ARG;
-  if (ch->dtype != CDL_F64 && ch->dtype != CDL_F32 && k > 128) return CDL_ERR_UNSUPPORTED;   // tensor-core apply: N = 2 kp <= 256
   CDL_TRY(set_device(ctx));
   CDL_TRY(dev_ptr(ctx, A));
   CDL_TRY(dev_ptr(ctx, Y));

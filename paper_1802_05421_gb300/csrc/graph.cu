@@ -916,27 +916,79 @@ static __device__ __align__(256) unsigned char g_graph_scratch[STATIC_SCRATCH_BY
 
 namespace {
 
-constexpr int MAX_DEVICES = 64;
+// The device address of g_graph_scratch belongs to the CUDA context that was
+// current when it was looked up: another context on the same device (one the
+// caller made current through the driver API, or the primary context
+// re-created after cudaDeviceReset) has its own copy of the array at another
+// address. So the address is cached per context, keyed by the context's
+// unique ID (cuCtxGetId: IDs are never reused within a process), and the
+// host-side name of the array, which is only a stand-in for the symbol, is
+// never passed to a kernel.
+constexpr int MAX_CONTEXTS = 64;
 std::mutex g_static_mu;
-void* g_static_addr[MAX_DEVICES] = {nullptr};
+unsigned long long g_static_ctx_id[MAX_CONTEXTS] = {0};
+void* g_static_addr[MAX_CONTEXTS] = {nullptr};
+int g_static_used = 0;
 
-// Device address of g_graph_scratch on the current device. The host-side
-// name is only a stand-in for the symbol, so the address is looked up once
-// per device (with that device current) and cached.
-int static_scratch(void** out) {
-  int dev = 0;
-  CDL_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= MAX_DEVICES) return CDL_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+typedef int (*PFN_ctx_get_current)(void** ctx);
+typedef int (*PFN_ctx_get_id)(void* ctx, unsigned long long* id);
+
+// ID of the current CUDA context. Driver entry points are taken through the
+// runtime, so the library does not link libcuda itself.
+int current_context_id(unsigned long long* id) {
+  static PFN_ctx_get_current get_current = nullptr;
+  static PFN_ctx_get_id get_id = nullptr;
+  if (!get_current || !get_id) {
     void* p = nullptr;
-    CDL_CUDA_TRY(cudaGetSymbolAddress(&p, g_graph_scratch));
-    g_static_addr[dev] = p;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return CDL_ERR_CUDA;
+    get_current = reinterpret_cast<PFN_ctx_get_current>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return CDL_ERR_CUDA;
+    get_id = reinterpret_cast<PFN_ctx_get_id>(p);
   }
-  *out = g_static_addr[dev];
+  // the pointer checks before this call have already made the runtime's
+  // context current when the caller had none
+  void* c = nullptr;
+  if (get_current(&c) != 0 || !c) {
+    set_last_error("no current CUDA context", __FILE__, __LINE__);
+    return CDL_ERR_CUDA;
+  }
+  if (get_id(c, id) != 0) {
+    set_last_error("cuCtxGetId failed", __FILE__, __LINE__);
+    return CDL_ERR_CUDA;
+  }
   return CDL_OK;
 }
 
+// Device address of g_graph_scratch in the current context, looked up with
+// that context current on the first call in it and cached.
+int static_scratch(void** out) {
+  unsigned long long id = 0;
+  CDL_TRY(current_context_id(&id));
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  for (int i = 0; i < g_static_used; ++i)
+    if (g_static_ctx_id[i] == id) {
+      *out = g_static_addr[i];
+      return CDL_OK;
+    }
+  void* p = nullptr;
+  CDL_CUDA_TRY(cudaGetSymbolAddress(&p, g_graph_scratch));
+  // a full table starts over: the contexts it names may be gone, and a
+  // lookup costs one symbol query
+  if (g_static_used == MAX_CONTEXTS) g_static_used = 0;
+  g_static_ctx_id[g_static_used] = id;
+  g_static_addr[g_static_used] = p;
+  ++g_static_used;
+  *out = p;
+  return CDL_OK;
+}
+
+// Device or managed memory reachable from the current device (the same
+// rule as the context-based entry points).
 int on_current_device(const void* p) {
   if (!p) return CDL_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(p) % 8) return CDL_ERR_INVALID_ARG;
@@ -947,7 +999,8 @@ int on_current_device(const void* p) {
     cudaGetLastError();
     return CDL_ERR_INVALID_ARG;
   }
-  if (at.type != cudaMemoryTypeDevice || at.device != dev) return CDL_ERR_INVALID_ARG;
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return CDL_ERR_INVALID_ARG;
+  if (at.type == cudaMemoryTypeDevice && at.device != dev) return CDL_ERR_INVALID_ARG;
   return CDL_OK;
 }
 

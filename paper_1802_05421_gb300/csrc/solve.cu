@@ -2,14 +2,28 @@
 // with the k right-hand sides of Alg. 3 processed together as in Sec. 4.1):
 //
 //   R_0 = Y, Z_0 = 0;  Z_{t+1} = Z_t + P R_t,  R_{t+1} = Y - L Z_{t+1},
-//   P R = D^{-1/2} (I + S~_{d-1}) ... (I + S~_0) D^{-1/2} R.
+//   P R = D^{-1/2} (I + S~_{d-1}) ... (I + S~_0) D^{-1/2} R,
 //
-// Starting from zero this is the paper's y_{t+1} = y_t - P2 y_t + chi with
-// chi = P1 b and P2 = P1 L. The paper fixes the step count q; here the loop
-// also stops once ||R||_F <= rel_tol ||Y||_F. The residual is recomputed from
-// Z every step (not updated recursively), in float-float arithmetic on the
-// float32 pipes (error-free products by fma and error-free sums), because
-// float64 runs at about 1/64 of the float32 rate on this GPU.
+// followed after every step by the shift of Z to D-weighted zero column
+// means. Starting from zero this is the paper's y_{t+1} = y_t - P2 y_t + chi
+// with chi = P1 b and P2 = P1 L. The paper fixes the step count q; here the
+// loop also stops once ||R||_F <= rel_tol ||Y||_F.
+//
+// Residual. The first step forms R = Y - D Z + A Z in full, to float64-class
+// accuracy: on tensor-core chains A Z comes from exact bf16 slices of A and
+// Z on the tensor cores with integer accumulation (k_tc_resid), on the
+// CUDA-core chains from float-float products and sums on the float32 pipes
+// (float64 runs at about 1/72 of the float32 rate on this GPU). Later steps
+// update it recursively, R -= D dZ - A dZ, on the tensor cores (bf16 hi + lo
+// operands) or in float32; each such update adds a bounded error (1e-5 of
+// the residual before it), summed as a drift bound. A recursive residual
+// that stops falling (less than halved) is formed again in full, and one
+// that meets the tolerance is certified by a full residual before the solve
+// stops, unless its drift bound is already below a tenth of the tolerance.
+// CDL_SOLVE_FULL_RESIDUAL forms it in full on every step.
+//
+// Tensor-core chains with k > 128 right-hand sides solve them as
+// independent column blocks of at most 128 (chain_solve at the end).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -787,8 +801,8 @@ inline unsigned blocks_for(size_t count, int threads) { return (unsigned)((count
 
 }  // namespace
 
-int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
-                const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats) {
+int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
+                      const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats, double* yy_out) {
   cudaStream_t st = ctx->stream;
   const int n = (int)ch->n, np = (int)ch->npad;
   const int kp = (int)round_up(k, 16);   // tensor-core N = 2 kp: multiple of 32
@@ -864,6 +878,7 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
 
   double yy = 0.0;
   CDL_TRY(sumsq(Y, nk, scal, &yy));
+  if (yy_out) *yy_out = yy;
   CDL_CUDA_TRY(cudaMemsetAsync(Z, 0, nk * 8, st));
   CDL_CUDA_TRY(cudaMemcpyAsync(R, Y, nk * 8, cudaMemcpyDeviceToDevice, st));
   if (stats) {
@@ -1083,6 +1098,88 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
   }
   if (!(rel <= 1e6)) return CDL_ERR_NOT_CONVERGED;
   return (opts->rel_tol > 0 && !(rel <= opts->rel_tol)) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
+}
+
+namespace {
+
+// columns c0 .. c0 + kb - 1 of the n x k matrix Y into the n x kb matrix Yb, and back
+__global__ void k_gather_cols(const double* __restrict__ Y, int n, int k, int c0, int kb, double* __restrict__ Yb) {
+  const size_t cnt = (size_t)n * kb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cnt; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / kb;
+    Yb[e] = Y[i * k + c0 + (e - i * kb)];
+  }
+}
+
+__global__ void k_scatter_cols(const double* __restrict__ Zb, int n, int kb, int c0, int k, double* __restrict__ Z) {
+  const size_t cnt = (size_t)n * kb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cnt; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / kb;
+    Z[i * k + c0 + (e - i * kb)] = Zb[e];
+  }
+}
+
+}  // namespace
+
+// The tensor-core apply multiplies a level by at most 128 right-hand sides
+// (MMA N = 2 kp <= 256 for the hi and lo halves). Alg. 2's Richardson
+// iteration and the chain apply act on each column on its own, so more
+// columns are solved as independent blocks of at most 128, each with its
+// own float64 residual and its own stopping test against its own ||Y_b||.
+// The reported residual is the one of all k columns,
+// sqrt(sum_b ||R_b||^2 / sum_b ||Y_b||^2), below rel_tol when every block
+// is; iters is the largest block count and history[t] combines the blocks'
+// residuals after t + 1 steps (a block that stopped earlier keeps its last).
+int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
+                const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats) {
+  const bool tensor = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3 || ch->dtype == CDL_FP8E4M3_T128;
+  if (!tensor || k <= 128) return chain_solve_block(ctx, ch, A, Y, k, opts, Z, stats, nullptr);
+  const int nblk = (k + 127) / 128;
+  const int kb_max = (int)round_up((k + nblk - 1) / nblk, 16);
+  const int n = (int)ch->n;
+  cudaStream_t st = ctx->stream;
+  void *vyb, *vzb;
+  CDL_TRY(ws_get(ctx, "solve.block_y", (size_t)n * kb_max * 8, &vyb));
+  CDL_TRY(ws_get(ctx, "solve.block_z", (size_t)n * kb_max * 8, &vzb));
+  double* Yb = static_cast<double*>(vyb);
+  double* Zb = static_cast<double*>(vzb);
+  const unsigned nb = (unsigned)std::min<size_t>(((size_t)n * kb_max + 255) / 256, (size_t)ctx->sm_count * 8);
+  double yy_all = 0.0, rr_all = 0.0;
+  double hist_rr[64] = {0};
+  int iters = 0, status = CDL_OK;
+  for (int c0 = 0; c0 < k; c0 += kb_max) {
+    const int kb = std::min(kb_max, k - c0);
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_gather_cols<<<nb, 256, 0, st>>>(Y, n, k, c0, kb, Yb);
+      CDL_TRY(L.done());
+    }
+    cdl_solve_stats sb;
+    double yy = 0.0;
+    const int r = chain_solve_block(ctx, ch, A, Yb, kb, opts, Zb, &sb, &yy);
+    if (r != CDL_OK && r != CDL_ERR_NOT_CONVERGED) return r;
+    if (r == CDL_ERR_NOT_CONVERGED) status = r;
+    {
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_scatter_cols<<<nb, 256, 0, st>>>(Zb, n, kb, c0, k, Z);
+      CDL_TRY(L.done());
+    }
+    yy_all += yy;
+    rr_all += sb.rel_res * sb.rel_res * yy;
+    iters = std::max(iters, sb.iters);
+    for (int t = 0; t < 64; ++t) {
+      const double h = t < sb.iters ? sb.history[t] : sb.rel_res;
+      hist_rr[t] += h * h * yy;
+    }
+  }
+  if (stats) {
+    stats->iters = iters;
+    stats->rel_res = yy_all > 0 ? std::sqrt(rr_all / yy_all) : 0.0;
+    for (int t = 0; t < 64; ++t)
+      stats->history[t] = (t < iters && yy_all > 0) ? std::sqrt(hist_rr[t] / yy_all) : 0.0;
+  }
+  CDL_CUDA_TRY(cudaStreamSynchronize(st));
+  return status;
 }
 
 void batch_residual_tile(int k, int* tm, int* tn) {

@@ -34,14 +34,22 @@ def G():
 
 
 def _oracle_pair(X1, X2, k, seed, topk):
-    """Alg. 4 on one pair with exact embeddings (projection by the oracle's C
-    version for speed)."""
+    """Alg. 4 on one pair with exact embeddings. For speed the projection and
+    the node scores come from the oracle's C versions, and the squared
+    distances of grid inputs from the oracle's exact-grid Gram form (the same
+    float64 numbers as the plain definition for these inputs)."""
     out = []
     for X in (X1, X2):
-        A, D, vol, sigma = O.gaussian_graph(X)
+        try:
+            d2 = O.squared_distances_exact_grid(X)
+        except ValueError:
+            d2 = None
+        A, D, vol, sigma = O.gaussian_graph(X, d2=d2)
         Y = O.project_rows_c(A, range(A.shape[0]), seed, k)
         out.append(dict(A=A, vol=vol, Z=O.exact_embedding(A, Y)))
-    F = O.node_scores(out[0]["A"], out[1]["A"], out[0]["Z"], out[1]["Z"], out[0]["vol"], out[1]["vol"])
+    n = X1.shape[0]
+    F = O.node_scores_c(out[0]["A"], out[1]["A"], range(n), out[0]["Z"], out[1]["Z"], out[0]["vol"],
+                        out[1]["vol"])
     return F, O.top_anomalies(F, topk)
 
 
@@ -99,6 +107,23 @@ def test_batched_matches_oracle(G, ragged, score):
     dt = cdl.CDL_F32 if score == "f32" else cdl.CDL_F64
     Fs, tops, stats = _run(G, ragged, d=10, topk=5, score=dt)
     _check(ragged, Fs, tops, stats, 5)
+
+
+def test_batched_64_ragged_pairs_full_size(G):
+    """The batched workload at its own size, as the benchmark runs it: 64 pairs
+    with n log-uniform in [256, 4096] (seed 7; drawn orders 258 ... 4045),
+    T = 64, 1-5 perturbed nodes each, k = 32, d = 10, bf16 chain, float32
+    scores, top-10, recorded as a CUDA graph with the autotuner's tiles and
+    replayed. Every pair against the oracle; the replay equals the recording
+    call bit for bit."""
+    cdl = G.cdl
+    pairs = ragged_pairs(G=64, n_lo=256, n_hi=4096, T=64, seed=7)
+    assert max(p.X[0].shape[0] for p in pairs) > 4000
+    Fs, tops, stats = _run(G, pairs, d=10, topk=10, score=cdl.CDL_F32, use_graph=1)
+    Fr, topr, statr = _run(G, pairs, d=10, topk=10, score=cdl.CDL_F32, use_graph=1)
+    for p in range(len(pairs)):
+        assert np.array_equal(Fs[p], Fr[p]) and list(tops[p]) == list(topr[p])
+    _check(pairs, Fr, topr, statr, 10)
 
 
 def test_batched_full_residual_flag(G, ragged):

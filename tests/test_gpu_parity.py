@@ -311,6 +311,54 @@ def test_solve_reports_not_converged(G):
     assert stats.iters == 1 and stats.rel_res > 1e-14
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "fp8t"])
+@pytest.mark.parametrize("k", [136, 192, 300])
+def test_solve_more_than_128_columns(G, dtype, k):
+    """Tensor-core chains apply a level to at most 128 right-hand sides at a
+    time; more columns are solved as independent column blocks (Alg. 2 acts on
+    each column on its own). k = 136 and 300 leave ragged blocks, 192 is the
+    projection dimension of the n = 131072 configuration. Checked against the
+    exact embedding L^+ Y, column by column and as a whole."""
+    cdl = G.cdl
+    n, tol = 700, 1e-10
+    X = iid_pair(n, 32, 1, seed=k).X[0]
+    Ao, Do, volo, _ = O.gaussian_graph(X)
+    Yo = O.project(Ao, 5, k)
+    Zo = O.exact_embedding(Ao, Yo)
+    A = torch.from_numpy(Ao).cuda()
+    D = torch.from_numpy(Do).cuda()
+    vol = torch.tensor([volo], dtype=torch.float64, device="cuda")
+    ch = G.chain(A, D, vol, 7, DT[dtype])
+    try:
+        Z, stats = G.solve(ch, A, torch.from_numpy(Yo).cuda(), max_iter=30, rel_tol=tol)
+    finally:
+        cdl.cdl_chain_free(ch)
+    Zg = _h(Z)
+    assert stats.rel_res <= tol and stats.iters >= 1
+    res = O.residual_norm(Ao, Yo, Zg)
+    assert res <= 3 * tol and abs(res - stats.rel_res) <= 0.1 * tol + 0.5 * stats.rel_res
+    for c in range(k):                     # every column block solved, none left at zero
+        assert np.linalg.norm(Zg[:, c] - Zo[:, c]) <= 100 * tol * np.linalg.norm(Zo[:, c])
+    assert np.abs(Do @ Zg).max() <= 1e-12 * np.abs(Zg).max() * Do.sum()
+    assert 0 < stats.history[stats.iters - 1] <= tol
+
+
+def test_pair_k192_bf16_matches_oracle(G):
+    """The whole pair (Alg. 4) with k = 192 on a bf16 chain, against the
+    oracle's exact embeddings."""
+    cdl = G.cdl
+    wl = iid_pair(600, 32, 4, seed=192)
+    k, seed, topk = 192, 11, 10
+    F, top, s1, s2 = G.pair(wl.X[0], wl.X[1], k, 8, cdl.CDL_BF16, cdl.CDL_F32, seed, topk, max_iter=40,
+                            rel_tol=1e-12)
+    ref = O.caddelag_pair(wl.X[0], wl.X[1], k, seed, topk)
+    Fo, topo = ref["F"], ref["top"]
+    assert s1.rel_res <= 1e-12 and s2.rel_res <= 1e-12
+    assert np.max(np.abs(F - Fo) / Fo) <= 1e-6
+    if O.min_relative_gap(Fo, topk) > 1e-5:
+        assert list(top) == list(topo)
+
+
 # ------------------------------------------------------------------ scores
 
 SCORE_DT = {"f64": "CDL_F64", "f32": "CDL_F32", "bf16": "CDL_BF16"}

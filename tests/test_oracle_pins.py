@@ -341,6 +341,34 @@ def test_chain_levels_are_powers():
     assert np.allclose(lv[3], np.linalg.matrix_power(S, 8), atol=1e-14)
 
 
+def test_chain_level0_is_the_normalised_adjacency():
+    """Level 0 of Alg. 2's ChainProduct is S = D^{-1/2} A D^{-1/2}: symmetric,
+    eigenvalue 1 with eigenvector D^{1/2} 1, the same spectrum as the random-
+    walk matrix D^{-1} A (similar to S), all eigenvalues in [-1, 1]; on the
+    unit-weight complete graph K_n it is (J - I) / (n - 1) exactly. A wrong
+    normalisation (D^{-1} A, A D^{-1}, D^{-1/2} A, a missing square root)
+    fails at least one of these; level i is S^{2^i} through S's own
+    eigenbasis (not by repeated products)."""
+    A = _random_graph(40, 21)
+    D = A.sum(1)
+    lv = O.chain_levels(A, 4)
+    S = lv[0]
+    assert np.allclose(S, S.T, rtol=4e-16, atol=0)        # (r_i A_ij) r_j vs (r_j A_ji) r_i
+    v = np.sqrt(D)
+    assert np.allclose(S @ v, v, rtol=0, atol=1e-14 * np.abs(v).max())
+    lam = np.linalg.eigvalsh(S)
+    rw = np.sort(np.linalg.eigvals(A / D[:, None]).real)
+    assert np.allclose(lam, rw, atol=1e-12)
+    assert abs(lam[-1] - 1.0) <= 1e-13 and lam[0] >= -1.0 - 1e-13
+    lam_all, V = np.linalg.eigh(S)
+    for i in (1, 2, 3):
+        assert np.allclose(lv[i], (V * lam_all ** (2 ** i)) @ V.T, atol=1e-13)
+    for n in (2, 5, 9):
+        Kn = np.ones((n, n)) - np.eye(n)
+        S0 = O.chain_levels(Kn, 1)[0]
+        assert np.allclose(S0, Kn / (n - 1), rtol=0, atol=1e-15)
+
+
 def test_literal_solver_converges_to_exact():
     A = _random_graph(60, 17, lo=0.3)
     Y = O.project(A, 8, 10)
@@ -393,6 +421,40 @@ def test_scores_brute_force_and_invariants():
     # centring shift leaves scores unchanged
     F2 = O.node_scores(A1, A2, Z1 + 3.0, Z2 - 1.0, v1, v2)
     assert np.allclose(F, F2, rtol=1e-9)
+
+
+def test_c_node_scores_match_brute_force_and_numpy():
+    """The oracle's C node scores (oracle/cscore.c) against scalar loops over
+    the definition (Alg. 4: F_i = sum_j |A1 - A2|_ij |c2 - c1|_ij with
+    c = vol ||z_i - z_j||^2) on a tiny pair, and against ``node_scores`` on a
+    larger one, on a subset of rows and on all of them."""
+    n, k = 9, 3
+    A1 = _random_graph(n, 24)
+    A2 = A1.copy()
+    A2[1, 6] = A2[6, 1] = A1[1, 6] * 2.5
+    A2[0, 3] = A2[3, 0] = 0.0
+    rng = np.random.default_rng(25)
+    Z1, Z2 = rng.standard_normal((n, k)), rng.standard_normal((n, k))
+    v1, v2 = 3.5, 0.75
+    Fc = O.node_scores_c(A1, A2, range(n), Z1, Z2, v1, v2)
+    for i in range(n):
+        ref = 0.0
+        for j in range(n):
+            if j == i:
+                continue
+            c1 = v1 * sum((Z1[i, r] - Z1[j, r]) ** 2 for r in range(k))
+            c2 = v2 * sum((Z2[i, r] - Z2[j, r]) ** 2 for r in range(k))
+            ref += abs(A1[i, j] - A2[i, j]) * abs(c2 - c1)
+        assert math.isclose(Fc[i], ref, rel_tol=1e-14, abs_tol=0.0)
+    assert set(np.nonzero(Fc)[0]) == {0, 1, 3, 6}
+    n, k = 300, 37
+    A1 = _random_graph(n, 26)
+    A2 = _random_graph(n, 27)
+    Z1, Z2 = rng.standard_normal((n, k)), rng.standard_normal((n, k))
+    F = O.node_scores(A1, A2, Z1, Z2, 2.0, 5.0)
+    assert np.allclose(O.node_scores_c(A1, A2, range(n), Z1, Z2, 2.0, 5.0), F, rtol=1e-13, atol=0)
+    rows = [299, 0, 17, 17, 150]
+    assert np.allclose(O.node_scores_c(A1[rows], A2[rows], rows, Z1, Z2, 2.0, 5.0), F[rows], rtol=1e-13, atol=0)
 
 
 def test_top_anomalies_ties_and_order():

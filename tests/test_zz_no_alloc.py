@@ -71,3 +71,59 @@ def test_static_graph_build_rejects_oversized_input():
     s = torch.zeros(2, dtype=torch.float64, device="cuda")
     assert cdl.cdl_build_graph_static(X, n, T, 0.0, A, s, s[0:1].data_ptr(), s[1:2].data_ptr(), None) == \
         cdl.CDL_ERR_INVALID_ARG
+
+
+def _cudart():
+    import ctypes
+    import glob
+    import os
+    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    for cand in ["libcudart.so"] + sorted(glob.glob(os.path.join(home, "lib64", "libcudart.so*"))) + \
+            sorted(glob.glob(os.path.join(home, "targets", "*", "lib", "libcudart.so*"))):
+        try:
+            return ctypes.CDLL(cand)
+        except OSError:
+            continue
+    pytest.skip("libcudart not found")
+
+
+def test_static_graph_build_accepts_managed_memory():
+    """Inputs and outputs in managed memory (cudaMallocManaged, made by the
+    caller) give the same results as device memory, as for the entry points
+    that take a context."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes
+    from gpu_util import lib
+    cdl = lib()
+    rt = _cudart()
+    X = iid_pair(500, 24, 2, seed=37).X[0]
+    n, T = X.shape
+    stream = torch.cuda.current_stream()
+    Xd = torch.from_numpy(X).cuda()
+    A0, D0, s0 = _outputs(n)
+    assert cdl.cdl_build_graph_static(Xd, n, T, 0.0, A0, D0, s0[0:1].data_ptr(), s0[1:2].data_ptr(),
+                                      stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    sizes = {"X": n * T * 8, "A": n * n * 8, "D": n * 8, "s": 2 * 8}
+    ptr = {}
+    try:
+        for k, b in sizes.items():
+            p = ctypes.c_void_p()
+            assert rt.cudaMallocManaged(ctypes.byref(p), ctypes.c_size_t(b), ctypes.c_uint(1)) == 0
+            ptr[k] = p.value
+        assert rt.cudaDeviceSynchronize() == 0
+        ctypes.memmove(ptr["X"], X.ctypes.data, sizes["X"])
+        assert cdl.cdl_build_graph_static(ptr["X"], n, T, 0.0, ptr["A"], ptr["D"], ptr["s"], ptr["s"] + 8,
+                                          stream.cuda_stream) == 0
+        torch.cuda.synchronize()
+        assert rt.cudaDeviceSynchronize() == 0
+
+        def view(k, count):
+            return np.ctypeslib.as_array(ctypes.cast(ptr[k], ctypes.POINTER(ctypes.c_double)), (count,)).copy()
+        assert np.array_equal(view("A", n * n).reshape(n, n), A0.cpu().numpy())
+        assert np.array_equal(view("D", n), D0.cpu().numpy())
+        assert np.array_equal(view("s", 2), s0.cpu().numpy())
+    finally:
+        for p in ptr.values():
+            rt.cudaFree(ctypes.c_void_p(p))
