@@ -240,10 +240,12 @@ int cdl_graph_add_edges(cdl_ctx* ctx, void* A, cdl_dtype a_dtype, int64_t n, int
  *   max |S~_0| and m_{i+1} = max_r |row r of S~_i|^2 bounds every entry of
  *   S~_i^2 (|(S S)_ab| <= |row a| |row b|; attained on the diagonal); a bf16
  *   copy of each level is kept for the solve's apply), or CDL_FP8E4M3_T128
- *   (e4m3 levels with one scale per 128 x 128 tile, scale = tile max / 448:
- *   each K-tile product runs on tcgen05 kind::f8f6f4 into TMEM and is added
- *   to float32 accumulators times s_IK s_KJ; the finished tile's maximum sets
- *   its scale; bf16 copies kept for the apply).
+ *   (e4m3 levels with one scale per 128 x 128 tile, a power of two: the
+ *   least 2^e with tile max <= 448 * 2^e; each squaring runs on tcgen05
+ *   kind::mxf8f6f4 with block scaling, the tensor core applying the tiles'
+ *   e8m0 scales to every 32-element K block, so the whole K range
+ *   accumulates in float32 in TMEM; the finished tile's maximum sets its
+ *   scale; bf16 copies kept for the apply).
  * flags: CDL_CHAIN_* below.
  * inout: if *inout is NULL a chain is allocated (cdl_chain_free releases it);
  *   if it points to a chain created with the same (n, d, chain_dtype) its
@@ -286,7 +288,8 @@ int cdl_chain_level(const cdl_chain* chain, int32_t i, void** level, int64_t* np
 int cdl_chain_apply_level(const cdl_chain* chain, int32_t i, void** level);
 /* CDL_FP8E4M3_T128 chains: device pointer to the nt x nt float32 tile scales
  * of level i (nt = npad / 128; value of tile (I, J) = scale[I nt + J] times
- * the stored e4m3 values). CDL_ERR_INVALID_ARG for other chains. */
+ * the stored e4m3 values; every scale a power of two). CDL_ERR_INVALID_ARG
+ * for other chains. */
 int cdl_chain_tile_scales(const cdl_chain* chain, int32_t i, float** scales, int64_t* nt);
 /* Scale of level i: stored value times *scale is the level's value (1 for
  * every dtype but CDL_FP8E4M3). Synchronises the chain's device. */

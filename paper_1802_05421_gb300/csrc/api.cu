@@ -354,6 +354,7 @@ int cdl_chain_free(cdl_chain* ch) {
   cudaFree(ch->aslices);
   cudaFree(ch->a_scale);
   cudaFree(ch->tscale);
+  cudaFree(ch->tatoms);
   cudaFree(ch->rsqrt_d);
   cudaFree(ch->D);
   cudaFree(ch->vol);
@@ -445,6 +446,7 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
     const size_t l16_bytes = (chain_dtype == CDL_FP8E4M3 || fp8t) ? (size_t)d * npad * npad * 2 : 0;
     const size_t ts_bytes = fp8t ? (size_t)d * (npad / 128) * (npad / 128) * sizeof(float) : 0;
+    const size_t atom_bytes = fp8t ? 2 * (size_t)(npad / 128) * (npad / 128) * 512 : 0;
     // float-float residual operand (CUDA-core chains) or exact bf16 slices (tensor chains)
     const size_t ahl_bytes = tensor ? 0 : 2 * (size_t)n * n * sizeof(float);
     const size_t slice_bytes = tensor ? 6 * (size_t)npad * npad * 2 : 0;
@@ -459,6 +461,7 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
         (l16_bytes && (cudaMalloc(&ch->levels16, l16_bytes) != cudaSuccess ||
                        cudaMalloc(&ch->amax, d * sizeof(unsigned)) != cudaSuccess)) ||
         (ts_bytes && cudaMalloc(&ch->tscale, ts_bytes) != cudaSuccess) ||
+        (atom_bytes && cudaMalloc(&ch->tatoms, atom_bytes) != cudaSuccess) ||
         (host_levels ? ooc_init(ch) != CDL_OK : cudaMalloc(&ch->levels, bytes) != cudaSuccess) ||
         cudaMalloc(&ch->rsqrt_d, npad * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ch->D, npad * sizeof(double)) != cudaSuccess ||

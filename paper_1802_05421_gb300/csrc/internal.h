@@ -90,7 +90,9 @@ struct cdl_chain {
   void* levels16 = nullptr;   // fp8 chains: bf16 copies of the levels (the apply's operand)
   unsigned* amax = nullptr;   // fp8 chains: per-level bound of |value| (float bits), scale = amax/448
   float* ahl = nullptr;       // A as float hi + lo planes (n x n each), the float-float residual's operand
-  float* tscale = nullptr;    // per-tile e4m3 chains: d x (npad/128)^2 tile scales
+  float* tscale = nullptr;    // per-tile e4m3 chains: d x (npad/128)^2 tile scales (powers of two)
+  uint8_t* tatoms = nullptr;  // per-tile e4m3 chains: two (ping-pong by level parity) sets of
+                              // (npad/128)^2 512-byte atoms, each the tile's e8m0 scale byte repeated
   void* aslices = nullptr;    // tensor chains: A / a_scale as 6 bf16 planes npad x npad on the grids 2^-8s
   double* a_scale = nullptr;  // tensor chains (device, 2 words): [0] the power of two >= max A that the
                               // slices are taken of, [1] the float64 bits of max |A|

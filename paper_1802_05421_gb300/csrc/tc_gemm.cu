@@ -1631,10 +1631,351 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- e4m3 squaring, hardware block scaling
+// S~^2 for an e4m3 level with one power-of-two scale 2^e per 128 x 128 tile,
+// on tcgen05.mma kind::mxf8f6f4 with block scaling: the tensor core applies
+// the e8m0 scale of each operand's 32-element K block itself, so the whole
+// K range accumulates in one float32 TMEM accumulator (no per-K-tile
+// promotion in the epilogue). A tile's 128 rows share one scale per 128-wide
+// K tile, so every scale byte of an A operand K tile is e(I, K); the 256
+// columns of a B operand take e(J0, K) for the first 128 and e(J1, K) for the
+// second (the level is symmetric: e(K, J) = e(J, K)). The scales sit in
+// global memory as 512-byte atoms, one per tile, every byte the tile's e8m0
+// exponent; each pipeline stage brings the A atom and the two B atoms with
+// its operand tiles (bulk copies on the same barrier), and the MMA issuer
+// moves them into a TMEM ring (tcgen05.cp 32x128b, replicated to the four
+// lane quarters) right before the stage's MMAs. An atom's bytes are all
+// equal, so where the MMA reads inside an atom does not matter; which atom
+// covers which 128 columns of B does, and the exact-product test checks it.
+// The epilogue drains the accumulator into registers at once (one buffer:
+// TMEM holds it plus the scale ring), then forms each output tile's
+// power-of-two scale from its maximum, stores e4m3 and the bf16 copy (both
+// mirrored), the float scales and the output level's atoms.
+constexpr int M8_STAGES = 4;
+constexpr int M8_SF = 512;                            // one scale atom: 32 rows x 16 bytes
+constexpr int M8_OPS = M8_STAGES * T8_STAGE_BYTES;    // operand tiles (1024-aligned stages)
+constexpr int M8_SFB = 3 * M8_SF;                     // atoms per stage: A, B0, B1
+constexpr int M8_SMEM_BYTES = M8_OPS + M8_STAGES * M8_SFB + 512 + 1024;
+constexpr int M8_TMEM_COLS = 512;                     // accumulator [0, 256) + scale ring [256, 320)
+constexpr int M8_SF_COL = 256;
+constexpr int M8_SF_SLOT = 16;                        // TMEM columns per stage: A at +0, B at +4 .. +11
+
+struct Mx8Params {
+  const uint32_t* tiles;   // square tile descriptors (as for the bf16 squaring)
+  int num_tiles;
+  int nt;                  // npad / 128
+  int npad;
+  uint8_t* out8;
+  __nv_bfloat16* out16;
+  const uint8_t* atoms_in;  // nt x nt atoms of the input level
+  uint8_t* atoms_out;       // nt x nt atoms of the output level
+  float* sout;              // nt x nt float scales (2^e) of the output level
+  uint32_t idesc[4];        // per K step of a K tile (scale byte id = step)
+  unsigned* status;
+};
+
+// Least e with amax <= 448 * 2^e (448 = largest finite e4m3), in [-126, 126];
+// 0 for amax = 0. From the bits of amax = m 2^x (1 <= m < 2): 448 = 1.75 * 2^8,
+// so e = x - 8 when m <= 1.75, else x - 7.
+__device__ __forceinline__ int fp8_tile_exp(float amax) {
+  if (!(amax > 0.f)) return 0;
+  const unsigned b = __float_as_uint(amax);
+  const unsigned ef = (b >> 23) & 255u;
+  if (ef == 0) return -126;   // subnormal amax: 448 * 2^-126 covers it
+  const int x = (int)ef - 127;
+  const int e = (b & 0x7FFFFFu) <= 0x600000u ? x - 8 : x - 7;
+  return max(-126, min(126, e));
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Shared-memory descriptor of a scale atom for tcgen05.cp: no swizzle, 8-row
+// core matrices of 16-byte rows, 128 bytes apart.
+__device__ __forceinline__ uint64_t atom_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(128 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ void sf_copy(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
+__device__ __forceinline__ void mma_mx8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(T8_THREADS, 1)
+    k_tc_mx8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Mx8Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sf_smem = smem + M8_OPS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sf_smem + M8_STAGES * M8_SFB);
+  // bars[0..S) full, [S..2S) empty, [2S] accumulator full, [2S+1] accumulator empty, [2S+2] drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * M8_STAGES + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * M8_STAGES + 5);
+  float* red = reinterpret_cast<float*>(bars + 2 * M8_STAGES + 6);   // [2 output tiles][8 warps]
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (M8_STAGES + s); };
+  const uint32_t afull_bar = bar0 + 8u * (2 * M8_STAGES);
+  const uint32_t aempty_bar = bar0 + 8u * (2 * M8_STAGES + 1);
+  const uint32_t drain_bar = bar0 + 8u * (2 * M8_STAGES + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = p.nt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < M8_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(afull_bar, 1);
+    mbar_init(aempty_bar, T8_EPI);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(M8_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer: operand tiles and scale atoms
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      const uint32_t td = p.tiles[t];
+      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF, half = (td >> 30) & 1;
+      const int R = 2 * I + half;
+      for (int kb = 0; kb < nt; ++kb, ++it) {
+        const int s = it % M8_STAGES;
+        const uint32_t r = (uint32_t)(it / M8_STAGES);
+        if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const uint32_t a_dst = smem_u32(smem + s * T8_STAGE_BYTES);
+        const uint32_t f_dst = smem_u32(sf_smem + s * M8_SFB);
+        mbar_expect_tx(full_bar(s), T8_STAGE_BYTES + M8_SFB);
+        tma_load_2d(a_dst, &tmA, kb * 128, R * 128, full_bar(s));
+        tma_load_2d(a_dst + T8_A, &tmB, kb * 128, J * 256, full_bar(s));
+        bulk_load(f_dst, p.atoms_in + ((size_t)R * nt + kb) * M8_SF, M8_SF, full_bar(s));
+        bulk_load(f_dst + M8_SF, p.atoms_in + ((size_t)(2 * J) * nt + kb) * M8_SF, M8_SF, full_bar(s));
+        bulk_load(f_dst + 2 * M8_SF, p.atoms_in + ((size_t)(2 * J + 1) * nt + kb) * M8_SF, M8_SF, full_bar(s));
+      }
+    }
+    if (!ok) {
+      for (int j = (it > M8_STAGES ? it - M8_STAGES : 0); j < it; ++j) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full_bar(j % M8_STAGES), (uint32_t)(j / M8_STAGES) & 1) &&
+               globaltimer() - t0 < WAIT_LIMIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer: the whole K range into one accumulator
+    int it = 0, tc = 0;
+    bool ok = true, issued = false;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++tc) {
+      if (!mbar_wait(aempty_bar, ((uint32_t)tc & 1) ^ 1, abort_flag, p.status)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      for (int kb = 0; kb < nt; ++kb, ++it) {
+        const int s = it % M8_STAGES;
+        if (!mbar_wait(full_bar(s), (uint32_t)(it / M8_STAGES) & 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(smem + s * T8_STAGE_BYTES);
+        const uint32_t f_addr = smem_u32(sf_smem + s * M8_SFB);
+        const uint32_t sf_t = tmem_base + (uint32_t)(M8_SF_COL + s * M8_SF_SLOT);
+        sf_copy(sf_t, atom_desc(f_addr));                  // A: columns +0 .. +3
+        sf_copy(sf_t + 4, atom_desc(f_addr + M8_SF));      // B columns 0-127: +4 .. +7
+        sf_copy(sf_t + 8, atom_desc(f_addr + 2 * M8_SF));  // B columns 128-255: +8 .. +11
+        const uint64_t adesc = smem_desc(a_addr);
+        const uint64_t bdesc = smem_desc(a_addr + T8_A);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)   // 32 e4m3 (32 bytes, one scale block) per MMA
+          mma_mx8(tmem_base, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc[kk], sf_t, sf_t + 4,
+                  (kb | kk) != 0);
+        issued = true;
+        mma_commit(empty_bar(s));
+      }
+      if (!ok) break;
+      mma_commit(afull_bar);
+    }
+    if (!ok && issued) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue: drain, scale, store
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int cq = (warp - 2) >> 2;          // 64-column quarter of the 256 columns
+    const int ob = cq >> 1;                  // output tile (0: first 128 columns, 1: second)
+    const int row_in_tile = q * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int np = p.npad;
+    int tc = 0;
+    // as in k_tc_fp8t: after a failed wait a warp keeps meeting the named
+    // barriers but stops loading and storing
+    bool failed = false;
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++tc) {
+      const uint32_t td = p.tiles[t];
+      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF, half = (td >> 30) & 1;
+      const int R = 2 * I + half, C = 2 * J + ob;   // output 128-block
+      float acc[T8_COLS];
+#pragma unroll
+      for (int c = 0; c < T8_COLS; ++c) acc[c] = 0.f;
+      if (!failed) {
+        if (!mbar_wait(afull_bar, (uint32_t)tc & 1, abort_flag, p.status)) {
+          failed = true;
+        } else {
+          tc_fence_after();
+#pragma unroll
+          for (int c = 0; c < T8_COLS / 16; ++c) {
+            float v[16];
+            tmem_ld16(tmem_base + lane_off + (uint32_t)(cq * T8_COLS + c * 16), v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[c * 16 + e] = v[e];
+          }
+          tc_fence_before();
+          mbar_arrive(aempty_bar);
+        }
+      }
+      float m = 0.f;
+#pragma unroll
+      for (int c = 0; c < T8_COLS; ++c) m = fmaxf(m, fabsf(acc[c]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const int slot = ob * 8 + (q + 4 * (cq & 1));
+      if (lane == 0) red[slot] = m;
+      if (ob == 0)
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+      else
+        asm volatile("bar.sync 2, 256;" ::: "memory");
+      float amax = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) amax = fmaxf(amax, red[ob * 8 + w]);
+      if (ob == 0)
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+      else
+        asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (failed || R > C) continue;   // R > C: the mirror of (C, R), written by the other half
+      const int e = fp8_tile_exp(amax);
+      const float scale = __int_as_float((e + 127) << 23);
+      const float inv = __int_as_float((127 - e) << 23);
+      const int r = R * 128 + row_in_tile;
+      const int col0 = C * 128 + (cq & 1) * T8_COLS;
+      uint8_t* C8 = p.out8;
+      __nv_bfloat16* C16 = p.out16;
+      if (R != C) {
+#pragma unroll
+        for (int c = 0; c < T8_COLS / 16; ++c) {   // 16 columns per 16-byte store
+          uint32_t w8[4];
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            uint32_t wv = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+              wv |= (uint32_t)__nv_cvt_float_to_fp8(acc[c * 16 + g * 4 + f] * inv, __NV_SATFINITE, __NV_E4M3)
+                    << (8 * f);
+            w8[g] = wv;
+          }
+          *reinterpret_cast<uint4*>(C8 + (size_t)r * np + col0 + c * 16) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+        }
+#pragma unroll
+        for (int c = 0; c < T8_COLS / 8; ++c) {   // 8 columns per 16-byte store
+          uint32_t w[4];
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            __nv_bfloat162 hh = __floats2bfloat162_rn(acc[c * 8 + 2 * g], acc[c * 8 + 2 * g + 1]);
+            w[g] = *reinterpret_cast<uint32_t*>(&hh);
+          }
+          *reinterpret_cast<uint4*>(C16 + (size_t)r * np + col0 + c * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        {   // mirrored tile: lanes write consecutive rows of a column
+          uint8_t* m8 = C8 + (size_t)col0 * np + r;
+          __nv_bfloat16* m16 = C16 + (size_t)col0 * np + r;
+#pragma unroll
+          for (int c = 0; c < T8_COLS; ++c) {
+            m8[(size_t)c * np] = (uint8_t)__nv_cvt_float_to_fp8(acc[c] * inv, __NV_SATFINITE, __NV_E4M3);
+            m16[(size_t)c * np] = __float2bfloat16_rn(acc[c]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < T8_COLS; ++c) {
+          const int col = col0 + c;
+          const uint8_t q8 = (uint8_t)__nv_cvt_float_to_fp8(acc[c] * inv, __NV_SATFINITE, __NV_E4M3);
+          const __nv_bfloat16 hv = __float2bfloat16_rn(acc[c]);
+          if (col >= r) {
+            C8[(size_t)r * np + col] = q8;
+            C16[(size_t)r * np + col] = hv;
+          }
+          if (col > r) {
+            C8[(size_t)col * np + r] = q8;
+            C16[(size_t)col * np + r] = hv;
+          }
+        }
+      }
+      if (q == 0 && (cq & 1) == 0) {   // one warp per output tile: scales and atoms
+        const uint32_t wb = (uint32_t)(e + 127) * 0x01010101u;
+        const uint4 atom = make_uint4(wb, wb, wb, wb);
+        *reinterpret_cast<uint4*>(p.atoms_out + ((size_t)R * nt + C) * M8_SF + lane * 16) = atom;
+        *reinterpret_cast<uint4*>(p.atoms_out + ((size_t)C * nt + R) * M8_SF + lane * 16) = atom;
+        if (lane == 0) {
+          p.sout[R * nt + C] = scale;
+          p.sout[C * nt + R] = scale;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(M8_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Level 0 of a per-tile e4m3 chain from its bf16 copy: one block per 128 x
-// 128 tile; scale = tile max / 448.
+// 128 tile; scale = the least power of two 2^e with tile max <= 448 * 2^e,
+// stored as a float and as the tile's 512-byte atom of e8m0 bytes.
 __global__ void __launch_bounds__(256) k_quant_fp8_tiles(const __nv_bfloat16* __restrict__ L16, int np,
-                                                          uint8_t* __restrict__ L8, float* __restrict__ scales) {
+                                                          uint8_t* __restrict__ L8, float* __restrict__ scales,
+                                                          uint8_t* __restrict__ atoms) {
   __shared__ float red[8];
   const int nt = np / 128;
   const int I = blockIdx.x / nt, J = blockIdx.x % nt;
@@ -1649,13 +1990,18 @@ __global__ void __launch_bounds__(256) k_quant_fp8_tiles(const __nv_bfloat16* __
   __syncthreads();
   float amax = 0.f;
   for (int w = 0; w < 8; ++w) amax = fmaxf(amax, red[w]);
-  const float scale = amax > 0.f ? amax * (1.0f / 448.0f) : 1.0f;
-  const float inv = 1.0f / scale;
+  const int ex = fp8_tile_exp(amax);
+  const float scale = __int_as_float((ex + 127) << 23);
+  const float inv = __int_as_float((127 - ex) << 23);
   for (int e = threadIdx.x; e < 128 * 128; e += 256) {
     const size_t o = (size_t)(I * 128 + e / 128) * np + J * 128 + e % 128;
     L8[o] = (uint8_t)__nv_cvt_float_to_fp8(__bfloat162float(L16[o]) * inv, __NV_SATFINITE, __NV_E4M3);
   }
   if (threadIdx.x == 0) scales[I * nt + J] = scale;
+  if (threadIdx.x < 32) {
+    const uint32_t wb = (uint32_t)(ex + 127) * 0x01010101u;
+    *reinterpret_cast<uint4*>(atoms + ((size_t)I * nt + J) * M8_SF + threadIdx.x * 16) = make_uint4(wb, wb, wb, wb);
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -1906,6 +2252,17 @@ int tc_apply_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgr
   return launch(ctx, host_first->mapA, host_first->mapB, p, kc, work);
 }
 
+// Instruction descriptor of kind::mxf8f6f4 with block scaling: e4m3 A and B,
+// K-major, float32 accumulator, e8m0 scales, scale byte `id` of A and B.
+uint32_t make_idesc_mx8(int n, int id) {
+  return ((uint32_t)id << 4)              // B scale byte
+         | (0u << 7) | (0u << 10)         // A, B: e4m3
+         | ((uint32_t)(n >> 3) << 17)     // N / 8
+         | (1u << 23)                     // scales: ue8m0
+         | ((uint32_t)(BM >> 4) << 24)    // M / 16
+         | ((uint32_t)id << 29);          // A scale byte
+}
+
 int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level) {
   const int np = (int)ch->npad;   // multiple of 256
   const int nt = np / 128;
@@ -1916,6 +2273,32 @@ int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level) {
   CUtensorMap ma, mb;
   CDL_TRY(make_map(&ma, ch->level(level), np, np, 128, 1));
   CDL_TRY(make_map(&mb, ch->level(level), np, np, 256, 1));
+  if (ch->tatoms) {
+    static bool mattr = false;
+    if (!mattr) {
+      CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_mx8, cudaFuncAttributeMaxDynamicSharedMemorySize, M8_SMEM_BYTES));
+      mattr = true;
+    }
+    const size_t atoms = (size_t)nt * nt * M8_SF;
+    Mx8Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.tiles = tiles;
+    p.num_tiles = count;
+    p.nt = nt;
+    p.npad = np;
+    p.out8 = static_cast<uint8_t*>(ch->level(level + 1));
+    p.out16 = static_cast<__nv_bfloat16*>(ch->level16(level + 1));
+    p.atoms_in = ch->tatoms + (size_t)(level & 1) * atoms;
+    p.atoms_out = ch->tatoms + (size_t)((level + 1) & 1) * atoms;
+    p.sout = ch->tscale + (size_t)(level + 1) * nt * nt;
+    for (int kk = 0; kk < 4; ++kk) p.idesc[kk] = make_idesc_mx8(256, kk);
+    p.status = ctx->dev_status;
+    const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
+    const int grid = std::min(count, ctx->sm_count);
+    Launch L(ctx, CDL_KC_SQUARE, flops);
+    k_tc_mx8<<<grid, T8_THREADS, M8_SMEM_BYTES, ctx->stream>>>(ma, mb, p);
+    return L.done();
+  }
   static bool attr = false;
   if (!attr) {
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_fp8t, cudaFuncAttributeMaxDynamicSharedMemorySize, T8_SMEM_BYTES));
@@ -1945,7 +2328,7 @@ int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch) {
   const int nt = np / 128;
   Launch L(ctx, CDL_KC_CHAIN_INIT, 3.0 * np * (double)np);
   k_quant_fp8_tiles<<<nt * nt, 256, 0, ctx->stream>>>(static_cast<const __nv_bfloat16*>(ch->level16(0)), np,
-                                                      static_cast<uint8_t*>(ch->level(0)), ch->tscale);
+                                                      static_cast<uint8_t*>(ch->level(0)), ch->tscale, ch->tatoms);
   return L.done();
 }
 

@@ -190,12 +190,15 @@ def test_tcgen05_square_is_exact_product_of_its_inputs(G, n):
 
 @pytest.mark.parametrize("n", [300, 1000, 2100])
 def test_tcgen05_fp8_tile_square_is_exact_product_of_its_inputs(G, n):
-    """One e4m3 squaring with 128 x 128 tile scales against the float64
-    product of the same dequantized input: the bf16 copy may differ by the
-    float32 accumulation (per K-tile MMA plus the scaled promotion) and bf16
-    rounding; each output tile's scale is its maximum over 448 and its e4m3
+    """One e4m3 squaring with 128 x 128 tile scales (tcgen05 kind::mxf8f6f4,
+    the tensor core applying each operand tile's e8m0 scale) against the
+    float64 product of the same dequantized input: the bf16 copy may differ
+    by the float32 accumulation and bf16 rounding; each output tile's scale is
+    the least power of two 2^e with tile maximum <= 448 * 2^e, and its e4m3
     values are the tile divided by the scale, rounded (2^-4 relative, or one
-    subnormal step of the tile)."""
+    subnormal step of the tile). A tile scale applied to the wrong 128
+    columns of an operand would be off by powers of two and fail the bounds;
+    n = 1000 and 2100 have several tiles per row with different scales."""
     cdl = G.cdl
     X = iid_pair(n, 24, 1, seed=17).X[0]
     A, D, vol, _ = G.graph(X)
@@ -203,6 +206,7 @@ def test_tcgen05_fp8_tile_square_is_exact_product_of_its_inputs(G, n):
     try:
         V0 = G.level_values(ch, 0, "fp8t")
         V1 = G.level_values(ch, 1, "fp8t")
+        S0 = G.tile_scales(ch, 0)
         S1 = G.tile_scales(ch, 1)
         L16 = G.level16(ch, 1)
     finally:
@@ -217,9 +221,14 @@ def test_tcgen05_fp8_tile_square_is_exact_product_of_its_inputs(G, n):
         for J in range(nt):
             blk = np.s_[I * 128:(I + 1) * 128, J * 128:(J + 1) * 128]
             m = np.abs(R[blk]).max()
+            sc = S1[I, J]
+            assert sc > 0 and math.frexp(sc)[0] == 0.5, (I, J, sc)          # a power of two
             if m > 0:
-                assert abs(448 * S1[I, J] - m) <= 2.0 ** -8 * m + acc[blk].max(), (I, J)
-            assert np.abs(V1[blk]).max() <= 448 * S1[I, J] * (1 + 1e-6)
+                slack = 2.0 ** -20 * m + acc[blk].max()
+                assert m <= 448 * sc + slack and m > 224 * sc - slack, (I, J, m, sc)
+            assert np.abs(V1[blk]).max() <= 448 * sc * (1 + 1e-6)
+    # the level-0 scales are powers of two too
+    assert all(math.frexp(v)[0] == 0.5 for v in np.unique(S0))
     assert np.array_equal(S1, S1.T)
     assert np.array_equal(V1, V1.T) and np.array_equal(L16, L16.T)
 
