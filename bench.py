@@ -1068,7 +1068,7 @@ def main():
                 "same_top": t8.cpu().tolist() == top.cpu().tolist(),
                 "max_rel_diff_F_vs_bf16": float(((F8 - F).abs() / F).max()),
                 "square_ms_per_launch": sq_ms / max(sq_cnt, 1),
-                "square_roofline": {"kernel": "k_tc_fp8t", "achieved": ach8, "peak": peak8, "unit": "TFLOP/s",
+                "square_roofline": {"kernel": "k_tc_mx8", "achieved": ach8, "peak": peak8, "unit": "TFLOP/s",
                                     "frac": ach8 / peak8,
                                     "peak_source": "2 x measured bf16_tflops_sustained (nominal e4m3/bf16 ratio)"}}
 
@@ -1141,7 +1141,7 @@ def main():
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
         elif args.chain in ("fp8", "fp8t"):   # measured bf16 peak x the nominal fp8/bf16 dense ratio (4.5 / 2.25)
             peak = 2.0 * pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        kname = {"bf16": "k_tc_gemm", "fp8": "k_tc_gemm<fp8>", "fp8t": "k_tc_fp8t"}.get(args.chain, "k_gemm_tn")
+        kname = {"bf16": "k_tc_gemm", "fp8": "k_tc_gemm<fp8>", "fp8t": "k_tc_mx8"}.get(args.chain, "k_gemm_tn")
         roof = {"kernel": kname + " (chain squaring)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if peak else None,

@@ -521,17 +521,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 
-// ---------------------------------------------------------------- fp8, per-tile scales
-// Squaring of an e4m3 level stored with one scale per 128 x 128 tile: level
-// value (I, K) = s_IK * stored. The product of tiles needs a different scale
-// for every K, so each 128-wide K-tile's MMA (M = 128, N = 256, K = 128,
-// float32) goes to one of two TMEM buffers, and the epilogue warps add
-// s_IK s_KJ times it to float32 accumulators in registers (promotion after
-// every K-tile). The 128 x 256 MMA tile covers two 128 x 128 output tiles;
-// when a tile is complete its maximum sets its scale, and it is stored in
-// e4m3 (value / scale) and in bf16 (the apply's copy), both mirrored. The
-// MMA tiles are the upper-triangle 256-blocks (two 128-row halves each), as
-// in the bf16 squaring.
+// ---------------------------------------------------------------- 576-thread tensor-core kernels
+// Shared by the e4m3 tile squaring (k_tc_mx8), the exact-slice residual, the
+// distance and the score kernels: warp 0 TMA, warp 1 MMA, warps 2-17
+// epilogue. The e4m3 squaring's stage: an A K tile of 128 rows and a B K
+// tile of 256 rows, 128 e4m3 (128 bytes) each.
 constexpr int T8_STAGES = 4;
 constexpr int T8_A = 128 * 128;                       // A k-tile bytes
 constexpr int T8_B = 256 * 128;                       // B k-tile bytes
@@ -542,18 +536,6 @@ constexpr int T8_THREADS = 576;   // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr int T8_EPI = 512;       // epilogue threads
 constexpr int T8_COLS = 64;       // output columns per epilogue thread
 
-struct Fp8tParams {
-  const uint32_t* tiles;   // square tile descriptors (I | J << 15 | half << 30, 256-blocks)
-  int num_tiles;
-  int nt;                  // npad / 128
-  int npad;
-  uint8_t* out8;
-  __nv_bfloat16* out16;
-  const float* sin;        // nt x nt scales of the input level
-  float* sout;             // nt x nt scales of the output level
-  uint32_t idesc;
-  unsigned* status;
-};
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -566,257 +548,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 18 warps: an SM sub-partition holds five of them, so at most 96 registers
-// per thread fit.
-__global__ void __launch_bounds__(T8_THREADS, 1)
-    k_tc_fp8t(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const Fp8tParams p) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T8_STAGES * T8_STAGE_BYTES);
-  // bars[0..S) full, [S..2S) empty, [2S, 2S+2) partial full, [2S+2, 2S+4) partial empty, [2S+4] drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * T8_STAGES + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * T8_STAGES + 7);
-  float* red = reinterpret_cast<float*>(bars + 2 * T8_STAGES + 8);   // [2 output tiles][8 warps]
-  const uint32_t bar0 = smem_u32(bars);
-  auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (T8_STAGES + s); };
-  auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * T8_STAGES + b); };
-  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * T8_STAGES + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * T8_STAGES + 4);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt = p.nt;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < T8_STAGES; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(pfull_bar(b), 1);
-      mbar_init(pempty_bar(b), T8_EPI);
-    }
-    mbar_init(drain_bar, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(T8_TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-
-  if (warp == 0 && lane == 0) {
-    // ------------------------------------------------ TMA producer
-    int it = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-      const uint32_t td = p.tiles[t];
-      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF, half = (td >> 30) & 1;
-      for (int kb = 0; kb < nt; ++kb, ++it) {
-        const int s = it % T8_STAGES;
-        const uint32_t r = (uint32_t)(it / T8_STAGES);
-        if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
-          ok = false;
-          break;
-        }
-        const uint32_t a_dst = smem_u32(smem + s * T8_STAGE_BYTES);
-        mbar_expect_tx(full_bar(s), T8_STAGE_BYTES);
-        tma_load_2d(a_dst, &tmA, kb * 128, I * 256 + half * 128, full_bar(s));
-        tma_load_2d(a_dst + T8_A, &tmB, kb * 128, J * 256, full_bar(s));
-      }
-    }
-    if (!ok) {
-      for (int j = (it > T8_STAGES ? it - T8_STAGES : 0); j < it; ++j) {
-        const unsigned long long t0 = globaltimer();
-        while (!mbar_try_wait(full_bar(j % T8_STAGES), (uint32_t)(j / T8_STAGES) & 1) &&
-               globaltimer() - t0 < WAIT_LIMIT_NS) {
-        }
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------ MMA issuer: one K-tile per TMEM buffer
-    int it = 0, pc = 0;
-    bool ok = true, issued = false;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-      for (int kb = 0; kb < nt; ++kb, ++it, ++pc) {
-        const int b = pc & 1;
-        const uint32_t pr = (uint32_t)(pc >> 1);
-        if (!mbar_wait(pempty_bar(b), (pr & 1) ^ 1, abort_flag, p.status)) {
-          ok = false;
-          break;
-        }
-        const int s = it % T8_STAGES;
-        if (!mbar_wait(full_bar(s), (uint32_t)(it / T8_STAGES) & 1, abort_flag, p.status)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t a_addr = smem_u32(smem + s * T8_STAGE_BYTES);
-        const uint64_t adesc = smem_desc(a_addr);
-        const uint64_t bdesc = smem_desc(a_addr + T8_A);
-        const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)   // 32 e4m3 (32 bytes) per MMA
-          mma_fp8(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, kk != 0);
-        issued = true;
-        mma_commit(empty_bar(s));
-        mma_commit(pfull_bar(b));
-      }
-    }
-    if (!ok && issued) {
-      mma_commit(drain_bar);
-      const unsigned long long t0 = globaltimer();
-      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
-      }
-    }
-  } else if (warp >= 2) {
-    // ------------------------------------------------ epilogue: promotion, scale, store
-    const int q = warp & 3;                  // TMEM lane quarter
-    const int cq = (warp - 2) >> 2;          // 64-column quarter of the 256 columns
-    const int ob = cq >> 1;                  // output tile (0: first 128 columns, 1: second)
-    const int wi = (warp - 2) & 7;           // warp index among the 8 warps of this output tile... (see red)
-    const int row_in_tile = q * 32 + lane;
-    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const int np = p.npad;
-    int pc = 0;
-    // The epilogue warps of an output tile meet at a named barrier per tile,
-    // so they walk the same tiles whatever happens: after a failed (expired
-    // or aborted) wait a warp stops loading and storing but keeps the barrier
-    // count, and every later wait returns at once because the abort flag is set.
-    bool failed = false;
-    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
-      const uint32_t td = p.tiles[t];
-      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF, half = (td >> 30) & 1;
-      const int R = 2 * I + half, C = 2 * J + ob;   // output 128-block
-      float acc[T8_COLS];
-#pragma unroll
-      for (int c = 0; c < T8_COLS; ++c) acc[c] = 0.f;
-      const float* srow = p.sin + (size_t)R * nt;   // s_RK (the level's scales are symmetric: s_KC = s_CK)
-      const float* scol = p.sin + (size_t)C * nt;
-      float sc_next = srow[0] * scol[0];
-      for (int kb = 0; kb < nt; ++kb, ++pc) {
-        if (failed) continue;
-        const float sc = sc_next;
-        if (kb + 1 < nt) sc_next = srow[kb + 1] * scol[kb + 1];   // issued before the wait
-        const int b = pc & 1;
-        const uint32_t pr = (uint32_t)(pc >> 1);
-        if (!mbar_wait(pfull_bar(b), pr & 1, abort_flag, p.status)) {
-          failed = true;
-          continue;
-        }
-        tc_fence_after();
-#pragma unroll
-        for (int c = 0; c < T8_COLS / 16; ++c) {
-          float v[16];
-          tmem_ld16(tmem_base + lane_off + (uint32_t)(b * 256 + cq * T8_COLS + c * 16), v);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) acc[c * 16 + e] = __fmaf_rn(sc, v[e], acc[c * 16 + e]);
-        }
-        tc_fence_before();
-        mbar_arrive(pempty_bar(b));
-      }
-      // output tile scale from the tile's largest magnitude (8 warps per output tile)
-      float m = 0.f;
-#pragma unroll
-      for (int c = 0; c < T8_COLS; ++c) m = fmaxf(m, fabsf(acc[c]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      const int slot = ob * 8 + (q + 4 * (cq & 1));
-      if (lane == 0) red[slot] = m;
-      if (ob == 0)
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-      else
-        asm volatile("bar.sync 2, 256;" ::: "memory");
-      float amax = 0.f;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) amax = fmaxf(amax, red[ob * 8 + w]);
-      if (ob == 0)
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-      else
-        asm volatile("bar.sync 2, 256;" ::: "memory");
-      if (failed || R > C) continue;   // R > C: the mirror of (C, R), written by the other half
-      const float scale = amax > 0.f ? amax * (1.0f / 448.0f) : 1.0f;
-      const float inv = 1.0f / scale;
-      const int r = R * 128 + row_in_tile;
-      const int col0 = C * 128 + (cq & 1) * T8_COLS;
-      uint8_t* C8 = p.out8;
-      __nv_bfloat16* C16 = p.out16;
-      if (R != C) {
-#pragma unroll
-        for (int c = 0; c < T8_COLS / 16; ++c) {   // 16 columns per 16-byte store
-          uint32_t w8[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            uint32_t wv = 0;
-#pragma unroll
-            for (int f = 0; f < 4; ++f)
-              wv |= (uint32_t)__nv_cvt_float_to_fp8(acc[c * 16 + e * 4 + f] * inv, __NV_SATFINITE, __NV_E4M3)
-                    << (8 * f);
-            w8[e] = wv;
-          }
-          *reinterpret_cast<uint4*>(C8 + (size_t)r * np + col0 + c * 16) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
-        }
-#pragma unroll
-        for (int c = 0; c < T8_COLS / 8; ++c) {   // 8 columns per 16-byte store
-          uint32_t w[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            __nv_bfloat162 hh = __floats2bfloat162_rn(acc[c * 8 + 2 * e], acc[c * 8 + 2 * e + 1]);
-            w[e] = *reinterpret_cast<uint32_t*>(&hh);
-          }
-          *reinterpret_cast<uint4*>(C16 + (size_t)r * np + col0 + c * 8) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        {   // mirrored tile: lanes write consecutive rows of a column
-          uint8_t* m8 = C8 + (size_t)col0 * np + r;
-          __nv_bfloat16* m16 = C16 + (size_t)col0 * np + r;
-#pragma unroll
-          for (int c = 0; c < T8_COLS; ++c) {
-            m8[(size_t)c * np] = (uint8_t)__nv_cvt_float_to_fp8(acc[c] * inv, __NV_SATFINITE, __NV_E4M3);
-            m16[(size_t)c * np] = __float2bfloat16_rn(acc[c]);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < T8_COLS; ++c) {
-          const int col = col0 + c;
-          const uint8_t q8 = (uint8_t)__nv_cvt_float_to_fp8(acc[c] * inv, __NV_SATFINITE, __NV_E4M3);
-          const __nv_bfloat16 hv = __float2bfloat16_rn(acc[c]);
-          if (col >= r) {
-            C8[(size_t)r * np + col] = q8;
-            C16[(size_t)r * np + col] = hv;
-          }
-          if (col > r) {
-            C8[(size_t)col * np + r] = q8;
-            C16[(size_t)col * np + r] = hv;
-          }
-        }
-      }
-      if (q == 0 && (cq & 1) == 0 && lane == 0) {   // one thread per output tile
-        p.sout[R * nt + C] = scale;
-        p.sout[C * nt + R] = scale;
-      }
-    }
-    (void)wi;
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) {
-    __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(T8_TMEM_COLS)
-                 : "memory");
-  }
 }
 
 // ---------------------------------------------------------------- exact-slice residual product
@@ -833,7 +564,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // accumulators, and every 64 chunks (at most 2^30 steps) adds them, scaled
 // by 2^-8(s+t), to the float64 result G. The 21 slice pairs with s + t <= 7
 // leave about 2^-50 of |A| |Z / c|: A Z = 2^q c G to float64 accuracy, as
-// the ordering of the float64 additions allows. Warp roles as in k_tc_fp8t
+// the ordering of the float64 additions allows. Warp roles as in k_tc_mx8
 // (576 threads, 16 epilogue warps).
 constexpr int RS_SLICES = 6;
 constexpr int RS_MAX_PAIRS = 21;
@@ -1845,8 +1576,10 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int np = p.npad;
     int tc = 0;
-    // as in k_tc_fp8t: after a failed wait a warp keeps meeting the named
-    // barriers but stops loading and storing
+    // The epilogue warps of an output tile meet at a named barrier per tile,
+    // so they walk the same tiles whatever happens: after a failed (expired
+    // or aborted) wait a warp stops loading and storing but keeps the barrier
+    // count, and every later wait returns at once because the abort flag is set.
     bool failed = false;
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++tc) {
       const uint32_t td = p.tiles[t];
@@ -2273,7 +2006,8 @@ int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level) {
   CUtensorMap ma, mb;
   CDL_TRY(make_map(&ma, ch->level(level), np, np, 128, 1));
   CDL_TRY(make_map(&mb, ch->level(level), np, np, 256, 1));
-  if (ch->tatoms) {
+  if (!ch->tatoms) return CDL_ERR_INVALID_ARG;
+  {
     static bool mattr = false;
     if (!mattr) {
       CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_mx8, cudaFuncAttributeMaxDynamicSharedMemorySize, M8_SMEM_BYTES));
@@ -2299,28 +2033,6 @@ int chain_square_fp8t(cdl_ctx* ctx, cdl_chain* ch, int level) {
     k_tc_mx8<<<grid, T8_THREADS, M8_SMEM_BYTES, ctx->stream>>>(ma, mb, p);
     return L.done();
   }
-  static bool attr = false;
-  if (!attr) {
-    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_fp8t, cudaFuncAttributeMaxDynamicSharedMemorySize, T8_SMEM_BYTES));
-    attr = true;
-  }
-  Fp8tParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.tiles = tiles;
-  p.num_tiles = count;
-  p.nt = nt;
-  p.npad = np;
-  p.out8 = static_cast<uint8_t*>(ch->level(level + 1));
-  p.out16 = static_cast<__nv_bfloat16*>(ch->level16(level + 1));
-  p.sin = ch->tscale + (size_t)level * nt * nt;
-  p.sout = ch->tscale + (size_t)(level + 1) * nt * nt;
-  p.idesc = make_idesc(256, true);
-  p.status = ctx->dev_status;
-  const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
-  const int grid = std::min(count, ctx->sm_count);
-  Launch L(ctx, CDL_KC_SQUARE, flops);
-  k_tc_fp8t<<<grid, T8_THREADS, T8_SMEM_BYTES, ctx->stream>>>(ma, mb, p);
-  return L.done();
 }
 
 int fp8t_quantize_level0(cdl_ctx* ctx, cdl_chain* ch) {
