@@ -272,6 +272,14 @@ int cdl_graph_add_edges(cdl_ctx* ctx, void* A, cdl_dtype a_dtype, int64_t n, int
  * lambda_2^(2^i) and d_eff is a few levels. Changes the configured d, hence
  * opt-in. */
 enum { CDL_CHAIN_DEFAULT = 0, CDL_CHAIN_HOST_LEVELS = 1, CDL_CHAIN_TRUNCATE = 2 };
+/* With CDL_CHAIN_HOST_LEVELS, bits 8-15 of the flags = r keep levels
+ * 0 .. r - 1 in device memory and only the others on the host (a chain
+ * larger than the host's memory keeps what fits on the device); 0 = every
+ * level on the host. Only cdl_caddelag_pair with CDL_PAIR_REGEN_GRAPHS takes
+ * r = 255: as many as fit in the free device memory beside the pair's own
+ * buffers. */
+enum { CDL_CHAIN_RESIDENT_SHIFT = 8, CDL_CHAIN_RESIDENT_MASK = 0xFF00 };
+#define CDL_CHAIN_RESIDENT(r) ((((int32_t)(r)) << CDL_CHAIN_RESIDENT_SHIFT) & CDL_CHAIN_RESIDENT_MASK)
 /* Levels in use: d, or fewer after CDL_CHAIN_TRUNCATE. */
 int cdl_chain_depth(const cdl_chain* chain, int32_t* d_eff);
 int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double* D,
@@ -475,9 +483,31 @@ typedef struct {
   int32_t host_io;         /* 1: X1, X2, F, top_idx are host pointers and
                               the call copies them in and out (synchronous);
                               0: device pointers (asynchronous)            */
-  int32_t chain_flags;     /* CDL_CHAIN_* flags of cdl_chain_build          */
+  int32_t chain_flags;     /* CDL_CHAIN_* flags of cdl_chain_build, and
+                              CDL_PAIR_REGEN_GRAPHS / CDL_PAIR_PANEL below  */
   int32_t score_flags;     /* CDL_SCORE_* flags                             */
 } cdl_pair_opts;
+
+/* cdl_pair_opts.chain_flags for graphs too large to keep (the paper's
+ * larger-than-memory aim, Sec. 1 and Sec. 3.2). With CDL_PAIR_REGEN_GRAPHS
+ * neither n x n graph is stored: each is regenerated from its node series
+ * in row panels (default 4096 rows; bits 16-23 = log2 of the panel rows,
+ * 8 .. 16) wherever it is needed: the exact median sigma (radix select,
+ * every pass over the upper-triangle distances of each panel), the degrees,
+ * level 0 of the chain and the projection (one pass), the full residual of
+ * every refinement step (A Z summed over the panels' exact bf16 slices on
+ * the tensor cores) and the scores (both graphs' panels side by side). The
+ * panels hold the same A values as cdl_build_graph; degrees and sums differ
+ * only in summation order. Needs chain_dtype = score_dtype = CDL_BF16, node
+ * series on the 2^-16 grid (else CDL_ERR_UNSUPPORTED) and no
+ * CDL_CHAIN_TRUNCATE; the solve forms the full residual after every step.
+ * Levels: all in device memory, or with CDL_CHAIN_HOST_LEVELS levels
+ * 0 .. r - 1 on the device and the rest in pinned host memory, r from
+ * CDL_CHAIN_RESIDENT(r) (255: as many as fit; at least one is needed,
+ * level 0 being formed in place). Device memory: the levels on the device,
+ * two level slots with host levels, two P x n float64 panels, 12 npad P
+ * bytes of slices and the O(n k) vectors. */
+enum { CDL_PAIR_REGEN_GRAPHS = 4, CDL_PAIR_PANEL_SHIFT = 16, CDL_PAIR_PANEL_MASK = 0xFF0000 };
 
 /* One graph pair end to end (Alg. 4): graph build, chain, projection and
  * solve for each graph (Alg. 3), then scores and top anomalies.

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcdl.so")
-SOURCES = ["api.cu", "graph.cu", "chain.cu", "tc_gemm.cu", "solve.cu", "project.cu", "score.cu", "batch.cu", "ooc.cu"]
+SOURCES = ["api.cu", "graph.cu", "chain.cu", "tc_gemm.cu", "solve.cu", "project.cu", "score.cu", "batch.cu", "ooc.cu",
+           "regen.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr"]

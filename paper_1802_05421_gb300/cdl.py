@@ -28,6 +28,19 @@ CDL_SOLVE_FULL_RESIDUAL = 1
 CDL_CHAIN_DEFAULT = 0
 CDL_CHAIN_HOST_LEVELS = 1
 CDL_CHAIN_TRUNCATE = 2
+CDL_CHAIN_RESIDENT_SHIFT, CDL_CHAIN_RESIDENT_MASK = 8, 0xFF00
+CDL_PAIR_REGEN_GRAPHS = 4
+CDL_PAIR_PANEL_SHIFT, CDL_PAIR_PANEL_MASK = 16, 0xFF0000
+
+
+def CDL_CHAIN_RESIDENT(r):
+    """Chain flag bits: keep levels 0 .. r - 1 in device memory (with CDL_CHAIN_HOST_LEVELS)."""
+    return (int(r) << CDL_CHAIN_RESIDENT_SHIFT) & CDL_CHAIN_RESIDENT_MASK
+
+
+def CDL_PAIR_PANEL_LOG2(p):
+    """Pair flag bits: regenerated graphs in row panels of 2^p rows."""
+    return (int(p) << CDL_PAIR_PANEL_SHIFT) & CDL_PAIR_PANEL_MASK
 CDL_SCORE_CHANGED_ONLY = 1
 CDL_KERNEL_GAUSSIAN, CDL_KERNEL_EXP = 0, 1
 CDL_DEBUG_WITHHOLD_TC_LOAD = 1

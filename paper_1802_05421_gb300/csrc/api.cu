@@ -160,6 +160,37 @@ static int set_device(cdl_ctx* ctx) {
   return CDL_OK;
 }
 
+int chain_create_regen(cdl_ctx* ctx, int64_t n, int d, int resident, cdl_chain** out) {
+  if (!tc_supported(ctx)) return CDL_ERR_UNSUPPORTED;
+  const int64_t npad = round_up(n, 256);
+  cdl_chain* ch = new cdl_chain();
+  ch->device = ctx->device;
+  ch->n = n;
+  ch->npad = npad;
+  ch->d = d;
+  ch->d_eff = d;
+  ch->dtype = CDL_BF16;
+  ch->elem = 2;
+  ch->resident = resident;
+  const double one = 1.0;
+  if (ooc_init(ch) != CDL_OK || cudaMalloc(&ch->a_scale, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ch->rsqrt_d, npad * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ch->D, npad * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ch->vol, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cdl_chain_free(ch);
+    return CDL_ERR_OOM;
+  }
+  // Gaussian-kernel graphs: A <= 1, so the exact slices are taken of A itself
+  // (a_scale[0] = 1) and 1 bounds max A (a_scale[1], the projection's grids)
+  if (cudaMemcpy(ch->a_scale, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ch->a_scale + 1, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cdl_chain_free(ch);
+    return CDL_ERR_CUDA;
+  }
+  *out = ch;
+  return CDL_OK;
+}
 }  // namespace cdl
 
 using namespace cdl;
@@ -214,6 +245,7 @@ int cdl_ctx_destroy(cdl_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pair_chain) cdl_chain_free(ctx->pair_chain);
+  if (ctx->regen_chain) cdl_chain_free(ctx->regen_chain);
   if (ctx->batch) batch_plan_free(ctx->batch);
   for (auto& kv : ctx->ws) cudaFree(kv.second.first);
   for (auto& ev : ctx->pending) {
@@ -370,8 +402,8 @@ int cdl_chain_depth(const cdl_chain* ch, int32_t* d_eff) {
 
 int cdl_chain_level(const cdl_chain* ch, int32_t i, void** level, int64_t* npad) {
   if (!ch || i < 0 || i >= ch->d_eff) return CDL_ERR_INVALID_ARG;
-  if (ch->host_levels) CDL_CUDA_TRY(cudaStreamSynchronize(ch->copy));   // copies to the host complete
-  if (level) *level = ch->level(i);
+  if (ch->host_levels && ch->copy) CDL_CUDA_TRY(cudaStreamSynchronize(ch->copy));   // copies to the host complete
+  if (level) *level = ch->host_levels ? ooc_level_ptr(ch, i) : ch->level(i);
   if (npad) *npad = ch->npad;
   return CDL_OK;
 }
@@ -411,9 +443,12 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
                     const double* vol, int64_t n, int32_t d, cdl_dtype chain_dtype,
                     int32_t flags, cdl_chain** inout) {
   if (!ctx || !inout) return CDL_ERR_INVALID_ARG;
-  if (n < 2 || n > (1 << 20) || d < 1 || d > 64 || (flags & ~(CDL_CHAIN_HOST_LEVELS | CDL_CHAIN_TRUNCATE)))
+  if (n < 2 || n > (1 << 20) || d < 1 || d > 64 ||
+      (flags & ~(CDL_CHAIN_HOST_LEVELS | CDL_CHAIN_TRUNCATE | CDL_CHAIN_RESIDENT_MASK)))
     return CDL_ERR_INVALID_ARG;
   const bool host_levels = (flags & CDL_CHAIN_HOST_LEVELS) != 0;
+  const int resident = (flags & CDL_CHAIN_RESIDENT_MASK) >> CDL_CHAIN_RESIDENT_SHIFT;
+  if (resident && !host_levels) return CDL_ERR_INVALID_ARG;
   const bool truncate = (flags & CDL_CHAIN_TRUNCATE) != 0;
   if (host_levels && truncate) return CDL_ERR_UNSUPPORTED;
   if (host_levels && chain_dtype != CDL_BF16) return CDL_ERR_UNSUPPORTED;
@@ -432,7 +467,7 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
   cdl_chain* ch = *inout;
   if (ch) {
     if (ch->n != n || ch->d != d || ch->dtype != chain_dtype || ch->device != ctx->device ||
-        ch->host_levels != host_levels)
+        ch->host_levels != host_levels || (host_levels && ch->resident != std::min(resident, d)) || ch->regen)
       return CDL_ERR_INVALID_ARG;
   } else {
     ch = new cdl_chain();
@@ -442,7 +477,9 @@ int cdl_chain_build(cdl_ctx* ctx, const void* A, cdl_dtype a_dtype, const double
     ch->d = d;
     ch->dtype = chain_dtype;
     ch->elem = chain_dtype == CDL_F64 ? 8 : chain_dtype == CDL_F32 ? 4 : chain_dtype == CDL_BF16 ? 2 : 1;
-    size_t bytes = host_levels ? 2 * (size_t)npad * npad * ch->elem : (size_t)d * npad * npad * ch->elem;
+    ch->resident = resident;
+    size_t bytes = host_levels ? (2 + (size_t)std::min(resident, d)) * npad * npad * ch->elem
+                               : (size_t)d * npad * npad * ch->elem;
     const size_t aop_bytes = tensor ? 2 * (size_t)npad * npad * 2 : 0;
     const size_t l16_bytes = (chain_dtype == CDL_FP8E4M3 || fp8t) ? (size_t)d * npad * npad * 2 : 0;
     const size_t ts_bytes = fp8t ? (size_t)d * (npad / 128) * (npad / 128) * sizeof(float) : 0;
@@ -640,9 +677,16 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
       o->topk < 0 || o->topk > 1024 || o->topk > n || (o->topk > 0 && !top_idx) ||
       (o->score_dtype != CDL_F64 && o->score_dtype != CDL_F32 && o->score_dtype != CDL_BF16) ||
       (o->score_flags & ~CDL_SCORE_CHANGED_ONLY) ||
-      ((o->score_flags & CDL_SCORE_CHANGED_ONLY) && (!(o->sigma > 0) || o->score_dtype == CDL_BF16)))
+      ((o->score_flags & CDL_SCORE_CHANGED_ONLY) && (!(o->sigma > 0) || o->score_dtype == CDL_BF16)) ||
+      (o->chain_flags & ~(CDL_CHAIN_HOST_LEVELS | CDL_CHAIN_TRUNCATE | CDL_CHAIN_RESIDENT_MASK |
+                          CDL_PAIR_REGEN_GRAPHS | CDL_PAIR_PANEL_MASK)))
     return CDL_ERR_INVALID_ARG;
   CDL_TRY(set_device(ctx));
+  if (o->chain_flags & CDL_PAIR_REGEN_GRAPHS) {
+    if (o->chain_flags & CDL_CHAIN_TRUNCATE) return CDL_ERR_UNSUPPORTED;
+    return pair_regen(ctx, X1, X2, n, T, o, F, top_idx, stats1, stats2);
+  }
+  if (o->chain_flags & CDL_PAIR_PANEL_MASK) return CDL_ERR_INVALID_ARG;
   const size_t nn = (size_t)n * n;
   void *dX, *dA1, *dA2, *dvec, *dY, *dZ1, *dZ2, *dF, *dtop;
   CDL_TRY(ws_get(ctx, "pair.X", 2 * (size_t)n * T * sizeof(double), &dX));
@@ -675,7 +719,9 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
   cdl_solve_stats* sts[2] = {stats1, stats2};
   if (ctx->pair_chain && (ctx->pair_chain->n != n || ctx->pair_chain->d != o->d ||
                           ctx->pair_chain->dtype != o->chain_dtype ||
-                          ctx->pair_chain->host_levels != ((o->chain_flags & CDL_CHAIN_HOST_LEVELS) != 0))) {
+                          ctx->pair_chain->host_levels != ((o->chain_flags & CDL_CHAIN_HOST_LEVELS) != 0) ||
+                          ctx->pair_chain->resident !=
+                              std::min(o->d, (o->chain_flags & CDL_CHAIN_RESIDENT_MASK) >> CDL_CHAIN_RESIDENT_SHIFT))) {
     CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     cdl_chain_free(ctx->pair_chain);
     ctx->pair_chain = nullptr;

@@ -427,6 +427,68 @@ int square_impl(cdl_ctx* ctx, cdl_chain* ch, int level) {
   }
 }
 
+
+// ---- graphs regenerated in row panels (the pair driver's larger-than-memory form)
+// Level-0 rows r0 .. r0 + rows - 1 of a bf16 chain from a panel holding those
+// rows of A (A[(i - r0) n + j]): the same arithmetic as k_chain_init_tc, so
+// the level equals the one formed from the whole matrix; padding zero.
+__global__ void __launch_bounds__(256) k_panel_level0(const double* __restrict__ P, int n, int npad, int r0,
+                                                       int rows, const float* __restrict__ rsf,
+                                                       const float* __restrict__ uf, __nv_bfloat16* __restrict__ L0) {
+  const int gpr = npad / 8;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < (size_t)rows * gpr;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int i = r0 + (int)(g / gpr), j0 = (int)(g % gpr) * 8;
+    uint32_t wl[4] = {0, 0, 0, 0};
+    if (i < n) {
+      const float ri = rsf[i], ui = uf[i];
+      const double* row = P + (size_t)(i - r0) * n;
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        float v[2] = {0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = j0 + e + h;
+          if (j < n) v[h] = __fmaf_rn(d2f_rn_nonneg(row[j]), __fmul_rn(ri, rsf[j]), -__fmul_rn(ui, uf[j]));
+        }
+        const __nv_bfloat162 lv = __floats2bfloat162_rn(v[0], v[1]);
+        wl[e / 2] = *reinterpret_cast<const uint32_t*>(&lv);
+      }
+    }
+    *reinterpret_cast<uint4*>(L0 + (size_t)i * npad + j0) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+  }
+}
+
+// The six exact bf16 slices (grid48 with s = 0: Gaussian-kernel graphs have
+// A <= 1) of a panel of A holding rows r0 .. r0 + rows - 1 (A[(i - r0) n + j]),
+// transposed: plane t, row i, column c holds digit t of A[r0 + c][i] = A[i][r0 + c]
+// (A is symmetric), so each row i of a plane is a K-major operand row over the
+// panel's columns. Planes are npad x P; zero for i >= n or c >= rows. 32 x 32
+// tiles through shared memory: read along i, written along c.
+__global__ void __launch_bounds__(256) k_panel_slices_t(const double* __restrict__ P, int n, int npad, int r0,
+                                                         int rows, int Pw, uint16_t* __restrict__ S) {
+  __shared__ double tile[32][33];
+  const int ntc = Pw / 32, nti = npad / 32;
+  const size_t plane = (size_t)npad * Pw;
+  for (long long t = blockIdx.x; t < (long long)ntc * nti; t += gridDim.x) {
+    const int c0 = (int)(t % ntc) * 32, i0 = (int)(t / ntc) * 32;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int cc = e / 32, ii = e % 32;                   // panel row c0 + cc, column i0 + ii
+      const int c = c0 + cc, i = i0 + ii;
+      tile[cc][ii] = (c < rows && r0 + c < n && i < n) ? P[(size_t)c * n + i] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int ii = e / 32, cc = e % 32;                   // output row i0 + ii, column c0 + cc
+      uint32_t dg[6];
+      digits6_fbits(grid48(tile[cc][ii], 0), dg);
+      const size_t o = (size_t)(i0 + ii) * Pw + c0 + cc;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) S[(size_t)q * plane + o] = (uint16_t)(dg[q] >> 16);
+    }
+  }
+}
 }  // namespace
 
 int abs_max_bits(cdl_ctx* ctx, const double* x, size_t count, unsigned long long* out) {
@@ -611,6 +673,42 @@ int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void
     return L.done();
   }
   return CDL_ERR_UNSUPPORTED;
+}
+
+
+// Chain vectors (D^{-1/2}, u and their float copies) from the chain's D and
+// vol, for a chain whose level 0 is formed panel by panel.
+int chain_vectors_only(cdl_ctx* ctx, cdl_chain* ch) {
+  const int n = (int)ch->n, np = (int)ch->npad;
+  void* wsu;
+  CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * (sizeof(double) + 2 * sizeof(float)), &wsu));
+  double* u = static_cast<double*>(wsu);
+  float* rsf = reinterpret_cast<float*>(u + np);
+  float* uf = rsf + np;
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_chain_vectors<<<(np + 255) / 256, 256, 0, ctx->stream>>>(ch->D, ch->vol, n, np, ch->rsqrt_d, u, rsf, uf);
+  return L.done();
+}
+
+int chain_level0_panel(cdl_ctx* ctx, cdl_chain* ch, void* L0, const double* panel, int r0, int rows) {
+  const int n = (int)ch->n, np = (int)ch->npad;
+  if (ch->dtype != CDL_BF16 || r0 % 8) return CDL_ERR_UNSUPPORTED;
+  void* wsu;
+  CDL_TRY(ws_get(ctx, "chain.u", (size_t)np * (sizeof(double) + 2 * sizeof(float)), &wsu));
+  const float* rsf = reinterpret_cast<const float*>(static_cast<double*>(wsu) + np);
+  const float* uf = rsf + np;
+  Launch L(ctx, CDL_KC_CHAIN_INIT, 8.0 * rows * (double)n + 2.0 * rows * (double)np);
+  k_panel_level0<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(panel, n, np, r0, rows, rsf, uf,
+                                                             static_cast<__nv_bfloat16*>(L0));
+  return L.done();
+}
+
+int panel_slices_t(cdl_ctx* ctx, const double* panel, int n, int np, int r0, int rows, int Pw, void* slicesT) {
+  if (Pw % 32 || np % 32) return CDL_ERR_INVALID_ARG;
+  Launch L(ctx, CDL_KC_RESIDUAL, 0);
+  k_panel_slices_t<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(panel, n, np, r0, rows, Pw,
+                                                               static_cast<uint16_t*>(slicesT));
+  return L.done();
 }
 
 }  // namespace cdl

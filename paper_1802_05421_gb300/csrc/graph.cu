@@ -9,10 +9,12 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include <cuda_bf16.h>
 
 #include "ff.cuh"
+
 #include "internal.h"
 #include "tiles.cuh"
 
@@ -230,9 +232,11 @@ __global__ void k_select_init(SelectState* st, long long rank) {
 // Histogram of the `bits`-wide digit at `shift` over keys of the upper
 // triangle matching the current prefix.
 // rows r0, r0 + rstep, ... < r1 of the upper triangle
+// (A holds rows roff .. : row i at A + (i - roff) n)
 __device__ __forceinline__ void select_hist_rows(const double* __restrict__ A, int n, int shift, int bits,
                                                  const SelectState* __restrict__ st,
-                                                 unsigned long long* __restrict__ hist, int r0, int r1, int rstep) {
+                                                 unsigned long long* __restrict__ hist, int r0, int r1, int rstep,
+                                                 int roff = 0) {
   __shared__ unsigned int h[RADIX_BINS];
   for (int b = threadIdx.x; b < RADIX_BINS; b += blockDim.x) h[b] = 0;
   __syncthreads();
@@ -240,7 +244,7 @@ __device__ __forceinline__ void select_hist_rows(const double* __restrict__ A, i
   const unsigned long long dmask = (1ull << bits) - 1ull;
   const unsigned long long* K = reinterpret_cast<const unsigned long long*>(A);
   for (int i = r0; i < r1; i += rstep) {
-    const unsigned long long* row = K + (size_t)i * n;
+    const unsigned long long* row = K + (size_t)(i - roff) * n;
     for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
       unsigned long long key = row[j];
       if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & dmask], 1u);
@@ -255,6 +259,13 @@ __global__ void __launch_bounds__(512) k_select_hist(const double* __restrict__ 
                                                       int bits, const SelectState* __restrict__ st,
                                                       unsigned long long* __restrict__ hist) {
   select_hist_rows(A, n, shift, bits, st, hist, blockIdx.x, n - 1, gridDim.x);
+}
+
+// The same histogram over rows r0 .. r1 - 1 of a panel holding rows r0 ..
+__global__ void __launch_bounds__(512) k_select_hist_panel(const double* __restrict__ P, int n, int shift, int bits,
+                                                            const SelectState* __restrict__ st,
+                                                            unsigned long long* __restrict__ hist, int r0, int r1) {
+  select_hist_rows(P, n, shift, bits, st, hist, r0 + blockIdx.x, r1, gridDim.x, r0);
 }
 
 // The third pass: the histogram of select_hist_rows, and every key matching
@@ -360,10 +371,10 @@ enum { KERNEL_GAUSSIAN = 0, KERNEL_EXP = 1 };
 
 template <int KERN = KERNEL_GAUSSIAN>
 __device__ __forceinline__ void kernel_row(double* __restrict__ A, int n, double rcp, double* __restrict__ D,
-                                           int i, const ff* __restrict__ tab) {
+                                           int i, const ff* __restrict__ tab, int roff = 0) {
   __shared__ double red[8];
   {
-    double* row = A + (size_t)i * n;
+    double* row = A + (size_t)(i - roff) * n;
     const float rcpf = d2f_trunc(rcp);
     ff acc = {0.f, 0.f};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -410,6 +421,19 @@ __global__ void __launch_bounds__(256) k_kernel_rows(double* __restrict__ A, int
   ff_exp_table(tab);
   __syncthreads();
   for (int i = blockIdx.x; i < n; i += gridDim.x) kernel_row<KERN>(A, n, rcp, D, i, tab);
+}
+
+// Rows r0 .. r1 - 1 of a panel holding rows r0 .. (squared distances in,
+// kernel values out), their degrees into D[i].
+__global__ void __launch_bounds__(256) k_kernel_rows_panel(double* __restrict__ P, int n,
+                                                            const double* __restrict__ sigma, double* __restrict__ D,
+                                                            int r0, int r1) {
+  const double s = *sigma;
+  const double rcp = 1.0 / (2.0 * (s * s));
+  __shared__ ff tab[FF_EXP_TABLE];
+  ff_exp_table(tab);
+  __syncthreads();
+  for (int i = r0 + blockIdx.x; i < r1; i += gridDim.x) kernel_row<KERNEL_GAUSSIAN>(P, n, rcp, D, i, tab, r0);
 }
 
 // Kernel values over the upper block triangle of 64 x 64 tiles (A is
@@ -794,6 +818,113 @@ int graph_build(cdl_ctx* ctx, const double* X, int64_t n64, int T, double sigma,
     CDL_TRY(L.done());
   }
   return CDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Graphs too large to keep: the Gaussian-kernel graph regenerated from the
+// node series in row panels of P rows wherever it is needed. The series'
+// digit planes and squared norms are formed once (distances exact on the
+// tensor cores; inputs must lie on the 2^-16 grid), sigma by the same exact
+// radix select as graph_build with every histogram pass streaming the
+// upper-triangle part of each panel's distances, then the degrees from the
+// panels' kernel rows. The panel A values equal graph_build's (exact
+// distances, the same exponential), the degrees up to summation order.
+int graph_regen_init(cdl_ctx* ctx, RegenGraph& g, const double* X, int64_t n64, int T, double sigma, double* panel,
+                     int P) {
+  const int n = (int)n64;
+  cudaStream_t s = ctx->stream;
+  g.X = X;
+  g.n = n;
+  g.T = T;
+  g.rows = (n + 127) / 128 * 128;
+  g.tp = (T + 63) / 64 * 64;
+  const std::string tag = "regen." + std::to_string(g.id) + ".";
+  void *wsXi, *wsSt, *wsHist, *wsPl, *wsNo, *wsSc;
+  CDL_TRY(ws_get(ctx, (tag + "Xi").c_str(), (size_t)n * T * sizeof(int), &wsXi));
+  CDL_TRY(ws_get(ctx, (tag + "state").c_str(), sizeof(SelectState), &wsSt));
+  CDL_TRY(ws_get(ctx, (tag + "hist").c_str(), RADIX_BINS * sizeof(unsigned long long), &wsHist));
+  CDL_TRY(ws_get(ctx, (tag + "planes").c_str(), 3 * (size_t)g.rows * g.tp * 2, &wsPl));
+  CDL_TRY(ws_get(ctx, (tag + "norms").c_str(), (size_t)g.rows * sizeof(long long), &wsNo));
+  CDL_TRY(ws_get(ctx, (tag + "scalars").c_str(), 2 * sizeof(double), &wsSc));
+  SelectState* st = static_cast<SelectState*>(wsSt);
+  unsigned long long* hist = static_cast<unsigned long long*>(wsHist);
+  g.planes = wsPl;
+  g.norms = static_cast<const long long*>(wsNo);
+  g.offgrid = &st->flags;
+  g.sigma = static_cast<double*>(wsSc);
+  const long long m = (long long)n * (n - 1) / 2;
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_select_init<<<1, 1, 0, s>>>(st, (m - 1) / 2);
+    CDL_TRY(L.done());
+  }
+  CDL_CUDA_TRY(cudaMemsetAsync(hist, 0, RADIX_BINS * sizeof(unsigned long long), s));
+  {
+    const size_t total = (size_t)n * T;
+    Launch L(ctx, CDL_KC_DISTANCE, 0);
+    k_to_fixed<<<(int)std::min<size_t>((total + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, s>>>(
+        X, static_cast<int*>(wsXi), n, T, st);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_DISTANCE, 0);
+    const size_t cnt = (size_t)g.rows * g.tp;
+    k_slice_x<<<(unsigned)std::min<size_t>((cnt + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, s>>>(
+        X, n, T, g.rows, g.tp, static_cast<__nv_bfloat16*>(wsPl));
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_DISTANCE, 0);
+    k_row_norms<<<g.rows / 8, 256, 0, s>>>(X, n, T, g.rows, static_cast<long long*>(wsNo));
+    CDL_TRY(L.done());
+  }
+  int flags = 0;
+  CDL_CUDA_TRY(cudaMemcpyAsync(&flags, &st->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CDL_CUDA_TRY(cudaStreamSynchronize(s));
+  if (flags & 1) {
+    set_last_error("graph regeneration needs inputs on the 2^-16 grid", __FILE__, __LINE__);
+    return CDL_ERR_UNSUPPORTED;
+  }
+  if (sigma > 0) {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_set_scalar<<<1, 1, 0, s>>>(g.sigma, sigma);
+    CDL_TRY(L.done());
+  } else {
+    const int shifts[6] = {52, 40, 28, 16, 4, 0};
+    const int widths[6] = {12, 12, 12, 12, 12, 4};
+    for (int p = 0; p < 6; ++p) {
+      for (int r0 = 0; r0 < g.rows; r0 += P) {
+        const int pr = std::min(P, g.rows - r0);
+        CDL_TRY(dist_tc_panel(ctx, g.planes, g.norms, n, g.rows, g.tp, panel, r0, pr, true, g.offgrid));
+        const int r1 = std::min(n - 1, r0 + pr);
+        if (r1 <= r0) continue;
+        Launch L(ctx, CDL_KC_SELECT, 8.0 * (double)pr * n);
+        k_select_hist_panel<<<std::min(r1 - r0, ctx->sm_count * 4), 512, 0, s>>>(panel, n, shifts[p], widths[p], st,
+                                                                               hist, r0, r1);
+        CDL_TRY(L.done());
+      }
+      Launch L(ctx, CDL_KC_SELECT, 0);
+      k_select_step<<<1, 256, 0, s>>>(st, hist, shifts[p], widths[p], g.sigma, p == 5);
+      CDL_TRY(L.done());
+    }
+  }
+  // degrees: every panel's kernel rows once
+  for (int r0 = 0; r0 < n; r0 += P) {
+    const int pr = std::min(P, n - r0);
+    CDL_TRY(regen_panel(ctx, g, panel, r0, pr, g.D));
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_sum<<<1, 1024, 0, s>>>(g.D, n, g.vol);
+  return L.done();
+}
+
+int regen_panel(cdl_ctx* ctx, const RegenGraph& g, double* panel, int r0, int rows, double* D) {
+  const int pr = (int)std::min<long long>(round_up(rows, 128), g.rows - r0);
+  CDL_TRY(dist_tc_panel(ctx, g.planes, g.norms, g.n, g.rows, g.tp, panel, r0, pr, false, g.offgrid));
+  const int r1 = std::min(g.n, r0 + rows);
+  Launch L(ctx, CDL_KC_KERNEL, 16.0 * (double)(r1 - r0) * g.n);
+  k_kernel_rows_panel<<<std::min(r1 - r0, ctx->sm_count * 8), 256, 0, ctx->stream>>>(panel, g.n, g.sigma, D, r0, r1);
+  return L.done();
 }
 
 // ---------------------------------------------------------------------------

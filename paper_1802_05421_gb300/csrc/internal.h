@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -67,6 +68,7 @@ struct cdl_ctx {
   double kc_work[CDL_KC_COUNT] = {0};
   // chains owned by cdl_caddelag_pair
   cdl_chain* pair_chain = nullptr;
+  cdl_chain* regen_chain = nullptr;   // the chain of pairs whose graphs are regenerated in panels
   // tile schedules uploaded to the workspace, by workspace name -> tile count
   std::map<std::string, int> tile_lists;
   int debug_flags = 0;   // CDL_DEBUG_* test hooks
@@ -77,6 +79,10 @@ struct cdl_ctx {
   const double* amax_hint_A = nullptr;
   const unsigned long long* amax_hint_bits = nullptr;
 };
+
+namespace cdl {
+struct RegenSource;
+}
 
 struct cdl_chain {
   int device = 0;
@@ -99,9 +105,13 @@ struct cdl_chain {
   double* rsqrt_d = nullptr;  // npad: D_i^{-1/2} (0 in padding)
   double* D = nullptr;        // npad: degrees (0 in padding)
   double* vol = nullptr;      // 1
-  // CDL_CHAIN_HOST_LEVELS: `levels` is pinned host memory; two device slots
-  // hold the levels in use, filled and drained on a copy stream.
+  // CDL_CHAIN_HOST_LEVELS: levels 0 .. resident - 1 in device memory
+  // (dev_levels), the others in pinned host memory (`levels`, level i at
+  // (i - resident) npad^2); two device slots hold the host levels in use,
+  // filled and drained on a copy stream.
   bool host_levels = false;
+  int resident = 0;
+  void* dev_levels = nullptr;
   void* slot[2] = {nullptr, nullptr};
   int slot_level[2] = {-1, -1};
   int last_level = -1;                            // level written or read last
@@ -109,6 +119,9 @@ struct cdl_chain {
   cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // slot content complete
   cudaEvent_t ev_free[2] = {nullptr, nullptr};    // slot's last copy-out or reader done
   double link_bytes = 0;                          // host <-> device bytes moved
+  // Graphs not kept (cdl_caddelag_pair with CDL_PAIR_REGEN_GRAPHS): the solve
+  // forms A Z from the graph regenerated panel by panel.
+  const cdl::RegenSource* regen = nullptr;
   void* level(int i) const {
     return static_cast<char*>(levels) + (size_t)i * (size_t)npad * (size_t)npad * elem;
   }
@@ -178,9 +191,12 @@ int fp8_level_bound(cdl_ctx* ctx, cdl_chain* ch, int level);
 int level_inf_norm(cdl_ctx* ctx, const cdl_chain* ch, int level, unsigned* out_bits);
 int apply_simt(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* x, void* partial,
                int k, int splits);
-// ooc.cu: levels in pinned host memory (bf16 chains)
+// ooc.cu: levels in pinned host memory (bf16 chains), the first ch->resident
+// of them in device memory
 int ooc_init(cdl_chain* ch);
 void ooc_destroy(cdl_chain* ch);
+// Where level i lives (device pointer for resident levels, else host).
+void* ooc_level_ptr(const cdl_chain* ch, int i);
 // Device slot to write level i into (waits until the slot's old level is
 // saved and read); ooc_write_end saves it to the host on the copy stream.
 void* ooc_write_begin(cdl_ctx* ctx, cdl_chain* ch, int i);
@@ -387,6 +403,73 @@ struct ScoreJob {
 // cmax_all: the G x 2k column bounds the jobs point into (one block).
 int cad_score_grouped(cdl_ctx* ctx, const ScoreJob* jobs, int G, int k, bool fp64, int topk, BTiles elem,
                       BTiles pairs, BTiles nodes, double bytes, unsigned* cmax_all);
+
+// ---- graphs regenerated in row panels (larger than device memory) ----
+// A Gaussian-kernel graph kept only as its node series (graph.cu): exact
+// distances of grid inputs from three bf16 digit planes, sigma, degrees.
+struct RegenGraph {
+  int id = 0;                       // workspace tag (the graphs of a pair: 0, 1)
+  const double* X = nullptr;        // n x T, on the 2^-16 grid
+  int n = 0, T = 0, rows = 0, tp = 0;
+  const void* planes = nullptr;     // three bf16 digit planes, rows x tp
+  const long long* norms = nullptr; // |a_i|^2
+  const int* offgrid = nullptr;     // bit 0: input off the grid
+  double* sigma = nullptr;          // device
+  double* D = nullptr;              // device n (the caller's)
+  double* vol = nullptr;            // device 1 (the caller's)
+};
+// Planes, norms, sigma (lower median unless sigma > 0), D and vol; `panel`
+// is P x n float64 scratch.
+int graph_regen_init(cdl_ctx* ctx, RegenGraph& g, const double* X, int64_t n, int T, double sigma, double* panel,
+                     int P);
+// Rows r0 .. r0 + rows - 1 of A into panel (A[(i - r0) n + j]), their
+// degrees into D[i] (r0 a multiple of 128, rows <= the panel's rows).
+int regen_panel(cdl_ctx* ctx, const RegenGraph& g, double* panel, int r0, int rows, double* D);
+// What the solve needs to form A Z of such a graph.
+struct RegenSource {
+  const RegenGraph* g = nullptr;
+  double* panel = nullptr;          // P x n float64
+  void* slicesT = nullptr;          // 6 x npad x P bf16 (transposed exact slices of a panel)
+  double* Dscratch = nullptr;       // n (degrees recomputed by each regeneration)
+  int P = 0;
+};
+// tc_gemm.cu: squared distances of a panel (rows row0 .. row0 + prows - 1,
+// multiples of 128) into panel[(i - row0) n + j]: whole rows, or (upper)
+// only the tiles of the upper block triangle.
+int dist_tc_panel(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* panel,
+                  int row0, int prows, bool upper, const int* offgrid);
+// G (npad x kp) += A[:, c0 .. c0 + Pk) Z[c0 .. c0 + Pk) from the transposed
+// exact slices of the panel (6 planes npad x Pw, Pk <= Pw columns in use,
+// multiples of 256) and Z / c's slices (6 planes kp x npad).
+int resid_tc_panel(cdl_ctx* ctx, const void* slicesT, int np, int Pw, int Pk, int c0, const void* zslices, int kp,
+                   double* G);
+// Score tiles tile0 .. tile1 - 1 of the upper-triangle numbering (tile1 < 0:
+// all), A1 and A2 holding rows row0 .. (A[(i - row0) n + j]).
+int score_tc_tiles(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long long* dint,
+                   const double* oscale, int n, int rows, int k2p, const double* A1, const double* A2, int row0,
+                   long long tile0, long long tile1, double* contrib);
+// chain.cu: chain vectors from ch->D and ch->vol; level-0 rows from a panel;
+// the panel's transposed exact slices.
+int chain_vectors_only(cdl_ctx* ctx, cdl_chain* ch);
+int chain_level0_panel(cdl_ctx* ctx, cdl_chain* ch, void* L0, const double* panel, int r0, int rows);
+int panel_slices_t(cdl_ctx* ctx, const double* panel, int n, int np, int r0, int rows, int Pw, void* slicesT);
+// project.cu: rows r0 .. r0 + rows - 1 of Y from a panel; column centring.
+int project_panel(cdl_ctx* ctx, const double* panel, int64_t n, int r0, int rows, int k, uint64_t seed, double* Y,
+                  const unsigned long long* amax_bits);
+int project_center(cdl_ctx* ctx, int64_t n, int k, double* Y);
+// score.cu: CAD scores (bf16 tensor-core Gram) with A1 and A2 supplied row
+// panel by row panel: fill(r0, rows, &A1, &A2) makes rows r0 .. r0 + rows - 1
+// of both graphs available.
+int cad_score_panels(cdl_ctx* ctx, const double* Z1, const double* Z2, const double* vol1, const double* vol2,
+                     int64_t n, int k, int P,
+                     const std::function<int(int r0, int rows, const double** A1, const double** A2)>& fill, int topk,
+                     double* F, int64_t* top_idx);
+// regen.cu: the whole pair with graphs regenerated in row panels.
+int pair_regen(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n, int T, const cdl_pair_opts* o,
+               double* F, int64_t* top_idx, cdl_solve_stats* stats1, cdl_solve_stats* stats2);
+// api.cu: a bf16 chain for graphs given by panels (no A operands), levels
+// 0 .. resident - 1 on the device, the rest in pinned host memory.
+int chain_create_regen(cdl_ctx* ctx, int64_t n, int d, int resident, cdl_chain** out);
 
 // solve.cu
 int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,

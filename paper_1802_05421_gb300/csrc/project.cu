@@ -72,10 +72,12 @@ __host__ __device__ inline size_t project_smem_bytes(int rpb, int W) {
 // Rows [bidx * rpb, bidx * rpb + rpb) of Y over the edges to nodes j in
 // [jbeg, jend) (jbeg a multiple of CHUNK): written, not accumulated, and
 // multiplied by `scale` when `final` (otherwise left unscaled: a partial sum).
+// With a row window [r0, r1) (r1 > 0) the rows are r0 + bidx * rpb ... < r1
+// and A holds rows r0 .. (A[(i - r0) n + j]).
 __device__ __forceinline__ void project_rows_block(const double* __restrict__ A, int n, int k, int W, int rpb,
                                                    uint32_t key0, uint32_t key1, double scale,
                                                    double* __restrict__ Y, int bidx, int gexp, int jbeg, int jend,
-                                                   bool final) {
+                                                   bool final, int r0 = 0, int r1 = 0) {
   // piece grids 2^(gexp - 12) and 2^(gexp - 24) (gexp = h of the comment above)
   const float up1 = __int_as_float((127 + 12 - gexp) << 23), dn1 = __int_as_float((127 - 12 + gexp) << 23);
   const float up2 = __int_as_float((127 + 24 - gexp) << 23), dn2 = __int_as_float((127 - 24 + gexp) << 23);
@@ -90,9 +92,10 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
   const int t = threadIdx.x;
   const int rl = t / H, h = t % H;
   const int w = h >> 1, shift = (h & 1) * RB;
-  const int i0 = bidx * rpb;
+  const int rend = r1 > 0 ? r1 : n;
+  const int i0 = r0 + bidx * rpb;
   const int i = i0 + rl;
-  const bool active = rl < rpb && i < n;
+  const bool active = rl < rpb && i < rend;
   // With s = 2 bit - 1, sum_j s x_j = 2 sum_{bit set} x_j - sum_j x_j: the
   // a-accumulators take the terms whose sign bit is set (one predicated add per
   // piece), t the plain totals (shared by all projection rows of the thread).
@@ -123,8 +126,8 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
       const int rr = e / JT, jj = e % JT;
       const int ii = i0 + rr, j = j0 + jj;
       float p1 = 0.f, p2 = 0.f, p3 = 0.f;
-      if (ii < n && j < jend && j != ii) {
-        const ff a = split_nonneg(A[(size_t)ii * n + j]);   // integer split, no float64 ops
+      if (ii < rend && j < jend && j != ii) {
+        const ff a = split_nonneg(A[(size_t)(ii - r0) * n + j]);   // integer split, no float64 ops
         const float ah = a.hi, al = a.lo;
         if (ah > 0.f) {
           // sqrt(ah + al) = sh + sl with sl = (ah - sh^2 + al) / (2 sh)
@@ -152,7 +155,7 @@ __device__ __forceinline__ void project_rows_block(const double* __restrict__ A,
       const int rr = e / JT, jj = e % JT;
       const int ii = i0 + rr, j = j0 + jj;
       uint4 o = make_uint4(0u, 0u, 0u, 0u);
-      if (ii < n && j < jend && j != ii)
+      if (ii < rend && j < jend && j != ii)
         o = philox4x32_10(make_uint4((uint32_t)min(ii, j), (uint32_t)max(ii, j), (uint32_t)rb, 0u), key0, key1);
       Wd[rr * WS + jj * nrb + rb] = o;
     }
@@ -202,6 +205,17 @@ __global__ void __launch_bounds__(256, 2) k_project(const double* __restrict__ A
   const int jbeg = split * CHUNK, jend = nsplit == 1 ? n : min(n, jbeg + CHUNK);
   project_rows_block(A, n, k, W, rpb, key0, key1, scale, Y + (size_t)split * n * k, blockIdx.x, h, jbeg, jend,
                      nsplit == 1);
+}
+
+// Rows r0 .. r1 - 1 of Y (unscaled sums, then scaled) from a panel holding
+// those rows of A (A[(i - r0) n + j]); block b covers rows r0 + b rpb ...
+__global__ void __launch_bounds__(256, 2) k_project_panel(const double* __restrict__ P, int n, int k, int W, int rpb,
+                                                           uint32_t key0, uint32_t key1, double scale,
+                                                           double* __restrict__ Y,
+                                                           const unsigned long long* __restrict__ amax_bits, int r0,
+                                                           int r1) {
+  const int h = min((pow2_exp_above(*amax_bits) + 1) / 2, 100);
+  project_rows_block(P, n, k, W, rpb, key0, key1, scale, Y, blockIdx.x, h, 0, n, true, r0, r1);
 }
 
 __global__ void k_project_sum(const double* __restrict__ part, int nsplit, size_t count, double scale,
@@ -292,6 +306,51 @@ __global__ void k_g_sub_mean(const uint32_t* __restrict__ tiles, const PGraph* _
 
 }  // namespace
 
+int project_panel(cdl_ctx* ctx, const double* panel, int64_t n64, int r0, int rows, int k, uint64_t seed,
+                  double* Y, const unsigned long long* amax_bits) {
+  const int n = (int)n64;
+  const int W = (k + 31) / 32;
+  const int rpb = std::max(1, std::min(MAX_RPB, 256 / (2 * W)));
+  const int threads = rpb * 2 * W;
+  const size_t smem = project_smem_bytes(rpb, W);
+  const int r1 = std::min(n, r0 + rows);
+  const int blocks = (r1 - r0 + rpb - 1) / rpb;
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_project_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr = true;
+  }
+  if (blocks <= 0) return CDL_OK;
+  Launch L(ctx, CDL_KC_PROJECT, (double)(r1 - r0) * (n - 1) * k);
+  k_project_panel<<<blocks, threads, smem, ctx->stream>>>(panel, n, k, W, rpb, (uint32_t)(seed & 0xffffffffu),
+                                                          (uint32_t)(seed >> 32), 1.0 / std::sqrt((double)k), Y,
+                                                          amax_bits, r0, r1);
+  return L.done();
+}
+
+// Y -= column means (the exact Y has zero column sums), over all n rows.
+int project_center(cdl_ctx* ctx, int64_t n64, int k, double* Y) {
+  const int n = (int)n64;
+  const int nparts = (n + 255) / 256;
+  void* vpart;
+  CDL_TRY(ws_get(ctx, "project.colsum", (size_t)(nparts + 1) * k * sizeof(double), &vpart));
+  double* part = static_cast<double*>(vpart);
+  double* mean = part + (size_t)nparts * k;
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_colsum<<<nparts, 256, 0, ctx->stream>>>(Y, n, k, part);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_col_mean<<<(k + 255) / 256, 256, 0, ctx->stream>>>(part, nparts, n, k, mean);
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_MISC, 0);
+  k_sub_mean<<<(unsigned)(((size_t)n * k + 255) / 256), 256, 0, ctx->stream>>>(Y, n, k, mean);
+  return L.done();
+}
+
 int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, double* Y,
             const unsigned long long* amax_bits) {
   const int n = (int)n64;
@@ -338,24 +397,7 @@ int project(cdl_ctx* ctx, const double* A, int64_t n64, int k, uint64_t seed, do
         out, nsplit, cnt, scale, Y);
     CDL_TRY(L.done());
   }
-  const int nparts = (n + 255) / 256;
-  void* vpart;
-  CDL_TRY(ws_get(ctx, "project.colsum", (size_t)(nparts + 1) * k * sizeof(double), &vpart));
-  double* part = static_cast<double*>(vpart);
-  double* mean = part + (size_t)nparts * k;
-  {
-    Launch L2(ctx, CDL_KC_MISC, 0);
-    k_colsum<<<nparts, 256, 0, ctx->stream>>>(Y, n, k, part);
-    CDL_TRY(L2.done());
-  }
-  {
-    Launch L2(ctx, CDL_KC_MISC, 0);
-    k_col_mean<<<(k + 255) / 256, 256, 0, ctx->stream>>>(part, nparts, n, k, mean);
-    CDL_TRY(L2.done());
-  }
-  Launch L3(ctx, CDL_KC_MISC, 0);
-  k_sub_mean<<<(unsigned)(((size_t)n * k + 255) / 256), 256, 0, ctx->stream>>>(Y, n, k, mean);
-  return L3.done();
+  return project_center(ctx, n, k, Y);
 }
 
 int project_rows_per_block(int k) {

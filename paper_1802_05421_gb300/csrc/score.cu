@@ -1003,6 +1003,99 @@ int score_prepare(cdl_ctx* ctx, const double* Z1, const double* Z2, const double
   return L.done();
 }
 
+namespace {
+// The Z side of the tensor-core scores: column scales, the six slice planes
+// of u / c and v / c, d_i in units of c^2 2^-48.
+struct TcScorePrep {
+  int rows = 0, k2p = 0;
+  const void* u = nullptr;
+  const void* v = nullptr;
+  const long long* d = nullptr;
+  const double* oscale = nullptr;
+};
+
+int tc_score_prepare(cdl_ctx* ctx, const double* Z1, const double* Z2, const double* vol1, const double* vol2, int n,
+                     int k, TcScorePrep& q) {
+  cudaStream_t st = ctx->stream;
+  const int rows = (n + 127) / 128 * 128, k2p = (2 * k + 63) / 64 * 64;
+  void *vcm, *vg, *vcs, *vu, *vv, *vd;
+  CDL_TRY(ws_get(ctx, "score.tc.cmax", 2 * (size_t)k * sizeof(unsigned long long), &vcm));
+  CDL_TRY(ws_get(ctx, "score.tc.g", (size_t)k * sizeof(double), &vg));
+  CDL_TRY(ws_get(ctx, "score.tc.scale", 2 * sizeof(double), &vcs));
+  CDL_TRY(ws_get(ctx, "score.tc.u", 6 * (size_t)rows * k2p * 2, &vu));
+  CDL_TRY(ws_get(ctx, "score.tc.v", 6 * (size_t)rows * k2p * 2, &vv));
+  CDL_TRY(ws_get(ctx, "score.tc.d", (size_t)rows * sizeof(long long), &vd));
+  unsigned long long* cm = static_cast<unsigned long long*>(vcm);
+  double* cs = static_cast<double*>(vcs);
+  CDL_CUDA_TRY(cudaMemsetAsync(cm, 0, 2 * (size_t)k * sizeof(unsigned long long), st));
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_tcs_colmax<<<(unsigned)std::min(n, ctx->sm_count * 4), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cm);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_tcs_scales<<<1, 256, 0, st>>>(cm, k, static_cast<double*>(vg), cs);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    const size_t cnt = (size_t)rows * k2p;
+    k_tcs_slice<<<(unsigned)std::min<size_t>((cnt + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, st>>>(
+        Z1, Z2, vol1, vol2, n, k, rows, k2p, static_cast<const double*>(vg), cs, static_cast<__nv_bfloat16*>(vu),
+        static_cast<__nv_bfloat16*>(vv));
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_tcs_diag<<<(rows + 7) / 8, 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, rows, cs, static_cast<long long*>(vd));
+    CDL_TRY(L.done());
+  }
+  q.rows = rows;
+  q.k2p = k2p;
+  q.u = vu;
+  q.v = vv;
+  q.d = static_cast<const long long*>(vd);
+  q.oscale = cs + 1;
+  return CDL_OK;
+}
+}  // namespace
+
+int cad_score_panels(cdl_ctx* ctx, const double* Z1, const double* Z2, const double* vol1, const double* vol2,
+                     int64_t n64, int k, int P,
+                     const std::function<int(int r0, int rows, const double** A1, const double** A2)>& fill, int topk,
+                     double* F, int64_t* top_idx) {
+  const int n = (int)n64;
+  if (P % 128 || P <= 0) return CDL_ERR_INVALID_ARG;
+  cudaStream_t st = ctx->stream;
+  const int nb = (n + ST - 1) / ST;
+  void* vc;
+  CDL_TRY(ws_get(ctx, "score.contrib", (size_t)nb * n * sizeof(double), &vc));
+  TcScorePrep q;
+  CDL_TRY(tc_score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, q));
+  const long long nb64 = 2 * (q.rows / 128);
+  auto off = [&](long long I) { return I * nb64 - I * (I - 1); };   // first upper tile of 128-row block I
+  for (int r0 = 0; r0 < n; r0 += P) {
+    const int rows = std::min(P, n - r0);
+    const double *a1 = nullptr, *a2 = nullptr;
+    CDL_TRY(fill(r0, rows, &a1, &a2));
+    const long long I0 = r0 / 128, I1 = (r0 + rows + 127) / 128;
+    CDL_TRY(score_tc_tiles(ctx, q.u, q.v, q.d, q.oscale, n, q.rows, q.k2p, a1, a2, r0, off(I0), off(I1),
+                           static_cast<double*>(vc)));
+  }
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_score_reduce<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const double*>(vc), nb, n, F);
+    CDL_TRY(L.done());
+  }
+  if (topk > 0) {
+    Launch L(ctx, CDL_KC_TOPK, 0);
+    k_topk<<<1, 1024, 0, st>>>(F, n, topk, top_idx);
+    CDL_TRY(L.done());
+  }
+  return CDL_OK;
+}
+
 int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1, const double* Z2,
               const double* vol1, const double* vol2, int64_t n64, int k, cdl_dtype score_dtype, int topk,
               double* F, int64_t* top_idx) {
@@ -1015,43 +1108,9 @@ int cad_score(cdl_ctx* ctx, const double* A1, const double* A2, const double* Z1
   CDL_TRY(ws_get(ctx, "score.contrib", (size_t)nb * n * sizeof(double), &vc));
   if (score_dtype == CDL_BF16) {
     // Gram on the tensor cores from exact bf16 slices
-    const int rows = (n + 127) / 128 * 128, k2p = (2 * k + 63) / 64 * 64;
-    void *vcm, *vg, *vcs, *vu, *vv, *vd;
-    CDL_TRY(ws_get(ctx, "score.tc.cmax", 2 * (size_t)k * sizeof(unsigned long long), &vcm));
-    CDL_TRY(ws_get(ctx, "score.tc.g", (size_t)k * sizeof(double), &vg));
-    CDL_TRY(ws_get(ctx, "score.tc.scale", 2 * sizeof(double), &vcs));
-    CDL_TRY(ws_get(ctx, "score.tc.u", 6 * (size_t)rows * k2p * 2, &vu));
-    CDL_TRY(ws_get(ctx, "score.tc.v", 6 * (size_t)rows * k2p * 2, &vv));
-    CDL_TRY(ws_get(ctx, "score.tc.d", (size_t)rows * sizeof(long long), &vd));
-    unsigned long long* cm = static_cast<unsigned long long*>(vcm);
-    double* cs = static_cast<double*>(vcs);
-    CDL_CUDA_TRY(cudaMemsetAsync(cm, 0, 2 * (size_t)k * sizeof(unsigned long long), st));
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_tcs_colmax<<<(unsigned)std::min(n, ctx->sm_count * 4), 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, cm);
-      CDL_TRY(L.done());
-    }
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_tcs_scales<<<1, 256, 0, st>>>(cm, k, static_cast<double*>(vg), cs);
-      CDL_TRY(L.done());
-    }
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      const size_t cnt = (size_t)rows * k2p;
-      k_tcs_slice<<<(unsigned)std::min<size_t>((cnt + 255) / 256, (size_t)ctx->sm_count * 8), 256, 0, st>>>(
-          Z1, Z2, vol1, vol2, n, k, rows, k2p, static_cast<const double*>(vg), cs,
-          static_cast<__nv_bfloat16*>(vu), static_cast<__nv_bfloat16*>(vv));
-      CDL_TRY(L.done());
-    }
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_tcs_diag<<<(rows + 7) / 8, 256, 0, st>>>(Z1, Z2, vol1, vol2, n, k, rows, cs,
-                                                 static_cast<long long*>(vd));
-      CDL_TRY(L.done());
-    }
-    CDL_TRY(score_tc(ctx, vu, vv, static_cast<const long long*>(vd), cs + 1, n, rows, k2p, A1, A2,
-                     static_cast<double*>(vc)));
+    TcScorePrep q;
+    CDL_TRY(tc_score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, q));
+    CDL_TRY(score_tc(ctx, q.u, q.v, q.d, q.oscale, n, q.rows, q.k2p, A1, A2, static_cast<double*>(vc)));
   } else {
   CDL_TRY(score_prepare(ctx, Z1, Z2, vol1, vol2, n, k, fp64, &vab));
   const long long tiles = (long long)nb * (nb + 1) / 2;

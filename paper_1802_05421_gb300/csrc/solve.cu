@@ -891,6 +891,50 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
   int nparts = res_gx * res_gy;   // per-block partial sums of R^2 written by the last residual kernel
   // Full float-float residual R = Y - L Z.
   auto full_residual = [&](double* rel_out) -> int {
+    if (ch->regen) {
+      // A Z of a graph regenerated panel by panel: each panel's transposed
+      // exact slices are one K range of A Z (A symmetric), added into G
+      const RegenSource& rs = *ch->regen;
+      const int ngroups = (k + 127) / 128;
+      void *vzs, *vG, *vmb, *vcs;
+      CDL_TRY(ws_get(ctx, "solve.zslices", 6 * (size_t)128 * np * 2, &vzs));
+      CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * np * 128 * sizeof(double), &vG));
+      CDL_TRY(ws_get(ctx, "solve.zmax", (size_t)k * 8, &vmb));
+      CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcs));
+      CDL_CUDA_TRY(cudaMemsetAsync(vmb, 0, (size_t)k * 8, st));
+      {
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_zcolmax<<<std::min<size_t>(blocks_for(nk, 256), (size_t)ctx->sm_count * 8), 256, 0, st>>>(
+            Z, nk, k, static_cast<unsigned long long*>(vmb));
+        CDL_TRY(L.done());
+      }
+      for (int g = 0; g < ngroups; ++g) {
+        const int c0 = g * 128;
+        const int kg = std::min(128, (k - c0 + 31) / 32 * 32);
+        double* Gg = static_cast<double*>(vG) + (size_t)g * np * 128;
+        {
+          Launch L(ctx, CDL_KC_MISC, 0);
+          k_zslice<<<ctx->sm_count * 4, 256, 0, st>>>(Z, n, k, np, c0, kg,
+                                                       static_cast<const unsigned long long*>(vmb),
+                                                       static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcs));
+          CDL_TRY(L.done());
+        }
+        CDL_CUDA_TRY(cudaMemsetAsync(Gg, 0, (size_t)np * kg * sizeof(double), st));
+        for (int r0 = 0; r0 < n; r0 += rs.P) {
+          const int rows = std::min(rs.P, n - r0);
+          CDL_TRY(regen_panel(ctx, *rs.g, rs.panel, r0, rows, rs.Dscratch));
+          CDL_TRY(panel_slices_t(ctx, rs.panel, n, np, r0, rows, rs.P, rs.slicesT));
+          CDL_TRY(resid_tc_panel(ctx, rs.slicesT, np, rs.P, std::min(rs.P, np - r0), r0, vzs, kg, Gg));
+        }
+      }
+      const int nb = std::min(1024, (int)blocks_for(nk, 256));
+      Launch L(ctx, CDL_KC_RESIDUAL, 0);
+      k_resid_combine<<<nb, 256, 0, st>>>(Y, Z, ch->D, n, k, np, static_cast<const double*>(vG),
+                                          static_cast<const double*>(vcs), ch->a_scale, R, red);
+      CDL_TRY(L.done());
+      nparts = nb;
+      return CDL_OK;
+    }
     if (ch->aslices) {
       // A Z from exact bf16 slices on the tensor cores, in column groups of <= 128
       const int ngroups = (k + 127) / 128;
@@ -985,7 +1029,8 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
   int iters = 0;
   bool exact_r = true;      // R was last formed in full (not recursively)
   double drift = 0.0;       // bound on the recursive residual's accumulated error
-  const bool always_full = (opts->flags & CDL_SOLVE_FULL_RESIDUAL) != 0;
+  // a regenerated graph keeps no A operand for the recursive update
+  const bool always_full = (opts->flags & CDL_SOLVE_FULL_RESIDUAL) != 0 || ch->regen != nullptr;
   while (true) {
     if (opts->rel_tol > 0 && rel <= opts->rel_tol) {
       if (!exact_r && rel + drift > 0.1 * opts->rel_tol) {

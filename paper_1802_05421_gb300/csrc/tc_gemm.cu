@@ -822,6 +822,16 @@ struct DistParams {
   const int* offgrid;         // bit 0 set: input off the grid (the float64 kernel runs instead)
   uint32_t idesc;
   unsigned* status;
+  // Row panels (graphs regenerated panel by panel): A holds rows row0 ..
+  // (A[(i - row0) n + j]), nothing is mirrored, and the tiles are either the
+  // upper-triangle tiles tile0 .. tile0 + num_tiles - 1 (rect = 0; the rows of
+  // the panel when the range is the panel's row blocks) or every tile
+  // (I0 + t / nb64, t % nb64) of the panel's rect row blocks (rect > 0: whole rows).
+  int panel;
+  int row0;
+  long long tile0;
+  int rect;
+  int I0;
 };
 
 // tile t -> (I, J): row block I holds nb64 - 2 I tiles J = 2 I .. nb64 - 1
@@ -834,6 +844,15 @@ __device__ __forceinline__ void dist_tile(int t, int nb128, int nb64, int& I, in
   }
   I = lo;
   J = 2 * lo + (int)(t - ((long long)lo * nb64 - (long long)lo * (lo - 1)));
+}
+
+__device__ __forceinline__ void dist_decode(const DistParams& p, int t, int& I, int& J) {
+  if (p.rect > 0) {
+    I = p.I0 + t / p.nb64;
+    J = t % p.nb64;
+  } else {
+    dist_tile((int)(t + p.tile0), p.nb128, p.nb64, I, J);
+  }
 }
 
 __global__ void __launch_bounds__(T8_THREADS, 1)
@@ -884,7 +903,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
       int I, J;
-      dist_tile(t, p.nb128, p.nb64, I, J);
+      dist_decode(p, t, I, J);
       // one stage per K block: the three digit planes of the row block and of the column block
       for (int kb = 0; kb < p.kblocks && ok; ++kb, ++it) {
         const int s = it % DS_STAGES;
@@ -967,7 +986,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     bool failed = false;
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
       int I, J;
-      dist_tile(t, p.nb128, p.nb64, I, J);
+      dist_decode(p, t, I, J);
       long long g[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) g[e] = 0;
@@ -996,7 +1015,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       const bool rowok = row < p.n;
       const long long ni = rowok ? p.norms[row] : 0;
       const int col0 = J * DS_N + part * 16;
-      const bool mirror = J >= 2 * I + 2;                // off the diagonal 128-block
+      const bool mirror = !p.panel && J >= 2 * I + 2;    // off the diagonal 128-block
       double* stg = stage + (warp - 2) * (32 * 17);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
@@ -1015,7 +1034,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       for (int it = 0; it < 16; ++it) {
         const int rr = 2 * it + (lane >> 4), c = lane & 15;
         const int grow = I * 128 + q * 32 + rr, gcol = col0 + c;
-        if (grow < p.n && gcol < p.n) p.A[(size_t)grow * p.n + gcol] = stg[rr * 17 + c];
+        if (grow < p.n && gcol < p.n) p.A[(size_t)(grow - p.row0) * p.n + gcol] = stg[rr * 17 + c];
       }
       __syncwarp();
     }
@@ -1073,6 +1092,8 @@ struct ScoreMaps {
 
 struct ScoreParams {
   int nb128, nb64, num_tiles, kblocks, n;
+  long long tile0;            // first tile of the upper-triangle numbering
+  int row0;                   // A1, A2 hold rows row0 .. (A[(i - row0) n + j])
   const double* A1;
   const double* A2;
   const long long* dint;      // d_i in units of c^2 2^-48 (padded rows 0)
@@ -1143,7 +1164,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
       int I, J;
-      dist_tile(t, p.nb128, p.nb64, I, J);
+      dist_tile((int)(t + p.tile0), p.nb128, p.nb64, I, J);
       for (int kb = 0; kb < p.kblocks && ok; ++kb)
         for (int h = 0; h < 2 && ok; ++h, ++it) {
           const int s = it % SC_STAGES;
@@ -1233,12 +1254,12 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     bool failed = false;
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
       int I, J;
-      dist_tile(t, p.nb128, p.nb64, I, J);
+      dist_tile((int)(t + p.tile0), p.nb128, p.nb64, I, J);
       {
         // bring this thread's A1 and A2 row segments into L2 while the MMAs run
         const int prow = I * 128 + q * 32 + lane, pc0 = J * SC_N + part * 16;
         if (prow < p.n && pc0 < p.n) {
-          const size_t o0 = (size_t)prow * p.n + pc0, o1 = o0 + min(15, p.n - 1 - pc0);
+          const size_t o0 = (size_t)(prow - p.row0) * p.n + pc0, o1 = o0 + min(15, p.n - 1 - pc0);
           asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o0));
           asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o0));
           asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A1 + o1));
@@ -1294,7 +1315,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         if (rowok && col < p.n && (br < J || row < col)) {
           const long long dc = di + p.dint[col] - m[e];
           const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
-          const size_t o = (size_t)row * p.n + col;
+          const size_t o = (size_t)(row - p.row0) * p.n + col;
           x = ff_mul(split_nonneg(fabs(p.A1[o] - p.A2[o])), ff_from_u64(adc));
         }
         ev[e] = x;
@@ -1758,11 +1779,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D tensor map over a rows x cols row-major matrix of bf16 (elem = 2) or
 // fp8 bytes (elem = 1); box = one 128-byte row segment x box_rows.
-int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows, int elem = 2) {
+// 2-D tensor map of a row-major matrix (rows x cols, `stride` elements
+// between rows, 0 = cols), 128-byte boxes of box_rows rows, 128-byte swizzle.
+int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows, int elem = 2,
+             int64_t stride = 0) {
   auto fn = encode_fn();
   if (!fn) return CDL_ERR_UNSUPPORTED;
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)cols * elem};
+  cuuint64_t gstride[1] = {(cuuint64_t)(stride ? stride : cols) * elem};
   cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
@@ -2083,9 +2107,8 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
   return L.done();
 }
 
-int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
-            const int* offgrid, double terms) {
-  if (rows % 128 || tp % 64 || rows < n || tp < 64) return CDL_ERR_INVALID_ARG;
+namespace {
+int dist_launch(cdl_ctx* ctx, const void* planes, int rows, int tp, DistParams& p, double terms) {
   DistMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int s = 0; s < DS_SLICES; ++s) {
@@ -2093,18 +2116,7 @@ int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int
     CDL_TRY(make_map(&maps.a[s], base, rows, tp, 128));
     CDL_TRY(make_map(&maps.b[s], base, rows, tp, DS_N));
   }
-  DistParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.nb128 = rows / 128;
-  p.nb64 = 2 * p.nb128;
-  const long long tiles = (long long)p.nb128 * p.nb64 - (long long)p.nb128 * (p.nb128 - 1);
-  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
-  p.num_tiles = (int)tiles;
   p.kblocks = tp / 64;
-  p.n = n;
-  p.norms = norms;
-  p.A = A;
-  p.offgrid = offgrid;
   p.idesc = make_idesc(DS_N);
   p.status = ctx->dev_status;
   static bool attr = false;
@@ -2112,14 +2124,107 @@ int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, DS_SMEM_BYTES));
     attr = true;
   }
-  const int grid = (int)std::min<long long>(tiles, ctx->sm_count);
-  Launch L(ctx, CDL_KC_DISTANCE, terms);   // algorithmic work: n (n - 1) T / 2 squared differences
+  if (p.num_tiles <= 0) return CDL_OK;
+  const int grid = std::min(p.num_tiles, ctx->sm_count);
+  Launch L(ctx, CDL_KC_DISTANCE, terms);
   k_tc_dist<<<grid, T8_THREADS, DS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
 }
+}  // namespace
 
-int score_tc(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long long* dint, const double* oscale,
-             int n, int rows, int k2p, const double* A1, const double* A2, double* contrib) {
+int dist_tc(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* A,
+            const int* offgrid, double terms) {
+  if (rows % 128 || tp % 64 || rows < n || tp < 64) return CDL_ERR_INVALID_ARG;
+  DistParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nb128 = rows / 128;
+  p.nb64 = 2 * p.nb128;
+  const long long tiles = (long long)p.nb128 * p.nb64 - (long long)p.nb128 * (p.nb128 - 1);
+  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  p.num_tiles = (int)tiles;
+  p.n = n;
+  p.norms = norms;
+  p.A = A;
+  p.offgrid = offgrid;
+  // algorithmic work: n (n - 1) T / 2 squared differences
+  return dist_launch(ctx, planes, rows, tp, p, terms);
+}
+
+int dist_tc_panel(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* panel,
+                  int row0, int prows, bool upper, const int* offgrid) {
+  if (rows % 128 || tp % 64 || rows < n || tp < 64 || row0 % 128 || prows % 128 || prows <= 0 ||
+      row0 + prows > rows)
+    return CDL_ERR_INVALID_ARG;
+  DistParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nb128 = rows / 128;
+  p.nb64 = 2 * p.nb128;
+  p.n = n;
+  p.norms = norms;
+  p.A = panel;
+  p.offgrid = offgrid;
+  p.panel = 1;
+  p.row0 = row0;
+  const int I0 = row0 / 128, PI = prows / 128;
+  auto off = [&](long long I) { return I * p.nb64 - I * (I - 1); };   // first upper tile of row block I
+  long long tiles;
+  if (upper) {
+    p.tile0 = off(I0);
+    tiles = off(I0 + PI) - off(I0);
+  } else {
+    p.rect = PI;
+    p.I0 = I0;
+    tiles = (long long)PI * p.nb64;
+  }
+  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  p.num_tiles = (int)tiles;
+  const double terms = (double)tiles * 128.0 * DS_N * tp;
+  return dist_launch(ctx, planes, rows, tp, p, terms);
+}
+
+int resid_tc_panel(cdl_ctx* ctx, const void* slicesT, int np, int Pw, int Pk, int c0, const void* zslices, int kp,
+                   double* G) {
+  if (kp % 32 || kp > 128 || np % 256 || Pw % 256 || Pk % 256 || Pk <= 0 || Pk > Pw || c0 % 64 || c0 + Pk > np)
+    return CDL_ERR_INVALID_ARG;
+  ResidMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int s = 0; s < RS_SLICES; ++s) {
+    // A operand: the panel's Pk columns of rows 0 .. np - 1 (the transposed panel slices, np x Pw planes)
+    CDL_TRY(make_map(&maps.a[s], static_cast<const char*>(slicesT) + (size_t)s * np * Pw * 2, np, Pk, 128, 2, Pw));
+    // B operand: columns c0 .. c0 + Pk - 1 of the kp x np slice plane of Z / c
+    CDL_TRY(make_map(&maps.b[s], static_cast<const char*>(zslices) + (size_t)s * kp * np * 2 + (size_t)c0 * 2, kp,
+                     Pk, kp, 2, np));
+  }
+  ResidParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.num_tiles = np / 128;
+  p.kblocks = Pk / 64;
+  p.kp = kp;
+  for (int m = 2; m <= RS_SLICES + 1; ++m)
+    for (int sa = 1; sa < m; ++sa) {
+      const int sz = m - sa;
+      if (sa > RS_SLICES || sz > RS_SLICES) continue;
+      p.pair_s[p.npairs] = sa;
+      p.pair_t[p.npairs] = sz;
+      ++p.npairs;
+    }
+  p.G = G;
+  p.idesc = make_idesc(kp);
+  p.status = ctx->dev_status;
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_BYTES));
+    attr = true;
+  }
+  const int grid = std::min(p.num_tiles, ctx->sm_count);
+  Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * Pk * kp);
+  k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
+  return L.done();
+}
+
+int score_tc_tiles(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long long* dint,
+                   const double* oscale, int n, int rows, int k2p, const double* A1, const double* A2, int row0,
+                   long long tile0, long long tile1, double* contrib) {
   if (rows % 128 || k2p % 64 || rows < n || k2p < 64) return CDL_ERR_INVALID_ARG;
   ScoreMaps maps;
   std::memset(&maps, 0, sizeof(maps));
@@ -2132,9 +2237,14 @@ int score_tc(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long 
   std::memset(&p, 0, sizeof(p));
   p.nb128 = rows / 128;
   p.nb64 = 2 * p.nb128;
-  const long long tiles = (long long)p.nb128 * p.nb64 - (long long)p.nb128 * (p.nb128 - 1);
-  if (tiles > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  const long long all = (long long)p.nb128 * p.nb64 - (long long)p.nb128 * (p.nb128 - 1);
+  if (tile1 < 0) tile1 = all;
+  if (tile0 < 0 || tile1 > all || tile0 > tile1 || tile1 - tile0 > 0x7fffffffLL) return CDL_ERR_INVALID_ARG;
+  const long long tiles = tile1 - tile0;
+  if (tiles == 0) return CDL_OK;
   p.num_tiles = (int)tiles;
+  p.tile0 = tile0;
+  p.row0 = row0;
   p.kblocks = k2p / 64;
   p.n = n;
   p.A1 = A1;
@@ -2154,6 +2264,11 @@ int score_tc(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long 
   Launch L(ctx, CDL_KC_SCORE, 2.0 * 21 * (double)tiles * 128 * SC_N * k2p);
   k_tc_score<<<grid, T8_THREADS, SC_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
+}
+
+int score_tc(cdl_ctx* ctx, const void* uplanes, const void* vplanes, const long long* dint, const double* oscale,
+             int n, int rows, int k2p, const double* A1, const double* A2, double* contrib) {
+  return score_tc_tiles(ctx, uplanes, vplanes, dint, oscale, n, rows, k2p, A1, A2, 0, 0, -1, contrib);
 }
 
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial, int kp,

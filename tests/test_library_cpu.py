@@ -58,13 +58,13 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
 
 
 def declared_constants():
-    """Every enumerator of include/cdl.h with its value (explicit values only,
-    which is how the header writes them)."""
+    """Every enumerator of include/cdl.h with its value (explicit decimal or
+    hexadecimal values only, which is how the header writes them)."""
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     out = {}
     for body in re.findall(r"enum\s*(?:\w+\s*)?\{(.*?)\}", text, flags=re.S):
-        for name, value in re.findall(r"\b(CDL_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
-            out[name] = int(value)
+        for name, value in re.findall(r"\b(CDL_[A-Z0-9_]+)\s*=\s*(-?(?:0x[0-9A-Fa-f]+|\d+))", body):
+            out[name] = int(value, 0)
     return out
 
 
