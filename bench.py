@@ -591,6 +591,122 @@ GMM_N = 32768
 GMM_WORKLOAD = "gmm_n32768_pair"
 
 
+C5_WORKLOAD = "field_n131072_pair"
+C5_METRIC = "graph pairs/s at n=131072 (graphs regenerated in row panels, chain levels partly in pinned host memory)"
+C5_K, C5_D, C5_TOPK = 192, 10, 100
+
+
+def config5_workload():
+    from workloads import field_sequence
+    return field_sequence(256, 512, 365, 2, patch=16, patch_transition=0, seasonal=0.5, seed=5)
+
+
+def run_config5(args):
+    """The larger-than-memory form at its own size: one pair at n = 131072
+    (256 x 512 grid, T = 365 field samples plus a seasonal sinusoid, a
+    planted 16 x 16 patch), k = 192, d = 10, bf16 levels (as many as fit on
+    the device, the rest in pinned host memory), refinement to 1e-10,
+    top-100; neither float64 graph (137 GB each) is stored: both are
+    regenerated from the node series in row panels wherever they are needed.
+    One warm-up pair (it allocates and pins the levels), then --steps pairs
+    (default 1) between CUDA events; then one pair with per-class timing."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1802_05421_gb300 import build as B
+    B.build()
+    from paper_1802_05421_gb300 import cdl
+    wl = config5_workload()
+    n, T = wl.X[0].shape
+    stream = torch.cuda.Stream()
+    st, ctx = cdl.cdl_ctx_create(0, stream.cuda_stream, 0)
+    assert st == 0
+    X1 = torch.from_numpy(wl.X[0]).cuda()
+    X2 = torch.from_numpy(wl.X[1]).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    top = torch.empty(C5_TOPK, dtype=torch.int64, device="cuda")
+    s1, s2 = cdl.cdl_solve_stats(), cdl.cdl_solve_stats()
+    flags = cdl.CDL_PAIR_REGEN_GRAPHS | cdl.CDL_CHAIN_HOST_LEVELS | cdl.CDL_CHAIN_RESIDENT(255)
+    o = cdl.cdl_pair_opts(C5_K, C5_D, cdl.CDL_BF16, cdl.CDL_BF16, SEED, 0.0, cdl.cdl_solve_opts(40, REL_TOL, 0),
+                          C5_TOPK, 0, flags)
+
+    def call(opts=o, x1=X1, x2=X2, f=F, t=top):
+        r = cdl.cdl_caddelag_pair(ctx, x1, x2, n, T, opts, f, t, s1, s2)
+        if r != 0:
+            raise RuntimeError(f"cdl_caddelag_pair: {cdl.cdl_status_string(r)} {cdl.cdl_last_error_detail()}")
+
+    t0 = time.perf_counter()
+    call()
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    steps = max(1, args.c5_steps)
+    _, l0 = cdl.cdl_ctx_launch_count(ctx)
+    sampler = ClockSampler(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_ms = e0.elapsed_time(e1) / steps
+    _, l1 = cdl.cdl_ctx_launch_count(ctx)
+    top_dev = top.cpu().tolist()
+    iters = (s1.iters, s2.iters)
+    rel_res = max(s1.rel_res, s2.rel_res)
+    # one pair with per-class timing: phases, the squaring's rate, the host link
+    cdl.cdl_ctx_reset_counters(ctx)
+    cdl.cdl_ctx_set_timing(ctx, True)
+    call()
+    kc = {}
+    for i, name in enumerate(cdl.KERNEL_CLASSES + ["host_link"]):
+        _, ms, cnt, work = cdl.cdl_ctx_timing(ctx, i)
+        kc[name] = dict(ms=ms, launches=cnt, work=work)
+    cdl.cdl_ctx_set_timing(ctx, False)
+    # end to end with host buffers (the series in, scores and top-100 out)
+    h1 = torch.from_numpy(wl.X[0]).pin_memory()
+    h2 = torch.from_numpy(wl.X[1]).pin_memory()
+    hF = torch.empty(n, dtype=torch.float64).pin_memory()
+    ht = torch.empty(C5_TOPK, dtype=torch.int64).pin_memory()
+    oh = cdl.cdl_pair_opts(C5_K, C5_D, cdl.CDL_BF16, cdl.CDL_BF16, SEED, 0.0, cdl.cdl_solve_opts(40, REL_TOL, 0),
+                           C5_TOPK, 1, flags)
+    t0 = time.perf_counter()
+    call(oh, h1.data_ptr(), h2.data_ptr(), hF.data_ptr(), ht.data_ptr())
+    e2e_s = time.perf_counter() - t0
+    pk, src = peaks()
+    sq = kc["square"]
+    ach = sq["work"] / (sq["ms"] * 1e-3) / 1e12 if sq["ms"] else 0.0
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    npad = (n + 255) // 256 * 256
+    lb = npad * npad * 2
+    link = kc["host_link"]
+    line = {
+        "metric": C5_METRIC, "value": 1000.0 / step_ms, "unit": "pairs/s", "n_gpus": 1, "steps": steps,
+        "warmup": 1, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": C5_WORKLOAD, "n": n, "T": T, "k": C5_K, "d": C5_D, "topk": C5_TOPK,
+                   "chain": "bf16", "score": "bf16", "refine_rel_tol": REL_TOL, "solve_iters": list(iters),
+                   "rel_res": rel_res, "graphs": "regenerated in row panels of 4096 (not stored)",
+                   "levels": "as many on the device as fit, the rest in pinned host memory",
+                   "level_bytes": lb, "float64_graph_bytes": 8 * n * n,
+                   "l2": "no flush: each step streams hundreds of GB"},
+        "first_call_s": first_s,
+        "roofline": {"kernel": "k_tc_gemm (chain squaring)", "bound": "tensor", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak if peak else None, "traffic": None,
+                     "peak_source": f"{src} bf16_tflops_sustained",
+                     "ms_per_launch": sq["ms"] / max(sq["launches"], 1), "launches": sq["launches"]},
+        "link": {"copies_per_pair": link["launches"], "bytes_per_pair": link["work"], "copy_ms_per_pair": link["ms"]},
+        "e2e": {"value": 1.0 / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 2 * n * T * 8,
+                "d2h_bytes_per_step": n * 8 + C5_TOPK * 8, "same_top_as_device_run": ht.tolist() == top_dev},
+        "gpu_launches": int((l1 - l0) // steps),
+        "clocks": clocks,
+        "phases_ms_per_step": {k: round(v["ms"], 1) for k, v in kc.items()},
+        "planted_in_top": len(set(top_dev) & set(wl.planted[0].tolist())),
+    }
+    print(json.dumps(line), flush=True)
+    cdl.cdl_ctx_destroy(ctx)
+    return 0
+
+
 def run_gmm(args):
     """The paper's synthetic data (Sec. 4.2.1) at n = 32768: graph 1 is the
     exp(-d) kernel graph of a 4-component 2-D Gaussian mixture, graph 2 that
@@ -922,7 +1038,9 @@ def main():
                     help="run a small single-kernel case for a profiler capture instead of the bench")
     ap.add_argument("--n", type=int, default=12288)
     ap.add_argument("--reps", type=int, default=1)
-    ap.add_argument("--workload", default="pair", choices=["pair", "batched", "host-levels", "gmm", "sequence"],
+    ap.add_argument("--c5-steps", type=int, default=1, help="timed pairs of --workload larger-than-hbm")
+    ap.add_argument("--workload", default="pair",
+                    choices=["pair", "batched", "host-levels", "gmm", "sequence", "larger-than-hbm"],
                     help="pair: the n = 32768 field pair (default); batched: 64 ragged pairs; "
                          "host-levels: the pair with chain levels in pinned host memory; "
                          "gmm: the synthetic mixture pair at n = 32768")
@@ -941,6 +1059,8 @@ def main():
         return run_sequence(args)
     if args.workload == "gmm":
         return run_gmm(args)
+    if args.workload == "larger-than-hbm":
+        return run_config5(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

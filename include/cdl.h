@@ -521,6 +521,15 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
                       const cdl_pair_opts* opts, double* F, int64_t* top_idx,
                       cdl_solve_stats* stats1, cdl_solve_stats* stats2);
 
+/* The embeddings of the last cdl_caddelag_pair call on this context (Alg. 3,
+ * what the scores were computed from), for inspection and checking: Z1, Z2
+ * receive n x k float64 each (device or host memory, NULL to skip);
+ * scalars (4 float64, device or host, NULL to skip) = vol1, vol2, sigma1,
+ * sigma2. The values stay valid until the next call that uses the
+ * context's workspace. Synchronises. CDL_ERR_INVALID_ARG if no pair has
+ * run on the context. */
+int cdl_pair_embeddings(cdl_ctx* ctx, double* Z1, double* Z2, double* scalars);
+
 /* ---------------------------------------------------------------- batched form */
 
 typedef struct {

@@ -26,6 +26,7 @@ design notes of the repository):
 from __future__ import annotations
 
 import math
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -85,6 +86,89 @@ def squared_distances_exact_grid(X: np.ndarray, row_block: int = 4096) -> np.nda
         d2i = norms[r0:r1, None] + norms[None, :] - 2 * gram
         out[r0:r1] = d2i.astype(np.float64) * 2.0 ** -32
     return out
+
+
+def _grid_upper_blocks(X: np.ndarray, row_block: int, threads: int, fn):
+    """Stream the exact squared distances of node series on the 2**-16 grid
+    (x = a 2**-16, integer a) over row blocks of the upper triangle: for rows
+    r0 .. r1 - 1 and columns j > r0, the integers D_ij = |a_i - a_j|^2 (the
+    integer Gram from float64 products of 12-bit pieces, exact, as in
+    ``squared_distances_exact_grid``) and the mask j > i go to
+    fn(r0, r1, D, upper); the results come back in block order. A single
+    float64 product a_i . a_j replaces the pieces when (max |a|)^2 T < 2^53
+    (every partial sum exact). Blocks run on threads (NumPy and BLAS release
+    the GIL)."""
+    import concurrent.futures as cf
+    X = np.asarray(X, dtype=np.float64)
+    a = X * 65536.0
+    if not np.array_equal(a, np.rint(a)) or np.abs(a).max() >= 2.0 ** 23:
+        raise ValueError("input is not on the 2**-16 grid")
+    ai = a.astype(np.int64)
+    hi = (ai >> 12).astype(np.float64)
+    lo = (ai & 4095).astype(np.float64)
+    norms = (ai * ai).sum(axis=1)
+    n = X.shape[0]
+    # one float64 product is exact when every partial sum of a_i . a_j stays
+    # below 2^53: (max |a|)^2 T < 2^53; else the 12-bit pieces
+    amax = int(np.abs(ai).max()) if ai.size else 0
+    direct = amax * amax * X.shape[1] < 2 ** 53
+
+    def block(r0):
+        r1 = min(n, r0 + row_block)
+        c0 = r0 + 1                                   # columns j > i start after the block's first row
+        if direct:
+            g = (a[r0:r1] @ a[c0:].T).astype(np.int64)
+        else:
+            g = ((hi[r0:r1] @ hi[c0:].T).astype(np.int64) << 24) + \
+                (((hi[r0:r1] @ lo[c0:].T) + (lo[r0:r1] @ hi[c0:].T)).astype(np.int64) << 12) + \
+                (lo[r0:r1] @ lo[c0:].T).astype(np.int64)
+        D = norms[r0:r1, None] + norms[None, c0:] - 2 * g
+        upper = np.arange(c0, n)[None, :] > np.arange(r0, r1)[:, None]
+        return fn(r0, r1, D, upper)
+
+    starts = list(range(0, n - 1, row_block))
+    workers = threads or min(4, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(block, starts))
+
+
+def grid_distance_counts(X: np.ndarray, key: int, row_block: int = 512, threads: int = 0):
+    """For node series on the 2**-16 grid: the numbers of pairs i < j whose
+    exact squared distance, as the integer D_ij = ||x_i - x_j||^2 2**32, is
+    below ``key`` and at most ``key``. The lower median of the distances
+    (Sec. 4.2.1 kernel width: rank (m - 1) // 2 of the m = n (n - 1) / 2
+    sorted distances) is the key with count_below <= rank < count_at_most.
+    Streamed (no n x n matrix is held)."""
+    parts = _grid_upper_blocks(X, row_block, threads, lambda r0, r1, D, up: (
+        int(np.count_nonzero((D < key) & up)), int(np.count_nonzero((D <= key) & up))))
+    return sum(p[0] for p in parts), sum(p[1] for p in parts)
+
+
+def gaussian_degrees_streamed(X: np.ndarray, sigma: float, row_block: int = 512, threads: int = 0,
+                              key: Optional[int] = None):
+    """D_i = sum_{j != i} exp(-||x_i - x_j||^2 / (2 sigma^2)) (Sec. 3.2: D = A 1)
+    for node series on the 2**-16 grid, streamed over the upper triangle
+    (each pair's value added to both of its rows; no n x n matrix is held).
+    With ``key``, also the two counts of ``grid_distance_counts`` from the
+    same pass: returns (D, count_below, count_at_most)."""
+    n = X.shape[0]
+    two_s2 = 2.0 * (sigma * sigma)
+
+    def fn(r0, r1, Dk, up):
+        A = np.exp(-((Dk.astype(np.float64) * 2.0 ** -32) / two_s2))
+        A[~up] = 0.0
+        cnt = (int(np.count_nonzero((Dk < key) & up)), int(np.count_nonzero((Dk <= key) & up))) if key is not None \
+            else (0, 0)
+        return r0, r1, A.sum(axis=1), A.sum(axis=0), cnt
+
+    D = np.zeros(n)
+    lt = le = 0
+    for r0, r1, rs, cs, cnt in _grid_upper_blocks(X, row_block, threads, fn):
+        D[r0:r1] += rs
+        D[r0 + 1:] += cs
+        lt += cnt[0]
+        le += cnt[1]
+    return (D, lt, le) if key is not None else D
 
 
 def median_sigma(d2: np.ndarray) -> float:

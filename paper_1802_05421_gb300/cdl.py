@@ -128,6 +128,7 @@ _SIGS = {
     "cdl_changed_nodes": [_P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_I32)],
     "cdl_cad_score_changed": [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _I64, _I32, ctypes.c_int, _P, _I32, _I32,
                               _P, _P],
+    "cdl_pair_embeddings": [_P, _P, _P, _P],
     "cdl_caddelag_pair": [_P, _P, _P, _I64, _I32, ctypes.POINTER(cdl_pair_opts), _P, _P,
                           ctypes.POINTER(cdl_solve_stats), ctypes.POINTER(cdl_solve_stats)],
     "cdl_caddelag_batched": [_P, _I32, _P, _I32, _P, _P, ctypes.POINTER(cdl_batch_opts), _P, _P, _P],
@@ -323,6 +324,10 @@ def cdl_caddelag_pair(ctx, X1, X2, n, T, opts: cdl_pair_opts, F, top_idx, stats1
                                   _ptr(top_idx),
                                   ctypes.byref(stats1) if stats1 is not None else None,
                                   ctypes.byref(stats2) if stats2 is not None else None)
+
+
+def cdl_pair_embeddings(ctx, Z1, Z2, scalars) -> int:
+    return _lib.cdl_pair_embeddings(ctx, _ptr(Z1), _ptr(Z2), _ptr(scalars))
 
 
 def cdl_caddelag_batched(ctx, G, n, T, X1, X2, opts: cdl_batch_opts, F, top_idx, stats=None) -> int:

@@ -766,6 +766,13 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
   } else {
     CDL_TRY(cad_score(ctx, As[0], As[1], Zs[0], Zs[1], sc, sc + 1, n, o->k, o->score_dtype, o->topk, Fd, topd));
   }
+  ctx->last_pair.n = n;
+  ctx->last_pair.k = o->k;
+  for (int g = 0; g < 2; ++g) {
+    ctx->last_pair.Z[g] = Zs[g];
+    ctx->last_pair.vol[g] = sc + g;
+    ctx->last_pair.sigma[g] = sc + 2 + g;
+  }
   if (o->host_io) {
     CDL_CUDA_TRY(cudaMemcpyAsync(F, Fd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (o->topk > 0)
@@ -774,6 +781,24 @@ int cdl_caddelag_pair(cdl_ctx* ctx, const double* X1, const double* X2, int64_t 
     CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   }
   return converged ? CDL_OK : CDL_ERR_NOT_CONVERGED;
+}
+
+int cdl_pair_embeddings(cdl_ctx* ctx, double* Z1, double* Z2, double* scalars) {
+  if (!ctx || !ctx->last_pair.Z[0]) return CDL_ERR_INVALID_ARG;
+  CDL_TRY(set_device(ctx));
+  const size_t nk = (size_t)ctx->last_pair.n * ctx->last_pair.k;
+  double* Zo[2] = {Z1, Z2};
+  for (int g = 0; g < 2; ++g)
+    if (Zo[g]) CDL_CUDA_TRY(cudaMemcpyAsync(Zo[g], ctx->last_pair.Z[g], nk * sizeof(double), cudaMemcpyDefault,
+                                            ctx->stream));
+  if (scalars) {
+    const double* src[4] = {ctx->last_pair.vol[0], ctx->last_pair.vol[1], ctx->last_pair.sigma[0],
+                            ctx->last_pair.sigma[1]};
+    for (int q = 0; q < 4; ++q)
+      CDL_CUDA_TRY(cudaMemcpyAsync(scalars + q, src[q], sizeof(double), cudaMemcpyDefault, ctx->stream));
+  }
+  CDL_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return CDL_OK;
 }
 
 }  // extern "C"

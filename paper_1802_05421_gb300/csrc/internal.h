@@ -69,6 +69,14 @@ struct cdl_ctx {
   // chains owned by cdl_caddelag_pair
   cdl_chain* pair_chain = nullptr;
   cdl_chain* regen_chain = nullptr;   // the chain of pairs whose graphs are regenerated in panels
+  // where the last cdl_caddelag_pair left its embeddings (workspace, device)
+  struct {
+    int64_t n = 0;
+    int k = 0;
+    const double* Z[2] = {nullptr, nullptr};
+    const double* vol[2] = {nullptr, nullptr};
+    const double* sigma[2] = {nullptr, nullptr};
+  } last_pair;
   // tile schedules uploaded to the workspace, by workspace name -> tile count
   std::map<std::string, int> tile_lists;
   int debug_flags = 0;   // CDL_DEBUG_* test hooks

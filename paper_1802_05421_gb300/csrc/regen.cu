@@ -157,6 +157,13 @@ int pair_regen(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n64, in
     if (o->topk > 0) CDL_TRY(check_dev_ptr(ctx, top_idx, 8));
   }
   CDL_TRY(cad_score_panels(ctx, Zs[0], Zs[1], sc, sc + 1, n64, k, P, fill, o->topk, Fo, To));
+  ctx->last_pair.n = n64;
+  ctx->last_pair.k = k;
+  for (int g = 0; g < 2; ++g) {
+    ctx->last_pair.Z[g] = Zs[g];
+    ctx->last_pair.vol[g] = sc + g;
+    ctx->last_pair.sigma[g] = G[g].sigma;
+  }
   if (o->host_io) {
     CDL_CUDA_TRY(cudaMemcpyAsync(F, Fo, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (o->topk > 0)

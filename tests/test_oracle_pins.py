@@ -457,6 +457,57 @@ def test_c_node_scores_match_brute_force_and_numpy():
     assert np.allclose(O.node_scores_c(A1[rows], A2[rows], rows, Z1, Z2, 2.0, 5.0), F[rows], rtol=1e-13, atol=0)
 
 
+def test_grid_distance_counts_locate_the_lower_median():
+    """The streamed counts against sorted brute-force distances: the lower
+    median's integer key k (||x_i - x_j||^2 2^32) has count_below <= rank <
+    count_at_most, a key between two distance values has count_below ==
+    count_at_most, and the counts at the smallest and beyond the largest key
+    are 0 and m. Row blocks smaller than n exercise the block seams."""
+    wl = iid_pair(157, 9, 1, seed=41)
+    X = wl.X[0]
+    n = X.shape[0]
+    d2 = O.squared_distances(X)
+    iu = np.triu_indices(n, 1)
+    keys = np.sort(np.rint(d2[iu] * 2.0 ** 32).astype(np.int64))
+    m = keys.size
+    rank = (m - 1) // 2
+    med = int(keys[rank])
+    lt, le = O.grid_distance_counts(X, med, row_block=40, threads=3)
+    assert lt == int(np.count_nonzero(keys < med)) and le == int(np.count_nonzero(keys <= med))
+    assert lt <= rank < le
+    assert math.sqrt(med * 2.0 ** -32) == O.median_sigma(d2)
+    gap = next(int(a) + 1 for a, v in zip(keys[rank:], keys[rank + 1:]) if v > a + 1)   # a < gap < v
+    lt2, le2 = O.grid_distance_counts(X, gap, row_block=64)
+    assert lt2 == le2 == int(np.count_nonzero(keys < gap))
+    assert O.grid_distance_counts(X, int(keys[0]) - 1) == (0, 0)
+    assert O.grid_distance_counts(X, int(keys[-1]) + 1) == (m, m)
+    # values near 2^7 over 300 samples: (max |a|)^2 T >= 2^53, the 12-bit pieces
+    rng = np.random.default_rng(44)
+    W = np.rint(rng.uniform(-127.0, 127.0, (90, 300)) * 65536.0) / 65536.0
+    assert (np.abs(W).max() * 65536.0) ** 2 * 300 >= 2.0 ** 53
+    kw = np.sort(np.rint(O.squared_distances_exact_grid(W)[np.triu_indices(90, 1)] * 2.0 ** 32).astype(np.int64))
+    medw = int(kw[(kw.size - 1) // 2])
+    assert O.grid_distance_counts(W, medw, row_block=17) == (int(np.count_nonzero(kw < medw)),
+                                                             int(np.count_nonzero(kw <= medw)))
+
+
+def test_streamed_degrees_equal_the_dense_graph():
+    """Degrees streamed over row blocks (each upper-triangle value added to
+    both rows) against D = A 1 of the dense Gaussian graph (Sec. 3.2)."""
+    wl = field_sequence(9, 21, 30, 1, seed=43)
+    X = wl.X[0]
+    A, D, vol, sig = O.gaussian_graph(X)
+    Ds = O.gaussian_degrees_streamed(X, sig, row_block=50, threads=2)
+    np.testing.assert_allclose(Ds, D, rtol=1e-13, atol=0)
+    # the same pass with the median counts of grid_distance_counts
+    key = int(round(sig * sig * 2.0 ** 32))
+    D2, lt, le = O.gaussian_degrees_streamed(X, sig, row_block=37, key=key)
+    assert np.array_equal(D2, Ds) or np.allclose(D2, Ds, rtol=1e-15, atol=0)
+    assert (lt, le) == O.grid_distance_counts(X, key, row_block=64)
+    m = X.shape[0] * (X.shape[0] - 1) // 2
+    assert lt <= (m - 1) // 2 < le
+
+
 def test_top_anomalies_ties_and_order():
     F = np.array([1.0, 3.0, 3.0, 2.0, 3.0, 0.5])
     assert list(O.top_anomalies(F, 4)) == [1, 2, 4, 3]
