@@ -97,7 +97,7 @@ int pair_regen(cdl_ctx* ctx, const double* X1, const double* X2, int64_t n64, in
     ctx->regen_chain = nullptr;
   }
   if (!ctx->regen_chain) {
-    const size_t reserve = (size_t)48 << 30;   // the rest of this call's buffers and headroom
+    const size_t reserve = (size_t)24 << 30;   // the rest of this call's buffers and headroom
     const int resident = host_levels ? resident_levels(ctx, npad, o->d, res_req, reserve) : o->d;
     CDL_TRY(chain_create_regen(ctx, n64, o->d, resident, &ctx->regen_chain));
   }
