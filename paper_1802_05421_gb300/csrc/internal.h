@@ -217,8 +217,11 @@ int ooc_read_done(cdl_ctx* ctx, cdl_chain* ch, int i);
 int ooc_prefetch(cdl_ctx* ctx, cdl_chain* ch, int i);
 // tc_gemm.cu
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level);
+// Number of exact-slice pairs of the residual product (s + t <= 7 of six slices).
+constexpr int RESID_PAIRS = 21;
 // A Z on the tensor cores from exact bf16 slices (A's in the chain, Z / c in
-// zslices: 6 planes kp x npad) into G (npad x kp float64).
+// zslices: 6 planes kp x npad) into G: RESID_PAIRS float64 planes npad x kp,
+// one per slice pair; A Z = the sum of the planes in order.
 int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, double* G);
 // Exact squared distances of grid inputs on the tensor cores: planes = three
 // bf16 digit planes (rows x tp each, rows = n rounded up to 128, tp = T
@@ -446,9 +449,10 @@ struct RegenSource {
 // only the tiles of the upper block triangle.
 int dist_tc_panel(cdl_ctx* ctx, const void* planes, const long long* norms, int n, int rows, int tp, double* panel,
                   int row0, int prows, bool upper, const int* offgrid);
-// G (npad x kp) += A[:, c0 .. c0 + Pk) Z[c0 .. c0 + Pk) from the transposed
-// exact slices of the panel (6 planes npad x Pw, Pk <= Pw columns in use,
-// multiples of 256) and Z / c's slices (6 planes kp x npad).
+// G (RESID_PAIRS planes npad x kp, as for resid_tc) += the pair products of
+// A[:, c0 .. c0 + Pk) Z[c0 .. c0 + Pk) from the transposed exact slices of
+// the panel (6 planes npad x Pw, Pk <= Pw columns in use, multiples of 256)
+// and Z / c's slices (6 planes kp x npad).
 int resid_tc_panel(cdl_ctx* ctx, const void* slicesT, int np, int Pw, int Pk, int c0, const void* zslices, int kp,
                    double* G);
 // Score tiles tile0 .. tile1 - 1 of the upper-triangle numbering (tile1 < 0:

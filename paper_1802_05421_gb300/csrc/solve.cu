@@ -465,8 +465,9 @@ __global__ void __launch_bounds__(256) k_zslice(const double* __restrict__ Z, in
   }
 }
 
-// R = (Y - D o Z) + (2^s c_r) G (G from the column groups of at most 128;
-// 2^s = a_scale[0], the scale of A's slices), and per-block sums of R^2.
+// R = (Y - D o Z) + (2^s c_r) G (G from the column groups of at most 128,
+// each the sum of its RESID_PAIRS slice-pair planes; 2^s = a_scale[0], the
+// scale of A's slices), and per-block sums of R^2.
 __global__ void __launch_bounds__(256) k_resid_combine(const double* __restrict__ Y, const double* __restrict__ Z,
                                                         const double* __restrict__ D, int n, int k, int np,
                                                         const double* __restrict__ G, const double* __restrict__ cs,
@@ -480,7 +481,10 @@ __global__ void __launch_bounds__(256) k_resid_combine(const double* __restrict_
     const int i = (int)(idx / k), r = (int)(idx % k);
     const int g = r / 128, rl = r % 128;
     const int kg = min(128, ((k - g * 128) + 31) / 32 * 32);
-    const double az = (cs[r] * as) * G[(size_t)g * np * 128 + (size_t)i * kg + rl];   // powers of two: exact
+    const double* Gg = G + (size_t)g * RESID_PAIRS * np * 128 + (size_t)i * kg + rl;
+    double sum = 0.0;
+    for (int pr = 0; pr < RESID_PAIRS; ++pr) sum += Gg[(size_t)pr * np * kg];   // the slice pairs in order
+    const double az = (cs[r] * as) * sum;   // powers of two: exact
     const double v = (Y[idx] - D[i] * Z[idx]) + az;
     R[idx] = v;
     sq = fma(v, v, sq);
@@ -898,7 +902,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
       const int ngroups = (k + 127) / 128;
       void *vzs, *vG, *vmb, *vcs;
       CDL_TRY(ws_get(ctx, "solve.zslices", 6 * (size_t)128 * np * 2, &vzs));
-      CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * np * 128 * sizeof(double), &vG));
+      CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * RESID_PAIRS * np * 128 * sizeof(double), &vG));
       CDL_TRY(ws_get(ctx, "solve.zmax", (size_t)k * 8, &vmb));
       CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcs));
       CDL_CUDA_TRY(cudaMemsetAsync(vmb, 0, (size_t)k * 8, st));
@@ -911,7 +915,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
       for (int g = 0; g < ngroups; ++g) {
         const int c0 = g * 128;
         const int kg = std::min(128, (k - c0 + 31) / 32 * 32);
-        double* Gg = static_cast<double*>(vG) + (size_t)g * np * 128;
+        double* Gg = static_cast<double*>(vG) + (size_t)g * RESID_PAIRS * np * 128;
         {
           Launch L(ctx, CDL_KC_MISC, 0);
           k_zslice<<<ctx->sm_count * 4, 256, 0, st>>>(Z, n, k, np, c0, kg,
@@ -919,7 +923,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
                                                        static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcs));
           CDL_TRY(L.done());
         }
-        CDL_CUDA_TRY(cudaMemsetAsync(Gg, 0, (size_t)np * kg * sizeof(double), st));
+        CDL_CUDA_TRY(cudaMemsetAsync(Gg, 0, (size_t)RESID_PAIRS * np * kg * sizeof(double), st));
         for (int r0 = 0; r0 < n; r0 += rs.P) {
           const int rows = std::min(rs.P, n - r0);
           CDL_TRY(regen_panel(ctx, *rs.g, rs.panel, r0, rows, rs.Dscratch));
@@ -940,7 +944,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
       const int ngroups = (k + 127) / 128;
       void *vzs, *vG, *vmb, *vcs;
       CDL_TRY(ws_get(ctx, "solve.zslices", 6 * (size_t)128 * np * 2, &vzs));
-      CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * np * 128 * sizeof(double), &vG));
+      CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * RESID_PAIRS * np * 128 * sizeof(double), &vG));
       CDL_TRY(ws_get(ctx, "solve.zmax", (size_t)k * 8, &vmb));
       CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcs));
       CDL_CUDA_TRY(cudaMemsetAsync(vmb, 0, (size_t)k * 8, st));
@@ -960,7 +964,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
                                                        static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcs));
           CDL_TRY(L.done());
         }
-        CDL_TRY(resid_tc(ctx, ch, vzs, kg, static_cast<double*>(vG) + (size_t)g * np * 128));
+        CDL_TRY(resid_tc(ctx, ch, vzs, kg, static_cast<double*>(vG) + (size_t)g * RESID_PAIRS * np * 128));
       }
       const int nb = std::min(1024, (int)blocks_for(nk, 256));
       Launch L(ctx, CDL_KC_RESIDUAL, 0);

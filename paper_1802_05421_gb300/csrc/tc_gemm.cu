@@ -562,10 +562,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // steps). The MMA sums one K-chunk of one slice pair into a TMEM buffer; the
 // epilogue converts it to an integer count of grid steps, adds it to int32
 // accumulators, and every 64 chunks (at most 2^30 steps) adds them, scaled
-// by 2^-8(s+t), to the float64 result G. The 21 slice pairs with s + t <= 7
-// leave about 2^-50 of |A| |Z / c|: A Z = 2^q c G to float64 accuracy, as
-// the ordering of the float64 additions allows. Warp roles as in k_tc_mx8
-// (576 threads, 16 epilogue warps).
+// by 2^-8(s+t), to the float64 plane of its slice pair. The 21 slice pairs
+// with s + t <= 7 leave about 2^-50 of |A| |Z / c|: A Z = 2^q c G with G
+// the sum of the 21 planes in pair order, to float64 accuracy, as the
+// ordering of the float64 additions allows. A CTA's unit of work is one
+// 128-row tile with one slice pair over the whole K range, units numbered
+// tile-major, so the pairs sharing an A slice tile run on neighbouring CTAs
+// at the same time and read it from L2 (pair-major per CTA, each A slice
+// would come from HBM once for every pair it is in: 21 / 6 times the bytes).
+// Warp roles as in k_tc_mx8 (576 threads, 16 epilogue warps).
 constexpr int RS_SLICES = 6;
 constexpr int RS_MAX_PAIRS = 21;
 constexpr int RS_STAGES = 6;
@@ -588,7 +593,8 @@ struct ResidParams {
   int npairs;
   int pair_s[RS_MAX_PAIRS];
   int pair_t[RS_MAX_PAIRS];
-  double* G;       // npad x kp, zeroed before
+  double* G;       // npairs planes npad x kp (one per slice pair, gstride apart), zeroed before
+  size_t gstride;
   uint32_t idesc;
   unsigned* status;
 };
@@ -650,8 +656,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     // ------------------------------------------------ TMA producer
     int it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
-      for (int pr = 0; pr < p.npairs && ok; ++pr) {
+    for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x) {
+      const int t = u / p.npairs, pr = u % p.npairs;
+      {
         const CUtensorMap* ma = &maps.a[p.pair_s[pr] - 1];
         const CUtensorMap* mb = &maps.b[p.pair_t[pr] - 1];
         for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
@@ -667,6 +674,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           tma_load_2d(a_dst + RS_A, mb, kb * 64, 0, full_bar(s));
         }
       }
+    }
     if (!ok) {
       for (int j = (it > RS_STAGES ? it - RS_STAGES : 0); j < it; ++j) {
         const unsigned long long t0 = globaltimer();
@@ -679,8 +687,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     // ------------------------------------------------ MMA issuer: one exact K-chunk per TMEM buffer
     int it = 0, pc = 0;
     bool ok = true, issued = false;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
-      for (int pr = 0; pr < p.npairs && ok; ++pr)
+    for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x)
         for (int c = 0; c < nchunks && ok; ++c, ++pc) {
           const int b = pc & 1;
           const uint32_t ph = (uint32_t)(pc >> 1);
@@ -724,10 +731,11 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int pc = 0;
     bool failed = false;
-    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+    for (int u = blockIdx.x; u < p.num_tiles * p.npairs; u += gridDim.x) {
+      const int t = u / p.npairs, pr = u % p.npairs;
       const int row = t * 128 + q * 32 + lane;
-      double* Grow = p.G + (size_t)row * p.kp + col0;
-      for (int pr = 0; pr < p.npairs; ++pr) {
+      double* Grow = p.G + (size_t)pr * p.gstride + (size_t)row * p.kp + col0;
+      {
         const int m = p.pair_s[pr] + p.pair_t[pr];
         const float up = __int_as_float((127 + 8 * m) << 23);   // 2^(8m)
         int acc[32];
@@ -2093,6 +2101,7 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
       ++p.npairs;
     }
   p.G = G;
+  p.gstride = (size_t)np * kp;
   p.idesc = make_idesc(kp);
   p.status = ctx->dev_status;
   static bool attr = false;
@@ -2100,8 +2109,8 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_BYTES));
     attr = true;
   }
-  CDL_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)np * kp * sizeof(double), ctx->stream));
-  const int grid = std::min(p.num_tiles, ctx->sm_count);
+  CDL_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)p.npairs * np * kp * sizeof(double), ctx->stream));
+  const int grid = std::min(p.num_tiles * p.npairs, ctx->sm_count);
   Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * np * kp);
   k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
@@ -2209,6 +2218,7 @@ int resid_tc_panel(cdl_ctx* ctx, const void* slicesT, int np, int Pw, int Pk, in
       ++p.npairs;
     }
   p.G = G;
+  p.gstride = (size_t)np * kp;
   p.idesc = make_idesc(kp);
   p.status = ctx->dev_status;
   static bool attr = false;
@@ -2216,7 +2226,7 @@ int resid_tc_panel(cdl_ctx* ctx, const void* slicesT, int np, int Pw, int Pk, in
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_BYTES));
     attr = true;
   }
-  const int grid = std::min(p.num_tiles, ctx->sm_count);
+  const int grid = std::min(p.num_tiles * p.npairs, ctx->sm_count);
   Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * Pk * kp);
   k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
