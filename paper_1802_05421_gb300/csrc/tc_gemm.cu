@@ -577,7 +577,8 @@ constexpr int RS_STAGES = 6;
 constexpr int RS_A = 128 * 128;                 // A k-block: 128 rows x 64 bf16
 constexpr int RS_STAGE_BYTES = RS_A + 128 * 128; // + B k-block: up to 128 rows x 64 bf16
 constexpr int RS_SMEM_BYTES = RS_STAGES * RS_STAGE_BYTES + 512 + 1024;
-constexpr int RS_TMEM_COLS = 256;                // two buffers of up to 128 columns
+constexpr int RS_NBUF = 4;                       // ring of TMEM accumulators of up to 128 columns
+constexpr int RS_TMEM_COLS = RS_NBUF * 128;
 constexpr int RS_CHUNK_KB = 4;                   // k-blocks (of 64) per exact chunk: K = 256
 constexpr int RS_FLUSH = 64;                     // chunks per int32 flush
 
@@ -616,14 +617,14 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RS_STAGES * RS_STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * RS_STAGES + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * RS_STAGES + 7);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * RS_STAGES + 2 * RS_NBUF + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * RS_STAGES + 2 * RS_NBUF + 3);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (RS_STAGES + s); };
   auto pfull_bar = [&](int b) { return bar0 + 8u * (2 * RS_STAGES + b); };
-  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * RS_STAGES + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * RS_STAGES + 4);
+  auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * RS_STAGES + RS_NBUF + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * RS_STAGES + 2 * RS_NBUF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = p.kblocks / RS_CHUNK_KB;
   const uint32_t b_bytes = (uint32_t)p.kp * 128;
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < RS_NBUF; ++b) {
       mbar_init(pfull_bar(b), 1);
       mbar_init(pempty_bar(b), T8_EPI);
     }
@@ -689,8 +690,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     bool ok = true, issued = false;
     for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x)
         for (int c = 0; c < nchunks && ok; ++c, ++pc) {
-          const int b = pc & 1;
-          const uint32_t ph = (uint32_t)(pc >> 1);
+          const int b = pc % RS_NBUF;
+          const uint32_t ph = (uint32_t)(pc / RS_NBUF);
           if (!mbar_wait(pempty_bar(b), (ph & 1) ^ 1, abort_flag, p.status)) {
             ok = false;
             break;
@@ -743,19 +744,26 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         for (int c = 0; c < 32; ++c) acc[c] = 0;
         for (int ch = 0; ch < nchunks; ++ch, ++pc) {
           if (!failed) {
-            const int b = pc & 1;
-            const uint32_t ph = (uint32_t)(pc >> 1);
+            const int b = pc % RS_NBUF;
+            const uint32_t ph = (uint32_t)(pc / RS_NBUF);
             if (!mbar_wait(pfull_bar(b), ph & 1, abort_flag, p.status)) {
               failed = true;
             } else {
               tc_fence_after();
+              if (ncol == 32) {   // one load and one wait per drain
+                float v[32];
+                tmem_ld32(tmem_base + lane_off + (uint32_t)(b * 128 + col0), v);
 #pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                if (g * 8 < ncol) {
-                  float v[8];
-                  tmem_ld8(tmem_base + lane_off + (uint32_t)(b * 128 + col0 + g * 8), v);
+                for (int e = 0; e < 32; ++e) acc[e] += __float2int_rn(v[e] * up);
+              } else {
 #pragma unroll
-                  for (int e = 0; e < 8; ++e) acc[g * 8 + e] += __float2int_rn(v[e] * up);
+                for (int g = 0; g < 4; ++g) {
+                  if (g * 8 < ncol) {
+                    float v[8];
+                    tmem_ld8(tmem_base + lane_off + (uint32_t)(b * 128 + col0 + g * 8), v);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[g * 8 + e] += __float2int_rn(v[e] * up);
+                  }
                 }
               }
               tc_fence_before();
@@ -1008,12 +1016,11 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
             continue;
           }
           tc_fence_after();
+          {
+            float v[16];   // one load and one wait per drain
+            tmem_ld16(tmem_base + lane_off + (uint32_t)(b * DS_N + part * 16), v);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[8];
-            tmem_ld8(tmem_base + lane_off + (uint32_t)(b * DS_N + part * 16 + h * 8), v);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) g[h * 8 + e] += (long long)__float2int_rn(v[e]) * (1LL << (8 * w));
+            for (int e = 0; e < 16; ++e) g[e] += (long long)__float2int_rn(v[e]) * (1LL << (8 * w));
           }
           tc_fence_before();
           mbar_arrive(pempty_bar(b));
@@ -1292,14 +1299,13 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           tc_fence_after();
           const float up = __int_as_float((127 + 8 * w) << 23);   // 2^(8w)
           const int sh = 48 - 8 * w;
+          {
+            float v[16];   // one load and one wait per drain
+            tmem_ld16(tmem_base + lane_off + (uint32_t)(b * SC_N + part * 16), v);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[8];
-            tmem_ld8(tmem_base + lane_off + (uint32_t)(b * SC_N + part * 16 + h * 8), v);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < 16; ++e) {
               const long long x = __float2int_rn(v[e] * up);
-              m[h * 8 + e] += sh >= 0 ? x * (1LL << sh) : (x + (1LL << (-sh - 1))) >> (-sh);
+              m[e] += sh >= 0 ? x * (1LL << sh) : (x + (1LL << (-sh - 1))) >> (-sh);
             }
           }
           tc_fence_before();
