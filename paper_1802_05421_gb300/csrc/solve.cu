@@ -27,6 +27,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <string>
+#include <vector>
 
 #include "ff.cuh"
 #include "internal.h"
@@ -805,106 +807,135 @@ inline unsigned blocks_for(size_t count, int threads) { return (unsigned)((count
 
 }  // namespace
 
-int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
-                      const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats, double* yy_out) {
-  cudaStream_t st = ctx->stream;
-  const int n = (int)ch->n, np = (int)ch->npad;
-  const int kp = (int)round_up(k, 16);   // tensor-core N = 2 kp: multiple of 32
-  const bool bf16 = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3 ||
-                    ch->dtype == CDL_FP8E4M3_T128;   // tensor-core apply
-  const size_t xe = ch->dtype == CDL_F64 ? 8 : 4;
-  const int kblocks = np / 64;
-  int splits;
-  if (bf16) {
-    // split-K of the persistent apply (one CTA per SM over np / 128 row tiles x
-    // splits): the fewest splits (a divisor of the K blocks, at most 16) whose
-    // tiles fill the last round of CTAs to 95 %, else the best filling
-    const int mb = np / 128, sm = ctx->sm_count;
-    splits = 1;
-    double best = 0.0;
-    for (int sp = 1; sp <= 16 && sp <= kblocks; ++sp) {
-      if (kblocks % sp) continue;
-      const long long tl = (long long)mb * sp;
-      const double fill = (double)tl / (double)(((tl + sm - 1) / sm) * sm);
-      if (fill > best + 1e-9) {
-        best = fill;
-        splits = sp;
+namespace {
+
+// One block of at most 128 right-hand sides (any number for CUDA-core
+// chains) of the Richardson refinement, with its own residual, iterate,
+// operand buffers and stopping state; chain_solve steps every block together
+// so that each chain level is applied to all of them while it is loaded.
+struct SolveBlock {
+  cdl_ctx* ctx = nullptr;
+  const cdl_chain* ch = nullptr;
+  const double* A = nullptr;
+  const double* Y = nullptr;
+  double* Z = nullptr;
+  cdl_solve_stats* stats = nullptr;
+  cudaStream_t st = nullptr;
+  int n = 0, np = 0, k = 0, kp = 0, splits = 1;
+  bool bf16 = false;
+  size_t xe = 4, nk = 0;
+  int res_gx = 0, res_gy = 0, upd_gx = 0, upd_gy = 0, cs_rows = 256, cs_parts = 0;
+  void *vR = nullptr, *vx = nullptr, *vxop = nullptr, *vpart = nullptr, *vred = nullptr, *vscal = nullptr;
+  void *vzh = nullptr, *vzl = nullptr, *vcs = nullptr, *vdz = nullptr, *vpart2 = nullptr, *vdzop = nullptr;
+  double *R = nullptr, *red = nullptr, *scal = nullptr;
+  double yy = 0.0, rel = 1.0, drift = 0.0;
+  int iters = 0, nparts = 0;
+  bool exact_r = true;   // R was last formed in full (not recursively)
+  bool done = false;
+
+  int ws(const char* name, int idx, size_t bytes, void** out) {
+    if (idx == 0) return ws_get(ctx, name, bytes, out);
+    const std::string nm = std::string(name) + "#" + std::to_string(idx);
+    return ws_get(ctx, nm.c_str(), bytes, out);
+  }
+
+  // workspace (block idx > 0 under its own names), ||Y||^2, Z = 0, R = Y
+  int init(int idx) {
+    st = ctx->stream;
+    n = (int)ch->n;
+    np = (int)ch->npad;
+    kp = (int)round_up(k, 16);   // tensor-core N = 2 kp: multiple of 32
+    bf16 = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3 || ch->dtype == CDL_FP8E4M3_T128;   // tensor-core apply
+    xe = ch->dtype == CDL_F64 ? 8 : 4;
+    const int kblocks = np / 64;
+    if (bf16) {
+      // split-K of the persistent apply (one CTA per SM over np / 128 row tiles x
+      // splits): the fewest splits (a divisor of the K blocks, at most 16) whose
+      // tiles fill the last round of CTAs to 95 %, else the best filling
+      const int mb = np / 128, sm = ctx->sm_count;
+      splits = 1;
+      double best = 0.0;
+      for (int sp = 1; sp <= 16 && sp <= kblocks; ++sp) {
+        if (kblocks % sp) continue;
+        const long long tl = (long long)mb * sp;
+        const double fill = (double)tl / (double)(((tl + sm - 1) / sm) * sm);
+        if (fill > best + 1e-9) {
+          best = fill;
+          splits = sp;
+        }
+        if (fill >= 0.95) break;
       }
-      if (fill >= 0.95) break;
+    } else {
+      const int bm = ch->dtype == CDL_F32 ? 128 : 64;
+      const int cols = (kp + 63) / 64;
+      const int target = std::max(1, (8 * ctx->sm_count) / ((np / bm) * cols));
+      splits = largest_divisor_at_most(np / 8, std::min(target, 16));
     }
-  } else {
-    const int bm = ch->dtype == CDL_F32 ? 128 : 64;
-    const int cols = (kp + 63) / 64;
-    const int target = std::max(1, (8 * ctx->sm_count) / ((np / bm) * cols));
-    splits = largest_divisor_at_most(np / 8, std::min(target, 16));
-  }
-  const size_t part_cols = bf16 ? 2 * (size_t)kp : (size_t)kp;
-  void *vR, *vx, *vxop = nullptr, *vpart, *vred, *vscal, *vzh, *vzl, *vcs;
-  const int res_gx = (n + RB_M - 1) / RB_M, res_gy = (k + RB_N - 1) / RB_N;
-  const int nred = std::max(res_gx * res_gy, std::max(1024, ctx->sm_count * 4));
-  const int cs_rows = 256, cs_parts = (n + cs_rows - 1) / cs_rows;
-  CDL_TRY(ws_get(ctx, "solve.R", (size_t)n * k * 8, &vR));
-  CDL_TRY(ws_get(ctx, "solve.x", (size_t)np * kp * xe, &vx));
-  if (bf16) CDL_TRY(ws_get(ctx, "solve.xop", 2 * (size_t)kp * np * 2, &vxop));
-  CDL_TRY(ws_get(ctx, "solve.part", (size_t)splits * np * part_cols * xe, &vpart));
-  CDL_TRY(ws_get(ctx, "solve.red", (size_t)nred * 8, &vred));
-  CDL_TRY(ws_get(ctx, "solve.scal", 64, &vscal));
-  CDL_TRY(ws_get(ctx, "solve.zh", (size_t)n * k * 4, &vzh));
-  CDL_TRY(ws_get(ctx, "solve.zl", (size_t)n * k * 4, &vzl));
-  CDL_TRY(ws_get(ctx, "solve.colsum", (size_t)(cs_parts + 1) * k * 8, &vcs));   // partial sums, then the shift
-  void *vdz, *vpart2 = nullptr, *vdzop = nullptr;
-  CDL_TRY(ws_get(ctx, "solve.dz", (size_t)np * kp * 4, &vdz));
-  if (bf16) {
-    CDL_TRY(ws_get(ctx, "solve.part2", (size_t)splits * np * part_cols * xe, &vpart2));
-    CDL_TRY(ws_get(ctx, "solve.dzop", 2 * (size_t)kp * np * 2, &vdzop));
-  }
-  double* R = static_cast<double*>(vR);
-  double* red = static_cast<double*>(vred);
-  double* scal = static_cast<double*>(vscal);
-  const size_t nk = (size_t)n * k;
-
-  auto sumsq = [&](const double* v, size_t count, double* out, double* host) -> int {
-    const int nb = (int)std::min<size_t>(1024, (count + RED_THREADS - 1) / RED_THREADS);
+    const size_t part_cols = bf16 ? 2 * (size_t)kp : (size_t)kp;
+    res_gx = (n + RB_M - 1) / RB_M;
+    res_gy = (k + RB_N - 1) / RB_N;
+    upd_gx = (n + RU_M - 1) / RU_M;
+    upd_gy = (k + RU_N - 1) / RU_N;
+    const int nred = std::max(res_gx * res_gy, std::max(1024, ctx->sm_count * 4));
+    cs_parts = (n + cs_rows - 1) / cs_rows;
+    CDL_TRY(ws("solve.R", idx, (size_t)n * k * 8, &vR));
+    CDL_TRY(ws("solve.x", idx, (size_t)np * kp * xe, &vx));
+    if (bf16) CDL_TRY(ws("solve.xop", idx, 2 * (size_t)kp * np * 2, &vxop));
+    CDL_TRY(ws("solve.part", idx, (size_t)splits * np * part_cols * xe, &vpart));
+    CDL_TRY(ws("solve.red", idx, (size_t)nred * 8, &vred));
+    CDL_TRY(ws("solve.scal", idx, 64, &vscal));
+    CDL_TRY(ws("solve.zh", idx, (size_t)n * k * 4, &vzh));
+    CDL_TRY(ws("solve.zl", idx, (size_t)n * k * 4, &vzl));
+    CDL_TRY(ws("solve.colsum", idx, (size_t)(cs_parts + 1) * k * 8, &vcs));   // partial sums, then the shift
+    CDL_TRY(ws("solve.dz", idx, (size_t)np * kp * 4, &vdz));
+    if (bf16) {
+      CDL_TRY(ws("solve.part2", idx, (size_t)splits * np * part_cols * xe, &vpart2));
+      CDL_TRY(ws("solve.dzop", idx, 2 * (size_t)kp * np * 2, &vdzop));
+    }
+    R = static_cast<double*>(vR);
+    red = static_cast<double*>(vred);
+    scal = static_cast<double*>(vscal);
+    nk = (size_t)n * k;
+    nparts = res_gx * res_gy;   // per-block partial sums of R^2 written by the last residual kernel
     {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_sumsq<<<nb, RED_THREADS, 0, st>>>(v, count, red);
-      CDL_TRY(L.done());
+      const int nb = (int)std::min<size_t>(1024, (nk + RED_THREADS - 1) / RED_THREADS);
+      {
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_sumsq<<<nb, RED_THREADS, 0, st>>>(Y, nk, red);
+        CDL_TRY(L.done());
+      }
+      {
+        Launch L(ctx, CDL_KC_MISC, 0);
+        k_reduce<<<1, 1024, 0, st>>>(red, nb, scal);
+        CDL_TRY(L.done());
+      }
+      CDL_CUDA_TRY(cudaMemcpyAsync(&yy, scal, 8, cudaMemcpyDeviceToHost, st));
+      CDL_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_reduce<<<1, 1024, 0, st>>>(red, nb, out);
-      CDL_TRY(L.done());
+    CDL_CUDA_TRY(cudaMemsetAsync(Z, 0, nk * 8, st));
+    CDL_CUDA_TRY(cudaMemcpyAsync(R, Y, nk * 8, cudaMemcpyDeviceToDevice, st));
+    if (stats) {
+      stats->iters = 0;
+      stats->rel_res = yy > 0 ? 1.0 : 0.0;
+      for (double& h : stats->history) h = 0.0;
     }
-    CDL_CUDA_TRY(cudaMemcpyAsync(host, out, 8, cudaMemcpyDeviceToHost, st));
-    CDL_CUDA_TRY(cudaStreamSynchronize(st));
+    done = yy == 0.0;
+    rel = yy > 0 ? 1.0 : 0.0;
     return CDL_OK;
-  };
-
-  double yy = 0.0;
-  CDL_TRY(sumsq(Y, nk, scal, &yy));
-  if (yy_out) *yy_out = yy;
-  CDL_CUDA_TRY(cudaMemsetAsync(Z, 0, nk * 8, st));
-  CDL_CUDA_TRY(cudaMemcpyAsync(R, Y, nk * 8, cudaMemcpyDeviceToDevice, st));
-  if (stats) {
-    stats->iters = 0;
-    stats->rel_res = yy > 0 ? 1.0 : 0.0;
-    for (double& h : stats->history) h = 0.0;
   }
-  if (yy == 0.0) return CDL_OK;
-  const int upd_gx = (n + RU_M - 1) / RU_M, upd_gy = (k + RU_N - 1) / RU_N;
-  int nparts = res_gx * res_gy;   // per-block partial sums of R^2 written by the last residual kernel
-  // Full float-float residual R = Y - L Z.
-  auto full_residual = [&](double* rel_out) -> int {
+
+  // Full residual R = Y - L Z (float64-class).
+  int full_residual() {
     if (ch->regen) {
       // A Z of a graph regenerated panel by panel: each panel's transposed
       // exact slices are one K range of A Z (A symmetric), added into G
       const RegenSource& rs = *ch->regen;
       const int ngroups = (k + 127) / 128;
-      void *vzs, *vG, *vmb, *vcs;
+      void *vzs, *vG, *vmb, *vcz;
       CDL_TRY(ws_get(ctx, "solve.zslices", 6 * (size_t)128 * np * 2, &vzs));
       CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * RESID_PAIRS * np * 128 * sizeof(double), &vG));
       CDL_TRY(ws_get(ctx, "solve.zmax", (size_t)k * 8, &vmb));
-      CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcs));
+      CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcz));
       CDL_CUDA_TRY(cudaMemsetAsync(vmb, 0, (size_t)k * 8, st));
       {
         Launch L(ctx, CDL_KC_MISC, 0);
@@ -920,7 +951,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
           Launch L(ctx, CDL_KC_MISC, 0);
           k_zslice<<<ctx->sm_count * 4, 256, 0, st>>>(Z, n, k, np, c0, kg,
                                                        static_cast<const unsigned long long*>(vmb),
-                                                       static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcs));
+                                                       static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcz));
           CDL_TRY(L.done());
         }
         CDL_CUDA_TRY(cudaMemsetAsync(Gg, 0, (size_t)RESID_PAIRS * np * kg * sizeof(double), st));
@@ -934,7 +965,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
       const int nb = std::min(1024, (int)blocks_for(nk, 256));
       Launch L(ctx, CDL_KC_RESIDUAL, 0);
       k_resid_combine<<<nb, 256, 0, st>>>(Y, Z, ch->D, n, k, np, static_cast<const double*>(vG),
-                                          static_cast<const double*>(vcs), ch->a_scale, R, red);
+                                          static_cast<const double*>(vcz), ch->a_scale, R, red);
       CDL_TRY(L.done());
       nparts = nb;
       return CDL_OK;
@@ -942,11 +973,11 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
     if (ch->aslices) {
       // A Z from exact bf16 slices on the tensor cores, in column groups of <= 128
       const int ngroups = (k + 127) / 128;
-      void *vzs, *vG, *vmb, *vcs;
+      void *vzs, *vG, *vmb, *vcz;
       CDL_TRY(ws_get(ctx, "solve.zslices", 6 * (size_t)128 * np * 2, &vzs));
       CDL_TRY(ws_get(ctx, "solve.G", (size_t)ngroups * RESID_PAIRS * np * 128 * sizeof(double), &vG));
       CDL_TRY(ws_get(ctx, "solve.zmax", (size_t)k * 8, &vmb));
-      CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcs));
+      CDL_TRY(ws_get(ctx, "solve.zc", (size_t)k * 8, &vcz));
       CDL_CUDA_TRY(cudaMemsetAsync(vmb, 0, (size_t)k * 8, st));
       {
         Launch L(ctx, CDL_KC_MISC, 0);
@@ -961,7 +992,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
           Launch L(ctx, CDL_KC_MISC, 0);
           k_zslice<<<ctx->sm_count * 4, 256, 0, st>>>(Z, n, k, np, c0, kg,
                                                        static_cast<const unsigned long long*>(vmb),
-                                                       static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcs));
+                                                       static_cast<__nv_bfloat16*>(vzs), static_cast<double*>(vcz));
           CDL_TRY(L.done());
         }
         CDL_TRY(resid_tc(ctx, ch, vzs, kg, static_cast<double*>(vG) + (size_t)g * RESID_PAIRS * np * 128));
@@ -969,7 +1000,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
       const int nb = std::min(1024, (int)blocks_for(nk, 256));
       Launch L(ctx, CDL_KC_RESIDUAL, 0);
       k_resid_combine<<<nb, 256, 0, st>>>(Y, Z, ch->D, n, k, np, static_cast<const double*>(vG),
-                                          static_cast<const double*>(vcs), ch->a_scale, R, red);
+                                          static_cast<const double*>(vcz), ch->a_scale, R, red);
       CDL_TRY(L.done());
       nparts = nb;
       return CDL_OK;
@@ -988,9 +1019,10 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
     }
     nparts = res_gx * res_gy;
     return CDL_OK;
-  };
+  }
+
   // Recursive update R -= L dZ in float32.
-  auto update_residual = [&]() -> int {
+  int update_residual() {
     if (bf16 && ch->aop) {
       // dZ -> bf16 hi/lo operand, then A_hi and A_lo times it on the tensor cores
       {
@@ -1015,8 +1047,9 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
     k_residual_update<<<g, 256, 0, st>>>(A, static_cast<const float*>(vdz), ch->D, n, k, kp, R, red);
     nparts = upd_gx * upd_gy;
     return L.done();
-  };
-  auto read_norm = [&](double* rel_out) -> int {
+  }
+
+  int read_norm() {
     double rr = 0.0;
     {
       Launch L(ctx, CDL_KC_MISC, 0);
@@ -1025,32 +1058,34 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
     }
     CDL_CUDA_TRY(cudaMemcpyAsync(&rr, scal + 1, 8, cudaMemcpyDeviceToHost, st));
     CDL_CUDA_TRY(cudaStreamSynchronize(st));
-    *rel_out = std::sqrt(rr / yy);
+    rel = std::sqrt(rr / yy);
     return CDL_OK;
-  };
+  }
 
-  double rel = 1.0;
-  int iters = 0;
-  bool exact_r = true;      // R was last formed in full (not recursively)
-  double drift = 0.0;       // bound on the recursive residual's accumulated error
-  // a regenerated graph keeps no A operand for the recursive update
-  const bool always_full = (opts->flags & CDL_SOLVE_FULL_RESIDUAL) != 0 || ch->regen != nullptr;
-  while (true) {
-    if (opts->rel_tol > 0 && rel <= opts->rel_tol) {
-      if (!exact_r && rel + drift > 0.1 * opts->rel_tol) {
-        // certify a recursively updated residual with a full one
-        CDL_TRY(full_residual(nullptr));
-        CDL_TRY(read_norm(&rel));
-        exact_r = true;
-        drift = 0.0;
-        if (stats && iters >= 1 && iters <= 64) stats->history[iters - 1] = rel;
-        continue;
+  // Before a step: stop when the residual is certified below the tolerance
+  // (a recursively updated one is formed in full first unless its drift
+  // bound is below a tenth of it), at the iteration cap, or on divergence.
+  int pre_step(const cdl_solve_opts* opts) {
+    while (true) {
+      if (opts->rel_tol > 0 && rel <= opts->rel_tol) {
+        if (!exact_r && rel + drift > 0.1 * opts->rel_tol) {
+          CDL_TRY(full_residual());
+          CDL_TRY(read_norm());
+          exact_r = true;
+          drift = 0.0;
+          if (stats && iters >= 1 && iters <= 64) stats->history[iters - 1] = rel;
+          continue;
+        }
+        done = true;
+        return CDL_OK;
       }
-      break;
+      if (iters >= opts->max_iter || !(rel <= 1e6)) done = true;   // NaN or growing: no contraction
+      return CDL_OK;
     }
-    if (iters >= opts->max_iter) break;
-    if (!(rel <= 1e6)) break;   // NaN or a growing residual: the preconditioner does not converge
-    // x = D^{-1/2} R in the chain's working precision
+  }
+
+  // x = D^{-1/2} R in the chain's working precision (and its bf16 operand)
+  int precond_in() {
     {
       const size_t cnt = (size_t)np * kp;
       Launch L(ctx, CDL_KC_MISC, 0);
@@ -1069,29 +1104,34 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
                                        static_cast<__nv_bfloat16*>(vxop), 0);
       CDL_TRY(L.done());
     }
-    // x <- (I + S~_lvl) x for every level
-    for (int lvl = 0; lvl < ch->d_eff; ++lvl) {
-      if (bf16) {
-        CDL_TRY(apply_tc(ctx, ch, lvl, vxop, static_cast<float*>(vpart), kp, splits));
-        dim3 g((np + 31) / 32, (kp + 31) / 32);
-        Launch L(ctx, CDL_KC_MISC, 0);
-        k_update_bf16<<<g, 256, 0, st>>>(static_cast<float*>(vx), static_cast<const float*>(vpart), splits,
-                                         np, kp, static_cast<__nv_bfloat16*>(vxop), 1);
-        CDL_TRY(L.done());
-      } else {
-        CDL_TRY(apply_simt(ctx, ch, lvl, vx, vpart, kp, splits));
-        const size_t cnt = (size_t)np * kp;
-        Launch L(ctx, CDL_KC_MISC, 0);
-        if (ch->dtype == CDL_F64)
-          k_update_simt<double><<<blocks_for(cnt, 256), 256, 0, st>>>(
-              static_cast<double*>(vx), static_cast<const double*>(vpart), splits, cnt);
-        else
-          k_update_simt<float><<<blocks_for(cnt, 256), 256, 0, st>>>(
-              static_cast<float*>(vx), static_cast<const float*>(vpart), splits, cnt);
-        CDL_TRY(L.done());
-      }
+    return CDL_OK;
+  }
+
+  // x <- (I + S~_lvl) x
+  int apply_level(int lvl) {
+    if (bf16) {
+      CDL_TRY(apply_tc(ctx, ch, lvl, vxop, static_cast<float*>(vpart), kp, splits));
+      dim3 g((np + 31) / 32, (kp + 31) / 32);
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_update_bf16<<<g, 256, 0, st>>>(static_cast<float*>(vx), static_cast<const float*>(vpart), splits, np, kp,
+                                       static_cast<__nv_bfloat16*>(vxop), 1);
+      return L.done();
     }
-    // Z += D^{-1/2} x, then D-weighted centring
+    CDL_TRY(apply_simt(ctx, ch, lvl, vx, vpart, kp, splits));
+    const size_t cnt = (size_t)np * kp;
+    Launch L(ctx, CDL_KC_MISC, 0);
+    if (ch->dtype == CDL_F64)
+      k_update_simt<double><<<blocks_for(cnt, 256), 256, 0, st>>>(
+          static_cast<double*>(vx), static_cast<const double*>(vpart), splits, cnt);
+    else
+      k_update_simt<float><<<blocks_for(cnt, 256), 256, 0, st>>>(
+          static_cast<float*>(vx), static_cast<const float*>(vpart), splits, cnt);
+    return L.done();
+  }
+
+  // Z += D^{-1/2} x, D-weighted centring, then the residual (in full on the
+  // first step or always_full, else recursively) and its norm.
+  int finish_step(bool always_full) {
     {
       Launch L(ctx, CDL_KC_MISC, 0);
       if (ch->dtype == CDL_F64)
@@ -1122,7 +1162,7 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
     ++iters;
     const double prev = rel;
     if (iters == 1 || always_full) {
-      CDL_TRY(full_residual(nullptr));
+      CDL_TRY(full_residual());
       exact_r = true;
       drift = 0.0;
     } else {
@@ -1130,26 +1170,24 @@ int chain_solve_block(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const 
       drift += 1e-5 * rel;   // error of the L dZ product (16-bit operands or float32), |L dZ| ~ |R| before
       exact_r = false;
     }
-    CDL_TRY(read_norm(&rel));
+    CDL_TRY(read_norm());
     if (!exact_r && rel > 0.5 * prev) {
       // a recursive residual that stops falling is dominated by its own
       // rounding: form it again in full
-      CDL_TRY(full_residual(nullptr));
-      CDL_TRY(read_norm(&rel));
+      CDL_TRY(full_residual());
+      CDL_TRY(read_norm());
       exact_r = true;
       drift = 0.0;
     }
     if (stats && iters <= 64) stats->history[iters - 1] = rel;
+    return CDL_OK;
   }
-  if (stats) {
-    stats->iters = iters;
-    stats->rel_res = rel;
-  }
-  if (!(rel <= 1e6)) return CDL_ERR_NOT_CONVERGED;
-  return (opts->rel_tol > 0 && !(rel <= opts->rel_tol)) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
-}
 
-namespace {
+  int status(const cdl_solve_opts* opts) const {
+    if (!(rel <= 1e6)) return CDL_ERR_NOT_CONVERGED;
+    return (opts->rel_tol > 0 && !(rel <= opts->rel_tol)) ? CDL_ERR_NOT_CONVERGED : CDL_OK;
+  }
+};
 
 // columns c0 .. c0 + kb - 1 of the n x k matrix Y into the n x kb matrix Yb, and back
 __global__ void k_gather_cols(const double* __restrict__ Y, int n, int k, int c0, int kb, double* __restrict__ Yb) {
@@ -1173,52 +1211,87 @@ __global__ void k_scatter_cols(const double* __restrict__ Zb, int n, int kb, int
 // The tensor-core apply multiplies a level by at most 128 right-hand sides
 // (MMA N = 2 kp <= 256 for the hi and lo halves). Alg. 2's Richardson
 // iteration and the chain apply act on each column on its own, so more
-// columns are solved as independent blocks of at most 128, each with its
-// own float64 residual and its own stopping test against its own ||Y_b||.
-// The reported residual is the one of all k columns,
+// columns are solved as blocks of at most 128, each with its own float64
+// residual and its own stopping test against its own ||Y_b||; the blocks
+// step together, and each level is applied to every block still running
+// while it is loaded (levels in host memory cross the link once per step,
+// not once per block). The reported residual is the one of all k columns,
 // sqrt(sum_b ||R_b||^2 / sum_b ||Y_b||^2), below rel_tol when every block
 // is; iters is the largest block count and history[t] combines the blocks'
 // residuals after t + 1 steps (a block that stopped earlier keeps its last).
 int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double* Y, int k,
                 const cdl_solve_opts* opts, double* Z, cdl_solve_stats* stats) {
   const bool tensor = ch->dtype == CDL_BF16 || ch->dtype == CDL_FP8E4M3 || ch->dtype == CDL_FP8E4M3_T128;
-  if (!tensor || k <= 128) return chain_solve_block(ctx, ch, A, Y, k, opts, Z, stats, nullptr);
-  const int nblk = (k + 127) / 128;
-  const int kb_max = (int)round_up((k + nblk - 1) / nblk, 16);
+  const int nblk = (tensor && k > 128) ? (k + 127) / 128 : 1;
+  const int kb_max = nblk == 1 ? k : (int)round_up((k + nblk - 1) / nblk, 16);
   const int n = (int)ch->n;
   cudaStream_t st = ctx->stream;
-  void *vyb, *vzb;
-  CDL_TRY(ws_get(ctx, "solve.block_y", (size_t)n * kb_max * 8, &vyb));
-  CDL_TRY(ws_get(ctx, "solve.block_z", (size_t)n * kb_max * 8, &vzb));
-  double* Yb = static_cast<double*>(vyb);
-  double* Zb = static_cast<double*>(vzb);
-  const unsigned nb = (unsigned)std::min<size_t>(((size_t)n * kb_max + 255) / 256, (size_t)ctx->sm_count * 8);
+  std::vector<SolveBlock> B(nblk);
+  std::vector<cdl_solve_stats> bst(nblk);
+  const unsigned gb = (unsigned)std::min<size_t>(((size_t)n * kb_max + 255) / 256, (size_t)ctx->sm_count * 8);
+  for (int b = 0; b < nblk; ++b) {
+    SolveBlock& s = B[b];
+    s.ctx = ctx;
+    s.ch = ch;
+    s.A = A;
+    const int c0 = b * kb_max;
+    s.k = std::min(kb_max, k - c0);
+    if (nblk == 1) {
+      s.Y = Y;
+      s.Z = Z;
+      s.stats = stats;
+    } else {
+      void *vyb, *vzb;
+      CDL_TRY(ws_get(ctx, ("solve.block_y#" + std::to_string(b)).c_str(), (size_t)n * kb_max * 8, &vyb));
+      CDL_TRY(ws_get(ctx, ("solve.block_z#" + std::to_string(b)).c_str(), (size_t)n * kb_max * 8, &vzb));
+      s.Y = static_cast<double*>(vyb);
+      s.Z = static_cast<double*>(vzb);
+      s.stats = &bst[b];
+      Launch L(ctx, CDL_KC_MISC, 0);
+      k_gather_cols<<<gb, 256, 0, st>>>(Y, n, k, c0, s.k, static_cast<double*>(vyb));
+      CDL_TRY(L.done());
+    }
+    CDL_TRY(s.init(b));
+  }
+  // a regenerated graph keeps no A operand for the recursive update
+  const bool always_full = (opts->flags & CDL_SOLVE_FULL_RESIDUAL) != 0 || ch->regen != nullptr;
+  while (true) {
+    std::vector<SolveBlock*> run;
+    for (SolveBlock& s : B) {
+      if (s.done) continue;
+      CDL_TRY(s.pre_step(opts));
+      if (!s.done) run.push_back(&s);
+    }
+    if (run.empty()) break;
+    for (SolveBlock* s : run) CDL_TRY(s->precond_in());
+    for (int lvl = 0; lvl < ch->d_eff; ++lvl)
+      for (SolveBlock* s : run) CDL_TRY(s->apply_level(lvl));
+    for (SolveBlock* s : run) CDL_TRY(s->finish_step(always_full));
+  }
+  if (nblk == 1) {
+    if (stats) {
+      stats->iters = B[0].iters;
+      stats->rel_res = B[0].rel;
+    }
+    return B[0].status(opts);
+  }
   double yy_all = 0.0, rr_all = 0.0;
   double hist_rr[64] = {0};
   int iters = 0, status = CDL_OK;
-  for (int c0 = 0; c0 < k; c0 += kb_max) {
-    const int kb = std::min(kb_max, k - c0);
+  for (int b = 0; b < nblk; ++b) {
+    const SolveBlock& s = B[b];
+    if (s.status(opts) != CDL_OK) status = CDL_ERR_NOT_CONVERGED;
     {
       Launch L(ctx, CDL_KC_MISC, 0);
-      k_gather_cols<<<nb, 256, 0, st>>>(Y, n, k, c0, kb, Yb);
+      k_scatter_cols<<<gb, 256, 0, st>>>(s.Z, n, s.k, b * kb_max, k, Z);
       CDL_TRY(L.done());
     }
-    cdl_solve_stats sb;
-    double yy = 0.0;
-    const int r = chain_solve_block(ctx, ch, A, Yb, kb, opts, Zb, &sb, &yy);
-    if (r != CDL_OK && r != CDL_ERR_NOT_CONVERGED) return r;
-    if (r == CDL_ERR_NOT_CONVERGED) status = r;
-    {
-      Launch L(ctx, CDL_KC_MISC, 0);
-      k_scatter_cols<<<nb, 256, 0, st>>>(Zb, n, kb, c0, k, Z);
-      CDL_TRY(L.done());
-    }
-    yy_all += yy;
-    rr_all += sb.rel_res * sb.rel_res * yy;
-    iters = std::max(iters, sb.iters);
+    yy_all += s.yy;
+    rr_all += s.rel * s.rel * s.yy;
+    iters = std::max(iters, s.iters);
     for (int t = 0; t < 64; ++t) {
-      const double h = t < sb.iters ? sb.history[t] : sb.rel_res;
-      hist_rr[t] += h * h * yy;
+      const double h = t < s.iters ? bst[b].history[t] : s.rel;
+      hist_rr[t] += h * h * s.yy;
     }
   }
   if (stats) {
