@@ -46,6 +46,10 @@ struct BatchPlan {
   BatchSolve bs;
   GraphBatch gb;
   const PGraph* pgs = nullptr;
+  // level 0 of every graph in three grouped launches
+  const CGraph* cgs = nullptr;
+  BTiles cvec, csplit, cinit;
+  double cinit_bytes = 0;
   // autotuned variants: squaring tile width per graph size, projection rows per block
   struct SqVariant {
     int max_npad_128;            // graphs up to this order use 128 x 128 tiles
@@ -186,8 +190,12 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   int res_tm, res_tn;
   batch_residual_tile(k, &res_tm, &res_tn);
   const int ncb = (k + res_tn - 1) / res_tn;
+  std::vector<uint32_t> cvec, csplit, cinit;
   for (int g : P->order) {
     const int nn = gn(g), np = gnp(g);
+    for (int b = 0; b < (np + 255) / 256; ++b) cvec.push_back(((uint32_t)b << 12) | (uint32_t)g);
+    for (size_t b = 0; b * 2048 < (size_t)nn * nn; ++b) csplit.push_back(((uint32_t)b << 12) | (uint32_t)g);
+    for (size_t b = 0; b * 2048 < (size_t)np * (np / 8); ++b) cinit.push_back(((uint32_t)b << 12) | (uint32_t)g);
     for (int b = 0; b < np / 32; ++b) t32.push_back(((uint32_t)b << 12) | (uint32_t)g);
     const int eb = (int)(((size_t)nn * k + 255) / 256);
     for (int b = 0; b < eb; ++b) elem.push_back(((uint32_t)b << 12) | (uint32_t)g);
@@ -224,13 +232,16 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     P->pv.push_back(pvar);
   }
   size_t ntiles = ap.size() + t32.size() + elem.size() + res.size() + csb.size() + sel.size() + spairs.size() +
-                  snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size();
+                  snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size() + cvec.size() + csplit.size() +
+                  cinit.size();
   for (auto& v : sq) ntiles += v.size();
   for (auto& v : pblocks) ntiles += v.size();
   std::vector<GGraph> ggs(G2);
   std::vector<PGraph> pgs(G2);
+  std::vector<CGraph> cgs(G2);
   GGraph* d_ggs = nullptr;
   PGraph* d_pgs = nullptr;
+  CGraph* d_cgs = nullptr;
   int4* d_sel = nullptr;
   char* sel_all = nullptr;
   const size_t sel_one = graph_select_bytes();
@@ -252,6 +263,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     d_tiles = c.take<uint32_t>(ntiles);
     d_ggs = c.take<GGraph>(G2);
     d_pgs = c.take<PGraph>(G2);
+    d_cgs = c.take<CGraph>(G2);
     d_sel = c.take<int4>(gt.sel.size());
     sel_all = c.take<char>(G2 * sel_one);
     for (int g = 0; g < G2; ++g) {
@@ -268,6 +280,9 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
       ch.aop = c.take<uint16_t>((size_t)2 * np * np);
       ch.ahl = c.take<float>((size_t)2 * nn * nn);
       ch.rsqrt_d = c.take<double>(np);
+      cgs[g].u = c.take<double>(np);
+      cgs[g].rsf = c.take<float>(np);
+      cgs[g].uf = c.take<float>(np);
       B.Z = c.take<double>(nk);
       B.R = c.take<double>(nk);
       B.x = c.take<float>((size_t)np * kp);
@@ -349,6 +364,17 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     Gg.sel = sel_all + (size_t)g * sel_one;
     Gg.n = nn;
     Gg.T = T;
+    CGraph& Cg = cgs[g];
+    Cg.A = P->A[g];
+    Cg.D = ch.D;
+    Cg.vol = ch.vol;
+    Cg.rsd = ch.rsqrt_d;
+    Cg.ahl = ch.ahl;
+    Cg.L0 = ch.level(0);
+    Cg.aop = ch.aop;
+    Cg.n = nn;
+    Cg.npad = np;
+    P->cinit_bytes += 8.0 * nn * (double)nn + 6.0 * np * (double)np;
     PGraph& Pg = pgs[g];
     Pg.A = P->A[g];
     Pg.Y = P->Y[g];
@@ -433,13 +459,18 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   add(gt.dist, gb.dist);
   add(gt.rows, gb.rows);
   for (size_t v = 0; v < pblocks.size(); ++v) add(pblocks[v], P->pv[v].blocks);
+  add(cvec, P->cvec);
+  add(csplit, P->csplit);
+  add(cinit, P->cinit);
   // before tuning: 128 x 128 tiles up to order 1024, the widest projection blocks
   P->sq_choice = std::min<int>(1, (int)P->sqv.size() - 1);
   P->pv_choice = 0;
   if ((st = upload(P->stream, d_tiles, all)) != CDL_OK || (st = upload(P->stream, d_gs, gs)) != CDL_OK ||
       (st = upload(P->stream, P->jobs, jobs)) != CDL_OK || (st = upload(P->stream, d_ggs, ggs)) != CDL_OK ||
-      (st = upload(P->stream, d_pgs, pgs)) != CDL_OK || (st = upload(P->stream, d_sel, gt.sel)) != CDL_OK)
+      (st = upload(P->stream, d_pgs, pgs)) != CDL_OK || (st = upload(P->stream, d_sel, gt.sel)) != CDL_OK ||
+      (st = upload(P->stream, d_cgs, cgs)) != CDL_OK)
     return fail(st);
+  P->cgs = d_cgs;
   gb.G2 = G2;
   gb.sigma = o->sigma;
   gb.gs = d_ggs;
@@ -513,7 +544,7 @@ int run_batch(BatchPlan* P, int fixed_slots) {
   cdl_ctx* c = P->inner;
   const int G2 = 2 * P->G;
   CDL_TRY(graph_build_grouped(c, P->gb));
-  for (int g : P->order) CDL_TRY(chain_init(c, &P->chains[g], P->A[g]));
+  CDL_TRY(chain_init_grouped(c, P->cgs, P->cvec, P->csplit, P->cinit, P->cinit_bytes));
   const BatchPlan::SqVariant& sv = P->sqv[P->sq_choice];
   for (int l = 0; l + 1 < P->d; ++l)
     CDL_TRY(tc_square_grouped(c, &sv.first[l], sv.groups + (size_t)l * G2, sv.tiles.p, sv.tiles.count, P->sq_flops));

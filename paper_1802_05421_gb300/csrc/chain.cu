@@ -21,11 +21,9 @@ namespace {
 
 // rsqrt_d_i = D_i^{-1/2}, u_i = (D_i / vol)^{1/2}; zero in the padding.
 // Float copies rsf, uf feed the bf16 level-0 pass.
-__global__ void k_chain_vectors(const double* __restrict__ D, const double* __restrict__ vol,
-                                int n, int npad, double* __restrict__ rsd, double* __restrict__ u,
-                                float* __restrict__ rsf, float* __restrict__ uf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npad) return;
+__device__ __forceinline__ void chain_vector(const double* __restrict__ D, const double* __restrict__ vol, int n,
+                                             double* __restrict__ rsd, double* __restrict__ u,
+                                             float* __restrict__ rsf, float* __restrict__ uf, int i) {
   if (i < n) {
     double di = D[i];
     rsd[i] = 1.0 / sqrt(di);
@@ -36,6 +34,13 @@ __global__ void k_chain_vectors(const double* __restrict__ D, const double* __re
   }
   rsf[i] = (float)rsd[i];
   uf[i] = (float)u[i];
+}
+
+__global__ void k_chain_vectors(const double* __restrict__ D, const double* __restrict__ vol,
+                                int n, int npad, double* __restrict__ rsd, double* __restrict__ u,
+                                float* __restrict__ rsf, float* __restrict__ uf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npad) chain_vector(D, vol, n, rsd, u, rsf, uf, i);
 }
 
 template <typename T>
@@ -234,21 +239,17 @@ __device__ __forceinline__ void digits6_fbits(long long N, uint32_t (&f)[6]) {
 
 // SL = false (the batched form's chains, which keep no slices): S and
 // a_scale are not touched (they may be null).
+// One group of 8 columns (index g over the npad x npad / 8 groups, row-major)
+// of k_chain_init_tc's outputs.
 template <bool SL>
-__global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict__ A, int n, int npad,
-                                                        const float* __restrict__ rsf, const float* __restrict__ uf,
-                                                        __nv_bfloat16* __restrict__ L0, __nv_bfloat16* __restrict__ Ahi,
-                                                        __nv_bfloat16* __restrict__ Alo, uint16_t* __restrict__ S,
-                                                        double* __restrict__ a_scale) {
-  int sexp = 0;
-  if constexpr (SL) {
-    sexp = pow2_exp_above((unsigned long long)__double_as_longlong(a_scale[1]));
-    if (blockIdx.x == 0 && threadIdx.x == 0) a_scale[0] = __longlong_as_double((long long)(1023 + sexp) << 52);
-  }
+__device__ __forceinline__ void chain_init_tc_group(const double* __restrict__ A, int n, int npad,
+                                                    const float* __restrict__ rsf, const float* __restrict__ uf,
+                                                    __nv_bfloat16* __restrict__ L0, __nv_bfloat16* __restrict__ Ahi,
+                                                    __nv_bfloat16* __restrict__ Alo, uint16_t* __restrict__ S, int sexp,
+                                                    size_t g) {
   const size_t plane = (size_t)npad * npad;
   const int gpr = npad / 8;                               // groups of 8 columns per row
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < (size_t)npad * gpr;
-       g += (size_t)gridDim.x * blockDim.x) {
+  {
     const int i = (int)(g / gpr), j0 = (int)(g % gpr) * 8;
     const size_t o = (size_t)i * npad + j0;
     uint32_t wl[4] = {0, 0, 0, 0}, wh[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0}, ws[6][4] = {};
@@ -292,6 +293,23 @@ __global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict_
         *reinterpret_cast<uint4*>(S + (size_t)t * plane + o) = make_uint4(ws[t][0], ws[t][1], ws[t][2], ws[t][3]);
     }
   }
+}
+
+template <bool SL>
+__global__ void __launch_bounds__(256) k_chain_init_tc(const double* __restrict__ A, int n, int npad,
+                                                        const float* __restrict__ rsf, const float* __restrict__ uf,
+                                                        __nv_bfloat16* __restrict__ L0, __nv_bfloat16* __restrict__ Ahi,
+                                                        __nv_bfloat16* __restrict__ Alo, uint16_t* __restrict__ S,
+                                                        double* __restrict__ a_scale) {
+  int sexp = 0;
+  if constexpr (SL) {
+    sexp = pow2_exp_above((unsigned long long)__double_as_longlong(a_scale[1]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) a_scale[0] = __longlong_as_double((long long)(1023 + sexp) << 52);
+  }
+  const int gpr = npad / 8;                               // groups of 8 columns per row
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < (size_t)npad * gpr;
+       g += (size_t)gridDim.x * blockDim.x)
+    chain_init_tc_group<SL>(A, n, npad, rsf, uf, L0, Ahi, Alo, S, sexp, g);
 }
 
 
@@ -488,6 +506,39 @@ __global__ void __launch_bounds__(256) k_panel_slices_t(const double* __restrict
       for (int q = 0; q < 6; ++q) S[(size_t)q * plane + o] = (uint16_t)(dg[q] >> 16);
     }
   }
+}
+
+// ---- batched form: level 0 of every graph in three launches
+__global__ void __launch_bounds__(256) k_g_chain_vectors(const uint32_t* __restrict__ tiles,
+                                                          const CGraph* __restrict__ cg) {
+  const uint32_t t = tiles[blockIdx.x];
+  const CGraph& G = cg[t & 0xFFFu];
+  const int i = (int)(t >> 12) * 256 + threadIdx.x;
+  if (i < G.npad) chain_vector(G.D, G.vol, G.n, G.rsd, G.u, G.rsf, G.uf, i);
+}
+
+__global__ void __launch_bounds__(256) k_g_split_a(const uint32_t* __restrict__ tiles, const CGraph* __restrict__ cg) {
+  const uint32_t t = tiles[blockIdx.x];
+  const CGraph& G = cg[t & 0xFFFu];
+  const size_t cnt = (size_t)G.n * G.n;
+  const size_t e1 = min(cnt, ((size_t)(t >> 12) + 1) * 2048);
+  for (size_t i = (size_t)(t >> 12) * 2048 + threadIdx.x; i < e1; i += 256) {
+    const ff v = split_nonneg(G.A[i]);
+    G.ahl[i] = v.hi;
+    G.ahl[cnt + i] = v.lo;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_g_chain_init(const uint32_t* __restrict__ tiles, const CGraph* __restrict__ cg) {
+  const uint32_t t = tiles[blockIdx.x];
+  const CGraph& G = cg[t & 0xFFFu];
+  const size_t groups = (size_t)G.npad * (G.npad / 8);
+  const size_t g1 = min(groups, ((size_t)(t >> 12) + 1) * 2048);
+  __nv_bfloat16* L0 = static_cast<__nv_bfloat16*>(G.L0);
+  __nv_bfloat16* ahi = static_cast<__nv_bfloat16*>(G.aop);
+  __nv_bfloat16* alo = ahi + (size_t)G.npad * G.npad;
+  for (size_t g = (size_t)(t >> 12) * 2048 + threadIdx.x; g < g1; g += 256)
+    chain_init_tc_group<false>(G.A, G.n, G.npad, G.rsf, G.uf, L0, ahi, alo, nullptr, 0, g);
 }
 }  // namespace
 
@@ -708,6 +759,23 @@ int panel_slices_t(cdl_ctx* ctx, const double* panel, int n, int np, int r0, int
   Launch L(ctx, CDL_KC_RESIDUAL, 0);
   k_panel_slices_t<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(panel, n, np, r0, rows, Pw,
                                                                static_cast<uint16_t*>(slicesT));
+  return L.done();
+}
+
+
+int chain_init_grouped(cdl_ctx* ctx, const CGraph* cg, BTiles vec, BTiles split, BTiles init, double bytes) {
+  {
+    Launch L(ctx, CDL_KC_MISC, 0);
+    k_g_chain_vectors<<<vec.count, 256, 0, ctx->stream>>>(vec.p, cg);
+    CDL_TRY(L.done());
+  }
+  {
+    Launch L(ctx, CDL_KC_CHAIN_INIT, 0);
+    k_g_split_a<<<split.count, 256, 0, ctx->stream>>>(split.p, cg);
+    CDL_TRY(L.done());
+  }
+  Launch L(ctx, CDL_KC_CHAIN_INIT, bytes);
+  k_g_chain_init<<<init.count, 256, 0, ctx->stream>>>(init.p, cg);
   return L.done();
 }
 

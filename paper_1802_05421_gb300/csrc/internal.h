@@ -318,6 +318,27 @@ struct GraphBatch {
 };
 int graph_build_grouped(cdl_ctx* ctx, const GraphBatch& b);
 
+// Level-0 formation of one graph of a batch: bf16 chain with A kept as bf16
+// hi/lo (the recursive update's operand) and as float hi/lo planes (the
+// float-float residual's operand).
+struct CGraph {
+  const double* A;   // n x n
+  const double* D;   // npad, zero padded
+  const double* vol;
+  double* rsd;       // npad: D^{-1/2}
+  double* u;         // npad
+  float* rsf;        // npad
+  float* uf;         // npad
+  float* ahl;        // 2 n n: float hi, lo
+  void* L0;          // bf16 npad x npad
+  void* aop;         // bf16 2 npad x npad: A_hi, A_lo
+  int n, npad;
+};
+// Tile tables: vec (b << 12) | g over npad / 256 blocks; split and init
+// (b << 12) | g over 2048-element blocks of n^2 and 2048-group blocks of
+// npad^2 / 8.
+int chain_init_grouped(cdl_ctx* ctx, const CGraph* cg, BTiles vec, BTiles split, BTiles init, double bytes);
+
 // Projection of one graph of a batch.
 struct PGraph {
   const double* A;
