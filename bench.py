@@ -303,11 +303,14 @@ def pairs_per_second(step_ms_max: float, world: int) -> float:
 def run_case(args):
     """Small single-kernel cases for profiler captures (not a bench line):
     graph build, then per case: square (one bf16 chain squaring), solve
-    (bf16 chain d=4 + refinement), project, score."""
+    (bf16 chain d=4 + refinement), project, score; batched: --n ragged pairs
+    (n log-uniform in [256, 4096]) through one eager batched call per rep."""
     import torch
     from paper_1802_05421_gb300 import build as B
     B.build()
     from paper_1802_05421_gb300 import cdl
+    if args.case == "batched":
+        return run_case_batched(args, cdl)
     from workloads import iid_pair
     wl = iid_pair(args.n, 64, 8, seed=5)
     n, T = wl.X[0].shape
@@ -345,6 +348,30 @@ def run_case(args):
         cdl.cdl_chain_free(ch)
     cdl.cdl_ctx_destroy(ctx)
     print(f"case {args.case} n={n} reps={args.reps} ok")
+    return 0
+
+
+def run_case_batched(args, cdl):
+    import torch
+    from workloads import ragged_pairs
+    pairs = ragged_pairs(G=args.n, n_lo=256, n_hi=4096, T=64, seed=7)
+    G = len(pairs)
+    n = np.array([p.X[0].shape[0] for p in pairs], dtype=np.int64)
+    N = int(n.sum())
+    X1 = torch.from_numpy(np.ascontiguousarray(np.concatenate([p.X[0] for p in pairs]))).cuda()
+    X2 = torch.from_numpy(np.ascontiguousarray(np.concatenate([p.X[1] for p in pairs]))).cuda()
+    F = torch.empty(N, dtype=torch.float64, device="cuda")
+    top = torch.empty(G * BATCH_TOPK, dtype=torch.int64, device="cuda")
+    stats = (cdl.cdl_solve_stats * (2 * G))()
+    st, ctx = cdl.cdl_ctx_create(0, torch.cuda.current_stream().cuda_stream, 0)
+    assert st == 0
+    o = cdl.cdl_batch_opts(BATCH_K, BATCH_D, cdl.CDL_BF16, cdl.CDL_F32, SEED, 0.0,
+                           cdl.cdl_solve_opts(30, BATCH_TOL, 0), BATCH_TOPK, 0, 0)
+    for _ in range(args.reps):
+        assert cdl.cdl_caddelag_batched(ctx, G, n, 64, X1, X2, o, F, top, stats) == 0
+    assert cdl.cdl_sync(ctx) == 0
+    cdl.cdl_ctx_destroy(ctx)
+    print(f"case batched pairs={G} sum_n={N} reps={args.reps} ok")
     return 0
 
 
@@ -1034,7 +1061,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-compare-f32", dest="compare_f32", action="store_false",
                     help="skip the plain float32 GPU path comparison step")
-    ap.add_argument("--case", default=None, choices=["square", "solve", "project", "score"],
+    ap.add_argument("--case", default=None, choices=["square", "solve", "project", "score", "batched"],
                     help="run a small single-kernel case for a profiler capture instead of the bench")
     ap.add_argument("--n", type=int, default=12288)
     ap.add_argument("--reps", type=int, default=1)
