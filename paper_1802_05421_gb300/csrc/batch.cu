@@ -169,8 +169,11 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   uint32_t* d_tiles = nullptr;
   // tile tables (host)
   std::vector<uint32_t> t32, elem, res, csb, sel, spairs, snodes;
-  std::vector<int> npads(G2);
-  for (int g = 0; g < G2; ++g) npads[g] = gnp(g);
+  std::vector<int> npads(G2), ns(G2);
+  for (int g = 0; g < G2; ++g) {
+    npads[g] = gnp(g);
+    ns[g] = gn(g);
+  }
   // squaring variants: 128 x 128 tiles up to a graph order (always where the
   // padded order is not a multiple of 256), 128 x 256 tiles above it
   const int thresholds[4] = {0, 1024, 2048, 32768};
@@ -185,7 +188,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     P->sqv.push_back(v);
   }
   std::vector<std::vector<uint32_t>> sq;
-  for (auto& bn : sq_bn) sq.push_back(tc_grouped_square_tiles(npads, bn));
+  for (auto& bn : sq_bn) sq.push_back(tc_grouped_square_tiles(npads, ns, bn));
   const std::vector<uint32_t> ap = tc_grouped_apply_tiles(npads);
   int res_tm, res_tn;
   batch_residual_tile(k, &res_tm, &res_tn);
@@ -393,8 +396,8 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
       const int* gate = &d_st[g].cmd;
       for (size_t v = 0; v < P->sqv.size(); ++v)
         for (int l = 0; l + 1 < d; ++l)
-          if ((st = tc_group_square(&sqg[v][(size_t)l * G2 + g], ch.level(l), ch.level(l + 1), np, sq_bn[v][g])) !=
-              CDL_OK)
+          if ((st = tc_group_square(&sqg[v][(size_t)l * G2 + g], ch.level(l), ch.level(l + 1), np, sq_bn[v][g],
+                                    gn(g))) != CDL_OK)
             return fail(st);
       for (int l = 0; l < d; ++l)
         if ((st = tc_group_apply(&lvg[(size_t)l * G2 + g], ch.level(l), gs[g].xop, gs[g].part, np, kp, gate)) !=

@@ -255,9 +255,10 @@ struct TcGroup {
 static_assert(sizeof(TcGroup) % 64 == 0, "TcGroup keeps its tensor maps 64-byte aligned in arrays");
 // bn = 256: 128 x 256 tiles in 256-blocks (npad % 256 == 0); bn = 128:
 // 128 x 128 tiles (npad % 128 == 0).
-int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn);
+int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn, int n);
 int tc_group_apply(TcGroup* g, const void* amat, const void* xop, float* out, int np, int kp, const int* gate);
-std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, const std::vector<int>& bn);
+std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, const std::vector<int>& n,
+                                              const std::vector<int>& bn);
 std::vector<uint32_t> tc_grouped_apply_tiles(const std::vector<int>& npad);
 int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
                       int ntiles, double flops);

@@ -43,6 +43,10 @@ constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
 constexpr int THREADS = 192;
+constexpr int PACE_KB = 32;                          // k-blocks per pacing step (2048 of K)
+constexpr int PACE_SLACK = 2;                        // steps a CTA may run ahead of the slowest
+constexpr int PACE_MIN_KBLOCKS = 1024;               // paced from K = 65536 on
+constexpr unsigned long long PACE_WAIT_NS = 200000;  // a wait longer than this ends the CTA's pacing
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
@@ -69,6 +73,11 @@ struct TcParams {
   int debug_withhold_load;   // test hook: never issue the first A load (its wait must expire)
   const TcGroup* groups;     // grouped launch: per-graph maps/outputs (nullptr otherwise)
   int gate_mask;             // grouped: a graph's tiles run iff *gate & gate_mask (or gate is null)
+  // K pacing (long k loops): the producer of every CTA counts its arrival at
+  // each step of PACE_KB k-blocks in pace[step] and does not start step s
+  // before all CTAs have reached step s - PACE_SLACK (bounded wait; null: off)
+  unsigned* pace;
+  int pace_steps;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -297,6 +306,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------------------------ TMA producer
     int it = 0;
     bool ok = true;
+    // K pacing: the CTAs sweeping K over tiles that share row panels stay
+    // within a few steps of each other, so a panel's k-blocks are read from
+    // DRAM once and served from L2 to the other CTAs (without it, CTAs drift
+    // apart over long k loops and each streams its panels from DRAM)
+    bool pacing = p.pace != nullptr;
+    const int steps_per_tile = (p.kblocks + PACE_KB - 1) / PACE_KB;
+    int lt = 0;   // tiles this CTA has started
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
       const uint32_t td = p.tiles[t];
       if (!tile_runs(p, td)) continue;
@@ -318,6 +334,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
       }
       for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        if (p.pace && kb % PACE_KB == 0) {
+          const int step = lt * steps_per_tile + kb / PACE_KB;
+          if (step < p.pace_steps) atomicAdd(p.pace + step, 1u);
+          if (pacing && step >= PACE_SLACK && step - PACE_SLACK < p.pace_steps) {
+            const unsigned* c = p.pace + step - PACE_SLACK;
+            const unsigned long long t0 = globaltimer();
+            unsigned v;
+            for (;;) {
+              asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+              if (v >= gridDim.x) break;
+              if (globaltimer() - t0 > PACE_WAIT_NS) {   // a CTA not resident or stalled: stop pacing
+                pacing = false;
+                break;
+              }
+            }
+          }
+        }
         const int s = it % STAGES;
         const uint32_t r = (uint32_t)(it / STAGES);
         if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
@@ -330,7 +363,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!(p.debug_withhold_load && it == 0)) tma_load_2d(a_dst, ma, k0 + kb * BKE, a_row, full_bar(s));
         tma_load_2d(b_dst, mb, k0 + kb * BKE, b_row, full_bar(s));
       }
+      ++lt;
     }
+    if (p.pace)   // arrive at the steps this CTA has no tile for, so no CTA waits on it
+      for (int step = lt * steps_per_tile; step < p.pace_steps; ++step) atomicAdd(p.pace + step, 1u);
     if (!ok) {
       // let copies already issued land before the CTA exits (bounded)
       for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j) {
@@ -1909,7 +1945,7 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   CUtensorMap ma, mb;
   CDL_TRY(make_map(&ma, in, np, np, 128, elem));
   CDL_TRY(make_map(&mb, in, np, np, 256, elem));
-  TcParams p;
+  TcParams p{};
   p.tiles = tiles;
   p.num_tiles = count;
   p.kblocks = np / (128 / elem);
@@ -1925,19 +1961,29 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   p.out16 = fp8 ? ch->level16(level + 1) : nullptr;
   p.debug_withhold_load = ctx->debug_flags & 1;
   p.groups = nullptr;
+  p.pace = nullptr;
+  p.pace_steps = 0;
+  if (p.kblocks >= PACE_MIN_KBLOCKS) {
+    const int grid = std::min(p.num_tiles, ctx->sm_count);
+    p.pace_steps = ((p.num_tiles + grid - 1) / grid) * ((p.kblocks + PACE_KB - 1) / PACE_KB);
+    void* pb;
+    CDL_TRY(ws_get(ctx, "tc.pace", (size_t)p.pace_steps * sizeof(unsigned), &pb));
+    CDL_CUDA_TRY(cudaMemsetAsync(pb, 0, (size_t)p.pace_steps * sizeof(unsigned), ctx->stream));
+    p.pace = static_cast<unsigned*>(pb);
+  }
   const double flops = (double)ch->n * ch->n * (ch->n + 1.0);
   CDL_TRY(launch(ctx, ma, mb, p, CDL_KC_SQUARE, flops, fp8));
   return ch->host_levels ? ooc_write_end(ctx, ch, level + 1) : CDL_OK;
 }
 
-int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn) {
+int tc_group_square(TcGroup* g, const void* level, void* out, int np, int bn, int n) {
   std::memset(g, 0, sizeof(TcGroup));
-  if ((bn != 128 && bn != 256) || np % bn || np > 32768) return CDL_ERR_INVALID_ARG;
+  if ((bn != 128 && bn != 256) || np % bn || np > 32768 || n < 1 || n > np) return CDL_ERR_INVALID_ARG;
   CDL_TRY(make_map(&g->mapA, level, np, np, 128));
   CDL_TRY(make_map(&g->mapB, level, np, np, bn));
   g->out = out;
   g->npad = np;
-  g->kblocks = np / BK;
+  g->kblocks = (n + BK - 1) / BK;   // k-blocks past n hold only zero padding
   g->bn = bn;
   g->idesc = make_idesc(bn);
   return CDL_OK;
@@ -1960,22 +2006,27 @@ int tc_group_apply(TcGroup* g, const void* amat, const void* xop, float* out, in
 
 // Upper-triangle blocks of every graph (256-blocks as two 128 x 256 tiles,
 // or 128 x 128 tiles), graphs ordered largest first.
-std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, const std::vector<int>& bn) {
+std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, const std::vector<int>& n,
+                                              const std::vector<int>& bn) {
   std::vector<int> order(npad.size());
   for (size_t g = 0; g < order.size(); ++g) order[g] = (int)g;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return npad[a] > npad[b]; });
   std::vector<uint32_t> v;
+  // only tiles with a row of the graph (rows and columns past n are zero
+  // padding in every level: the plan's memory starts zeroed and no tile
+  // writes there)
   for (int g : order) {
     if (bn[g] == 128) {
-      const int nb = npad[g] / 128;
+      const int nb = (n[g] + 127) / 128;
       for (int I = 0; I < nb; ++I)
         for (int J = I; J < nb; ++J) v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 24));
     } else {
-      const int nb = npad[g] / 256;
+      const int nb = (n[g] + 255) / 256;
       for (int I = 0; I < nb; ++I)
         for (int J = I; J < nb; ++J)
           for (int h = 0; h < 2; ++h)
-            v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 23) | ((uint32_t)h << 30));
+            if (I * 256 + h * 128 < n[g])
+              v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 23) | ((uint32_t)h << 30));
     }
   }
   return v;
@@ -1994,7 +2045,7 @@ std::vector<uint32_t> tc_grouped_apply_tiles(const std::vector<int>& npad) {
 
 int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
                       int ntiles, double flops) {
-  TcParams p;
+  TcParams p{};
   std::memset(&p, 0, sizeof(p));
   p.tiles = dtiles;
   p.num_tiles = ntiles;
@@ -2009,7 +2060,7 @@ int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dg
 
 int tc_apply_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
                      int ntiles, int kp, int gate_mask, int kc, double work) {
-  TcParams p;
+  TcParams p{};
   std::memset(&p, 0, sizeof(p));
   p.tiles = dtiles;
   p.num_tiles = ntiles;
@@ -2310,7 +2361,7 @@ int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float*
   CUtensorMap ma, mbm;
   CDL_TRY(make_map(&ma, amat, np, np, 128));
   CDL_TRY(make_map(&mbm, xop, bn, np, bn));
-  TcParams p;
+  TcParams p{};
   p.tiles = tiles;
   p.num_tiles = count;
   p.kblocks = np / BK / splits;
