@@ -1433,6 +1433,292 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- bf16 squaring on CTA pairs
+// S~^2 with tcgen05.mma.cta_group::2: the two CTAs of a cluster compute one
+// 256 x 256 block (I, J) of the upper block triangle. CTA rank r loads, per
+// 64-wide k-block, rows I*256 + 128 r of the level (its A half) and rows
+// J*256 + 128 r (its half of B) into its own shared memory; each copy
+// completes on the rank-0 CTA's stage barrier. The rank-0 CTA issues one
+// M = 256, N = 256 MMA per 16 of K that reads both CTAs' halves; each CTA's
+// TMEM holds its 128 rows of the block (two 256-column accumulators, so one
+// block drains while the next accumulates), and both CTAs' epilogues store
+// their rows (mirrored below the diagonal) as in the one-CTA kernel. Per SM
+// a k-block stages 32 KB (16 KB of A, 16 KB of B) for a 128 x 256 x 64
+// product instead of 48 KB, so six stages fit and the L2-to-shared traffic
+// per flop drops by a third. Stage release and accumulator-full signals are
+// multicast by the MMA commits to both CTAs; the epilogue warps of both
+// CTAs arrive on the rank-0 accumulator-empty barrier. K pacing as in the
+// one-CTA kernel. Every wait is bounded; the teardown waits for the last
+// stage releases (no signal lands after a CTA has left) and passes a
+// cluster barrier before the pair frees its TMEM.
+constexpr int S2_STAGES = 6;
+constexpr int S2_HALF = 128 * BK * 2;                  // 16 KiB: 128 rows x 64 bf16
+constexpr int S2_STAGE = 2 * S2_HALF;                  // A half + B half
+constexpr int S2_NBARS = 2 * S2_STAGES + 5;            // full, empty, tfull x2, tempty x2, drain
+constexpr int S2_SMEM_BYTES = S2_STAGES * S2_STAGE + 256 + 1024;
+constexpr int S2_TMEM_COLS = 512;
+
+struct Sq2Params {
+  const uint32_t* tiles;   // upper-triangle 256-blocks: I (bits 0-14), J (bits 15-29)
+  int num_tiles;
+  int kblocks;
+  int npad;
+  uint32_t idesc;          // kind::f16, bf16 x bf16 -> f32, M = 256, N = 256
+  __nv_bfloat16* out;
+  unsigned* status;
+  unsigned* pace;          // K pacing counters (null: off)
+  int pace_steps;
+  int debug_withhold_load;   // test hook: the rank-0 CTA never issues its first A load
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMA load into this CTA's shared memory, completing on a barrier of either
+// CTA of the pair (cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
+      : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the barrier at this offset in both CTAs once the MMAs issued so
+// far have completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((unsigned short)3)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+// Rows r of a 128 x 256 accumulator chunk of 32 columns to the bf16 level:
+// off the diagonal block the row segment and its mirror, on it the upper
+// triangle and its mirror.
+__device__ __forceinline__ void square_store32(__nv_bfloat16* C, int npad, int r, int col0, bool diag,
+                                               const float (&v)[32]) {
+  if (!diag) {
+    uint32_t packed[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      packed[e] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(C + (size_t)r * npad + col0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dst[e] = make_uint4(packed[4 * e], packed[4 * e + 1], packed[4 * e + 2], packed[4 * e + 3]);
+#pragma unroll
+    for (int e = 0; e < 32; ++e) C[(size_t)(col0 + e) * npad + r] = __float2bfloat16_rn(v[e]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int col = col0 + e;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
+      if (col >= r) C[(size_t)r * npad + col] = h;
+      if (col > r) C[(size_t)col * npad + r] = h;
+    }
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    k_tc_sq2(const __grid_constant__ CUtensorMap tmL, const Sq2Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S2_STAGES * S2_STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S2_NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S2_NBARS + 1);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S2_STAGES + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * S2_STAGES + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * S2_STAGES + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S2_STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const uint32_t lead_bar0 = mapa_rank(bar0, 0);   // the rank-0 CTA's barriers, cluster addresses
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S2_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 8);   // the four epilogue warps of each CTA
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmL)) : "memory");
+  }
+  if (warp == 0) {   // one warp of each CTA allocates the pair's TMEM
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S2_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync_all();   // both CTAs' barriers initialised before any remote signal
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer (both CTAs)
+    int it = 0;
+    bool ok = true;
+    bool pacing = p.pace != nullptr;
+    const int steps_per_tile = (p.kblocks + PACE_KB - 1) / PACE_KB;
+    int lt = 0;
+    for (int t = cid; t < p.num_tiles && ok; t += ncl) {
+      const uint32_t td = p.tiles[t];
+      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF;
+      const int a_row = I * 256 + (int)rank * 128, b_row = J * 256 + (int)rank * 128;
+      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        if (p.pace && kb % PACE_KB == 0) {
+          const int step = lt * steps_per_tile + kb / PACE_KB;
+          if (step < p.pace_steps) atomicAdd(p.pace + step, 1u);
+          if (pacing && step >= PACE_SLACK && step - PACE_SLACK < p.pace_steps) {
+            const unsigned* c = p.pace + step - PACE_SLACK;
+            const unsigned long long t0 = globaltimer();
+            unsigned v;
+            for (;;) {
+              asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+              if (v >= gridDim.x) break;
+              if (globaltimer() - t0 > PACE_WAIT_NS) {
+                pacing = false;
+                break;
+              }
+            }
+          }
+        }
+        const int s = it % S2_STAGES;
+        const uint32_t r = (uint32_t)(it / S2_STAGES);
+        if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        if (rank == 0) mbar_expect_tx(full_bar(s), 2 * S2_STAGE);   // both CTAs' copies
+        const uint32_t dst = smem_u32(smem + s * S2_STAGE);
+        const uint32_t fb = lead_bar0 + 8u * s;
+        if (!(p.debug_withhold_load && it == 0 && rank == 0)) tma_load_2d_pair(dst, &tmL, kb * BK, a_row, fb);
+        tma_load_2d_pair(dst + S2_HALF, &tmL, kb * BK, b_row, fb);
+      }
+      ++lt;
+    }
+    if (p.pace)
+      for (int step = lt * steps_per_tile; step < p.pace_steps; ++step) atomicAdd(p.pace + step, 1u);
+    if (ok) {
+      // the last releases of every stage (MMA commits multicast to this CTA)
+      for (int j = it; j < it + S2_STAGES && ok; ++j)
+        if (!mbar_wait(empty_bar(j % S2_STAGES), ((uint32_t)(j / S2_STAGES) & 1) ^ 1, abort_flag, p.status)) ok = false;
+    }
+    if (!ok) {   // copies already issued land within microseconds: give them time (bounded)
+      const unsigned long long t0 = globaltimer();
+      while (globaltimer() - t0 < 50000ull) {
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------ MMA issuer (rank 0 for the pair)
+    int it = 0, tc = 0;
+    bool ok = true, issued = false;
+    for (int t = cid; t < p.num_tiles && ok; t += ncl) {
+      const int acc = tc & 1;
+      const uint32_t ar = (uint32_t)(tc >> 1);
+      ++tc;
+      if (!mbar_wait(tempty_bar(acc), (ar & 1) ^ 1, abort_flag, p.status)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
+      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        const int s = it % S2_STAGES;
+        const uint32_t r = (uint32_t)(it / S2_STAGES);
+        if (!mbar_wait(full_bar(s), r & 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(smem + s * S2_STAGE);
+        const uint64_t adesc = smem_desc(a_addr);
+        const uint64_t bdesc = smem_desc(a_addr + S2_HALF);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16_pair(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
+        issued = true;
+        mma_commit_pair(empty_bar(s));
+      }
+      if (!ok) break;
+      mma_commit_pair(tfull_bar(acc));
+    }
+    if (!ok && issued) {
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain_bar)
+                   : "memory");
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue (both CTAs: 128 rows each)
+    const int q = warp & 3;
+    const int row_in_tile = q * 32 + lane;
+    int tc = 0;
+    for (int t = cid; t < p.num_tiles; t += ncl) {
+      const int acc = tc & 1;
+      const uint32_t ar = (uint32_t)(tc >> 1);
+      ++tc;
+      if (!mbar_wait(tfull_bar(acc), ar & 1, abort_flag, p.status)) break;
+      tc_fence_after();
+      const uint32_t td = p.tiles[t];
+      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF;
+      const int r = I * 256 + (int)rank * 128 + row_in_tile;
+      const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
+      for (int c = 0; c < 8; ++c) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(c * 32), v);
+        square_store32(p.out, p.npad, r, J * 256 + c * 32, I == J, v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_bar0 + 8u * (2 * S2_STAGES + 2 + acc));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();   // neither CTA leaves (or frees TMEM) while the pair still works
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S2_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- e4m3 squaring, hardware block scaling
 // S~^2 for an e4m3 level with one power-of-two scale 2^e per 128 x 128 tile,
 // on tcgen05.mma kind::mxf8f6f4 with block scaling: the tensor core applies
@@ -1872,6 +2158,18 @@ std::vector<uint32_t> square_tiles(int nb) {
   return v;
 }
 
+// Upper-triangle 256-blocks for the CTA-pair kernel, in the same 8 x 8
+// super-block order (one entry per block).
+std::vector<uint32_t> square_pair_tiles(int nb) {
+  std::vector<uint32_t> v;
+  const int G = 8;
+  for (int P = 0; P < nb; P += G)
+    for (int Q = P; Q < nb; Q += G)
+      for (int I = P; I < std::min(P + G, nb); ++I)
+        for (int J = std::max(Q, I); J < std::min(Q + G, nb); ++J) v.push_back((uint32_t)I | ((uint32_t)J << 15));
+  return v;
+}
+
 std::vector<uint32_t> apply_tiles(int mb, int splits) {
   std::vector<uint32_t> v;
   for (int s = 0; s < splits; ++s)
@@ -1927,6 +2225,65 @@ bool tc_supported(cdl_ctx* ctx) {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
+// kind::f16 instruction descriptor for the CTA-pair MMA (M = 256)
+uint32_t make_idesc_m256(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+// Clusters of two that can be resident at once (0: cluster launch unavailable).
+int pair_clusters(cdl_ctx* ctx) {
+  static int max_clusters = -1;
+  if (max_clusters < 0) {
+    if (cudaFuncSetAttribute(k_tc_sq2, cudaFuncAttributeMaxDynamicSharedMemorySize, S2_SMEM_BYTES) != cudaSuccess) {
+      cudaGetLastError();
+      max_clusters = 0;
+      return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (ctx->sm_count / 2), 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = S2_SMEM_BYTES;
+    int mc = 0;
+    if (cudaOccupancyMaxActiveClusters(&mc, k_tc_sq2, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      mc = 0;
+    }
+    max_clusters = std::max(mc, 0);
+  }
+  return max_clusters;
+}
+
+// bf16 squaring of a level on CTA pairs (k_tc_sq2)
+int square_pairs(cdl_ctx* ctx, const void* in, void* out, int np, double flops, int clusters_max) {
+  const int nb = np / 256;
+  const uint32_t* tiles;
+  int count;
+  CDL_TRY(get_tiles(ctx, "tc.sq2." + std::to_string(nb), [&] { return square_pair_tiles(nb); }, &tiles, &count));
+  CUtensorMap ml;
+  CDL_TRY(make_map(&ml, in, np, np, 128));
+  Sq2Params p{};
+  p.tiles = tiles;
+  p.num_tiles = count;
+  p.kblocks = np / BK;
+  p.npad = np;
+  p.idesc = make_idesc_m256(256);
+  p.out = static_cast<__nv_bfloat16*>(out);
+  p.status = ctx->dev_status;
+  p.debug_withhold_load = ctx->debug_flags & 1;
+  const int clusters = std::min(count, clusters_max);
+  if (p.kblocks >= PACE_MIN_KBLOCKS) {
+    const int steps_per_tile = (p.kblocks + PACE_KB - 1) / PACE_KB;
+    p.pace_steps = ((count + clusters - 1) / clusters) * steps_per_tile;
+    void* pb;
+    CDL_TRY(ws_get(ctx, "tc.pace", (size_t)p.pace_steps * sizeof(unsigned), &pb));
+    CDL_CUDA_TRY(cudaMemsetAsync(pb, 0, (size_t)p.pace_steps * sizeof(unsigned), ctx->stream));
+    p.pace = static_cast<unsigned*>(pb);
+  }
+  Launch L(ctx, CDL_KC_SQUARE, flops);
+  k_tc_sq2<<<2 * clusters, THREADS, S2_SMEM_BYTES, ctx->stream>>>(ml, p);
+  return L.done();
+}
+
 int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
   const int np = (int)ch->npad;
   const int nb = np / 256;
@@ -1941,6 +2298,11 @@ int chain_square_tc(cdl_ctx* ctx, cdl_chain* ch, int level) {
     in = ooc_read(ctx, ch, level);
     out = ooc_write_begin(ctx, ch, level + 1);
     if (!in) return CDL_ERR_CUDA;
+  }
+  const int clusters = fp8 ? 0 : pair_clusters(ctx);
+  if (clusters > 0) {   // bf16: CTA pairs
+    CDL_TRY(square_pairs(ctx, in, out, np, (double)ch->n * ch->n * (ch->n + 1.0), clusters));
+    return ch->host_levels ? ooc_write_end(ctx, ch, level + 1) : CDL_OK;
   }
   CUtensorMap ma, mb;
   CDL_TRY(make_map(&ma, in, np, np, 128, elem));
