@@ -579,8 +579,9 @@ int cdl_caddelag_batched(cdl_ctx* ctx, int32_t G, const int64_t* n, int32_t T, c
  * timings and the refinement slots recorded in the CUDA graph. The tuner
  * runs once per plan, on the first call, over the batch's own data: each
  * squaring variant (128 x 128 tiles for graphs up to an order, 128 x 256
- * above) squares level 0 of every graph, each projection variant (node rows
- * per block) projects every graph; the fastest of each is kept. */
+ * above; max_npad_128 = -1: 256 x 256 blocks on CTA pairs for every graph)
+ * squares level 0 of every graph, each projection variant (node rows per
+ * block) projects every graph; the fastest of each is kept. */
 typedef struct {
   int32_t ready;                        /* 1 once a batched call built a plan  */
   int32_t square_max_npad_128;          /* chosen squaring variant             */

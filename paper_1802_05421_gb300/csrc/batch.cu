@@ -52,7 +52,7 @@ struct BatchPlan {
   double cinit_bytes = 0;
   // autotuned variants: squaring tile width per graph size, projection rows per block
   struct SqVariant {
-    int max_npad_128;            // graphs up to this order use 128 x 128 tiles
+    int max_npad_128;            // graphs up to this order use 128 x 128 tiles; -1: CTA pairs (256 x 256)
     std::vector<TcGroup> first;  // host copy of entry 0 of each level's array
     TcGroup* groups = nullptr;   // device, (d - 1) x G2
     BTiles tiles;
@@ -189,6 +189,13 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   }
   std::vector<std::vector<uint32_t>> sq;
   for (auto& bn : sq_bn) sq.push_back(tc_grouped_square_tiles(npads, ns, bn));
+  if (pair_clusters(ctx) > 0) {   // and every graph on CTA pairs
+    sq_bn.push_back(std::vector<int>(G2, 128));
+    sq.push_back(pair_tiles_grouped(npads, ns));
+    BatchPlan::SqVariant v;
+    v.max_npad_128 = -1;
+    P->sqv.push_back(v);
+  }
   const std::vector<uint32_t> ap = tc_grouped_apply_tiles(npads);
   int res_tm, res_tn;
   batch_residual_tile(k, &res_tm, &res_tn);
@@ -543,6 +550,13 @@ int score_batch(BatchPlan* P) {
 // The whole batch on the plan's private context. fixed_slots > 0 issues that
 // many refinement slots with no host synchronisation (the form recorded as a
 // CUDA graph); 0 runs them adaptively.
+// Level l -> l + 1 of every graph in one launch of a squaring variant.
+int square_variant(cdl_ctx* c, const BatchPlan::SqVariant& sv, int l, int G2, double flops) {
+  if (sv.max_npad_128 < 0)
+    return tc_square_grouped_pairs(c, &sv.first[l], sv.groups + (size_t)l * G2, sv.tiles.p, sv.tiles.count, flops);
+  return tc_square_grouped(c, &sv.first[l], sv.groups + (size_t)l * G2, sv.tiles.p, sv.tiles.count, flops);
+}
+
 int run_batch(BatchPlan* P, int fixed_slots) {
   cdl_ctx* c = P->inner;
   const int G2 = 2 * P->G;
@@ -550,7 +564,7 @@ int run_batch(BatchPlan* P, int fixed_slots) {
   CDL_TRY(chain_init_grouped(c, P->cgs, P->cvec, P->csplit, P->cinit, P->cinit_bytes));
   const BatchPlan::SqVariant& sv = P->sqv[P->sq_choice];
   for (int l = 0; l + 1 < P->d; ++l)
-    CDL_TRY(tc_square_grouped(c, &sv.first[l], sv.groups + (size_t)l * G2, sv.tiles.p, sv.tiles.count, P->sq_flops));
+    CDL_TRY(square_variant(c, sv, l, G2, P->sq_flops));
   const BatchPlan::ProjVariant& pvar = P->pv[P->pv_choice];
   CDL_TRY(project_grouped(c, P->pgs, G2, pvar.blocks, pvar.rpb, P->k, P->seed, P->bs.cs, P->bs.elem,
                           P->proj_adds));
@@ -597,8 +611,7 @@ int autotune(BatchPlan* P) {
   if (P->d > 1)
     for (size_t v = 0; v < P->sqv.size() && st == CDL_OK; ++v) {
       BatchPlan::SqVariant& sv = P->sqv[v];
-      st = time_it([&] { return tc_square_grouped(c, &sv.first[0], sv.groups, sv.tiles.p, sv.tiles.count, 0.0); },
-                   &sv.ms);
+      st = time_it([&] { return square_variant(c, sv, 0, G2, 0.0); }, &sv.ms);
     }
   for (size_t v = 0; v < P->pv.size() && st == CDL_OK; ++v) {
     BatchPlan::ProjVariant& pvar = P->pv[v];

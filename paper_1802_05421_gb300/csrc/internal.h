@@ -262,6 +262,13 @@ std::vector<uint32_t> tc_grouped_square_tiles(const std::vector<int>& npad, cons
 std::vector<uint32_t> tc_grouped_apply_tiles(const std::vector<int>& npad);
 int tc_square_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
                       int ntiles, double flops);
+// The same squarings on CTA pairs (256 x 256 blocks, tcgen05.mma.cta_group::2);
+// uses each group's mapA (128-row boxes), out, npad and kblocks.
+std::vector<uint32_t> pair_tiles_grouped(const std::vector<int>& npad, const std::vector<int>& n);
+int tc_square_grouped_pairs(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups,
+                            const uint32_t* dtiles, int ntiles, double flops);
+// Clusters of two the CTA-pair squaring can keep resident (0: unavailable).
+int pair_clusters(cdl_ctx* ctx);
 int tc_apply_grouped(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups, const uint32_t* dtiles,
                      int ntiles, int kp, int gate_mask, int kc, double work);
 int apply_tc(cdl_ctx* ctx, const cdl_chain* ch, int level, const void* xop, float* partial,

@@ -1459,10 +1459,12 @@ constexpr int S2_SMEM_BYTES = S2_STAGES * S2_STAGE + 256 + 1024;
 constexpr int S2_TMEM_COLS = 512;
 
 struct Sq2Params {
-  const uint32_t* tiles;   // upper-triangle 256-blocks: I (bits 0-14), J (bits 15-29)
+  const uint32_t* tiles;   // upper-triangle 256-blocks: I (bits 0-14), J (bits 15-29); grouped: graph
+                           // (bits 0-15), I (16-22), J (23-29)
   int num_tiles;
   int kblocks;
   int npad;
+  const TcGroup* groups;   // grouped launch: each graph's level map (mapA), output, order, k loop
   uint32_t idesc;          // kind::f16, bf16 x bf16 -> f32, M = 256, N = 256
   __nv_bfloat16* out;
   unsigned* status;
@@ -1470,6 +1472,33 @@ struct Sq2Params {
   int pace_steps;
   int debug_withhold_load;   // test hook: the rank-0 CTA never issues its first A load
 };
+
+// One pair tile: its blocks, the level's map, k loop, output and order.
+struct Sq2Tile {
+  int I, J, kblocks, npad;
+  const CUtensorMap* map;
+  __nv_bfloat16* out;
+};
+__device__ __forceinline__ Sq2Tile sq2_tile(const Sq2Params& p, const CUtensorMap* tm, uint32_t td) {
+  Sq2Tile q;
+  if (p.groups) {
+    const TcGroup& g = p.groups[td & 0xFFFF];
+    q.I = (td >> 16) & 0x7F;
+    q.J = (td >> 23) & 0x7F;
+    q.kblocks = g.kblocks;
+    q.npad = g.npad;
+    q.map = &g.mapA;
+    q.out = static_cast<__nv_bfloat16*>(g.out);
+  } else {
+    q.I = td & 0x7FFF;
+    q.J = (td >> 15) & 0x7FFF;
+    q.kblocks = p.kblocks;
+    q.npad = p.npad;
+    q.map = tm;
+    q.out = p.out;
+  }
+  return q;
+}
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -1594,10 +1623,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     const int steps_per_tile = (p.kblocks + PACE_KB - 1) / PACE_KB;
     int lt = 0;
     for (int t = cid; t < p.num_tiles && ok; t += ncl) {
-      const uint32_t td = p.tiles[t];
-      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF;
-      const int a_row = I * 256 + (int)rank * 128, b_row = J * 256 + (int)rank * 128;
-      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+      const Sq2Tile q = sq2_tile(p, &tmL, p.tiles[t]);
+      if (p.groups)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(q.map))
+                     : "memory");
+      // grouped: a 256-block may end past the padded order (a multiple of
+      // 128); those rows come back as the map's zero fill
+      const int a_row = q.I * 256 + (int)rank * 128, b_row = q.J * 256 + (int)rank * 128;
+      for (int kb = 0; kb < q.kblocks; ++kb, ++it) {
         if (p.pace && kb % PACE_KB == 0) {
           const int step = lt * steps_per_tile + kb / PACE_KB;
           if (step < p.pace_steps) atomicAdd(p.pace + step, 1u);
@@ -1624,8 +1657,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         if (rank == 0) mbar_expect_tx(full_bar(s), 2 * S2_STAGE);   // both CTAs' copies
         const uint32_t dst = smem_u32(smem + s * S2_STAGE);
         const uint32_t fb = lead_bar0 + 8u * s;
-        if (!(p.debug_withhold_load && it == 0 && rank == 0)) tma_load_2d_pair(dst, &tmL, kb * BK, a_row, fb);
-        tma_load_2d_pair(dst + S2_HALF, &tmL, kb * BK, b_row, fb);
+        if (!(p.debug_withhold_load && it == 0 && rank == 0)) tma_load_2d_pair(dst, q.map, kb * BK, a_row, fb);
+        tma_load_2d_pair(dst + S2_HALF, q.map, kb * BK, b_row, fb);
       }
       ++lt;
     }
@@ -1655,7 +1688,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
-      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+      const int kblocks = p.groups ? p.groups[p.tiles[t] & 0xFFFF].kblocks : p.kblocks;
+      for (int kb = 0; kb < kblocks; ++kb, ++it) {
         const int s = it % S2_STAGES;
         const uint32_t r = (uint32_t)(it / S2_STAGES);
         if (!mbar_wait(full_bar(s), r & 1, abort_flag, p.status)) {
@@ -1693,14 +1727,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       ++tc;
       if (!mbar_wait(tfull_bar(acc), ar & 1, abort_flag, p.status)) break;
       tc_fence_after();
-      const uint32_t td = p.tiles[t];
-      const int I = td & 0x7FFF, J = (td >> 15) & 0x7FFF;
-      const int r = I * 256 + (int)rank * 128 + row_in_tile;
+      const Sq2Tile tq = sq2_tile(p, &tmL, p.tiles[t]);
+      const int r = tq.I * 256 + (int)rank * 128 + row_in_tile;
       const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
       for (int c = 0; c < 8; ++c) {
         float v[32];
-        tmem_ld32(taddr + (uint32_t)(c * 32), v);
-        square_store32(p.out, p.npad, r, J * 256 + c * 32, I == J, v);
+        tmem_ld32(taddr + (uint32_t)(c * 32), v);   // every warp loads (.sync.aligned), in range or not
+        const int col0 = tq.J * 256 + c * 32;
+        if (r < tq.npad && col0 < tq.npad) square_store32(tq.out, tq.npad, r, col0, tq.I == tq.J, v);
       }
       tc_fence_before();
       __syncwarp();
@@ -2225,6 +2259,21 @@ bool tc_supported(cdl_ctx* ctx) {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
+// Grouped CTA-pair squaring: the 256-blocks holding rows of each graph
+// (largest graphs first), as graph | I << 16 | J << 23.
+std::vector<uint32_t> pair_tiles_grouped(const std::vector<int>& npad, const std::vector<int>& n) {
+  std::vector<int> order(npad.size());
+  for (size_t g = 0; g < order.size(); ++g) order[g] = (int)g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return npad[a] > npad[b]; });
+  std::vector<uint32_t> v;
+  for (int g : order) {
+    const int nb = (n[g] + 255) / 256;
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J) v.push_back((uint32_t)g | ((uint32_t)I << 16) | ((uint32_t)J << 23));
+  }
+  return v;
+}
+
 // kind::f16 instruction descriptor for the CTA-pair MMA (M = 256)
 uint32_t make_idesc_m256(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
@@ -2281,6 +2330,23 @@ int square_pairs(cdl_ctx* ctx, const void* in, void* out, int np, double flops, 
   }
   Launch L(ctx, CDL_KC_SQUARE, flops);
   k_tc_sq2<<<2 * clusters, THREADS, S2_SMEM_BYTES, ctx->stream>>>(ml, p);
+  return L.done();
+}
+
+int tc_square_grouped_pairs(cdl_ctx* ctx, const TcGroup* host_first, const TcGroup* dgroups,
+                            const uint32_t* dtiles, int ntiles, double flops) {
+  const int mc = pair_clusters(ctx);
+  if (mc < 1) return CDL_ERR_UNSUPPORTED;
+  Sq2Params p{};
+  p.tiles = dtiles;
+  p.num_tiles = ntiles;
+  p.groups = dgroups;
+  p.idesc = make_idesc_m256(256);
+  p.status = ctx->dev_status;
+  const int clusters = std::min(ntiles, mc);
+  Launch L(ctx, CDL_KC_SQUARE, flops);
+  // the kernel-parameter map is unused in grouped mode: pass the first graph's
+  k_tc_sq2<<<2 * clusters, THREADS, S2_SMEM_BYTES, ctx->stream>>>(host_first->mapA, p);
   return L.done();
 }
 
