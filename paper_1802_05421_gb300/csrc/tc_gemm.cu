@@ -1457,6 +1457,8 @@ constexpr int S2_STAGE = 2 * S2_HALF;                  // A half + B half
 constexpr int S2_NBARS = 2 * S2_STAGES + 5;            // full, empty, tfull x2, tempty x2, drain
 constexpr int S2_SMEM_BYTES = S2_STAGES * S2_STAGE + 256 + 1024;
 constexpr int S2_TMEM_COLS = 512;
+constexpr int S2_THREADS = 320;                        // producer, MMA issuer, 8 epilogue warps
+constexpr int S2_PACE_MIN_KBLOCKS = 512;               // K pacing from n = 32768 on
 
 struct Sq2Params {
   const uint32_t* tiles;   // upper-triangle 256-blocks: I (bits 0-14), J (bits 15-29); grouped: graph
@@ -1572,7 +1574,7 @@ __device__ __forceinline__ void square_store32(__nv_bfloat16* C, int npad, int r
   }
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
     k_tc_sq2(const __grid_constant__ CUtensorMap tmL, const Sq2Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1597,7 +1599,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 8);   // the four epilogue warps of each CTA
+      mbar_init(tempty_bar(a), 16);   // the eight epilogue warps of each CTA
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -1717,8 +1719,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp >= 2) {
-    // ------------------------------------------------ epilogue (both CTAs: 128 rows each)
+    // ------------------------------------------------ epilogue (both CTAs: 128 rows each; two
+    // warps per TMEM lane quarter, 128 columns each)
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row_in_tile = q * 32 + lane;
     int tc = 0;
     for (int t = cid; t < p.num_tiles; t += ncl) {
@@ -1730,7 +1734,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       const Sq2Tile tq = sq2_tile(p, &tmL, p.tiles[t]);
       const int r = tq.I * 256 + (int)rank * 128 + row_in_tile;
       const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
-      for (int c = 0; c < 8; ++c) {
+      for (int c = half * 4; c < half * 4 + 4; ++c) {
         float v[32];
         tmem_ld32(taddr + (uint32_t)(c * 32), v);   // every warp loads (.sync.aligned), in range or not
         const int col0 = tq.J * 256 + c * 32;
@@ -2290,7 +2294,7 @@ int pair_clusters(cdl_ctx* ctx) {
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * (ctx->sm_count / 2), 1, 1);
-    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.blockDim = dim3(S2_THREADS, 1, 1);
     cfg.dynamicSmemBytes = S2_SMEM_BYTES;
     int mc = 0;
     if (cudaOccupancyMaxActiveClusters(&mc, k_tc_sq2, &cfg) != cudaSuccess) {
@@ -2320,7 +2324,7 @@ int square_pairs(cdl_ctx* ctx, const void* in, void* out, int np, double flops, 
   p.status = ctx->dev_status;
   p.debug_withhold_load = ctx->debug_flags & 1;
   const int clusters = std::min(count, clusters_max);
-  if (p.kblocks >= PACE_MIN_KBLOCKS) {
+  if (p.kblocks >= S2_PACE_MIN_KBLOCKS) {
     const int steps_per_tile = (p.kblocks + PACE_KB - 1) / PACE_KB;
     p.pace_steps = ((count + clusters - 1) / clusters) * steps_per_tile;
     void* pb;
@@ -2329,7 +2333,7 @@ int square_pairs(cdl_ctx* ctx, const void* in, void* out, int np, double flops, 
     p.pace = static_cast<unsigned*>(pb);
   }
   Launch L(ctx, CDL_KC_SQUARE, flops);
-  k_tc_sq2<<<2 * clusters, THREADS, S2_SMEM_BYTES, ctx->stream>>>(ml, p);
+  k_tc_sq2<<<2 * clusters, S2_THREADS, S2_SMEM_BYTES, ctx->stream>>>(ml, p);
   return L.done();
 }
 
@@ -2346,7 +2350,7 @@ int tc_square_grouped_pairs(cdl_ctx* ctx, const TcGroup* host_first, const TcGro
   const int clusters = std::min(ntiles, mc);
   Launch L(ctx, CDL_KC_SQUARE, flops);
   // the kernel-parameter map is unused in grouped mode: pass the first graph's
-  k_tc_sq2<<<2 * clusters, THREADS, S2_SMEM_BYTES, ctx->stream>>>(host_first->mapA, p);
+  k_tc_sq2<<<2 * clusters, S2_THREADS, S2_SMEM_BYTES, ctx->stream>>>(host_first->mapA, p);
   return L.done();
 }
 
