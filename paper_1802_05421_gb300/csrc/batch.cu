@@ -48,7 +48,7 @@ struct BatchPlan {
   const PGraph* pgs = nullptr;
   // level 0 of every graph in three grouped launches
   const CGraph* cgs = nullptr;
-  BTiles cvec, csplit, cinit;
+  BTiles cvec, cinit;
   double cinit_bytes = 0;
   // autotuned variants: squaring tile width per graph size, projection rows per block
   struct SqVariant {
@@ -168,7 +168,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   BState* d_st = nullptr;
   uint32_t* d_tiles = nullptr;
   // tile tables (host)
-  std::vector<uint32_t> t32, elem, res, csb, sel, spairs, snodes;
+  std::vector<uint32_t> t32, elem, csb, sel, spairs, snodes;
   std::vector<int> npads(G2), ns(G2);
   for (int g = 0; g < G2; ++g) {
     npads[g] = gnp(g);
@@ -197,20 +197,17 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     P->sqv.push_back(v);
   }
   const std::vector<uint32_t> ap = tc_grouped_apply_tiles(npads);
-  int res_tm, res_tn;
-  batch_residual_tile(k, &res_tm, &res_tn);
-  const int ncb = (k + res_tn - 1) / res_tn;
-  std::vector<uint32_t> cvec, csplit, cinit;
+  const int kg = (int)round_up(k, 32);   // Z slice rows of the exact residual
+  std::vector<uint32_t> cvec, cinit, zst, runits;
   for (int g : P->order) {
     const int nn = gn(g), np = gnp(g);
     for (int b = 0; b < (np + 255) / 256; ++b) cvec.push_back(((uint32_t)b << 12) | (uint32_t)g);
-    for (size_t b = 0; b * 2048 < (size_t)nn * nn; ++b) csplit.push_back(((uint32_t)b << 12) | (uint32_t)g);
     for (size_t b = 0; b * 2048 < (size_t)np * (np / 8); ++b) cinit.push_back(((uint32_t)b << 12) | (uint32_t)g);
     for (int b = 0; b < np / 32; ++b) t32.push_back(((uint32_t)b << 12) | (uint32_t)g);
     const int eb = (int)(((size_t)nn * k + 255) / 256);
     for (int b = 0; b < eb; ++b) elem.push_back(((uint32_t)b << 12) | (uint32_t)g);
-    const int rt = ((nn + res_tm - 1) / res_tm) * ncb;
-    for (int b = 0; b < rt; ++b) res.push_back(((uint32_t)b << 12) | (uint32_t)g);
+    for (size_t b = 0; b * 256 < (size_t)kg * np; ++b) zst.push_back(((uint32_t)b << 12) | (uint32_t)g);
+    for (int t = 0; t < np / 128; ++t) runits.push_back((uint32_t)g | ((uint32_t)t << 16));
     for (int b = 0; b < (nn + 255) / 256; ++b) csb.push_back(((uint32_t)b << 12) | (uint32_t)g);
   }
   std::vector<int> porder(G);
@@ -241,8 +238,8 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     pvar.rpb = rpb;
     P->pv.push_back(pvar);
   }
-  size_t ntiles = ap.size() + t32.size() + elem.size() + res.size() + csb.size() + sel.size() + spairs.size() +
-                  snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size() + cvec.size() + csplit.size() +
+  size_t ntiles = ap.size() + t32.size() + elem.size() + zst.size() + runits.size() + csb.size() + sel.size() +
+                  spairs.size() + snodes.size() + gt.fixed.size() + gt.dist.size() + gt.rows.size() + cvec.size() +
                   cinit.size();
   for (auto& v : sq) ntiles += v.size();
   for (auto& v : pblocks) ntiles += v.size();
@@ -254,6 +251,8 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   CGraph* d_cgs = nullptr;
   int4* d_sel = nullptr;
   char* sel_all = nullptr;
+  ResidGroup* d_rgroups = nullptr;
+  unsigned long long* zmax_all = nullptr;
   const size_t sel_one = graph_select_bytes();
 
   for (int pass = 0; pass < 2; ++pass) {
@@ -276,6 +275,8 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     d_cgs = c.take<CGraph>(G2);
     d_sel = c.take<int4>(gt.sel.size());
     sel_all = c.take<char>(G2 * sel_one);
+    d_rgroups = c.take<ResidGroup>(G2);
+    zmax_all = c.take<unsigned long long>((size_t)G2 * k);
     for (int g = 0; g < G2; ++g) {
       const int nn = gn(g), np = gnp(g);
       const size_t nk = (size_t)nn * k;
@@ -288,7 +289,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
       P->Y[g] = c.take<double>(nk);
       ch.levels = c.take<uint16_t>((size_t)d * np * np);
       ch.aop = c.take<uint16_t>((size_t)2 * np * np);
-      ch.ahl = c.take<float>((size_t)2 * nn * nn);
+      cgs[g].aslices = c.take<uint16_t>((size_t)6 * np * np);
       ch.rsqrt_d = c.take<double>(np);
       cgs[g].u = c.take<double>(np);
       cgs[g].rsf = c.take<float>(np);
@@ -301,11 +302,14 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
       B.part2 = c.take<float>((size_t)np * 2 * kp);
       B.dz = c.take<float>((size_t)np * kp);
       B.dzop = c.take<uint16_t>((size_t)2 * kp * np);
-      B.zh = c.take<float>(nk);
-      B.zl = c.take<float>(nk);
-      B.res_tiles = ((nn + res_tm - 1) / res_tm) * ncb;
+      B.kg = kg;
+      B.zmax = zmax_all ? zmax_all + (size_t)g * k : nullptr;
+      B.zc = c.take<double>(k);
+      B.zs = c.take<uint16_t>((size_t)6 * kg * np);
+      B.Gp = c.take<double>((size_t)RESID_PAIRS * np * kg);
       B.elem_blocks = (int)((nk + 255) / 256);
-      B.red = c.take<double>(std::max(B.res_tiles, B.elem_blocks));
+      B.res_tiles = B.elem_blocks;   // the full residual leaves one partial sum per element block
+      B.red = c.take<double>(B.elem_blocks);
       B.cs = c.take<double>((size_t)((nn + 255) / 256) * k);
     }
     for (int p = 0; p < G; ++p) {
@@ -361,8 +365,6 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     B.D = ch.D;
     B.rsd = ch.rsqrt_d;
     B.vol = ch.vol;
-    B.ahi = ch.ahl;
-    B.alo = ch.ahl + (size_t)nn * nn;
     B.Y = P->Y[g];
     GGraph& Gg = ggs[g];
     const int p = g / 2;
@@ -379,12 +381,11 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     Cg.D = ch.D;
     Cg.vol = ch.vol;
     Cg.rsd = ch.rsqrt_d;
-    Cg.ahl = ch.ahl;
     Cg.L0 = ch.level(0);
     Cg.aop = ch.aop;
     Cg.n = nn;
     Cg.npad = np;
-    P->cinit_bytes += 8.0 * nn * (double)nn + 6.0 * np * (double)np;
+    P->cinit_bytes += 8.0 * nn * (double)nn + 18.0 * np * (double)np;   // A read; level 0, A hi/lo, 6 slices
     PGraph& Pg = pgs[g];
     Pg.A = P->A[g];
     Pg.Y = P->Y[g];
@@ -397,6 +398,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   {
     std::vector<std::vector<TcGroup>> sqg(P->sqv.size(), std::vector<TcGroup>(n_sq_groups));
     std::vector<TcGroup> lvg(n_lvl_groups), rsg(2 * G2);
+    std::vector<ResidGroup> rg(G2);
     for (int g = 0; g < G2; ++g) {
       const cdl_chain& ch = P->chains[g];
       const int np = (int)ch.npad;
@@ -410,6 +412,9 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
         if ((st = tc_group_apply(&lvg[(size_t)l * G2 + g], ch.level(l), gs[g].xop, gs[g].part, np, kp, gate)) !=
             CDL_OK)
           return fail(st);
+      if ((st = resid_group_init(&rg[g], cgs[g].aslices, gs[g].zs, const_cast<double*>(gs[g].Gp), np, kg, gate)) !=
+          CDL_OK)
+        return fail(st);
       const uint16_t* aop = static_cast<const uint16_t*>(ch.aop);
       if ((st = tc_group_apply(&rsg[g], aop, gs[g].dzop, gs[g].part, np, kp, gate)) != CDL_OK ||
           (st = tc_group_apply(&rsg[G2 + g], aop + (size_t)np * np, gs[g].dzop, gs[g].part2, np, kp, gate)) !=
@@ -425,7 +430,7 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
     P->res_first[0] = rsg[0];
     P->res_first[1] = rsg[G2];
     if ((st = upload(P->stream, lvl_groups, lvg)) != CDL_OK ||
-        (st = upload(P->stream, res_groups, rsg)) != CDL_OK)
+        (st = upload(P->stream, res_groups, rsg)) != CDL_OK || (st = upload(P->stream, d_rgroups, rg)) != CDL_OK)
       return fail(st);
     // the host vectors are read by the copies above: finish them before they go
     if (cudaStreamSynchronize(P->stream) != cudaSuccess) return fail(CDL_ERR_CUDA);
@@ -459,7 +464,8 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   add(ap, bs.apply);
   add(t32, bs.t32);
   add(elem, bs.elem);
-  add(res, bs.res);
+  add(zst, bs.zst);
+  add(runits, bs.runits);
   add(csb, bs.cs);
   add(sel, P->score_elem);
   add(spairs, P->score_pairs);
@@ -470,7 +476,6 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   add(gt.rows, gb.rows);
   for (size_t v = 0; v < pblocks.size(); ++v) add(pblocks[v], P->pv[v].blocks);
   add(cvec, P->cvec);
-  add(csplit, P->csplit);
   add(cinit, P->cinit);
   // before tuning: 128 x 128 tiles up to order 1024, the widest projection blocks
   P->sq_choice = std::min<int>(1, (int)P->sqv.size() - 1);
@@ -514,9 +519,14 @@ int build_plan(cdl_ctx* ctx, int G, const int64_t* n, int T, const cdl_batch_opt
   bs.lvl_first = P->lvl_first.data();
   bs.res_groups = res_groups;
   bs.res_first = P->res_first.data();
+  bs.rgroups = d_rgroups;
+  bs.zmax_all = zmax_all;
+  bs.zmax_bytes = (size_t)G2 * k * sizeof(unsigned long long);
+  bs.kg = kg;
   for (int g = 0; g < G2; ++g) {
     const double np = gnp(g);
     bs.apply_bytes += 2.0 * np * np;
+    bs.resid_work += 2.0 * RESID_PAIRS * np * np * kg;
     P->sq_flops += (double)gn(g) * gn(g) * (gn(g) + 1.0);
   }
   for (int p = 0; p < G; ++p) P->score_bytes += 8.0 * (double)n[p] * (n[p] - 1);
@@ -561,7 +571,7 @@ int run_batch(BatchPlan* P, int fixed_slots) {
   cdl_ctx* c = P->inner;
   const int G2 = 2 * P->G;
   CDL_TRY(graph_build_grouped(c, P->gb));
-  CDL_TRY(chain_init_grouped(c, P->cgs, P->cvec, P->csplit, P->cinit, P->cinit_bytes));
+  CDL_TRY(chain_init_grouped(c, P->cgs, P->cvec, P->cinit, P->cinit_bytes));
   const BatchPlan::SqVariant& sv = P->sqv[P->sq_choice];
   for (int l = 0; l + 1 < P->d; ++l)
     CDL_TRY(square_variant(c, sv, l, G2, P->sq_flops));

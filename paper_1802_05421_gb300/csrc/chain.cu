@@ -517,18 +517,6 @@ __global__ void __launch_bounds__(256) k_g_chain_vectors(const uint32_t* __restr
   if (i < G.npad) chain_vector(G.D, G.vol, G.n, G.rsd, G.u, G.rsf, G.uf, i);
 }
 
-__global__ void __launch_bounds__(256) k_g_split_a(const uint32_t* __restrict__ tiles, const CGraph* __restrict__ cg) {
-  const uint32_t t = tiles[blockIdx.x];
-  const CGraph& G = cg[t & 0xFFFu];
-  const size_t cnt = (size_t)G.n * G.n;
-  const size_t e1 = min(cnt, ((size_t)(t >> 12) + 1) * 2048);
-  for (size_t i = (size_t)(t >> 12) * 2048 + threadIdx.x; i < e1; i += 256) {
-    const ff v = split_nonneg(G.A[i]);
-    G.ahl[i] = v.hi;
-    G.ahl[cnt + i] = v.lo;
-  }
-}
-
 __global__ void __launch_bounds__(256) k_g_chain_init(const uint32_t* __restrict__ tiles, const CGraph* __restrict__ cg) {
   const uint32_t t = tiles[blockIdx.x];
   const CGraph& G = cg[t & 0xFFFu];
@@ -537,8 +525,9 @@ __global__ void __launch_bounds__(256) k_g_chain_init(const uint32_t* __restrict
   __nv_bfloat16* L0 = static_cast<__nv_bfloat16*>(G.L0);
   __nv_bfloat16* ahi = static_cast<__nv_bfloat16*>(G.aop);
   __nv_bfloat16* alo = ahi + (size_t)G.npad * G.npad;
+  // the exact slices of A on the grids 2^-8s (kernel weights are at most 1: scale 2^0)
   for (size_t g = (size_t)(t >> 12) * 2048 + threadIdx.x; g < g1; g += 256)
-    chain_init_tc_group<false>(G.A, G.n, G.npad, G.rsf, G.uf, L0, ahi, alo, nullptr, 0, g);
+    chain_init_tc_group<true>(G.A, G.n, G.npad, G.rsf, G.uf, L0, ahi, alo, G.aslices, 0, g);
 }
 }  // namespace
 
@@ -763,15 +752,10 @@ int panel_slices_t(cdl_ctx* ctx, const double* panel, int n, int np, int r0, int
 }
 
 
-int chain_init_grouped(cdl_ctx* ctx, const CGraph* cg, BTiles vec, BTiles split, BTiles init, double bytes) {
+int chain_init_grouped(cdl_ctx* ctx, const CGraph* cg, BTiles vec, BTiles init, double bytes) {
   {
     Launch L(ctx, CDL_KC_MISC, 0);
     k_g_chain_vectors<<<vec.count, 256, 0, ctx->stream>>>(vec.p, cg);
-    CDL_TRY(L.done());
-  }
-  {
-    Launch L(ctx, CDL_KC_CHAIN_INIT, 0);
-    k_g_split_a<<<split.count, 256, 0, ctx->stream>>>(split.p, cg);
     CDL_TRY(L.done());
   }
   Launch L(ctx, CDL_KC_CHAIN_INIT, bytes);

@@ -223,6 +223,26 @@ constexpr int RESID_PAIRS = 21;
 // zslices: 6 planes kp x npad) into G: RESID_PAIRS float64 planes npad x kp,
 // one per slice pair; A Z = the sum of the planes in order.
 int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, double* G);
+// The same product for many graphs in one launch (batched form): each graph's
+// A slice planes (6 x npad x npad, npad a multiple of 128), Z slice planes
+// (6 x kg x npad) and RESID_PAIRS output planes (npad x kg, assigned, not
+// added: no zeroing needed) sit in a device array of ResidGroup; units lists
+// graph | row tile << 16 for every 128-row tile of every graph; a graph's
+// units run iff *gate & gate_mask.
+struct ResidGroup {
+  CUtensorMap a[6];    // A slice planes, 128-row boxes
+  CUtensorMap b[6];    // Z slice planes (transposed, kg x npad), kg-row boxes
+  double* G;
+  size_t gstride;      // npad x kg
+  const int* gate;
+  int kblocks;         // npad rounded up to 256, in 64-wide k-blocks (zero fill past npad)
+  int pad[9];
+};
+static_assert(sizeof(ResidGroup) % 64 == 0, "ResidGroup keeps its tensor maps 64-byte aligned in arrays");
+int resid_group_init(ResidGroup* g, const void* aslices, const void* zslices, double* G, int npad, int kg,
+                     const int* gate);
+int resid_tc_grouped(cdl_ctx* ctx, const ResidGroup* dgroups, const uint32_t* units, int nunits, int kg,
+                     int gate_mask, double work);
 // Exact squared distances of grid inputs on the tensor cores: planes = three
 // bf16 digit planes (rows x tp each, rows = n rounded up to 128, tp = T
 // rounded up to 64, zero padded), norms = |a_i|^2 (rows, int64); writes the
@@ -337,15 +357,15 @@ struct CGraph {
   double* u;         // npad
   float* rsf;        // npad
   float* uf;         // npad
-  float* ahl;        // 2 n n: float hi, lo
+  uint16_t* aslices; // bf16 6 npad x npad: the exact slices of A (weights at most 1)
   void* L0;          // bf16 npad x npad
   void* aop;         // bf16 2 npad x npad: A_hi, A_lo
   int n, npad;
 };
-// Tile tables: vec (b << 12) | g over npad / 256 blocks; split and init
-// (b << 12) | g over 2048-element blocks of n^2 and 2048-group blocks of
-// npad^2 / 8.
-int chain_init_grouped(cdl_ctx* ctx, const CGraph* cg, BTiles vec, BTiles split, BTiles init, double bytes);
+// Tile tables: vec (b << 12) | g over npad / 256 blocks; init (b << 12) | g
+// over 2048-group blocks of npad^2 / 8 (level 0, A hi/lo and A's six exact
+// slices).
+int chain_init_grouped(cdl_ctx* ctx, const CGraph* cg, BTiles vec, BTiles init, double bytes);
 
 // Projection of one graph of a batch.
 struct PGraph {
@@ -367,13 +387,17 @@ enum { CMD_STEP = 1, CMD_FULL = 2, CMD_RECUR = 4 };
 // npad-padded operands as in the single-graph solve).
 struct BGraph {
   int n, np;
-  int res_tiles;    // 64 x 64 float-float residual tiles
+  int res_tiles;    // blocks whose partial sums a full residual leaves in red (= elem_blocks)
   int elem_blocks;  // 256-element blocks of n x k
+  int kg;           // Z slice rows (k rounded up to 32)
+  int pad0;
   const double* D;
   const double* rsd;
   const double* vol;
-  const float* ahi;
-  const float* alo;
+  unsigned long long* zmax;   // k: bits of max |Z| per column
+  double* zc;                 // k: the column scales (powers of two)
+  void* zs;                   // bf16 6 kg x npad: the exact slices of Z / c, transposed
+  const double* Gp;           // RESID_PAIRS planes npad x kg of A Z
   const double* Y;
   double* Z;
   double* R;
@@ -383,9 +407,7 @@ struct BGraph {
   float* part2;
   float* dz;        // npad x kp
   void* dzop;       // bf16 2kp x npad
-  float* zh;
-  float* zl;
-  double* red;      // max(res_tiles, elem_blocks)
+  double* red;      // elem_blocks
   double* cs;       // ceil(n / 256) x k
 };
 
@@ -407,7 +429,14 @@ struct BatchSolve {
   const BGraph* gs = nullptr;
   BState* st = nullptr;
   int* active = nullptr;                 // device: graphs still running after the last slot
-  BTiles t32, elem, res, cs, apply;
+  BTiles t32, elem, cs, apply;
+  BTiles zst;                            // (b << 12) | g over 256-element blocks of kg x npad
+  BTiles runits;                         // g | row tile << 16 over the 128-row tiles of every graph
+  const ResidGroup* rgroups = nullptr;   // device, G2
+  unsigned long long* zmax_all = nullptr;   // every graph's zmax, contiguous
+  size_t zmax_bytes = 0;
+  int kg = 0;
+  double resid_work = 0;                 // flops of one full exact residual of every graph
   const TcGroup* lvl_groups = nullptr;   // device, d arrays of G2 (level-major)
   const TcGroup* lvl_first = nullptr;    // host, entry 0 of each level array
   const TcGroup* res_groups = nullptr;   // device, A_hi then A_lo arrays of G2
@@ -419,7 +448,7 @@ int batch_solve_start(cdl_ctx* ctx, const BatchSolve& b);
 // One refinement slot (a step or a certification per graph that has not
 // stopped); *b.active counts the graphs still running after it.
 int batch_solve_slot(cdl_ctx* ctx, const BatchSolve& b);
-// Tile of the batched float-float residual for k right-hand sides.
+// Tile of the batched exact residual for k right-hand sides: 128 rows x kg.
 void batch_residual_tile(int k, int* tm, int* tn);
 
 // One pair of a batch for the grouped scoring launches.

@@ -699,32 +699,70 @@ __global__ void __launch_bounds__(256) k_b_center(const uint32_t* __restrict__ t
   G.Z[idx] -= s / *G.vol;
 }
 
-// Z -> float hi + lo for the float-float residual.
-__global__ void __launch_bounds__(256) k_b_split(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
-                                                  const BState* __restrict__ st, int k) {
+// Full residual of the graphs due one (the exact-slice form of the single
+// graph path, Sec. 5): max |Z| per column ...
+__global__ void __launch_bounds__(256) k_b_zcolmax(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                    const BState* __restrict__ st, int k) {
   int g, b;
   tdec(tiles[blockIdx.x], g, b);
   if (!(st[g].cmd & CMD_FULL)) return;
   const BGraph& G = gs[g];
   const size_t idx = (size_t)b * 256 + threadIdx.x;
   if (idx >= (size_t)G.n * k) return;
-  const double z = G.Z[idx];
-  const float h = (float)z;
-  G.zh[idx] = h;
-  G.zl[idx] = (float)(z - (double)h);
+  atomicMax(G.zmax + idx % k, (unsigned long long)__double_as_longlong(fabs(G.Z[idx])));
 }
 
-// Full float-float residual R = Y - D o Z + A Z, one TM x TN tile per block.
-template <int TM, int TN>
-__global__ void __launch_bounds__(256) k_b_residual(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
-                                                     const BState* __restrict__ st, int k) {
+// ... the six exact slices of Z / c, transposed (kg x npad), and c per column ...
+__global__ void __launch_bounds__(256) k_b_zslice(const uint32_t* __restrict__ tiles, const BGraph* __restrict__ gs,
+                                                   const BState* __restrict__ st, int k) {
   int g, b;
   tdec(tiles[blockIdx.x], g, b);
   if (!(st[g].cmd & CMD_FULL)) return;
   const BGraph& G = gs[g];
-  const int ncb = (k + TN - 1) / TN;
-  const double t = residual_tile<TM, TN>(G.ahi, G.alo, G.zh, G.zl, G.Z, G.Y, G.D, G.n, k, G.R, (b / ncb) * TM,
-                                         (b % ncb) * TN);
+  const size_t plane = (size_t)G.kg * G.np;
+  const size_t idx = (size_t)b * 256 + threadIdx.x;
+  if (idx >= plane) return;
+  const int r = (int)(idx / G.np), j = (int)(idx % G.np);
+  long long N = 0;
+  if (r < k) {
+    const double c = pow2_above(G.zmax[r]);
+    if (j == 0) G.zc[r] = c;
+    if (j < G.n) N = llrint(G.Z[(size_t)j * k + r] / c * 0x1p48);   // |Z / c| < 1; the division is exact
+  }
+  __nv_bfloat16* S = static_cast<__nv_bfloat16*>(G.zs);
+#pragma unroll
+  for (int t = 1; t <= 6; ++t) {
+    const int sh = 48 - 8 * t;
+    long long d = N;
+    if (sh > 0) d = (N + (1LL << (sh - 1))) >> sh;
+    N -= d << sh;
+    S[(size_t)(t - 1) * plane + idx] = __float2bfloat16_rn(ldexpf((float)d, -8 * t));
+  }
+}
+
+// ... and, after the slice products (resid_tc_grouped), R = Y - D o Z + c A Z
+// with A Z the sum of the RESID_PAIRS planes in pair order; per-block sums of
+// R^2 (the kernel graphs' slices carry scale 2^0).
+__global__ void __launch_bounds__(256) k_b_resid_combine(const uint32_t* __restrict__ tiles,
+                                                          const BGraph* __restrict__ gs,
+                                                          const BState* __restrict__ st, int k) {
+  int g, b;
+  tdec(tiles[blockIdx.x], g, b);
+  if (!(st[g].cmd & CMD_FULL)) return;
+  const BGraph& G = gs[g];
+  const size_t idx = (size_t)b * 256 + threadIdx.x;
+  double sq = 0.0;
+  if (idx < (size_t)G.n * k) {
+    const int i = (int)(idx / k), r = (int)(idx % k);
+    const size_t pl = (size_t)G.np * G.kg;
+    const double* Gg = G.Gp + (size_t)i * G.kg + r;
+    double sum = 0.0;
+    for (int pr = 0; pr < RESID_PAIRS; ++pr) sum += Gg[(size_t)pr * pl];   // the slice pairs in order
+    const double v = (G.Y[idx] - G.D[i] * G.Z[idx]) + G.zc[r] * sum;   // a power of two: exact
+    G.R[idx] = v;
+    sq = v * v;
+  }
+  const double t = block_sum256(sq);
   if (threadIdx.x == 0) G.red[b] = t;
 }
 
@@ -1305,8 +1343,8 @@ int chain_solve(cdl_ctx* ctx, const cdl_chain* ch, const double* A, const double
 }
 
 void batch_residual_tile(int k, int* tm, int* tn) {
-  *tm = k <= 32 ? 128 : 64;
-  *tn = k <= 32 ? 32 : 64;
+  *tm = 128;
+  *tn = (k + 31) / 32 * 32;
 }
 
 namespace {
@@ -1338,12 +1376,13 @@ int batch_solve_slot(cdl_ctx* ctx, const BatchSolve& B) {
   CDL_TRY(run_tiles(ctx, B, k_b_precond_out, B.t32, CDL_KC_MISC, 0.0, cst, B.k, B.kp));
   CDL_TRY(run_tiles(ctx, B, k_b_colsum, B.cs, CDL_KC_MISC, 0.0, cst, B.k));
   CDL_TRY(run_tiles(ctx, B, k_b_center, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
-  // full residual (first step, certification) or recursive update
-  CDL_TRY(run_tiles(ctx, B, k_b_split, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
-  if (B.k <= 32)
-    CDL_TRY(run_tiles(ctx, B, k_b_residual<128, 32>, B.res, CDL_KC_RESIDUAL, 0.0, cst, B.k));
-  else
-    CDL_TRY(run_tiles(ctx, B, k_b_residual<64, 64>, B.res, CDL_KC_RESIDUAL, 0.0, cst, B.k));
+  // full residual (first step, certification) on the tensor cores from exact
+  // slices, or the recursive update
+  CDL_CUDA_TRY(cudaMemsetAsync(B.zmax_all, 0, B.zmax_bytes, ctx->stream));
+  CDL_TRY(run_tiles(ctx, B, k_b_zcolmax, B.elem, CDL_KC_MISC, 0.0, cst, B.k));
+  CDL_TRY(run_tiles(ctx, B, k_b_zslice, B.zst, CDL_KC_MISC, 0.0, cst, B.k));
+  CDL_TRY(resid_tc_grouped(ctx, B.rgroups, B.runits.p, B.runits.count, B.kg, CMD_FULL, B.resid_work));
+  CDL_TRY(run_tiles(ctx, B, k_b_resid_combine, B.elem, CDL_KC_RESIDUAL, 0.0, cst, B.k));
   if (!B.always_full) {
     CDL_TRY(tc_apply_grouped(ctx, B.res_first, B.res_groups, B.apply.p, B.apply.count, B.kp, CMD_RECUR,
                              CDL_KC_RESIDUAL, 0.0));

@@ -624,7 +624,7 @@ struct ResidMaps {
 };
 
 struct ResidParams {
-  int num_tiles;   // npad / 128
+  int num_tiles;   // npad / 128 (grouped: entries of units)
   int kblocks;     // npad / 64
   int kp;          // MMA N (multiple of 32, <= 128)
   int npairs;
@@ -634,7 +634,48 @@ struct ResidParams {
   size_t gstride;
   uint32_t idesc;
   unsigned* status;
+  const ResidGroup* groups;   // grouped launch: per-graph maps, planes, k loop, gate (null otherwise)
+  const uint32_t* units;      // grouped: graph | row tile << 16
+  int gate_mask;
+  int assign;                 // the first flush of a unit stores instead of adding
 };
+
+// Unit u of a launch: its row tile, slice pair, operand maps, k loop and
+// output planes, and whether it runs (grouped: its graph's gate).
+struct ResidUnit {
+  bool run;
+  int t, pr, kblocks;
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  double* G;
+  size_t gstride;
+};
+__device__ __forceinline__ ResidUnit resid_unit(const ResidMaps& maps, const ResidParams& p, int u) {
+  ResidUnit r;
+  const int e = u / p.npairs;
+  r.pr = u % p.npairs;
+  const int sa = p.pair_s[r.pr] - 1, sz = p.pair_t[r.pr] - 1;
+  if (p.groups) {
+    const uint32_t ud = p.units[e];
+    const ResidGroup& gr = p.groups[ud & 0xFFFF];
+    r.run = gr.gate == nullptr || (*gr.gate & p.gate_mask) != 0;
+    r.t = (int)(ud >> 16);
+    r.kblocks = gr.kblocks;
+    r.ma = &gr.a[sa];
+    r.mb = &gr.b[sz];
+    r.G = gr.G;
+    r.gstride = gr.gstride;
+  } else {
+    r.run = true;
+    r.t = e;
+    r.kblocks = p.kblocks;
+    r.ma = &maps.a[sa];
+    r.mb = &maps.b[sz];
+    r.G = p.G;
+    r.gstride = p.gstride;
+  }
+  return r;
+}
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
@@ -662,7 +703,6 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
   auto pempty_bar = [&](int b) { return bar0 + 8u * (2 * RS_STAGES + RS_NBUF + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * RS_STAGES + 2 * RS_NBUF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nchunks = p.kblocks / RS_CHUNK_KB;
   const uint32_t b_bytes = (uint32_t)p.kp * 128;
 
   if (threadIdx.x == 0) {
@@ -694,11 +734,19 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     int it = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x) {
-      const int t = u / p.npairs, pr = u % p.npairs;
+      const ResidUnit ru = resid_unit(maps, p, u);
+      if (!ru.run) continue;
+      const int t = ru.t;
       {
-        const CUtensorMap* ma = &maps.a[p.pair_s[pr] - 1];
-        const CUtensorMap* mb = &maps.b[p.pair_t[pr] - 1];
-        for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        const CUtensorMap* ma = ru.ma;
+        const CUtensorMap* mb = ru.mb;
+        if (p.groups) {
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma))
+                       : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb))
+                       : "memory");
+        }
+        for (int kb = 0; kb < ru.kblocks; ++kb, ++it) {
           const int s = it % RS_STAGES;
           const uint32_t r = (uint32_t)(it / RS_STAGES);
           if (!mbar_wait(empty_bar(s), (r & 1) ^ 1, abort_flag, p.status)) {
@@ -724,7 +772,10 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     // ------------------------------------------------ MMA issuer: one exact K-chunk per TMEM buffer
     int it = 0, pc = 0;
     bool ok = true, issued = false;
-    for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x)
+    for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x) {
+        const ResidUnit ru = resid_unit(maps, p, u);
+        if (!ru.run) continue;
+        const int nchunks = ru.kblocks / RS_CHUNK_KB;
         for (int c = 0; c < nchunks && ok; ++c, ++pc) {
           const int b = pc % RS_NBUF;
           const uint32_t ph = (uint32_t)(pc / RS_NBUF);
@@ -753,6 +804,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           if (!ok) break;
           mma_commit(pfull_bar(b));
         }
+    }
     if (!ok && issued) {
       mma_commit(drain_bar);
       const unsigned long long t0 = globaltimer();
@@ -769,9 +821,13 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     int pc = 0;
     bool failed = false;
     for (int u = blockIdx.x; u < p.num_tiles * p.npairs; u += gridDim.x) {
-      const int t = u / p.npairs, pr = u % p.npairs;
+      const ResidUnit ru = resid_unit(maps, p, u);
+      if (!ru.run) continue;
+      const int t = ru.t, pr = ru.pr;
+      const int nchunks = ru.kblocks / RS_CHUNK_KB;
       const int row = t * 128 + q * 32 + lane;
-      double* Grow = p.G + (size_t)pr * p.gstride + (size_t)row * p.kp + col0;
+      double* Grow = ru.G + (size_t)pr * ru.gstride + (size_t)row * p.kp + col0;
+      bool first_flush = p.assign != 0;
       {
         const int m = p.pair_s[pr] + p.pair_t[pr];
         const float up = __int_as_float((127 + 8 * m) << 23);   // 2^(8m)
@@ -810,9 +866,10 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
             const double down = ldexp(1.0, -8 * m);
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-              if (c < ncol) Grow[c] += (double)acc[c] * down;
+              if (c < ncol) Grow[c] = (first_flush ? 0.0 : Grow[c]) + (double)acc[c] * down;
               acc[c] = 0;
             }
+            first_flush = false;
           }
         }
       }
@@ -2601,6 +2658,56 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
   CDL_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)p.npairs * np * kp * sizeof(double), ctx->stream));
   const int grid = std::min(p.num_tiles * p.npairs, ctx->sm_count);
   Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * np * kp);
+  k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
+  return L.done();
+}
+
+int resid_group_init(ResidGroup* g, const void* aslices, const void* zslices, double* G, int npad, int kg,
+                     const int* gate) {
+  std::memset(g, 0, sizeof(ResidGroup));
+  if (kg % 32 || kg > 128 || npad % 128) return CDL_ERR_INVALID_ARG;
+  for (int s = 0; s < RS_SLICES; ++s) {
+    CDL_TRY(make_map(&g->a[s], static_cast<const char*>(aslices) + (size_t)s * npad * npad * 2, npad, npad, 128));
+    CDL_TRY(make_map(&g->b[s], static_cast<const char*>(zslices) + (size_t)s * kg * npad * 2, kg, npad, kg));
+  }
+  g->G = G;
+  g->gstride = (size_t)npad * kg;
+  g->gate = gate;
+  g->kblocks = (npad + 255) / 256 * 4;
+  return CDL_OK;
+}
+
+int resid_tc_grouped(cdl_ctx* ctx, const ResidGroup* dgroups, const uint32_t* units, int nunits, int kg,
+                     int gate_mask, double work) {
+  if (kg % 32 || kg > 128) return CDL_ERR_INVALID_ARG;
+  if (nunits == 0) return CDL_OK;
+  ResidMaps maps;   // unused in grouped mode
+  std::memset(&maps, 0, sizeof(maps));
+  ResidParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.num_tiles = nunits;
+  p.kp = kg;
+  for (int m = 2; m <= RS_SLICES + 1; ++m)
+    for (int sa = 1; sa < m; ++sa) {
+      const int sz = m - sa;
+      if (sa > RS_SLICES || sz > RS_SLICES) continue;
+      p.pair_s[p.npairs] = sa;
+      p.pair_t[p.npairs] = sz;
+      ++p.npairs;
+    }
+  p.idesc = make_idesc(kg);
+  p.status = ctx->dev_status;
+  p.groups = dgroups;
+  p.units = units;
+  p.gate_mask = gate_mask;
+  p.assign = 1;
+  static bool attr = false;
+  if (!attr) {
+    CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_BYTES));
+    attr = true;
+  }
+  const int grid = std::min(nunits * p.npairs, ctx->sm_count);
+  Launch L(ctx, CDL_KC_RESIDUAL, work);
   k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
   return L.done();
 }
