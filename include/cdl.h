@@ -563,11 +563,13 @@ typedef struct {
  * Refinement: each graph follows the rules of cdl_chain_solve, decided on
  * the device; the host issues max_iter + 4 step slots (max_iter with
  * CDL_SOLVE_FULL_RESIDUAL), where a slot is one application of the
- * preconditioner or one float-float certification of a recursively updated
- * residual; a graph that has stopped skips the remaining slots.
- * Device buffers of the batch (graphs, chains, embeddings; about
- * sum over graphs of (d + 2) 2 npad^2 + 16 n^2 bytes, npad = n rounded up to
- * 256) are owned by the context and kept for the next call with the same
+ * preconditioner or one certification of a recursively updated residual; a
+ * graph that has stopped skips the remaining slots. Full residuals (first
+ * step, certifications) are formed on the tensor cores from six exact bf16
+ * slices of A and of Z / c, as for a single tensor chain (float64-class).
+ * Device buffers of the batch (graphs, chains, A's slices, embeddings; about
+ * sum over graphs of (2 d + 16) npad^2 + 8 n^2 bytes, npad = n rounded up to
+ * 128) are owned by the context and kept for the next call with the same
  * sizes and options. The call returns after the results are written (it
  * synchronises); it returns CDL_ERR_NOT_CONVERGED (results still written)
  * when any solve missed its tolerance, CDL_ERR_UNSUPPORTED without tcgen05. */
