@@ -132,6 +132,10 @@ def phase_rooflines(kc, n, pk, src, sm_count, sm_mhz):
       apply       bytes of chain levels (and A operands) read        -> HBM
       residual    bf16 slice-product flops of the exact residual     -> bf16 tensor
       score       8 n (n - 1) bytes: the upper halves of float64 A1, A2 -> HBM
+      score_tensor  the same phase against the bf16 flops of its 21 exact
+                  slice products over the upper triangle (library count) -> bf16
+                  tensor: the bound of the exact design (it exceeds the HBM
+                  time at every n)
     A phase's time includes its small helper kernels."""
     hbm = pk.get("hbm_gbs")
     bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
@@ -146,10 +150,11 @@ def phase_rooflines(kc, n, pk, src, sm_count, sm_mhz):
         "apply": ("hbm", None),
         "residual": ("tensor", None),
         "score": ("hbm", 8.0 * n * (n - 1)),
+        "score_tensor": ("tensor", None),
     }
     out = {}
     for name, (bound, work) in spec.items():
-        v = kc.get(name)
+        v = kc.get("score" if name == "score_tensor" else name)
         if not v or not v["ms_per_step"]:
             continue
         if work is None:

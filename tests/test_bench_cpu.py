@@ -59,7 +59,10 @@ def test_phase_rooflines_arithmetic():
           "distance": dict(ms_per_step=4.0, launches=1, work=7.0)}
     pk = {"hbm_gbs": 5000.0, "bf16_tflops_sustained": 1000.0}
     out = bench.phase_rooflines(kc, n, pk, "measured", 100, 2000.0)
-    assert set(out) == {"square", "score", "project", "distance"}
+    assert set(out) == {"square", "score", "score_tensor", "project", "distance"}
+    # the score phase also against the tensor flops the library counts for it
+    assert out["score_tensor"]["bound"] == "tensor" and out["score_tensor"]["work_per_pair"] == 123.0
+    assert abs(out["score_tensor"]["achieved"] - 123.0 / 1e-3 / 1e12) < 1e-15
     assert out["square"]["bound"] == "tensor" and abs(out["square"]["achieved"] - 2000.0) < 1e-9
     assert abs(out["square"]["frac"] - 2.0) < 1e-12
     assert out["score"]["work_per_pair"] == 8.0 * n * (n - 1)
