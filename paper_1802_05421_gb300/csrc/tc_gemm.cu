@@ -1187,7 +1187,8 @@ constexpr int SC_A = 128 * 128;                  // one slice plane: 128 rows x 
 constexpr int SC_B = SC_N * 128;                 // one slice plane: 64 rows x 64 bf16
 constexpr int SC_HALF = SC_SLICES / 2;           // u slices per stage (two stages per K block)
 constexpr int SC_STAGE_BYTES = SC_HALF * SC_A + SC_SLICES * SC_B;   // 3 u planes + all 6 v planes
-constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N;
+constexpr int SC_XPOSE = 32 * 4;                 // per epilogue warp: |A1 - A2| of 32 rows x 4 columns
+constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N + 16 * SC_XPOSE;
 constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + SC_EPI_DOUBLES * 8 + 1024;
 constexpr int SC_NBUF = 8;                     // ring of TMEM accumulators
 constexpr int SC_TMEM_COLS = SC_NBUF * SC_N;
@@ -1415,18 +1416,40 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       const long long di = rowok ? p.dint[row] : 0;
       ff ev[16];
       ff rs = {0.f, 0.f};
+      // |A1 - A2| of the warp's 32 rows x 16 columns, four columns at a time:
+      // loaded with lanes along the columns (each load instruction reads eight
+      // 32-byte row segments instead of 32 single elements of 32 rows), passed
+      // through shared memory to the row-per-lane layout of the drained sums
+      double* xp = epi + 128 * 4 + 4 * SC_N + (warp - 2) * SC_XPOSE;
+      const int rbase = I * 128 + q * 32;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int col = col0 + e;
-        ff x = {0.f, 0.f};
-        if (rowok && col < p.n && (br < J || row < col)) {
-          const long long dc = di + p.dint[col] - m[e];
-          const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
-          const size_t o = (size_t)(row - p.row0) * p.n + col;
-          x = ff_mul(split_nonneg(fabs(p.A1[o] - p.A2[o])), ff_from_u64(adc));
+      for (int jq = 0; jq < 4; ++jq) {
+        __syncwarp();
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+          const int rr = st * 8 + (lane >> 2), cc = jq * 4 + (lane & 3);
+          const int grow = rbase + rr, gcol = col0 + cc;
+          double da = 0.0;
+          if (!failed && grow < p.n && gcol < p.n) {
+            const size_t o = (size_t)(grow - p.row0) * p.n + gcol;
+            da = fabs(p.A1[o] - p.A2[o]);
+          }
+          xp[rr * 4 + (lane & 3)] = da;
         }
-        ev[e] = x;
-        rs = ff_add(rs, x);
+        __syncwarp();
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const int e = jq * 4 + e4;
+          const int col = col0 + e;
+          ff x = {0.f, 0.f};
+          if (rowok && col < p.n && (br < J || row < col)) {
+            const long long dc = di + p.dint[col] - m[e];
+            const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
+            x = ff_mul(split_nonneg(xp[lane * 4 + e4]), ff_from_u64(adc));
+          }
+          ev[e] = x;
+          rs = ff_add(rs, x);
+        }
       }
       rowpart[rl * 4 + part] = (double)rs.hi + (double)rs.lo;
       // column sums over the warp's 32 rows: reduce-scatter, lane pairs end with one column each
