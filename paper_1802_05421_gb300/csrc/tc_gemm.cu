@@ -1535,7 +1535,8 @@ constexpr int S2_STAGES = 6;
 constexpr int S2_HALF = 128 * BK * 2;                  // 16 KiB: 128 rows x 64 bf16
 constexpr int S2_STAGE = 2 * S2_HALF;                  // A half + B half
 constexpr int S2_NBARS = 2 * S2_STAGES + 5;            // full, empty, tfull x2, tempty x2, drain
-constexpr int S2_SMEM_BYTES = S2_STAGES * S2_STAGE + 256 + 1024;
+constexpr int S2_XT_WORDS = 32 * 17;                   // per epilogue warp: a 32 x 32 bf16 chunk, padded rows
+constexpr int S2_SMEM_BYTES = S2_STAGES * S2_STAGE + 256 + 8 * S2_XT_WORDS * 4 + 1024;
 constexpr int S2_TMEM_COLS = 512;
 constexpr int S2_THREADS = 320;                        // producer, MMA issuer, 8 epilogue warps
 constexpr int S2_PACE_MIN_KBLOCKS = 512;               // K pacing from n = 32768 on
@@ -1652,6 +1653,36 @@ __device__ __forceinline__ void square_store32(__nv_bfloat16* C, int npad, int r
       if (col > r) C[(size_t)col * npad + r] = h;
     }
   }
+}
+
+// An off-diagonal 32 x 32 chunk through the warp's staging tile T: rows
+// r0 + lane (one per lane, as drained from TMEM), columns col0 .. col0 + 31.
+// The rows are stored two per instruction (16 lanes x 4 bytes: one 64-byte
+// segment each) and so are the mirrored rows, where stores straight from
+// the row-per-lane layout touch 32 rows per instruction. Same values as
+// square_store32.
+__device__ __forceinline__ void square_store32_staged(__nv_bfloat16* C, int npad, int r0, int col0, int lane,
+                                                      const float (&v)[32], uint32_t* T) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    T[lane * 17 + e] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  __syncwarp();
+  const int w = lane & 15, hl = lane >> 4;
+#pragma unroll
+  for (int it = 0; it < 16; ++it) {
+    const int row = 2 * it + hl;
+    reinterpret_cast<uint32_t*>(C + (size_t)(r0 + row) * npad + col0)[w] = T[row * 17 + w];
+  }
+#pragma unroll
+  for (int it = 0; it < 16; ++it) {
+    const int e = 2 * it + hl;   // mirrored row col0 + e, columns r0 + 2w, r0 + 2w + 1
+    const uint32_t a = T[(2 * w) * 17 + it], b = T[(2 * w + 1) * 17 + it];
+    const uint32_t lo = hl ? (a >> 16) : (a & 0xFFFFu), hi = hl ? (b >> 16) : (b & 0xFFFFu);
+    reinterpret_cast<uint32_t*>(C + (size_t)(col0 + e) * npad + r0)[w] = lo | (hi << 16);
+  }
+  __syncwarp();
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
@@ -1804,6 +1835,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const int row_in_tile = q * 32 + lane;
+    uint32_t* xt = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(bars) + 256) + (warp - 2) * S2_XT_WORDS;
     int tc = 0;
     for (int t = cid; t < p.num_tiles; t += ncl) {
       const int acc = tc & 1;
@@ -1818,7 +1850,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
         float v[32];
         tmem_ld32(taddr + (uint32_t)(c * 32), v);   // every warp loads (.sync.aligned), in range or not
         const int col0 = tq.J * 256 + c * 32;
-        if (r < tq.npad && col0 < tq.npad) square_store32(tq.out, tq.npad, r, col0, tq.I == tq.J, v);
+        if (r - lane < tq.npad && col0 < tq.npad) {   // the warp's 32 rows and 32 columns are all in or all out
+          if (tq.I != tq.J)
+            square_store32_staged(tq.out, tq.npad, r - lane, col0, lane, v, xt);
+          else
+            square_store32(tq.out, tq.npad, r, col0, true, v);
+        }
       }
       tc_fence_before();
       __syncwarp();
