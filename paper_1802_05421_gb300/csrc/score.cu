@@ -331,9 +331,10 @@ __global__ void __launch_bounds__(256) k_tcs_colmax(const double* __restrict__ Z
 }
 
 // g_r = 2^e_r with e_r = floor((E(max|a_r|) - E(max|b_r|)) / 2) (E: binary
-// exponent), so that a / g and b g have maxima within a factor of 4; c = the
-// power of two strictly above every |a / g|, |b g| (cs[0]) and cs[1] =
-// c^2 2^-48, the unit of M and d. One block.
+// exponent), so that a / g and b g have maxima within a factor of 4; c = twice
+// the power of two strictly above every |a / g|, |b g| (cs[0]: every value
+// divided by c is below 1/2) and cs[1] = c^2 2^-48, the unit of M and d. One
+// block.
 __global__ void k_tcs_scales(const unsigned long long* __restrict__ cm, int k, double* __restrict__ g,
                              double* __restrict__ cs) {
   __shared__ int emax[256];
@@ -357,14 +358,14 @@ __global__ void k_tcs_scales(const unsigned long long* __restrict__ cm, int k, d
     int e = -1100;
     for (int t = 0; t < (int)blockDim.x; ++t) e = max(e, emax[t]);
     if (e < -1000) e = 0;                                   // all zero
-    cs[0] = ldexp(1.0, e + 1);                              // 2^E <= max < 2^(E+1) = c
-    cs[1] = ldexp(1.0, 2 * (e + 1) - 48);
+    cs[0] = ldexp(1.0, e + 2);                              // 2^E <= max < 2^(E+1) = c / 2
+    cs[1] = ldexp(1.0, 2 * (e + 2) - 48);
   }
 }
 
 // Six planes (rows x k2p bf16) each of u / c and v / c: signed base-256
-// digits of the values rounded to 2^-48 (|value| < 1: leading digit at most
-// 256, the others 128); zero padded.
+// digits of the values rounded to 2^-48 (|value| < 1/2: every digit at most
+// 128 in magnitude), plane t holding digit t times 2^-8t; zero padded.
 __global__ void __launch_bounds__(256) k_tcs_slice(const double* __restrict__ Z1, const double* __restrict__ Z2,
                                                     const double* __restrict__ vol1, const double* __restrict__ vol2,
                                                     int n, int k, int rows, int k2p, const double* __restrict__ g,

@@ -1164,15 +1164,20 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 // d_i = a_i.b_i and M_ij = a_i.b_j + b_i.a_j = u_i.v_j for the rows
 // u = [a / g | b g] and v = [b g | a / g] (g a power of two per column that
 // balances the two halves; it cancels in every product). u / c and v / c
-// (c a power of two above every entry) are six bf16 slices on the grids
-// 2^-8s (signed base-256 digits of the values rounded to 2^-48: the leading
-// digit at most 256 in magnitude, the others 128). The slice pairs of one
-// weight w = s + t (w = 2 .. 7, 21 pairs) summed over a K-chunk of 128 stay
-// within 2^24 grid steps, so each TMEM buffer holds an exact integer; the
-// epilogue adds each chunk, shifted to the common unit c^2 2^-48, in int64.
-// Per K block two pipeline stages (u slices 1-3, then 4-6, each with all six
-// v slices) feed the six live weight accumulators of the chunk. With d_i in the same unit, Delta c_ij is formed
-// in int64 (no cancellation error beyond the slicing's 2^-49 of |a| |b|),
+// (c twice a power of two above every entry) are six bf16 slices on the
+// grids 2^-8s (signed base-256 digits of the values rounded to 2^-48, each at
+// most 128 in magnitude, so every digit product is at most 2^14). The slice
+// pairs s + t = w of the weights w = 2, 3, 4 and 5 (1, 2, 3 and 4 pairs)
+// summed over a K-chunk of 256 stay within 2^24 grid steps of 2^-8w, so those
+// four TMEM accumulators hold exact integers; the pairs of weights 6 and 7
+// (11 pairs, 21 in all) share a fifth accumulator in plain float32 (the
+// slices carry their 2^-8s scales), whose value is below 2^-23 of the top
+// weight's bound and is rounded to the unit. The epilogue adds each chunk,
+// shifted to the common unit c^2 2^-48, in int64. Per K block two pipeline
+// stages (u slices 1-3 with all six v slices, then u slices 4-6 with v slices
+// 1-3) feed the five live accumulators of the chunk. With d_i in the same unit, Delta c_ij is
+// formed in int64 (no cancellation error beyond the slicing's, about 2^-45
+// of max |u . v|),
 // and E_ij = |A1_ij - A2_ij| |Delta c_ij| and its row and column sums are
 // float64. Tiles are 128 x 64 of the upper block triangle (pairs i < j only);
 // each 64 x 64 sub-block writes its row sums to contrib[partner block][i]
@@ -1188,11 +1193,16 @@ constexpr int SC_B = SC_N * 128;                 // one slice plane: 64 rows x 6
 constexpr int SC_HALF = SC_SLICES / 2;           // u slices per stage (two stages per K block)
 constexpr int SC_STAGE_BYTES = SC_HALF * SC_A + SC_SLICES * SC_B;   // 3 u planes + all 6 v planes
 constexpr int SC_XPOSE = 32 * 4;                 // per epilogue warp: |A1 - A2| of 32 rows x 4 columns
-constexpr int SC_EPI_DOUBLES = 128 * 4 + 4 * SC_N + 16 * SC_XPOSE;
+constexpr int SC_PARTS = 128 * 4 + 4 * SC_N;        // row and column partials of one tile
+constexpr int SC_EPI_DOUBLES = SC_PARTS + 16 * SC_XPOSE + SC_PARTS;   // partials double-buffered
 constexpr int SC_SMEM_BYTES = SC_STAGES * SC_STAGE_BYTES + 512 + SC_EPI_DOUBLES * 8 + 1024;
 constexpr int SC_NBUF = 8;                     // ring of TMEM accumulators
 constexpr int SC_TMEM_COLS = SC_NBUF * SC_N;
-constexpr int SC_CHUNK_KB = 2;                   // 128 K per exact chunk
+constexpr int SC_CHUNK_KB = 4;                   // 256 K per exact chunk
+constexpr int SC_NW = 5;                         // accumulators per chunk: weights 2, 3, 4, 5 and 6-7
+
+// accumulator of a slice pair's weight w = s + t within a chunk
+__device__ __forceinline__ int sc_slot(int w) { return w < 6 ? w - 2 : 4; }
 
 struct ScoreMaps {
   CUtensorMap u[SC_SLICES];   // slices of u, box 64 x 128 rows
@@ -1268,7 +1278,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------ TMA producer: per K block two stages, u slices
-    // 1-3 then 4-6, each with all six v slices
+    // 1-3 with v slices 1-6, then u slices 4-6 with v slices 1-3
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
@@ -1283,10 +1293,12 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
             break;
           }
           const uint32_t dst = smem_u32(smem + s * SC_STAGE_BYTES);
-          mbar_expect_tx(full_bar(s), SC_STAGE_BYTES);
+          // u slices 4-6 pair with v slices 1-3 only (s + t <= 7)
+          const int nv = h == 0 ? SC_SLICES : SC_SLICES + 1 - (SC_HALF + 1);
+          mbar_expect_tx(full_bar(s), SC_HALF * SC_A + nv * SC_B);
           for (int pl = 0; pl < SC_HALF; ++pl)
             tma_load_2d(dst + pl * SC_A, &maps.u[h * SC_HALF + pl], kb * 64, I * 128, full_bar(s));
-          for (int pl = 0; pl < SC_SLICES; ++pl)
+          for (int pl = 0; pl < nv; ++pl)
             tma_load_2d(dst + SC_HALF * SC_A + pl * SC_B, &maps.v[pl], kb * 64, J * SC_N, full_bar(s));
         }
     }
@@ -1299,9 +1311,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------ MMA issuer: per K chunk, the six weight
-    // accumulators w = 2 .. 7 (ring slots pc .. pc + 5) take the 21 slice products of each K block
-    constexpr int NW = SC_SLICES;                        // weights 2 .. SC_SLICES + 1
+    // ------------------------------------------------ MMA issuer: per K chunk, the five
+    // accumulators (ring slots pc .. pc + 4) take the 21 slice products of each K block
+    constexpr int NW = SC_NW;
     int it = 0, pc = 0;
     bool ok = true, issued = false;
     for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x)
@@ -1327,9 +1339,10 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
               const int sa = h * SC_HALF + pl + 1;         // u slice, 1-based
               for (int sb = 1; sa + sb <= SC_SLICES + 1; ++sb) {
                 const int w = sa + sb;                     // 2 .. 7
-                const uint32_t d_tmem = tmem_base + (uint32_t)(((pc + w - 2) % SC_NBUF) * SC_N);
-                // the first product of a weight in the chunk (u slice 1) starts its accumulator
-                const bool first = first_kb && sa == 1;
+                const uint32_t d_tmem = tmem_base + (uint32_t)(((pc + sc_slot(w)) % SC_NBUF) * SC_N);
+                // the first product of an accumulator in the chunk (u slice 1; for weights
+                // 6 and 7 the pair (1, 5)) starts it
+                const bool first = first_kb && sa == 1 && sb <= 5;
                 const uint64_t adesc = smem_desc(base + pl * SC_A);
                 const uint64_t bdesc = smem_desc(base + SC_HALF * SC_A + (sb - 1) * SC_B);
 #pragma unroll
@@ -1356,8 +1369,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     const int part = (warp - 2) >> 2;                    // 16-column part of the tile
     const int et = threadIdx.x - 64;                     // epilogue thread 0 .. 511
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    double* rowpart = epi;                               // [128][4]
-    double* colpart = epi + 128 * 4;                     // [4][64]
+    // partials of even tiles at epi, of odd tiles past the transposition buffers, so
+    // one barrier per tile separates their writes from their reads
+    int tpar = 0;
     const double osc = *p.oscale;
     int pc = 0;
     bool failed = false;
@@ -1375,14 +1389,16 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(p.A2 + o1));
         }
       }
+      // d_j of the warp's 16 columns, one per lane (lanes 16-31 repeat them)
+      const long long dcol = p.dint[J * SC_N + part * 16 + (lane & 15)];
       long long m[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) m[e] = 0;
-      // drains in the ring order of the MMA issuer: K chunk outer, weight inner; each
-      // exact chunk sum goes to the unit c^2 2^-48 (weight 7 rounded there: below
-      // one unit per chunk)
+      // drains in the ring order of the MMA issuer: K chunk outer, accumulator inner;
+      // each chunk sum goes to the unit c^2 2^-48 (the exact weights 2-5 shifted
+      // there, the float32 sum of weights 6 and 7 rounded there)
       for (int c = 0; c < nchunks; ++c)
-        for (int w = 2; w <= SC_SLICES + 1; ++w, ++pc) {
+        for (int a = 0; a < SC_NW; ++a, ++pc) {
           if (failed) continue;
           const int b = pc % SC_NBUF;
           const uint32_t ph = (uint32_t)(pc / SC_NBUF);
@@ -1391,16 +1407,15 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
             continue;
           }
           tc_fence_after();
-          const float up = __int_as_float((127 + 8 * w) << 23);   // 2^(8w)
-          const int sh = 48 - 8 * w;
+          // weight w = a + 2 for the exact accumulators: 2^(8w) makes the sum an integer
+          // (|x| <= 2^24), shifted by 48 - 8w; the last one times 2^48 is below 2^31
+          const float up = __int_as_float((127 + (a < 4 ? 8 * (a + 2) : 48)) << 23);
+          const int sh = a < 4 ? 48 - 8 * (a + 2) : 0;
           {
             float v[16];   // one load and one wait per drain
             tmem_ld16(tmem_base + lane_off + (uint32_t)(b * SC_N + part * 16), v);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const long long x = __float2int_rn(v[e] * up);
-              m[e] += sh >= 0 ? x * (1LL << sh) : (x + (1LL << (-sh - 1))) >> (-sh);
-            }
+            for (int e = 0; e < 16; ++e) m[e] += (long long)__float2int_rn(v[e] * up) * (1LL << sh);
           }
           tc_fence_before();
           mbar_arrive(pempty_bar(b));
@@ -1420,7 +1435,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
       // loaded with lanes along the columns (each load instruction reads eight
       // 32-byte row segments instead of 32 single elements of 32 rows), passed
       // through shared memory to the row-per-lane layout of the drained sums
-      double* xp = epi + 128 * 4 + 4 * SC_N + (warp - 2) * SC_XPOSE;
+      double* xp = epi + SC_PARTS + (warp - 2) * SC_XPOSE;
       const int rbase = I * 128 + q * 32;
 #pragma unroll
       for (int jq = 0; jq < 4; ++jq) {
@@ -1442,8 +1457,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           const int e = jq * 4 + e4;
           const int col = col0 + e;
           ff x = {0.f, 0.f};
+          const long long dj = __shfl_sync(0xffffffffu, dcol, e);   // converged: the whole warp
           if (rowok && col < p.n && (br < J || row < col)) {
-            const long long dc = di + p.dint[col] - m[e];
+            const long long dc = di + dj - m[e];
             const unsigned long long adc = dc < 0 ? (unsigned long long)(-dc) : (unsigned long long)dc;
             x = ff_mul(split_nonneg(xp[lane * 4 + e4]), ff_from_u64(adc));
           }
@@ -1451,6 +1467,9 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           rs = ff_add(rs, x);
         }
       }
+      double* rowpart = epi + tpar * (SC_PARTS + 16 * SC_XPOSE);   // [128][4]
+      double* colpart = rowpart + 128 * 4;                          // [4][64]
+      tpar ^= 1;
       rowpart[rl * 4 + part] = (double)rs.hi + (double)rs.lo;
       // column sums over the warp's 32 rows: reduce-scatter, lane pairs end with one column each
 #pragma unroll
@@ -1499,7 +1518,6 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
         if (col < p.n && b2 < J)
           p.contrib[(size_t)b2 * p.n + col] = (colpart[(2 * hh) * SC_N + c] + colpart[(2 * hh + 1) * SC_N + c]) * osc;
       }
-      asm volatile("bar.sync 1, 512;" ::: "memory");
     }
   }
 
