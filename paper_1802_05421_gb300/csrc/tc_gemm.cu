@@ -134,6 +134,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+// The same load with an L2 eviction policy (createpolicy), for operands that
+// many CTAs read again later and should outlive streamed data in L2.
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -733,6 +748,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
     // ------------------------------------------------ TMA producer
     int it = 0;
     bool ok = true;
+    const uint64_t zpol = l2_policy_evict_last();
     for (int u = blockIdx.x; u < p.num_tiles * p.npairs && ok; u += gridDim.x) {
       const ResidUnit ru = resid_unit(maps, p, u);
       if (!ru.run) continue;
@@ -756,7 +772,8 @@ __global__ void __launch_bounds__(T8_THREADS, 1)
           const uint32_t a_dst = smem_u32(smem + s * RS_STAGE_BYTES);
           mbar_expect_tx(full_bar(s), RS_A + b_bytes);
           tma_load_2d(a_dst, ma, kb * 64, t * 128, full_bar(s));
-          tma_load_2d(a_dst + RS_A, mb, kb * 64, 0, full_bar(s));
+          // every unit reads a whole Z slice: keep the Z slices in L2 while the A slices stream
+          tma_load_2d_hint(a_dst + RS_A, mb, kb * 64, 0, full_bar(s), zpol);
         }
       }
     }
