@@ -1239,18 +1239,6 @@ struct ScoreParams {
   unsigned* status;
 };
 
-__device__ __forceinline__ int sc_pairs(int w, int (&ps)[SC_SLICES], int (&pt)[SC_SLICES]) {
-  int c = 0;
-  for (int sa = 1; sa <= SC_SLICES; ++sa) {
-    const int sb = w - sa;
-    if (sb >= 1 && sb <= SC_SLICES) {
-      ps[c] = sa - 1;
-      pt[c] = sb - 1;
-      ++c;
-    }
-  }
-  return c;
-}
 
 __global__ void __launch_bounds__(T8_THREADS, 1)
     k_tc_score(const __grid_constant__ ScoreMaps maps, const ScoreParams p) {
@@ -1662,40 +1650,20 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
-// Rows r of a 128 x 256 accumulator chunk of 32 columns to the bf16 level:
-// off the diagonal block the row segment and its mirror, on it the upper
-// triangle and its mirror.
-__device__ __forceinline__ void square_store32(__nv_bfloat16* C, int npad, int r, int col0, bool diag,
-                                               const float (&v)[32]) {
-  if (!diag) {
-    uint32_t packed[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-      packed[e] = *reinterpret_cast<uint32_t*>(&h);
-    }
-    uint4* dst = reinterpret_cast<uint4*>(C + (size_t)r * npad + col0);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) dst[e] = make_uint4(packed[4 * e], packed[4 * e + 1], packed[4 * e + 2], packed[4 * e + 3]);
-#pragma unroll
-    for (int e = 0; e < 32; ++e) C[(size_t)(col0 + e) * npad + r] = __float2bfloat16_rn(v[e]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-      const int col = col0 + e;
-      const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
-      if (col >= r) C[(size_t)r * npad + col] = h;
-      if (col > r) C[(size_t)col * npad + r] = h;
-    }
-  }
-}
+// A 32 x 32 chunk (rows r0 .., columns col0 ..) of a block on the diagonal:
+// above the diagonal as any other chunk (rows and mirrored rows, staged);
+// below it nothing (the mirror of the chunk above writes it); the chunk the
+// diagonal crosses (col0 == r0) through shared memory too, its upper
+// triangle row by row and its strict upper triangle mirrored, each store
+// instruction covering 32 consecutive columns of one row.
+__device__ __forceinline__ void square_store32_diag(__nv_bfloat16* C, int npad, int r0, int col0, int lane,
+                                                    const float (&v)[32], uint32_t* T);
 
 // An off-diagonal 32 x 32 chunk through the warp's staging tile T: rows
 // r0 + lane (one per lane, as drained from TMEM), columns col0 .. col0 + 31.
 // The rows are stored two per instruction (16 lanes x 4 bytes: one 64-byte
 // segment each) and so are the mirrored rows, where stores straight from
-// the row-per-lane layout touch 32 rows per instruction. Same values as
-// square_store32.
+// the row-per-lane layout touch 32 rows per instruction.
 __device__ __forceinline__ void square_store32_staged(__nv_bfloat16* C, int npad, int r0, int col0, int lane,
                                                       const float (&v)[32], uint32_t* T) {
 #pragma unroll
@@ -1717,6 +1685,30 @@ __device__ __forceinline__ void square_store32_staged(__nv_bfloat16* C, int npad
     const uint32_t lo = hl ? (a >> 16) : (a & 0xFFFFu), hi = hl ? (b >> 16) : (b & 0xFFFFu);
     reinterpret_cast<uint32_t*>(C + (size_t)(col0 + e) * npad + r0)[w] = lo | (hi << 16);
   }
+  __syncwarp();
+}
+__device__ __forceinline__ void square_store32_diag(__nv_bfloat16* C, int npad, int r0, int col0, int lane,
+                                                    const float (&v)[32], uint32_t* T) {
+  if (col0 >= r0 + 32) {
+    square_store32_staged(C, npad, r0, col0, lane, v, T);
+    return;
+  }
+  if (col0 + 32 <= r0) return;
+  // col0 == r0: this lane holds row r0 + lane; T[row * 17 + c / 2] holds columns c, c + 1
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    T[lane * 17 + e] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  __syncwarp();
+  auto elem = [&](int row, int col) {
+    const uint32_t w = T[row * 17 + (col >> 1)];
+    return __ushort_as_bfloat16((unsigned short)((col & 1) ? (w >> 16) : (w & 0xFFFFu)));
+  };
+  for (int row = 0; row < 32; ++row)   // row r0 + row, columns col0 + lane >= that row
+    if (lane >= row) C[(size_t)(r0 + row) * npad + col0 + lane] = elem(row, lane);
+  for (int m = 1; m < 32; ++m)         // mirrored row col0 + m, columns r0 + lane < that row
+    if (lane < m) C[(size_t)(col0 + m) * npad + r0 + lane] = elem(lane, m);
   __syncwarp();
 }
 
@@ -1889,7 +1881,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
           if (tq.I != tq.J)
             square_store32_staged(tq.out, tq.npad, r - lane, col0, lane, v, xt);
           else
-            square_store32(tq.out, tq.npad, r, col0, true, v);
+            square_store32_diag(tq.out, tq.npad, r - lane, col0, lane, v, xt);
         }
       }
       tc_fence_before();
