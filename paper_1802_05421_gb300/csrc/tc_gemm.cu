@@ -1901,6 +1901,187 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- chain application on CTA pairs
+// x <- level x for one level, as k_tc_gemm's apply mode computes it (float
+// partial products per split of K, summed by the update kernel), with
+// tcgen05.mma.cta_group::2: the two CTAs of a cluster compute a 256-row block
+// of one split, each CTA's 128 rows in its TMEM. Per 64-wide k-block CTA rank
+// r stages its 128 rows of the level (16 KB) and rows r bn / 2 .. (r + 1)
+// bn / 2 of the right-hand-side operand (the pair's B operand is split
+// between the two CTAs, at most 16 KB), so a stage is at most 32 KB and six
+// stages fit: twice the level bytes in flight of the one-CTA kernel's four
+// 48 KB stages (the level streams from HBM). Barriers as in k_tc_sq2.
+struct Apply2Params {
+  int num_units;   // 256-row blocks x splits (block-major)
+  int splits;
+  int kblocks;     // k-blocks per split
+  int npad;
+  int bn;          // N = 2 kp (hi and lo halves of the right-hand sides)
+  uint32_t idesc;  // kind::f16, M = 256, N = bn
+  float* out;      // splits x npad x bn partial products
+  unsigned* status;
+};
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S2_THREADS, 1)
+    k_tc_apply2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const Apply2Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S2_STAGES * S2_STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S2_NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S2_NBARS + 1);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S2_STAGES + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * S2_STAGES + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S2_STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const uint32_t lead_bar0 = mapa_rank(bar0, 0);   // the rank-0 CTA's barriers, cluster addresses
+  const int bhalf = p.bn / 2;
+  const uint32_t b_bytes = (uint32_t)bhalf * 128;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S2_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(bar0 + 8u * (2 * S2_STAGES + 2 + a), 16);   // tempty: the eight epilogue warps of each CTA
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // one warp of each CTA allocates the pair's TMEM
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S2_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync_all();   // both CTAs' barriers initialised before any remote signal
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer (both CTAs)
+    int it = 0;
+    bool ok = true;
+    for (int u = cid; u < p.num_units && ok; u += ncl) {
+      const int m = u / p.splits, split = u % p.splits;
+      const int a_row = m * 256 + (int)rank * 128, b_row = (int)rank * bhalf;
+      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        const int s = it % S2_STAGES;
+        if (!mbar_wait(empty_bar(s), ((uint32_t)(it / S2_STAGES) & 1) ^ 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        if (rank == 0) mbar_expect_tx(full_bar(s), 2 * (S2_HALF + b_bytes));   // both CTAs' copies
+        const uint32_t dst = smem_u32(smem + s * S2_STAGE);
+        const uint32_t fb = lead_bar0 + 8u * s;
+        const int kx = (split * p.kblocks + kb) * BK;
+        tma_load_2d_pair(dst, &tmA, kx, a_row, fb);
+        tma_load_2d_pair(dst + S2_HALF, &tmB, kx, b_row, fb);
+      }
+    }
+    if (ok) {
+      // the last releases of every stage (MMA commits multicast to this CTA)
+      for (int j = it; j < it + S2_STAGES && ok; ++j)
+        if (!mbar_wait(empty_bar(j % S2_STAGES), ((uint32_t)(j / S2_STAGES) & 1) ^ 1, abort_flag, p.status)) ok = false;
+    }
+    if (!ok) {   // copies already issued land within microseconds: give them time (bounded)
+      const unsigned long long t0 = globaltimer();
+      while (globaltimer() - t0 < 50000ull) {
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------ MMA issuer (rank 0 for the pair)
+    int it = 0, tc = 0;
+    bool ok = true, issued = false;
+    for (int u = cid; u < p.num_units && ok; u += ncl) {
+      const int acc = tc & 1;
+      const uint32_t ar = (uint32_t)(tc >> 1);
+      ++tc;
+      if (!mbar_wait(bar0 + 8u * (2 * S2_STAGES + 2 + acc), (ar & 1) ^ 1, abort_flag, p.status)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
+      for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+        const int s = it % S2_STAGES;
+        if (!mbar_wait(full_bar(s), (uint32_t)(it / S2_STAGES) & 1, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(smem + s * S2_STAGE);
+        const uint64_t adesc = smem_desc(a_addr);
+        const uint64_t bdesc = smem_desc(a_addr + S2_HALF);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16_pair(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), p.idesc, (kb | kk) != 0);
+        issued = true;
+        mma_commit_pair(empty_bar(s));
+      }
+      if (!ok) break;
+      mma_commit_pair(tfull_bar(acc));
+    }
+    if (!ok && issued) {
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain_bar)
+                   : "memory");
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer() - t0 < WAIT_LIMIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue (both CTAs: 128 rows each; two
+    // warps per TMEM lane quarter, half of the columns each)
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row_in_tile = q * 32 + lane;
+    const int nchunk = p.bn / 64;   // 32-column chunks per warp
+    int tc = 0;
+    for (int u = cid; u < p.num_units; u += ncl) {
+      const int acc = tc & 1;
+      const uint32_t ar = (uint32_t)(tc >> 1);
+      ++tc;
+      if (!mbar_wait(tfull_bar(acc), ar & 1, abort_flag, p.status)) break;
+      tc_fence_after();
+      const int m = u / p.splits, split = u % p.splits;
+      const int r = m * 256 + (int)rank * 128 + row_in_tile;
+      const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
+      float* P = p.out + ((size_t)split * p.npad + r) * p.bn;
+      const bool in = r - lane < p.npad;   // the warp's 32 rows are all in or all past the padded order
+      for (int c = half * nchunk; c < half * nchunk + nchunk; ++c) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(c * 32), v);   // every warp loads (.sync.aligned)
+        if (in) {
+          float4* dst = reinterpret_cast<float4*>(P + c * 32);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_bar0 + 8u * (2 * S2_STAGES + 2 + acc));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();   // neither CTA leaves (or frees TMEM) while the pair still works
+  tc_fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S2_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- e4m3 squaring, hardware block scaling
 // S~^2 for an e4m3 level with one power-of-two scale 2^e per 128 x 128 tile,
 // on tcgen05.mma kind::mxf8f6f4 with block scaling: the tensor core applies
@@ -2980,6 +3161,31 @@ int apply_tc_mat(cdl_ctx* ctx, const void* amat, int np, const void* xop, float*
   if (bn % 32 || bn < 32 || bn > MAX_BN) return CDL_ERR_UNSUPPORTED;
   const int mb = np / BM;
   if ((np / BK) % splits) return CDL_ERR_INVALID_ARG;
+  const int ncl = pair_clusters(ctx);
+  if (ncl > 0 && bn % 64 == 0) {
+    // CTA pairs: 256-row blocks, each CTA staging half of the right-hand-side operand
+    static bool attr = false;
+    if (!attr) {
+      CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_apply2, cudaFuncAttributeMaxDynamicSharedMemorySize, S2_SMEM_BYTES));
+      attr = true;
+    }
+    CUtensorMap ma, mbm;
+    CDL_TRY(make_map(&ma, amat, np, np, 128));
+    CDL_TRY(make_map(&mbm, xop, bn, np, bn / 2));
+    Apply2Params p{};
+    p.num_units = ((np + 255) / 256) * splits;
+    p.splits = splits;
+    p.kblocks = np / BK / splits;
+    p.npad = np;
+    p.bn = bn;
+    p.idesc = make_idesc_m256(bn);
+    p.out = partial;
+    p.status = ctx->dev_status;
+    const int clusters = std::min(p.num_units, ncl);
+    Launch L(ctx, CDL_KC_APPLY, 2.0 * np * (double)np);
+    k_tc_apply2<<<2 * clusters, S2_THREADS, S2_SMEM_BYTES, ctx->stream>>>(ma, mbm, p);
+    return L.done();
+  }
   const uint32_t* tiles;
   int count;
   CDL_TRY(get_tiles(ctx, "tc.apply." + std::to_string(mb) + "." + std::to_string(splits),
