@@ -122,7 +122,10 @@ def test_graph_field_workload(G):
 
 # ------------------------------------------------------------------ projection
 
-@pytest.mark.parametrize("n,k,seed", [(50, 1, 1), (97, 5, 2), (300, 32, 3), (200, 130, 2 ** 40 + 7)])
+@pytest.mark.parametrize("n,k,seed", [(50, 1, 1), (97, 5, 2), (300, 32, 3), (200, 130, 2 ** 40 + 7),
+                                      # k of the benchmarks and beyond: ragged row blocks and edge
+                                      # tiles, two 128-row Philox blocks per edge
+                                      (300, 128, 4), (211, 192, 5), (77, 256, 2 ** 33 + 1)])
 def test_projection_matches_oracle(G, n, k, seed):
     X = iid_pair(n, 16, 1, seed=n + k).X[0]
     Ao, *_ = O.gaussian_graph(X)
@@ -130,6 +133,17 @@ def test_projection_matches_oracle(G, n, k, seed):
     Yo = O.project(Ao, seed, k)
     assert np.abs(Y - Yo).max() <= 1e-12 * np.abs(Yo).max()
     assert np.abs(Y.sum(0)).max() <= 1e-11 * np.abs(Yo).max()
+
+
+def test_projection_scales_with_weights_k128(G):
+    """The piece grids follow sqrt(max A): weights four times larger (max A
+    above 1) give exactly twice the projection at the benchmark's k = 128."""
+    X = iid_pair(260, 16, 1, seed=41).X[0]
+    Ao, *_ = O.gaussian_graph(X)
+    A = torch.from_numpy(Ao).cuda()
+    Y = _h(G.project(A, 128, 9))
+    Y4 = _h(G.project(4.0 * A, 128, 9))
+    assert np.array_equal(Y4, 2.0 * Y)
 
 
 # ------------------------------------------------------------------ chain
