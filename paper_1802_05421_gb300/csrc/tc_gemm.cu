@@ -2918,12 +2918,12 @@ int resid_tc(cdl_ctx* ctx, const cdl_chain* ch, const void* zslices, int kp, dou
   p.gstride = (size_t)np * kp;
   p.idesc = make_idesc(kp);
   p.status = ctx->dev_status;
+  p.assign = 1;   // every element of every plane belongs to one unit: its first flush stores it
   static bool attr = false;
   if (!attr) {
     CDL_CUDA_TRY(cudaFuncSetAttribute(k_tc_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_BYTES));
     attr = true;
   }
-  CDL_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)p.npairs * np * kp * sizeof(double), ctx->stream));
   const int grid = std::min(p.num_tiles * p.npairs, ctx->sm_count);
   Launch L(ctx, CDL_KC_RESIDUAL, 2.0 * p.npairs * (double)np * np * kp);
   k_tc_resid<<<grid, T8_THREADS, RS_SMEM_BYTES, ctx->stream>>>(maps, p);
