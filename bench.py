@@ -173,7 +173,7 @@ def phase_rooflines(kc, n, pk, src, sm_count, sm_mhz):
     return out
 
 
-def config1_oracle_full():
+def oracle_full_pair_n1024():
     """The float64 oracle on the whole of the small pair (n = 1024, T = 64,
     k = 32, top-10; exact embeddings), timed in full: a CPU baseline that is
     measured, not extrapolated."""
@@ -265,7 +265,7 @@ def run_reference(args):
             est.append(t)
     sec = statistics.median(est)        # extrapolated seconds for one whole pair
     value = 1.0 / sec
-    c1_sec, _, _ = config1_oracle_full()
+    c1_sec, _, _ = oracle_full_pair_n1024()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.median(walls) * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -628,12 +628,12 @@ C5_METRIC = "graph pairs/s at n=131072 (graphs regenerated in row panels, chain 
 C5_K, C5_D, C5_TOPK = 192, 10, 100
 
 
-def config5_workload():
+def field_pair_n131072():
     from workloads import field_sequence
     return field_sequence(256, 512, 365, 2, patch=16, patch_transition=0, seasonal=0.5, seed=5)
 
 
-def run_config5(args):
+def run_larger_than_hbm(args):
     """The larger-than-memory form at its own size: one pair at n = 131072
     (256 x 512 grid, T = 365 field samples plus a seasonal sinusoid, a
     planted 16 x 16 patch), k = 192, d = 10, bf16 levels (as many as fit on
@@ -647,7 +647,7 @@ def run_config5(args):
     from paper_1802_05421_gb300 import build as B
     B.build()
     from paper_1802_05421_gb300 import cdl
-    wl = config5_workload()
+    wl = field_pair_n131072()
     n, T = wl.X[0].shape
     stream = torch.cuda.Stream()
     st, ctx = cdl.cdl_ctx_create(0, stream.cuda_stream, 0)
@@ -670,7 +670,7 @@ def run_config5(args):
     call()
     torch.cuda.synchronize()
     first_s = time.perf_counter() - t0
-    steps = max(1, args.c5_steps)
+    steps = max(1, args.large_steps)
     _, l0 = cdl.cdl_ctx_launch_count(ctx)
     sampler = ClockSampler(0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1071,7 +1071,7 @@ def main():
                     help="run a small single-kernel case for a profiler capture instead of the bench")
     ap.add_argument("--n", type=int, default=12288)
     ap.add_argument("--reps", type=int, default=1)
-    ap.add_argument("--c5-steps", type=int, default=1, help="timed pairs of --workload larger-than-hbm")
+    ap.add_argument("--large-steps", type=int, default=1, help="timed pairs of --workload larger-than-hbm")
     ap.add_argument("--workload", default="pair",
                     choices=["pair", "batched", "host-levels", "gmm", "sequence", "larger-than-hbm"],
                     help="pair: the n = 32768 field pair (default); batched: 64 ragged pairs; "
@@ -1093,7 +1093,7 @@ def main():
     if args.workload == "gmm":
         return run_gmm(args)
     if args.workload == "larger-than-hbm":
-        return run_config5(args)
+        return run_larger_than_hbm(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1307,7 +1307,7 @@ def main():
             cpu = {"value": 1.0 / sec, "unit": "pairs/s", "cores": cpu_cores(), "kind": "oracle",
                    "sample": desc, "seconds_per_pair": sec, "value_basis": "extrapolated from the sample",
                    "phases_s": {k: round(v, 2) for k, v in phases.items()}}
-            c1_sec, c1_top, _ = config1_oracle_full()
+            c1_sec, c1_top, _ = oracle_full_pair_n1024()
             cpu["measured_full_pair_n1024"] = {"workload": "iid_n1024 (n = 1024, T = 64, k = 32, top-10, "
                                                            "exact embeddings)",
                                                "seconds": c1_sec, "pairs_per_s": 1.0 / c1_sec}

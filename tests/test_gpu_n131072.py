@@ -35,7 +35,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.fullsize]
 K, DCH, SEED, TOPK, TOL = 192, 10, 2024, 100, 1e-10
 
 
-def config5_workload():
+def field_pair_n131072():
     return field_sequence(256, 512, 365, 2, patch=16, patch_transition=0, seasonal=0.5, seed=5)
 
 
@@ -47,7 +47,7 @@ def test_field_pair_n131072_regenerated_graphs():
     torch.cuda.empty_cache()
     G = Ctx(lib())
     cdl = G.cdl
-    wl = config5_workload()
+    wl = field_pair_n131072()
     n, T = wl.X[0].shape
     flags = cdl.CDL_PAIR_REGEN_GRAPHS | cdl.CDL_CHAIN_HOST_LEVELS | cdl.CDL_CHAIN_RESIDENT(255)
     try:
