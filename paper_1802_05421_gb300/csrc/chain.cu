@@ -49,10 +49,6 @@ template <>
 __device__ __forceinline__ double to_level<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ float to_level<float>(double v) { return (float)v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_level<__nv_bfloat16>(double v) {
-  return __float2bfloat16_rn((float)v);
-}
 
 // S~_0[i][j] = A_ij (rsd_i rsd_j) - u_i u_j (float64 arithmetic, each product
 // formed symmetrically in i and j so the level is exactly symmetric), zero padded.
